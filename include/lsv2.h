@@ -1,0 +1,206 @@
+/*
+ * lsv2.h -- C ABI of the B300 (sm_103a) sparse-coefficient Gaussian splatting library.
+ *
+ * The library implements the rendering and query path of LangSplatV2 (arXiv 2507.07136):
+ * every 3D Gaussian carries, per semantic level, K (index, weight) pairs over an L-entry
+ * codebook S of D-dim language features (Sec. 3.3, Eq. 5).  The path is
+ *
+ *   lsv2_project       Gaussians -> 2D means, conics, tile rectangles, depth keys
+ *                      (Sec. 3.1, Eq. 1-2 and EWA projection)
+ *   lsv2_bin_sort      per-tile lists ordered by depth ("ordered Gaussian points within a
+ *                      tile", Eq. 3)
+ *   lsv2_splat_coeffs  front-to-back alpha blending of only the K nonzero coefficients into
+ *                      an L-dim coefficient map per pixel and level (Sec. 3.4, Algorithm 1;
+ *                      weights e_i of Eq. 7)
+ *   lsv2_decode        F = W S per level (Eq. 7)
+ *   lsv2_query         relevancy of each pixel for text queries (Sec. 3.2), computed through
+ *                      the linearity of Eq. 7 without materialising F
+ *   lsv2_splat_backward, lsv2_l1_decode_backward
+ *                      gradients of an L1 feature loss (no counterpart in the paper, which
+ *                      trains the field but does not describe its gradient)
+ *
+ * Conventions shared by every entry point:
+ *   - All array pointers are DEVICE pointers owned by the caller, unless a parameter says
+ *     otherwise.  The library never allocates device memory; scratch space is passed in as
+ *     a workspace sized by the matching *_workspace_bytes query.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Every call is
+ *     stream-ordered and asynchronous; no call synchronises the host.
+ *   - Errors found on the host (null pointers, sizes, unsupported shapes) are returned
+ *     immediately and nothing is launched.  Conditions found on the device are written to
+ *     `*dev_status` (an int32 in device memory the caller zeroes): the first nonzero
+ *     lsv2_status wins; kernels never trap.  LSV2_ERR_CUDA reports a launch error.
+ *   - Pixel (i, j) is evaluated at image-plane point (i, j).  Images are row-major.
+ *   - Constants of the 3DGS rasteriser the paper builds on: 0.3 px^2 dilation, screen
+ *     radius ceil(3 sqrt(lambda_max)), guard band 1.3 tan(fov/2), alpha clamp 0.99,
+ *     skip alpha < 1/255, stop before a Gaussian that would take T below 1e-4.  All
+ *     thresholds are float32 values.
+ */
+#ifndef LSV2_H
+#define LSV2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LSV2_ABI_VERSION 1
+
+typedef enum {
+    LSV2_OK = 0,
+    LSV2_ERR_INVALID_ARGUMENT = 1,
+    LSV2_ERR_UNSUPPORTED = 2,
+    LSV2_ERR_CAPACITY = 3,  /* more Gaussian-tile instances than the caller's capacity */
+    LSV2_ERR_CUDA = 4,      /* a CUDA launch or runtime call failed */
+    LSV2_ERR_TIMEOUT = 5,   /* a bounded device-side wait ran out */
+    LSV2_ERR_NONFINITE = 6
+} lsv2_status;
+
+typedef enum { LSV2_F32 = 0, LSV2_BF16 = 1 } lsv2_dtype;
+
+/* Pinhole camera.  World -> camera: t = R m + t0 (x right, y down, z forward).
+ * Supported tiles: 16x16 (default), 8x8, 32x8. */
+typedef struct {
+    int32_t width, height;
+    int32_t tile_w, tile_h;
+    float fx, fy, cx, cy;
+    float near_z;
+    float R[9]; /* row-major */
+    float t[3];
+} lsv2_camera;
+
+/* Per-Gaussian outputs of lsv2_project (device arrays of n entries each, caller-owned).
+ *   xy       float[n][4]  2D mean as an unevaluated float pair: u = u_hi + u_lo,
+ *                         v = v_hi + v_lo, stored (u_hi, v_hi, u_lo, v_lo)
+ *   conic_o  float[n][4]  (a, b, c, opacity); [[a, b], [b, c]] is the inverse of the
+ *                         dilated 2D covariance
+ *   extent   float[n][2]  half-widths (px) of the bounding box of the ellipse on which
+ *                         alpha >= 1/255; negative when no pixel can reach 1/255
+ *   depth    float[n]     depth key (camera-space z)
+ *   radius   int32[n]     screen radius, ceil(3 sqrt(lambda_max))
+ *   rect     int32[n][4]  tile rectangle x0, y0, x1, y1 (max exclusive)
+ *   tiles_touched uint32[n]  (x1 - x0) (y1 - y0), 0 when not visible
+ *   flags    uint8[n]     bit0 visible, bit1 near-degenerate (FP64 decisions)
+ * All arrays must be 16-byte aligned. */
+typedef struct {
+    float* xy;
+    float* conic_o;
+    float* extent;
+    float* depth;
+    int32_t* radius;
+    int32_t* rect;
+    uint32_t* tiles_touched;
+    uint8_t* flags;
+} lsv2_proj;
+
+int32_t lsv2_abi_version(void);
+const char* lsv2_status_string(lsv2_status s);
+
+/* Project n Gaussians (Sec. 3.1, Eq. 1-2, EWA splatting).
+ * means float[n][3], scales float[n][3] (activated, > 0), quats float[n][4] (w, x, y, z;
+ * normalised inside; a zero quaternion culls the Gaussian), opacity float[n] (activated).
+ * Integer outputs follow a fixed FP32 decision specification (correctly rounded operations
+ * in a fixed order); Gaussians whose undilated 2D covariance has condition number above
+ * ~1e6 take the covariance and depth-key decisions in FP64.  2D means and conics are
+ * evaluated in double-float arithmetic so the FP32 blend downstream is not limited by
+ * their rounding. */
+lsv2_status lsv2_project(const lsv2_camera* cam, int64_t n, const float* means,
+                         const float* scales, const float* quats, const float* opacity,
+                         const lsv2_proj* out, int32_t* dev_status, void* stream);
+
+/* Workspace for lsv2_bin_sort: tile counters and two key buffers of `capacity` entries. */
+size_t lsv2_bin_sort_workspace_bytes(int64_t n, int64_t capacity, int32_t num_tiles);
+
+/* Bin and depth-sort (Eq. 3's ordered per-tile lists).  One instance per (visible Gaussian,
+ * tile in its rect), ordered by (tile id = ty * GX + tx, depth key bits, Gaussian id).
+ *   gauss_ids   uint32[capacity]      Gaussian id per instance, tile-major
+ *   tile_ranges uint32[num_tiles][2]  [start, end) into gauss_ids
+ *   dev_num_instances int64 (device)  total instance count I (may exceed capacity)
+ * If I > capacity, *dev_status = LSV2_ERR_CAPACITY and the lists are truncated (all ranges
+ * stay inside [0, capacity)). */
+lsv2_status lsv2_bin_sort(const lsv2_camera* cam, int64_t n, const lsv2_proj* proj,
+                          void* workspace, size_t workspace_bytes, uint32_t* gauss_ids,
+                          int64_t capacity, uint32_t* tile_ranges, int64_t* dev_num_instances,
+                          int32_t* dev_status, void* stream);
+
+/* Workspace for lsv2_splat_coeffs: one packed splat record per Gaussian. */
+size_t lsv2_splat_workspace_bytes(int64_t n, int32_t levels, int32_t K);
+
+/* Sparse-coefficient splatting (Sec. 3.4, Algorithm 1): per pixel, front to back over its
+ * tile's list, W_lev[idx_k] += w_k alpha_i T_i for the K pairs of every level.
+ *   idx   uint8[n][levels][K]  codebook indices (< L; repeats are allowed and add up;
+ *                              an index >= L sets LSV2_ERR_INVALID_ARGUMENT and is ignored)
+ *   w     float[n][levels][K]
+ *   coeff float[levels][H*W][L]  output coefficient map W (pixel-major, L contiguous)
+ *   final_T float[H*W], n_last uint32[H*W]: transmittance after the last contributor and
+ *   the list position (+1, relative to the tile start) of that contributor (0: none).
+ * Blending is FP32.  Supported: L = 64; levels 1 with K in {2, 4, 6, 8}, levels 2 or 3
+ * with K = 4; tiles 16x16, 8x8, 32x8. */
+lsv2_status lsv2_splat_coeffs(const lsv2_camera* cam, int64_t n, const lsv2_proj* proj,
+                              const uint32_t* tile_ranges, const uint32_t* gauss_ids,
+                              int32_t levels, int32_t K, int32_t L, const uint8_t* idx,
+                              const float* w, void* workspace, size_t workspace_bytes,
+                              float* coeff, float* final_T, uint32_t* n_last,
+                              int32_t* dev_status, void* stream);
+
+/* Decode (Eq. 7): feat[lev][p][:] = coeff[lev][p][:] . codebook[lev].
+ *   coeff    [levels][P][L]  dtype coeff_dtype (F32 or BF16)
+ *   codebook [levels][L][D]  dtype codebook_dtype
+ *   feat     [levels][P][D]  dtype out_dtype
+ * Supported: (F32, F32, F32) on CUDA cores (FP32 FMA); (BF16 or F32 coeff, BF16 codebook,
+ * BF16 or F32 out) on the tensor cores (tcgen05, FP32 accumulation).  L = 64, D % 128 == 0. */
+lsv2_status lsv2_decode(int32_t levels, int64_t P, int32_t L, int32_t D, const void* coeff,
+                        lsv2_dtype coeff_dtype, const void* codebook, lsv2_dtype codebook_dtype,
+                        void* feat, lsv2_dtype out_dtype, void* stream);
+
+/* Workspace for lsv2_query: per level the Gram matrix S S^T and the projected texts S t. */
+size_t lsv2_query_workspace_bytes(int32_t levels, int32_t L, int32_t Q, int32_t n_neg);
+
+/* Relevancy (Sec. 3.2) through the linearity of Eq. 7: with u_t = S t and G = S S^T,
+ *   <F, t> = W . u_t,  |F|^2 = W^T G W,  cos_t = <F, t> / (|F| |t|)  (0 when |F| < 1e-12)
+ *   rel[q][lev][p] = min_i softmax(tau [cos_pos, cos_neg_i])_0
+ *                  = sigmoid(tau (cos_pos - max_i cos_neg_i))
+ *   coeff    [levels][P][L]  F32 (or BF16 with compute = BF16)
+ *   codebook float[levels][L][D]
+ *   text     float[Q][1 + n_neg][D]  (positive first)
+ *   rel      [Q][levels][P]  dtype rel_dtype
+ * compute_dtype F32: FP32 FMA on CUDA cores; BF16: tcgen05 tensor cores, FP32 accumulation.
+ * Supported: L = 64, 1 <= n_neg, Q (1 + n_neg) <= 512. */
+lsv2_status lsv2_query(int32_t levels, int64_t P, int32_t L, int32_t D, const void* coeff,
+                       lsv2_dtype coeff_dtype, const float* codebook, int32_t Q, int32_t n_neg,
+                       const float* text, float tau, void* workspace, size_t workspace_bytes,
+                       void* rel, lsv2_dtype rel_dtype, lsv2_dtype compute_dtype, void* stream);
+
+/* Backward of Loss = mean_{lev,p,d} |F - target| with F = W S (decode + L1 adjoint).
+ *   loss      float (device scalar, accumulated: zero it first)
+ *   dcoeff    float[levels][P][L]   dLoss/dW  (overwritten)
+ *   dcodebook float[levels][L][D]   dLoss/dS  (accumulated: zero it first)
+ * sign(0) = 0.  F is recomputed, not read. */
+lsv2_status lsv2_l1_decode_backward(int32_t levels, int64_t P, int32_t L, int32_t D,
+                                    const float* coeff, const float* codebook,
+                                    const float* target, float* loss, float* dcoeff,
+                                    float* dcodebook, void* stream);
+
+/* Workspace for lsv2_splat_backward: per-Gaussian 2D-mean and conic gradients. */
+size_t lsv2_splat_backward_workspace_bytes(int64_t n);
+
+/* Backward of lsv2_splat_coeffs and lsv2_project.  Given dLoss/dW (dcoeff, same layout as
+ * coeff), walks each pixel's list back to front from n_last, recomputing the transmittance
+ * from final_T (T_i = T_{i+1} / (1 - alpha_i)), and accumulates per Gaussian:
+ *   dw float[n][levels][K], dopacity float[n], dmeans float[n][3], dscales float[n][3],
+ *   dquats float[n][4] (gradient w.r.t. the raw, unnormalised quaternion).
+ * All five outputs are accumulated with atomics: zero them first. */
+lsv2_status lsv2_splat_backward(const lsv2_camera* cam, int64_t n, const float* means,
+                                const float* scales, const float* quats, const lsv2_proj* proj,
+                                const uint32_t* tile_ranges, const uint32_t* gauss_ids,
+                                int32_t levels, int32_t K, int32_t L, const uint8_t* idx,
+                                const float* w, const float* final_T, const uint32_t* n_last,
+                                const float* dcoeff, void* workspace, size_t workspace_bytes,
+                                float* dw, float* dopacity, float* dmeans, float* dscales,
+                                float* dquats, int32_t* dev_status, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LSV2_H */

@@ -318,7 +318,7 @@ void orc_project(const orc_camera* c, int64_t n, const float* means, const float
 {
     for (int64_t g = 0; g < n; ++g) {
         decision d = decide(c, means + 3 * g, scales + 3 * g, quats + 4 * g);
-        flags[g] = (uint8_t)((d.visible ? 1 : 0) | (d.degenerate ? 2 : 0));
+        flags[g] = (uint8_t)((d.visible ? 1 : 0) | (d.visible && d.degenerate ? 2 : 0));
         radius[g] = d.visible ? d.radius : 0;
         rect[4 * g + 0] = d.visible ? d.x0 : 0;
         rect[4 * g + 1] = d.visible ? d.y0 : 0;

@@ -1,0 +1,557 @@
+// backward.cu -- gradients of an L1 feature loss through decode, splat and projection.
+//
+// The paper trains the coefficient field (Sec. 3.3, Sec. 4.1) but gives no gradient; this
+// is the adjoint of the forward path implemented here.
+//
+// 1. l1_decode_backward: Loss = mean |F - target|, F = W S (Eq. 7).  G = sign(F - target)/N,
+//    dW = G S^T, dS = W^T G.  Persistent CTAs walk 64-pixel tiles; F is recomputed per
+//    128-feature chunk (never stored), dW accumulates in registers across chunks, and each
+//    CTA keeps its dS partial in shared memory and adds it to HBM once at the end.
+// 2. splat_backward: per pixel, back to front from its last contributor.  The transmittance
+//    is recomputed from final_T as T_i = T_{i+1} / (1 - alpha_i).  Because each Gaussian has
+//    only K nonzeros per level, the running sum of later contributions is one scalar:
+//        g_i = sum_pairs dW[col] w,   dalpha_i = T_i (g_i - B),   B <- alpha_i g_i + (1 - alpha_i) B.
+//    Per-Gaussian sums over the 32 pixels of a warp use a butterfly reduce-scatter (31
+//    shuffles for up to 32 quantities), then one atomic per quantity.
+// 3. project_backward: one thread per Gaussian, chain rule from (u, v, conic) to (mean,
+//    scale, quaternion) through Sigma' = N N^T + 0.3 I, N = J W R diag(s).
+#include "device.cuh"
+#include "backward.cuh"
+
+#include <algorithm>
+
+namespace lsv2 {
+namespace {
+
+// ------------------------------------------------------------------------------------ 1
+constexpr int kBP = 64;    // pixels per tile
+constexpr int kBC = 128;   // feature chunk
+constexpr int kL = 64;
+
+__global__ void __launch_bounds__(256) l1_decode_backward_kernel(int64_t P, int D, float inv_n,
+                                                                 const float* __restrict__ W,
+                                                                 const float* __restrict__ S,
+                                                                 const float* __restrict__ target,
+                                                                 float* __restrict__ loss,
+                                                                 float* __restrict__ dW,
+                                                                 float* __restrict__ dS)
+{
+    extern __shared__ __align__(16) float sm[];
+    float* dSacc = sm;                          // [64][D]
+    float* Wt = dSacc + kL * D;                 // [64 l][kBP + 4]
+    float* Sc = Wt + kL * (kBP + 4);            // [64 l][kBC]
+    float* Gs = Sc + kL * kBC;                  // [kBP][kBC + 4]
+    __shared__ float red[8];
+    const int lev = blockIdx.y;
+    const int tid = threadIdx.x;
+    const float* Wl = W + (size_t)lev * P * kL;
+    const float* Sl = S + (size_t)lev * kL * D;
+    const float* Tl = target + (size_t)lev * P * D;
+    float* dWl = dW + (size_t)lev * P * kL;
+    for (int i = tid; i < kL * D; i += 256) dSacc[i] = 0.0f;
+    float lsum = 0.0f;
+    const int64_t ntiles = (P + kBP - 1) / kBP;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t p0 = tile * kBP;
+        __syncthreads();
+        // W tile, transposed: Wt[l][px]
+        for (int i = tid; i < kBP * kL / 4; i += 256) {
+            const int px = i >> 4, c4 = (i & 15) * 4;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (p0 + px < P) v = __ldg(reinterpret_cast<const float4*>(Wl + (p0 + px) * kL + c4));
+            Wt[(c4 + 0) * (kBP + 4) + px] = v.x;
+            Wt[(c4 + 1) * (kBP + 4) + px] = v.y;
+            Wt[(c4 + 2) * (kBP + 4) + px] = v.z;
+            Wt[(c4 + 3) * (kBP + 4) + px] = v.w;
+        }
+        float dwacc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) dwacc[i][j] = 0.0f;
+        for (int c0 = 0; c0 < D; c0 += kBC) {
+            __syncthreads();
+            for (int i = tid; i < kL * kBC / 4; i += 256) {
+                const int l = i >> 5, c4 = (i & 31) * 4;
+                *reinterpret_cast<float4*>(Sc + l * kBC + c4) =
+                    __ldg(reinterpret_cast<const float4*>(Sl + (size_t)l * D + c0 + c4));
+            }
+            __syncthreads();
+            // F block: thread (ty: 4 pixels, tx: 8 features)
+            {
+                const int tx = tid & 15, ty = tid >> 4;
+                float f[4][8];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) f[i][j] = 0.0f;
+                for (int l = 0; l < kL; ++l) {
+                    const float4 a = *reinterpret_cast<const float4*>(Wt + l * (kBP + 4) + ty * 4);
+                    const float4 b0 = *reinterpret_cast<const float4*>(Sc + l * kBC + tx * 8);
+                    const float4 b1 = *reinterpret_cast<const float4*>(Sc + l * kBC + tx * 8 + 4);
+                    const float av[4] = {a.x, a.y, a.z, a.w};
+                    const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) f[i][j] = fmaf(av[i], bv[j], f[i][j]);
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int px = ty * 4 + i;
+                    float g[8];
+                    if (p0 + px < P) {
+                        const float4* tp = reinterpret_cast<const float4*>(Tl + (p0 + px) * D + c0 + tx * 8);
+                        const float4 t0 = __ldcs(tp), t1 = __ldcs(tp + 1);
+                        const float tv[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const float r = f[i][j] - tv[j];
+                            lsum += fabsf(r);
+                            g[j] = r > 0.0f ? inv_n : (r < 0.0f ? -inv_n : 0.0f);
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) g[j] = 0.0f;
+                    }
+                    *reinterpret_cast<float4*>(Gs + px * (kBC + 4) + tx * 8) = make_float4(g[0], g[1], g[2], g[3]);
+                    *reinterpret_cast<float4*>(Gs + px * (kBC + 4) + tx * 8 + 4) = make_float4(g[4], g[5], g[6], g[7]);
+                }
+            }
+            __syncthreads();
+            // dS chunk: dSacc[l][c0 + c] += sum_px Wt[l][px] Gs[px][c]   (thread: 4 l x 8 c)
+            {
+                const int tc = tid & 15, tl = tid >> 4;
+                float s[4][8];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) s[i][j] = 0.0f;
+                for (int px = 0; px < kBP; ++px) {
+                    const float4 g0 = *reinterpret_cast<const float4*>(Gs + px * (kBC + 4) + tc * 8);
+                    const float4 g1 = *reinterpret_cast<const float4*>(Gs + px * (kBC + 4) + tc * 8 + 4);
+                    const float gv[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float wv = Wt[(tl * 4 + i) * (kBP + 4) + px];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) s[i][j] = fmaf(wv, gv[j], s[i][j]);
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) dSacc[(tl * 4 + i) * D + c0 + tc * 8 + j] += s[i][j];
+            }
+            // dW: dwacc[px][l] += sum_c Gs[px][c] Sc[l][c]   (thread: 4 px x 4 l)
+            {
+                const int tl = tid & 15, tp = tid >> 4;
+                for (int c = 0; c < kBC; ++c) {
+                    float gv[4], sv[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) gv[i] = Gs[(tp * 4 + i) * (kBC + 4) + c];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) sv[j] = Sc[(tl * 4 + j) * kBC + c];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) dwacc[i][j] = fmaf(gv[i], sv[j], dwacc[i][j]);
+                }
+            }
+        }
+        {
+            const int tl = tid & 15, tp = tid >> 4;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int64_t p = p0 + tp * 4 + i;
+                if (p < P)
+                    *reinterpret_cast<float4*>(dWl + p * kL + tl * 4) =
+                        make_float4(dwacc[i][0], dwacc[i][1], dwacc[i][2], dwacc[i][3]);
+            }
+        }
+    }
+    __syncthreads();
+    float* dSl = dS + (size_t)lev * kL * D;
+    for (int i = tid; i < kL * D; i += 256) atomicAdd(dSl + i, dSacc[i]);
+    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+    if ((tid & 31) == 0) red[tid >> 5] = lsum;
+    __syncthreads();
+    if (tid == 0) {
+        float t = 0.0f;
+        for (int i = 0; i < 8; ++i) t += red[i];
+        atomicAdd(loss, t * inv_n);
+    }
+}
+
+// ------------------------------------------------------------------------------------ 2
+// Backward splat record (global, per Gaussian): g0 = (u_hi, v_hi, u_lo, v_lo),
+// g1 = (A, B, C, o) exactly as in the forward record (so alpha is recomputed bit for bit),
+// g2 = (a, b, c, 0) the conic itself, then P weights and P column bytes (no merging).
+__host__ __device__ constexpr int bwd_record_floats(int P) { return (48 + 5 * P + 15) / 16 * 4; }
+
+__global__ void __launch_bounds__(256) pack_bwd_kernel(int64_t n, int levels, int K, const float* xy,
+                                                       const float* conic_o, const uint8_t* idx, const float* w,
+                                                       float* recs)
+{
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    const int P = levels * K;
+    float* rec = recs + (size_t)g * bwd_record_floats(P);
+    const float4 cn = reinterpret_cast<const float4*>(conic_o)[g];
+    reinterpret_cast<float4*>(rec)[0] = reinterpret_cast<const float4*>(xy)[g];
+    reinterpret_cast<float4*>(rec)[1] = make_float4(-0.5f * kLog2e * cn.x, -kLog2e * cn.y, -0.5f * kLog2e * cn.z, cn.w);
+    reinterpret_cast<float4*>(rec)[2] = make_float4(cn.x, cn.y, cn.z, 0.0f);
+    uint8_t* cb = reinterpret_cast<uint8_t*>(rec + 12 + P);
+    for (int p = 0; p < P; ++p) {
+        const int lev = p / K;
+        const size_t src = (size_t)g * P + p;
+        const int ix = idx[src];
+        const bool ok = ix < 64;
+        rec[12 + p] = ok ? w[src] : 0.0f;
+        cb[p] = (uint8_t)(ok ? lev * 64 + ix : levels * 64);
+    }
+}
+
+// lane L ends with the warp-wide sum of v[L]
+__device__ __forceinline__ float reduce_scatter32(float (&v)[32], int lane)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < o; ++i) {
+            const float send = upper ? v[i] : v[i + o];
+            const float keep = upper ? v[i + o] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    return v[0];
+}
+
+template <int LEVELS, int K, int TW, int TH>
+struct BwdCfg {
+    static constexpr int kWarps = TW * TH / 32;
+    static constexpr int kPairs = LEVELS * K;
+    static constexpr int kCols = LEVELS * 64 + 1;
+    static constexpr int kGFloats = (kCols * 33 + 3) / 4 * 4;
+    static constexpr int kRecFloats = bwd_record_floats(kPairs);
+    static constexpr int kSmemRecFloats = kRecFloats - 4;  // staged without the 2D mean
+    static constexpr int kSmemBytes = kWarps * (kGFloats + 32 * kSmemRecFloats) * 4;
+    static_assert(kPairs + 6 <= 32, "quantities per Gaussian");
+};
+
+template <int LEVELS, int K, int TW, int TH>
+__global__ void __launch_bounds__(TW* TH) splat_backward_kernel(SplatBwdArgs a)
+{
+    using C = BwdCfg<LEVELS, K, TW, TH>;
+    extern __shared__ __align__(16) float smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float* gW = smem + warp * C::kGFloats;
+    float* stage = smem + C::kWarps * C::kGFloats + warp * 32 * C::kSmemRecFloats;
+    const int GX = (a.cam.width + TW - 1) / TW;
+    const int tile = blockIdx.x;
+    const int tx = tile % GX, ty = tile / GX;
+    constexpr int kRows = 32 / TW;
+    const int lx = threadIdx.x % TW, ly = threadIdx.x / TW;
+    const int px = tx * TW + lx, py = ty * TH + ly;
+    const bool inside = px < a.cam.width && py < a.cam.height;
+    const size_t P = (size_t)a.cam.width * a.cam.height;
+    const size_t pix = (size_t)py * a.cam.width + px;
+    const float wx0 = (float)(tx * TW), wx1 = (float)(tx * TW + TW - 1);
+    const float wy0 = (float)(ty * TH + warp * kRows), wy1 = wy0 + (float)(kRows - 1);
+
+    // stage dLoss/dW of this warp's pixels as columns gW[col][lane]
+    for (int lev = 0; lev < LEVELS; ++lev)
+        for (int q = lane; q < 32 * 16; q += 32) {
+            const int pl = q >> 4, c4 = (q & 15) * 4;
+            const int gx = tx * TW + (pl % TW), gy = ty * TH + warp * kRows + pl / TW;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (gx < a.cam.width && gy < a.cam.height)
+                v = __ldg(reinterpret_cast<const float4*>(a.dcoeff + ((size_t)lev * P + (size_t)gy * a.cam.width + gx) * 64 + c4));
+            float* col = gW + (lev * 64 + c4) * 33 + pl;
+            col[0] = v.x;
+            col[33] = v.y;
+            col[66] = v.z;
+            col[99] = v.w;
+        }
+    for (int i = lane; i < 33; i += 32) gW[(LEVELS * 64) * 33 + i] = 0.0f;
+    __syncwarp();
+
+    const uint32_t beg = a.tile_ranges[2 * tile];
+    const uint32_t my_last = inside ? a.n_last[pix] : 0u;
+    float T = inside ? a.final_T[pix] : 1.0f;
+    float Bsum = 0.0f;
+    uint32_t wmax = my_last;
+    for (int o = 16; o > 0; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+    const float pxf = (float)px, pyf = (float)py;
+
+    for (int top = (int)wmax; top > 0; top -= 32) {
+        const int lo = max(0, top - 32);
+        // stage positions [lo, top) of the tile list, lane i <-> position lo + i; the 2D mean
+        // and the Gaussian id stay in the staging lane's registers
+        bool keep = false;
+        const int pos = lo + lane;
+        uint32_t my_g = 0u;
+        float4 my_xy = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (pos < top) {
+            my_g = a.gauss_ids[beg + pos];
+            my_xy = __ldg(reinterpret_cast<const float4*>(a.xy) + my_g);
+            const float2 ex = __ldg(reinterpret_cast<const float2*>(a.extent) + my_g);
+            keep = ex.x >= 0.0f && my_xy.x + ex.x >= wx0 && my_xy.x - ex.x <= wx1 && my_xy.y + ex.y >= wy0 &&
+                   my_xy.y - ex.y <= wy1;
+            if (keep) {
+                const float4* src = reinterpret_cast<const float4*>(a.recs + (size_t)my_g * C::kRecFloats) + 1;
+                float4* dst = reinterpret_cast<float4*>(stage + lane * C::kSmemRecFloats);
+#pragma unroll
+                for (int v = 0; v < C::kSmemRecFloats / 4; ++v) dst[v] = __ldg(src + v);
+            }
+        }
+        uint32_t mask = __ballot_sync(0xffffffffu, keep);
+        __syncwarp();
+        while (mask) {
+            const int i = 31 - __clz(mask);
+            mask &= ~(1u << i);
+            const uint32_t g = __shfl_sync(0xffffffffu, my_g, i);
+            float4 g0;
+            g0.x = __shfl_sync(0xffffffffu, my_xy.x, i);
+            g0.y = __shfl_sync(0xffffffffu, my_xy.y, i);
+            g0.z = __shfl_sync(0xffffffffu, my_xy.z, i);
+            g0.w = __shfl_sync(0xffffffffu, my_xy.w, i);
+            const float* r = stage + i * C::kSmemRecFloats;
+            const float4 g1 = *reinterpret_cast<const float4*>(r);
+            const float4 g2 = *reinterpret_cast<const float4*>(r + 4);
+            const float* wr = r + 8;
+            const uint8_t* cr = reinterpret_cast<const uint8_t*>(r + 8 + C::kPairs);
+            const float dx = __fadd_rn(__fsub_rn(g0.x, pxf), g0.z);
+            const float dy = __fadd_rn(__fsub_rn(g0.y, pyf), g0.w);
+            const float p2 = fmaf(g1.x * dx, dx, fmaf(g1.z * dy, dy, g1.y * dx * dy));
+            float vals[32];
+#pragma unroll
+            for (int k = 0; k < 32; ++k) vals[k] = 0.0f;
+            bool contrib = false;
+            if (lo + i < (int)my_last && p2 <= 0.0f) {
+                float ex2;
+                asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(ex2) : "f"(p2));
+                const float raw = g1.w * ex2;
+                const float alpha = fminf(kAlphaMax, raw);
+                if (alpha >= kAlphaMin) {
+                    contrib = true;
+                    const float Ti = T / (1.0f - alpha);
+                    const float e = alpha * Ti;
+                    float gsum = 0.0f;
+#pragma unroll
+                    for (int p = 0; p < C::kPairs; ++p) {
+                        const float gw = gW[(int)cr[p] * 33 + lane];
+                        vals[p] = gw * e;
+                        gsum = fmaf(gw, wr[p], gsum);
+                    }
+                    const float dalpha = Ti * (gsum - Bsum);
+                    Bsum = fmaf(alpha, gsum, (1.0f - alpha) * Bsum);
+                    T = Ti;
+                    if (!(raw > kAlphaMax)) {
+                        const float dpow = dalpha * alpha;
+                        const float ca = g2.x, cb = g2.y, cc = g2.z;
+                        vals[C::kPairs + 0] = dpow * -(ca * dx + cb * dy);        // d/du
+                        vals[C::kPairs + 1] = dpow * -(cb * dx + cc * dy);        // d/dv
+                        vals[C::kPairs + 2] = dpow * (-0.5f * dx * dx);           // d/da
+                        vals[C::kPairs + 3] = dpow * (-dx * dy);                  // d/db
+                        vals[C::kPairs + 4] = dpow * (-0.5f * dy * dy);           // d/dc
+                        vals[C::kPairs + 5] = dalpha * ex2;                       // d/dopacity
+                    }
+                }
+            }
+            if (__any_sync(0xffffffffu, contrib)) {
+                const float tot = reduce_scatter32(vals, lane);
+                if (lane < C::kPairs) {
+                    atomicAdd(a.dw + (size_t)g * C::kPairs + lane, tot);
+                } else if (lane < C::kPairs + 5) {
+                    atomicAdd(a.grad2d + (size_t)g * 8 + (lane - C::kPairs), tot);
+                } else if (lane == C::kPairs + 5) {
+                    atomicAdd(a.dopacity + g, tot);
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+template <int LEVELS, int K, int TW, int TH>
+cudaError_t launch_bwd_t(const SplatBwdArgs& a, cudaStream_t stream)
+{
+    using C = BwdCfg<LEVELS, K, TW, TH>;
+    static_assert(C::kSmemBytes <= 232448, "shared memory budget");
+    auto kern = splat_backward_kernel<LEVELS, K, TW, TH>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
+    if (e != cudaSuccess) return e;
+    const int GX = (a.cam.width + TW - 1) / TW, GY = (a.cam.height + TH - 1) / TH;
+    if (GX * GY == 0) return cudaSuccess;
+    kern<<<GX * GY, TW * TH, C::kSmemBytes, stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <int LEVELS, int K>
+cudaError_t launch_bwd_tile(const SplatBwdArgs& a, cudaStream_t stream)
+{
+    if (a.cam.tile_w == 16 && a.cam.tile_h == 16) return launch_bwd_t<LEVELS, K, 16, 16>(a, stream);
+    if (a.cam.tile_w == 8 && a.cam.tile_h == 8) return launch_bwd_t<LEVELS, K, 8, 8>(a, stream);
+    if (a.cam.tile_w == 32 && a.cam.tile_h == 8) return launch_bwd_t<LEVELS, K, 32, 8>(a, stream);
+    return cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------------------------------------------ 3
+__global__ void __launch_bounds__(256) project_backward_kernel(ProjBwdArgs a)
+{
+    const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi >= a.n || !(a.flags[gi] & 1)) return;
+    const lsv2_camera& c = a.cam;
+    const float* gr = a.grad2d + (size_t)gi * 8;
+    const float du = gr[0], dv = gr[1], dA = gr[2], dB = gr[3], dC = gr[4];
+    const float m[3] = {a.means[3 * gi], a.means[3 * gi + 1], a.means[3 * gi + 2]};
+    const float s[3] = {a.scales[3 * gi], a.scales[3 * gi + 1], a.scales[3 * gi + 2]};
+    const float4 q4 = reinterpret_cast<const float4*>(a.quats)[gi];
+    // forward quantities (float32)
+    float t[3];
+    for (int i = 0; i < 3; ++i) t[i] = c.R[3 * i] * m[0] + c.R[3 * i + 1] * m[1] + c.R[3 * i + 2] * m[2] + c.t[i];
+    const float qn = sqrtf(q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w);
+    const float w = q4.x / qn, x = q4.y / qn, y = q4.z / qn, z = q4.w / qn;
+    float R[9] = {1.f - 2.f * (y * y + z * z), 2.f * (x * y - w * z), 2.f * (x * z + w * y),
+                  2.f * (x * y + w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z - w * x),
+                  2.f * (x * z - w * y), 2.f * (y * z + w * x), 1.f - 2.f * (x * x + y * y)};
+    float M[9];
+    for (int k = 0; k < 3; ++k)
+        for (int j = 0; j < 3; ++j) M[3 * k + j] = R[3 * k + j] * s[j];
+    const float limx = kGuard * ((float)c.width / (2.0f * c.fx)), limy = kGuard * ((float)c.height / (2.0f * c.fy));
+    const float tz = t[2], itz = 1.0f / tz;
+    const float txz = t[0] * itz, tyz = t[1] * itz;
+    const bool clx = txz > limx || txz < -limx, cly = tyz > limy || tyz < -limy;
+    const float cxz = fminf(limx, fmaxf(-limx, txz)), cyz = fminf(limy, fmaxf(-limy, tyz));
+    const float J00 = c.fx * itz, J11 = c.fy * itz, J02 = -c.fx * cxz * itz, J12 = -c.fy * cyz * itz;
+    float T[6];
+    for (int j = 0; j < 3; ++j) {
+        T[j] = J00 * c.R[j] + J02 * c.R[6 + j];
+        T[3 + j] = J11 * c.R[3 + j] + J12 * c.R[6 + j];
+    }
+    float N[6];
+    for (int r = 0; r < 2; ++r)
+        for (int j = 0; j < 3; ++j) N[3 * r + j] = T[3 * r] * M[j] + T[3 * r + 1] * M[3 + j] + T[3 * r + 2] * M[6 + j];
+    const float c00 = N[0] * N[0] + N[1] * N[1] + N[2] * N[2] + kDilation;
+    const float c11 = N[3] * N[3] + N[4] * N[4] + N[5] * N[5] + kDilation;
+    const float c01 = N[0] * N[3] + N[1] * N[4] + N[2] * N[5];
+    const float idet = 1.0f / (c00 * c11 - c01 * c01);
+    const float qa = c11 * idet, qb = -c01 * idet, qc = c00 * idet;  // conic
+    // dL/dSigma' = -Q Ghat Q, Ghat = [[dA, dB/2], [dB/2, dC]]
+    const float g01 = 0.5f * dB;
+    const float X00 = dA * qa + g01 * qb, X01 = dA * qb + g01 * qc;   // Ghat Q
+    const float X10 = g01 * qa + dC * qb, X11 = g01 * qb + dC * qc;
+    const float H00 = -(qa * X00 + qb * X10), H01 = -(qa * X01 + qb * X11), H11 = -(qb * X01 + qc * X11);
+    // Sigma' = N N^T + d I  ->  dN = 2 H N
+    float dN[6];
+    for (int j = 0; j < 3; ++j) {
+        dN[j] = 2.0f * (H00 * N[j] + H01 * N[3 + j]);
+        dN[3 + j] = 2.0f * (H01 * N[j] + H11 * N[3 + j]);
+    }
+    // N = T M
+    float dT[6], dM[9];
+    for (int r = 0; r < 2; ++r)
+        for (int k = 0; k < 3; ++k) dT[3 * r + k] = dN[3 * r] * M[3 * k] + dN[3 * r + 1] * M[3 * k + 1] + dN[3 * r + 2] * M[3 * k + 2];
+    for (int k = 0; k < 3; ++k)
+        for (int j = 0; j < 3; ++j) dM[3 * k + j] = T[k] * dN[j] + T[3 + k] * dN[3 + j];
+    float ds[3], dR[9];
+    for (int j = 0; j < 3; ++j) ds[j] = dM[j] * R[j] + dM[3 + j] * R[3 + j] + dM[6 + j] * R[6 + j];
+    for (int k = 0; k < 3; ++k)
+        for (int j = 0; j < 3; ++j) dR[3 * k + j] = dM[3 * k + j] * s[j];
+    // rotation matrix of the unit quaternion (w, x, y, z)
+    float dw_ = 2.f * (-z * dR[1] + y * dR[2] + z * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
+    float dx_ = 2.f * (y * dR[1] + z * dR[2] + y * dR[3] - 2.f * x * dR[4] - w * dR[5] + z * dR[6] + w * dR[7] - 2.f * x * dR[8]);
+    float dy_ = 2.f * (-2.f * y * dR[0] + x * dR[1] + w * dR[2] + x * dR[3] + z * dR[5] - w * dR[6] + z * dR[7] - 2.f * y * dR[8]);
+    float dz_ = 2.f * (-2.f * z * dR[0] - w * dR[1] + x * dR[2] + w * dR[3] - 2.f * z * dR[4] + y * dR[5] + x * dR[6] + y * dR[7]);
+    const float dot = w * dw_ + x * dx_ + y * dy_ + z * dz_;
+    const float iq = 1.0f / qn;
+    // T = J W:  dJ
+    const float dJ00 = dT[0] * c.R[0] + dT[1] * c.R[1] + dT[2] * c.R[2];
+    const float dJ02 = dT[0] * c.R[6] + dT[1] * c.R[7] + dT[2] * c.R[8];
+    const float dJ11 = dT[3] * c.R[3] + dT[4] * c.R[4] + dT[5] * c.R[5];
+    const float dJ12 = dT[3] * c.R[6] + dT[4] * c.R[7] + dT[5] * c.R[8];
+    float dt[3] = {0.f, 0.f, 0.f};
+    const float itz2 = itz * itz;
+    dt[2] += -c.fx * itz2 * dJ00 - c.fy * itz2 * dJ11;
+    if (!clx) {
+        dt[0] += -c.fx * itz2 * dJ02;
+        dt[2] += 2.0f * c.fx * t[0] * itz2 * itz * dJ02;
+    } else {
+        dt[2] += c.fx * cxz * itz2 * dJ02;
+    }
+    if (!cly) {
+        dt[1] += -c.fy * itz2 * dJ12;
+        dt[2] += 2.0f * c.fy * t[1] * itz2 * itz * dJ12;
+    } else {
+        dt[2] += c.fy * cyz * itz2 * dJ12;
+    }
+    // u = fx tx / tz + cx
+    dt[0] += du * c.fx * itz;
+    dt[1] += dv * c.fy * itz;
+    dt[2] += -(du * c.fx * t[0] + dv * c.fy * t[1]) * itz2;
+    for (int j = 0; j < 3; ++j)
+        a.dmeans[3 * gi + j] += c.R[j] * dt[0] + c.R[3 + j] * dt[1] + c.R[6 + j] * dt[2];
+    for (int j = 0; j < 3; ++j) a.dscales[3 * gi + j] += ds[j];
+    a.dquats[4 * gi + 0] += (dw_ - w * dot) * iq;
+    a.dquats[4 * gi + 1] += (dx_ - x * dot) * iq;
+    a.dquats[4 * gi + 2] += (dy_ - y * dot) * iq;
+    a.dquats[4 * gi + 3] += (dz_ - z * dot) * iq;
+}
+
+}  // namespace
+
+size_t splat_backward_workspace_bytes(int64_t n, int levels, int K)
+{
+    const size_t g2 = ((size_t)n * 8 * 4 + 255) / 256 * 256;
+    const size_t recs = ((size_t)n * bwd_record_floats(levels * K) * 4 + 255) / 256 * 256;
+    return g2 + recs;
+}
+
+cudaError_t launch_l1_decode_backward(int levels, int64_t P, int D, const float* W, const float* S,
+                                      const float* target, float* loss, float* dW, float* dS, int num_sms,
+                                      cudaStream_t stream)
+{
+    if (P == 0) return cudaSuccess;
+    const size_t smem = (size_t)(kL * D + kL * (kBP + 4) + kL * kBC + kBP * (kBC + 4)) * 4;
+    cudaError_t e = cudaFuncSetAttribute(l1_decode_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t ntiles = (P + kBP - 1) / kBP;
+    const int ctas = (int)std::min<int64_t>(ntiles, (int64_t)num_sms);
+    const float inv_n = (float)(1.0 / ((double)levels * (double)P * (double)D));
+    l1_decode_backward_kernel<<<dim3(ctas, levels), 256, smem, stream>>>(P, D, inv_n, W, S, target, loss, dW, dS);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_splat_backward(int levels, int K, const SplatBwdArgs& args, const ProjBwdArgs& pargs,
+                                  const uint8_t* idx, const float* w, cudaStream_t stream)
+{
+    SplatBwdArgs a = args;
+    const size_t g2 = ((size_t)pargs.n * 8 * 4 + 255) / 256 * 256;
+    a.grad2d = static_cast<float*>(a.workspace);
+    a.recs = reinterpret_cast<float*>(static_cast<char*>(a.workspace) + g2);
+    cudaError_t e = cudaMemsetAsync(a.grad2d, 0, (size_t)pargs.n * 8 * 4, stream);
+    if (e != cudaSuccess) return e;
+    if (pargs.n > 0)
+        pack_bwd_kernel<<<(unsigned)((pargs.n + 255) / 256), 256, 0, stream>>>(pargs.n, levels, K, a.xy, a.conic_o,
+                                                                              idx, w, a.recs);
+    if (levels == 1 && K == 4) e = launch_bwd_tile<1, 4>(a, stream);
+    else if (levels == 1 && K == 2) e = launch_bwd_tile<1, 2>(a, stream);
+    else if (levels == 1 && K == 8) e = launch_bwd_tile<1, 8>(a, stream);
+    else if (levels == 2 && K == 4) e = launch_bwd_tile<2, 4>(a, stream);
+    else if (levels == 3 && K == 4) e = launch_bwd_tile<3, 4>(a, stream);
+    else return cudaErrorInvalidValue;
+    if (e != cudaSuccess) return e;
+    ProjBwdArgs pa = pargs;
+    pa.grad2d = a.grad2d;
+    if (pa.n > 0) project_backward_kernel<<<(unsigned)((pa.n + 255) / 256), 256, 0, stream>>>(pa);
+    return cudaGetLastError();
+}
+
+bool splat_backward_supported(int levels, int K)
+{
+    return (levels == 1 && (K == 2 || K == 4 || K == 8)) || ((levels == 2 || levels == 3) && K == 4);
+}
+
+}  // namespace lsv2

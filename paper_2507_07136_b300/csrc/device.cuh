@@ -1,0 +1,107 @@
+// device.cuh -- constants, status reporting and double-float arithmetic shared by the
+// sm_103a kernels of the sparse-coefficient splatting library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lsv2.h"
+
+namespace lsv2 {
+
+// Rasteriser constants (3DGS conventions the paper's CUDA path builds on, Sec. 3.4).
+// They are float32 values; every comparison is made against exactly these numbers.
+constexpr float kDilation = 0.3f;         // px^2 added to the 2D covariance diagonal
+constexpr float kGuard = 1.3f;            // guard band on tan(fov/2) for the EWA Jacobian
+constexpr float kDegenerateCond = 1e6f;   // tr^2 / det of the undilated 2D covariance
+constexpr float kDiscFloor = 0.1f;        // floor of the eigenvalue discriminant
+constexpr float kRadiusCap = 1048576.0f;  // screen radius cap (2^20 px)
+constexpr float kAlphaMax = 0.99f;
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kTMin = 1e-4f;
+constexpr float kLog2e = 1.4426950408889634f;
+
+// First nonzero status wins; never traps.
+__device__ __forceinline__ void report(int32_t* status, int32_t code)
+{
+    if (status) atomicCAS(status, 0, code);
+}
+
+// ----------------------------------------------------------------------------------------
+// Double-float ("double-word") arithmetic: a value is the unevaluated sum hi + lo of two
+// floats with |lo| <= ulp(hi)/2.  Error-free transformations after Dekker (1971) and Knuth
+// (TwoSum); the double-word operations follow Joldes, Muller & Popescu, "Tight and
+// rigorous error bounds for basic building blocks of double-word arithmetic" (ACM TOMS
+// 2017): accurate DW+DW, DW*FP and DW*DW with FMA.  Every step uses explicitly rounded
+// intrinsics so no contraction or reassociation can change it.
+struct dfloat {
+    float hi, lo;
+};
+
+__device__ __forceinline__ dfloat df(float a) { return {a, 0.0f}; }
+
+__device__ __forceinline__ dfloat two_sum(float a, float b)
+{
+    float s = __fadd_rn(a, b);
+    float bp = __fsub_rn(s, a);
+    float ap = __fsub_rn(s, bp);
+    float e = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+    return {s, e};
+}
+
+// Requires |a| >= |b| (or a == 0).
+__device__ __forceinline__ dfloat fast_two_sum(float a, float b)
+{
+    float s = __fadd_rn(a, b);
+    float e = __fsub_rn(b, __fsub_rn(s, a));
+    return {s, e};
+}
+
+__device__ __forceinline__ dfloat two_prod(float a, float b)
+{
+    float p = __fmul_rn(a, b);
+    float e = __fmaf_rn(a, b, -p);
+    return {p, e};
+}
+
+__device__ __forceinline__ dfloat df_add(dfloat x, dfloat y)
+{
+    dfloat s = two_sum(x.hi, y.hi);
+    dfloat t = two_sum(x.lo, y.lo);
+    float c = __fadd_rn(s.lo, t.hi);
+    dfloat v = fast_two_sum(s.hi, c);
+    float w = __fadd_rn(t.lo, v.lo);
+    return fast_two_sum(v.hi, w);
+}
+
+__device__ __forceinline__ dfloat df_neg(dfloat x) { return {-x.hi, -x.lo}; }
+__device__ __forceinline__ dfloat df_sub(dfloat x, dfloat y) { return df_add(x, df_neg(y)); }
+
+__device__ __forceinline__ dfloat df_mul_f(dfloat x, float y)
+{
+    dfloat c = two_prod(x.hi, y);
+    float l = __fmaf_rn(x.lo, y, c.lo);
+    return fast_two_sum(c.hi, l);
+}
+
+__device__ __forceinline__ dfloat df_mul(dfloat x, dfloat y)
+{
+    dfloat c = two_prod(x.hi, y.hi);
+    float t0 = __fmul_rn(x.lo, y.lo);
+    float t1 = __fmaf_rn(x.hi, y.lo, t0);
+    float l2 = __fmaf_rn(x.lo, y.hi, t1);
+    float l3 = __fadd_rn(c.lo, l2);
+    return fast_two_sum(c.hi, l3);
+}
+
+// Quotient with one correction step: q1 = x_hi / y_hi, r = x - y q1 (in double-float),
+// q2 = r_hi / y_hi.  Relative error about 2^-44.
+__device__ __forceinline__ dfloat df_div(dfloat x, dfloat y)
+{
+    float q1 = __fdiv_rn(x.hi, y.hi);
+    dfloat r = df_sub(x, df_mul_f(y, q1));
+    float q2 = __fdiv_rn(r.hi, y.hi);
+    return fast_two_sum(q1, q2);
+}
+
+}  // namespace lsv2

@@ -1,0 +1,146 @@
+// query.cu -- relevancy scores (Sec. 3.2) through the linearity of Eq. 7.
+//
+// The rendered feature is F = W S, so for a text embedding t
+//     <F, t> = W . (S t),     |F|^2 = W^T (S S^T) W,
+// and the relevancy never needs the D-dim feature map.  Per level a small prepare kernel
+// forms, in FP64 accumulation rounded to float, the columns of
+//     B = [ S S^T | S t_0 | S t_1 | ... ]            (64 x (64 + #texts))
+// and the text norms; the main kernel gives every (pixel, level) one thread that holds W in
+// registers, forms y = W^T B column by column (B^T in shared memory, read as warp-wide
+// broadcasts), |F|^2 = sum_j W_j y_j, and writes
+//     rel = min_i softmax(tau [cos_pos, cos_neg_i])_0 = sigmoid(tau (cos_pos - max_i cos_neg_i)).
+#include "device.cuh"
+#include "query.cuh"
+
+namespace lsv2 {
+namespace {
+
+constexpr int kL = 64;
+
+// grid (64 + nt, levels), 128 threads: column j of B for level lev (j < 64: Gram row j).
+__global__ void __launch_bounds__(128) query_prepare_kernel(int D, int nt, const float* __restrict__ S,
+                                                            const float* __restrict__ text,
+                                                            float* __restrict__ Bt, float* __restrict__ tnorm)
+{
+    const int j = blockIdx.x, lev = blockIdx.y;
+    const int ncol = kL + nt;
+    const float* Sl = S + (size_t)lev * kL * D;
+    const float* v = j < kL ? Sl + (size_t)j * D : text + (size_t)(j - kL) * D;
+    __shared__ double red[4];
+    for (int k = 0; k < kL; k += 1) {
+        double acc = 0.0;
+        for (int d = threadIdx.x; d < D; d += 128) acc += (double)Sl[(size_t)k * D + d] * (double)v[d];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) Bt[((size_t)lev * ncol + j) * kL + k] = (float)((red[0] + red[1]) + (red[2] + red[3]));
+        __syncthreads();
+    }
+    if (lev == 0 && j >= kL) {
+        double acc = 0.0;
+        for (int d = threadIdx.x; d < D; d += 128) acc += (double)v[d] * (double)v[d];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) tnorm[j - kL] = (float)sqrt((red[0] + red[1]) + (red[2] + red[3]));
+    }
+}
+
+// grid (ceil(P / 128), levels), 128 threads, dynamic smem = (64 + nt) * 64 floats.
+__global__ void __launch_bounds__(128) query_f32_kernel(int64_t P, int Q, int n_neg, float tau,
+                                                        const float* __restrict__ W, const float* __restrict__ Bt,
+                                                        const float* __restrict__ tnorm, float* __restrict__ rel)
+{
+    extern __shared__ __align__(16) float sB[];
+    const int lev = blockIdx.y, levels = gridDim.y;
+    const int nt = Q * (1 + n_neg), ncol = kL + nt;
+    const float* Bl = Bt + (size_t)lev * ncol * kL;
+    for (int i = threadIdx.x * 4; i < ncol * kL; i += 512)
+        *reinterpret_cast<float4*>(sB + i) = __ldg(reinterpret_cast<const float4*>(Bl + i));
+    __syncthreads();
+    const int64_t p = (int64_t)blockIdx.x * 128 + threadIdx.x;
+    if (p >= P) return;
+    float w[kL];
+    const float4* src = reinterpret_cast<const float4*>(W + ((size_t)lev * P + p) * kL);
+#pragma unroll
+    for (int i = 0; i < kL / 4; ++i) {
+        const float4 v = __ldcs(src + i);
+        w[4 * i] = v.x;
+        w[4 * i + 1] = v.y;
+        w[4 * i + 2] = v.z;
+        w[4 * i + 3] = v.w;
+    }
+    float n2 = 0.0f;
+#pragma unroll
+    for (int j = 0; j < kL; ++j) {
+        const float* col = sB + j * kL;
+        float y = 0.0f;
+#pragma unroll
+        for (int k = 0; k < kL; k += 4) {
+            const float4 b = *reinterpret_cast<const float4*>(col + k);
+            y = fmaf(w[k], b.x, y);
+            y = fmaf(w[k + 1], b.y, y);
+            y = fmaf(w[k + 2], b.z, y);
+            y = fmaf(w[k + 3], b.w, y);
+        }
+        n2 = fmaf(w[j], y, n2);
+    }
+    const float nf = sqrtf(fmaxf(n2, 0.0f));
+    for (int q = 0; q < Q; ++q) {
+        float best = -INFINITY, cpos = 0.0f;
+        for (int t = 0; t <= n_neg; ++t) {
+            const int tt = q * (1 + n_neg) + t;
+            const float* col = sB + (kL + tt) * kL;
+            float s = 0.0f;
+#pragma unroll
+            for (int k = 0; k < kL; k += 4) {
+                const float4 b = *reinterpret_cast<const float4*>(col + k);
+                s = fmaf(w[k], b.x, s);
+                s = fmaf(w[k + 1], b.y, s);
+                s = fmaf(w[k + 2], b.z, s);
+                s = fmaf(w[k + 3], b.w, s);
+            }
+            const float c = nf < 1e-12f ? 0.0f : s / (nf * tnorm[tt]);
+            if (t == 0) cpos = c;
+            else best = fmaxf(best, c);
+        }
+        const float r = 1.0f / (1.0f + expf(-tau * (cpos - best)));
+        rel[((size_t)q * levels + lev) * P + p] = r;
+    }
+}
+
+}  // namespace
+
+size_t query_workspace_bytes(int levels, int nt)
+{
+    return ((size_t)levels * (kL + nt) * kL * 4 + 255) / 256 * 256 + ((size_t)nt * 4 + 255) / 256 * 256;
+}
+
+cudaError_t launch_query_prepare(int levels, int D, int nt, const float* S, const float* text, void* ws,
+                                 cudaStream_t stream)
+{
+    float* Bt = static_cast<float*>(ws);
+    float* tnorm = reinterpret_cast<float*>(static_cast<char*>(ws) +
+                                            ((size_t)levels * (kL + nt) * kL * 4 + 255) / 256 * 256);
+    dim3 grid((unsigned)(kL + nt), (unsigned)levels);
+    query_prepare_kernel<<<grid, 128, 0, stream>>>(D, nt, S, text, Bt, tnorm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_query_f32(int levels, int64_t P, int Q, int n_neg, float tau, const float* W, const void* ws,
+                             float* rel, cudaStream_t stream)
+{
+    if (P == 0) return cudaSuccess;
+    const int nt = Q * (1 + n_neg);
+    const float* Bt = static_cast<const float*>(ws);
+    const float* tnorm = reinterpret_cast<const float*>(static_cast<const char*>(ws) +
+                                                        ((size_t)levels * (kL + nt) * kL * 4 + 255) / 256 * 256);
+    const size_t smem = (size_t)(kL + nt) * kL * 4;
+    cudaError_t e = cudaFuncSetAttribute(query_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((P + 127) / 128), (unsigned)levels);
+    query_f32_kernel<<<grid, 128, smem, stream>>>(P, Q, n_neg, tau, W, Bt, tnorm, rel);
+    return cudaGetLastError();
+}
+
+}  // namespace lsv2

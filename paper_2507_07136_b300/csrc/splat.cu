@@ -1,0 +1,254 @@
+// splat.cu -- efficient sparse-coefficient splatting (Sec. 3.4, Algorithm 1) on sm_103a.
+//
+// Per pixel, front to back over its tile's depth-ordered list (Eq. 3), with the weights
+// e_i = alpha_i prod_{j<i} (1 - alpha_j) of Eq. 7, only the K nonzero coefficients of each
+// level are blended: W_lev[idx_k] += w_k e_i.  Blending stays in FP32.
+//
+// Layout on the SM (one CTA per tile, one thread per pixel, warps independent):
+//  * Every warp owns the FP32 accumulators of its 32 pixels in shared memory as columns:
+//    acc[col][lane] with col = lev * 64 + idx and a stride of 33 floats.  The codebook index
+//    of a Gaussian is the same for every pixel of the tile, so a pair update is one
+//    conflict-free LDS / FFMA / STS on a warp-uniform column.  (Registers cannot be indexed
+//    by a runtime value on this architecture; a jump table would cost a uniform indirect
+//    branch per pair.)
+//  * Gaussians are staged per warp in batches of 32 records (one coalesced 16-byte-vector
+//    copy per lane).  While staging, each lane tests its record's alpha >= 1/255 bounding box
+//    against the warp's pixel strip; a ballot keeps only the records that can touch the strip
+//    and the warp walks the set bits in list order ("warp-ballot culling").  Culling skips
+//    only work whose alpha is below 1/255 everywhere on the strip, so it changes no result.
+//  * A pre-pass packs per-Gaussian records (2D mean pair, conic pre-scaled by -log2(e)/2,
+//    opacity, weights, columns).  Repeated indices within one level are merged into the
+//    first occurrence and the repeat is pointed at a sink column, so the loads of a record's
+//    pairs can all be issued before any store.
+#include "device.cuh"
+#include "splat.cuh"
+
+namespace lsv2 {
+
+__global__ void __launch_bounds__(256) pack_records_kernel(PackArgs a)
+{
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= a.n) return;
+    const int P = a.levels * a.K;
+    const int rec_floats = a.rec_bytes / 4;
+    float* rec = a.recs + (size_t)g * rec_floats;
+    float4 xy = reinterpret_cast<const float4*>(a.xy)[g];
+    float4 cn = reinterpret_cast<const float4*>(a.conic_o)[g];
+    float2 ex = reinterpret_cast<const float2*>(a.extent)[g];
+    reinterpret_cast<float4*>(rec)[0] = xy;
+    reinterpret_cast<float4*>(rec)[1] =
+        make_float4(-0.5f * kLog2e * cn.x, -kLog2e * cn.y, -0.5f * kLog2e * cn.z, cn.w);
+    float wv[kMaxPairs];
+    int col[kMaxPairs];
+    const int sink = a.levels * 64;
+    for (int lev = 0; lev < a.levels; ++lev) {
+        for (int k = 0; k < a.K; ++k) {
+            const int p = lev * a.K + k;
+            const size_t src = ((size_t)g * a.levels + lev) * a.K + k;
+            int ix = a.idx[src];
+            float w = a.w[src];
+            if (ix >= 64) {
+                report(a.status, LSV2_ERR_INVALID_ARGUMENT);
+                ix = -1;
+                w = 0.0f;
+            }
+            col[p] = ix < 0 ? sink : lev * 64 + ix;
+            wv[p] = w;
+            for (int k2 = 0; k2 < k; ++k2) {
+                const int p2 = lev * a.K + k2;
+                if (ix >= 0 && col[p2] == col[p]) {
+                    wv[p2] += w;
+                    col[p] = sink;
+                    wv[p] = 0.0f;
+                    break;
+                }
+            }
+        }
+    }
+    for (int p = 0; p < P; ++p) rec[8 + p] = wv[p];
+    uint8_t* cb = reinterpret_cast<uint8_t*>(rec + 8 + P);
+    for (int p = 0; p < P; ++p) cb[p] = (uint8_t)col[p];
+    // culling extents live in the last 16 bytes of the record
+    reinterpret_cast<float2*>(rec + rec_floats - 4)[0] = ex;
+}
+
+template <int LEVELS, int K, int TW, int TH>
+__global__ void __launch_bounds__(TW* TH) splat_kernel(SplatArgs a)
+{
+    using C = SplatCfg<LEVELS, K, TW, TH>;
+    extern __shared__ __align__(16) float smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float* acc = smem + warp * C::kAccFloats;
+    float* stage = smem + C::kWarps * C::kAccFloats + warp * (C::kBatch * C::kSmemRecFloats);
+
+    const int GX = (a.cam.width + TW - 1) / TW;
+    const int tile = blockIdx.x;
+    const int tx = tile % GX, ty = tile / GX;
+    const int lx = threadIdx.x % TW, ly = threadIdx.x / TW;
+    const int px = tx * TW + lx, py = ty * TH + ly;
+    const bool inside = px < a.cam.width && py < a.cam.height;
+    // pixel strip covered by this warp
+    constexpr int kRows = 32 / TW;
+    const float wx0 = (float)(tx * TW), wx1 = (float)(tx * TW + TW - 1);
+    const float wy0 = (float)(ty * TH + warp * kRows), wy1 = wy0 + (float)(kRows - 1);
+
+    for (int i = lane * 4; i < C::kAccFloats; i += 128)
+        *reinterpret_cast<float4*>(acc + i) = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncwarp();
+
+    const uint32_t beg = a.tile_ranges[2 * tile], end = a.tile_ranges[2 * tile + 1];
+    float T = 1.0f;
+    uint32_t last = 0;
+    bool done = !inside;
+    const float pxf = (float)px, pyf = (float)py;
+
+    for (uint32_t base = beg; base < end; base += C::kBatch) {
+        if (__all_sync(0xffffffffu, done)) break;
+        bool keep = false;
+        const uint32_t j = base + lane;
+        if (lane < C::kBatch && j < end) {
+            const uint32_t g = a.gauss_ids[j];
+            const float4* src = reinterpret_cast<const float4*>(a.recs + (size_t)g * C::kRecFloats);
+            const float4 g0 = __ldg(src);
+            const float2 ex = __ldg(reinterpret_cast<const float2*>(a.recs + (size_t)g * C::kRecFloats + C::kRecFloats - 4));
+            keep = ex.x >= 0.0f && g0.x + ex.x >= wx0 && g0.x - ex.x <= wx1 && g0.y + ex.y >= wy0 &&
+                   g0.y - ex.y <= wy1;
+            if (keep) {
+                float4* dst = reinterpret_cast<float4*>(stage + lane * C::kSmemRecFloats);
+                dst[0] = g0;
+#pragma unroll
+                for (int v = 1; v < C::kSmemRecFloats / 4; ++v) dst[v] = __ldg(src + v);
+            }
+        }
+        uint32_t mask = __ballot_sync(0xffffffffu, keep);
+        __syncwarp();
+        while (mask) {
+            const int i = __ffs(mask) - 1;
+            mask &= mask - 1;
+            const float* r = stage + i * C::kSmemRecFloats;
+            const float4 g0 = *reinterpret_cast<const float4*>(r);
+            const float4 g1 = *reinterpret_cast<const float4*>(r + 4);
+            const float dx = __fadd_rn(__fsub_rn(g0.x, pxf), g0.z);
+            const float dy = __fadd_rn(__fsub_rn(g0.y, pyf), g0.w);
+            const float p2 = fmaf(g1.x * dx, dx, fmaf(g1.z * dy, dy, g1.y * dx * dy));
+            float e = 0.0f;
+            if (!done && p2 <= 0.0f) {
+                float ex2;
+                asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(ex2) : "f"(p2));
+                const float alpha = fminf(kAlphaMax, g1.w * ex2);
+                if (alpha >= kAlphaMin) {
+                    const float test_T = T * (1.0f - alpha);
+                    if (test_T < kTMin) {
+                        done = true;
+                    } else {
+                        e = alpha * T;
+                        T = test_T;
+                        last = base + i - beg + 1;
+                    }
+                }
+            }
+            if (__any_sync(0xffffffffu, e > 0.0f)) {
+                const float* wr = r + 8;
+                const uint8_t* cr = reinterpret_cast<const uint8_t*>(r + 8 + C::kPairs);
+                float v[C::kPairs];
+                int o[C::kPairs];
+#pragma unroll
+                for (int p = 0; p < C::kPairs; ++p) {
+                    o[p] = (int)cr[p] * 33 + lane;
+                    v[p] = acc[o[p]];
+                }
+#pragma unroll
+                for (int p = 0; p < C::kPairs; ++p) v[p] = fmaf(e, wr[p], v[p]);
+#pragma unroll
+                for (int p = 0; p < C::kPairs; ++p) acc[o[p]] = v[p];
+            }
+        }
+        __syncwarp();
+    }
+
+    if (inside) {
+        const size_t pix = (size_t)py * a.cam.width + px;
+        a.final_T[pix] = T;
+        a.n_last[pix] = last;
+    }
+    __syncwarp();
+    // write this warp's 32 pixels: per row segment TW pixels x 64 floats (contiguous in HBM)
+    const size_t P = (size_t)a.cam.width * a.cam.height;
+#pragma unroll
+    for (int lev = 0; lev < LEVELS; ++lev) {
+        for (int q = lane; q < 32 * 16; q += 32) {
+            const int pl = q >> 4;  // pixel within the warp (row-major over the strip)
+            const int c4 = (q & 15) * 4;
+            const int gx = tx * TW + (pl % TW), gy = ty * TH + warp * kRows + pl / TW;
+            if (gx < a.cam.width && gy < a.cam.height) {
+                const float* col = acc + (lev * 64 + c4) * 33 + pl;
+                float4 val = make_float4(col[0], col[33], col[66], col[99]);
+                __stcs(reinterpret_cast<float4*>(a.coeff + ((size_t)lev * P + (size_t)gy * a.cam.width + gx) * 64 + c4), val);
+            }
+        }
+    }
+}
+
+namespace {
+
+template <int LEVELS, int K, int TW, int TH>
+cudaError_t launch_t(const SplatArgs& a, cudaStream_t stream)
+{
+    using C = SplatCfg<LEVELS, K, TW, TH>;
+    static_assert(C::kSmemBytes <= 232448, "shared memory budget");
+    auto kern = splat_kernel<LEVELS, K, TW, TH>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
+    if (e != cudaSuccess) return e;
+    const int GX = (a.cam.width + TW - 1) / TW, GY = (a.cam.height + TH - 1) / TH;
+    if (GX * GY == 0) return cudaSuccess;
+    kern<<<GX * GY, TW * TH, C::kSmemBytes, stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <int LEVELS, int K>
+cudaError_t launch_tile(const SplatArgs& a, cudaStream_t stream)
+{
+    if (a.cam.tile_w == 16 && a.cam.tile_h == 16) return launch_t<LEVELS, K, 16, 16>(a, stream);
+    if (a.cam.tile_w == 8 && a.cam.tile_h == 8) return launch_t<LEVELS, K, 8, 8>(a, stream);
+    if (a.cam.tile_w == 32 && a.cam.tile_h == 8) return launch_t<LEVELS, K, 32, 8>(a, stream);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+bool splat_supported(int levels, int K, int L, int tw, int th)
+{
+    if (L != 64) return false;
+    const bool tile_ok = (tw == 16 && th == 16) || (tw == 8 && th == 8) || (tw == 32 && th == 8);
+    if (!tile_ok) return false;
+    if (levels == 1) return K == 2 || K == 4 || K == 6 || K == 8;
+    if (levels == 2 || levels == 3) return K == 4;
+    return false;
+}
+
+int splat_record_bytes(int levels, int K) { return record_bytes(levels * K); }
+
+cudaError_t launch_pack(const PackArgs& a, cudaStream_t stream)
+{
+    if (a.n == 0) return cudaSuccess;
+    const int threads = 256;
+    pack_records_kernel<<<(unsigned)((a.n + threads - 1) / threads), threads, 0, stream>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_splat(int levels, int K, const SplatArgs& a, cudaStream_t stream)
+{
+    if (levels == 1) {
+        switch (K) {
+            case 2: return launch_tile<1, 2>(a, stream);
+            case 4: return launch_tile<1, 4>(a, stream);
+            case 6: return launch_tile<1, 6>(a, stream);
+            case 8: return launch_tile<1, 8>(a, stream);
+        }
+    }
+    if (levels == 2 && K == 4) return launch_tile<2, 4>(a, stream);
+    if (levels == 3 && K == 4) return launch_tile<3, 4>(a, stream);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace lsv2

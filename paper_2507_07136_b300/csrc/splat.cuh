@@ -1,0 +1,65 @@
+// splat.cuh -- record layout and launch configuration of the sparse-coefficient splat.
+#pragma once
+
+#include "device.cuh"
+
+namespace lsv2 {
+
+constexpr int kMaxPairs = 24;  // levels * K
+
+// Per-Gaussian splat record (global memory, 16-byte aligned), P = levels * K pairs:
+//   floats [0, 4)   u_hi, v_hi, u_lo, v_lo          2D mean as a float pair
+//   floats [4, 8)   A, B, C, opacity                 power * log2(e) = A dx^2 + B dx dy + C dy^2
+//   floats [8, 8+P) merged weights
+//   bytes after     P column indices (lev * 64 + idx; sink column for merged repeats)
+//   last 16 bytes   culling half-extents (ex, ey, 0, 0)
+// The part before the extents is what a warp stages in shared memory.
+__host__ __device__ constexpr int smem_record_bytes(int P) { return ((32 + 5 * P) + 15) / 16 * 16; }
+__host__ __device__ constexpr int record_bytes(int P) { return smem_record_bytes(P) + 16; }
+
+template <int LEVELS, int K, int TW, int TH>
+struct SplatCfg {
+    static constexpr int kThreads = TW * TH;
+    static constexpr int kWarps = kThreads / 32;
+    static constexpr int kPairs = LEVELS * K;
+    static constexpr int kCols = LEVELS * 64 + 1;  // + sink column
+    static constexpr int kAccFloats = (kCols * 33 + 3) / 4 * 4;
+    static constexpr int kSmemRecFloats = smem_record_bytes(kPairs) / 4;
+    static constexpr int kRecFloats = record_bytes(kPairs) / 4;
+    static constexpr int kAccBytes = kWarps * kAccFloats * 4;
+    static constexpr int kBatch =
+        (kAccBytes + kWarps * 32 * kSmemRecFloats * 4 <= 232448) ? 32 : 16;
+    static constexpr int kSmemBytes = kAccBytes + kWarps * kBatch * kSmemRecFloats * 4;
+    static_assert(kThreads % 32 == 0 && 32 % TW == 0, "a warp covers whole rows of a tile");
+    static_assert(kPairs <= kMaxPairs, "pairs per record");
+};
+
+struct PackArgs {
+    int64_t n;
+    int levels, K, rec_bytes;
+    const float* xy;
+    const float* conic_o;
+    const float* extent;
+    const uint8_t* idx;
+    const float* w;
+    float* recs;
+    int32_t* status;
+};
+
+struct SplatArgs {
+    lsv2_camera cam;
+    const uint32_t* tile_ranges;
+    const uint32_t* gauss_ids;
+    const float* recs;
+    float* coeff;
+    float* final_T;
+    uint32_t* n_last;
+    int32_t* status;
+};
+
+bool splat_supported(int levels, int K, int L, int tw, int th);
+int splat_record_bytes(int levels, int K);
+cudaError_t launch_pack(const PackArgs& a, cudaStream_t stream);
+cudaError_t launch_splat(int levels, int K, const SplatArgs& a, cudaStream_t stream);
+
+}  // namespace lsv2

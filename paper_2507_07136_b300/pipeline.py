@@ -1,0 +1,143 @@
+"""Torch-side pipeline around the C ABI: device buffers, streams, and the call sequence.
+
+PyTorch only provides device memory and streams here; every step of the path runs in the
+CUDA library through ``_lib``.  ``Frame`` owns the per-camera buffers, so the steady-state
+call sequence allocates nothing and can be captured in a CUDA graph.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import torch
+
+from . import _lib as L
+
+L_CODEBOOK = 64
+
+
+def _ptr(t: torch.Tensor | None) -> int:
+    return 0 if t is None else t.data_ptr()
+
+
+def _stream(stream: torch.cuda.Stream | None) -> int:
+    return (stream or torch.cuda.current_stream()).cuda_stream
+
+
+@dataclass
+class DeviceScene:
+    """Gaussians and their sparse coefficients, resident in HBM (activated values)."""
+    means: torch.Tensor      # f32 [N, 3]
+    scales: torch.Tensor     # f32 [N, 3]
+    quats: torch.Tensor      # f32 [N, 4]
+    opacity: torch.Tensor    # f32 [N]
+    idx: torch.Tensor        # u8  [N, levels, K]
+    weights: torch.Tensor    # f32 [N, levels, K]
+    codebook: torch.Tensor   # f32 [levels, L, D]
+
+    @property
+    def n(self) -> int:
+        return int(self.means.shape[0])
+
+    @property
+    def levels(self) -> int:
+        return int(self.idx.shape[1])
+
+    @property
+    def K(self) -> int:
+        return int(self.idx.shape[2])
+
+    @property
+    def D(self) -> int:
+        return int(self.codebook.shape[2])
+
+    @staticmethod
+    def from_numpy(sc, device="cuda") -> "DeviceScene":
+        def f(a, dt=torch.float32):
+            return torch.as_tensor(a).to(device=device, dtype=dt).contiguous()
+        return DeviceScene(f(sc.means), f(sc.scales), f(sc.quats), f(sc.opacity), f(sc.idx, torch.uint8),
+                           f(sc.weights), f(sc.codebook))
+
+
+class Frame:
+    """Per-camera buffers and the project -> bin_sort -> splat -> decode / query sequence."""
+
+    def __init__(self, scene: DeviceScene, cam, capacity: int | None = None, device="cuda"):
+        self.scene, self.cam, self.device = scene, cam, device
+        self.ccam = L.camera(cam)
+        n = scene.n
+        dev = torch.device(device)
+        self.xy = torch.empty((n, 4), dtype=torch.float32, device=dev)
+        self.conic_o = torch.empty((n, 4), dtype=torch.float32, device=dev)
+        self.extent = torch.empty((n, 2), dtype=torch.float32, device=dev)
+        self.depth = torch.empty(n, dtype=torch.float32, device=dev)
+        self.radius = torch.empty(n, dtype=torch.int32, device=dev)
+        self.rect = torch.empty((n, 4), dtype=torch.int32, device=dev)
+        self.tiles_touched = torch.empty(n, dtype=torch.int32, device=dev)
+        self.flags = torch.empty(n, dtype=torch.uint8, device=dev)
+        self.proj = L.lsv2_proj(_ptr(self.xy), _ptr(self.conic_o), _ptr(self.extent), _ptr(self.depth),
+                                _ptr(self.radius), _ptr(self.rect), _ptr(self.tiles_touched), _ptr(self.flags))
+        self.status = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.num_instances = torch.zeros(1, dtype=torch.int64, device=dev)
+        self.T = cam.num_tiles
+        self.P = cam.num_pixels
+        self.tile_ranges = torch.empty((self.T, 2), dtype=torch.int32, device=dev)
+        if capacity is None:
+            self.project()
+            capacity = max(1024, int(self.tiles_touched.sum().item() * 1.25) + 1024)
+        self.capacity = int(capacity)
+        self.gauss_ids = torch.empty(self.capacity, dtype=torch.int32, device=dev)
+        self.bin_ws_bytes = L.lsv2_bin_sort_workspace_bytes(n, self.capacity, self.T)
+        self.bin_ws = torch.empty(self.bin_ws_bytes, dtype=torch.uint8, device=dev)
+        self.splat_ws_bytes = L.lsv2_splat_workspace_bytes(n, scene.levels, scene.K)
+        self.splat_ws = torch.empty(max(self.splat_ws_bytes, 16), dtype=torch.uint8, device=dev)
+        self.coeff = torch.empty((scene.levels, self.P, L_CODEBOOK), dtype=torch.float32, device=dev)
+        self.final_T = torch.empty(self.P, dtype=torch.float32, device=dev)
+        self.n_last = torch.empty(self.P, dtype=torch.int32, device=dev)
+        self.query_ws = None
+
+    # ------------------------------------------------------------------ steps
+    def project(self, stream=None):
+        s = self.scene
+        L.lsv2_project(self.ccam, s.n, _ptr(s.means), _ptr(s.scales), _ptr(s.quats), _ptr(s.opacity), self.proj,
+                       _ptr(self.status), _stream(stream))
+
+    def bin_sort(self, stream=None):
+        L.lsv2_bin_sort(self.ccam, self.scene.n, self.proj, _ptr(self.bin_ws), self.bin_ws_bytes,
+                        _ptr(self.gauss_ids), self.capacity, _ptr(self.tile_ranges), _ptr(self.num_instances),
+                        _ptr(self.status), _stream(stream))
+
+    def splat(self, stream=None):
+        s = self.scene
+        L.lsv2_splat_coeffs(self.ccam, s.n, self.proj, _ptr(self.tile_ranges), _ptr(self.gauss_ids), s.levels, s.K,
+                            L_CODEBOOK, _ptr(s.idx), _ptr(s.weights), _ptr(self.splat_ws), self.splat_ws_bytes,
+                            _ptr(self.coeff), _ptr(self.final_T), _ptr(self.n_last), _ptr(self.status),
+                            _stream(stream))
+
+    def render(self, stream=None):
+        self.project(stream)
+        self.bin_sort(stream)
+        self.splat(stream)
+
+    def decode(self, out: torch.Tensor, codebook: torch.Tensor | None = None, stream=None):
+        cb = self.scene.codebook if codebook is None else codebook
+        cb_dt = L.LSV2_BF16 if cb.dtype == torch.bfloat16 else L.LSV2_F32
+        out_dt = L.LSV2_BF16 if out.dtype == torch.bfloat16 else L.LSV2_F32
+        L.lsv2_decode(self.scene.levels, self.P, L_CODEBOOK, self.scene.D, _ptr(self.coeff), L.LSV2_F32, _ptr(cb),
+                      cb_dt, _ptr(out), out_dt, _stream(stream))
+
+    def query(self, text: torch.Tensor, out: torch.Tensor, tau: float = 10.0, compute=L.LSV2_F32, stream=None):
+        Q, nt, D = text.shape
+        need = L.lsv2_query_workspace_bytes(self.scene.levels, L_CODEBOOK, Q, nt - 1)
+        if self.query_ws is None or self.query_ws.numel() < need:
+            self.query_ws = torch.empty(need, dtype=torch.uint8, device=self.device)
+        out_dt = L.LSV2_BF16 if out.dtype == torch.bfloat16 else L.LSV2_F32
+        L.lsv2_query(self.scene.levels, self.P, L_CODEBOOK, D, _ptr(self.coeff), L.LSV2_F32, _ptr(self.scene.codebook),
+                     Q, nt - 1, _ptr(text), float(tau), _ptr(self.query_ws), need, _ptr(out), out_dt, compute,
+                     _stream(stream))
+
+    def check(self):
+        """Synchronise and raise if a kernel reported a device-side condition."""
+        torch.cuda.synchronize()
+        code = int(self.status.item())
+        if code != 0:
+            raise L.LSV2Error("device status", code)

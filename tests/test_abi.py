@@ -1,0 +1,67 @@
+"""The C-ABI library loads, exports every entry point include/lsv2.h declares, and rejects bad
+arguments on the host (no GPU needed: these paths return before any CUDA call)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_2507_07136_b300 import _lib as L
+from paper_2507_07136_b300.build import build as build_lib
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "lsv2.h")
+
+
+def declared_in_header():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lsv2_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build_lib()
+    return L.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_in_header()
+    assert len(names) >= 13
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(L.declared_symbols()) == names
+
+
+def test_version_and_status_strings(lib):
+    assert L.lsv2_abi_version() == 1
+    assert lib.lsv2_status_string(0) == b"ok"
+    assert lib.lsv2_status_string(3) == b"instance capacity exceeded"
+
+
+def test_workspace_queries(lib):
+    assert L.lsv2_splat_workspace_bytes(1000, 3, 4) >= 1000 * 112
+    assert L.lsv2_bin_sort_workspace_bytes(10, 1 << 20, 6120) >= 2 * 8 * (1 << 20)
+    assert L.lsv2_query_workspace_bytes(3, 64, 1, 4) >= 3 * 69 * 64 * 4
+    assert L.lsv2_query_workspace_bytes(3, 32, 1, 4) == 0
+
+
+def _cam(w=64, h=48, tile=16):
+    import lsv2_synth as syn
+    return L.camera(syn.orbit_camera(w, h, 4.0, tile=(tile, tile)))
+
+
+def test_host_validation_rejects_bad_arguments(lib):
+    cam = _cam()
+    proj = L.lsv2_proj()
+    # null camera, null projection buffers, bad tile shape: all rejected before any launch
+    assert lib.lsv2_project(None, 10, 0, 0, 0, 0, C.byref(proj), 0, 0) == 1
+    assert lib.lsv2_project(C.byref(cam), 10, 0, 0, 0, 0, C.byref(proj), 0, 0) == 1
+    bad = _cam(tile=12)
+    assert lib.lsv2_project(C.byref(bad), 0, 0, 0, 0, 0, C.byref(proj), 0, 0) == 1
+    # unsupported decode shapes
+    assert lib.lsv2_decode(1, 10, 32, 512, 16, 0, 16, 0, 16, 0, 0) == 2
+    assert lib.lsv2_decode(1, 10, 64, 500, 16, 0, 16, 0, 16, 0, 0) == 2
+    # query: null text
+    assert lib.lsv2_query(1, 10, 64, 512, 16, 0, 16, 1, 4, 0, 10.0, 16, 1 << 20, 16, 0, 0, 0) == 1
+    with pytest.raises(L.LSV2Error):
+        L.call("lsv2_decode", 1, 10, 32, 512, 16, 0, 16, 0, 16, 0, 0)
