@@ -1,0 +1,287 @@
+"""Benchmark of the sparse-coefficient splatting hot path on one B300 (or N replicas).
+
+Workload: 300,000 Gaussians (means N(0, 2^2), log-scales N(-4.5, 0.5)), three semantic levels,
+K = 4 pairs over an L = 64 codebook of D = 512 features, one 1440x1080 camera at radius 6, one
+text query with four negatives.  One step renders one frame through every stage of the path:
+project -> bin_sort -> splat_coeffs -> decode (F materialised in HBM) -> query (relevancy).
+
+Printed as one JSON line.  `value` is frames per second over all ranks, device-timed with CUDA
+events per step (L2 flushed between steps, flush not timed).  `e2e` runs the same steps through
+the C ABI with the per-step inputs (camera, text embeddings) copied from pinned host memory
+and the relevancy map copied back, host-timed.  `roofline` is for the stage that dominates the
+step.  `cpu_baseline` times the FP64 oracle (single thread) on a bounded sample of the frame.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "coeff-splat+decode FPS and query FPS @1440x1080, 300k Gaussians; % HBM/tensor roofline"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_PEAKS = {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}
+# FP32 FMA pipe: 148 SMs x 128 lanes x 2 flop x 2.032 GHz (maximum SM clock)
+FP32_ALU_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return FALLBACK_PEAKS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while the timed region runs."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index, self.rows, self.proc = index, [], None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ----------------------------------------------------------------------------- CPU baseline
+def cpu_baseline(max_seconds: float = 20.0):
+    """The FP64 oracle as it stands, single-threaded, on a bounded sample of one frame:
+    projection + binning of all 300k Gaussians, then blend + decode + relevancy of a random
+    pixel sample, scaled to the full 1,555,200-pixel frame."""
+    import lsv2_synth as syn
+    from oracle import oracle as O
+    sc, cam, text = syn.at_scale()
+    t0 = time.perf_counter()
+    pr = O.project(cam, sc.means, sc.scales, sc.quats)
+    ids, ranges = O.bin(cam, pr)
+    t_geom = time.perf_counter() - t0
+    rng = np.random.default_rng(0)
+    npix = 2000
+    px = rng.integers(0, cam.width, npix).astype(np.int32)
+    py = rng.integers(0, cam.height, npix).astype(np.int32)
+    t1 = time.perf_counter()
+    bl = O.blend(cam, pr, sc.opacity, ids, ranges, idx=sc.idx, w=sc.weights, px=px, py=py)
+    F = O.decode(bl.out, sc.codebook)
+    O.relevancy(F, text, 10.0)
+    t_pix = (time.perf_counter() - t1) / npix
+    frame_s = t_geom + t_pix * cam.num_pixels
+    return {"value": 1.0 / frame_s, "unit": "frames/s", "cores": 1, "kind": "oracle",
+            "sample": f"project+bin all 300k Gaussians ({t_geom:.2f} s) + blend/decode/relevancy of {npix} random "
+                      f"pixels ({t_pix * 1e3:.3f} ms/px), scaled to 1,555,200 px; single thread, FP64"}
+
+
+def reference_arm(args):
+    """The oracle as the reference arm: each step is one bounded-sample frame estimate."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        cpu_baseline()
+    t0 = time.perf_counter()
+    samples = [cpu_baseline() for _ in range(args.steps)]
+    elapsed = time.perf_counter() - t0
+    v = float(np.mean([c["value"] for c in samples]))
+    cb = dict(samples[-1])
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "frames/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "300k Gaussians, 3 levels, K=4, L=64, D=512, 1440x1080, 1 query + 4 negatives"},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "note": f"FP64 CPU oracle as the reference arm; {args.steps} sampled frames in {elapsed:.1f} s"}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+    import lsv2_synth as syn
+    from paper_2507_07136_b300.pipeline import DeviceScene, Frame
+    from paper_2507_07136_b300 import build as _  # noqa: F401
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    assert args.warmup >= 3, "at least 3 warm-up steps"
+    dev = torch.device("cuda", local)
+
+    sc, cam, text = syn.at_scale()
+    scene = DeviceScene.from_numpy(sc, device=dev)
+    frame = Frame(scene, cam, device=dev)
+    P = cam.num_pixels
+    F = torch.empty((scene.levels, P, scene.D), dtype=torch.float32, device=dev)
+    text_d = torch.as_tensor(text, device=dev)
+    rel = torch.empty((text.shape[0], scene.levels, P), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    stages = ["project", "bin_sort", "splat", "decode", "query"]
+    fns = {"project": frame.project, "bin_sort": frame.bin_sort, "splat": frame.splat,
+           "decode": lambda: frame.decode(F), "query": lambda: frame.query(text_d, rel)}
+    launches_per_step = {"project": 1, "bin_sort": 5, "splat": 2, "decode": 1, "query": 2}
+
+    def step(ev=None):
+        for i, s in enumerate(stages):
+            if ev is not None:
+                ev[i].record(stream)
+            fns[s]()
+        if ev is not None:
+            ev[len(stages)].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+        flush.fill_(1)
+    frame.check()
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(stages) + 1)] for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_wall = time.perf_counter()
+        for k in range(args.steps):
+            step(evs[k])
+            flush.fill_(1)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    if world > 1:
+        dist.barrier()
+    frame.check()
+    stage_ms = {s: float(np.mean([evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.steps)]))
+                for i, s in enumerate(stages)}
+    step_ms = float(np.mean([evs[k][0].elapsed_time(evs[k][len(stages)]) for k in range(args.steps)]))
+    if world > 1:
+        t = torch.tensor([step_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t.item())
+    value = world * 1e3 / step_ms
+
+    # ---- end to end through the C ABI with host buffers ----
+    text_h = torch.as_tensor(text).pin_memory()
+    rel_h = torch.empty(rel.shape, dtype=rel.dtype).pin_memory()
+    for _ in range(2):
+        text_d.copy_(text_h, non_blocking=True)
+        step()
+        rel_h.copy_(rel, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_steps = max(3, args.steps // 2)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        text_d.copy_(text_h, non_blocking=True)
+        step()
+        rel_h.copy_(rel, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    # ---- roofline of the dominant stage ----
+    pk, pk_kind = peaks()
+    dom = max(stage_ms, key=stage_ms.get)
+    levels, D = scene.levels, scene.D
+    if dom == "decode":
+        flops = 2.0 * P * 64 * D * levels
+        roof = {"bound": "alu", "achieved": flops / (stage_ms[dom] * 1e-3) / 1e12, "peak": FP32_ALU_TFLOPS,
+                "unit": "TFLOP/s", "traffic": None, "kernel": "decode_f32_kernel",
+                "peak_source": "148 SM x 128 FP32 lanes x 2 flop x 2.032 GHz"}
+    else:
+        nbytes = levels * P * 64 * 4
+        roof = {"bound": "hbm", "achieved": nbytes / (stage_ms[dom] * 1e-3) / 1e9, "peak": pk["hbm_gbs"],
+                "unit": "GB/s", "traffic": None, "kernel": dom, "peak_source": pk_kind}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    gpu_launches = sum(launches_per_step.values()) * args.steps
+
+    line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "300k Gaussians, 3 levels, K=4, L=64, D=512, 1440x1080, 1 query + 4 negatives",
+                       "path": "FP32 (CUDA-core decode and query)", "parallelism": f"replicas x{world}",
+                       "l2": "flushed between steps (256 MiB write, untimed)",
+                       "instances": int(frame.num_instances.item())},
+            "stages_ms": stage_ms,
+            "splat_decode_fps": 1e3 / (stage_ms["project"] + stage_ms["bin_sort"] + stage_ms["splat"] + stage_ms["decode"]),
+            "query_fps": 1e3 / (stage_ms["project"] + stage_ms["bin_sort"] + stage_ms["splat"] + stage_ms["query"]),
+            "roofline": roof,
+            "e2e": {"value": world * 1e3 / e2e_ms, "unit": "frames/s", "h2d_bytes_per_step": text_h.numel() * 4,
+                    "d2h_bytes_per_step": rel_h.numel() * 4},
+            "gpu_launches": gpu_launches,
+            "clocks": clk.summary(),
+            "wall_s_timed_region": t_wall}
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -146,13 +146,14 @@ lsv2_status lsv2_splat_coeffs(const lsv2_camera* cam, int64_t n, const lsv2_proj
 
 /* Decode (Eq. 7): feat[lev][p][:] = coeff[lev][p][:] . codebook[lev].
  *   coeff    [levels][P][L]  dtype coeff_dtype (F32 or BF16)
- *   codebook [levels][L][D]  dtype codebook_dtype
- *   feat     [levels][P][D]  dtype out_dtype
- * Supported: (F32, F32, F32) on CUDA cores (FP32 FMA); (BF16 or F32 coeff, BF16 codebook,
- * BF16 or F32 out) on the tensor cores (tcgen05, FP32 accumulation).  L = 64, D % 128 == 0. */
+ *   codebook [levels][L][D]  dtype codebook_dtype (F32 or BF16)
+ *   feat     [levels][P][D]  dtype out_dtype (F32 or BF16)
+ * All three F32: FP32 FMA on the CUDA cores.  Any BF16 among them: tensor cores (tcgen05),
+ * with both operands rounded to BF16 and FP32 accumulation.  L = 64, D % 128 == 0 (tensor
+ * cores: D <= 512).  A bounded device wait that expires sets LSV2_ERR_TIMEOUT. */
 lsv2_status lsv2_decode(int32_t levels, int64_t P, int32_t L, int32_t D, const void* coeff,
                         lsv2_dtype coeff_dtype, const void* codebook, lsv2_dtype codebook_dtype,
-                        void* feat, lsv2_dtype out_dtype, void* stream);
+                        void* feat, lsv2_dtype out_dtype, int32_t* dev_status, void* stream);
 
 /* Workspace for lsv2_query: per level the Gram matrix S S^T and the projected texts S t. */
 size_t lsv2_query_workspace_bytes(int32_t levels, int32_t L, int32_t Q, int32_t n_neg);

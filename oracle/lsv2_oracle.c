@@ -391,7 +391,8 @@ int64_t orc_count_instances(const orc_camera* c, int64_t n, const uint8_t* flags
     return total;
 }
 
-/* Fills gauss_ids[I] and tile_ranges[num_tiles][2] = [start, end). Returns I. */
+/* Fills gauss_ids[I] and tile_ranges[num_tiles][2] = [start, end) with start = number of
+ * instances in earlier tiles (so empty tiles have start == end == that prefix). Returns I. */
 int64_t orc_bin(const orc_camera* c, int64_t n, const uint8_t* flags, const int32_t* rect,
                 const float* depth_key, uint32_t* gauss_ids, uint32_t* tile_ranges)
 {
@@ -412,12 +413,18 @@ int64_t orc_bin(const orc_camera* c, int64_t n, const uint8_t* flags, const int3
             }
     }
     qsort(keys, (size_t)total, sizeof(inst_key), inst_cmp);
+    /* ranges as prefix sums: [number of instances in earlier tiles, ... + this tile's count) */
     for (int64_t t = 0; t < (int64_t)GX * GY; ++t) { tile_ranges[2 * t] = 0; tile_ranges[2 * t + 1] = 0; }
     for (int64_t i = 0; i < total; ++i) {
         gauss_ids[i] = keys[i].gid;
-        uint32_t t = keys[i].tile;
-        if (i == 0 || keys[i - 1].tile != t) tile_ranges[2 * t] = (uint32_t)i;
-        tile_ranges[2 * t + 1] = (uint32_t)(i + 1);
+        tile_ranges[2 * keys[i].tile + 1] += 1; /* count */
+    }
+    uint32_t run = 0;
+    for (int64_t t = 0; t < (int64_t)GX * GY; ++t) {
+        uint32_t cnt = tile_ranges[2 * t + 1];
+        tile_ranges[2 * t] = run;
+        run += cnt;
+        tile_ranges[2 * t + 1] = run;
     }
     free(keys);
     return total;

@@ -44,7 +44,7 @@ _SIGS = {
     "lsv2_bin_sort": ([P, I64, P, P, SZ, P, I64, P, P, P, P], I32),
     "lsv2_splat_workspace_bytes": ([I64, I32, I32], SZ),
     "lsv2_splat_coeffs": ([P, I64, P, P, P, I32, I32, I32, P, P, P, SZ, P, P, P, P, P], I32),
-    "lsv2_decode": ([I32, I64, I32, I32, P, I32, P, I32, P, I32, P], I32),
+    "lsv2_decode": ([I32, I64, I32, I32, P, I32, P, I32, P, I32, P, P], I32),
     "lsv2_query_workspace_bytes": ([I32, I32, I32, I32], SZ),
     "lsv2_query": ([I32, I64, I32, I32, P, I32, P, I32, I32, P, F32, P, SZ, P, I32, I32, P], I32),
     "lsv2_l1_decode_backward": ([I32, I64, I32, I32, P, P, P, P, P, P, P], I32),
@@ -122,8 +122,9 @@ def lsv2_splat_coeffs(cam, n, proj, tile_ranges, gauss_ids, levels, K, L, idx, w
          ws_bytes, coeff, final_T, n_last, dev_status, stream)
 
 
-def lsv2_decode(levels, P_, L, D, coeff, coeff_dtype, codebook, codebook_dtype, feat, out_dtype, stream):
-    call("lsv2_decode", levels, P_, L, D, coeff, coeff_dtype, codebook, codebook_dtype, feat, out_dtype, stream)
+def lsv2_decode(levels, P_, L, D, coeff, coeff_dtype, codebook, codebook_dtype, feat, out_dtype, dev_status, stream):
+    call("lsv2_decode", levels, P_, L, D, coeff, coeff_dtype, codebook, codebook_dtype, feat, out_dtype, dev_status,
+         stream)
 
 
 def lsv2_query_workspace_bytes(levels, L, Q, n_neg) -> int:

@@ -6,6 +6,7 @@
 #include "backward.cuh"
 #include "binsort.cuh"
 #include "decode.cuh"
+#include "decode_tc.cuh"
 #include "device.cuh"
 #include "project.cuh"
 #include "query.cuh"
@@ -132,16 +133,23 @@ lsv2_status lsv2_splat_coeffs(const lsv2_camera* cam, int64_t n, const lsv2_proj
 
 lsv2_status lsv2_decode(int32_t levels, int64_t P, int32_t L, int32_t D, const void* coeff, lsv2_dtype coeff_dtype,
                         const void* codebook, lsv2_dtype codebook_dtype, void* feat, lsv2_dtype out_dtype,
-                        void* stream)
+                        int32_t* dev_status, void* stream)
 {
     if (levels < 1 || P < 0 || !coeff || !codebook || !feat) return LSV2_ERR_INVALID_ARGUMENT;
     if (L != 64 || D <= 0 || D % 128 != 0) return LSV2_ERR_UNSUPPORTED;
     if (!aligned16(coeff) || !aligned16(codebook) || !aligned16(feat)) return LSV2_ERR_INVALID_ARGUMENT;
+    const bool dt_ok = (coeff_dtype == LSV2_F32 || coeff_dtype == LSV2_BF16) &&
+                       (codebook_dtype == LSV2_F32 || codebook_dtype == LSV2_BF16) &&
+                       (out_dtype == LSV2_F32 || out_dtype == LSV2_BF16);
+    if (!dt_ok) return LSV2_ERR_INVALID_ARGUMENT;
     if (coeff_dtype == LSV2_F32 && codebook_dtype == LSV2_F32 && out_dtype == LSV2_F32)
         return cuda_status(launch_decode_f32(levels, P, D, static_cast<const float*>(coeff),
                                              static_cast<const float*>(codebook), static_cast<float*>(feat),
                                              S(stream)));
-    return LSV2_ERR_UNSUPPORTED;
+    if (!decode_tc_supported(D)) return LSV2_ERR_UNSUPPORTED;
+    return cuda_status(launch_decode_tc(levels, P, D, coeff, coeff_dtype == LSV2_BF16, codebook,
+                                        codebook_dtype == LSV2_BF16, feat, out_dtype == LSV2_BF16, sm_count(),
+                                        dev_status, S(stream)));
 }
 
 size_t lsv2_query_workspace_bytes(int32_t levels, int32_t L, int32_t Q, int32_t n_neg)

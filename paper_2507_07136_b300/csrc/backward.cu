@@ -336,7 +336,8 @@ __global__ void __launch_bounds__(TW* TH) splat_backward_kernel(SplatBwdArgs a)
                 const float alpha = fminf(kAlphaMax, raw);
                 if (alpha >= kAlphaMin) {
                     contrib = true;
-                    const float Ti = T / (1.0f - alpha);
+                    const float oma = one_minus_alpha(alpha, g1.w, p2);
+                    const float Ti = T / oma;
                     const float e = alpha * Ti;
                     float gsum = 0.0f;
 #pragma unroll
@@ -346,7 +347,7 @@ __global__ void __launch_bounds__(TW* TH) splat_backward_kernel(SplatBwdArgs a)
                         gsum = fmaf(gw, wr[p], gsum);
                     }
                     const float dalpha = Ti * (gsum - Bsum);
-                    Bsum = fmaf(alpha, gsum, (1.0f - alpha) * Bsum);
+                    Bsum = fmaf(alpha, gsum, oma * Bsum);
                     T = Ti;
                     if (!(raw > kAlphaMax)) {
                         const float dpow = dalpha * alpha;

@@ -20,11 +20,23 @@ constexpr float kAlphaMax = 0.99f;
 constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kTMin = 1e-4f;
 constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
 
 // First nonzero status wins; never traps.
 __device__ __forceinline__ void report(int32_t* status, int32_t code)
 {
     if (status) atomicCAS(status, 0, code);
+}
+
+// 1 - alpha for alpha = min(0.99, o 2^p2) with p2 = power * log2(e) <= 0, without the
+// cancellation of `1 - alpha` near alpha = 1 (which would multiply alpha's relative error by
+// alpha / (1 - alpha) in every later transmittance): for alpha > 1/2 (hence o > 1/2, where
+// 1 - o is exact), 1 - o e^p = (1 - o) - o expm1(p), a sum of two non-negative terms.
+__device__ __forceinline__ float one_minus_alpha(float alpha, float o, float p2)
+{
+    if (alpha == kAlphaMax) return 1.0f - kAlphaMax;
+    if (alpha <= 0.5f) return 1.0f - alpha;
+    return fmaf(-o, expm1f(p2 * kLn2), 1.0f - o);
 }
 
 // ----------------------------------------------------------------------------------------

@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(TW* TH) splat_kernel(SplatArgs a)
                 asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(ex2) : "f"(p2));
                 const float alpha = fminf(kAlphaMax, g1.w * ex2);
                 if (alpha >= kAlphaMin) {
-                    const float test_T = T * (1.0f - alpha);
+                    const float test_T = T * one_minus_alpha(alpha, g1.w, p2);
                     if (test_T < kTMin) {
                         done = true;
                     } else {

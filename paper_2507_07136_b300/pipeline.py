@@ -118,12 +118,17 @@ class Frame:
         self.bin_sort(stream)
         self.splat(stream)
 
-    def decode(self, out: torch.Tensor, codebook: torch.Tensor | None = None, stream=None):
+    def decode(self, out: torch.Tensor, codebook: torch.Tensor | None = None, tensor_cores: bool | None = None,
+               stream=None):
+        """F = W S.  FP32 out + FP32 codebook -> CUDA-core FP32 path unless tensor_cores=True;
+        any BF16 operand or tensor_cores=True -> tcgen05 path (BF16 operands, FP32 accumulation)."""
         cb = self.scene.codebook if codebook is None else codebook
         cb_dt = L.LSV2_BF16 if cb.dtype == torch.bfloat16 else L.LSV2_F32
         out_dt = L.LSV2_BF16 if out.dtype == torch.bfloat16 else L.LSV2_F32
+        if tensor_cores and cb_dt == L.LSV2_F32 and out_dt == L.LSV2_F32:
+            raise ValueError("the tensor-core decode needs a BF16 codebook or BF16 output")
         L.lsv2_decode(self.scene.levels, self.P, L_CODEBOOK, self.scene.D, _ptr(self.coeff), L.LSV2_F32, _ptr(cb),
-                      cb_dt, _ptr(out), out_dt, _stream(stream))
+                      cb_dt, _ptr(out), out_dt, _ptr(self.status), _stream(stream))
 
     def query(self, text: torch.Tensor, out: torch.Tensor, tau: float = 10.0, compute=L.LSV2_F32, stream=None):
         Q, nt, D = text.shape

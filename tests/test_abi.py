@@ -59,9 +59,10 @@ def test_host_validation_rejects_bad_arguments(lib):
     bad = _cam(tile=12)
     assert lib.lsv2_project(C.byref(bad), 0, 0, 0, 0, 0, C.byref(proj), 0, 0) == 1
     # unsupported decode shapes
-    assert lib.lsv2_decode(1, 10, 32, 512, 16, 0, 16, 0, 16, 0, 0) == 2
-    assert lib.lsv2_decode(1, 10, 64, 500, 16, 0, 16, 0, 16, 0, 0) == 2
+    assert lib.lsv2_decode(1, 10, 32, 512, 16, 0, 16, 0, 16, 0, 0, 0) == 2
+    assert lib.lsv2_decode(1, 10, 64, 500, 16, 0, 16, 0, 16, 0, 0, 0) == 2
+    assert lib.lsv2_decode(1, 10, 64, 512, 16, 0, 16, 7, 16, 0, 0, 0) == 1
     # query: null text
     assert lib.lsv2_query(1, 10, 64, 512, 16, 0, 16, 1, 4, 0, 10.0, 16, 1 << 20, 16, 0, 0, 0) == 1
     with pytest.raises(L.LSV2Error):
-        L.call("lsv2_decode", 1, 10, 32, 512, 16, 0, 16, 0, 16, 0, 0)
+        L.call("lsv2_decode", 1, 10, 32, 512, 16, 0, 16, 0, 16, 0, 0, 0)
