@@ -55,7 +55,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -149,10 +149,11 @@ def reference_arm(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp32-path", action="store_true", help="skip the plain FP32 comparison measurement")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)
@@ -175,15 +176,17 @@ def main():
     scene = DeviceScene.from_numpy(sc, device=dev)
     frame = Frame(scene, cam, device=dev)
     P = cam.num_pixels
-    F = torch.empty((scene.levels, P, scene.D), dtype=torch.float32, device=dev)
+    levels, D = scene.levels, scene.D
+    F = torch.empty((levels, P, D), dtype=torch.bfloat16, device=dev)
+    cb16 = scene.codebook.to(torch.bfloat16)
     text_d = torch.as_tensor(text, device=dev)
-    rel = torch.empty((text.shape[0], scene.levels, P), dtype=torch.float32, device=dev)
+    rel = torch.empty((text.shape[0], levels, P), dtype=torch.float32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
     stages = ["project", "bin_sort", "splat", "decode", "query"]
     fns = {"project": frame.project, "bin_sort": frame.bin_sort, "splat": frame.splat,
-           "decode": lambda: frame.decode(F), "query": lambda: frame.query(text_d, rel)}
+           "decode": lambda: frame.decode(F, codebook=cb16), "query": lambda: frame.query(text_d, rel)}
     launches_per_step = {"project": 1, "bin_sort": 5, "splat": 2, "decode": 1, "query": 2}
 
     def step(ev=None):
@@ -194,33 +197,48 @@ def main():
         if ev is not None:
             ev[len(stages)].record(stream)
 
+    def timed(n_steps):
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(stages) + 1)] for _ in range(n_steps)]
+        for k in range(n_steps):
+            step(evs[k])
+            flush.fill_(1)
+        torch.cuda.synchronize()
+        st = {s: float(np.mean([evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(n_steps)]))
+              for i, s in enumerate(stages)}
+        return st, float(np.mean([evs[k][0].elapsed_time(evs[k][len(stages)]) for k in range(n_steps)]))
+
     for _ in range(args.warmup):
         step()
         flush.fill_(1)
     frame.check()
-
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(stages) + 1)] for _ in range(args.steps)]
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         t_wall = time.perf_counter()
-        for k in range(args.steps):
-            step(evs[k])
-            flush.fill_(1)
-        torch.cuda.synchronize()
+        stage_ms, step_ms = timed(args.steps)
         t_wall = time.perf_counter() - t_wall
     if world > 1:
         dist.barrier()
     frame.check()
-    stage_ms = {s: float(np.mean([evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.steps)]))
-                for i, s in enumerate(stages)}
-    step_ms = float(np.mean([evs[k][0].elapsed_time(evs[k][len(stages)]) for k in range(args.steps)]))
     if world > 1:
         t = torch.tensor([step_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         step_ms = float(t.item())
     value = world * 1e3 / step_ms
+
+    # ---- the plain FP32 GPU form (CUDA-core decode to an FP32 feature map), for comparison ----
+    fp32 = None
+    if not args.no_fp32_path:
+        del F
+        F32 = torch.empty((levels, P, D), dtype=torch.float32, device=dev)
+        fns["decode"] = lambda: frame.decode(F32)
+        timed(2)
+        st32, ms32 = timed(max(3, args.steps // 4))
+        fp32 = {"ms_per_step": ms32, "fps": 1e3 / ms32, "stages_ms": st32}
+        del F32
+        F = torch.empty((levels, P, D), dtype=torch.bfloat16, device=dev)
+        fns["decode"] = lambda: frame.decode(F, codebook=cb16)
 
     # ---- end to end through the C ABI with host buffers ----
     text_h = torch.as_tensor(text).pin_memory()
@@ -243,33 +261,39 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = float(t.item())
 
-    # ---- roofline of the dominant stage ----
+    # ---- rooflines (algorithmic bytes per launch / CUDA-event duration) ----
     pk, pk_kind = peaks()
-    dom = max(stage_ms, key=stage_ms.get)
-    levels, D = scene.levels, scene.D
-    if dom == "decode":
-        flops = 2.0 * P * 64 * D * levels
-        roof = {"bound": "alu", "achieved": flops / (stage_ms[dom] * 1e-3) / 1e12, "peak": FP32_ALU_TFLOPS,
-                "unit": "TFLOP/s", "traffic": None, "kernel": "decode_f32_kernel",
-                "peak_source": "148 SM x 128 FP32 lanes x 2 flop x 2.032 GHz"}
-    else:
-        nbytes = levels * P * 64 * 4
-        roof = {"bound": "hbm", "achieved": nbytes / (stage_ms[dom] * 1e-3) / 1e9, "peak": pk["hbm_gbs"],
-                "unit": "GB/s", "traffic": None, "kernel": dom, "peak_source": pk_kind}
-    roof["frac"] = roof["achieved"] / roof["peak"]
+    inst = int(frame.num_instances.item())
+    from paper_2507_07136_b300 import _lib as Lb
+    rec_bytes = Lb.lsv2_splat_workspace_bytes(scene.n, levels, scene.K)
+    splat_bytes = levels * P * 64 * 4 + rec_bytes + inst * 4 + P * 8
+    decode_bytes = levels * P * (64 * 4 + D * 2)
+    roofs = {
+        "splat": {"bound": "hbm", "achieved": splat_bytes / (stage_ms["splat"] * 1e-3) / 1e9, "peak": pk["hbm_gbs"],
+                  "unit": "GB/s", "traffic": None, "kernel": "splat_kernel<3,4,16,16>",
+                  "algorithmic_bytes": splat_bytes, "peak_source": pk_kind},
+        "decode": {"bound": "hbm", "achieved": decode_bytes / (stage_ms["decode"] * 1e-3) / 1e9, "peak": pk["hbm_gbs"],
+                   "unit": "GB/s", "traffic": None, "kernel": "decode_tc_kernel",
+                   "algorithmic_bytes": decode_bytes, "peak_source": pk_kind},
+    }
+    for r in roofs.values():
+        r["frac"] = r["achieved"] / r["peak"]
+    dom = max(["splat", "decode"], key=lambda k: stage_ms[k])
     gpu_launches = sum(launches_per_step.values()) * args.steps
 
     line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic",
             "config": {"workload": "300k Gaussians, 3 levels, K=4, L=64, D=512, 1440x1080, 1 query + 4 negatives",
-                       "path": "FP32 (CUDA-core decode and query)", "parallelism": f"replicas x{world}",
-                       "l2": "flushed between steps (256 MiB write, untimed)",
-                       "instances": int(frame.num_instances.item())},
+                       "path": "FP32 projection/splat/query, BF16 tensor-core decode (FP32 accumulate) to a BF16 "
+                               "feature map", "parallelism": f"replicas x{world}",
+                       "l2": "flushed between steps (256 MiB write, untimed)", "instances": inst},
             "stages_ms": stage_ms,
             "splat_decode_fps": 1e3 / (stage_ms["project"] + stage_ms["bin_sort"] + stage_ms["splat"] + stage_ms["decode"]),
             "query_fps": 1e3 / (stage_ms["project"] + stage_ms["bin_sort"] + stage_ms["splat"] + stage_ms["query"]),
-            "roofline": roof,
+            "roofline": dict(roofs[dom]),
+            "rooflines": roofs,
+            "fp32_path": fp32,
             "e2e": {"value": world * 1e3 / e2e_ms, "unit": "frames/s", "h2d_bytes_per_step": text_h.numel() * 4,
                     "d2h_bytes_per_step": rel_h.numel() * 4},
             "gpu_launches": gpu_launches,

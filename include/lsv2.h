@@ -82,6 +82,11 @@ typedef struct {
  *   rect     int32[n][4]  tile rectangle x0, y0, x1, y1 (max exclusive)
  *   tiles_touched uint32[n]  (x1 - x0) (y1 - y0), 0 when not visible
  *   flags    uint8[n]     bit0 visible, bit1 near-degenerate (FP64 decisions)
+ *   axes     float[n][8]  principal frame of the conic, used to evaluate the Gaussian:
+ *                         (c_hi, s_hi, A, B, c_lo, s_lo, kappa, 0) where (c, s) = (c_hi + c_lo,
+ *                         s_hi + s_lo) is the unit stiff axis (largest conic eigenvalue q1),
+ *                         A = -q1 log2(e) / 2, B = -q2 log2(e) / 2 (q2 the smallest), kappa =
+ *                         q1 / q2; power * log2(e) = A (e_stiff . d)^2 + B (e_soft . d)^2
  * All arrays must be 16-byte aligned. */
 typedef struct {
     float* xy;
@@ -92,6 +97,7 @@ typedef struct {
     int32_t* rect;
     uint32_t* tiles_touched;
     uint8_t* flags;
+    float* axes;
 } lsv2_proj;
 
 int32_t lsv2_abi_version(void);

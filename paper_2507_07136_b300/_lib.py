@@ -33,7 +33,7 @@ class lsv2_camera(C.Structure):
 
 class lsv2_proj(C.Structure):
     _fields_ = [("xy", P), ("conic_o", P), ("extent", P), ("depth", P), ("radius", P), ("rect", P),
-                ("tiles_touched", P), ("flags", P)]
+                ("tiles_touched", P), ("flags", P), ("axes", P)]
 
 
 _SIGS = {

@@ -36,7 +36,7 @@ bool camera_ok(const lsv2_camera* c)
 bool proj_ok(const lsv2_proj* p)
 {
     return p && p->xy && p->conic_o && p->extent && p->depth && p->radius && p->rect && p->tiles_touched &&
-           p->flags && aligned16(p->xy) && aligned16(p->conic_o) && aligned16(p->rect) &&
+           p->flags && p->axes && aligned16(p->xy) && aligned16(p->conic_o) && aligned16(p->rect) && aligned16(p->axes) &&
            (reinterpret_cast<uintptr_t>(p->extent) & 7u) == 0;
 }
 
@@ -123,8 +123,8 @@ lsv2_status lsv2_splat_coeffs(const lsv2_camera* cam, int64_t n, const lsv2_proj
     if (!aligned16(coeff) || !workspace || !aligned16(workspace) ||
         workspace_bytes < lsv2_splat_workspace_bytes(n, levels, K))
         return LSV2_ERR_INVALID_ARGUMENT;
-    PackArgs pa{n, levels, K, splat_record_bytes(levels, K), proj->xy, proj->conic_o, proj->extent, idx, w,
-                static_cast<float*>(workspace), dev_status};
+    PackArgs pa{n, levels, K, splat_record_bytes(levels, K), proj->xy, proj->axes, proj->conic_o, proj->extent, idx,
+                w, static_cast<float*>(workspace), dev_status};
     cudaError_t e = launch_pack(pa, S(stream));
     if (e != cudaSuccess) return LSV2_ERR_CUDA;
     SplatArgs sa{*cam, tile_ranges, gauss_ids, static_cast<const float*>(workspace), coeff, final_T, n_last, dev_status};
@@ -216,6 +216,7 @@ lsv2_status lsv2_splat_backward(const lsv2_camera* cam, int64_t n, const float* 
     a.tile_ranges = tile_ranges;
     a.gauss_ids = gauss_ids;
     a.xy = proj->xy;
+    a.axes = proj->axes;
     a.conic_o = proj->conic_o;
     a.extent = proj->extent;
     a.final_T = final_T;

@@ -184,31 +184,33 @@ __global__ void __launch_bounds__(256) l1_decode_backward_kernel(int64_t P, int 
 }
 
 // ------------------------------------------------------------------------------------ 2
-// Backward splat record (global, per Gaussian): g0 = (u_hi, v_hi, u_lo, v_lo),
-// g1 = (A, B, C, o) exactly as in the forward record (so alpha is recomputed bit for bit),
-// g2 = (a, b, c, 0) the conic itself, then P weights and P column bytes (no merging).
-__host__ __device__ constexpr int bwd_record_floats(int P) { return (48 + 5 * P + 15) / 16 * 4; }
+// Backward splat record (global, per Gaussian): g0 = (u_hi, v_hi, u_lo, v_lo), the principal
+// frame and opacity exactly as in the forward record (so alpha is recomputed bit for bit), the
+// conic (a, b, c, 0) for the gradient formulas, then P weights and P column bytes (no merging).
+__host__ __device__ constexpr int bwd_record_floats(int P) { return (64 + 5 * P + 15) / 16 * 4; }
 
 __global__ void __launch_bounds__(256) pack_bwd_kernel(int64_t n, int levels, int K, const float* xy,
-                                                       const float* conic_o, const uint8_t* idx, const float* w,
-                                                       float* recs)
+                                                       const float* axes, const float* conic_o, const uint8_t* idx,
+                                                       const float* w, float* recs)
 {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n) return;
     const int P = levels * K;
     float* rec = recs + (size_t)g * bwd_record_floats(P);
     const float4 cn = reinterpret_cast<const float4*>(conic_o)[g];
+    const float4 ax1 = reinterpret_cast<const float4*>(axes)[2 * g + 1];
     reinterpret_cast<float4*>(rec)[0] = reinterpret_cast<const float4*>(xy)[g];
-    reinterpret_cast<float4*>(rec)[1] = make_float4(-0.5f * kLog2e * cn.x, -kLog2e * cn.y, -0.5f * kLog2e * cn.z, cn.w);
-    reinterpret_cast<float4*>(rec)[2] = make_float4(cn.x, cn.y, cn.z, 0.0f);
-    uint8_t* cb = reinterpret_cast<uint8_t*>(rec + 12 + P);
+    reinterpret_cast<float4*>(rec)[1] = reinterpret_cast<const float4*>(axes)[2 * g];
+    reinterpret_cast<float4*>(rec)[2] = make_float4(ax1.x, ax1.y, ax1.z, cn.w);
+    reinterpret_cast<float4*>(rec)[3] = make_float4(cn.x, cn.y, cn.z, 0.0f);
+    uint8_t* cb = reinterpret_cast<uint8_t*>(rec + 16 + P);
     for (int p = 0; p < P; ++p) {
         const int lev = p / K;
         const size_t src = (size_t)g * P + p;
         const int ix = idx[src];
         const bool ok = ix < 64;
-        rec[12 + p] = ok ? w[src] : 0.0f;
-        cb[p] = (uint8_t)(ok ? lev * 64 + ix : levels * 64);
+        rec[16 + p] = ok ? w[src] : 0.0f;
+        cb[p] = (uint8_t)(lev * 64 + (ok ? ix : 0));
     }
 }
 
@@ -232,7 +234,7 @@ template <int LEVELS, int K, int TW, int TH>
 struct BwdCfg {
     static constexpr int kWarps = TW * TH / 32;
     static constexpr int kPairs = LEVELS * K;
-    static constexpr int kCols = LEVELS * 64 + 1;
+    static constexpr int kCols = LEVELS * 64;
     static constexpr int kGFloats = (kCols * 33 + 3) / 4 * 4;
     static constexpr int kRecFloats = bwd_record_floats(kPairs);
     static constexpr int kSmemRecFloats = kRecFloats - 4;  // staged without the 2D mean
@@ -274,7 +276,6 @@ __global__ void __launch_bounds__(TW* TH) splat_backward_kernel(SplatBwdArgs a)
             col[66] = v.z;
             col[99] = v.w;
         }
-    for (int i = lane; i < 33; i += 32) gW[(LEVELS * 64) * 33 + i] = 0.0f;
     __syncwarp();
 
     const uint32_t beg = a.tile_ranges[2 * tile];
@@ -318,13 +319,14 @@ __global__ void __launch_bounds__(TW* TH) splat_backward_kernel(SplatBwdArgs a)
             g0.z = __shfl_sync(0xffffffffu, my_xy.z, i);
             g0.w = __shfl_sync(0xffffffffu, my_xy.w, i);
             const float* r = stage + i * C::kSmemRecFloats;
-            const float4 g1 = *reinterpret_cast<const float4*>(r);
-            const float4 g2 = *reinterpret_cast<const float4*>(r + 4);
-            const float* wr = r + 8;
-            const uint8_t* cr = reinterpret_cast<const uint8_t*>(r + 8 + C::kPairs);
+            const float4 ax = *reinterpret_cast<const float4*>(r);
+            const float4 axl = *reinterpret_cast<const float4*>(r + 4);
+            const float4 g2 = *reinterpret_cast<const float4*>(r + 8);
+            const float* wr = r + 12;
+            const uint8_t* cr = reinterpret_cast<const uint8_t*>(r + 12 + C::kPairs);
             const float dx = __fadd_rn(__fsub_rn(g0.x, pxf), g0.z);
             const float dy = __fadd_rn(__fsub_rn(g0.y, pyf), g0.w);
-            const float p2 = fmaf(g1.x * dx, dx, fmaf(g1.z * dy, dy, g1.y * dx * dy));
+            const float p2 = eval_power2(g0, ax, axl, pxf, pyf);
             float vals[32];
 #pragma unroll
             for (int k = 0; k < 32; ++k) vals[k] = 0.0f;
@@ -332,11 +334,11 @@ __global__ void __launch_bounds__(TW* TH) splat_backward_kernel(SplatBwdArgs a)
             if (lo + i < (int)my_last && p2 <= 0.0f) {
                 float ex2;
                 asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(ex2) : "f"(p2));
-                const float raw = g1.w * ex2;
+                const float raw = axl.w * ex2;
                 const float alpha = fminf(kAlphaMax, raw);
                 if (alpha >= kAlphaMin) {
                     contrib = true;
-                    const float oma = one_minus_alpha(alpha, g1.w, p2);
+                    const float oma = one_minus_alpha(alpha, axl.w, p2);
                     const float Ti = T / oma;
                     const float e = alpha * Ti;
                     float gsum = 0.0f;
@@ -535,8 +537,8 @@ cudaError_t launch_splat_backward(int levels, int K, const SplatBwdArgs& args, c
     cudaError_t e = cudaMemsetAsync(a.grad2d, 0, (size_t)pargs.n * 8 * 4, stream);
     if (e != cudaSuccess) return e;
     if (pargs.n > 0)
-        pack_bwd_kernel<<<(unsigned)((pargs.n + 255) / 256), 256, 0, stream>>>(pargs.n, levels, K, a.xy, a.conic_o,
-                                                                              idx, w, a.recs);
+        pack_bwd_kernel<<<(unsigned)((pargs.n + 255) / 256), 256, 0, stream>>>(pargs.n, levels, K, a.xy, a.axes,
+                                                                              a.conic_o, idx, w, a.recs);
     if (levels == 1 && K == 4) e = launch_bwd_tile<1, 4>(a, stream);
     else if (levels == 1 && K == 2) e = launch_bwd_tile<1, 2>(a, stream);
     else if (levels == 1 && K == 8) e = launch_bwd_tile<1, 8>(a, stream);

@@ -10,6 +10,7 @@ struct SplatBwdArgs {
     const uint32_t* tile_ranges;
     const uint32_t* gauss_ids;
     const float* xy;
+    const float* axes;
     const float* conic_o;
     const float* extent;
     const float* final_T;

@@ -116,4 +116,41 @@ __device__ __forceinline__ dfloat df_div(dfloat x, dfloat y)
     return fast_two_sum(q1, q2);
 }
 
+// Square root with one correction step: s = sqrt(x_hi), then (x - s^2) / (2 s).
+__device__ __forceinline__ dfloat df_sqrt(dfloat x)
+{
+    if (!(x.hi > 0.0f)) return df(0.0f);
+    float s = __fsqrt_rn(x.hi);
+    dfloat r = df_sub(x, two_prod(s, s));
+    return fast_two_sum(s, __fdiv_rn(r.hi, __fmul_rn(2.0f, s)));
+}
+
+// ----------------------------------------------------------------------------------------
+// Evaluation of a projected Gaussian at a pixel, shared by the forward and backward splat.
+//   power = -1/2 d^T Q d,  d = mean2d - pixel,  Q = conic = q1 e1 e1^T + q2 e2 e2^T.
+// The conic's own entries can cancel badly for elongated footprints (terms of +-100 summing to
+// -2 at 100 px along the long axis, where rounding the entries alone moves the power by 1e-5),
+// so it is evaluated in its principal frame: power * log2(e) = A u^2 + B v^2 with u = e1 . d
+// (stiff axis) and v = e2 . d.  The stiff axis is stored as a float pair; when the footprint is
+// elongated (kappa = q1 / q2 > 4) u is formed with its low part and an exact product, so its
+// error is one rounding of u itself.  `g0` = (u_hi, v_hi, u_lo, v_lo) of the 2D mean,
+// `ax` = (c_hi, s_hi, A, B), `axl` = (c_lo, s_lo, kappa, .).
+__device__ __forceinline__ float eval_power2(const float4& g0, const float4& ax, const float4& axl, float pxf,
+                                             float pyf)
+{
+    const float dx = __fadd_rn(__fsub_rn(g0.x, pxf), g0.z);
+    const float dy = __fadd_rn(__fsub_rn(g0.y, pyf), g0.w);
+    const float v = fmaf(ax.x, dy, -(ax.y * dx));
+    float u;
+    if (axl.z > 4.0f) {
+        const float t = __fmul_rn(ax.y, dy);
+        const float te = __fmaf_rn(ax.y, dy, -t);
+        const float corr = __fmaf_rn(axl.x, dx, __fmaf_rn(axl.y, dy, te));
+        u = __fadd_rn(__fmaf_rn(ax.x, dx, t), corr);
+    } else {
+        u = fmaf(ax.x, dx, ax.y * dy);
+    }
+    return fmaf(ax.z * u, u, ax.w * v * v);
+}
+
 }  // namespace lsv2

@@ -12,7 +12,9 @@
 //  * The value path computes the 2D mean and the conic that the blend uses, in double-float
 //    arithmetic.  A float32 2D mean at u ~ 1000 px carries ~1e-4 px of error from the
 //    camera transform alone, which moves alpha by ~1e-4 relative at the footprint edge; the
-//    double-float mean is stored as a (hi, lo) pair so the blend can form u - x exactly.
+//    double-float mean is stored as a (hi, lo) pair so the blend can form u - x exactly.  The
+//    same path produces the conic's principal frame (stiff axis as a float pair, eigenvalues)
+//    in which the blend evaluates the Gaussian without cancellation.
 #include "device.cuh"
 #include "project.cuh"
 
@@ -195,6 +197,7 @@ __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a)
 
     float4 xy = make_float4(0.f, 0.f, 0.f, 0.f), cn = make_float4(0.f, 0.f, 0.f, opac);
     float2 ext = make_float2(-1.0f, -1.0f);
+    float4 ax0 = make_float4(0.f, 0.f, 0.f, 0.f), ax1 = make_float4(0.f, 0.f, 0.f, 0.f);
     if (visible) {
         // ---- value path (double-float) ----
         dfloat td[3];
@@ -257,6 +260,23 @@ __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a)
         dfloat c00 = df_add(s00, df(kDilation)), c11 = df_add(s11, df(kDilation));
         float ca = df_div(c11, det).hi, cb = -df_div(s01, det).hi, cc = df_div(c00, det).hi;
         cn = make_float4(ca, cb, cc, opac);
+        // principal frame: the covariance's long axis is the conic's soft axis
+        dfloat hd = df_mul_f(df_sub(c00, c11), 0.5f);
+        dfloat r = df_sqrt(df_add(df_mul(hd, hd), df_mul(s01, s01)));
+        dfloat lmax = df_add(df_mul_f(df_add(c00, c11), 0.5f), r);
+        dfloat lmin = df_div(det, lmax);
+        dfloat sx = df(1.0f), sy = df(0.0f);
+        if (r.hi > 0.0f) {
+            dfloat x = hd.hi >= 0.0f ? df_add(hd, r) : s01;
+            dfloat y = hd.hi >= 0.0f ? s01 : df_sub(r, hd);
+            dfloat nrm = df_sqrt(df_add(df_mul(x, x), df_mul(y, y)));
+            sx = df_div(x, nrm);
+            sy = df_div(y, nrm);
+        }
+        const float q1 = df_div(df(1.0f), lmin).hi, q2 = df_div(df(1.0f), lmax).hi;
+        // stiff axis = soft axis rotated by +90 degrees: (-sy, sx)
+        ax0 = make_float4(-sy.hi, sx.hi, -0.5f * kLog2e * q1, -0.5f * kLog2e * q2);
+        ax1 = make_float4(-sy.lo, sx.lo, __fdiv_rn(lmax.hi, lmin.hi), 0.0f);
         // bounding box of {alpha >= 1/255}: d^T Q d <= 2 ln(255 o); half-widths sqrt(t c00),
         // sqrt(t c11).  Widened by 1e-3 relative so float rounding in the blend can never
         // put a contributing pixel outside it.
@@ -268,6 +288,8 @@ __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a)
     reinterpret_cast<float4*>(a.out.xy)[g] = xy;
     reinterpret_cast<float4*>(a.out.conic_o)[g] = cn;
     reinterpret_cast<float2*>(a.out.extent)[g] = ext;
+    reinterpret_cast<float4*>(a.out.axes)[2 * g] = ax0;
+    reinterpret_cast<float4*>(a.out.axes)[2 * g + 1] = ax1;
     a.out.depth[g] = visible ? depth_key : 0.0f;
     a.out.radius[g] = visible ? radius : 0;
     reinterpret_cast<int4*>(a.out.rect)[g] = visible ? make_int4(x0, y0, x1, y1) : make_int4(0, 0, 0, 0);

@@ -16,10 +16,10 @@
 //    against the warp's pixel strip; a ballot keeps only the records that can touch the strip
 //    and the warp walks the set bits in list order ("warp-ballot culling").  Culling skips
 //    only work whose alpha is below 1/255 everywhere on the strip, so it changes no result.
-//  * A pre-pass packs per-Gaussian records (2D mean pair, conic pre-scaled by -log2(e)/2,
-//    opacity, weights, columns).  Repeated indices within one level are merged into the
-//    first occurrence and the repeat is pointed at a sink column, so the loads of a record's
-//    pairs can all be issued before any store.
+//  * A pre-pass packs per-Gaussian records (2D mean pair, principal frame of the conic,
+//    opacity, weights, columns).  Repeated indices within one level are merged into one pair
+//    and the emptied repeats are stored first, so the loads of a record's pairs can all be
+//    issued before any store.
 #include "device.cuh"
 #include "splat.cuh"
 
@@ -32,44 +32,53 @@ __global__ void __launch_bounds__(256) pack_records_kernel(PackArgs a)
     const int P = a.levels * a.K;
     const int rec_floats = a.rec_bytes / 4;
     float* rec = a.recs + (size_t)g * rec_floats;
-    float4 xy = reinterpret_cast<const float4*>(a.xy)[g];
-    float4 cn = reinterpret_cast<const float4*>(a.conic_o)[g];
-    float2 ex = reinterpret_cast<const float2*>(a.extent)[g];
-    reinterpret_cast<float4*>(rec)[0] = xy;
-    reinterpret_cast<float4*>(rec)[1] =
-        make_float4(-0.5f * kLog2e * cn.x, -kLog2e * cn.y, -0.5f * kLog2e * cn.z, cn.w);
+    const float4 ax1 = reinterpret_cast<const float4*>(a.axes)[2 * g + 1];
+    reinterpret_cast<float4*>(rec)[0] = reinterpret_cast<const float4*>(a.xy)[g];
+    reinterpret_cast<float4*>(rec)[1] = reinterpret_cast<const float4*>(a.axes)[2 * g];
+    reinterpret_cast<float4*>(rec)[2] = make_float4(ax1.x, ax1.y, ax1.z, reinterpret_cast<const float4*>(a.conic_o)[g].w);
+    // gather pairs, merge repeats of a column into the first occurrence
     float wv[kMaxPairs];
     int col[kMaxPairs];
-    const int sink = a.levels * 64;
-    for (int lev = 0; lev < a.levels; ++lev) {
+    bool real[kMaxPairs];
+    for (int lev = 0; lev < a.levels; ++lev)
         for (int k = 0; k < a.K; ++k) {
             const int p = lev * a.K + k;
             const size_t src = ((size_t)g * a.levels + lev) * a.K + k;
-            int ix = a.idx[src];
-            float w = a.w[src];
-            if (ix >= 64) {
-                report(a.status, LSV2_ERR_INVALID_ARGUMENT);
-                ix = -1;
-                w = 0.0f;
-            }
-            col[p] = ix < 0 ? sink : lev * 64 + ix;
-            wv[p] = w;
-            for (int k2 = 0; k2 < k; ++k2) {
-                const int p2 = lev * a.K + k2;
-                if (ix >= 0 && col[p2] == col[p]) {
-                    wv[p2] += w;
-                    col[p] = sink;
+            const int ix = a.idx[src];
+            col[p] = lev * 64 + (ix < 64 ? ix : 0);
+            wv[p] = ix < 64 ? a.w[src] : 0.0f;
+            real[p] = ix < 64;
+            if (ix >= 64) report(a.status, LSV2_ERR_INVALID_ARGUMENT);
+            for (int p2 = lev * a.K; p2 < p; ++p2)
+                if (real[p] && real[p2] && col[p2] == col[p]) {
+                    wv[p2] += wv[p];
                     wv[p] = 0.0f;
+                    real[p] = false;
                     break;
                 }
-            }
         }
-    }
-    for (int p = 0; p < P; ++p) rec[8 + p] = wv[p];
-    uint8_t* cb = reinterpret_cast<uint8_t*>(rec + 8 + P);
-    for (int p = 0; p < P; ++p) cb[p] = (uint8_t)col[p];
-    // culling extents live in the last 16 bytes of the record
-    reinterpret_cast<float2*>(rec + rec_floats - 4)[0] = ex;
+    // emptied pairs first (pointing at the first real pair's column), real pairs last
+    int first_real = -1;
+    for (int p = 0; p < P; ++p)
+        if (real[p]) {
+            first_real = p;
+            break;
+        }
+    uint8_t* cb = reinterpret_cast<uint8_t*>(rec + 12 + P);
+    int o = 0;
+    for (int p = 0; p < P; ++p)
+        if (!real[p]) {
+            rec[12 + o] = 0.0f;
+            cb[o] = (uint8_t)(first_real >= 0 ? col[first_real] : 0);
+            ++o;
+        }
+    for (int p = 0; p < P; ++p)
+        if (real[p]) {
+            rec[12 + o] = wv[p];
+            cb[o] = (uint8_t)col[p];
+            ++o;
+        }
+    reinterpret_cast<float2*>(rec + rec_floats - 4)[0] = reinterpret_cast<const float2*>(a.extent)[g];
 }
 
 template <int LEVELS, int K, int TW, int TH>
@@ -127,17 +136,16 @@ __global__ void __launch_bounds__(TW* TH) splat_kernel(SplatArgs a)
             mask &= mask - 1;
             const float* r = stage + i * C::kSmemRecFloats;
             const float4 g0 = *reinterpret_cast<const float4*>(r);
-            const float4 g1 = *reinterpret_cast<const float4*>(r + 4);
-            const float dx = __fadd_rn(__fsub_rn(g0.x, pxf), g0.z);
-            const float dy = __fadd_rn(__fsub_rn(g0.y, pyf), g0.w);
-            const float p2 = fmaf(g1.x * dx, dx, fmaf(g1.z * dy, dy, g1.y * dx * dy));
+            const float4 ax = *reinterpret_cast<const float4*>(r + 4);
+            const float4 axl = *reinterpret_cast<const float4*>(r + 8);
+            const float p2 = eval_power2(g0, ax, axl, pxf, pyf);
             float e = 0.0f;
             if (!done && p2 <= 0.0f) {
                 float ex2;
                 asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(ex2) : "f"(p2));
-                const float alpha = fminf(kAlphaMax, g1.w * ex2);
+                const float alpha = fminf(kAlphaMax, axl.w * ex2);
                 if (alpha >= kAlphaMin) {
-                    const float test_T = T * one_minus_alpha(alpha, g1.w, p2);
+                    const float test_T = T * one_minus_alpha(alpha, axl.w, p2);
                     if (test_T < kTMin) {
                         done = true;
                     } else {
@@ -148,8 +156,8 @@ __global__ void __launch_bounds__(TW* TH) splat_kernel(SplatArgs a)
                 }
             }
             if (__any_sync(0xffffffffu, e > 0.0f)) {
-                const float* wr = r + 8;
-                const uint8_t* cr = reinterpret_cast<const uint8_t*>(r + 8 + C::kPairs);
+                const float* wr = r + 12;
+                const uint8_t* cr = reinterpret_cast<const uint8_t*>(r + 12 + C::kPairs);
                 float v[C::kPairs];
                 int o[C::kPairs];
 #pragma unroll

@@ -8,13 +8,17 @@ namespace lsv2 {
 constexpr int kMaxPairs = 24;  // levels * K
 
 // Per-Gaussian splat record (global memory, 16-byte aligned), P = levels * K pairs:
-//   floats [0, 4)   u_hi, v_hi, u_lo, v_lo          2D mean as a float pair
-//   floats [4, 8)   A, B, C, opacity                 power * log2(e) = A dx^2 + B dx dy + C dy^2
-//   floats [8, 8+P) merged weights
-//   bytes after     P column indices (lev * 64 + idx; sink column for merged repeats)
-//   last 16 bytes   culling half-extents (ex, ey, 0, 0)
-// The part before the extents is what a warp stages in shared memory.
-__host__ __device__ constexpr int smem_record_bytes(int P) { return ((32 + 5 * P) + 15) / 16 * 16; }
+//   floats [0, 4)    u_hi, v_hi, u_lo, v_lo       2D mean as a float pair
+//   floats [4, 8)    c_hi, s_hi, A, B             principal frame (see eval_power2)
+//   floats [8, 12)   c_lo, s_lo, kappa, opacity
+//   floats [12, 12+P) weights
+//   bytes after      P column indices (lev * 64 + idx)
+//   last 16 bytes    culling half-extents (ex, ey, 0, 0)
+// The part before the extents is what a warp stages in shared memory.  Repeated indices of one
+// level are merged into one pair; the emptied repeats (weight 0, same column) and any invalid
+// index (weight 0) are placed FIRST, so when a record's pairs are loaded together and then
+// stored in order, the pair carrying the weight is stored last and wins.
+__host__ __device__ constexpr int smem_record_bytes(int P) { return ((48 + 5 * P) + 15) / 16 * 16; }
 __host__ __device__ constexpr int record_bytes(int P) { return smem_record_bytes(P) + 16; }
 
 template <int LEVELS, int K, int TW, int TH>
@@ -22,7 +26,7 @@ struct SplatCfg {
     static constexpr int kThreads = TW * TH;
     static constexpr int kWarps = kThreads / 32;
     static constexpr int kPairs = LEVELS * K;
-    static constexpr int kCols = LEVELS * 64 + 1;  // + sink column
+    static constexpr int kCols = LEVELS * 64;
     static constexpr int kAccFloats = (kCols * 33 + 3) / 4 * 4;
     static constexpr int kSmemRecFloats = smem_record_bytes(kPairs) / 4;
     static constexpr int kRecFloats = record_bytes(kPairs) / 4;
@@ -38,6 +42,7 @@ struct PackArgs {
     int64_t n;
     int levels, K, rec_bytes;
     const float* xy;
+    const float* axes;
     const float* conic_o;
     const float* extent;
     const uint8_t* idx;

@@ -74,8 +74,10 @@ class Frame:
         self.rect = torch.empty((n, 4), dtype=torch.int32, device=dev)
         self.tiles_touched = torch.empty(n, dtype=torch.int32, device=dev)
         self.flags = torch.empty(n, dtype=torch.uint8, device=dev)
+        self.axes = torch.empty((n, 8), dtype=torch.float32, device=dev)
         self.proj = L.lsv2_proj(_ptr(self.xy), _ptr(self.conic_o), _ptr(self.extent), _ptr(self.depth),
-                                _ptr(self.radius), _ptr(self.rect), _ptr(self.tiles_touched), _ptr(self.flags))
+                                _ptr(self.radius), _ptr(self.rect), _ptr(self.tiles_touched), _ptr(self.flags),
+                                _ptr(self.axes))
         self.status = torch.zeros(1, dtype=torch.int32, device=dev)
         self.num_instances = torch.zeros(1, dtype=torch.int64, device=dev)
         self.T = cam.num_tiles
