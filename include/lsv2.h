@@ -150,6 +150,31 @@ lsv2_status lsv2_splat_coeffs(const lsv2_camera* cam, int64_t n, const lsv2_proj
                               float* coeff, float* final_T, uint32_t* n_last,
                               int32_t* dev_status, void* stream);
 
+/* Size of the fixed device scratch used by lsv2_splat_coeffs_noalloc (held on every device
+ * that loads this library, until the process exits). */
+#define LSV2_SPLAT_NOALLOC_SCRATCH_BYTES (8u << 20)
+
+/* lsv2_splat_coeffs for callers that cannot allocate device memory.  The paper has no
+ * counterpart; it exists because some callers cannot call cudaMalloc or provide a workspace
+ * (a render loop with a fixed memory budget, a runtime that owns all device memory and only
+ * exposes input and output buffers, a host without an allocator of its own).  Same arguments,
+ * layouts and results as lsv2_splat_coeffs, minus the workspace: the per-Gaussian scratch
+ * lives in a file-scope device array of LSV2_SPLAT_NOALLOC_SCRATCH_BYTES.
+ *   - Limit: lsv2_splat_workspace_bytes(n, levels, K) must not exceed
+ *     LSV2_SPLAT_NOALLOC_SCRATCH_BYTES (8 MiB: 65,536 Gaussians at 3 levels, K = 4);
+ *     larger calls return LSV2_ERR_CAPACITY and launch nothing.
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ *     with that device current; make that first call before any stream capture.
+ *   - Nothing in the scratch must start at zero (every record is rewritten before use).
+ *   - All calls share the one array: calls that overlap on the GPU (e.g. on two streams)
+ *     race on it and must be serialised by the caller.
+ *   - Allocates nothing and calls no allocating routine. */
+lsv2_status lsv2_splat_coeffs_noalloc(const lsv2_camera* cam, int64_t n, const lsv2_proj* proj,
+                                      const uint32_t* tile_ranges, const uint32_t* gauss_ids,
+                                      int32_t levels, int32_t K, int32_t L, const uint8_t* idx,
+                                      const float* w, float* coeff, float* final_T,
+                                      uint32_t* n_last, int32_t* dev_status, void* stream);
+
 /* Decode (Eq. 7): feat[lev][p][:] = coeff[lev][p][:] . codebook[lev].
  *   coeff    [levels][P][L]  dtype coeff_dtype (F32 or BF16)
  *   codebook [levels][L][D]  dtype codebook_dtype (F32 or BF16)

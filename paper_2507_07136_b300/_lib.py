@@ -44,6 +44,7 @@ _SIGS = {
     "lsv2_bin_sort": ([P, I64, P, P, SZ, P, I64, P, P, P, P], I32),
     "lsv2_splat_workspace_bytes": ([I64, I32, I32], SZ),
     "lsv2_splat_coeffs": ([P, I64, P, P, P, I32, I32, I32, P, P, P, SZ, P, P, P, P, P], I32),
+    "lsv2_splat_coeffs_noalloc": ([P, I64, P, P, P, I32, I32, I32, P, P, P, P, P, P, P], I32),
     "lsv2_decode": ([I32, I64, I32, I32, P, I32, P, I32, P, I32, P, P], I32),
     "lsv2_query_workspace_bytes": ([I32, I32, I32, I32], SZ),
     "lsv2_query": ([I32, I64, I32, I32, P, I32, P, I32, I32, P, F32, P, SZ, P, I32, I32, P], I32),
