@@ -172,6 +172,7 @@ def main():
     assert args.warmup >= 3, "at least 3 warm-up steps"
     dev = torch.device("cuda", local)
 
+    from paper_2507_07136_b300 import _lib as Lb
     sc, cam, text = syn.at_scale()
     scene = DeviceScene.from_numpy(sc, device=dev)
     frame = Frame(scene, cam, device=dev)
@@ -186,8 +187,9 @@ def main():
 
     stages = ["project", "bin_sort", "splat", "decode", "query"]
     fns = {"project": frame.project, "bin_sort": frame.bin_sort, "splat": frame.splat,
-           "decode": lambda: frame.decode(F, codebook=cb16), "query": lambda: frame.query(text_d, rel)}
-    launches_per_step = {"project": 1, "bin_sort": 5, "splat": 2, "decode": 1, "query": 2}
+           "decode": lambda: frame.decode(F, codebook=cb16),
+           "query": lambda: frame.query(text_d, rel, compute=Lb.LSV2_BF16)}
+    launches_per_step = {"project": 1, "bin_sort": 5, "splat": 2, "decode": 1, "query": 2}  # prepare + query
 
     def step(ev=None):
         for i, s in enumerate(stages):
@@ -233,12 +235,14 @@ def main():
         del F
         F32 = torch.empty((levels, P, D), dtype=torch.float32, device=dev)
         fns["decode"] = lambda: frame.decode(F32)
+        fns["query"] = lambda: frame.query(text_d, rel)
         timed(2)
         st32, ms32 = timed(max(3, args.steps // 4))
         fp32 = {"ms_per_step": ms32, "fps": 1e3 / ms32, "stages_ms": st32}
         del F32
         F = torch.empty((levels, P, D), dtype=torch.bfloat16, device=dev)
         fns["decode"] = lambda: frame.decode(F, codebook=cb16)
+        fns["query"] = lambda: frame.query(text_d, rel, compute=Lb.LSV2_BF16)
 
     # ---- end to end through the C ABI with host buffers ----
     text_h = torch.as_tensor(text).pin_memory()
@@ -264,7 +268,6 @@ def main():
     # ---- rooflines (algorithmic bytes per launch / CUDA-event duration) ----
     pk, pk_kind = peaks()
     inst = int(frame.num_instances.item())
-    from paper_2507_07136_b300 import _lib as Lb
     rec_bytes = Lb.lsv2_splat_workspace_bytes(scene.n, levels, scene.K)
     splat_bytes = levels * P * 64 * 4 + rec_bytes + inst * 4 + P * 8
     decode_bytes = levels * P * (64 * 4 + D * 2)
@@ -285,8 +288,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic",
             "config": {"workload": "300k Gaussians, 3 levels, K=4, L=64, D=512, 1440x1080, 1 query + 4 negatives",
-                       "path": "FP32 projection/splat/query, BF16 tensor-core decode (FP32 accumulate) to a BF16 "
-                               "feature map", "parallelism": f"replicas x{world}",
+                       "path": "FP32 projection and splat; BF16 tensor-core decode to a BF16 feature map and "
+                               "BF16 tensor-core relevancy (FP32 accumulation)", "parallelism": f"replicas x{world}",
                        "l2": "flushed between steps (256 MiB write, untimed)", "instances": inst},
             "stages_ms": stage_ms,
             "splat_decode_fps": 1e3 / (stage_ms["project"] + stage_ms["bin_sort"] + stage_ms["splat"] + stage_ms["decode"]),

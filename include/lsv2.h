@@ -193,16 +193,19 @@ size_t lsv2_query_workspace_bytes(int32_t levels, int32_t L, int32_t Q, int32_t 
  *   <F, t> = W . u_t,  |F|^2 = W^T G W,  cos_t = <F, t> / (|F| |t|)  (0 when |F| < 1e-12)
  *   rel[q][lev][p] = min_i softmax(tau [cos_pos, cos_neg_i])_0
  *                  = sigmoid(tau (cos_pos - max_i cos_neg_i))
- *   coeff    [levels][P][L]  F32 (or BF16 with compute = BF16)
+ *   coeff    float[levels][P][L]
  *   codebook float[levels][L][D]
  *   text     float[Q][1 + n_neg][D]  (positive first)
- *   rel      [Q][levels][P]  dtype rel_dtype
- * compute_dtype F32: FP32 FMA on CUDA cores; BF16: tcgen05 tensor cores, FP32 accumulation.
- * Supported: L = 64, 1 <= n_neg, Q (1 + n_neg) <= 512. */
+ *   rel      [Q][levels][P]  dtype rel_dtype (F32 or BF16)
+ * compute_dtype F32: FP32 FMA on CUDA cores (rel_dtype F32).  BF16: tcgen05 tensor cores with
+ * W and [G | u] rounded to BF16 and FP32 accumulation.  S S^T and S t are formed per call with
+ * FP64 accumulation.  L = 64, n_neg >= 1, Q (1 + n_neg) <= 448 for BF16, <= 512 for F32.
+ * A bounded device wait that expires sets LSV2_ERR_TIMEOUT. */
 lsv2_status lsv2_query(int32_t levels, int64_t P, int32_t L, int32_t D, const void* coeff,
                        lsv2_dtype coeff_dtype, const float* codebook, int32_t Q, int32_t n_neg,
                        const float* text, float tau, void* workspace, size_t workspace_bytes,
-                       void* rel, lsv2_dtype rel_dtype, lsv2_dtype compute_dtype, void* stream);
+                       void* rel, lsv2_dtype rel_dtype, lsv2_dtype compute_dtype,
+                       int32_t* dev_status, void* stream);
 
 /* Backward of Loss = mean_{lev,p,d} |F - target| with F = W S (decode + L1 adjoint).
  *   loss      float (device scalar, accumulated: zero it first)

@@ -47,7 +47,7 @@ _SIGS = {
     "lsv2_splat_coeffs_noalloc": ([P, I64, P, P, P, I32, I32, I32, P, P, P, P, P, P, P], I32),
     "lsv2_decode": ([I32, I64, I32, I32, P, I32, P, I32, P, I32, P, P], I32),
     "lsv2_query_workspace_bytes": ([I32, I32, I32, I32], SZ),
-    "lsv2_query": ([I32, I64, I32, I32, P, I32, P, I32, I32, P, F32, P, SZ, P, I32, I32, P], I32),
+    "lsv2_query": ([I32, I64, I32, I32, P, I32, P, I32, I32, P, F32, P, SZ, P, I32, I32, P, P], I32),
     "lsv2_l1_decode_backward": ([I32, I64, I32, I32, P, P, P, P, P, P, P], I32),
     "lsv2_splat_backward_workspace_bytes": ([I64], SZ),
     "lsv2_splat_backward": ([P, I64, P, P, P, P, P, P, I32, I32, I32, P, P, P, P, P, P, SZ, P, P, P, P, P, P, P],
@@ -133,9 +133,9 @@ def lsv2_query_workspace_bytes(levels, L, Q, n_neg) -> int:
 
 
 def lsv2_query(levels, P_, L, D, coeff, coeff_dtype, codebook, Q, n_neg, text, tau, ws, ws_bytes, rel, rel_dtype,
-               compute_dtype, stream):
+               compute_dtype, dev_status, stream):
     call("lsv2_query", levels, P_, L, D, coeff, coeff_dtype, codebook, Q, n_neg, text, tau, ws, ws_bytes, rel,
-         rel_dtype, compute_dtype, stream)
+         rel_dtype, compute_dtype, dev_status, stream)
 
 
 def lsv2_l1_decode_backward(levels, P_, L, D, coeff, codebook, target, loss, dcoeff, dcodebook, stream):

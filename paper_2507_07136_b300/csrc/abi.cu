@@ -10,6 +10,7 @@
 #include "device.cuh"
 #include "project.cuh"
 #include "query.cuh"
+#include "query_tc.cuh"
 #include "splat.cuh"
 
 using namespace lsv2;
@@ -160,19 +161,29 @@ size_t lsv2_query_workspace_bytes(int32_t levels, int32_t L, int32_t Q, int32_t 
 
 lsv2_status lsv2_query(int32_t levels, int64_t P, int32_t L, int32_t D, const void* coeff, lsv2_dtype coeff_dtype,
                        const float* codebook, int32_t Q, int32_t n_neg, const float* text, float tau, void* workspace,
-                       size_t workspace_bytes, void* rel, lsv2_dtype rel_dtype, lsv2_dtype compute_dtype, void* stream)
+                       size_t workspace_bytes, void* rel, lsv2_dtype rel_dtype, lsv2_dtype compute_dtype,
+                       int32_t* dev_status, void* stream)
 {
     if (levels < 1 || P < 0 || !coeff || !codebook || !text || !rel || Q < 1 || n_neg < 1 || D <= 0)
         return LSV2_ERR_INVALID_ARGUMENT;
     if (L != 64 || Q * (1 + n_neg) > 512) return LSV2_ERR_UNSUPPORTED;
-    if (!workspace || !aligned16(workspace) || workspace_bytes < query_workspace_bytes(levels, Q * (1 + n_neg)))
+    const int nt = Q * (1 + n_neg);
+    if (!workspace || !aligned16(workspace) || workspace_bytes < query_workspace_bytes(levels, nt))
         return LSV2_ERR_INVALID_ARGUMENT;
-    if (!aligned16(coeff)) return LSV2_ERR_INVALID_ARGUMENT;
-    cudaError_t e = launch_query_prepare(levels, D, Q * (1 + n_neg), codebook, text, workspace, S(stream));
+    if (!aligned16(coeff) || coeff_dtype != LSV2_F32) return coeff_dtype != LSV2_F32 ? LSV2_ERR_UNSUPPORTED
+                                                                                       : LSV2_ERR_INVALID_ARGUMENT;
+    if (rel_dtype != LSV2_F32 && rel_dtype != LSV2_BF16) return LSV2_ERR_INVALID_ARGUMENT;
+    cudaError_t e = launch_query_prepare(levels, D, nt, codebook, text, workspace, S(stream));
     if (e != cudaSuccess) return LSV2_ERR_CUDA;
-    if (compute_dtype == LSV2_F32 && coeff_dtype == LSV2_F32 && rel_dtype == LSV2_F32)
+    if (compute_dtype == LSV2_F32 && rel_dtype == LSV2_F32)
         return cuda_status(launch_query_f32(levels, P, Q, n_neg, tau, static_cast<const float*>(coeff), workspace,
                                             static_cast<float*>(rel), S(stream)));
+    if (compute_dtype == LSV2_BF16) {
+        if (!query_tc_supported(nt)) return LSV2_ERR_UNSUPPORTED;
+        return cuda_status(launch_query_tc(levels, P, Q, n_neg, tau, static_cast<const float*>(coeff),
+                                           query_ws_bt(workspace), query_ws_tnorm(workspace, levels, nt), rel,
+                                           rel_dtype == LSV2_BF16, sm_count(), dev_status, S(stream)));
+    }
     return LSV2_ERR_UNSUPPORTED;
 }
 

@@ -111,6 +111,14 @@ __global__ void __launch_bounds__(128) query_f32_kernel(int64_t P, int Q, int n_
 
 }  // namespace
 
+const float* query_ws_bt(const void* ws) { return static_cast<const float*>(ws); }
+
+const float* query_ws_tnorm(const void* ws, int levels, int nt)
+{
+    return reinterpret_cast<const float*>(static_cast<const char*>(ws) +
+                                          ((size_t)levels * (kL + nt) * kL * 4 + 255) / 256 * 256);
+}
+
 size_t query_workspace_bytes(int levels, int nt)
 {
     return ((size_t)levels * (kL + nt) * kL * 4 + 255) / 256 * 256 + ((size_t)nt * 4 + 255) / 256 * 256;

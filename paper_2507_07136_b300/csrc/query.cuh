@@ -6,6 +6,8 @@
 namespace lsv2 {
 
 size_t query_workspace_bytes(int levels, int nt);
+const float* query_ws_bt(const void* ws);
+const float* query_ws_tnorm(const void* ws, int levels, int nt);
 cudaError_t launch_query_prepare(int levels, int D, int nt, const float* S, const float* text, void* ws,
                                  cudaStream_t stream);
 cudaError_t launch_query_f32(int levels, int64_t P, int Q, int n_neg, float tau, const float* W, const void* ws,

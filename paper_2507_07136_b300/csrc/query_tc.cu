@@ -1,0 +1,267 @@
+// query_tc.cu -- relevancy (Sec. 3.2) through the linearity of Eq. 7 on the tensor cores.
+//
+// Per level, Y = W B with B = [S S^T | S t_0 | S t_1 | ...] (64 x N, N = 64 + #texts padded to a
+// multiple of 16) is one (128 x 64)(64 x N) tcgen05 product per 128-pixel tile (BF16 operands,
+// FP32 accumulation in TMEM).  The epilogue thread that owns a pixel (one TMEM lane) forms
+//     |F|^2 = sum_j W_j Y_j (j < 64),   cos_t = Y_{64+t} / (|F| |t|)   (0 when |F| < 1e-12),
+//     rel_q = sigmoid(tau (cos_pos - max_i cos_neg_i)),
+// and writes rel[q][lev][p] (coalesced over the warp's 32 consecutive pixels).  F is never
+// formed.  Persistent CTAs split over levels, B^T swizzled once per CTA.  Each 128-pixel W tile
+// is 32 KB contiguous in HBM: one thread keeps a ring of two cp.async.bulk copies in flight
+// (mbarrier transaction counts), all threads convert the landed tile to the swizzled BF16
+// operand, one thread issues the MMA.  All waits are bounded.
+#include "query_tc.cuh"
+#include "tc.cuh"
+
+namespace lsv2 {
+namespace {
+
+constexpr int kM = 128;
+constexpr int kK = 64;
+constexpr int kThreads = 256;
+
+struct QueryTcArgs {
+    int64_t P;
+    int Q, n_neg, ncol, npad;      // ncol = 64 + Q (1 + n_neg); npad = ncol rounded up to 16
+    float tau;
+    const float* W;                // [levels][P][64] f32
+    const float* Bt;               // [levels][ncol][64] f32 (rows of B^T)
+    const float* tnorm;            // [Q (1 + n_neg)]
+    void* rel;                     // [Q][levels][P]
+    int rel_bf16;
+    int levels;
+    int32_t* status;
+};
+
+constexpr int kStages = 2;                      // W tiles in flight per CTA (bulk copies)
+constexpr int kTileBytes = kM * kK * 4;         // one FP32 W tile: 32 KB, contiguous in HBM
+
+__host__ __device__ constexpr size_t smem_bytes(int npad, int nt)
+{
+    return 1024 + (size_t)kStages * kTileBytes + (size_t)npad * 128 + (size_t)kM * 128 + (size_t)nt * 4 + 128;
+}
+
+__host__ __device__ constexpr uint32_t tmem_cols(int npad)
+{
+    return npad <= 32 ? 32u : npad <= 64 ? 64u : npad <= 128 ? 128u : npad <= 256 ? 256u : 512u;
+}
+
+// FP32 tile (row-major, 64 floats per row, in the ring) -> BF16 swizzled K-major operand.
+__device__ __forceinline__ void convert_w(const float* src, int valid_rows, uint8_t* sA)
+{
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int c = threadIdx.x + kThreads * j, row = c >> 4, c4 = c & 15;
+        const float4 v = row < valid_rows ? *reinterpret_cast<const float4*>(src + row * kK + c4 * 4)
+                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+        *reinterpret_cast<uint2*>(sA + tc::sw128(row, c4 * 4)) =
+            make_uint2(tc::pack_bf16(v.x, v.y), tc::pack_bf16(v.z, v.w));
+    }
+}
+
+__device__ __forceinline__ float bf16_at(const uint8_t* sA, int row, int k)
+{
+    return __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(sA + tc::sw128(row, k)));
+}
+
+__global__ void __launch_bounds__(kThreads, 2) query_tc_kernel(QueryTcArgs a)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    float* ring = reinterpret_cast<float*>(smem);
+    uint8_t* sB = smem + (size_t)kStages * kTileBytes;
+    uint8_t* sA = sB + (size_t)a.npad * 128;
+    float* sTn = reinterpret_cast<float*>(sA + kM * 128);
+    const int nt = a.Q * (1 + a.n_neg);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(sTn) + (((size_t)nt * 4 + 15) & ~size_t(15)));
+    uint64_t* full = bar + 1;                 // kStages barriers: W tile landed in the ring
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(full + kStages);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int lev = blockIdx.y;
+    const uint32_t ncols_alloc = tmem_cols(a.npad);
+    const int64_t ntiles = (a.P + kM - 1) / kM;
+    const float* Wl = a.W + (size_t)lev * a.P * kK;
+    // tiles of this CTA: blockIdx.x + i * gridDim.x, i = 0, 1, ...
+    const int64_t my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    int64_t last_issued = -1;       // thread 0: index of the last tile whose copy was issued
+    auto issue = [&](int64_t i) {   // thread 0: bulk-copy the i-th tile of this CTA into its stage
+        last_issued = i;
+        const int64_t tile = blockIdx.x + i * gridDim.x;
+        const int64_t rows = a.P - tile * kM < kM ? a.P - tile * kM : kM;
+        const uint32_t bytes = (uint32_t)(rows * kK * 4);
+        const int s = (int)(i % kStages);
+        tc::bulk_load_arm(tc::smem_u32(full + s), bytes);
+        tc::bulk_load(tc::smem_u32(ring + (size_t)s * kM * kK), Wl + tile * kM * kK, bytes, tc::smem_u32(full + s));
+    };
+
+    if (warp == 0) tc::tmem_alloc(tc::smem_u32(tslot), ncols_alloc);
+    if (tid == 0) {
+        tc::mbar_init(tc::smem_u32(bar), 1);
+        for (int s = 0; s < kStages; ++s) tc::mbar_init(tc::smem_u32(full + s), 1);
+    }
+    // B^T rows (N x 64 K-major, swizzled), zero padding rows
+    const float* Bl = a.Bt + (size_t)lev * a.ncol * kK;
+    for (int i = tid; i < a.npad * kK; i += kThreads) {
+        const int n = i >> 6, k = i & 63;
+        const float v = n < a.ncol ? Bl[i] : 0.0f;
+        *reinterpret_cast<__nv_bfloat16*>(sB + tc::sw128(n, k)) = __float2bfloat16_rn(v);
+    }
+    for (int i = tid; i < nt; i += kThreads) sTn[i] = 1.0f / a.tnorm[i];   // reciprocal norms
+    tc::fence_proxy_async();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (tid == 0)
+        for (int64_t i = 0; i < kStages && i < my_tiles; ++i) issue(i);
+    const uint32_t tmem = *tslot;
+    const int q4 = warp & 3, half = warp >> 2;
+    const int row = q4 * 32 + lane;
+    const uint32_t trow = tmem + ((uint32_t)(q4 * 32) << 16);
+    // queries handled by this warp: half 0 -> [0, Qh), half 1 -> [Qh, Q)
+    const int Qh = (a.Q + 1) / 2;
+    const int qb = half ? Qh : 0, qe = half ? a.Q : Qh;
+    const int per = 1 + a.n_neg;
+    uint32_t phase = 0;
+    bool failed = false;
+
+    for (int64_t i = 0; i < my_tiles; ++i) {
+        const int64_t tile = blockIdx.x + i * gridDim.x;
+        const int64_t p0 = tile * kM;
+        const int s = (int)(i % kStages);
+        const bool landed = tc::mbar_wait(tc::smem_u32(full + s), (uint32_t)((i / kStages) & 1));
+        if (__syncthreads_or(!landed)) {
+            failed = true;
+            break;
+        }
+        const int valid = a.P - p0 < kM ? (int)(a.P - p0) : kM;
+        convert_w(ring + (size_t)s * kM * kK, valid, sA);
+        tc::fence_proxy_async();
+        tc::fence_before();
+        __syncthreads();          // stage s is consumed; sA holds this tile; TMEM drained
+        if (tid == 0) {
+            if (i + kStages < my_tiles) issue(i + kStages);
+            tc::fence_after();
+            const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB);
+            for (int n0 = 0; n0 < a.npad; n0 += 256) {
+                const int nn = a.npad - n0 < 256 ? a.npad - n0 : 256;
+                const uint32_t idesc = tc::idesc_bf16(kM, nn);
+#pragma unroll
+                for (int k = 0; k < kK / 16; ++k)
+                    tc::mma_bf16(tmem + (uint32_t)n0, tc::desc_sw128(a0 + k * 32), tc::desc_sw128(b0 + n0 * 128 + k * 32),
+                                 idesc, k > 0 ? 1u : 0u);
+            }
+            tc::mma_commit(tc::smem_u32(bar));
+        }
+        const bool ok = tc::mbar_wait(tc::smem_u32(bar), phase);
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        phase ^= 1u;
+        tc::fence_after();
+        const int64_t p = p0 + row;
+        // |F|^2 = W . (G W): columns 0..63 of Y, W from the staged BF16 tile (16-byte chunks)
+        float n2 = 0.0f;
+        for (int c = 0; c < 64; c += 32) {
+            uint32_t r[32];
+            tc::tmem_ld32(trow + (uint32_t)c, r);
+            tc::tmem_wait_ld();
+#pragma unroll
+            for (int kc = 0; kc < 4; ++kc) {
+                const uint4 wq = *reinterpret_cast<const uint4*>(sA + row * 128 + ((((c >> 3) + kc) ^ (row & 7)) << 4));
+                const uint32_t wv[4] = {wq.x, wq.y, wq.z, wq.w};
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const __nv_bfloat162 w2 = *reinterpret_cast<const __nv_bfloat162*>(&wv[h]);
+                    n2 = fmaf(__low2float(w2), __uint_as_float(r[kc * 8 + 2 * h]), n2);
+                    n2 = fmaf(__high2float(w2), __uint_as_float(r[kc * 8 + 2 * h + 1]), n2);
+                }
+            }
+        }
+        const float nf = sqrtf(fmaxf(n2, 0.0f));
+        const float inv = nf < 1e-12f ? 0.0f : 1.0f / nf;
+        // text columns of this warp's queries, read in 32-column chunks; (query, text) counters
+        // advance column by column (the columns of a query are consecutive)
+        const int cb = 64 + qb * per, ce = 64 + qe * per;
+        float cpos = 0.0f, best = -INFINITY;
+        int q = qb, t = 0;
+        for (int c0 = cb & ~31; qb < qe && c0 < ce; c0 += 32) {
+            uint32_t r[32];
+            tc::tmem_ld32(trow + (uint32_t)c0, r);
+            tc::tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int c = c0 + j;
+                if (c < cb || c >= ce) continue;
+                const float cv = __uint_as_float(r[j]) * inv * sTn[c - 64];
+                if (t == 0) {
+                    cpos = cv;
+                    best = -INFINITY;
+                } else {
+                    best = fmaxf(best, cv);
+                }
+                if (t == a.n_neg) {
+                    if (p < a.P) {
+                        const float rv = 1.0f / (1.0f + __expf(-a.tau * (cpos - best)));
+                        const size_t o = ((size_t)q * a.levels + lev) * a.P + p;
+                        if (a.rel_bf16) static_cast<__nv_bfloat16*>(a.rel)[o] = __float2bfloat16_rn(rv);
+                        else static_cast<float*>(a.rel)[o] = rv;
+                    }
+                    t = 0;
+                    ++q;
+                } else {
+                    ++t;
+                }
+            }
+        }
+        tc::fence_before();
+        __syncthreads();   // TMEM and the W tile are free
+    }
+    if (failed && tid == 0) report(a.status, LSV2_ERR_TIMEOUT);
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after();
+        tc::tmem_dealloc(tmem, ncols_alloc);
+    }
+    // A CTA that gave up may still have bulk copies in flight into its shared memory: wait for
+    // them (bounded) before the CTA retires.
+    if (failed && tid == 0)
+        for (int64_t i = last_issued; i >= 0 && i > last_issued - kStages; --i)
+            (void)tc::mbar_wait(tc::smem_u32(full + (int)(i % kStages)), (uint32_t)((i / kStages) & 1), 100000000ull);
+}
+
+}  // namespace
+
+bool query_tc_supported(int nt)
+{
+    const int npad = ((64 + nt) + 15) / 16 * 16;
+    return 64 + nt <= 512 && smem_bytes(npad, nt) <= 232448 && (512u / tmem_cols(npad) >= 2 || smem_bytes(npad, nt) >= 117760);
+}
+
+cudaError_t launch_query_tc(int levels, int64_t P, int Q, int n_neg, float tau, const float* W, const float* Bt,
+                            const float* tnorm, void* rel, bool rel_bf16, int num_sms, int32_t* status,
+                            cudaStream_t stream)
+{
+    if (P == 0) return cudaSuccess;
+    const int nt = Q * (1 + n_neg), ncol = 64 + nt, npad = (ncol + 15) / 16 * 16;
+    QueryTcArgs a{P, Q, n_neg, ncol, npad, tau, W, Bt, tnorm, rel, rel_bf16 ? 1 : 0, levels, status};
+    // Two CTAs per SM when their TMEM allocations fit (one CTA's MMA and W conversion overlap the
+    // other's epilogue); the shared-memory request keeps one more CTA from being resident, so
+    // tcgen05.alloc never waits on another CTA.
+    const int resident = 512u / tmem_cols(npad) >= 2 ? 2 : 1;
+    size_t smem = smem_bytes(npad, nt);
+    const size_t floor_bytes = 233472 / (size_t)(resident + 1) + 1024;
+    if (smem < floor_bytes) smem = floor_bytes;
+    if (smem > 232448) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(query_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t ntiles = (P + kM - 1) / kM;
+    int per_level = num_sms * resident / levels;
+    if (per_level < 1) per_level = 1;
+    if (per_level > ntiles) per_level = (int)ntiles;
+    query_tc_kernel<<<dim3(per_level, levels), kThreads, smem, stream>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace lsv2

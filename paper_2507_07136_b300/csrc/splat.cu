@@ -11,8 +11,8 @@
 //    conflict-free LDS / FFMA / STS on a warp-uniform column.  (Registers cannot be indexed
 //    by a runtime value on this architecture; a jump table would cost a uniform indirect
 //    branch per pair.)
-//  * Gaussians are staged per warp in batches of 32 records (one coalesced 16-byte-vector
-//    copy per lane).  While staging, each lane tests its record's alpha >= 1/255 bounding box
+//  * Gaussians are staged per warp in batches of 32 records (one 16-byte-vector gather per
+//    lane, issued one batch ahead into registers).  Each lane tests its record's alpha >= 1/255 bounding box
 //    against the warp's pixel strip; a ballot keeps only the records that can touch the strip
 //    and the warp walks the set bits in list order ("warp-ballot culling").  Culling skips
 //    only work whose alpha is below 1/255 everywhere on the strip, so it changes no result.
@@ -111,64 +111,96 @@ __global__ void __launch_bounds__(TW* TH) splat_kernel(SplatArgs a)
     bool done = !inside;
     const float pxf = (float)px, pyf = (float)py;
 
-    for (uint32_t base = beg; base < end; base += C::kBatch) {
-        if (__all_sync(0xffffffffu, done)) break;
-        bool keep = false;
-        const uint32_t j = base + lane;
-        if (lane < C::kBatch && j < end) {
+    // Next batch's record for this lane, fetched into registers while the current batch is
+    // processed (the gather from L2 is the other latency the warp would otherwise wait on).
+    constexpr int kV = C::kSmemRecFloats / 4;
+    float4 nx[kV];
+    float2 nex = make_float2(-1.0f, -1.0f);
+    bool nvalid = false;
+    auto fetch = [&](uint32_t b) {
+        const uint32_t j = b + lane;
+        nvalid = lane < C::kBatch && j < end;
+        if (nvalid) {
             const uint32_t g = a.gauss_ids[j];
             const float4* src = reinterpret_cast<const float4*>(a.recs + (size_t)g * C::kRecFloats);
-            const float4 g0 = __ldg(src);
-            const float2 ex = __ldg(reinterpret_cast<const float2*>(a.recs + (size_t)g * C::kRecFloats + C::kRecFloats - 4));
-            keep = ex.x >= 0.0f && g0.x + ex.x >= wx0 && g0.x - ex.x <= wx1 && g0.y + ex.y >= wy0 &&
-                   g0.y - ex.y <= wy1;
-            if (keep) {
-                float4* dst = reinterpret_cast<float4*>(stage + lane * C::kSmemRecFloats);
-                dst[0] = g0;
 #pragma unroll
-                for (int v = 1; v < C::kSmemRecFloats / 4; ++v) dst[v] = __ldg(src + v);
-            }
+            for (int v = 0; v < kV; ++v) nx[v] = __ldg(src + v);
+            nex = __ldg(reinterpret_cast<const float2*>(a.recs + (size_t)g * C::kRecFloats + C::kRecFloats - 4));
+        }
+    };
+    if (beg < end) fetch(beg);
+
+    for (uint32_t base = beg; base < end; base += C::kBatch) {
+        if (__all_sync(0xffffffffu, done)) break;
+        const bool keep = nvalid && nex.x >= 0.0f && nx[0].x + nex.x >= wx0 && nx[0].x - nex.x <= wx1 &&
+                          nx[0].y + nex.y >= wy0 && nx[0].y - nex.y <= wy1;
+        if (keep) {
+            float4* dst = reinterpret_cast<float4*>(stage + lane * C::kSmemRecFloats);
+#pragma unroll
+            for (int v = 0; v < kV; ++v) dst[v] = nx[v];
         }
         uint32_t mask = __ballot_sync(0xffffffffu, keep);
         __syncwarp();
-        while (mask) {
-            const int i = __ffs(mask) - 1;
+        if (base + C::kBatch < end) fetch(base + C::kBatch);
+        if (mask) {
+            // software pipeline: the next record's power and 2^power (independent of T) are
+            // formed before this record's transmittance update and accumulation
+            int i = __ffs(mask) - 1;
             mask &= mask - 1;
             const float* r = stage + i * C::kSmemRecFloats;
-            const float4 g0 = *reinterpret_cast<const float4*>(r);
-            const float4 ax = *reinterpret_cast<const float4*>(r + 4);
-            const float4 axl = *reinterpret_cast<const float4*>(r + 8);
-            const float p2 = eval_power2(g0, ax, axl, pxf, pyf);
-            float e = 0.0f;
-            if (!done && p2 <= 0.0f) {
-                float ex2;
-                asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(ex2) : "f"(p2));
-                const float alpha = fminf(kAlphaMax, axl.w * ex2);
-                if (alpha >= kAlphaMin) {
-                    const float test_T = T * one_minus_alpha(alpha, axl.w, p2);
-                    if (test_T < kTMin) {
-                        done = true;
-                    } else {
-                        e = alpha * T;
-                        T = test_T;
-                        last = base + i - beg + 1;
+            float p2 = eval_power2(*reinterpret_cast<const float4*>(r), *reinterpret_cast<const float4*>(r + 4),
+                                   *reinterpret_cast<const float4*>(r + 8), pxf, pyf);
+            float o = r[11];
+            float ex2;
+            asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(ex2) : "f"(p2));
+            while (true) {
+                int jn = -1;
+                const float* rn = r;
+                float p2n = 0.0f, on = 0.0f, exn = 0.0f;
+                if (mask) {
+                    jn = __ffs(mask) - 1;
+                    mask &= mask - 1;
+                    rn = stage + jn * C::kSmemRecFloats;
+                    p2n = eval_power2(*reinterpret_cast<const float4*>(rn), *reinterpret_cast<const float4*>(rn + 4),
+                                      *reinterpret_cast<const float4*>(rn + 8), pxf, pyf);
+                    on = rn[11];
+                    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(exn) : "f"(p2n));
+                }
+                float e = 0.0f;
+                if (!done && p2 <= 0.0f) {
+                    const float alpha = fminf(kAlphaMax, o * ex2);
+                    if (alpha >= kAlphaMin) {
+                        const float test_T = T * one_minus_alpha(alpha, o, p2);
+                        if (test_T < kTMin) {
+                            done = true;
+                        } else {
+                            e = alpha * T;
+                            T = test_T;
+                            last = base + i - beg + 1;
+                        }
                     }
                 }
-            }
-            if (__any_sync(0xffffffffu, e > 0.0f)) {
-                const float* wr = r + 12;
-                const uint8_t* cr = reinterpret_cast<const uint8_t*>(r + 12 + C::kPairs);
-                float v[C::kPairs];
-                int o[C::kPairs];
+                if (__any_sync(0xffffffffu, e > 0.0f)) {
+                    const float* wr = r + 12;
+                    const uint8_t* cr = reinterpret_cast<const uint8_t*>(r + 12 + C::kPairs);
+                    float v[C::kPairs];
+                    int off[C::kPairs];
 #pragma unroll
-                for (int p = 0; p < C::kPairs; ++p) {
-                    o[p] = (int)cr[p] * 33 + lane;
-                    v[p] = acc[o[p]];
+                    for (int p = 0; p < C::kPairs; ++p) {
+                        off[p] = (int)cr[p] * 33 + lane;
+                        v[p] = acc[off[p]];
+                    }
+#pragma unroll
+                    for (int p = 0; p < C::kPairs; ++p) v[p] = fmaf(e, wr[p], v[p]);
+#pragma unroll
+                    for (int p = 0; p < C::kPairs; ++p) acc[off[p]] = v[p];
                 }
-#pragma unroll
-                for (int p = 0; p < C::kPairs; ++p) v[p] = fmaf(e, wr[p], v[p]);
-#pragma unroll
-                for (int p = 0; p < C::kPairs; ++p) acc[o[p]] = v[p];
+                if (jn < 0) break;
+                i = jn;
+                r = rn;
+                p2 = p2n;
+                o = on;
+                ex2 = exn;
             }
         }
         __syncwarp();

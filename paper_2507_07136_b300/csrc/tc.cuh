@@ -112,6 +112,19 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// Bulk copy global -> shared completing on an mbarrier (transaction bytes); the issuing thread
+// first arms the barrier with the byte count.  Both addresses 16-byte aligned, size % 16 == 0.
+__device__ __forceinline__ void bulk_load_arm(uint32_t mbar_saddr, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar_saddr), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_load(uint32_t sdst, const void* gsrc, uint32_t bytes, uint32_t mbar_saddr)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(sdst),
+                 "l"(gsrc), "r"(bytes), "r"(mbar_saddr)
+                 : "memory");
+}
+
 // Bulk copy shared -> global (both 16-byte aligned, size a multiple of 16).
 __device__ __forceinline__ void bulk_store(void* gdst, uint32_t ssrc, uint32_t bytes)
 {

@@ -140,7 +140,7 @@ class Frame:
         out_dt = L.LSV2_BF16 if out.dtype == torch.bfloat16 else L.LSV2_F32
         L.lsv2_query(self.scene.levels, self.P, L_CODEBOOK, D, _ptr(self.coeff), L.LSV2_F32, _ptr(self.scene.codebook),
                      Q, nt - 1, _ptr(text), float(tau), _ptr(self.query_ws), need, _ptr(out), out_dt, compute,
-                     _stream(stream))
+                     _ptr(self.status), _stream(stream))
 
     def check(self):
         """Synchronise and raise if a kernel reported a device-side condition."""

@@ -63,6 +63,6 @@ def test_host_validation_rejects_bad_arguments(lib):
     assert lib.lsv2_decode(1, 10, 64, 500, 16, 0, 16, 0, 16, 0, 0, 0) == 2
     assert lib.lsv2_decode(1, 10, 64, 512, 16, 0, 16, 7, 16, 0, 0, 0) == 1
     # query: null text
-    assert lib.lsv2_query(1, 10, 64, 512, 16, 0, 16, 1, 4, 0, 10.0, 16, 1 << 20, 16, 0, 0, 0) == 1
+    assert lib.lsv2_query(1, 10, 64, 512, 16, 0, 16, 1, 4, 0, 10.0, 16, 1 << 20, 16, 0, 0, 0, 0) == 1
     with pytest.raises(L.LSV2Error):
         L.call("lsv2_decode", 1, 10, 32, 512, 16, 0, 16, 0, 16, 0, 0, 0)
