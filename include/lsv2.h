@@ -115,7 +115,8 @@ lsv2_status lsv2_project(const lsv2_camera* cam, int64_t n, const float* means,
                          const float* scales, const float* quats, const float* opacity,
                          const lsv2_proj* out, int32_t* dev_status, void* stream);
 
-/* Workspace for lsv2_bin_sort: tile counters and two key buffers of `capacity` entries. */
+/* Workspace for lsv2_bin_sort: per-block tile histograms, tile counters and two key buffers of
+ * `capacity` entries. */
 size_t lsv2_bin_sort_workspace_bytes(int64_t n, int64_t capacity, int32_t num_tiles);
 
 /* Bin and depth-sort (Eq. 3's ordered per-tile lists).  One instance per (visible Gaussian,
@@ -124,7 +125,7 @@ size_t lsv2_bin_sort_workspace_bytes(int64_t n, int64_t capacity, int32_t num_ti
  *   tile_ranges uint32[num_tiles][2]  [start, end) into gauss_ids
  *   dev_num_instances int64 (device)  total instance count I (may exceed capacity)
  * If I > capacity, *dev_status = LSV2_ERR_CAPACITY and the lists are truncated (all ranges
- * stay inside [0, capacity)). */
+ * stay inside [0, capacity)).  At most 57,344 tiles per view. */
 lsv2_status lsv2_bin_sort(const lsv2_camera* cam, int64_t n, const lsv2_proj* proj,
                           void* workspace, size_t workspace_bytes, uint32_t* gauss_ids,
                           int64_t capacity, uint32_t* tile_ranges, int64_t* dev_num_instances,
@@ -199,7 +200,8 @@ size_t lsv2_query_workspace_bytes(int32_t levels, int32_t L, int32_t Q, int32_t 
  *   rel      [Q][levels][P]  dtype rel_dtype (F32 or BF16)
  * compute_dtype F32: FP32 FMA on CUDA cores (rel_dtype F32).  BF16: tcgen05 tensor cores with
  * W and [G | u] rounded to BF16 and FP32 accumulation.  S S^T and S t are formed per call with
- * FP64 accumulation.  L = 64, n_neg >= 1, Q (1 + n_neg) <= 448 for BF16, <= 512 for F32.
+ * FP64 accumulation.  L = 64, D % 4 == 0, n_neg >= 1, Q (1 + n_neg) <= 448 for BF16, <= 512 for
+ * F32.  All arrays 16-byte aligned.
  * A bounded device wait that expires sets LSV2_ERR_TIMEOUT. */
 lsv2_status lsv2_query(int32_t levels, int64_t P, int32_t L, int32_t D, const void* coeff,
                        lsv2_dtype coeff_dtype, const float* codebook, int32_t Q, int32_t n_neg,

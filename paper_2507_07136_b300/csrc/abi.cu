@@ -82,14 +82,13 @@ lsv2_status lsv2_project(const lsv2_camera* cam, int64_t n, const float* means, 
     if (!camera_ok(cam) || n < 0 || !proj_ok(out)) return LSV2_ERR_INVALID_ARGUMENT;
     if (n > 0 && (!means || !scales || !quats || !opacity || !aligned16(quats))) return LSV2_ERR_INVALID_ARGUMENT;
     if (n > (int64_t)0xFFFFFFFFll) return LSV2_ERR_UNSUPPORTED;
-    return cuda_status(launch_project(*cam, n, means, scales, quats, opacity, *out, dev_status, S(stream)));
+    return cuda_status(launch_project(cam, 1, n, means, scales, quats, opacity, *out, dev_status, S(stream)));
 }
 
 size_t lsv2_bin_sort_workspace_bytes(int64_t n, int64_t capacity, int32_t num_tiles_)
 {
-    (void)n;
-    if (capacity < 0 || num_tiles_ < 0) return 0;
-    return binsort_workspace_bytes(capacity, num_tiles_);
+    if (n < 0 || capacity < 0 || num_tiles_ < 0) return 0;
+    return binsort_workspace_bytes(n, capacity, num_tiles_);
 }
 
 lsv2_status lsv2_bin_sort(const lsv2_camera* cam, int64_t n, const lsv2_proj* proj, void* workspace,
@@ -99,11 +98,24 @@ lsv2_status lsv2_bin_sort(const lsv2_camera* cam, int64_t n, const lsv2_proj* pr
     if (!camera_ok(cam) || n < 0 || !proj_ok(proj) || !tile_ranges || !dev_num_instances) return LSV2_ERR_INVALID_ARGUMENT;
     if (capacity < 1 || capacity > 0x7FFFFFFFll || !gauss_ids) return LSV2_ERR_INVALID_ARGUMENT;
     const int T = num_tiles(cam);
-    if (!workspace || workspace_bytes < binsort_workspace_bytes(capacity, T) || !aligned16(workspace))
+    if (T > binsort_max_tiles_per_view()) return LSV2_ERR_UNSUPPORTED;
+    if (!workspace || workspace_bytes < binsort_workspace_bytes(n, capacity, T) || !aligned16(workspace))
         return LSV2_ERR_INVALID_ARGUMENT;
-    BinSortArgs a{n, (cam->width + cam->tile_w - 1) / cam->tile_w, T, proj->rect, proj->tiles_touched, proj->depth,
-                  workspace, gauss_ids, capacity, tile_ranges, dev_num_instances, dev_status};
-    return cuda_status(launch_binsort(a, S(stream)));
+    BinSortViews a{};
+    a.V = 1;
+    a.n = n;
+    a.GX[0] = (cam->width + cam->tile_w - 1) / cam->tile_w;
+    a.T[0] = T;
+    a.rect = proj->rect;
+    a.touched = proj->tiles_touched;
+    a.depth = proj->depth;
+    a.workspace = workspace;
+    a.gauss_ids = gauss_ids;
+    a.capacity = capacity;
+    a.tile_ranges = tile_ranges;
+    a.num_instances = dev_num_instances;
+    a.status = dev_status;
+    return cuda_status(launch_binsort_views(a, S(stream)));
 }
 
 size_t lsv2_splat_workspace_bytes(int64_t n, int32_t levels, int32_t K)
@@ -166,7 +178,8 @@ lsv2_status lsv2_query(int32_t levels, int64_t P, int32_t L, int32_t D, const vo
 {
     if (levels < 1 || P < 0 || !coeff || !codebook || !text || !rel || Q < 1 || n_neg < 1 || D <= 0)
         return LSV2_ERR_INVALID_ARGUMENT;
-    if (L != 64 || Q * (1 + n_neg) > 512) return LSV2_ERR_UNSUPPORTED;
+    if (L != 64 || Q * (1 + n_neg) > 512 || D % 4 != 0 || D > 12288) return LSV2_ERR_UNSUPPORTED;
+    if (!aligned16(codebook) || !aligned16(text)) return LSV2_ERR_INVALID_ARGUMENT;
     const int nt = Q * (1 + n_neg);
     if (!workspace || !aligned16(workspace) || workspace_bytes < query_workspace_bytes(levels, nt))
         return LSV2_ERR_INVALID_ARGUMENT;

@@ -1,47 +1,97 @@
 // binsort.cu -- tile binning and per-tile depth order ("ordered Gaussian points within a
-// tile", Eq. 3).  One instance per (visible Gaussian, tile of its rectangle), ordered by
-// (tile, depth key bits, Gaussian id).
+// tile", Eq. 3), for one view or several views at once.  One instance per (visible Gaussian,
+// tile of its rectangle), ordered by (tile, depth key bits, Gaussian id); tiles of view v are
+// numbered tile_base[v] + ty * GX_v + tx.
 //
-// Instead of one global radix sort over (tile, depth) keys, the instances are bucketed by
-// tile with a counting pass (atomic counts -> exclusive scan -> atomic scatter) and each
-// bucket is then sorted on its own by one CTA on the 64-bit key (depth bits << 32 | id):
-// small buckets by a bitonic sort in shared memory, large buckets by bitonic-sorted chunks
-// merged pairwise (each element's output slot = own index + rank in the other run; keys
-// are unique).  The scatter order is nondeterministic, the sorted result is not.
-// Capacity overflow is reported in the status word and every range is clipped to capacity,
-// so nothing downstream can read out of bounds.
-#include "device.cuh"
+// Counting sort by tile with no global atomics (same-address atomics on the densest tiles
+// serialise in L2):
+//   1. hist:    block b of view v counts its Gaussians' tiles in shared memory and writes the
+//               histogram row hist_v[b][t]
+//   2. columns: one thread per tile scans hist_v[.][t] over blocks (exclusive, in place) and
+//               writes the tile's total
+//   3. scan:    exclusive scan of the totals -> tile ranges (clipped to capacity), instance
+//               count, capacity check, list of tiles too large for the shared-memory sort
+//   4. scatter: block b starts per-tile shared-memory cursors at tile_start[t] + hist_v[b][t]
+//               and writes each instance's 64-bit key (depth bits << 32 | id) at its cursor
+//   5. sort:    per tile, bitonic sort in shared memory (<= 2048 keys); larger tiles (from the
+//               list) by bitonic-sorted chunks merged pairwise (output slot = own index + rank
+//               in the other run; keys are unique)
+// Slot assignment within a block is nondeterministic, the sorted lists are not.
 #include "binsort.cuh"
+#include "device.cuh"
 
 namespace lsv2 {
 namespace {
 
-constexpr int kSmallCap = 2048;   // keys per bucket sorted in one shared-memory bitonic pass
-constexpr int kChunk = 8192;      // chunk size of the large-bucket path (64 KB of keys)
+constexpr int kGB = 1024;          // Gaussians per histogram block
+constexpr int kSmallCap = 2048;    // keys sorted in one shared-memory bitonic pass
+constexpr int kChunk = 8192;       // chunk of the large-tile path (64 KB of keys)
 
-__global__ void __launch_bounds__(256) count_kernel(int64_t n, const int32_t* rect, const uint32_t* touched,
-                                                    int GX, uint32_t* count)
+struct ViewsDev {                  // per-view tables (device copies live in the workspace)
+    int32_t GX[kMaxViews];
+    int32_t T[kMaxViews];
+    int32_t tile_base[kMaxViews + 1];
+    int64_t hist_base[kMaxViews];
+};
+
+__device__ __forceinline__ int view_of_tile(const ViewsDev& vd, int V, int tg)
 {
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= n || touched[g] == 0) return;
-    const int4 r = reinterpret_cast<const int4*>(rect)[g];
-    for (int ty = r.y; ty < r.w; ++ty)
-        for (int tx = r.x; tx < r.z; ++tx) atomicAdd(&count[ty * GX + tx], 1u);
+    int v = 0;
+    while (v + 1 < V && tg >= vd.tile_base[v + 1]) ++v;
+    return v;
 }
 
-// Single CTA: exclusive scan of the bucket sizes, clipped ranges, capacity check; resets
-// the counters for the scatter pass.
-__global__ void __launch_bounds__(1024) scan_kernel(int T, uint32_t* count, uint32_t* start,
-                                                    uint32_t* tile_ranges, int64_t capacity,
-                                                    int64_t* num_instances, int32_t* status)
+__global__ void __launch_bounds__(kGB) hist_kernel(BinSortViews a, ViewsDev vd, uint32_t* hist)
+{
+    extern __shared__ uint32_t cnt[];
+    const int v = blockIdx.y, b = blockIdx.x, T = vd.T[v], GX = vd.GX[v];
+    for (int t = threadIdx.x; t < T; t += kGB) cnt[t] = 0;
+    __syncthreads();
+    const int64_t g = (int64_t)b * kGB + threadIdx.x;
+    if (g < a.n) {
+        const size_t o = (size_t)v * a.n + g;
+        if (a.touched[o] != 0) {
+            const int4 r = reinterpret_cast<const int4*>(a.rect)[o];
+            for (int ty = r.y; ty < r.w; ++ty)
+                for (int tx = r.x; tx < r.z; ++tx) atomicAdd(&cnt[ty * GX + tx], 1u);
+        }
+    }
+    __syncthreads();
+    uint32_t* row = hist + vd.hist_base[v] + (size_t)b * T;
+    for (int t = threadIdx.x; t < T; t += kGB) row[t] = cnt[t];
+}
+
+__global__ void __launch_bounds__(256) column_kernel(int V, int nblk, ViewsDev vd, uint32_t* hist, uint32_t* total,
+                                                     int T_total)
+{
+    const int tg = blockIdx.x * blockDim.x + threadIdx.x;
+    if (tg >= T_total) return;
+    const int v = view_of_tile(vd, V, tg);
+    const int t = tg - vd.tile_base[v], T = vd.T[v];
+    uint32_t* col = hist + vd.hist_base[v] + t;
+    uint32_t run = 0;
+    for (int b = 0; b < nblk; ++b) {
+        const uint32_t c = col[(size_t)b * T];
+        col[(size_t)b * T] = run;
+        run += c;
+    }
+    total[tg] = run;
+}
+
+// Single CTA: exclusive scan of the per-tile totals, clipped ranges, capacity check, and the list
+// of tiles that need the large-tile sort (count in big[0], ids from big[1]).
+__global__ void __launch_bounds__(1024) scan_kernel(int T, const uint32_t* total, uint32_t* start,
+                                                    uint32_t* tile_ranges, int64_t capacity, int64_t* num_instances,
+                                                    uint32_t* big, int32_t* status)
 {
     __shared__ unsigned long long warp_sums[32];
+    __shared__ uint32_t nbig;
     const int tid = threadIdx.x;
+    if (tid == 0) nbig = 0;
     const int per = (T + 1023) / 1024;
     const int b = tid * per, e = min(T, b + per);
     unsigned long long local = 0;
-    for (int t = b; t < e; ++t) local += count[t];
-    // inclusive scan of `local` across the block
+    for (int t = b; t < e; ++t) local += total[t];
     unsigned long long x = local;
     for (int o = 1; o < 32; o <<= 1) {
         unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
@@ -61,33 +111,40 @@ __global__ void __launch_bounds__(1024) scan_kernel(int T, uint32_t* count, uint
     unsigned long long run = x - local + ((tid >> 5) ? warp_sums[(tid >> 5) - 1] : 0ull);
     const unsigned long long cap = (unsigned long long)capacity;
     for (int t = b; t < e; ++t) {
-        const unsigned long long c = count[t];
-        start[t] = (uint32_t)min(run, cap);
-        tile_ranges[2 * t] = (uint32_t)min(run, cap);
-        tile_ranges[2 * t + 1] = (uint32_t)min(run + c, cap);
+        const unsigned long long c = total[t];
+        const uint32_t s = (uint32_t)min(run, cap), en = (uint32_t)min(run + c, cap);
+        start[t] = s;
+        tile_ranges[2 * t] = s;
+        tile_ranges[2 * t + 1] = en;
+        if (en - s > (uint32_t)kSmallCap) big[1 + atomicAdd(&nbig, 1u)] = (uint32_t)t;
         run += c;
-        count[t] = 0;
     }
+    __syncthreads();
+    if (tid == 0) big[0] = nbig;
     if (tid == 1023) {
         *num_instances = (int64_t)run;
         if (run > cap) report(status, LSV2_ERR_CAPACITY);
     }
 }
 
-__global__ void __launch_bounds__(256) scatter_kernel(int64_t n, const int32_t* rect, const uint32_t* touched,
-                                                      const float* depth, int GX, uint32_t* count,
-                                                      const uint32_t* start, int64_t capacity,
-                                                      unsigned long long* keys)
+__global__ void __launch_bounds__(kGB) scatter_kernel(BinSortViews a, ViewsDev vd, const uint32_t* hist,
+                                                      const uint32_t* start, unsigned long long* keys)
 {
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= n || touched[g] == 0) return;
-    const int4 r = reinterpret_cast<const int4*>(rect)[g];
-    const unsigned long long key = ((unsigned long long)__float_as_uint(depth[g]) << 32) | (unsigned long long)g;
+    extern __shared__ uint32_t cur[];
+    const int v = blockIdx.y, b = blockIdx.x, T = vd.T[v], GX = vd.GX[v], tb = vd.tile_base[v];
+    const uint32_t* row = hist + vd.hist_base[v] + (size_t)b * T;
+    for (int t = threadIdx.x; t < T; t += kGB) cur[t] = start[tb + t] + row[t];
+    __syncthreads();
+    const int64_t g = (int64_t)b * kGB + threadIdx.x;
+    if (g >= a.n) return;
+    const size_t o = (size_t)v * a.n + g;
+    if (a.touched[o] == 0) return;
+    const int4 r = reinterpret_cast<const int4*>(a.rect)[o];
+    const unsigned long long key = ((unsigned long long)__float_as_uint(a.depth[o]) << 32) | (unsigned long long)g;
     for (int ty = r.y; ty < r.w; ++ty)
         for (int tx = r.x; tx < r.z; ++tx) {
-            const int t = ty * GX + tx;
-            const unsigned long long dst = (unsigned long long)start[t] + atomicAdd(&count[t], 1u);
-            if (dst < (unsigned long long)capacity) keys[dst] = key;
+            const uint32_t dst = atomicAdd(&cur[ty * GX + tx], 1u);
+            if ((int64_t)dst < a.capacity) keys[dst] = key;
         }
 }
 
@@ -98,11 +155,11 @@ __device__ void bitonic_smem(unsigned long long* s, int npow2)
             for (int i = threadIdx.x; i < npow2; i += blockDim.x) {
                 const int ixj = i ^ j;
                 if (ixj > i) {
-                    const unsigned long long a = s[i], b = s[ixj];
+                    const unsigned long long x = s[i], y = s[ixj];
                     const bool up = (i & k) == 0;
-                    if ((a > b) == up) {
-                        s[i] = b;
-                        s[ixj] = a;
+                    if ((x > y) == up) {
+                        s[i] = y;
+                        s[ixj] = x;
                     }
                 }
             }
@@ -130,7 +187,6 @@ __global__ void __launch_bounds__(256) sort_small_kernel(const uint32_t* tile_ra
     for (int i = threadIdx.x; i < n; i += blockDim.x) ids[b + i] = (uint32_t)s[i];
 }
 
-// rank of `key` in the sorted run r[0, len): number of elements smaller than key
 __device__ __forceinline__ int lower_rank(const unsigned long long* r, int len, unsigned long long key)
 {
     int lo = 0, hi = len;
@@ -142,78 +198,131 @@ __device__ __forceinline__ int lower_rank(const unsigned long long* r, int len, 
     return lo;
 }
 
-__global__ void __launch_bounds__(1024) sort_large_kernel(const uint32_t* tile_ranges, unsigned long long* keys,
-                                                          unsigned long long* alt, uint32_t* ids)
+// Persistent over the list of large tiles.
+__global__ void __launch_bounds__(1024) sort_large_kernel(const uint32_t* tile_ranges, const uint32_t* big,
+                                                          unsigned long long* keys, unsigned long long* alt,
+                                                          uint32_t* ids)
 {
     extern __shared__ unsigned long long sk[];
-    const uint32_t b = tile_ranges[2 * blockIdx.x], e = tile_ranges[2 * blockIdx.x + 1];
-    const int n = (int)(e - b);
-    if (n <= kSmallCap) return;
-    unsigned long long* src = keys + b;
-    unsigned long long* dst = alt + b;
-    // 1. sort chunks in shared memory
-    for (int c0 = 0; c0 < n; c0 += kChunk) {
-        const int len = min(kChunk, n - c0);
-        int np = 2;
-        while (np < len) np <<= 1;
-        for (int i = threadIdx.x; i < np; i += blockDim.x) sk[i] = i < len ? src[c0 + i] : ~0ull;
-        __syncthreads();
-        bitonic_smem(sk, np);
-        for (int i = threadIdx.x; i < len; i += blockDim.x) src[c0 + i] = sk[i];
-        __syncthreads();
-    }
-    // 2. merge runs pairwise until one run remains
-    for (int run = kChunk; run < n; run <<= 1) {
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const int r0 = (i / (2 * run)) * 2 * run;      // start of this pair of runs
-            const int a_len = min(run, n - r0);
-            const int b0 = r0 + a_len, b_len = max(0, min(run, n - b0));
-            const unsigned long long k = src[i];
-            int pos;
-            if (i < b0) pos = (i - r0) + lower_rank(src + b0, b_len, k);
-            else pos = (i - b0) + lower_rank(src + r0, a_len, k);
-            dst[r0 + pos] = k;
+    const uint32_t nbig = big[0];
+    for (uint32_t it = blockIdx.x; it < nbig; it += gridDim.x) {
+        const uint32_t tile = big[1 + it];
+        const uint32_t b = tile_ranges[2 * tile], e = tile_ranges[2 * tile + 1];
+        const int n = (int)(e - b);
+        unsigned long long* src = keys + b;
+        unsigned long long* dst = alt + b;
+        for (int c0 = 0; c0 < n; c0 += kChunk) {
+            const int len = min(kChunk, n - c0);
+            int np = 2;
+            while (np < len) np <<= 1;
+            for (int i = threadIdx.x; i < np; i += blockDim.x) sk[i] = i < len ? src[c0 + i] : ~0ull;
+            __syncthreads();
+            bitonic_smem(sk, np);
+            for (int i = threadIdx.x; i < len; i += blockDim.x) src[c0 + i] = sk[i];
+            __syncthreads();
         }
+        for (int run = kChunk; run < n; run <<= 1) {
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                const int r0 = (i / (2 * run)) * 2 * run;
+                const int a_len = min(run, n - r0);
+                const int b0 = r0 + a_len, b_len = max(0, min(run, n - b0));
+                const unsigned long long k = src[i];
+                int pos;
+                if (i < b0) pos = (i - r0) + lower_rank(src + b0, b_len, k);
+                else pos = (i - b0) + lower_rank(src + r0, a_len, k);
+                dst[r0 + pos] = k;
+            }
+            __syncthreads();
+            unsigned long long* t = src;
+            src = dst;
+            dst = t;
+        }
+        for (int i = threadIdx.x; i < n; i += blockDim.x) ids[b + i] = (uint32_t)src[i];
         __syncthreads();
-        unsigned long long* t = src;
-        src = dst;
-        dst = t;
     }
-    for (int i = threadIdx.x; i < n; i += blockDim.x) ids[b + i] = (uint32_t)src[i];
+}
+
+size_t a256(size_t b) { return (b + 255) / 256 * 256; }
+
+struct Layout {
+    size_t total, start, big, hist, keys, alt, bytes;
+};
+
+Layout layout(int64_t n, int64_t capacity, const int32_t* T, int V)
+{
+    int64_t nblk = (n + kGB - 1) / kGB;
+    if (nblk < 1) nblk = 1;
+    int64_t Tt = 0, hist = 0;
+    for (int v = 0; v < V; ++v) {
+        Tt += T[v];
+        hist += nblk * T[v];
+    }
+    Layout L{};
+    L.total = 0;
+    L.start = L.total + a256((size_t)Tt * 4);
+    L.big = L.start + a256((size_t)Tt * 4);
+    L.hist = L.big + a256((size_t)(Tt + 1) * 4);
+    L.keys = L.hist + a256((size_t)hist * 4);
+    L.alt = L.keys + a256((size_t)capacity * 8);
+    L.bytes = L.alt + a256((size_t)capacity * 8);
+    return L;
 }
 
 }  // namespace
 
-size_t binsort_workspace_bytes(int64_t capacity, int32_t num_tiles)
+size_t binsort_views_workspace_bytes(int64_t n, int64_t capacity, const int32_t* num_tiles, int V)
 {
-    const size_t t4 = ((size_t)num_tiles * 4 + 255) / 256 * 256;
-    return 2 * t4 + 2 * (((size_t)capacity * 8 + 255) / 256 * 256);
+    return layout(n, capacity, num_tiles, V).bytes;
 }
 
-cudaError_t launch_binsort(const BinSortArgs& a, cudaStream_t stream)
+size_t binsort_workspace_bytes(int64_t n, int64_t capacity, int32_t num_tiles)
 {
-    const size_t t4 = ((size_t)a.num_tiles * 4 + 255) / 256 * 256;
-    const size_t kbytes = ((size_t)a.capacity * 8 + 255) / 256 * 256;
+    return layout(n, capacity, &num_tiles, 1).bytes;
+}
+
+int binsort_max_tiles_per_view() { return 56 * 1024; }
+
+cudaError_t launch_binsort_views(const BinSortViews& a, cudaStream_t stream)
+{
+    const int V = a.V;
+    ViewsDev vd{};
+    int Tt = 0, Tmax = 0;
+    int64_t nblk = (a.n + kGB - 1) / kGB;
+    if (nblk < 1) nblk = 1;
+    int64_t hb = 0;
+    for (int v = 0; v < V; ++v) {
+        vd.GX[v] = a.GX[v];
+        vd.T[v] = a.T[v];
+        vd.tile_base[v] = Tt;
+        vd.hist_base[v] = hb;
+        hb += nblk * a.T[v];
+        Tt += a.T[v];
+        Tmax = a.T[v] > Tmax ? a.T[v] : Tmax;
+    }
+    vd.tile_base[V] = Tt;
+    const Layout L = layout(a.n, a.capacity, a.T, V);
     char* ws = static_cast<char*>(a.workspace);
-    uint32_t* count = reinterpret_cast<uint32_t*>(ws);
-    uint32_t* start = reinterpret_cast<uint32_t*>(ws + t4);
-    unsigned long long* keys = reinterpret_cast<unsigned long long*>(ws + 2 * t4);
-    unsigned long long* alt = reinterpret_cast<unsigned long long*>(ws + 2 * t4 + kbytes);
-    cudaError_t e = cudaMemsetAsync(count, 0, (size_t)a.num_tiles * 4, stream);
+    uint32_t* total = reinterpret_cast<uint32_t*>(ws + L.total);
+    uint32_t* start = reinterpret_cast<uint32_t*>(ws + L.start);
+    uint32_t* big = reinterpret_cast<uint32_t*>(ws + L.big);
+    uint32_t* hist = reinterpret_cast<uint32_t*>(ws + L.hist);
+    unsigned long long* keys = reinterpret_cast<unsigned long long*>(ws + L.keys);
+    unsigned long long* alt = reinterpret_cast<unsigned long long*>(ws + L.alt);
+    const size_t cnt_smem = (size_t)Tmax * 4;
+    cudaError_t e = cudaFuncSetAttribute(hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cnt_smem);
     if (e != cudaSuccess) return e;
-    const int threads = 256;
-    const unsigned blocks = (unsigned)((a.n + threads - 1) / threads);
-    if (a.n > 0) count_kernel<<<blocks, threads, 0, stream>>>(a.n, a.rect, a.touched, a.GX, count);
-    scan_kernel<<<1, 1024, 0, stream>>>(a.num_tiles, count, start, a.tile_ranges, a.capacity,
-                                        a.num_instances, a.status);
-    if (a.n > 0)
-        scatter_kernel<<<blocks, threads, 0, stream>>>(a.n, a.rect, a.touched, a.depth, a.GX, count, start,
-                                                      a.capacity, keys);
-    sort_small_kernel<<<a.num_tiles, 256, 0, stream>>>(a.tile_ranges, keys, a.gauss_ids);
+    e = cudaFuncSetAttribute(scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cnt_smem);
+    if (e != cudaSuccess) return e;
+    const dim3 grid((unsigned)nblk, (unsigned)V);
+    hist_kernel<<<grid, kGB, cnt_smem, stream>>>(a, vd, hist);
+    column_kernel<<<(Tt + 255) / 256, 256, 0, stream>>>(V, (int)nblk, vd, hist, total, Tt);
+    scan_kernel<<<1, 1024, 0, stream>>>(Tt, total, start, a.tile_ranges, a.capacity, a.num_instances, big, a.status);
+    scatter_kernel<<<grid, kGB, cnt_smem, stream>>>(a, vd, hist, start, keys);
+    sort_small_kernel<<<Tt, 256, 0, stream>>>(a.tile_ranges, keys, a.gauss_ids);
     const int large_smem = kChunk * 8;
     e = cudaFuncSetAttribute(sort_large_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, large_smem);
     if (e != cudaSuccess) return e;
-    sort_large_kernel<<<a.num_tiles, 1024, large_smem, stream>>>(a.tile_ranges, keys, alt, a.gauss_ids);
+    sort_large_kernel<<<64, 1024, large_smem, stream>>>(a.tile_ranges, big, keys, alt, a.gauss_ids);
     return cudaGetLastError();
 }
 

@@ -33,7 +33,7 @@ namespace {
 #define DSQRT __dsqrt_rn
 
 struct ProjectArgs {
-    lsv2_camera cam;
+    lsv2_camera cam[kMaxProjectViews];   // one camera per view (blockIdx.y)
     int64_t n;
     const float* means;
     const float* scales;
@@ -112,9 +112,11 @@ __device__ int32_t degenerate_radius(const lsv2_camera& c, const float m[3], con
 
 __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a)
 {
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= a.n) return;
-    const lsv2_camera& c = a.cam;
+    const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi >= a.n) return;
+    const lsv2_camera& c = a.cam[blockIdx.y];
+    const int64_t g = gi;                                 // Gaussian (inputs)
+    const int64_t o = (int64_t)blockIdx.y * a.n + gi;     // output slot of this view
     float m[3] = {a.means[3 * g], a.means[3 * g + 1], a.means[3 * g + 2]};
     float s[3] = {a.scales[3 * g], a.scales[3 * g + 1], a.scales[3 * g + 2]};
     float4 q4 = reinterpret_cast<const float4*>(a.quats)[g];
@@ -285,29 +287,38 @@ __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a)
             ext = make_float2(sqrtf(tcut * c00.hi) + 1e-3f, sqrtf(tcut * c11.hi) + 1e-3f);
         }
     }
-    reinterpret_cast<float4*>(a.out.xy)[g] = xy;
-    reinterpret_cast<float4*>(a.out.conic_o)[g] = cn;
-    reinterpret_cast<float2*>(a.out.extent)[g] = ext;
-    reinterpret_cast<float4*>(a.out.axes)[2 * g] = ax0;
-    reinterpret_cast<float4*>(a.out.axes)[2 * g + 1] = ax1;
-    a.out.depth[g] = visible ? depth_key : 0.0f;
-    a.out.radius[g] = visible ? radius : 0;
-    reinterpret_cast<int4*>(a.out.rect)[g] = visible ? make_int4(x0, y0, x1, y1) : make_int4(0, 0, 0, 0);
-    a.out.tiles_touched[g] = visible ? (uint32_t)((x1 - x0) * (y1 - y0)) : 0u;
-    a.out.flags[g] = (uint8_t)((visible ? 1 : 0) | (visible && degenerate ? 2 : 0));
+    reinterpret_cast<float4*>(a.out.xy)[o] = xy;
+    reinterpret_cast<float4*>(a.out.conic_o)[o] = cn;
+    reinterpret_cast<float2*>(a.out.extent)[o] = ext;
+    reinterpret_cast<float4*>(a.out.axes)[2 * o] = ax0;
+    reinterpret_cast<float4*>(a.out.axes)[2 * o + 1] = ax1;
+    a.out.depth[o] = visible ? depth_key : 0.0f;
+    a.out.radius[o] = visible ? radius : 0;
+    reinterpret_cast<int4*>(a.out.rect)[o] = visible ? make_int4(x0, y0, x1, y1) : make_int4(0, 0, 0, 0);
+    a.out.tiles_touched[o] = visible ? (uint32_t)((x1 - x0) * (y1 - y0)) : 0u;
+    a.out.flags[o] = (uint8_t)((visible ? 1 : 0) | (visible && degenerate ? 2 : 0));
 }
 
 }  // namespace
 
-cudaError_t launch_project(const lsv2_camera& cam, int64_t n, const float* means, const float* scales,
-                           const float* quats, const float* opacity, const lsv2_proj& out,
-                           int32_t* status, cudaStream_t stream)
+cudaError_t launch_project(const lsv2_camera* cams, int V, int64_t n, const float* means, const float* scales,
+                           const float* quats, const float* opacity, const lsv2_proj& out, int32_t* status,
+                           cudaStream_t stream)
 {
-    if (n == 0) return cudaSuccess;
-    ProjectArgs a{cam, n, means, scales, quats, opacity, out, status};
+    if (n == 0 || V == 0) return cudaSuccess;
+    if (V > kMaxProjectViews) return cudaErrorInvalidValue;
+    ProjectArgs a{};
+    for (int v = 0; v < V; ++v) a.cam[v] = cams[v];
+    a.n = n;
+    a.means = means;
+    a.scales = scales;
+    a.quats = quats;
+    a.opacity = opacity;
+    a.out = out;
+    a.status = status;
     const int threads = 256;
     const int64_t blocks = (n + threads - 1) / threads;
-    project_kernel<<<(unsigned)blocks, threads, 0, stream>>>(a);
+    project_kernel<<<dim3((unsigned)blocks, (unsigned)V), threads, 0, stream>>>(a);
     return cudaGetLastError();
 }
 

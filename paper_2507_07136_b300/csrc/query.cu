@@ -17,32 +17,38 @@ namespace {
 
 constexpr int kL = 64;
 
-// grid (64 + nt, levels), 128 threads: column j of B for level lev (j < 64: Gram row j).
-__global__ void __launch_bounds__(128) query_prepare_kernel(int D, int nt, const float* __restrict__ S,
-                                                            const float* __restrict__ text,
-                                                            float* __restrict__ Bt, float* __restrict__ tnorm)
+// grid (64 + nt, levels), 64 threads (one per codebook row k): B^T[lev][j][k] = <x_j, S_k> with
+// x_j = S_j (j < 64, Gram rows) or the text vector j - 64; FP64 accumulation, rounded to float.
+// Also the text norms (level 0 only).
+__global__ void __launch_bounds__(64) query_prepare_kernel(int D, int nt, const float* __restrict__ S,
+                                                           const float* __restrict__ text,
+                                                           float* __restrict__ Bt, float* __restrict__ tnorm)
 {
-    const int j = blockIdx.x, lev = blockIdx.y;
+    extern __shared__ float xs[];
+    __shared__ double red[2];
+    const int j = blockIdx.x, lev = blockIdx.y, k = threadIdx.x;
     const int ncol = kL + nt;
     const float* Sl = S + (size_t)lev * kL * D;
-    const float* v = j < kL ? Sl + (size_t)j * D : text + (size_t)(j - kL) * D;
-    __shared__ double red[4];
-    for (int k = 0; k < kL; k += 1) {
-        double acc = 0.0;
-        for (int d = threadIdx.x; d < D; d += 128) acc += (double)Sl[(size_t)k * D + d] * (double)v[d];
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-        __syncthreads();
-        if (threadIdx.x == 0) Bt[((size_t)lev * ncol + j) * kL + k] = (float)((red[0] + red[1]) + (red[2] + red[3]));
-        __syncthreads();
+    const float* x = j < kL ? Sl + (size_t)j * D : text + (size_t)(j - kL) * D;
+    for (int d = k; d < D; d += 64) xs[d] = x[d];
+    __syncthreads();
+    const float* sk = Sl + (size_t)k * D;
+    double acc = 0.0;
+    for (int d = 0; d < D; d += 4) {
+        const float4 s4 = __ldg(reinterpret_cast<const float4*>(sk + d));
+        acc = fma((double)xs[d], (double)s4.x, acc);
+        acc = fma((double)xs[d + 1], (double)s4.y, acc);
+        acc = fma((double)xs[d + 2], (double)s4.z, acc);
+        acc = fma((double)xs[d + 3], (double)s4.w, acc);
     }
+    Bt[((size_t)lev * ncol + j) * kL + k] = (float)acc;
     if (lev == 0 && j >= kL) {
-        double acc = 0.0;
-        for (int d = threadIdx.x; d < D; d += 128) acc += (double)v[d] * (double)v[d];
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+        double q = 0.0;
+        for (int d = k; d < D; d += 64) q = fma((double)xs[d], (double)xs[d], q);
+        for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+        if ((k & 31) == 0) red[k >> 5] = q;
         __syncthreads();
-        if (threadIdx.x == 0) tnorm[j - kL] = (float)sqrt((red[0] + red[1]) + (red[2] + red[3]));
+        if (k == 0) tnorm[j - kL] = (float)sqrt(red[0] + red[1]);
     }
 }
 
@@ -131,7 +137,7 @@ cudaError_t launch_query_prepare(int levels, int D, int nt, const float* S, cons
     float* tnorm = reinterpret_cast<float*>(static_cast<char*>(ws) +
                                             ((size_t)levels * (kL + nt) * kL * 4 + 255) / 256 * 256);
     dim3 grid((unsigned)(kL + nt), (unsigned)levels);
-    query_prepare_kernel<<<grid, 128, 0, stream>>>(D, nt, S, text, Bt, tnorm);
+    query_prepare_kernel<<<grid, 64, (size_t)D * 4, stream>>>(D, nt, S, text, Bt, tnorm);
     return cudaGetLastError();
 }
 

@@ -27,15 +27,16 @@ namespace lsv2 {
 
 __global__ void __launch_bounds__(256) pack_records_kernel(PackArgs a)
 {
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // Gaussian
     if (g >= a.n) return;
+    const int64_t o = (int64_t)blockIdx.y * a.n + g;                     // projection slot of this view
     const int P = a.levels * a.K;
     const int rec_floats = a.rec_bytes / 4;
-    float* rec = a.recs + (size_t)g * rec_floats;
-    const float4 ax1 = reinterpret_cast<const float4*>(a.axes)[2 * g + 1];
-    reinterpret_cast<float4*>(rec)[0] = reinterpret_cast<const float4*>(a.xy)[g];
-    reinterpret_cast<float4*>(rec)[1] = reinterpret_cast<const float4*>(a.axes)[2 * g];
-    reinterpret_cast<float4*>(rec)[2] = make_float4(ax1.x, ax1.y, ax1.z, reinterpret_cast<const float4*>(a.conic_o)[g].w);
+    float* rec = a.recs + (size_t)o * rec_floats;
+    const float4 ax1 = reinterpret_cast<const float4*>(a.axes)[2 * o + 1];
+    reinterpret_cast<float4*>(rec)[0] = reinterpret_cast<const float4*>(a.xy)[o];
+    reinterpret_cast<float4*>(rec)[1] = reinterpret_cast<const float4*>(a.axes)[2 * o];
+    reinterpret_cast<float4*>(rec)[2] = make_float4(ax1.x, ax1.y, ax1.z, reinterpret_cast<const float4*>(a.conic_o)[o].w);
     // gather pairs, merge repeats of a column into the first occurrence
     float wv[kMaxPairs];
     int col[kMaxPairs];
@@ -65,37 +66,48 @@ __global__ void __launch_bounds__(256) pack_records_kernel(PackArgs a)
             break;
         }
     uint8_t* cb = reinterpret_cast<uint8_t*>(rec + 12 + P);
-    int o = 0;
+    int slot = 0;
     for (int p = 0; p < P; ++p)
         if (!real[p]) {
-            rec[12 + o] = 0.0f;
-            cb[o] = (uint8_t)(first_real >= 0 ? col[first_real] : 0);
-            ++o;
+            rec[12 + slot] = 0.0f;
+            cb[slot] = (uint8_t)(first_real >= 0 ? col[first_real] : 0);
+            ++slot;
         }
     for (int p = 0; p < P; ++p)
         if (real[p]) {
-            rec[12 + o] = wv[p];
-            cb[o] = (uint8_t)col[p];
-            ++o;
+            rec[12 + slot] = wv[p];
+            cb[slot] = (uint8_t)col[p];
+            ++slot;
         }
-    reinterpret_cast<float2*>(rec + rec_floats - 4)[0] = reinterpret_cast<const float2*>(a.extent)[g];
+    reinterpret_cast<float2*>(rec + rec_floats - 4)[0] = reinterpret_cast<const float2*>(a.extent)[o];
 }
 
+// One tile of one view.  Only this warp's shared-memory region is touched, so the warps of a
+// CTA need no barrier between them.
+struct TileJob {
+    int width, height, GX, tile;
+    uint32_t beg, end;
+    const uint32_t* gauss_ids;
+    const float* recs;
+    float* coeff;
+    float* final_T;
+    uint32_t* n_last;
+};
+
 template <int LEVELS, int K, int TW, int TH>
-__global__ void __launch_bounds__(TW* TH) splat_kernel(SplatArgs a)
+__device__ __forceinline__ void splat_tile(const TileJob& a, float* smem)
 {
     using C = SplatCfg<LEVELS, K, TW, TH>;
-    extern __shared__ __align__(16) float smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float* acc = smem + warp * C::kAccFloats;
     float* stage = smem + C::kWarps * C::kAccFloats + warp * (C::kBatch * C::kSmemRecFloats);
 
-    const int GX = (a.cam.width + TW - 1) / TW;
-    const int tile = blockIdx.x;
+    const int GX = a.GX;
+    const int tile = a.tile;
     const int tx = tile % GX, ty = tile / GX;
     const int lx = threadIdx.x % TW, ly = threadIdx.x / TW;
     const int px = tx * TW + lx, py = ty * TH + ly;
-    const bool inside = px < a.cam.width && py < a.cam.height;
+    const bool inside = px < a.width && py < a.height;
     // pixel strip covered by this warp
     constexpr int kRows = 32 / TW;
     const float wx0 = (float)(tx * TW), wx1 = (float)(tx * TW + TW - 1);
@@ -105,7 +117,7 @@ __global__ void __launch_bounds__(TW* TH) splat_kernel(SplatArgs a)
         *reinterpret_cast<float4*>(acc + i) = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncwarp();
 
-    const uint32_t beg = a.tile_ranges[2 * tile], end = a.tile_ranges[2 * tile + 1];
+    const uint32_t beg = a.beg, end = a.end;
     float T = 1.0f;
     uint32_t last = 0;
     bool done = !inside;
@@ -207,25 +219,58 @@ __global__ void __launch_bounds__(TW* TH) splat_kernel(SplatArgs a)
     }
 
     if (inside) {
-        const size_t pix = (size_t)py * a.cam.width + px;
+        const size_t pix = (size_t)py * a.width + px;
         a.final_T[pix] = T;
         a.n_last[pix] = last;
     }
     __syncwarp();
     // write this warp's 32 pixels: per row segment TW pixels x 64 floats (contiguous in HBM)
-    const size_t P = (size_t)a.cam.width * a.cam.height;
+    const size_t P = (size_t)a.width * a.height;
 #pragma unroll
     for (int lev = 0; lev < LEVELS; ++lev) {
         for (int q = lane; q < 32 * 16; q += 32) {
             const int pl = q >> 4;  // pixel within the warp (row-major over the strip)
             const int c4 = (q & 15) * 4;
             const int gx = tx * TW + (pl % TW), gy = ty * TH + warp * kRows + pl / TW;
-            if (gx < a.cam.width && gy < a.cam.height) {
+            if (gx < a.width && gy < a.height) {
                 const float* col = acc + (lev * 64 + c4) * 33 + pl;
                 float4 val = make_float4(col[0], col[33], col[66], col[99]);
-                __stcs(reinterpret_cast<float4*>(a.coeff + ((size_t)lev * P + (size_t)gy * a.cam.width + gx) * 64 + c4), val);
+                __stcs(reinterpret_cast<float4*>(a.coeff + ((size_t)lev * P + (size_t)gy * a.width + gx) * 64 + c4), val);
             }
         }
+    }
+}
+
+template <int LEVELS, int K, int TW, int TH>
+__global__ void __launch_bounds__(TW* TH) splat_kernel(SplatArgs a)
+{
+    extern __shared__ __align__(16) float smem[];
+    const int tile = blockIdx.x;
+    TileJob j{a.cam.width, a.cam.height, (a.cam.width + TW - 1) / TW, tile, a.tile_ranges[2 * tile],
+              a.tile_ranges[2 * tile + 1], a.gauss_ids, a.recs, a.coeff, a.final_T, a.n_last};
+    splat_tile<LEVELS, K, TW, TH>(j, smem);
+}
+
+// Persistent over the (view, tile) work items of several views: each CTA takes the next global
+// tile id from an atomic counter (largest views first, as they come first in the numbering).
+template <int LEVELS, int K, int TW, int TH>
+__global__ void __launch_bounds__(TW* TH) splat_views_kernel(SplatViewsArgs a)
+{
+    extern __shared__ __align__(16) float smem[];
+    __shared__ int s_tile;
+    while (true) {
+        if (threadIdx.x == 0) s_tile = (int)atomicAdd(a.queue, 1u);
+        __syncthreads();
+        const int tg = s_tile;
+        __syncthreads();
+        if (tg >= a.total_tiles) break;
+        int v = 0;
+        while (v + 1 < a.V && tg >= a.view[v + 1].tile_base) ++v;
+        const SplatView& w = a.view[v];
+        TileJob j{w.width, w.height, w.GX, tg - w.tile_base, a.tile_ranges[2 * tg], a.tile_ranges[2 * tg + 1],
+                  a.gauss_ids, a.recs + w.rec_off, a.coeff + w.coeff_off, a.final_T + w.pix_off,
+                  a.n_last + w.pix_off};
+        splat_tile<LEVELS, K, TW, TH>(j, smem);
     }
 }
 
@@ -243,6 +288,33 @@ cudaError_t launch_t(const SplatArgs& a, cudaStream_t stream)
     if (GX * GY == 0) return cudaSuccess;
     kern<<<GX * GY, TW * TH, C::kSmemBytes, stream>>>(a);
     return cudaGetLastError();
+}
+
+template <int LEVELS, int K, int TW, int TH>
+cudaError_t launch_views_t(const SplatViewsArgs& a, int num_sms, cudaStream_t stream)
+{
+    using C = SplatCfg<LEVELS, K, TW, TH>;
+    auto kern = splat_views_kernel<LEVELS, K, TW, TH>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TW * TH, C::kSmemBytes);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    if (a.total_tiles == 0) return cudaSuccess;
+    e = cudaMemsetAsync(a.queue, 0, sizeof(uint32_t), stream);
+    if (e != cudaSuccess) return e;
+    kern<<<num_sms * per_sm, TW * TH, C::kSmemBytes, stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <int LEVELS, int K>
+cudaError_t launch_views_tile(const SplatViewsArgs& a, int tw, int th, int num_sms, cudaStream_t stream)
+{
+    if (tw == 16 && th == 16) return launch_views_t<LEVELS, K, 16, 16>(a, num_sms, stream);
+    if (tw == 8 && th == 8) return launch_views_t<LEVELS, K, 8, 8>(a, num_sms, stream);
+    if (tw == 32 && th == 8) return launch_views_t<LEVELS, K, 32, 8>(a, num_sms, stream);
+    return cudaErrorInvalidValue;
 }
 
 template <int LEVELS, int K>
@@ -268,12 +340,21 @@ bool splat_supported(int levels, int K, int L, int tw, int th)
 
 int splat_record_bytes(int levels, int K) { return record_bytes(levels * K); }
 
-cudaError_t launch_pack(const PackArgs& a, cudaStream_t stream)
+cudaError_t launch_pack(const PackArgs& a, cudaStream_t stream, int V)
 {
-    if (a.n == 0) return cudaSuccess;
+    if (a.n == 0 || V == 0) return cudaSuccess;
     const int threads = 256;
-    pack_records_kernel<<<(unsigned)((a.n + threads - 1) / threads), threads, 0, stream>>>(a);
+    pack_records_kernel<<<dim3((unsigned)((a.n + threads - 1) / threads), (unsigned)V), threads, 0, stream>>>(a);
     return cudaGetLastError();
+}
+
+cudaError_t launch_splat_views(int levels, int K, int tw, int th, const SplatViewsArgs& a, int num_sms,
+                               cudaStream_t stream)
+{
+    if (levels == 1 && K == 4) return launch_views_tile<1, 4>(a, tw, th, num_sms, stream);
+    if (levels == 2 && K == 4) return launch_views_tile<2, 4>(a, tw, th, num_sms, stream);
+    if (levels == 3 && K == 4) return launch_views_tile<3, 4>(a, tw, th, num_sms, stream);
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_splat(int levels, int K, const SplatArgs& a, cudaStream_t stream)

@@ -62,9 +62,34 @@ struct SplatArgs {
     int32_t* status;
 };
 
+constexpr int kMaxSplatViews = 64;
+
+struct SplatView {
+    int width, height, GX, tile_base;   // tile_base: first global tile id of this view
+    size_t rec_off;                     // floats: start of this view's records
+    size_t coeff_off;                   // floats: start of this view's coefficient map
+    size_t pix_off;                     // start of this view's final_T / n_last
+};
+
+struct SplatViewsArgs {
+    int V, total_tiles;
+    SplatView view[kMaxSplatViews + 1];
+    const uint32_t* tile_ranges;        // [total_tiles][2]
+    const uint32_t* gauss_ids;
+    const float* recs;
+    float* coeff;
+    float* final_T;
+    uint32_t* n_last;
+    uint32_t* queue;                    // work-queue counter (zeroed by the launcher)
+    int32_t* status;
+};
+
 bool splat_supported(int levels, int K, int L, int tw, int th);
+cudaError_t launch_splat_views(int levels, int K, int tw, int th, const SplatViewsArgs& a, int num_sms,
+                               cudaStream_t stream);
 int splat_record_bytes(int levels, int K);
-cudaError_t launch_pack(const PackArgs& a, cudaStream_t stream);
+// Packs records for V views: projection slot and record of (view v, Gaussian g) = v * n + g.
+cudaError_t launch_pack(const PackArgs& a, cudaStream_t stream, int V = 1);
 cudaError_t launch_splat(int levels, int K, const SplatArgs& a, cudaStream_t stream);
 
 }  // namespace lsv2
