@@ -15,6 +15,7 @@
  *   lsv2_decode        F = W S per level (Eq. 7)
  *   lsv2_query         relevancy of each pixel for text queries (Sec. 3.2), computed through
  *                      the linearity of Eq. 7 without materialising F
+ *   lsv2_query_views   all of the above for many views and queries in one call
  *   lsv2_splat_backward, lsv2_l1_decode_backward
  *                      gradients of an L1 feature loss (no counterpart in the paper, which
  *                      trains the field but does not describe its gradient)
@@ -208,6 +209,36 @@ lsv2_status lsv2_query(int32_t levels, int64_t P, int32_t L, int32_t D, const vo
                        const float* text, float tau, void* workspace, size_t workspace_bytes,
                        void* rel, lsv2_dtype rel_dtype, lsv2_dtype compute_dtype,
                        int32_t* dev_status, void* stream);
+
+/* Workspace for lsv2_query_views (projections, lists, records and coefficient maps of all
+ * views, the query matrices and a work-queue counter). */
+size_t lsv2_query_views_workspace_bytes(int32_t V, const lsv2_camera* cams, int64_t n,
+                                        int32_t levels, int32_t K, int64_t capacity, int32_t Q,
+                                        int32_t n_neg);
+
+/* Relevancy of Q text queries in V views of one scene in one call (Sec. 3.2 through Eq. 7, with
+ * the rendering of Sec. 3.4): project all views, bin and depth-sort the tiles of all views
+ * together, splat with a persistent kernel that takes (view, tile) work items from an atomic
+ * queue, then the tensor-core relevancy over all pixels of all views.  The same results as V
+ * separate lsv2_project / lsv2_bin_sort / lsv2_splat_coeffs / lsv2_query (BF16) calls.
+ *   cams     HOST array of V cameras (views may differ in resolution; one tile shape for all)
+ *   means..w as for lsv2_project / lsv2_splat_coeffs (device); codebook float[levels][64][D]
+ *   text     float[Q][1 + n_neg][D]; tau as for lsv2_query
+ *   capacity instance capacity over all views (LSV2_ERR_CAPACITY in *dev_status if exceeded)
+ *   stage_batch  Gaussian records a warp stages in shared memory at a time: 16, 32 or 0 (the
+ *            largest that fits); tuned together with the tile shape
+ *   rel      views concatenated, view v: [Q][levels][H_v W_v], dtype rel_dtype (F32 or BF16)
+ *   dev_num_instances  int64 (device): total instances over all views
+ * Everything is stream-ordered with no host synchronisation (capturable in a CUDA graph).
+ * Supported: V <= 64, K = 4, L = 64, Q (1 + n_neg) <= 448, workspace 256-byte aligned. */
+lsv2_status lsv2_query_views(int32_t V, const lsv2_camera* cams, int64_t n, const float* means,
+                             const float* scales, const float* quats, const float* opacity,
+                             int32_t levels, int32_t K, int32_t L, const uint8_t* idx,
+                             const float* w, const float* codebook, int32_t D, int32_t Q,
+                             int32_t n_neg, const float* text, float tau, int64_t capacity,
+                             int32_t stage_batch, void* workspace, size_t workspace_bytes, void* rel,
+                             lsv2_dtype rel_dtype, int64_t* dev_num_instances,
+                             int32_t* dev_status, void* stream);
 
 /* Backward of Loss = mean_{lev,p,d} |F - target| with F = W S (decode + L1 adjoint).
  *   loss      float (device scalar, accumulated: zero it first)

@@ -48,6 +48,9 @@ _SIGS = {
     "lsv2_decode": ([I32, I64, I32, I32, P, I32, P, I32, P, I32, P, P], I32),
     "lsv2_query_workspace_bytes": ([I32, I32, I32, I32], SZ),
     "lsv2_query": ([I32, I64, I32, I32, P, I32, P, I32, I32, P, F32, P, SZ, P, I32, I32, P, P], I32),
+    "lsv2_query_views_workspace_bytes": ([I32, P, I64, I32, I32, I64, I32, I32], SZ),
+    "lsv2_query_views": ([I32, P, I64, P, P, P, P, I32, I32, I32, P, P, P, I32, I32, I32, P, F32, I64, I32, P, SZ, P,
+                          I32, P, P, P], I32),
     "lsv2_l1_decode_backward": ([I32, I64, I32, I32, P, P, P, P, P, P, P], I32),
     "lsv2_splat_backward_workspace_bytes": ([I64], SZ),
     "lsv2_splat_backward": ([P, I64, P, P, P, P, P, P, I32, I32, I32, P, P, P, P, P, P, SZ, P, P, P, P, P, P, P],
@@ -136,6 +139,24 @@ def lsv2_query(levels, P_, L, D, coeff, coeff_dtype, codebook, Q, n_neg, text, t
                compute_dtype, dev_status, stream):
     call("lsv2_query", levels, P_, L, D, coeff, coeff_dtype, codebook, Q, n_neg, text, tau, ws, ws_bytes, rel,
          rel_dtype, compute_dtype, dev_status, stream)
+
+
+def cameras(cams) -> C.Array:
+    """Contiguous host array of lsv2_camera for lsv2_query_views."""
+    arr = (lsv2_camera * len(cams))()
+    for i, c in enumerate(cams):
+        arr[i] = camera(c)
+    return arr
+
+
+def lsv2_query_views_workspace_bytes(V, cams, n, levels, K, capacity, Q, n_neg) -> int:
+    return lib().lsv2_query_views_workspace_bytes(V, cams, n, levels, K, capacity, Q, n_neg)
+
+
+def lsv2_query_views(V, cams, n, means, scales, quats, opacity, levels, K, L, idx, w, codebook, D, Q, n_neg, text,
+                     tau, capacity, stage_batch, ws, ws_bytes, rel, rel_dtype, dev_num, dev_status, stream):
+    call("lsv2_query_views", V, cams, n, means, scales, quats, opacity, levels, K, L, idx, w, codebook, D, Q, n_neg,
+         text, tau, capacity, stage_batch, ws, ws_bytes, rel, rel_dtype, dev_num, dev_status, stream)
 
 
 def lsv2_l1_decode_backward(levels, P_, L, D, coeff, codebook, target, loss, dcoeff, dcodebook, stream):

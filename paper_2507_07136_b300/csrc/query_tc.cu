@@ -21,15 +21,17 @@ constexpr int kK = 64;
 constexpr int kThreads = 256;
 
 struct QueryTcArgs {
-    int64_t P;
     int Q, n_neg, ncol, npad;      // ncol = 64 + Q (1 + n_neg); npad = ncol rounded up to 16
     float tau;
-    const float* W;                // [levels][P][64] f32
+    const float* W;                // per view v: [levels][P_v][64] f32 at W + seg[v].w_off
     const float* Bt;               // [levels][ncol][64] f32 (rows of B^T)
     const float* tnorm;            // [Q (1 + n_neg)]
-    void* rel;                     // [Q][levels][P]
+    void* rel;                     // per view v: [Q][levels][P_v] at rel + seg[v].rel_off
     int rel_bf16;
     int levels;
+    int nseg;                      // views
+    int64_t total_tiles;           // 128-pixel tiles over all views (per level)
+    QuerySeg seg[kMaxQueryViews + 1];
     int32_t* status;
 };
 
@@ -79,19 +81,28 @@ __global__ void __launch_bounds__(kThreads, 2) query_tc_kernel(QueryTcArgs a)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int lev = blockIdx.y;
     const uint32_t ncols_alloc = tmem_cols(a.npad);
-    const int64_t ntiles = (a.P + kM - 1) / kM;
-    const float* Wl = a.W + (size_t)lev * a.P * kK;
+    const int64_t ntiles = a.total_tiles;
+    // global tile -> (view, first pixel); tiles of view v are [seg[v].tile_base, seg[v + 1].tile_base)
+    auto locate = [&](int64_t tile, int& v, int64_t& p0) {
+        v = 0;
+        while (v + 1 < a.nseg && tile >= a.seg[v + 1].tile_base) ++v;
+        p0 = (tile - a.seg[v].tile_base) * kM;
+    };
     // tiles of this CTA: blockIdx.x + i * gridDim.x, i = 0, 1, ...
     const int64_t my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     int64_t last_issued = -1;       // thread 0: index of the last tile whose copy was issued
     auto issue = [&](int64_t i) {   // thread 0: bulk-copy the i-th tile of this CTA into its stage
         last_issued = i;
-        const int64_t tile = blockIdx.x + i * gridDim.x;
-        const int64_t rows = a.P - tile * kM < kM ? a.P - tile * kM : kM;
+        int v;
+        int64_t p0;
+        locate(blockIdx.x + i * gridDim.x, v, p0);
+        const int64_t Pv = a.seg[v].P;
+        const int64_t rows = Pv - p0 < kM ? Pv - p0 : kM;
         const uint32_t bytes = (uint32_t)(rows * kK * 4);
         const int s = (int)(i % kStages);
+        const float* src = a.W + a.seg[v].w_off + ((size_t)lev * Pv + p0) * kK;
         tc::bulk_load_arm(tc::smem_u32(full + s), bytes);
-        tc::bulk_load(tc::smem_u32(ring + (size_t)s * kM * kK), Wl + tile * kM * kK, bytes, tc::smem_u32(full + s));
+        tc::bulk_load(tc::smem_u32(ring + (size_t)s * kM * kK), src, bytes, tc::smem_u32(full + s));
     };
 
     if (warp == 0) tc::tmem_alloc(tc::smem_u32(tslot), ncols_alloc);
@@ -125,15 +136,17 @@ __global__ void __launch_bounds__(kThreads, 2) query_tc_kernel(QueryTcArgs a)
     bool failed = false;
 
     for (int64_t i = 0; i < my_tiles; ++i) {
-        const int64_t tile = blockIdx.x + i * gridDim.x;
-        const int64_t p0 = tile * kM;
+        int vw;
+        int64_t p0;
+        locate(blockIdx.x + i * gridDim.x, vw, p0);
+        const int64_t Pv = a.seg[vw].P;
         const int s = (int)(i % kStages);
         const bool landed = tc::mbar_wait(tc::smem_u32(full + s), (uint32_t)((i / kStages) & 1));
         if (__syncthreads_or(!landed)) {
             failed = true;
             break;
         }
-        const int valid = a.P - p0 < kM ? (int)(a.P - p0) : kM;
+        const int valid = Pv - p0 < kM ? (int)(Pv - p0) : kM;
         convert_w(ring + (size_t)s * kM * kK, valid, sA);
         tc::fence_proxy_async();
         tc::fence_before();
@@ -201,9 +214,9 @@ __global__ void __launch_bounds__(kThreads, 2) query_tc_kernel(QueryTcArgs a)
                     best = fmaxf(best, cv);
                 }
                 if (t == a.n_neg) {
-                    if (p < a.P) {
+                    if (p < Pv) {
                         const float rv = 1.0f / (1.0f + __expf(-a.tau * (cpos - best)));
-                        const size_t o = ((size_t)q * a.levels + lev) * a.P + p;
+                        const size_t o = a.seg[vw].rel_off + ((size_t)q * a.levels + lev) * Pv + p;
                         if (a.rel_bf16) static_cast<__nv_bfloat16*>(a.rel)[o] = __float2bfloat16_rn(rv);
                         else static_cast<float*>(a.rel)[o] = rv;
                     }
@@ -239,13 +252,37 @@ bool query_tc_supported(int nt)
     return 64 + nt <= 512 && smem_bytes(npad, nt) <= 232448 && (512u / tmem_cols(npad) >= 2 || smem_bytes(npad, nt) >= 117760);
 }
 
-cudaError_t launch_query_tc(int levels, int64_t P, int Q, int n_neg, float tau, const float* W, const float* Bt,
-                            const float* tnorm, void* rel, bool rel_bf16, int num_sms, int32_t* status,
-                            cudaStream_t stream)
+cudaError_t launch_query_tc_views(int levels, int V, const int64_t* P, int Q, int n_neg, float tau, const float* W,
+                                  const float* Bt, const float* tnorm, void* rel, bool rel_bf16, int num_sms,
+                                  int32_t* status, cudaStream_t stream)
 {
-    if (P == 0) return cudaSuccess;
+    if (V < 1 || V > kMaxQueryViews) return cudaErrorInvalidValue;
     const int nt = Q * (1 + n_neg), ncol = 64 + nt, npad = (ncol + 15) / 16 * 16;
-    QueryTcArgs a{P, Q, n_neg, ncol, npad, tau, W, Bt, tnorm, rel, rel_bf16 ? 1 : 0, levels, status};
+    QueryTcArgs a{};
+    a.Q = Q;
+    a.n_neg = n_neg;
+    a.ncol = ncol;
+    a.npad = npad;
+    a.tau = tau;
+    a.W = W;
+    a.Bt = Bt;
+    a.tnorm = tnorm;
+    a.rel = rel;
+    a.rel_bf16 = rel_bf16 ? 1 : 0;
+    a.levels = levels;
+    a.nseg = V;
+    a.status = status;
+    int64_t tiles = 0;
+    size_t w_off = 0, rel_off = 0;
+    for (int v = 0; v < V; ++v) {
+        a.seg[v] = QuerySeg{P[v], tiles, w_off, rel_off};
+        tiles += (P[v] + kM - 1) / kM;
+        w_off += (size_t)levels * P[v] * kK;
+        rel_off += (size_t)Q * levels * P[v];
+    }
+    a.seg[V] = QuerySeg{0, tiles, w_off, rel_off};
+    a.total_tiles = tiles;
+    if (tiles == 0) return cudaSuccess;
     // Two CTAs per SM when their TMEM allocations fit (one CTA's MMA and W conversion overlap the
     // other's epilogue); the shared-memory request keeps one more CTA from being resident, so
     // tcgen05.alloc never waits on another CTA.
@@ -256,12 +293,19 @@ cudaError_t launch_query_tc(int levels, int64_t P, int Q, int n_neg, float tau, 
     if (smem > 232448) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(query_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int64_t ntiles = (P + kM - 1) / kM;
     int per_level = num_sms * resident / levels;
     if (per_level < 1) per_level = 1;
-    if (per_level > ntiles) per_level = (int)ntiles;
+    if (per_level > tiles) per_level = (int)tiles;
     query_tc_kernel<<<dim3(per_level, levels), kThreads, smem, stream>>>(a);
     return cudaGetLastError();
+}
+
+cudaError_t launch_query_tc(int levels, int64_t P, int Q, int n_neg, float tau, const float* W, const float* Bt,
+                            const float* tnorm, void* rel, bool rel_bf16, int num_sms, int32_t* status,
+                            cudaStream_t stream)
+{
+    if (P == 0) return cudaSuccess;
+    return launch_query_tc_views(levels, 1, &P, Q, n_neg, tau, W, Bt, tnorm, rel, rel_bf16, num_sms, status, stream);
 }
 
 }  // namespace lsv2

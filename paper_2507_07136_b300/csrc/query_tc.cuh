@@ -5,7 +5,19 @@
 
 namespace lsv2 {
 
+constexpr int kMaxQueryViews = 64;
+
+struct QuerySeg {
+    int64_t P;          // pixels of this view
+    int64_t tile_base;  // first 128-pixel tile of this view (per level)
+    size_t w_off;       // floats: this view's coefficient map
+    size_t rel_off;     // elements: this view's relevancy block [Q][levels][P_v]
+};
+
 bool query_tc_supported(int nt);
+cudaError_t launch_query_tc_views(int levels, int V, const int64_t* P, int Q, int n_neg, float tau, const float* W,
+                                  const float* Bt, const float* tnorm, void* rel, bool rel_bf16, int num_sms,
+                                  int32_t* status, cudaStream_t stream);
 cudaError_t launch_query_tc(int levels, int64_t P, int Q, int n_neg, float tau, const float* W, const float* Bt,
                             const float* tnorm, void* rel, bool rel_bf16, int num_sms, int32_t* status,
                             cudaStream_t stream);

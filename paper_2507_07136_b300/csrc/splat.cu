@@ -94,10 +94,10 @@ struct TileJob {
     uint32_t* n_last;
 };
 
-template <int LEVELS, int K, int TW, int TH>
+template <int LEVELS, int K, int TW, int TH, int BATCH = 0>
 __device__ __forceinline__ void splat_tile(const TileJob& a, float* smem)
 {
-    using C = SplatCfg<LEVELS, K, TW, TH>;
+    using C = SplatCfg<LEVELS, K, TW, TH, BATCH>;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float* acc = smem + warp * C::kAccFloats;
     float* stage = smem + C::kWarps * C::kAccFloats + warp * (C::kBatch * C::kSmemRecFloats);
@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(TW* TH) splat_kernel(SplatArgs a)
 
 // Persistent over the (view, tile) work items of several views: each CTA takes the next global
 // tile id from an atomic counter (largest views first, as they come first in the numbering).
-template <int LEVELS, int K, int TW, int TH>
+template <int LEVELS, int K, int TW, int TH, int BATCH>
 __global__ void __launch_bounds__(TW* TH) splat_views_kernel(SplatViewsArgs a)
 {
     extern __shared__ __align__(16) float smem[];
@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(TW* TH) splat_views_kernel(SplatViewsArgs a)
         TileJob j{w.width, w.height, w.GX, tg - w.tile_base, a.tile_ranges[2 * tg], a.tile_ranges[2 * tg + 1],
                   a.gauss_ids, a.recs + w.rec_off, a.coeff + w.coeff_off, a.final_T + w.pix_off,
                   a.n_last + w.pix_off};
-        splat_tile<LEVELS, K, TW, TH>(j, smem);
+        splat_tile<LEVELS, K, TW, TH, BATCH>(j, smem);
     }
 }
 
@@ -290,11 +290,12 @@ cudaError_t launch_t(const SplatArgs& a, cudaStream_t stream)
     return cudaGetLastError();
 }
 
-template <int LEVELS, int K, int TW, int TH>
+template <int LEVELS, int K, int TW, int TH, int BATCH>
 cudaError_t launch_views_t(const SplatViewsArgs& a, int num_sms, cudaStream_t stream)
 {
-    using C = SplatCfg<LEVELS, K, TW, TH>;
-    auto kern = splat_views_kernel<LEVELS, K, TW, TH>;
+    using C = SplatCfg<LEVELS, K, TW, TH, BATCH>;
+    static_assert(C::kSmemBytes <= 232448, "shared memory budget");
+    auto kern = splat_views_kernel<LEVELS, K, TW, TH, BATCH>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -308,12 +309,21 @@ cudaError_t launch_views_t(const SplatViewsArgs& a, int num_sms, cudaStream_t st
     return cudaGetLastError();
 }
 
-template <int LEVELS, int K>
-cudaError_t launch_views_tile(const SplatViewsArgs& a, int tw, int th, int num_sms, cudaStream_t stream)
+template <int LEVELS, int K, int TW, int TH>
+cudaError_t launch_views_b(const SplatViewsArgs& a, int batch, int num_sms, cudaStream_t stream)
 {
-    if (tw == 16 && th == 16) return launch_views_t<LEVELS, K, 16, 16>(a, num_sms, stream);
-    if (tw == 8 && th == 8) return launch_views_t<LEVELS, K, 8, 8>(a, num_sms, stream);
-    if (tw == 32 && th == 8) return launch_views_t<LEVELS, K, 32, 8>(a, num_sms, stream);
+    using Auto = SplatCfg<LEVELS, K, TW, TH>;
+    if (batch == 16) return launch_views_t<LEVELS, K, TW, TH, 16>(a, num_sms, stream);
+    if (batch == 0 || batch == Auto::kBatch) return launch_views_t<LEVELS, K, TW, TH, Auto::kBatch>(a, num_sms, stream);
+    return cudaErrorInvalidValue;   // 32 does not fit this configuration's shared memory
+}
+
+template <int LEVELS, int K>
+cudaError_t launch_views_tile(const SplatViewsArgs& a, int tw, int th, int batch, int num_sms, cudaStream_t stream)
+{
+    if (tw == 16 && th == 16) return launch_views_b<LEVELS, K, 16, 16>(a, batch, num_sms, stream);
+    if (tw == 8 && th == 8) return launch_views_b<LEVELS, K, 8, 8>(a, batch, num_sms, stream);
+    if (tw == 32 && th == 8) return launch_views_b<LEVELS, K, 32, 8>(a, batch, num_sms, stream);
     return cudaErrorInvalidValue;
 }
 
@@ -348,12 +358,12 @@ cudaError_t launch_pack(const PackArgs& a, cudaStream_t stream, int V)
     return cudaGetLastError();
 }
 
-cudaError_t launch_splat_views(int levels, int K, int tw, int th, const SplatViewsArgs& a, int num_sms,
+cudaError_t launch_splat_views(int levels, int K, int tw, int th, int batch, const SplatViewsArgs& a, int num_sms,
                                cudaStream_t stream)
 {
-    if (levels == 1 && K == 4) return launch_views_tile<1, 4>(a, tw, th, num_sms, stream);
-    if (levels == 2 && K == 4) return launch_views_tile<2, 4>(a, tw, th, num_sms, stream);
-    if (levels == 3 && K == 4) return launch_views_tile<3, 4>(a, tw, th, num_sms, stream);
+    if (levels == 1 && K == 4) return launch_views_tile<1, 4>(a, tw, th, batch, num_sms, stream);
+    if (levels == 2 && K == 4) return launch_views_tile<2, 4>(a, tw, th, batch, num_sms, stream);
+    if (levels == 3 && K == 4) return launch_views_tile<3, 4>(a, tw, th, batch, num_sms, stream);
     return cudaErrorInvalidValue;
 }
 

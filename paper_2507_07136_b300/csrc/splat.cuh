@@ -21,7 +21,8 @@ constexpr int kMaxPairs = 24;  // levels * K
 __host__ __device__ constexpr int smem_record_bytes(int P) { return ((48 + 5 * P) + 15) / 16 * 16; }
 __host__ __device__ constexpr int record_bytes(int P) { return smem_record_bytes(P) + 16; }
 
-template <int LEVELS, int K, int TW, int TH>
+// BATCH: records staged per warp at a time (16 or 32); 0 picks 32 when shared memory allows.
+template <int LEVELS, int K, int TW, int TH, int BATCH = 0>
 struct SplatCfg {
     static constexpr int kThreads = TW * TH;
     static constexpr int kWarps = kThreads / 32;
@@ -32,7 +33,7 @@ struct SplatCfg {
     static constexpr int kRecFloats = record_bytes(kPairs) / 4;
     static constexpr int kAccBytes = kWarps * kAccFloats * 4;
     static constexpr int kBatch =
-        (kAccBytes + kWarps * 32 * kSmemRecFloats * 4 <= 232448) ? 32 : 16;
+        BATCH != 0 ? BATCH : ((kAccBytes + kWarps * 32 * kSmemRecFloats * 4 <= 232448) ? 32 : 16);
     static constexpr int kSmemBytes = kAccBytes + kWarps * kBatch * kSmemRecFloats * 4;
     static_assert(kThreads % 32 == 0 && 32 % TW == 0, "a warp covers whole rows of a tile");
     static_assert(kPairs <= kMaxPairs, "pairs per record");
@@ -85,7 +86,8 @@ struct SplatViewsArgs {
 };
 
 bool splat_supported(int levels, int K, int L, int tw, int th);
-cudaError_t launch_splat_views(int levels, int K, int tw, int th, const SplatViewsArgs& a, int num_sms,
+// batch: records staged per warp (16 or 32; 0 = default).
+cudaError_t launch_splat_views(int levels, int K, int tw, int th, int batch, const SplatViewsArgs& a, int num_sms,
                                cudaStream_t stream);
 int splat_record_bytes(int levels, int K);
 // Packs records for V views: projection slot and record of (view v, Gaussian g) = v * n + g.
