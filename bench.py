@@ -145,6 +145,66 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- batched views
+def batched_section(dev, reps: int = 5):
+    """500,000 Gaussians, three levels, 16 views (4 each at 1440x1080, 960x720, 640x480, 320x240),
+    64 queries with four negatives each: one CUDA-graph launch of lsv2_query_views (tile shape and
+    staging batch from the autotuner) against 16 sequential single-view pipelines."""
+    import torch
+    import lsv2_synth as syn
+    from paper_2507_07136_b300 import _lib as Lb
+    from paper_2507_07136_b300.pipeline import DeviceScene, Frame
+    from paper_2507_07136_b300.views import ViewsBatch, autotune
+
+    sc, cams, text = syn.batched()
+    scene = DeviceScene.from_numpy(sc, device=dev)
+    t = torch.as_tensor(text, device=dev)
+    tile, batch = autotune(scene, cams, t, reps=3)
+    vb = ViewsBatch(scene, cams, text.shape[0], text.shape[1] - 1, tile=tile, stage_batch=batch)
+    vb.capture(t)
+    for _ in range(2):
+        vb.replay()
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(reps):
+        vb.replay()
+    e.record()
+    torch.cuda.synchronize()
+    vb.check()
+    batched_ms = s.elapsed_time(e) / reps
+    inst = int(vb.num_instances.item())
+    pix = sum(vb.P)
+    rel_elems = vb.rel.numel()
+    del vb
+    torch.cuda.empty_cache()
+    # 16 sequential single-view pipelines (same cameras, same tile shape), eager launches
+    frames = [Frame(scene, c.with_tile(*tile), device=dev) for c in cams]
+    rels = [torch.empty((text.shape[0], scene.levels, f.P), dtype=torch.bfloat16, device=dev) for f in frames]
+
+    def sequential():
+        for f, r in zip(frames, rels):
+            f.render()
+            f.query(t, r, compute=Lb.LSV2_BF16)
+    sequential()
+    torch.cuda.synchronize()
+    s.record()
+    for _ in range(reps):
+        sequential()
+    e.record()
+    torch.cuda.synchronize()
+    for f in frames:
+        f.check()
+    seq_ms = s.elapsed_time(e) / reps
+    nq = len(cams) * text.shape[0]
+    return {"workload": "500k Gaussians, 3 levels, 16 views (4 each 1440x1080, 960x720, 640x480, 320x240), "
+                        "64 queries x (1 + 4 negatives)",
+            "queries_per_s": nq * 1e3 / batched_ms, "ms_per_batch": batched_ms,
+            "sequential_ms": seq_ms, "sequential_queries_per_s": nq * 1e3 / seq_ms,
+            "speedup_vs_sequential": seq_ms / batched_ms, "tile": list(tile), "stage_batch": batch,
+            "pixels": pix, "instances": inst, "relevancy_values": rel_elems, "launch": "one CUDA graph"}
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -154,6 +214,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32-path", action="store_true", help="skip the plain FP32 comparison measurement")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 16-view x 64-query batched measurement")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)
@@ -302,6 +363,10 @@ def main():
             "gpu_launches": gpu_launches,
             "clocks": clk.summary(),
             "wall_s_timed_region": t_wall}
+    if not args.no_batched:
+        del F
+        torch.cuda.empty_cache()
+        line["batched"] = batched_section(dev)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()

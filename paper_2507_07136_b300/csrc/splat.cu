@@ -58,34 +58,38 @@ __global__ void __launch_bounds__(256) pack_records_kernel(PackArgs a)
                     break;
                 }
         }
-    // emptied pairs first (pointing at the first real pair's column), real pairs last
-    int first_real = -1;
-    for (int p = 0; p < P; ++p)
-        if (real[p]) {
-            first_real = p;
-            break;
-        }
+    // within each level: emptied pairs first (pointing at the level's first real column), real
+    // pairs last, so every level's K slots stay contiguous
     uint8_t* cb = reinterpret_cast<uint8_t*>(rec + 12 + P);
-    int slot = 0;
-    for (int p = 0; p < P; ++p)
-        if (!real[p]) {
-            rec[12 + slot] = 0.0f;
-            cb[slot] = (uint8_t)(first_real >= 0 ? col[first_real] : 0);
-            ++slot;
-        }
-    for (int p = 0; p < P; ++p)
-        if (real[p]) {
-            rec[12 + slot] = wv[p];
-            cb[slot] = (uint8_t)col[p];
-            ++slot;
-        }
+    for (int lev = 0; lev < a.levels; ++lev) {
+        const int p0 = lev * a.K;
+        int first_real = -1;
+        for (int p = p0; p < p0 + a.K; ++p)
+            if (real[p]) {
+                first_real = p;
+                break;
+            }
+        int slot = p0;
+        for (int p = p0; p < p0 + a.K; ++p)
+            if (!real[p]) {
+                rec[12 + slot] = 0.0f;
+                cb[slot] = (uint8_t)(first_real >= 0 ? col[first_real] : lev * 64);
+                ++slot;
+            }
+        for (int p = p0; p < p0 + a.K; ++p)
+            if (real[p]) {
+                rec[12 + slot] = wv[p];
+                cb[slot] = (uint8_t)col[p];
+                ++slot;
+            }
+    }
     reinterpret_cast<float2*>(rec + rec_floats - 4)[0] = reinterpret_cast<const float2*>(a.extent)[o];
 }
 
 // One tile of one view.  Only this warp's shared-memory region is touched, so the warps of a
 // CTA need no barrier between them.
 struct TileJob {
-    int width, height, GX, tile;
+    int width, height, GX, tile, lev0;   // lev0: first level accumulated by this CTA
     uint32_t beg, end;
     const uint32_t* gauss_ids;
     const float* recs;
@@ -94,10 +98,10 @@ struct TileJob {
     uint32_t* n_last;
 };
 
-template <int LEVELS, int K, int TW, int TH, int BATCH = 0>
+template <int LEVELS, int K, int TW, int TH, int BATCH = 0, int LCTA = LEVELS>
 __device__ __forceinline__ void splat_tile(const TileJob& a, float* smem)
 {
-    using C = SplatCfg<LEVELS, K, TW, TH, BATCH>;
+    using C = SplatCfg<LEVELS, K, TW, TH, BATCH, LCTA>;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float* acc = smem + warp * C::kAccFloats;
     float* stage = smem + C::kWarps * C::kAccFloats + warp * (C::kBatch * C::kSmemRecFloats);
@@ -193,19 +197,20 @@ __device__ __forceinline__ void splat_tile(const TileJob& a, float* smem)
                     }
                 }
                 if (__any_sync(0xffffffffu, e > 0.0f)) {
-                    const float* wr = r + 12;
-                    const uint8_t* cr = reinterpret_cast<const uint8_t*>(r + 12 + C::kPairs);
-                    float v[C::kPairs];
-                    int off[C::kPairs];
+                    const float* wr = r + 12 + a.lev0 * K;
+                    const uint8_t* cr = reinterpret_cast<const uint8_t*>(r + 12 + C::kPairs) + a.lev0 * K;
+                    const int cbase = a.lev0 * 64;
+                    float v[C::kCtaPairs];
+                    int off[C::kCtaPairs];
 #pragma unroll
-                    for (int p = 0; p < C::kPairs; ++p) {
-                        off[p] = (int)cr[p] * 33 + lane;
+                    for (int p = 0; p < C::kCtaPairs; ++p) {
+                        off[p] = ((int)cr[p] - cbase) * 33 + lane;
                         v[p] = acc[off[p]];
                     }
 #pragma unroll
-                    for (int p = 0; p < C::kPairs; ++p) v[p] = fmaf(e, wr[p], v[p]);
+                    for (int p = 0; p < C::kCtaPairs; ++p) v[p] = fmaf(e, wr[p], v[p]);
 #pragma unroll
-                    for (int p = 0; p < C::kPairs; ++p) acc[off[p]] = v[p];
+                    for (int p = 0; p < C::kCtaPairs; ++p) acc[off[p]] = v[p];
                 }
                 if (jn < 0) break;
                 i = jn;
@@ -218,7 +223,7 @@ __device__ __forceinline__ void splat_tile(const TileJob& a, float* smem)
         __syncwarp();
     }
 
-    if (inside) {
+    if (inside && a.lev0 == 0) {
         const size_t pix = (size_t)py * a.width + px;
         a.final_T[pix] = T;
         a.n_last[pix] = last;
@@ -227,13 +232,14 @@ __device__ __forceinline__ void splat_tile(const TileJob& a, float* smem)
     // write this warp's 32 pixels: per row segment TW pixels x 64 floats (contiguous in HBM)
     const size_t P = (size_t)a.width * a.height;
 #pragma unroll
-    for (int lev = 0; lev < LEVELS; ++lev) {
+    for (int lc = 0; lc < LCTA; ++lc) {
+        const int lev = a.lev0 + lc;
         for (int q = lane; q < 32 * 16; q += 32) {
             const int pl = q >> 4;  // pixel within the warp (row-major over the strip)
             const int c4 = (q & 15) * 4;
             const int gx = tx * TW + (pl % TW), gy = ty * TH + warp * kRows + pl / TW;
             if (gx < a.width && gy < a.height) {
-                const float* col = acc + (lev * 64 + c4) * 33 + pl;
+                const float* col = acc + (lc * 64 + c4) * 33 + pl;
                 float4 val = make_float4(col[0], col[33], col[66], col[99]);
                 __stcs(reinterpret_cast<float4*>(a.coeff + ((size_t)lev * P + (size_t)gy * a.width + gx) * 64 + c4), val);
             }
@@ -241,14 +247,15 @@ __device__ __forceinline__ void splat_tile(const TileJob& a, float* smem)
     }
 }
 
-template <int LEVELS, int K, int TW, int TH>
+template <int LEVELS, int K, int TW, int TH, int LCTA>
 __global__ void __launch_bounds__(TW* TH) splat_kernel(SplatArgs a)
 {
     extern __shared__ __align__(16) float smem[];
     const int tile = blockIdx.x;
-    TileJob j{a.cam.width, a.cam.height, (a.cam.width + TW - 1) / TW, tile, a.tile_ranges[2 * tile],
-              a.tile_ranges[2 * tile + 1], a.gauss_ids, a.recs, a.coeff, a.final_T, a.n_last};
-    splat_tile<LEVELS, K, TW, TH>(j, smem);
+    TileJob j{a.cam.width, a.cam.height, (a.cam.width + TW - 1) / TW, tile, (int)blockIdx.y * LCTA,
+              a.tile_ranges[2 * tile], a.tile_ranges[2 * tile + 1], a.gauss_ids, a.recs, a.coeff, a.final_T,
+              a.n_last};
+    splat_tile<LEVELS, K, TW, TH, 0, LCTA>(j, smem);
 }
 
 // Persistent over the (view, tile) work items of several views: each CTA takes the next global
@@ -267,7 +274,7 @@ __global__ void __launch_bounds__(TW* TH) splat_views_kernel(SplatViewsArgs a)
         int v = 0;
         while (v + 1 < a.V && tg >= a.view[v + 1].tile_base) ++v;
         const SplatView& w = a.view[v];
-        TileJob j{w.width, w.height, w.GX, tg - w.tile_base, a.tile_ranges[2 * tg], a.tile_ranges[2 * tg + 1],
+        TileJob j{w.width, w.height, w.GX, tg - w.tile_base, 0, a.tile_ranges[2 * tg], a.tile_ranges[2 * tg + 1],
                   a.gauss_ids, a.recs + w.rec_off, a.coeff + w.coeff_off, a.final_T + w.pix_off,
                   a.n_last + w.pix_off};
         splat_tile<LEVELS, K, TW, TH, BATCH>(j, smem);
@@ -276,18 +283,24 @@ __global__ void __launch_bounds__(TW* TH) splat_views_kernel(SplatViewsArgs a)
 
 namespace {
 
-template <int LEVELS, int K, int TW, int TH>
+template <int LEVELS, int K, int TW, int TH, int LCTA>
 cudaError_t launch_t(const SplatArgs& a, cudaStream_t stream)
 {
-    using C = SplatCfg<LEVELS, K, TW, TH>;
+    using C = SplatCfg<LEVELS, K, TW, TH, 0, LCTA>;
     static_assert(C::kSmemBytes <= 232448, "shared memory budget");
-    auto kern = splat_kernel<LEVELS, K, TW, TH>;
+    auto kern = splat_kernel<LEVELS, K, TW, TH, LCTA>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
     if (e != cudaSuccess) return e;
     const int GX = (a.cam.width + TW - 1) / TW, GY = (a.cam.height + TH - 1) / TH;
     if (GX * GY == 0) return cudaSuccess;
-    kern<<<GX * GY, TW * TH, C::kSmemBytes, stream>>>(a);
+    kern<<<dim3(GX * GY, LEVELS / LCTA), TW * TH, C::kSmemBytes, stream>>>(a);
     return cudaGetLastError();
+}
+
+template <int LEVELS, int K, int TW, int TH>
+cudaError_t launch_split(const SplatArgs& a, cudaStream_t stream)
+{
+    return launch_t<LEVELS, K, TW, TH, LEVELS>(a, stream);
 }
 
 template <int LEVELS, int K, int TW, int TH, int BATCH>
@@ -330,9 +343,9 @@ cudaError_t launch_views_tile(const SplatViewsArgs& a, int tw, int th, int batch
 template <int LEVELS, int K>
 cudaError_t launch_tile(const SplatArgs& a, cudaStream_t stream)
 {
-    if (a.cam.tile_w == 16 && a.cam.tile_h == 16) return launch_t<LEVELS, K, 16, 16>(a, stream);
-    if (a.cam.tile_w == 8 && a.cam.tile_h == 8) return launch_t<LEVELS, K, 8, 8>(a, stream);
-    if (a.cam.tile_w == 32 && a.cam.tile_h == 8) return launch_t<LEVELS, K, 32, 8>(a, stream);
+    if (a.cam.tile_w == 16 && a.cam.tile_h == 16) return launch_split<LEVELS, K, 16, 16>(a, stream);
+    if (a.cam.tile_w == 8 && a.cam.tile_h == 8) return launch_split<LEVELS, K, 8, 8>(a, stream);
+    if (a.cam.tile_w == 32 && a.cam.tile_h == 8) return launch_split<LEVELS, K, 32, 8>(a, stream);
     return cudaErrorInvalidValue;
 }
 
@@ -349,6 +362,7 @@ bool splat_supported(int levels, int K, int L, int tw, int th)
 }
 
 int splat_record_bytes(int levels, int K) { return record_bytes(levels * K); }
+
 
 cudaError_t launch_pack(const PackArgs& a, cudaStream_t stream, int V)
 {

@@ -22,12 +22,14 @@ __host__ __device__ constexpr int smem_record_bytes(int P) { return ((48 + 5 * P
 __host__ __device__ constexpr int record_bytes(int P) { return smem_record_bytes(P) + 16; }
 
 // BATCH: records staged per warp at a time (16 or 32); 0 picks 32 when shared memory allows.
-template <int LEVELS, int K, int TW, int TH, int BATCH = 0>
+// LCTA: levels accumulated by one CTA (LEVELS, or 1 when each level of a tile gets its own CTA).
+template <int LEVELS, int K, int TW, int TH, int BATCH = 0, int LCTA = LEVELS>
 struct SplatCfg {
     static constexpr int kThreads = TW * TH;
     static constexpr int kWarps = kThreads / 32;
-    static constexpr int kPairs = LEVELS * K;
-    static constexpr int kCols = LEVELS * 64;
+    static constexpr int kPairs = LEVELS * K;        // pairs in a record
+    static constexpr int kCtaPairs = LCTA * K;       // pairs this CTA accumulates
+    static constexpr int kCols = LCTA * 64;
     static constexpr int kAccFloats = (kCols * 33 + 3) / 4 * 4;
     static constexpr int kSmemRecFloats = smem_record_bytes(kPairs) / 4;
     static constexpr int kRecFloats = record_bytes(kPairs) / 4;
