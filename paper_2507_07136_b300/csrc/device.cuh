@@ -28,15 +28,40 @@ __device__ __forceinline__ void report(int32_t* status, int32_t code)
     if (status) atomicCAS(status, 0, code);
 }
 
+// 1 - 2^x for -1 <= x <= 0 from the Taylor series (2^x - 1) / x = sum_{n>=0} ln2^(n+1) x^n / (n+1)!
+// taken through x^8: the first omitted term is below 1.5e-8 of the sum on the interval, and the
+// Horner steps add a few ulp.  Outside [-1, 0] the result is meaningless (callers select it
+// only there).
+__host__ __device__ constexpr double exp2_taylor_coeff(int n)
+{
+    double c = 1.0;
+    for (int k = 1; k <= n + 1; ++k) c *= 0.6931471805599453 / (double)k;
+    return c;
+}
+__device__ __forceinline__ float one_minus_exp2(float x)
+{
+    float g = (float)exp2_taylor_coeff(8);
+    g = fmaf(g, x, (float)exp2_taylor_coeff(7));
+    g = fmaf(g, x, (float)exp2_taylor_coeff(6));
+    g = fmaf(g, x, (float)exp2_taylor_coeff(5));
+    g = fmaf(g, x, (float)exp2_taylor_coeff(4));
+    g = fmaf(g, x, (float)exp2_taylor_coeff(3));
+    g = fmaf(g, x, (float)exp2_taylor_coeff(2));
+    g = fmaf(g, x, (float)exp2_taylor_coeff(1));
+    g = fmaf(g, x, (float)exp2_taylor_coeff(0));
+    return -x * g;
+}
+
 // 1 - alpha for alpha = min(0.99, o 2^p2) with p2 = power * log2(e) <= 0, without the
 // cancellation of `1 - alpha` near alpha = 1 (which would multiply alpha's relative error by
 // alpha / (1 - alpha) in every later transmittance): for alpha > 1/2 (hence o > 1/2, where
-// 1 - o is exact), 1 - o e^p = (1 - o) - o expm1(p), a sum of two non-negative terms.
+// 1 - o is exact, and -1 < p2 <= 0), 1 - o 2^p2 = (1 - o) + o (1 - 2^p2), a sum of two
+// non-negative terms.  Branch-free: both forms are computed and one is selected.
 __device__ __forceinline__ float one_minus_alpha(float alpha, float o, float p2)
 {
-    if (alpha == kAlphaMax) return 1.0f - kAlphaMax;
-    if (alpha <= 0.5f) return 1.0f - alpha;
-    return fmaf(-o, expm1f(p2 * kLn2), 1.0f - o);
+    const float near_one = fmaf(o, one_minus_exp2(p2), 1.0f - o);
+    const float r = alpha <= 0.5f ? 1.0f - alpha : near_one;
+    return alpha == kAlphaMax ? 1.0f - kAlphaMax : r;
 }
 
 // ----------------------------------------------------------------------------------------

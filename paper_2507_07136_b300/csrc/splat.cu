@@ -22,6 +22,7 @@
 //    issued before any store.
 #include "device.cuh"
 #include "splat.cuh"
+#include "tc.cuh"
 
 namespace lsv2 {
 
@@ -86,30 +87,116 @@ __global__ void __launch_bounds__(256) pack_records_kernel(PackArgs a)
     reinterpret_cast<float2*>(rec + rec_floats - 4)[0] = reinterpret_cast<const float2*>(a.extent)[o];
 }
 
-// One tile of one view.  Only this warp's shared-memory region is touched, so the warps of a
-// CTA need no barrier between them.
+// One tile of one view.
 struct TileJob {
-    int width, height, GX, tile, lev0;   // lev0: first level accumulated by this CTA
+    int width, height, GX, tile;
     uint32_t beg, end;
     const uint32_t* gauss_ids;
     const float* recs;
     float* coeff;
     float* final_T;
     uint32_t* n_last;
+    int32_t* status;
 };
 
-template <int LEVELS, int K, int TW, int TH, int BATCH = 0, int LCTA = LEVELS>
-__device__ __forceinline__ void splat_tile(const TileJob& a, float* smem)
-{
-    using C = SplatCfg<LEVELS, K, TW, TH, BATCH, LCTA>;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float* acc = smem + warp * C::kAccFloats;
-    float* stage = smem + C::kWarps * C::kAccFloats + warp * (C::kBatch * C::kSmemRecFloats);
+namespace {
 
+constexpr uint64_t kWaitNs = 1000000000ull;   // bound of every wait on a stage barrier (1 s)
+
+// Shared memory of one tile: accumulators [kWarps][kAccFloats], stage barriers, the count of
+// consumer warps whose pixels have all terminated, then kStages stages of
+// [kBatch records][kBatch culling boxes (u, v, ex, ey)].
+template <class C>
+struct SplatSmem {
+    float* acc;
+    uint64_t* full;    // a stage's batch has landed (32 producer arrivals + the copies' bytes)
+    uint64_t* empty;   // every consumer warp is done with the stage (kWarps arrivals)
+    int* done_warps;
+    unsigned char* stages;
+    __device__ explicit SplatSmem(unsigned char* base)
+        : acc(reinterpret_cast<float*>(base)),
+          full(reinterpret_cast<uint64_t*>(base + C::kAccBytes)),
+          empty(reinterpret_cast<uint64_t*>(base + C::kAccBytes) + 8),
+          done_warps(reinterpret_cast<int*>(base + C::kAccBytes + 128)),
+          stages(base + C::kFixedBytes)
+    {
+    }
+    __device__ const unsigned char* rec(int s) const { return stages + s * C::kStageBytes; }
+    __device__ float4* box(int s) const
+    {
+        return reinterpret_cast<float4*>(stages + s * C::kStageBytes + C::kBatch * C::kRecBytes);
+    }
+};
+
+// Warp-uniform bounded wait for a barrier phase; `stop` (optional) ends the wait early once
+// every consumer warp has finished.  Returns 1 when the phase completed, 0 on stop, -1 on
+// timeout.
+__device__ __forceinline__ int warp_wait(uint64_t* bar, uint32_t parity, const volatile int* done_warps,
+                                         int all_done)
+{
+    const uint64_t t0 = tc::globaltimer();
+    while (true) {
+        if (__all_sync(0xffffffffu, tc::mbar_try(tc::smem_u32(bar), parity))) return 1;
+        if (done_warps && __shfl_sync(0xffffffffu, *done_warps, 0) >= all_done) return 0;
+        if (__any_sync(0xffffffffu, tc::globaltimer() - t0 > kWaitNs)) return -1;
+    }
+}
+
+// Producer warp: batch b goes to stage b % kStages once every consumer warp has released the
+// stage's previous batch; each lane copies one record (bulk async copy, completing on the
+// stage's barrier) and writes its culling box.  Before returning it waits until every copy it
+// issued has landed, so no copy is in flight into shared memory that is reused.
+template <class C>
+__device__ void splat_produce(const TileJob& a, const SplatSmem<C>& sm, int lane)
+{
+    const uint32_t n = a.end - a.beg;
+    const uint32_t nb = (n + C::kBatch - 1) / C::kBatch;
+    const volatile int* done_warps = sm.done_warps;
+    uint32_t issued = 0;
+    for (uint32_t b = 0; b < nb; ++b) {
+        const int s = (int)(b % C::kStages);
+        if (b >= (uint32_t)C::kStages) {
+            const int w = warp_wait(sm.empty + s, ((b / C::kStages) - 1u) & 1u, done_warps, C::kWarps);
+            if (w < 0 && lane == 0) report(a.status, LSV2_ERR_TIMEOUT);
+            if (w <= 0) break;
+        }
+        if (__shfl_sync(0xffffffffu, *done_warps, 0) >= C::kWarps) break;
+        const uint32_t cnt = min((uint32_t)C::kBatch, n - b * C::kBatch);
+        const uint32_t full = tc::smem_u32(sm.full + s);
+        if (lane == 0) tc::mbar_expect_tx(full, cnt * (uint32_t)C::kRecBytes);
+        __syncwarp();
+        float4 box = make_float4(0.0f, 0.0f, -1.0f, -1.0f);
+        if ((uint32_t)lane < cnt) {
+            const uint32_t g = a.gauss_ids[a.beg + b * C::kBatch + lane];
+            const float* src = a.recs + (size_t)g * C::kRecFloats;
+            tc::bulk_load(tc::smem_u32(sm.rec(s) + lane * C::kRecBytes), src, (uint32_t)C::kRecBytes, full);
+            const float2 xy = __ldg(reinterpret_cast<const float2*>(src));
+            const float2 ex = __ldg(reinterpret_cast<const float2*>(src + C::kRecFloats - 4));
+            box = make_float4(xy.x, xy.y, ex.x, ex.y);
+        }
+        if (lane < C::kBatch) sm.box(s)[lane] = box;
+        tc::mbar_arrive(full);
+        issued = b + 1;
+    }
+    const uint32_t first = issued > (uint32_t)C::kStages ? issued - C::kStages : 0u;
+    for (uint32_t b = first; b < issued; ++b) {
+        if (warp_wait(sm.full + (int)(b % C::kStages), (b / C::kStages) & 1u, nullptr, 0) < 0) {
+            if (lane == 0) report(a.status, LSV2_ERR_TIMEOUT);
+            break;
+        }
+    }
+}
+
+// Consumer warp: 32 pixels (one per lane), front to back over the tile's batches.
+template <class C, int LEVELS, int K, int TW, int TH>
+__device__ void splat_consume(const TileJob& a, const SplatSmem<C>& sm, int warp, int lane)
+{
+    constexpr int kB = C::kBatch;
+    constexpr int kChunk = 4;   // kept records evaluated together
+    float* acc = sm.acc + warp * C::kAccFloats;
     const int GX = a.GX;
-    const int tile = a.tile;
-    const int tx = tile % GX, ty = tile / GX;
-    const int lx = threadIdx.x % TW, ly = threadIdx.x / TW;
+    const int tx = a.tile % GX, ty = a.tile / GX;
+    const int lx = lane % TW, ly = warp * (32 / TW) + lane / TW;
     const int px = tx * TW + lx, py = ty * TH + ly;
     const bool inside = px < a.width && py < a.height;
     // pixel strip covered by this warp
@@ -121,109 +208,107 @@ __device__ __forceinline__ void splat_tile(const TileJob& a, float* smem)
         *reinterpret_cast<float4*>(acc + i) = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncwarp();
 
-    const uint32_t beg = a.beg, end = a.end;
+    const uint32_t n = a.end - a.beg;
+    const uint32_t nb = (n + kB - 1) / kB;
     float T = 1.0f;
     uint32_t last = 0;
-    bool done = !inside;
+    bool done = !inside, wdone = false;
     const float pxf = (float)px, pyf = (float)py;
+    const volatile int* done_warps = sm.done_warps;
 
-    // Next batch's record for this lane, fetched into registers while the current batch is
-    // processed (the gather from L2 is the other latency the warp would otherwise wait on).
-    constexpr int kV = C::kSmemRecFloats / 4;
-    float4 nx[kV];
-    float2 nex = make_float2(-1.0f, -1.0f);
-    bool nvalid = false;
-    auto fetch = [&](uint32_t b) {
-        const uint32_t j = b + lane;
-        nvalid = lane < C::kBatch && j < end;
-        if (nvalid) {
-            const uint32_t g = a.gauss_ids[j];
-            const float4* src = reinterpret_cast<const float4*>(a.recs + (size_t)g * C::kRecFloats);
-#pragma unroll
-            for (int v = 0; v < kV; ++v) nx[v] = __ldg(src + v);
-            nex = __ldg(reinterpret_cast<const float2*>(a.recs + (size_t)g * C::kRecFloats + C::kRecFloats - 4));
+    for (uint32_t b = 0; b < nb; ++b) {
+        const int s = (int)(b % C::kStages);
+        if (!wdone && __all_sync(0xffffffffu, done)) {
+            wdone = true;
+            if (lane == 0) atomicAdd(sm.done_warps, 1);
         }
-    };
-    if (beg < end) fetch(beg);
-
-    for (uint32_t base = beg; base < end; base += C::kBatch) {
-        if (__all_sync(0xffffffffu, done)) break;
-        const bool keep = nvalid && nex.x >= 0.0f && nx[0].x + nex.x >= wx0 && nx[0].x - nex.x <= wx1 &&
-                          nx[0].y + nex.y >= wy0 && nx[0].y - nex.y <= wy1;
-        if (keep) {
-            float4* dst = reinterpret_cast<float4*>(stage + lane * C::kSmemRecFloats);
-#pragma unroll
-            for (int v = 0; v < kV; ++v) dst[v] = nx[v];
+        if (wdone && __shfl_sync(0xffffffffu, *done_warps, 0) >= C::kWarps) break;
+        // (the producer issues no further batch once every warp is done)
+        const int w = warp_wait(sm.full + s, (b / C::kStages) & 1u, done_warps, C::kWarps);
+        if (w <= 0) {
+            if (w < 0 && lane == 0) report(a.status, LSV2_ERR_TIMEOUT);
+            if (!wdone && lane == 0) atomicAdd(sm.done_warps, 1);
+            break;
         }
-        uint32_t mask = __ballot_sync(0xffffffffu, keep);
-        __syncwarp();
-        if (base + C::kBatch < end) fetch(base + C::kBatch);
-        if (mask) {
-            // software pipeline: the next record's power and 2^power (independent of T) are
-            // formed before this record's transmittance update and accumulation
-            int i = __ffs(mask) - 1;
-            mask &= mask - 1;
-            const float* r = stage + i * C::kSmemRecFloats;
-            float p2 = eval_power2(*reinterpret_cast<const float4*>(r), *reinterpret_cast<const float4*>(r + 4),
-                                   *reinterpret_cast<const float4*>(r + 8), pxf, pyf);
-            float o = r[11];
-            float ex2;
-            asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(ex2) : "f"(p2));
-            while (true) {
-                int jn = -1;
-                const float* rn = r;
-                float p2n = 0.0f, on = 0.0f, exn = 0.0f;
-                if (mask) {
-                    jn = __ffs(mask) - 1;
-                    mask &= mask - 1;
-                    rn = stage + jn * C::kSmemRecFloats;
-                    p2n = eval_power2(*reinterpret_cast<const float4*>(rn), *reinterpret_cast<const float4*>(rn + 4),
-                                      *reinterpret_cast<const float4*>(rn + 8), pxf, pyf);
-                    on = rn[11];
-                    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(exn) : "f"(p2n));
+        if (!wdone) {
+            const float4 box = lane < kB ? sm.box(s)[lane] : make_float4(0.0f, 0.0f, -1.0f, -1.0f);
+            const bool keep = box.z >= 0.0f && box.x + box.z >= wx0 && box.x - box.z <= wx1 &&
+                              box.y + box.w >= wy0 && box.y - box.w <= wy1;
+            const unsigned char* recs = sm.rec(s);
+            // kept records in list order, kChunk at a time
+            uint32_t m = __ballot_sync(0xffffffffu, keep);
+            while (m != 0u) {
+                if (__all_sync(0xffffffffu, done)) break;
+                int sl[kChunk];
+#pragma unroll
+                for (int j = 0; j < kChunk; ++j) {
+                    sl[j] = m ? __ffs(m) - 1 : -1;
+                    m &= m - 1u;
                 }
-                float e = 0.0f;
-                if (!done && p2 <= 0.0f) {
-                    const float alpha = fminf(kAlphaMax, o * ex2);
-                    if (alpha >= kAlphaMin) {
-                        const float test_T = T * one_minus_alpha(alpha, o, p2);
-                        if (test_T < kTMin) {
-                            done = true;
-                        } else {
-                            e = alpha * T;
-                            T = test_T;
-                            last = base + i - beg + 1;
+                // (A) alpha_j and 1 - alpha_j of the chunk's records at this pixel: independent
+                // of one another (instruction-level parallelism across the chunk)
+                float al[kChunk], om[kChunk];
+#pragma unroll
+                for (int j = 0; j < kChunk; ++j) {
+                    const float* r = reinterpret_cast<const float*>(recs + max(sl[j], 0) * C::kRecBytes);
+                    const float4 g0 = *reinterpret_cast<const float4*>(r);
+                    const float4 ax = *reinterpret_cast<const float4*>(r + 4);
+                    const float4 axl = *reinterpret_cast<const float4*>(r + 8);
+                    const float p2 = eval_power2(g0, ax, axl, pxf, pyf);
+                    float ex2;
+                    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(ex2) : "f"(p2));
+                    const float alpha = fminf(kAlphaMax, axl.w * ex2);
+                    al[j] = (sl[j] >= 0 && p2 <= 0.0f && alpha >= kAlphaMin) ? alpha : 0.0f;
+                    om[j] = one_minus_alpha(alpha, axl.w, p2);
+                }
+                // (B) front-to-back transmittance (Eq. 3): e_j = alpha_j T_j, the serial part;
+                // al[j] becomes e_j (0 where the pixel skips or has terminated)
+                uint32_t take_bits = 0;
+                int li = -1;
+#pragma unroll
+                for (int j = 0; j < kChunk; ++j) {
+                    const bool act = !done && al[j] > 0.0f;
+                    const float test_T = T * om[j];
+                    const bool stop = act && test_T < kTMin;
+                    const bool take = act && !stop;
+                    done = done || stop;
+                    al[j] = take ? al[j] * T : 0.0f;
+                    T = take ? test_T : T;
+                    take_bits |= take ? (1u << j) : 0u;
+                    li = take ? sl[j] : li;
+                }
+                if (li >= 0) last = b * kB + (uint32_t)li + 1u;
+                // (C) W_col += w e_j for the pairs of every record some pixel of the warp takes
+                const uint32_t used = __reduce_or_sync(0xffffffffu, take_bits);
+#pragma unroll
+                for (int j = 0; j < kChunk; ++j) {
+                    if (used & (1u << j)) {
+                        const float* r = reinterpret_cast<const float*>(recs + sl[j] * C::kRecBytes);
+                        const float* wr = r + 12;
+                        const uint32_t* cw = reinterpret_cast<const uint32_t*>(r + 12 + C::kPairs);
+                        uint32_t cols[(C::kPairs + 3) / 4];
+#pragma unroll
+                        for (int q = 0; q < (C::kPairs + 3) / 4; ++q) cols[q] = cw[q];
+                        float v[C::kPairs];
+                        int off[C::kPairs];
+#pragma unroll
+                        for (int p = 0; p < C::kPairs; ++p) {
+                            off[p] = (int)__byte_perm(cols[p >> 2], 0u, 0x4440u | (uint32_t)(p & 3)) * 33 + lane;
+                            v[p] = acc[off[p]];
                         }
+#pragma unroll
+                        for (int p = 0; p < C::kPairs; ++p) v[p] = fmaf(al[j], wr[p], v[p]);
+#pragma unroll
+                        for (int p = 0; p < C::kPairs; ++p) acc[off[p]] = v[p];
                     }
                 }
-                if (__any_sync(0xffffffffu, e > 0.0f)) {
-                    const float* wr = r + 12 + a.lev0 * K;
-                    const uint8_t* cr = reinterpret_cast<const uint8_t*>(r + 12 + C::kPairs) + a.lev0 * K;
-                    const int cbase = a.lev0 * 64;
-                    float v[C::kCtaPairs];
-                    int off[C::kCtaPairs];
-#pragma unroll
-                    for (int p = 0; p < C::kCtaPairs; ++p) {
-                        off[p] = ((int)cr[p] - cbase) * 33 + lane;
-                        v[p] = acc[off[p]];
-                    }
-#pragma unroll
-                    for (int p = 0; p < C::kCtaPairs; ++p) v[p] = fmaf(e, wr[p], v[p]);
-#pragma unroll
-                    for (int p = 0; p < C::kCtaPairs; ++p) acc[off[p]] = v[p];
-                }
-                if (jn < 0) break;
-                i = jn;
-                r = rn;
-                p2 = p2n;
-                o = on;
-                ex2 = exn;
             }
         }
         __syncwarp();
+        if (lane == 0) tc::mbar_arrive(tc::smem_u32(sm.empty + s));
     }
 
-    if (inside && a.lev0 == 0) {
+    if (inside) {
         const size_t pix = (size_t)py * a.width + px;
         a.final_T[pix] = T;
         a.n_last[pix] = last;
@@ -231,15 +316,14 @@ __device__ __forceinline__ void splat_tile(const TileJob& a, float* smem)
     __syncwarp();
     // write this warp's 32 pixels: per row segment TW pixels x 64 floats (contiguous in HBM)
     const size_t P = (size_t)a.width * a.height;
-#pragma unroll
-    for (int lc = 0; lc < LCTA; ++lc) {
-        const int lev = a.lev0 + lc;
+#pragma unroll 1
+    for (int lev = 0; lev < LEVELS; ++lev) {
         for (int q = lane; q < 32 * 16; q += 32) {
             const int pl = q >> 4;  // pixel within the warp (row-major over the strip)
             const int c4 = (q & 15) * 4;
             const int gx = tx * TW + (pl % TW), gy = ty * TH + warp * kRows + pl / TW;
             if (gx < a.width && gy < a.height) {
-                const float* col = acc + (lc * 64 + c4) * 33 + pl;
+                const float* col = acc + (lev * 64 + c4) * 33 + pl;
                 float4 val = make_float4(col[0], col[33], col[66], col[99]);
                 __stcs(reinterpret_cast<float4*>(a.coeff + ((size_t)lev * P + (size_t)gy * a.width + gx) * 64 + c4), val);
             }
@@ -247,23 +331,45 @@ __device__ __forceinline__ void splat_tile(const TileJob& a, float* smem)
     }
 }
 
-template <int LEVELS, int K, int TW, int TH, int LCTA>
-__global__ void __launch_bounds__(TW* TH) splat_kernel(SplatArgs a)
+}  // namespace
+
+// All threads of the CTA: kWarps consumer warps and the producer warp (the last one).
+template <int LEVELS, int K, int TW, int TH, int BATCH = 0>
+__device__ __forceinline__ void splat_tile(const TileJob& a, unsigned char* smem)
 {
-    extern __shared__ __align__(16) float smem[];
+    using C = SplatCfg<LEVELS, K, TW, TH, BATCH>;
+    const SplatSmem<C> sm(smem);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < C::kStages; ++s) {
+            tc::mbar_init(tc::smem_u32(sm.full + s), 32);
+            tc::mbar_init(tc::smem_u32(sm.empty + s), C::kWarps);
+        }
+        *sm.done_warps = 0;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == C::kWarps)
+        splat_produce<C>(a, sm, lane);
+    else
+        splat_consume<C, LEVELS, K, TW, TH>(a, sm, warp, lane);
+}
+
+template <int LEVELS, int K, int TW, int TH>
+__global__ void __launch_bounds__(TW* TH + 32) splat_kernel(SplatArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
     const int tile = blockIdx.x;
-    TileJob j{a.cam.width, a.cam.height, (a.cam.width + TW - 1) / TW, tile, (int)blockIdx.y * LCTA,
-              a.tile_ranges[2 * tile], a.tile_ranges[2 * tile + 1], a.gauss_ids, a.recs, a.coeff, a.final_T,
-              a.n_last};
-    splat_tile<LEVELS, K, TW, TH, 0, LCTA>(j, smem);
+    TileJob j{a.cam.width, a.cam.height, (a.cam.width + TW - 1) / TW, tile, a.tile_ranges[2 * tile],
+              a.tile_ranges[2 * tile + 1], a.gauss_ids, a.recs, a.coeff, a.final_T, a.n_last, a.status};
+    splat_tile<LEVELS, K, TW, TH>(j, smem);
 }
 
 // Persistent over the (view, tile) work items of several views: each CTA takes the next global
 // tile id from an atomic counter (largest views first, as they come first in the numbering).
 template <int LEVELS, int K, int TW, int TH, int BATCH>
-__global__ void __launch_bounds__(TW* TH) splat_views_kernel(SplatViewsArgs a)
+__global__ void __launch_bounds__(TW* TH + 32) splat_views_kernel(SplatViewsArgs a)
 {
-    extern __shared__ __align__(16) float smem[];
+    extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_tile;
     while (true) {
         if (threadIdx.x == 0) s_tile = (int)atomicAdd(a.queue, 1u);
@@ -274,33 +380,27 @@ __global__ void __launch_bounds__(TW* TH) splat_views_kernel(SplatViewsArgs a)
         int v = 0;
         while (v + 1 < a.V && tg >= a.view[v + 1].tile_base) ++v;
         const SplatView& w = a.view[v];
-        TileJob j{w.width, w.height, w.GX, tg - w.tile_base, 0, a.tile_ranges[2 * tg], a.tile_ranges[2 * tg + 1],
+        TileJob j{w.width, w.height, w.GX, tg - w.tile_base, a.tile_ranges[2 * tg], a.tile_ranges[2 * tg + 1],
                   a.gauss_ids, a.recs + w.rec_off, a.coeff + w.coeff_off, a.final_T + w.pix_off,
-                  a.n_last + w.pix_off};
+                  a.n_last + w.pix_off, a.status};
         splat_tile<LEVELS, K, TW, TH, BATCH>(j, smem);
     }
 }
 
 namespace {
 
-template <int LEVELS, int K, int TW, int TH, int LCTA>
+template <int LEVELS, int K, int TW, int TH>
 cudaError_t launch_t(const SplatArgs& a, cudaStream_t stream)
 {
-    using C = SplatCfg<LEVELS, K, TW, TH, 0, LCTA>;
+    using C = SplatCfg<LEVELS, K, TW, TH>;
     static_assert(C::kSmemBytes <= 232448, "shared memory budget");
-    auto kern = splat_kernel<LEVELS, K, TW, TH, LCTA>;
+    auto kern = splat_kernel<LEVELS, K, TW, TH>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
     if (e != cudaSuccess) return e;
     const int GX = (a.cam.width + TW - 1) / TW, GY = (a.cam.height + TH - 1) / TH;
     if (GX * GY == 0) return cudaSuccess;
-    kern<<<dim3(GX * GY, LEVELS / LCTA), TW * TH, C::kSmemBytes, stream>>>(a);
+    kern<<<GX * GY, C::kThreads, C::kSmemBytes, stream>>>(a);
     return cudaGetLastError();
-}
-
-template <int LEVELS, int K, int TW, int TH>
-cudaError_t launch_split(const SplatArgs& a, cudaStream_t stream)
-{
-    return launch_t<LEVELS, K, TW, TH, LEVELS>(a, stream);
 }
 
 template <int LEVELS, int K, int TW, int TH, int BATCH>
@@ -312,13 +412,13 @@ cudaError_t launch_views_t(const SplatViewsArgs& a, int num_sms, cudaStream_t st
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TW * TH, C::kSmemBytes);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::kThreads, C::kSmemBytes);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     if (a.total_tiles == 0) return cudaSuccess;
     e = cudaMemsetAsync(a.queue, 0, sizeof(uint32_t), stream);
     if (e != cudaSuccess) return e;
-    kern<<<num_sms * per_sm, TW * TH, C::kSmemBytes, stream>>>(a);
+    kern<<<num_sms * per_sm, C::kThreads, C::kSmemBytes, stream>>>(a);
     return cudaGetLastError();
 }
 
@@ -328,7 +428,7 @@ cudaError_t launch_views_b(const SplatViewsArgs& a, int batch, int num_sms, cuda
     using Auto = SplatCfg<LEVELS, K, TW, TH>;
     if (batch == 16) return launch_views_t<LEVELS, K, TW, TH, 16>(a, num_sms, stream);
     if (batch == 0 || batch == Auto::kBatch) return launch_views_t<LEVELS, K, TW, TH, Auto::kBatch>(a, num_sms, stream);
-    return cudaErrorInvalidValue;   // 32 does not fit this configuration's shared memory
+    return cudaErrorInvalidValue;
 }
 
 template <int LEVELS, int K>
@@ -343,9 +443,9 @@ cudaError_t launch_views_tile(const SplatViewsArgs& a, int tw, int th, int batch
 template <int LEVELS, int K>
 cudaError_t launch_tile(const SplatArgs& a, cudaStream_t stream)
 {
-    if (a.cam.tile_w == 16 && a.cam.tile_h == 16) return launch_split<LEVELS, K, 16, 16>(a, stream);
-    if (a.cam.tile_w == 8 && a.cam.tile_h == 8) return launch_split<LEVELS, K, 8, 8>(a, stream);
-    if (a.cam.tile_w == 32 && a.cam.tile_h == 8) return launch_split<LEVELS, K, 32, 8>(a, stream);
+    if (a.cam.tile_w == 16 && a.cam.tile_h == 16) return launch_t<LEVELS, K, 16, 16>(a, stream);
+    if (a.cam.tile_w == 8 && a.cam.tile_h == 8) return launch_t<LEVELS, K, 8, 8>(a, stream);
+    if (a.cam.tile_w == 32 && a.cam.tile_h == 8) return launch_t<LEVELS, K, 32, 8>(a, stream);
     return cudaErrorInvalidValue;
 }
 

@@ -21,24 +21,30 @@ constexpr int kMaxPairs = 24;  // levels * K
 __host__ __device__ constexpr int smem_record_bytes(int P) { return ((48 + 5 * P) + 15) / 16 * 16; }
 __host__ __device__ constexpr int record_bytes(int P) { return smem_record_bytes(P) + 16; }
 
-// BATCH: records staged per warp at a time (16 or 32); 0 picks 32 when shared memory allows.
-// LCTA: levels accumulated by one CTA (LEVELS, or 1 when each level of a tile gets its own CTA).
-template <int LEVELS, int K, int TW, int TH, int BATCH = 0, int LCTA = LEVELS>
+// One CTA per tile: kWarps consumer warps (one pixel per lane, 32 pixels per warp) and one
+// producer warp that gathers the tile's records, BATCH at a time, into a ring of kStages
+// shared-memory stages with bulk async copies.  BATCH: 16 or 32 records per stage (0 = 32).
+template <int LEVELS, int K, int TW, int TH, int BATCH = 0>
 struct SplatCfg {
-    static constexpr int kThreads = TW * TH;
-    static constexpr int kWarps = kThreads / 32;
+    static constexpr int kPixels = TW * TH;
+    static constexpr int kWarps = kPixels / 32;      // consumer warps
+    static constexpr int kThreads = kPixels + 32;    // + the producer warp
     static constexpr int kPairs = LEVELS * K;        // pairs in a record
-    static constexpr int kCtaPairs = LCTA * K;       // pairs this CTA accumulates
-    static constexpr int kCols = LCTA * 64;
+    static constexpr int kCols = LEVELS * 64;
     static constexpr int kAccFloats = (kCols * 33 + 3) / 4 * 4;
-    static constexpr int kSmemRecFloats = smem_record_bytes(kPairs) / 4;
-    static constexpr int kRecFloats = record_bytes(kPairs) / 4;
+    static constexpr int kRecBytes = record_bytes(kPairs);
+    static constexpr int kRecFloats = kRecBytes / 4;
+    static constexpr int kBatch = BATCH != 0 ? BATCH : 32;
     static constexpr int kAccBytes = kWarps * kAccFloats * 4;
-    static constexpr int kBatch =
-        BATCH != 0 ? BATCH : ((kAccBytes + kWarps * 32 * kSmemRecFloats * 4 <= 232448) ? 32 : 16);
-    static constexpr int kSmemBytes = kAccBytes + kWarps * kBatch * kSmemRecFloats * 4;
-    static_assert(kThreads % 32 == 0 && 32 % TW == 0, "a warp covers whole rows of a tile");
+    static constexpr int kStageBytes = kBatch * (kRecBytes + 16);   // records + culling boxes
+    static constexpr int kFixedBytes = kAccBytes + 256;             // + barriers and flags
+    static constexpr int kStagesFit = (232448 - 64 - kFixedBytes) / kStageBytes;
+    static constexpr int kStages = kWarps >= 8 ? (kStagesFit < 8 ? kStagesFit : 8) : 4;
+    static constexpr int kSmemBytes = kFixedBytes + kStages * kStageBytes;
+    static_assert(kPixels % 32 == 0 && 32 % TW == 0, "a warp covers whole rows of a tile");
     static_assert(kPairs <= kMaxPairs, "pairs per record");
+    static_assert(kRecBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
+    static_assert(kStages >= 2, "at least two stages");
 };
 
 struct PackArgs {

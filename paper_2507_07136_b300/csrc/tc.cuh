@@ -80,6 +80,30 @@ __device__ __forceinline__ uint64_t globaltimer()
     return t;
 }
 
+// One non-blocking-ish probe of the phase with the given parity (acquire semantics).
+__device__ __forceinline__ bool mbar_try(uint32_t mbar_saddr, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar_saddr), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Arrival (release semantics) without and with a transaction-count increase, and a bare
+// transaction-count increase.
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar_saddr)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar_saddr) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar_saddr, uint32_t bytes)
+{
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(mbar_saddr), "r"(bytes) : "memory");
+}
+
 // Wait for the mbarrier phase with the given parity; gives up after `limit_ns` and returns false.
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar_saddr, uint32_t parity, uint64_t limit_ns = 1000000000ull)
 {
