@@ -163,7 +163,7 @@ lsv2_status lsv2_splat_coeffs(const lsv2_camera* cam, int64_t n, const lsv2_proj
  * layouts and results as lsv2_splat_coeffs, minus the workspace: the per-Gaussian scratch
  * lives in a file-scope device array of LSV2_SPLAT_NOALLOC_SCRATCH_BYTES.
  *   - Limit: lsv2_splat_workspace_bytes(n, levels, K) must not exceed
- *     LSV2_SPLAT_NOALLOC_SCRATCH_BYTES (8 MiB: 65,536 Gaussians at 3 levels, K = 4);
+ *     LSV2_SPLAT_NOALLOC_SCRATCH_BYTES (8 MiB: 52,428 Gaussians at 3 levels, K = 4);
  *     larger calls return LSV2_ERR_CAPACITY and launch nothing.
  *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
  *     with that device current; make that first call before any stream capture.

@@ -156,25 +156,22 @@ __device__ __forceinline__ dfloat df_sqrt(dfloat x)
 // The conic's own entries can cancel badly for elongated footprints (terms of +-100 summing to
 // -2 at 100 px along the long axis, where rounding the entries alone moves the power by 1e-5),
 // so it is evaluated in its principal frame: power * log2(e) = A u^2 + B v^2 with u = e1 . d
-// (stiff axis) and v = e2 . d.  The stiff axis is stored as a float pair; when the footprint is
-// elongated (kappa = q1 / q2 > 4) u is formed with its low part and an exact product, so its
-// error is one rounding of u itself.  `g0` = (u_hi, v_hi, u_lo, v_lo) of the 2D mean,
-// `ax` = (c_hi, s_hi, A, B), `axl` = (c_lo, s_lo, kappa, .).
+// (stiff axis) and v = e2 . d.  The stiff axis is stored as a float pair and u is formed with
+// its low part and an exact product, so its error is one rounding of u itself (needed when the
+// footprint is elongated; done for every footprint, which keeps the evaluation branch-free).
+// `g0` = (u_hi, v_hi, u_lo, v_lo) of the 2D mean, `ax` = (c_hi, s_hi, A, B),
+// `axl` = (c_lo, s_lo, kappa, .).
 __device__ __forceinline__ float eval_power2(const float4& g0, const float4& ax, const float4& axl, float pxf,
                                              float pyf)
 {
     const float dx = __fadd_rn(__fsub_rn(g0.x, pxf), g0.z);
     const float dy = __fadd_rn(__fsub_rn(g0.y, pyf), g0.w);
     const float v = fmaf(ax.x, dy, -(ax.y * dx));
-    float u;
-    if (axl.z > 4.0f) {
-        const float t = __fmul_rn(ax.y, dy);
-        const float te = __fmaf_rn(ax.y, dy, -t);
-        const float corr = __fmaf_rn(axl.x, dx, __fmaf_rn(axl.y, dy, te));
-        u = __fadd_rn(__fmaf_rn(ax.x, dx, t), corr);
-    } else {
-        u = fmaf(ax.x, dx, ax.y * dy);
-    }
+    // u = (c_hi + c_lo) dx + (s_hi + s_lo) dy with the product s_hi dy split exactly
+    const float t = __fmul_rn(ax.y, dy);
+    const float te = __fmaf_rn(ax.y, dy, -t);
+    const float corr = __fmaf_rn(axl.x, dx, __fmaf_rn(axl.y, dy, te));
+    const float u = __fadd_rn(__fmaf_rn(ax.x, dx, t), corr);
     return fmaf(ax.z * u, u, ax.w * v * v);
 }
 

@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(256) pack_records_kernel(PackArgs a)
         }
     // within each level: emptied pairs first (pointing at the level's first real column), real
     // pairs last, so every level's K slots stay contiguous
-    uint8_t* cb = reinterpret_cast<uint8_t*>(rec + 12 + P);
+    uint32_t* cb = reinterpret_cast<uint32_t*>(rec + 12 + P);
     for (int lev = 0; lev < a.levels; ++lev) {
         const int p0 = lev * a.K;
         int first_real = -1;
@@ -74,13 +74,13 @@ __global__ void __launch_bounds__(256) pack_records_kernel(PackArgs a)
         for (int p = p0; p < p0 + a.K; ++p)
             if (!real[p]) {
                 rec[12 + slot] = 0.0f;
-                cb[slot] = (uint8_t)(first_real >= 0 ? col[first_real] : lev * 64);
+                cb[slot] = (uint32_t)(first_real >= 0 ? col[first_real] : lev * 64) * 132u;
                 ++slot;
             }
         for (int p = p0; p < p0 + a.K; ++p)
             if (real[p]) {
                 rec[12 + slot] = wv[p];
-                cb[slot] = (uint8_t)col[p];
+                cb[slot] = (uint32_t)col[p] * 132u;
                 ++slot;
             }
     }
@@ -103,21 +103,28 @@ namespace {
 
 constexpr uint64_t kWaitNs = 1000000000ull;   // bound of every wait on a stage barrier (1 s)
 
-// Shared memory of one tile: accumulators [kWarps][kAccFloats], stage barriers, the count of
-// consumer warps whose pixels have all terminated, then kStages stages of
-// [kBatch records][kBatch culling boxes (u, v, ex, ey)].
+// Shared memory of one CTA: accumulators [kWarps][kAccFloats], stage barriers and flags, then
+// kStages stages of [kBatch records][kBatch culling boxes (u, v, ex, ey)].  The barriers are
+// initialised once per CTA; batches are numbered across the CTA's tiles (stage = batch %
+// kStages, phase parity = (batch / kStages) & 1), so a persistent CTA never re-initialises them.
 template <class C>
 struct SplatSmem {
     float* acc;
     uint64_t* full;    // a stage's batch has landed (32 producer arrivals + the copies' bytes)
     uint64_t* empty;   // every consumer warp is done with the stage (kWarps arrivals)
-    int* done_warps;
+    int* done_warps;   // consumer warps of the current tile whose pixels have all terminated
+    int* abort;        // a wait of this CTA ran out: every later wait gives up at once
+    uint32_t* issued;  // batches the producer issued for the current tile
+    int* skip;         // a wait ran out somewhere (status word): skip the remaining tiles
     unsigned char* stages;
     __device__ explicit SplatSmem(unsigned char* base)
         : acc(reinterpret_cast<float*>(base)),
           full(reinterpret_cast<uint64_t*>(base + C::kAccBytes)),
           empty(reinterpret_cast<uint64_t*>(base + C::kAccBytes) + 8),
           done_warps(reinterpret_cast<int*>(base + C::kAccBytes + 128)),
+          abort(reinterpret_cast<int*>(base + C::kAccBytes + 132)),
+          issued(reinterpret_cast<uint32_t*>(base + C::kAccBytes + 136)),
+          skip(reinterpret_cast<int*>(base + C::kAccBytes + 140)),
           stages(base + C::kFixedBytes)
     {
     }
@@ -126,39 +133,58 @@ struct SplatSmem {
     {
         return reinterpret_cast<float4*>(stages + s * C::kStageBytes + C::kBatch * C::kRecBytes);
     }
+    // once per CTA, by one thread, before a __syncthreads
+    __device__ void init() const
+    {
+        for (int s = 0; s < C::kStages; ++s) {
+            tc::mbar_init(tc::smem_u32(full + s), 32);
+            tc::mbar_init(tc::smem_u32(empty + s), C::kWarps);
+        }
+        *done_warps = 0;
+        *abort = 0;
+        *skip = 0;
+    }
 };
 
-// Warp-uniform bounded wait for a barrier phase; `stop` (optional) ends the wait early once
-// every consumer warp has finished.  Returns 1 when the phase completed, 0 on stop, -1 on
-// timeout.
+constexpr int kWaitDone = 1, kWaitStopped = 0, kWaitTimeout = -1, kWaitAborted = -2;
+
+// Warp-uniform bounded wait for a barrier phase.  `done_warps` (optional) ends the wait early
+// once all_done consumer warps have finished; a wait that runs out raises the CTA's abort flag
+// (and the caller reports LSV2_ERR_TIMEOUT), after which every other wait returns at once.
 __device__ __forceinline__ int warp_wait(uint64_t* bar, uint32_t parity, const volatile int* done_warps,
-                                         int all_done)
+                                         int all_done, volatile int* abort)
 {
     const uint64_t t0 = tc::globaltimer();
     while (true) {
-        if (__all_sync(0xffffffffu, tc::mbar_try(tc::smem_u32(bar), parity))) return 1;
-        if (done_warps && __shfl_sync(0xffffffffu, *done_warps, 0) >= all_done) return 0;
-        if (__any_sync(0xffffffffu, tc::globaltimer() - t0 > kWaitNs)) return -1;
+        if (__all_sync(0xffffffffu, tc::mbar_try(tc::smem_u32(bar), parity))) return kWaitDone;
+        if (__shfl_sync(0xffffffffu, *abort, 0)) return kWaitAborted;
+        if (done_warps && __shfl_sync(0xffffffffu, *done_warps, 0) >= all_done) return kWaitStopped;
+        if (__any_sync(0xffffffffu, tc::globaltimer() - t0 > kWaitNs)) {
+            *abort = 1;
+            return kWaitTimeout;
+        }
     }
 }
 
-// Producer warp: batch b goes to stage b % kStages once every consumer warp has released the
-// stage's previous batch; each lane copies one record (bulk async copy, completing on the
-// stage's barrier) and writes its culling box.  Before returning it waits until every copy it
-// issued has landed, so no copy is in flight into shared memory that is reused.
+// Producer warp: the tile's batch b is CTA batch g = bbase + b and goes to stage g % kStages
+// once every consumer warp has released the stage's previous batch; each lane copies one
+// record (bulk async copy, completing on the stage's barrier) and writes its culling box.
+// Before returning it waits until every copy it issued has landed, so no copy is in flight
+// into shared memory that is reused, and publishes the number of batches it issued.
 template <class C>
-__device__ void splat_produce(const TileJob& a, const SplatSmem<C>& sm, int lane)
+__device__ void splat_produce(const TileJob& a, const SplatSmem<C>& sm, int lane, uint32_t bbase)
 {
     const uint32_t n = a.end - a.beg;
     const uint32_t nb = (n + C::kBatch - 1) / C::kBatch;
     const volatile int* done_warps = sm.done_warps;
     uint32_t issued = 0;
     for (uint32_t b = 0; b < nb; ++b) {
-        const int s = (int)(b % C::kStages);
-        if (b >= (uint32_t)C::kStages) {
-            const int w = warp_wait(sm.empty + s, ((b / C::kStages) - 1u) & 1u, done_warps, C::kWarps);
-            if (w < 0 && lane == 0) report(a.status, LSV2_ERR_TIMEOUT);
-            if (w <= 0) break;
+        const uint32_t g = bbase + b;
+        const int s = (int)(g % C::kStages);
+        if (g >= (uint32_t)C::kStages) {
+            const int w = warp_wait(sm.empty + s, ((g / C::kStages) - 1u) & 1u, done_warps, C::kWarps, sm.abort);
+            if (w == kWaitTimeout && lane == 0) report(a.status, LSV2_ERR_TIMEOUT);
+            if (w != kWaitDone) break;
         }
         if (__shfl_sync(0xffffffffu, *done_warps, 0) >= C::kWarps) break;
         const uint32_t cnt = min((uint32_t)C::kBatch, n - b * C::kBatch);
@@ -167,8 +193,8 @@ __device__ void splat_produce(const TileJob& a, const SplatSmem<C>& sm, int lane
         __syncwarp();
         float4 box = make_float4(0.0f, 0.0f, -1.0f, -1.0f);
         if ((uint32_t)lane < cnt) {
-            const uint32_t g = a.gauss_ids[a.beg + b * C::kBatch + lane];
-            const float* src = a.recs + (size_t)g * C::kRecFloats;
+            const uint32_t id = a.gauss_ids[a.beg + b * C::kBatch + lane];
+            const float* src = a.recs + (size_t)id * C::kRecFloats;
             tc::bulk_load(tc::smem_u32(sm.rec(s) + lane * C::kRecBytes), src, (uint32_t)C::kRecBytes, full);
             const float2 xy = __ldg(reinterpret_cast<const float2*>(src));
             const float2 ex = __ldg(reinterpret_cast<const float2*>(src + C::kRecFloats - 4));
@@ -180,20 +206,22 @@ __device__ void splat_produce(const TileJob& a, const SplatSmem<C>& sm, int lane
     }
     const uint32_t first = issued > (uint32_t)C::kStages ? issued - C::kStages : 0u;
     for (uint32_t b = first; b < issued; ++b) {
-        if (warp_wait(sm.full + (int)(b % C::kStages), (b / C::kStages) & 1u, nullptr, 0) < 0) {
-            if (lane == 0) report(a.status, LSV2_ERR_TIMEOUT);
-            break;
-        }
+        const uint32_t g = bbase + b;
+        const int w = warp_wait(sm.full + (int)(g % C::kStages), (g / C::kStages) & 1u, nullptr, 0, sm.abort);
+        if (w == kWaitTimeout && lane == 0) report(a.status, LSV2_ERR_TIMEOUT);
+        if (w != kWaitDone) break;
     }
+    if (lane == 0) *sm.issued = issued;
 }
 
 // Consumer warp: 32 pixels (one per lane), front to back over the tile's batches.
 template <class C, int LEVELS, int K, int TW, int TH>
-__device__ void splat_consume(const TileJob& a, const SplatSmem<C>& sm, int warp, int lane)
+__device__ uint32_t splat_consume(const TileJob& a, const SplatSmem<C>& sm, int warp, int lane, uint32_t bbase)
 {
     constexpr int kB = C::kBatch;
     constexpr int kChunk = 4;   // kept records evaluated together
     float* acc = sm.acc + warp * C::kAccFloats;
+    unsigned char* acc_lane = reinterpret_cast<unsigned char*>(acc + lane);
     const int GX = a.GX;
     const int tx = a.tile % GX, ty = a.tile / GX;
     const int lx = lane % TW, ly = warp * (32 / TW) + lane / TW;
@@ -216,17 +244,19 @@ __device__ void splat_consume(const TileJob& a, const SplatSmem<C>& sm, int warp
     const float pxf = (float)px, pyf = (float)py;
     const volatile int* done_warps = sm.done_warps;
 
+    uint32_t consumed = 0;   // batches this warp has released
     for (uint32_t b = 0; b < nb; ++b) {
-        const int s = (int)(b % C::kStages);
+        const uint32_t g = bbase + b;
+        const int s = (int)(g % C::kStages);
         if (!wdone && __all_sync(0xffffffffu, done)) {
             wdone = true;
             if (lane == 0) atomicAdd(sm.done_warps, 1);
         }
         if (wdone && __shfl_sync(0xffffffffu, *done_warps, 0) >= C::kWarps) break;
         // (the producer issues no further batch once every warp is done)
-        const int w = warp_wait(sm.full + s, (b / C::kStages) & 1u, done_warps, C::kWarps);
-        if (w <= 0) {
-            if (w < 0 && lane == 0) report(a.status, LSV2_ERR_TIMEOUT);
+        const int w = warp_wait(sm.full + s, (g / C::kStages) & 1u, done_warps, C::kWarps, sm.abort);
+        if (w != kWaitDone) {
+            if (w == kWaitTimeout && lane == 0) report(a.status, LSV2_ERR_TIMEOUT);
             if (!wdone && lane == 0) atomicAdd(sm.done_warps, 1);
             break;
         }
@@ -247,7 +277,8 @@ __device__ void splat_consume(const TileJob& a, const SplatSmem<C>& sm, int warp
                 }
                 // (A) alpha_j and 1 - alpha_j of the chunk's records at this pixel: independent
                 // of one another (instruction-level parallelism across the chunk)
-                float al[kChunk], om[kChunk];
+                float al[kChunk], om[kChunk], p2s[kChunk], os[kChunk];
+                bool high = false;
 #pragma unroll
                 for (int j = 0; j < kChunk; ++j) {
                     const float* r = reinterpret_cast<const float*>(recs + max(sl[j], 0) * C::kRecBytes);
@@ -259,7 +290,16 @@ __device__ void splat_consume(const TileJob& a, const SplatSmem<C>& sm, int warp
                     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(ex2) : "f"(p2));
                     const float alpha = fminf(kAlphaMax, axl.w * ex2);
                     al[j] = (sl[j] >= 0 && p2 <= 0.0f && alpha >= kAlphaMin) ? alpha : 0.0f;
-                    om[j] = one_minus_alpha(alpha, axl.w, p2);
+                    om[j] = 1.0f - al[j];
+                    p2s[j] = p2;
+                    os[j] = axl.w;
+                    high = high || al[j] > 0.5f;
+                }
+                // 1 - alpha without cancellation where some pixel of the warp has alpha > 1/2
+                // (rare: the plain difference is exact to within alpha's own error otherwise)
+                if (__any_sync(0xffffffffu, high)) {
+#pragma unroll
+                    for (int j = 0; j < kChunk; ++j) om[j] = one_minus_alpha(al[j], os[j], p2s[j]);
                 }
                 // (B) front-to-back transmittance (Eq. 3): e_j = alpha_j T_j, the serial part;
                 // al[j] becomes e_j (0 where the pixel skips or has terminated)
@@ -286,26 +326,24 @@ __device__ void splat_consume(const TileJob& a, const SplatSmem<C>& sm, int warp
                         const float* r = reinterpret_cast<const float*>(recs + sl[j] * C::kRecBytes);
                         const float* wr = r + 12;
                         const uint32_t* cw = reinterpret_cast<const uint32_t*>(r + 12 + C::kPairs);
-                        uint32_t cols[(C::kPairs + 3) / 4];
-#pragma unroll
-                        for (int q = 0; q < (C::kPairs + 3) / 4; ++q) cols[q] = cw[q];
                         float v[C::kPairs];
-                        int off[C::kPairs];
+                        float* addr[C::kPairs];
 #pragma unroll
                         for (int p = 0; p < C::kPairs; ++p) {
-                            off[p] = (int)__byte_perm(cols[p >> 2], 0u, 0x4440u | (uint32_t)(p & 3)) * 33 + lane;
-                            v[p] = acc[off[p]];
+                            addr[p] = reinterpret_cast<float*>(acc_lane + cw[p]);
+                            v[p] = *addr[p];
                         }
 #pragma unroll
                         for (int p = 0; p < C::kPairs; ++p) v[p] = fmaf(al[j], wr[p], v[p]);
 #pragma unroll
-                        for (int p = 0; p < C::kPairs; ++p) acc[off[p]] = v[p];
+                        for (int p = 0; p < C::kPairs; ++p) *addr[p] = v[p];
                     }
                 }
             }
         }
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(tc::smem_u32(sm.empty + s));
+        consumed = b + 1;
     }
 
     if (inside) {
@@ -329,61 +367,84 @@ __device__ void splat_consume(const TileJob& a, const SplatSmem<C>& sm, int warp
             }
         }
     }
+    return consumed;
 }
 
 }  // namespace
 
-// All threads of the CTA: kWarps consumer warps and the producer warp (the last one).
-template <int LEVELS, int K, int TW, int TH, int BATCH = 0>
-__device__ __forceinline__ void splat_tile(const TileJob& a, unsigned char* smem)
+// One tile by all threads of the CTA: kWarps consumer warps and the producer warp (the last
+// one).  Precondition: the CTA's barriers are initialised, no tile is in progress and every
+// thread is synchronised.  Returns the number of batches the tile used (the caller adds it to
+// bbase).
+template <int LEVELS, int K, int TW, int TH, int BATCH>
+__device__ __forceinline__ uint32_t splat_tile(const TileJob& a, const SplatSmem<SplatCfg<LEVELS, K, TW, TH, BATCH>>& sm,
+                                               uint32_t bbase)
 {
     using C = SplatCfg<LEVELS, K, TW, TH, BATCH>;
-    const SplatSmem<C> sm(smem);
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < C::kStages; ++s) {
-            tc::mbar_init(tc::smem_u32(sm.full + s), 32);
-            tc::mbar_init(tc::smem_u32(sm.empty + s), C::kWarps);
-        }
-        *sm.done_warps = 0;
-    }
-    __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t consumed = 0;
     if (warp == C::kWarps)
-        splat_produce<C>(a, sm, lane);
+        splat_produce<C>(a, sm, lane, bbase);
     else
-        splat_consume<C, LEVELS, K, TW, TH>(a, sm, warp, lane);
+        consumed = splat_consume<C, LEVELS, K, TW, TH>(a, sm, warp, lane, bbase);
+    __syncthreads();
+    const uint32_t issued = *sm.issued;
+    if (threadIdx.x == 0) *sm.done_warps = 0;
+    // Warps that stopped early release the stages of the batches they skipped (every one of
+    // them lies within the last kStages batches, whose predecessors all warps released), so
+    // each stage's barriers stay in step for the next tile.
+    if (warp < C::kWarps && lane == 0 && !*reinterpret_cast<volatile int*>(sm.abort))
+        for (uint32_t b = consumed; b < issued; ++b) tc::mbar_arrive(tc::smem_u32(sm.empty + (int)((bbase + b) % C::kStages)));
+    return issued;
 }
 
 template <int LEVELS, int K, int TW, int TH>
-__global__ void __launch_bounds__(TW* TH + 32) splat_kernel(SplatArgs a)
+__global__ void __launch_bounds__(TW* TH + 32, 1) splat_kernel(SplatArgs a)
 {
+    using C = SplatCfg<LEVELS, K, TW, TH, 0>;
     extern __shared__ __align__(16) unsigned char smem[];
+    const SplatSmem<C> sm(smem);
+    if (threadIdx.x == 0) {
+        sm.init();
+        // after a wait ran out anywhere, the remaining tiles are skipped
+        *sm.skip = a.status && *reinterpret_cast<volatile int32_t*>(a.status) == LSV2_ERR_TIMEOUT;
+    }
+    __syncthreads();
+    if (*sm.skip) return;
     const int tile = blockIdx.x;
     TileJob j{a.cam.width, a.cam.height, (a.cam.width + TW - 1) / TW, tile, a.tile_ranges[2 * tile],
               a.tile_ranges[2 * tile + 1], a.gauss_ids, a.recs, a.coeff, a.final_T, a.n_last, a.status};
-    splat_tile<LEVELS, K, TW, TH>(j, smem);
+    (void)splat_tile<LEVELS, K, TW, TH, 0>(j, sm, 0u);
 }
 
 // Persistent over the (view, tile) work items of several views: each CTA takes the next global
 // tile id from an atomic counter (largest views first, as they come first in the numbering).
 template <int LEVELS, int K, int TW, int TH, int BATCH>
-__global__ void __launch_bounds__(TW* TH + 32) splat_views_kernel(SplatViewsArgs a)
+__global__ void __launch_bounds__(TW* TH + 32, 1) splat_views_kernel(SplatViewsArgs a)
 {
+    using C = SplatCfg<LEVELS, K, TW, TH, BATCH>;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_tile;
+    const SplatSmem<C> sm(smem);
+    if (threadIdx.x == 0) sm.init();
+    uint32_t bbase = 0;
     while (true) {
-        if (threadIdx.x == 0) s_tile = (int)atomicAdd(a.queue, 1u);
+        if (threadIdx.x == 0) {
+            s_tile = (int)atomicAdd(a.queue, 1u);
+            *sm.skip = *sm.abort || (a.status && *reinterpret_cast<volatile int32_t*>(a.status) == LSV2_ERR_TIMEOUT);
+        }
         __syncthreads();
         const int tg = s_tile;
+        const bool stop = *sm.skip;
         __syncthreads();
-        if (tg >= a.total_tiles) break;
+        if (tg >= a.total_tiles || stop) break;
         int v = 0;
         while (v + 1 < a.V && tg >= a.view[v + 1].tile_base) ++v;
         const SplatView& w = a.view[v];
         TileJob j{w.width, w.height, w.GX, tg - w.tile_base, a.tile_ranges[2 * tg], a.tile_ranges[2 * tg + 1],
                   a.gauss_ids, a.recs + w.rec_off, a.coeff + w.coeff_off, a.final_T + w.pix_off,
                   a.n_last + w.pix_off, a.status};
-        splat_tile<LEVELS, K, TW, TH, BATCH>(j, smem);
+        bbase += splat_tile<LEVELS, K, TW, TH, BATCH>(j, sm, bbase);
     }
 }
 

@@ -8,17 +8,18 @@ namespace lsv2 {
 constexpr int kMaxPairs = 24;  // levels * K
 
 // Per-Gaussian splat record (global memory, 16-byte aligned), P = levels * K pairs:
-//   floats [0, 4)    u_hi, v_hi, u_lo, v_lo       2D mean as a float pair
-//   floats [4, 8)    c_hi, s_hi, A, B             principal frame (see eval_power2)
-//   floats [8, 12)   c_lo, s_lo, kappa, opacity
+//   floats [0, 4)     u_hi, v_hi, u_lo, v_lo       2D mean as a float pair
+//   floats [4, 8)     c_hi, s_hi, A, B             principal frame (see eval_power2)
+//   floats [8, 12)    c_lo, s_lo, kappa, opacity
 //   floats [12, 12+P) weights
-//   bytes after      P column indices (lev * 64 + idx)
-//   last 16 bytes    culling half-extents (ex, ey, 0, 0)
-// The part before the extents is what a warp stages in shared memory.  Repeated indices of one
-// level are merged into one pair; the emptied repeats (weight 0, same column) and any invalid
-// index (weight 0) are placed FIRST, so when a record's pairs are loaded together and then
-// stored in order, the pair carrying the weight is stored last and wins.
-__host__ __device__ constexpr int smem_record_bytes(int P) { return ((48 + 5 * P) + 15) / 16 * 16; }
+//   words [12+P, 12+2P) byte offset of each pair's accumulator column in the splat's shared
+//                     memory: (lev * 64 + idx) * 33 * 4 (a column spans 33 floats)
+//   last 16 bytes     culling half-extents (ex, ey, 0, 0)
+// Repeated indices of one level are merged into one pair; the emptied repeats (weight 0, same
+// column) and any invalid index (weight 0) are placed FIRST, so when a record's pairs are
+// loaded together and then stored in order, the pair carrying the weight is stored last and
+// wins.
+__host__ __device__ constexpr int smem_record_bytes(int P) { return ((48 + 8 * P) + 15) / 16 * 16; }
 __host__ __device__ constexpr int record_bytes(int P) { return smem_record_bytes(P) + 16; }
 
 // One CTA per tile: kWarps consumer warps (one pixel per lane, 32 pixels per warp) and one
