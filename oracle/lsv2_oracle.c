@@ -737,3 +737,86 @@ void orc_project64(const orc_camera* c, int64_t n, const double* means, const do
     for (int64_t g = 0; g < n; ++g)
         project_d(c, means + 3 * g, scales + 3 * g, quats + 4 * g, mean2d + 2 * g, conic + 3 * g, 0);
 }
+
+/* ======================================================================================
+ * 8. Post-processing of the relevancy maps M (paper appendix, "Evaluation Details").
+ *    Mean filter ("average pooling", Avg(M)): out(x, y) is the mean of M over the pixels of
+ *    the k x k window centred on (x, y) that lie inside the image (k odd; the paper gives no
+ *    window size or border rule).
+ *    mode 0 (LERF): S = Avg(M) per level; the selected level is the one whose S has the
+ *      highest value (lowest level on a tie); the localisation point is the first pixel in
+ *      row-major order where that level's S is maximal; the segmentation mask is
+ *      (S - min S) / (max S - min S) > thr on that level (0 everywhere when max = min).
+ *    mode 1 (3D-OVS, Mip-NeRF360): S = 0.5 (M + Avg(M)); each level's mask as above; the
+ *      selected level has the highest mean of S over its own mask (an empty mask counts as
+ *      -infinity; lowest level on a tie); point and mask as in mode 0.
+ *    rel [levels][H*W] one query; smoothed [levels][H*W]; point = (x, y); mask [H*W].
+ * ==================================================================================== */
+
+void orc_mean_filter(int32_t H, int32_t W, int32_t k, const double* in, double* out)
+{
+    const int32_t r = (k - 1) / 2;
+    for (int32_t y = 0; y < H; ++y)
+        for (int32_t x = 0; x < W; ++x) {
+            const int32_t y0 = y - r < 0 ? 0 : y - r, y1 = y + r > H - 1 ? H - 1 : y + r;
+            const int32_t x0 = x - r < 0 ? 0 : x - r, x1 = x + r > W - 1 ? W - 1 : x + r;
+            double sum = 0.0;
+            for (int32_t yy = y0; yy <= y1; ++yy)
+                for (int32_t xx = x0; xx <= x1; ++xx) sum += in[(size_t)yy * W + xx];
+            out[(size_t)y * W + x] = sum / (double)((y1 - y0 + 1) * (x1 - x0 + 1));
+        }
+}
+
+static void normalised_mask(int64_t P, const double* s, double thr, uint8_t* mask)
+{
+    double mx = -INFINITY, mn = INFINITY;
+    for (int64_t p = 0; p < P; ++p) {
+        if (s[p] > mx) mx = s[p];
+        if (s[p] < mn) mn = s[p];
+    }
+    for (int64_t p = 0; p < P; ++p) {
+        const double nrm = mx > mn ? (s[p] - mn) / (mx - mn) : 0.0;
+        mask[p] = nrm > thr ? 1 : 0;
+    }
+}
+
+void orc_postprocess(int32_t levels, int32_t H, int32_t W, const double* rel, int32_t k, int32_t mode,
+                     double thr, double* smoothed, int32_t* point, int32_t* level, double* score,
+                     uint8_t* mask)
+{
+    const int64_t P = (int64_t)H * W;
+    for (int32_t l = 0; l < levels; ++l) {
+        double* s = smoothed + (size_t)l * P;
+        orc_mean_filter(H, W, k, rel + (size_t)l * P, s);
+        if (mode == 1)
+            for (int64_t p = 0; p < P; ++p) s[p] = 0.5 * (rel[(size_t)l * P + p] + s[p]);
+    }
+    int32_t sel = 0;
+    double best = -INFINITY;
+    for (int32_t l = 0; l < levels; ++l) {
+        const double* s = smoothed + (size_t)l * P;
+        double crit;
+        if (mode == 0) {
+            crit = -INFINITY;
+            for (int64_t p = 0; p < P; ++p)
+                if (s[p] > crit) crit = s[p];
+        } else {
+            normalised_mask(P, s, thr, mask);
+            double sum = 0.0;
+            int64_t cnt = 0;
+            for (int64_t p = 0; p < P; ++p)
+                if (mask[p]) { sum += s[p]; ++cnt; }
+            crit = cnt > 0 ? sum / (double)cnt : -INFINITY;
+        }
+        if (l == 0 || crit > best) { best = crit; sel = l; }
+    }
+    const double* s = smoothed + (size_t)sel * P;
+    int64_t arg = 0;
+    for (int64_t p = 1; p < P; ++p)
+        if (s[p] > s[arg]) arg = p;
+    point[0] = (int32_t)(arg % W);
+    point[1] = (int32_t)(arg / W);
+    *level = sel;
+    *score = s[arg];
+    normalised_mask(P, s, thr, mask);
+}

@@ -12,6 +12,8 @@ Each function names the passage of the paper it follows (LangSplatV2, arXiv
   blend         Eq. 3 / Eq. 7 weights, Algorithm 1 sparse accumulation
   decode        Eq. 7, F = W S
   relevancy     Sec. 3.2 relevancy score (cosine + pairwise softmax, min over negatives)
+  mean_filter,  appendix "Evaluation Details": average pooling of the relevancy map,
+  postprocess   level selection, localisation point, normalise + threshold mask
   l1_grads      gradient of the L1 feature loss (decode adjoint as matmuls,
                 blend adjoint as the literal derivative, projection Jacobian by
                 complex step)
@@ -73,6 +75,8 @@ def lib():
         _lib.orc_l1_loss_tiles.argtypes = [P, I64, P, P, P, P, P, P, P, I32, I32, I32, I32, P, P,
                                            P, P, P, P]
         _lib.orc_l1_loss_tiles.restype = D
+        _lib.orc_mean_filter.argtypes = [I32, I32, I32, P, P]
+        _lib.orc_postprocess.argtypes = [I32, I32, I32, P, I32, I32, D, P, P, P, P, P]
     return _lib
 
 
@@ -244,6 +248,46 @@ def relevancy(F, text, tau: float = 10.0) -> np.ndarray:
     rel = np.zeros((Q, lev, npix))
     lib().orc_relevancy(lev, npix, D, _p(F), Q, nt - 1, _p(text), float(tau), _p(rel))
     return rel
+
+
+def mean_filter(M, k: int) -> np.ndarray:
+    """Appendix "Evaluation Details", Avg(M): mean over the in-image part of the k x k window
+    centred on each pixel (k odd). M [H, W] -> [H, W] (FP64)."""
+    M = np.ascontiguousarray(M, np.float64)
+    H, W = M.shape
+    out = np.zeros((H, W))
+    lib().orc_mean_filter(H, W, int(k), _p(M), _p(out))
+    return out
+
+
+@dataclass
+class Post:
+    smoothed: np.ndarray   # f64 [Q, levels, H*W]
+    point: np.ndarray      # i32 [Q, 2] (x, y)
+    level: np.ndarray      # i32 [Q]
+    score: np.ndarray      # f64 [Q]
+    mask: np.ndarray       # u8 [Q, H*W]
+
+
+def postprocess(rel, H: int, W: int, k: int, mode: int = 0, thr: float = 0.5) -> Post:
+    """Appendix "Evaluation Details" post-processing of relevancy maps rel [Q, levels, H*W]:
+    mode 0 = LERF (Avg(M), level of the highest value), mode 1 = 3D-OVS / Mip-NeRF360
+    (0.5 (M + Avg(M)), level of the highest mean inside its mask)."""
+    rel = np.ascontiguousarray(rel, np.float64)
+    Q, levels, P = rel.shape
+    assert P == H * W
+    out = Post(np.zeros((Q, levels, P)), np.zeros((Q, 2), np.int32), np.zeros(Q, np.int32),
+               np.zeros(Q), np.zeros((Q, P), np.uint8))
+    for q in range(Q):
+        pt = np.zeros(2, np.int32)
+        lv = np.zeros(1, np.int32)
+        sc = np.zeros(1)
+        sm = np.zeros((levels, P))
+        mk = np.zeros(P, np.uint8)
+        lib().orc_postprocess(levels, H, W, _p(np.ascontiguousarray(rel[q])), int(k), int(mode), float(thr),
+                              _p(sm), _p(pt), _p(lv), _p(sc), _p(mk))
+        out.smoothed[q], out.point[q], out.level[q], out.score[q], out.mask[q] = sm, pt, lv[0], sc[0], mk
+    return out
 
 
 @dataclass

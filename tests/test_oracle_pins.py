@@ -420,3 +420,101 @@ def test_decode_adjoint_fd():
         Sm[0, j, d] -= h
         fd = (loss_terms(Sp) - loss_terms(Sm)).sum() / (2 * h) / W.shape[1] / 16
         assert fd == pytest.approx(g.dS[0, j, d], rel=1e-5, abs=1e-12)
+
+
+# ----------------------------------------------------------------------------- post-processing
+
+@pytest.mark.parametrize("k,H,W", [(1, 7, 9), (3, 13, 11), (7, 20, 17), (15, 9, 33)])
+def test_mean_filter_is_border_normalised_uniform_filter(k, H, W):
+    """Avg(M) (appendix "Evaluation Details") = scipy's zero-padded k x k mean divided by the same
+    mean of an all-ones image: the mean over the in-image part of the window."""
+    ndimage = pytest.importorskip("scipy.ndimage")
+    M = np.random.default_rng(k * 100 + H).random((H, W))
+    ref = (ndimage.uniform_filter(M, size=k, mode="constant", cval=0.0)
+           / ndimage.uniform_filter(np.ones((H, W)), size=k, mode="constant", cval=0.0))
+    assert np.allclose(O.mean_filter(M, k), ref, rtol=1e-12, atol=1e-14)
+
+
+def test_mean_filter_of_a_ramp_closed_form():
+    """A linear ramp M(x, y) = a x + b y + c: the mean over the clipped window [x0, x1] x [y0, y1]
+    is a (x0 + x1)/2 + b (y0 + y1)/2 + c, so it stays a x + b y + c away from the border and is
+    pulled inwards by the clipping at the border."""
+    H, W, k = 10, 14, 5
+    r = (k - 1) // 2
+    y, x = np.mgrid[0:H, 0:W].astype(np.float64)
+    a, b, c = 0.25, -0.5, 3.0
+    out = O.mean_filter(a * x + b * y + c, k)
+    x0, x1 = np.maximum(x - r, 0), np.minimum(x + r, W - 1)
+    y0, y1 = np.maximum(y - r, 0), np.minimum(y + r, H - 1)
+    assert np.allclose(out, a * (x0 + x1) / 2 + b * (y0 + y1) / 2 + c, atol=1e-12)
+    inner = (slice(r, H - r), slice(r, W - r))
+    assert np.allclose(out[inner], (a * x + b * y + c)[inner], atol=1e-12)
+
+
+def test_mean_filter_impulse():
+    """One impulse of height 1: every pixel within the window's reach gets 1 / (its window's
+    in-image pixel count); the corner pixel (0, 0) of a 3 x 3 window sees 4 pixels."""
+    M = np.zeros((6, 6))
+    M[0, 0] = 1.0
+    out = O.mean_filter(M, 3)
+    assert out[0, 0] == pytest.approx(1 / 4)
+    assert out[1, 1] == pytest.approx(1 / 9)
+    assert out[0, 1] == pytest.approx(1 / 6)
+    assert out[2, 2] == 0.0
+
+
+def test_postprocess_ramp_mask_and_point_closed_form():
+    """k = 1 (no smoothing) on a ramp M = x / (W - 1) in every row: the normalised map is the
+    ramp itself, the mask is the columns with x / (W - 1) > thr, and the point is the first
+    pixel of the last column (row 0)."""
+    H, W, thr = 5, 21, 0.3
+    ramp = np.tile(np.arange(W) / (W - 1), (H, 1)).reshape(1, 1, -1)
+    r = O.postprocess(ramp, H, W, k=1, mode=0, thr=thr)
+    assert tuple(r.point[0]) == (W - 1, 0) and r.level[0] == 0 and r.score[0] == 1.0
+    cols = np.arange(W) / (W - 1) > thr
+    assert np.array_equal(r.mask[0].reshape(H, W), np.tile(cols, (H, 1)).astype(np.uint8))
+    assert r.mask[0].sum() == H * int(np.sum(cols))
+
+
+def _blob(H, W, cx, cy, sigma, peak, base):
+    y, x = np.mgrid[0:H, 0:W].astype(np.float64)
+    return base + (peak - base) * np.exp(-((x - cx) ** 2 + (y - cy) ** 2) / (2 * sigma ** 2))
+
+
+def test_postprocess_level_rules_differ_as_the_appendix_says():
+    """LERF picks the level with the highest relevancy value; 3D-OVS / Mip-NeRF360 pick the level
+    with the highest mean inside its own mask.  Level 0 has a tall single-pixel spike (0.9) on a
+    broad plateau (0.6 over most of the image), level 1 a broad blob up to 0.8 on 0.1: LERF
+    takes level 0 (0.9 > 0.8); the mask rule takes level 1 (its masked mean ~0.7 > level 0's,
+    whose mask is the plateau at ~0.6).  With k = 1 both modes see S = M."""
+    H, W = 24, 32
+    lev0 = np.full((H, W), 0.6)
+    lev0[:, :4] = 0.0
+    lev0[5, 20] = 0.9
+    lev1 = _blob(H, W, 10.0, 12.0, 4.0, 0.8, 0.1)
+    rel = np.stack([lev0.reshape(-1), lev1.reshape(-1)])[None]
+    lerf = O.postprocess(rel, H, W, k=1, mode=0, thr=0.5)
+    assert lerf.level[0] == 0 and tuple(lerf.point[0]) == (20, 5) and lerf.score[0] == 0.9
+    ovs = O.postprocess(rel, H, W, k=1, mode=1, thr=0.5)
+    assert ovs.level[0] == 1 and tuple(ovs.point[0]) == (10, 12)
+    m1 = lev1 > 0.1 + 0.5 * (0.8 - 0.1)
+    assert np.array_equal(ovs.mask[0].reshape(H, W), m1.astype(np.uint8))
+    # mode 1 smooths as 0.5 (M + Avg(M)): with k = 3 the spike drops to 0.5 (0.9 + mean)
+    ovs3 = O.postprocess(rel, H, W, k=3, mode=1, thr=0.5)
+    spike_avg = (0.9 + 8 * 0.6) / 9
+    assert ovs3.smoothed[0, 0, 5 * W + 20] == pytest.approx(0.5 * (0.9 + spike_avg))
+
+
+def test_postprocess_ties_take_lowest_level_and_first_pixel():
+    """Two levels with identical maps and two equal maxima: level 0 and the first maximum in
+    row-major order; an exactly constant map normalises to 0 everywhere (empty mask).  (Smoothing
+    a constant map can leave one-ulp differences, which min-max normalisation then amplifies, so
+    the constant case is taken unsmoothed.)"""
+    H, W = 6, 8
+    M = np.zeros((H, W))
+    M[4, 1] = M[2, 6] = 1.0
+    rel = np.stack([M.reshape(-1)] * 2)[None]
+    r = O.postprocess(rel, H, W, k=1, mode=0, thr=0.5)
+    assert r.level[0] == 0 and tuple(r.point[0]) == (6, 2)
+    flat = O.postprocess(np.full((1, 1, H * W), 0.7), H, W, k=1, mode=0, thr=0.5)
+    assert flat.mask.sum() == 0 and flat.score[0] == pytest.approx(0.7)
