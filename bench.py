@@ -34,6 +34,11 @@ FALLBACK_PEAKS = {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustain
 FP32_ALU_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 
 
+# relevancy post-processing in the timed step: mean-filter window and mask threshold (the paper
+# gives neither)
+POST_WINDOW = 29
+POST_THRESHOLD = 0.5
+
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
 # this workload with the kernels as they are now; an entry is removed when its kernel changes.
 TRAFFIC = {
@@ -254,11 +259,17 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
-    stages = ["project", "bin_sort", "splat", "decode", "query"]
+    from paper_2507_07136_b300.pipeline import PostResult
+    post_out = PostResult(text.shape[0], levels, cam.height, cam.width, dev)
+    stages = ["project", "bin_sort", "splat", "decode", "query", "post"]
     fns = {"project": frame.project, "bin_sort": frame.bin_sort, "splat": frame.splat,
            "decode": lambda: frame.decode(F, codebook=cb16),
-           "query": lambda: frame.query(text_d, rel, compute=Lb.LSV2_BF16)}
-    launches_per_step = {"project": 1, "bin_sort": 5, "splat": 2, "decode": 1, "query": 2}  # prepare + query
+           "query": lambda: frame.query(text_d, rel, compute=Lb.LSV2_BF16),
+           "post": lambda: frame.postprocess(rel, k=POST_WINDOW, mode=Lb.LSV2_POST_LERF, threshold=POST_THRESHOLD,
+                                             out=post_out)}
+    # kernels per stage: project; hist/column/scan/scatter/sort (bin); pack + splat; decode;
+    # prepare + query; init + box filter + select + mask (post)
+    launches_per_step = {"project": 1, "bin_sort": 5, "splat": 2, "decode": 1, "query": 2, "post": 4}
 
     def step(ev=None):
         for i, s in enumerate(stages):
@@ -358,11 +369,14 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic",
             "config": {"workload": "300k Gaussians, 3 levels, K=4, L=64, D=512, 1440x1080, 1 query + 4 negatives",
                        "path": "FP32 projection and splat; BF16 tensor-core decode to a BF16 feature map and "
-                               "BF16 tensor-core relevancy (FP32 accumulation)", "parallelism": f"replicas x{world}",
+                               "BF16 tensor-core relevancy (FP32 accumulation); post-processing (LERF rule, "
+                               f"{POST_WINDOW}x{POST_WINDOW} mean filter, level, point, mask at {POST_THRESHOLD})",
+                       "parallelism": f"replicas x{world}",
                        "l2": "flushed between steps (256 MiB write, untimed)", "instances": inst},
             "stages_ms": stage_ms,
             "splat_decode_fps": 1e3 / (stage_ms["project"] + stage_ms["bin_sort"] + stage_ms["splat"] + stage_ms["decode"]),
-            "query_fps": 1e3 / (stage_ms["project"] + stage_ms["bin_sort"] + stage_ms["splat"] + stage_ms["query"]),
+            "query_fps": 1e3 / (stage_ms["project"] + stage_ms["bin_sort"] + stage_ms["splat"] + stage_ms["query"]
+                                + stage_ms["post"]),
             "roofline": dict(roofs[dom]),
             "rooflines": roofs,
             "fp32_path": fp32,

@@ -16,6 +16,8 @@
  *   lsv2_query         relevancy of each pixel for text queries (Sec. 3.2), computed through
  *                      the linearity of Eq. 7 without materialising F
  *   lsv2_query_views   all of the above for many views and queries in one call
+ *   lsv2_postprocess   mean filter, level selection, localisation point and segmentation mask
+ *                      of relevancy maps (appendix "Evaluation Details")
  *   lsv2_splat_backward, lsv2_l1_decode_backward
  *                      gradients of an L1 feature loss (no counterpart in the paper, which
  *                      trains the field but does not describe its gradient)
@@ -59,6 +61,10 @@ typedef enum {
 } lsv2_status;
 
 typedef enum { LSV2_F32 = 0, LSV2_BF16 = 1 } lsv2_dtype;
+
+/* Post-processing rule (appendix "Evaluation Details"): LERF, or the blended map and masked-mean
+ * level rule of the 3D-OVS and Mip-NeRF360 evaluations. */
+typedef enum { LSV2_POST_LERF = 0, LSV2_POST_BLENDED = 1 } lsv2_post_mode;
 
 /* Pinhole camera.  World -> camera: t = R m + t0 (x right, y down, z forward).
  * Supported tiles: 16x16 (default), 8x8, 32x8. */
@@ -225,8 +231,8 @@ size_t lsv2_query_views_workspace_bytes(int32_t V, const lsv2_camera* cams, int6
  *   means..w as for lsv2_project / lsv2_splat_coeffs (device); codebook float[levels][64][D]
  *   text     float[Q][1 + n_neg][D]; tau as for lsv2_query
  *   capacity instance capacity over all views (LSV2_ERR_CAPACITY in *dev_status if exceeded)
- *   stage_batch  Gaussian records a warp stages in shared memory at a time: 16, 32 or 0 (the
- *            largest that fits); tuned together with the tile shape
+ *   stage_batch  Gaussian records per stage of the splat's shared-memory ring (gathered by one
+ *            producer warp per tile): 16, 32 or 0 (= 32); tuned together with the tile shape
  *   rel      views concatenated, view v: [Q][levels][H_v W_v], dtype rel_dtype (F32 or BF16)
  *   dev_num_instances  int64 (device): total instances over all views
  * Everything is stream-ordered with no host synchronisation (capturable in a CUDA graph).
@@ -238,6 +244,34 @@ lsv2_status lsv2_query_views(int32_t V, const lsv2_camera* cams, int64_t n, cons
                              int32_t n_neg, const float* text, float tau, int64_t capacity,
                              int32_t stage_batch, void* workspace, size_t workspace_bytes, void* rel,
                              lsv2_dtype rel_dtype, int64_t* dev_num_instances,
+                             int32_t* dev_status, void* stream);
+
+/* Workspace for lsv2_postprocess: per (query, level) statistics (Q * levels * 32 bytes,
+ * rounded up to 256).  0 for invalid sizes. */
+size_t lsv2_postprocess_workspace_bytes(int32_t Q, int32_t levels);
+
+/* Post-processing of relevancy maps (paper appendix, "Evaluation Details"; Sec. 3.2 on running
+ * it on the GPU).  For each query q and level l, with M the map rel[q][l] (H x W, row-major):
+ *   Avg(M)  mean over the in-image part of the k x k window centred on each pixel (k odd)
+ *   S       mode LSV2_POST_LERF: Avg(M);  mode LSV2_POST_BLENDED: 0.5 (M + Avg(M))
+ *   mask_l  (S - min S) / (max S - min S) > threshold (all 0 when max S = min S)
+ *   level   LERF: the level whose S has the highest value; BLENDED: the level with the highest
+ *           mean of S over mask_l (an empty mask ranks lowest); the lowest level on a tie
+ *   point   (x, y) of the first pixel in row-major order where S of the selected level is
+ *           maximal; score = that maximum
+ * Arguments:
+ *   rel        [Q][levels][H*W], dtype rel_dtype (F32 or BF16), e.g. the output of lsv2_query
+ *   k          window, odd, 1..63;  threshold in [0, 1]
+ *   workspace  lsv2_postprocess_workspace_bytes(Q, levels) bytes, 16-byte aligned
+ *   smoothed   float[Q][levels][H*W] (written: S of every level)
+ *   point      int32[Q][2], level int32[Q], score float[Q] (written)
+ *   mask       uint8[Q][H*W]: mask of the selected level (written), or NULL to skip it
+ * Supported: levels <= 8, H * W < 2^32.  dev_status is unused (no device-detected condition).
+ * Stream-ordered, no host synchronisation (capturable in a CUDA graph). */
+lsv2_status lsv2_postprocess(int32_t Q, int32_t levels, int32_t H, int32_t W, const void* rel,
+                             lsv2_dtype rel_dtype, int32_t k, int32_t mode, float threshold,
+                             void* workspace, size_t workspace_bytes, float* smoothed,
+                             int32_t* point, int32_t* level, float* score, uint8_t* mask,
                              int32_t* dev_status, void* stream);
 
 /* Backward of Loss = mean_{lev,p,d} |F - target| with F = W S (decode + L1 adjoint).

@@ -14,7 +14,7 @@ pairs per Gaussian and semantic level over an L=64 codebook of D=512-d unit
 features (Sec. 3.3, Eq. 5; Sec. 4.1 sets L=64, K=4, three levels), and unit
 512-d text embeddings for the relevancy query (Sec. 3.2).
 
-Seeds: 20250707 scene, +1 codebook, +2 text, +3 L1 target, +4 batched scene.
+Seeds: 20250707 scene, +1 codebook, +2 text, +3 L1 target, +4 batched scene, +5 relevancy maps.
 """
 from __future__ import annotations
 
@@ -238,3 +238,22 @@ def batched(tile=(16, 16)):
             for k, (w, h) in enumerate(BATCH_RESOLUTIONS)]
     text = text_queries(SEED + 2, 64, 4)
     return sc, cams, text
+
+
+def relevancy_maps(seed: int, Q: int, levels: int, H: int, W: int, blobs: int = 6) -> np.ndarray:
+    """Relevancy-like maps for the post-processing stage, float32 [Q, levels, H*W] in (0, 1): a
+    few random Gaussian bumps of random height and width over a low noisy background per map
+    (relevancy maps of a text query are mostly low with a few high regions).  Seed: +5."""
+    rng = _rng(seed)
+    y, x = np.mgrid[0:H, 0:W].astype(np.float64)
+    out = np.empty((Q, levels, H * W), np.float32)
+    for q in range(Q):
+        for l in range(levels):
+            m = 0.15 + 0.05 * rng.random((H, W))
+            for _ in range(blobs):
+                cx, cy = rng.uniform(0, W), rng.uniform(0, H)
+                s = rng.uniform(1.5, 0.25 * max(H, W) + 2.0)
+                h = rng.uniform(0.1, 0.8)
+                m += h * np.exp(-((x - cx) ** 2 + (y - cy) ** 2) / (2 * s * s))
+            out[q, l] = (m / (1.0 + m)).reshape(-1)
+    return out

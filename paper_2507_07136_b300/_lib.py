@@ -15,6 +15,8 @@ I32, I64, F32, SZ = C.c_int32, C.c_int64, C.c_float, C.c_size_t
 
 LSV2_F32 = 0
 LSV2_BF16 = 1
+LSV2_POST_LERF = 0
+LSV2_POST_BLENDED = 1
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported configuration", 3: "instance capacity exceeded",
           4: "CUDA error", 5: "device wait timed out", 6: "non-finite value"}
@@ -51,6 +53,8 @@ _SIGS = {
     "lsv2_query_views_workspace_bytes": ([I32, P, I64, I32, I32, I64, I32, I32], SZ),
     "lsv2_query_views": ([I32, P, I64, P, P, P, P, I32, I32, I32, P, P, P, I32, I32, I32, P, F32, I64, I32, P, SZ, P,
                           I32, P, P, P], I32),
+    "lsv2_postprocess_workspace_bytes": ([I32, I32], SZ),
+    "lsv2_postprocess": ([I32, I32, I32, I32, P, I32, I32, I32, F32, P, SZ, P, P, P, P, P, P, P], I32),
     "lsv2_l1_decode_backward": ([I32, I64, I32, I32, P, P, P, P, P, P, P], I32),
     "lsv2_splat_backward_workspace_bytes": ([I64], SZ),
     "lsv2_splat_backward": ([P, I64, P, P, P, P, P, P, I32, I32, I32, P, P, P, P, P, P, SZ, P, P, P, P, P, P, P],
@@ -172,3 +176,13 @@ def lsv2_splat_backward(cam, n, means, scales, quats, proj, tile_ranges, gauss_i
     call("lsv2_splat_backward", C.byref(cam), n, means, scales, quats, C.byref(proj), tile_ranges, gauss_ids,
          levels, K, L, idx, w, final_T, n_last, dcoeff, ws, ws_bytes, dw, dopacity, dmeans, dscales, dquats,
          dev_status, stream)
+
+
+def lsv2_postprocess_workspace_bytes(Q, levels) -> int:
+    return lib().lsv2_postprocess_workspace_bytes(Q, levels)
+
+
+def lsv2_postprocess(Q, levels, H, W, rel, rel_dtype, k, mode, threshold, ws, ws_bytes, smoothed, point, level, score,
+                     mask, dev_status, stream):
+    call("lsv2_postprocess", Q, levels, H, W, rel, rel_dtype, k, mode, threshold, ws, ws_bytes, smoothed, point, level,
+         score, mask, dev_status, stream)

@@ -142,9 +142,46 @@ class Frame:
                      Q, nt - 1, _ptr(text), float(tau), _ptr(self.query_ws), need, _ptr(out), out_dt, compute,
                      _ptr(self.status), _stream(stream))
 
+    def postprocess(self, rel: torch.Tensor, k: int = 29, mode: int = L.LSV2_POST_LERF, threshold: float = 0.5,
+                    out: "PostResult | None" = None, with_mask: bool = True, stream=None) -> "PostResult":
+        """Mean filter, level selection, localisation point and mask of relevancy maps rel [Q, levels, P]
+        (lsv2_postprocess)."""
+        return postprocess(rel, self.cam.height, self.cam.width, k, mode, threshold, out, with_mask, self.status,
+                           stream)
+
     def check(self):
         """Synchronise and raise if a kernel reported a device-side condition."""
         torch.cuda.synchronize()
         code = int(self.status.item())
         if code != 0:
             raise L.LSV2Error("device status", code)
+
+
+class PostResult:
+    """Buffers written by lsv2_postprocess for Q queries over `levels` maps of H x W pixels."""
+
+    def __init__(self, Q: int, levels: int, H: int, W: int, device, with_mask: bool = True):
+        self.Q, self.levels, self.H, self.W = Q, levels, H, W
+        self.smoothed = torch.empty((Q, levels, H * W), dtype=torch.float32, device=device)
+        self.point = torch.empty((Q, 2), dtype=torch.int32, device=device)
+        self.level = torch.empty(Q, dtype=torch.int32, device=device)
+        self.score = torch.empty(Q, dtype=torch.float32, device=device)
+        self.mask = torch.empty((Q, H * W), dtype=torch.uint8, device=device) if with_mask else None
+        self.ws_bytes = L.lsv2_postprocess_workspace_bytes(Q, levels)
+        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=device)
+
+
+def postprocess(rel: torch.Tensor, H: int, W: int, k: int = 29, mode: int = L.LSV2_POST_LERF, threshold: float = 0.5,
+                out: PostResult | None = None, with_mask: bool = True, dev_status: torch.Tensor | None = None,
+                stream=None) -> PostResult:
+    """lsv2_postprocess over relevancy maps rel [Q, levels, H*W] (F32 or BF16, on the GPU)."""
+    Q, levels, P = rel.shape
+    assert P == H * W and rel.is_contiguous()
+    if out is None:
+        out = PostResult(Q, levels, H, W, rel.device, with_mask)
+    rel_dt = L.LSV2_BF16 if rel.dtype == torch.bfloat16 else L.LSV2_F32
+    L.lsv2_postprocess(Q, levels, H, W, _ptr(rel), rel_dt, int(k), int(mode), float(threshold), _ptr(out.ws),
+                       out.ws_bytes, _ptr(out.smoothed), _ptr(out.point), _ptr(out.level), _ptr(out.score),
+                       _ptr(out.mask) if out.mask is not None else None,
+                       _ptr(dev_status) if dev_status is not None else None, _stream(stream))
+    return out
