@@ -16,6 +16,7 @@
  *   lsv2_query         relevancy of each pixel for text queries (Sec. 3.2), computed through
  *                      the linearity of Eq. 7 without materialising F
  *   lsv2_query_views   all of the above for many views and queries in one call
+ *   lsv2_render_fused  splat + decode + query of one frame in one kernel (W stays on chip)
  *   lsv2_postprocess   mean filter, level selection, localisation point and segmentation mask
  *                      of relevancy maps (appendix "Evaluation Details")
  *   lsv2_splat_backward, lsv2_l1_decode_backward
@@ -207,8 +208,8 @@ size_t lsv2_query_workspace_bytes(int32_t levels, int32_t L, int32_t Q, int32_t 
  *   rel      [Q][levels][P]  dtype rel_dtype (F32 or BF16)
  * compute_dtype F32: FP32 FMA on CUDA cores (rel_dtype F32).  BF16: tcgen05 tensor cores with
  * W and [G | u] rounded to BF16 and FP32 accumulation.  S S^T and S t are formed per call with
- * FP64 accumulation.  L = 64, D % 4 == 0, n_neg >= 1, Q (1 + n_neg) <= 448 for BF16, <= 512 for
- * F32.  All arrays 16-byte aligned.
+ * FP64 accumulation.  L = 64, D % 4 == 0, n_neg >= 1; BF16: 64 + (1 + n_neg) * 8 * ceil(Q / 8)
+ * <= 512 (Q <= 88 at n_neg = 4); F32: Q (1 + n_neg) <= 512.  All arrays 16-byte aligned.
  * A bounded device wait that expires sets LSV2_ERR_TIMEOUT. */
 lsv2_status lsv2_query(int32_t levels, int64_t P, int32_t L, int32_t D, const void* coeff,
                        lsv2_dtype coeff_dtype, const float* codebook, int32_t Q, int32_t n_neg,
@@ -236,7 +237,8 @@ size_t lsv2_query_views_workspace_bytes(int32_t V, const lsv2_camera* cams, int6
  *   rel      views concatenated, view v: [Q][levels][H_v W_v], dtype rel_dtype (F32 or BF16)
  *   dev_num_instances  int64 (device): total instances over all views
  * Everything is stream-ordered with no host synchronisation (capturable in a CUDA graph).
- * Supported: V <= 64, K = 4, L = 64, Q (1 + n_neg) <= 448, workspace 256-byte aligned. */
+ * Supported: V <= 64, K = 4, L = 64, 64 + (1 + n_neg) * 8 * ceil(Q / 8) <= 512, workspace 256-byte
+ * aligned. */
 lsv2_status lsv2_query_views(int32_t V, const lsv2_camera* cams, int64_t n, const float* means,
                              const float* scales, const float* quats, const float* opacity,
                              int32_t levels, int32_t K, int32_t L, const uint8_t* idx,
@@ -245,6 +247,33 @@ lsv2_status lsv2_query_views(int32_t V, const lsv2_camera* cams, int64_t n, cons
                              int32_t stage_batch, void* workspace, size_t workspace_bytes, void* rel,
                              lsv2_dtype rel_dtype, int64_t* dev_num_instances,
                              int32_t* dev_status, void* stream);
+
+/* Workspace for lsv2_render_fused (per-Gaussian records, the BF16 codebook and query operands).
+ * 0 for an unsupported configuration. */
+size_t lsv2_render_fused_workspace_bytes(int64_t n, int32_t levels, int32_t K, int32_t D, int32_t Q,
+                                         int32_t n_neg);
+
+/* The splat of lsv2_splat_coeffs (Sec. 3.4, Algorithm 1), the decode of lsv2_decode (Eq. 7,
+ * BF16 operands and output, FP32 accumulation) and the relevancy of lsv2_query (Sec. 3.2 through
+ * Eq. 7, BF16 compute) in one kernel per tile: the coefficient map W stays in shared memory and
+ * tensor memory and is never written to HBM.  F and rel equal what lsv2_splat_coeffs followed by
+ * lsv2_decode (BF16) and lsv2_query (BF16 compute) produce.
+ *   cam, n, proj, tile_ranges, gauss_ids, idx, w   as for lsv2_splat_coeffs (tile 16 x 16)
+ *   codebook  float[levels][64][D], D a multiple of 128, <= 512
+ *   Q, n_neg, text, tau   as for lsv2_query; Q = 0: no relevancy
+ *   feat      BF16 [levels][P][D] (16-byte aligned), or NULL to skip the decode
+ *   rel       [Q][levels][P], dtype rel_dtype (F32 or BF16); unused when Q = 0
+ *   final_T, n_last   as for lsv2_splat_coeffs
+ *   workspace lsv2_render_fused_workspace_bytes(...) bytes, 256-byte aligned
+ * Supported: levels = 3, K = 4, L = 64, 64 + (1 + n_neg) * 8 * ceil(Q / 8) <= 256.  At least one of
+ * feat and Q > 0.  A bounded device wait that expires sets LSV2_ERR_TIMEOUT. */
+lsv2_status lsv2_render_fused(const lsv2_camera* cam, int64_t n, const lsv2_proj* proj,
+                              const uint32_t* tile_ranges, const uint32_t* gauss_ids, int32_t levels,
+                              int32_t K, int32_t L, const uint8_t* idx, const float* w,
+                              const float* codebook, int32_t D, int32_t Q, int32_t n_neg,
+                              const float* text, float tau, void* workspace, size_t workspace_bytes,
+                              void* feat, void* rel, lsv2_dtype rel_dtype, float* final_T,
+                              uint32_t* n_last, int32_t* dev_status, void* stream);
 
 /* Workspace for lsv2_postprocess: per (query, level) statistics (Q * levels * 32 bytes,
  * rounded up to 256).  0 for invalid sizes. */

@@ -53,6 +53,9 @@ _SIGS = {
     "lsv2_query_views_workspace_bytes": ([I32, P, I64, I32, I32, I64, I32, I32], SZ),
     "lsv2_query_views": ([I32, P, I64, P, P, P, P, I32, I32, I32, P, P, P, I32, I32, I32, P, F32, I64, I32, P, SZ, P,
                           I32, P, P, P], I32),
+    "lsv2_render_fused_workspace_bytes": ([I64, I32, I32, I32, I32, I32], SZ),
+    "lsv2_render_fused": ([P, I64, P, P, P, I32, I32, I32, P, P, P, I32, I32, I32, P, F32, P, SZ, P, P, I32, P, P, P, P],
+                          I32),
     "lsv2_postprocess_workspace_bytes": ([I32, I32], SZ),
     "lsv2_postprocess": ([I32, I32, I32, I32, P, I32, I32, I32, F32, P, SZ, P, P, P, P, P, P, P], I32),
     "lsv2_l1_decode_backward": ([I32, I64, I32, I32, P, P, P, P, P, P, P], I32),
@@ -186,3 +189,13 @@ def lsv2_postprocess(Q, levels, H, W, rel, rel_dtype, k, mode, threshold, ws, ws
                      mask, dev_status, stream):
     call("lsv2_postprocess", Q, levels, H, W, rel, rel_dtype, k, mode, threshold, ws, ws_bytes, smoothed, point, level,
          score, mask, dev_status, stream)
+
+
+def lsv2_render_fused_workspace_bytes(n, levels, K, D, Q, n_neg) -> int:
+    return lib().lsv2_render_fused_workspace_bytes(n, levels, K, D, Q, n_neg)
+
+
+def lsv2_render_fused(cam, n, proj, tile_ranges, gauss_ids, levels, K, L, idx, w, codebook, D, Q, n_neg, text, tau, ws,
+                      ws_bytes, feat, rel, rel_dtype, final_T, n_last, dev_status, stream):
+    call("lsv2_render_fused", C.byref(cam), n, C.byref(proj), tile_ranges, gauss_ids, levels, K, L, idx, w, codebook, D,
+         Q, n_neg, text, tau, ws, ws_bytes, feat, rel, rel_dtype, final_T, n_last, dev_status, stream)

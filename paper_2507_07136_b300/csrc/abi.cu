@@ -192,7 +192,7 @@ lsv2_status lsv2_query(int32_t levels, int64_t P, int32_t L, int32_t D, const vo
         return cuda_status(launch_query_f32(levels, P, Q, n_neg, tau, static_cast<const float*>(coeff), workspace,
                                             static_cast<float*>(rel), S(stream)));
     if (compute_dtype == LSV2_BF16) {
-        if (!query_tc_supported(nt)) return LSV2_ERR_UNSUPPORTED;
+        if (!query_tc_supported(Q, n_neg)) return LSV2_ERR_UNSUPPORTED;
         return cuda_status(launch_query_tc(levels, P, Q, n_neg, tau, static_cast<const float*>(coeff),
                                            query_ws_bt(workspace), query_ws_tnorm(workspace, levels, nt), rel,
                                            rel_dtype == LSV2_BF16, sm_count(), dev_status, S(stream)));

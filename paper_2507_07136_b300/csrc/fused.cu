@@ -1,0 +1,592 @@
+// fused.cu -- one frame's sparse-coefficient splat (Sec. 3.4, Algorithm 1), decode F = W S
+// (Eq. 7) and relevancy (Sec. 3.2 through Eq. 7) in one kernel: the coefficient map W never
+// leaves the SM.
+//
+// One CTA per 16x16 tile: 8 consumer warps and one producer warp, as in the plain splat
+// (splat_core.cuh).  After the splat each consumer warp holds the FP32 coefficients of its 32
+// pixels in shared-memory columns.  Then, per CTA:
+//  1. Transit: every thread stores its pixel's 3 x 64 coefficients, rounded to BF16, into its
+//     TMEM lane (tcgen05.st; lane = pixel row of a 128-pixel M tile), which frees the
+//     accumulator memory; after a barrier it reads them back (tcgen05.ld) and writes the
+//     128-byte-swizzled K-major A tiles (one per level and 128-pixel half) into that memory.
+//  2. The producer warp streams the codebook S_lev^T in 16 KB chunks (128 rows of the
+//     pre-swizzled BF16 copy) through a 3-slot ring with bulk async copies, and the query
+//     matrices [S S^T | S t ...] (text-major rows, as in query_tc.cu; all three levels at once
+//     when they fit in 32 KB, else one level at a time); its lane 0
+//     issues the tcgen05.mma: per level, Y = W [S S^T | S t] (M = 128, N = npadq) into TMEM
+//     columns [256, 256 + npadq), then F chunks of 128 features (M = 128, N = 128, K = 64) into
+//     two TMEM buffers [0, 128) and [128, 256) that alternate, each committed to an mbarrier.
+//  3. The consumer warps run the epilogues in the same order: relevancy as in query_tc.cu
+//     (|F|^2 = W . (S S^T W), sigmoid of the scaled cosine gap), and F chunks converted to BF16,
+//     staged per warp in shared memory (32 rows x 128 bytes) and written with coalesced
+//     512-byte warp stores (4 pixels' 128-byte segments per store).
+// The operands and the MMA sequence (K = 64 in four steps of 16) are those of decode_tc.cu and
+// query_tc.cu, so F and the relevancy equal those kernels' results on the splat's W.  Every wait
+// is time-bounded: on expiry the CTA records LSV2_ERR_TIMEOUT, skips the rest and frees TMEM.
+#include <cuda_bf16.h>
+
+#include "query.cuh"
+#include "splat_core.cuh"
+
+namespace lsv2 {
+namespace {
+
+constexpr int kLev = 3, kKp = 4, kTW = 16, kTH = 16;
+using FC = SplatCfg<kLev, kKp, kTW, kTH, 0>;
+constexpr int kM = 128;
+constexpr int kATile = kM * 128;             // one A tile: 128 rows x 64 BF16
+constexpr int kBChunk = 128 * 128;           // 128 codebook rows x 64 BF16
+constexpr int kBSlots = 3;
+constexpr int kAOff = 0;                           // A [level][half] (6 x 16 KB)
+constexpr int kBOff = kAOff + kLev * 2 * kATile;   // B ring (3 x 16 KB)
+constexpr int kQOff = kBOff + kBSlots * kBChunk;   // query matrices: all levels if they fit, else one
+constexpr int kQBytes = 32768;
+constexpr int kQMaxRows = 256;
+constexpr int kTnOff = kQOff + kQBytes;            // reciprocal text norms (<= 448 floats)
+constexpr int kStageRow = 128 + 16;                // F staging: 128 bytes per pixel row + skew
+constexpr int kStage0Off = kTnOff + 448 * 4;       // staging of the warps with column half 0
+constexpr int kBarOff = FC::kAccBytes + 256;       // fused-phase barriers (after the splat's)
+constexpr int kStage1Off = FC::kFixedBytes;        // column half 1: the splat's record ring
+static_assert(kStage0Off + kM * kStageRow <= FC::kAccBytes, "fused operands fit in the accumulator memory");
+static_assert(kStage1Off + kM * kStageRow <= FC::kSmemBytes, "staging fits in the record ring");
+static_assert(kBarOff + 32 * 8 <= FC::kFixedBytes, "fused barriers fit in the fixed area");
+
+struct FusedArgs {
+    int width, height, GX;
+    const uint32_t* tile_ranges;
+    const uint32_t* gauss_ids;
+    const float* recs;
+    float* final_T;
+    uint32_t* n_last;
+    int D;                       // features (multiple of 128, <= 512)
+    const uint8_t* Bdec;         // [levels][D / 128][128 rows x 128 B] swizzled BF16 S^T
+    void* F;                     // [levels][P][D] BF16, or null
+    int Q, n_neg, Qp, npadq;     // Q = 0: no query
+    float tau;
+    const uint8_t* Bq;           // [levels][npadq rows x 128 B] swizzled BF16 [S S^T | S t] (text-major)
+    const float* rtn;            // [(1 + n_neg) Qp] reciprocal text norms, text-major
+    void* rel;                   // [Q][levels][P]
+    int rel_bf16;
+    int32_t* status;
+};
+
+struct FusedBars {
+    uint64_t bfull[kBSlots], bempty[kBSlots], dfull[2], dempty[2], qfull, qempty, qload, qfree;
+    uint32_t tslot;
+};
+
+// (M-half h, lane quarter q, lane) -> pixel of the tile; false outside the image
+__device__ __forceinline__ bool tile_pixel(const FusedArgs& a, int tile, int h, int q, int lane, size_t& pix)
+{
+    const int tx = tile % a.GX, ty = tile / a.GX;
+    const int sw = 4 * h + q;   // splat warp: 2 rows of 16 pixels
+    const int px = tx * kTW + (lane % kTW), py = ty * kTH + sw * (32 / kTW) + lane / kTW;
+    pix = (size_t)py * a.width + px;
+    return px < a.width && py < a.height;
+}
+
+__global__ void __launch_bounds__(FC::kThreads, 1) fused_kernel(FusedArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // the swizzled operand tiles need 1024-byte alignment (1 KB of slack is requested)
+    unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const SplatSmem<FC> sm(smem);
+    FusedBars* fb = reinterpret_cast<FusedBars*>(smem + kBarOff);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tile = blockIdx.x;
+    const size_t P = (size_t)a.width * a.height;
+    const bool do_query = a.Q > 0, do_dec = a.F != nullptr;
+    const int nchunk = a.D / 128;
+
+    if (tid == 0) {
+        sm.init();
+        *sm.skip = a.status && *reinterpret_cast<volatile int32_t*>(a.status) == LSV2_ERR_TIMEOUT;
+        for (int s = 0; s < kBSlots; ++s) {
+            tc::mbar_init(tc::smem_u32(&fb->bfull[s]), 1);
+            tc::mbar_init(tc::smem_u32(&fb->bempty[s]), 1);
+        }
+        for (int s = 0; s < 2; ++s) {
+            tc::mbar_init(tc::smem_u32(&fb->dfull[s]), 1);
+            tc::mbar_init(tc::smem_u32(&fb->dempty[s]), FC::kWarps);
+        }
+        tc::mbar_init(tc::smem_u32(&fb->qfull), 1);
+        tc::mbar_init(tc::smem_u32(&fb->qempty), FC::kWarps);
+        tc::mbar_init(tc::smem_u32(&fb->qload), 1);
+        tc::mbar_init(tc::smem_u32(&fb->qfree), 1);
+    }
+    if (warp == 0) tc::tmem_alloc(tc::smem_u32(&fb->tslot), 512);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = fb->tslot;
+    const bool skip = *sm.skip;
+
+    if (!skip) {
+        // ---- splat: W stays in the consumer warps' shared-memory columns
+        TileJob j{a.width, a.height, a.GX, tile, a.tile_ranges[2 * tile], a.tile_ranges[2 * tile + 1], a.gauss_ids,
+                  a.recs, nullptr, a.final_T, a.n_last, a.status};
+        (void)splat_tile<kLev, kKp, kTW, kTH, 0, false>(j, sm, 0u);
+    }
+    bool ok = !skip && !*reinterpret_cast<volatile int*>(sm.abort);
+    // ---- transit: coefficients -> BF16 rows in TMEM (lane = pixel row of its 128-pixel half)
+    if (ok && warp < FC::kWarps) {
+        const float* acc = sm.acc + warp * FC::kAccFloats;
+        const uint32_t lrow = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+#pragma unroll 1
+        for (int l = 0; l < kLev; ++l) {
+            uint32_t r[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+                r[i] = tc::pack_bf16(acc[(l * 64 + 2 * i) * 33 + lane], acc[(l * 64 + 2 * i + 1) * 33 + lane]);
+            tc::tmem_st32(lrow + (uint32_t)(l * 64 + (warp >> 2) * 32), r);
+        }
+        tc::tmem_wait_st();
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    // ---- TMEM -> swizzled A tiles in the freed accumulator memory; the producer starts the
+    //      operand copies into the same memory
+    if (ok && warp < FC::kWarps) {
+        const int row = 32 * (warp & 3) + lane, h = warp >> 2;
+        const uint32_t lrow = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+#pragma unroll 1
+        for (int l = 0; l < kLev; ++l) {
+            uint32_t r[32];
+            tc::tmem_ld32(lrow + (uint32_t)(l * 64 + h * 32), r);
+            tc::tmem_wait_ld();
+            uint8_t* A = smem + kAOff + (l * 2 + h) * kATile;
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                *reinterpret_cast<uint4*>(A + tc::sw128(row, 8 * c)) = make_uint4(r[4 * c], r[4 * c + 1], r[4 * c + 2], r[4 * c + 3]);
+        }
+    }
+    const int nb = do_dec ? kLev * nchunk : 0;   // B chunks per tile
+    if (ok && warp == FC::kWarps && lane == 0) {
+        for (int g = 0; g < kBSlots && g < nb; ++g) {
+            tc::bulk_load_arm(tc::smem_u32(&fb->bfull[g]), kBChunk);
+            tc::bulk_load(tc::smem_u32(smem + kBOff + g * kBChunk), a.Bdec + (size_t)g * kBChunk, kBChunk,
+                          tc::smem_u32(&fb->bfull[g]));
+        }
+        if (do_query) {
+            const uint32_t qb = (uint32_t)a.npadq * 128;
+            const uint32_t first = kLev * qb <= (uint32_t)kQBytes ? kLev * qb : qb;   // all levels if they fit
+            tc::bulk_load_arm(tc::smem_u32(&fb->qload), first);
+            tc::bulk_load(tc::smem_u32(smem + kQOff), a.Bq, first, tc::smem_u32(&fb->qload));
+        }
+    }
+    if (do_query)
+        for (int i = tid; i < (1 + a.n_neg) * a.Qp; i += FC::kThreads)
+            reinterpret_cast<float*>(smem + kTnOff)[i] = a.rtn[i];
+    tc::fence_proxy_async();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+
+    volatile int* abort_flag = sm.abort;
+    if (ok && warp == FC::kWarps) {
+        // ---- MMA issue (lane 0) and operand copies, in the epilogue's order
+        const uint32_t idd = tc::idesc_bf16(kM, 128);
+        int g = 0;            // decode MMA groups issued
+        int bc = 0;           // B chunks consumed
+        int b_loaded = nb < kBSlots ? nb : kBSlots;   // B chunks whose copies were issued
+        int q_loaded = do_query ? 1 : 0;              // query-matrix copies issued
+        int last_commit = -1; // 0: qfull of group gq_last; 1: dfull of group g - 1
+        const uint32_t qb = (uint32_t)a.npadq * 128;
+        const bool q_all = kLev * qb <= (uint32_t)kQBytes;
+        for (int l = 0; l < kLev && ok; ++l) {
+            if (do_query) {
+                if ((l == 0 || !q_all) &&
+                    warp_wait(&fb->qload, (uint32_t)(l & 1), nullptr, 0, abort_flag) != kWaitDone) {
+                    ok = false;
+                    break;
+                }
+                for (int h = 0; h < 2; ++h) {
+                    const int gq = 2 * l + h;
+                    if (gq > 0 && warp_wait(&fb->qempty, (uint32_t)((gq - 1) & 1), nullptr, 0, abort_flag) != kWaitDone) {
+                        ok = false;
+                        break;
+                    }
+                    if (lane == 0) {
+                        tc::fence_after();
+                        const uint32_t a0 = tc::smem_u32(smem + kAOff + (l * 2 + h) * kATile);
+                        const uint32_t b0 = tc::smem_u32(smem + kQOff + (q_all ? l * qb : 0u));
+                        for (int n0 = 0; n0 < a.npadq; n0 += 256) {
+                            const int nn = a.npadq - n0 < 256 ? a.npadq - n0 : 256;
+#pragma unroll
+                            for (int k = 0; k < 4; ++k)
+                                tc::mma_bf16(tmem + 256u + (uint32_t)n0, tc::desc_sw128(a0 + k * 32),
+                                             tc::desc_sw128(b0 + n0 * 128 + k * 32), tc::idesc_bf16(kM, nn), k > 0 ? 1u : 0u);
+                        }
+                        tc::mma_commit(tc::smem_u32(&fb->qfull));
+                        if (h == 1) tc::mma_commit(tc::smem_u32(&fb->qfree));
+                    }
+                    __syncwarp();
+                    last_commit = 0;
+                }
+                if (!ok) break;
+                if (l + 1 < kLev && !q_all) {
+                    // the next level's query matrix replaces this one once its MMAs have read it
+                    if (warp_wait(&fb->qfree, (uint32_t)(l & 1), nullptr, 0, abort_flag) != kWaitDone) { ok = false; break; }
+                    if (lane == 0) {
+                        tc::bulk_load_arm(tc::smem_u32(&fb->qload), qb);
+                        tc::bulk_load(tc::smem_u32(smem + kQOff), a.Bq + (size_t)(l + 1) * qb, qb, tc::smem_u32(&fb->qload));
+                    }
+                    ++q_loaded;
+                }
+            }
+            if (!do_dec) continue;
+            for (int c = 0; c < nchunk; ++c, ++bc) {
+                const int s = bc % kBSlots;
+                if (warp_wait(&fb->bfull[s], (uint32_t)((bc / kBSlots) & 1), nullptr, 0, abort_flag) != kWaitDone) {
+                    ok = false;
+                    break;
+                }
+                for (int h = 0; h < 2; ++h, ++g) {
+                    const int buf = g & 1;
+                    if (g >= 2 && warp_wait(&fb->dempty[buf], (uint32_t)(((g - 2) >> 1) & 1), nullptr, 0, abort_flag) != kWaitDone) {
+                        ok = false;
+                        break;
+                    }
+                    if (lane == 0) {
+                        tc::fence_after();
+                        const uint32_t a0 = tc::smem_u32(smem + kAOff + (l * 2 + h) * kATile);
+                        const uint32_t b0 = tc::smem_u32(smem + kBOff + s * kBChunk);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            tc::mma_bf16(tmem + (uint32_t)(buf * 128), tc::desc_sw128(a0 + k * 32), tc::desc_sw128(b0 + k * 32),
+                                         idd, k > 0 ? 1u : 0u);
+                        tc::mma_commit(tc::smem_u32(&fb->dfull[buf]));
+                        if (h == 1) tc::mma_commit(tc::smem_u32(&fb->bempty[s]));
+                    }
+                    __syncwarp();
+                    last_commit = 1;
+                }
+                if (!ok) break;
+                // refill this slot with chunk bc + kBSlots once both MMAs have read it
+                const int nxt = bc + kBSlots;
+                if (nxt < nb) {
+                    if (warp_wait(&fb->bempty[s], (uint32_t)((bc / kBSlots) & 1), nullptr, 0, abort_flag) != kWaitDone) {
+                        ok = false;
+                        break;
+                    }
+                    if (lane == 0) {
+                        tc::bulk_load_arm(tc::smem_u32(&fb->bfull[s]), kBChunk);
+                        tc::bulk_load(tc::smem_u32(smem + kBOff + s * kBChunk), a.Bdec + (size_t)nxt * kBChunk, kBChunk,
+                                      tc::smem_u32(&fb->bfull[s]));
+                    }
+                    ++b_loaded;
+                }
+            }
+        }
+        if (!ok) {
+            if (lane == 0) report(a.status, LSV2_ERR_TIMEOUT);
+            // Before the CTA frees TMEM and retires: the copies it issued must have landed and
+            // its last MMAs completed (each wait bounded; the status already records the failure).
+            *abort_flag = 1;
+            for (int c = b_loaded > kBSlots ? b_loaded - kBSlots : 0; c < b_loaded; ++c)
+                (void)tc::mbar_wait(tc::smem_u32(&fb->bfull[c % kBSlots]), (uint32_t)((c / kBSlots) & 1), 100000000ull);
+            if (q_loaded > 0)
+                (void)tc::mbar_wait(tc::smem_u32(&fb->qload), (uint32_t)((q_loaded - 1) & 1), 100000000ull);
+            if (last_commit == 1 && g > 0)
+                (void)tc::mbar_wait(tc::smem_u32(&fb->dfull[(g - 1) & 1]), (uint32_t)(((g - 1) >> 1) & 1), 100000000ull);
+        }
+    } else if (ok && warp < FC::kWarps) {
+        // ---- epilogues
+        const int q4 = warp & 3, wh = warp >> 2;
+        const uint32_t lrow = tmem + ((uint32_t)(32 * q4) << 16);
+        const int row = 32 * q4 + lane;
+        const float* rtn = reinterpret_cast<const float*>(smem + kTnOff);
+        const int per = 1 + a.n_neg;
+        int g = 0;
+        for (int l = 0; l < kLev && ok; ++l) {
+            if (do_query) {
+                for (int h = 0; h < 2; ++h) {
+                    const int gq = 2 * l + h;
+                    if (warp_wait(&fb->qfull, (uint32_t)(gq & 1), nullptr, 0, abort_flag) != kWaitDone) { ok = false; break; }
+                    tc::fence_after();
+                    size_t pix;
+                    const bool in = tile_pixel(a, tile, h, q4, lane, pix);
+                    // |F|^2 = W . (S S^T W): columns 0..63, W from this level's A tile
+                    const uint8_t* A = smem + kAOff + (l * 2 + h) * kATile;
+                    float n2 = 0.0f;
+                    for (int c = 0; c < 64; c += 32) {
+                        uint32_t r[32];
+                        tc::tmem_ld32(lrow + 256u + (uint32_t)c, r);
+                        tc::tmem_wait_ld();
+#pragma unroll
+                        for (int kc = 0; kc < 4; ++kc) {
+                            const uint4 wq = *reinterpret_cast<const uint4*>(A + tc::sw128(row, c + 8 * kc));
+                            const uint32_t wv[4] = {wq.x, wq.y, wq.z, wq.w};
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const __nv_bfloat162 w2 = *reinterpret_cast<const __nv_bfloat162*>(&wv[e]);
+                                n2 = fmaf(__low2float(w2), __uint_as_float(r[kc * 8 + 2 * e]), n2);
+                                n2 = fmaf(__high2float(w2), __uint_as_float(r[kc * 8 + 2 * e + 1]), n2);
+                            }
+                        }
+                    }
+                    const float nf = sqrtf(fmaxf(n2, 0.0f));
+                    const float kneg = nf < 1e-12f ? 0.0f : -a.tau / nf;
+                    const int nch = a.Qp / 8, chh = (nch + 1) / 2;
+                    for (int c = wh ? chh : 0; c < (wh ? nch : chh); ++c) {
+                        const int q0 = c * 8;
+                        uint32_t rp[8], rn[8];
+                        tc::tmem_ld8(lrow + 256u + (uint32_t)(64 + q0), rp);
+                        float best[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) best[e] = -INFINITY;
+                        for (int t = 1; t < per; ++t) {
+                            tc::tmem_ld8(lrow + 256u + (uint32_t)(64 + t * a.Qp + q0), rn);
+                            tc::tmem_wait_ld();
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) best[e] = fmaxf(best[e], __uint_as_float(rn[e]) * rtn[t * a.Qp + q0 + e]);
+                        }
+                        tc::tmem_wait_ld();
+                        if (in) {
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) {
+                                const int q = q0 + e;
+                                if (q < a.Q) {
+                                    const float d = __uint_as_float(rp[e]) * rtn[q0 + e] - best[e];
+                                    const float rv = __fdividef(1.0f, 1.0f + __expf(kneg * d));
+                                    const size_t o = ((size_t)q * kLev + l) * P + pix;
+                                    if (a.rel_bf16) static_cast<__nv_bfloat16*>(a.rel)[o] = __float2bfloat16_rn(rv);
+                                    else static_cast<float*>(a.rel)[o] = rv;
+                                }
+                            }
+                        }
+                    }
+                    tc::fence_before();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(tc::smem_u32(&fb->qempty));
+                }
+                if (!ok) break;
+            }
+            if (!do_dec) continue;
+            for (int c = 0; c < nchunk && ok; ++c) {
+                for (int h = 0; h < 2; ++h, ++g) {
+                    const int buf = g & 1;
+                    if (warp_wait(&fb->dfull[buf], (uint32_t)((g >> 1) & 1), nullptr, 0, abort_flag) != kWaitDone) {
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after();
+                    uint32_t r[32], r2[32];
+                    tc::tmem_ld32(lrow + (uint32_t)(buf * 128 + wh * 64), r);
+                    tc::tmem_ld32(lrow + (uint32_t)(buf * 128 + wh * 64 + 32), r2);
+                    tc::tmem_wait_ld();
+                    tc::fence_before();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(tc::smem_u32(&fb->dempty[buf]));
+                    // stage this warp's 32 rows x 128 bytes, then write them with coalesced
+                    // 512-byte warp stores (4 pixel segments of 128 bytes each)
+                    uint8_t* stg = smem + (wh ? kStage1Off : kStage0Off);
+                    uint4* mine = reinterpret_cast<uint4*>(stg + row * kStageRow);
+#pragma unroll
+                    for (int v = 0; v < 4; ++v)
+                        mine[v] = make_uint4(tc::pack_bf16(__uint_as_float(r[8 * v]), __uint_as_float(r[8 * v + 1])),
+                                             tc::pack_bf16(__uint_as_float(r[8 * v + 2]), __uint_as_float(r[8 * v + 3])),
+                                             tc::pack_bf16(__uint_as_float(r[8 * v + 4]), __uint_as_float(r[8 * v + 5])),
+                                             tc::pack_bf16(__uint_as_float(r[8 * v + 6]), __uint_as_float(r[8 * v + 7])));
+#pragma unroll
+                    for (int v = 0; v < 4; ++v)
+                        mine[4 + v] = make_uint4(tc::pack_bf16(__uint_as_float(r2[8 * v]), __uint_as_float(r2[8 * v + 1])),
+                                                 tc::pack_bf16(__uint_as_float(r2[8 * v + 2]), __uint_as_float(r2[8 * v + 3])),
+                                                 tc::pack_bf16(__uint_as_float(r2[8 * v + 4]), __uint_as_float(r2[8 * v + 5])),
+                                                 tc::pack_bf16(__uint_as_float(r2[8 * v + 6]), __uint_as_float(r2[8 * v + 7])));
+                    __syncwarp();
+#pragma unroll
+                    for (int it = 0; it < 8; ++it) {
+                        const int lr = it * 4 + (lane >> 3), ch = lane & 7;   // row within the warp's 32, 16-byte chunk
+                        size_t px2;
+                        if (tile_pixel(a, tile, h, q4, lr, px2)) {
+                            const uint4 v = *reinterpret_cast<const uint4*>(stg + (32 * q4 + lr) * kStageRow + ch * 16);
+                            __stcs(reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(a.F) +
+                                                            ((size_t)l * P + px2) * a.D + c * 128 + wh * 64) + ch, v);
+                        }
+                    }
+                    __syncwarp();
+                }
+            }
+        }
+        if (!ok && lane == 0) report(a.status, LSV2_ERR_TIMEOUT);
+    }
+    // every MMA was waited on by an epilogue, or the issuer drained what it started
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after();
+        tc::tmem_dealloc(tmem, 512);
+    }
+}
+
+// Operands of the fused kernel: the codebook S^T of every level as swizzled BF16 chunks of 128
+// rows, and (with queries) the text-major [S S^T | S t] rows and reciprocal text norms.
+__global__ void fused_prep_kernel(int levels, int D, const float* S, int Q, int n_neg, int Qp, int npadq,
+                                  const float* Bt, const float* tnorm, uint8_t* Bdec, uint8_t* Bq, float* rtn)
+{
+    const int l = blockIdx.y;
+    const int per = 1 + n_neg;
+    const int n_dec = D * 64, n_q = Q > 0 ? npadq * 64 : 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_dec + n_q; i += gridDim.x * blockDim.x) {
+        if (i < n_dec) {
+            const int n = i >> 6, k = i & 63;      // row n of S^T = column n of S
+            const float v = S[((size_t)l * 64 + k) * D + n];
+            uint8_t* chunk = Bdec + ((size_t)l * (D / 128) + n / 128) * kBChunk;
+            *reinterpret_cast<__nv_bfloat16*>(chunk + tc::sw128(n % 128, k)) = __float2bfloat16_rn(v);
+        } else {
+            const int i2 = i - n_dec, n = i2 >> 6, k = i2 & 63;
+            int src = n < 64 ? n : -1;
+            if (n >= 64 && n < 64 + per * Qp) {
+                const int t = (n - 64) / Qp, q = (n - 64) % Qp;
+                src = q < Q ? 64 + q * per + t : -1;
+            }
+            const float v = src >= 0 ? Bt[((size_t)l * (64 + Q * per) + src) * 64 + k] : 0.0f;
+            *reinterpret_cast<__nv_bfloat16*>(Bq + (size_t)l * npadq * 128 + tc::sw128(n, k)) = __float2bfloat16_rn(v);
+        }
+    }
+    if (Q > 0 && l == 0 && blockIdx.x == 0)
+        for (int i = threadIdx.x; i < per * Qp; i += blockDim.x) {
+            const int t = i / Qp, q = i % Qp;
+            rtn[i] = q < Q ? 1.0f / tnorm[q * per + t] : 0.0f;
+        }
+}
+
+int pad8(int q) { return (q + 7) / 8 * 8; }
+int npadq_of(int Q, int n_neg) { return Q > 0 ? (64 + (1 + n_neg) * pad8(Q) + 15) / 16 * 16 : 0; }
+size_t a256(size_t b) { return (b + 255) / 256 * 256; }
+
+struct FusedLayout {
+    size_t recs, bdec, qws, bq, rtn, bytes;
+};
+
+FusedLayout fused_layout(int64_t n, int levels, int K, int D, int Q, int n_neg)
+{
+    FusedLayout L{};
+    size_t o = 0;
+    auto take = [&](size_t b) {
+        const size_t at = o;
+        o += a256(b);
+        return at;
+    };
+    L.recs = take((size_t)n * splat_record_bytes(levels, K));
+    L.bdec = take((size_t)levels * D * 128);
+    const int nt = Q * (1 + n_neg);
+    L.qws = take(Q > 0 ? query_workspace_bytes(levels, nt) : 0);
+    L.bq = take((size_t)levels * npadq_of(Q, n_neg) * 128);
+    L.rtn = take((size_t)(1 + n_neg) * pad8(Q) * 4);
+    L.bytes = o;
+    return L;
+}
+
+}  // namespace
+
+bool fused_supported(int levels, int K, int L, int D, int Q, int n_neg, int tw, int th)
+{
+    if (levels != kLev || K != kKp || L != 64 || tw != kTW || th != kTH) return false;
+    if (D < 128 || D > 512 || D % 128 != 0) return false;
+    if (Q < 0 || (Q > 0 && (n_neg < 1 || npadq_of(Q, n_neg) > kQMaxRows))) return false;
+    return true;
+}
+
+size_t fused_workspace_bytes(int64_t n, int levels, int K, int D, int Q, int n_neg)
+{
+    return fused_layout(n, levels, K, D, Q, n_neg).bytes;
+}
+
+cudaError_t launch_fused(const lsv2_camera& cam, int64_t n, const lsv2_proj& proj, const uint32_t* tile_ranges,
+                         const uint32_t* gauss_ids, const uint8_t* idx, const float* w, const float* codebook, int D,
+                         int Q, int n_neg, const float* text, float tau, void* ws, void* F, void* rel, bool rel_bf16,
+                         float* final_T, uint32_t* n_last, int32_t* status, cudaStream_t stream)
+{
+    const FusedLayout Lo = fused_layout(n, kLev, kKp, D, Q, n_neg);
+    char* base = static_cast<char*>(ws);
+    PackArgs pa{n, kLev, kKp, splat_record_bytes(kLev, kKp), proj.xy, proj.axes, proj.conic_o, proj.extent, idx, w,
+                reinterpret_cast<float*>(base + Lo.recs), status};
+    cudaError_t e = launch_pack(pa, stream);
+    if (e != cudaSuccess) return e;
+    const int nt = Q * (1 + n_neg);
+    if (Q > 0) {
+        e = launch_query_prepare(kLev, D, nt, codebook, text, base + Lo.qws, stream);
+        if (e != cudaSuccess) return e;
+    }
+    const int Qp = pad8(Q), npadq = npadq_of(Q, n_neg);
+    fused_prep_kernel<<<dim3(64, kLev), 256, 0, stream>>>(kLev, D, codebook, Q, n_neg, Qp, npadq,
+                                                          Q > 0 ? query_ws_bt(base + Lo.qws) : nullptr,
+                                                          Q > 0 ? query_ws_tnorm(base + Lo.qws, kLev, nt) : nullptr,
+                                                          reinterpret_cast<uint8_t*>(base + Lo.bdec),
+                                                          reinterpret_cast<uint8_t*>(base + Lo.bq),
+                                                          reinterpret_cast<float*>(base + Lo.rtn));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int GX = (cam.width + kTW - 1) / kTW, GY = (cam.height + kTH - 1) / kTH;
+    if (GX * GY == 0) return cudaSuccess;
+    FusedArgs a{};
+    a.width = cam.width;
+    a.height = cam.height;
+    a.GX = GX;
+    a.tile_ranges = tile_ranges;
+    a.gauss_ids = gauss_ids;
+    a.recs = reinterpret_cast<const float*>(base + Lo.recs);
+    a.final_T = final_T;
+    a.n_last = n_last;
+    a.D = D;
+    a.Bdec = reinterpret_cast<const uint8_t*>(base + Lo.bdec);
+    a.F = F;
+    a.Q = Q;
+    a.n_neg = n_neg;
+    a.Qp = Qp;
+    a.npadq = npadq;
+    a.tau = tau;
+    a.Bq = reinterpret_cast<const uint8_t*>(base + Lo.bq);
+    a.rtn = reinterpret_cast<const float*>(base + Lo.rtn);
+    a.rel = rel;
+    a.rel_bf16 = rel_bf16 ? 1 : 0;
+    a.status = status;
+    constexpr int kSmem = FC::kSmemBytes + 1024;
+    static_assert(kSmem <= 232448, "shared memory budget");
+    e = cudaFuncSetAttribute(fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    if (e != cudaSuccess) return e;
+    fused_kernel<<<GX * GY, FC::kThreads, kSmem, stream>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace lsv2
+
+using namespace lsv2;
+
+extern "C" size_t lsv2_render_fused_workspace_bytes(int64_t n, int32_t levels, int32_t K, int32_t D, int32_t Q,
+                                                   int32_t n_neg)
+{
+    if (n < 0 || !fused_supported(levels, K, 64, D, Q, n_neg, kTW, kTH)) return 0;
+    return fused_workspace_bytes(n, levels, K, D, Q, n_neg);
+}
+
+extern "C" lsv2_status lsv2_render_fused(const lsv2_camera* cam, int64_t n, const lsv2_proj* proj,
+                                         const uint32_t* tile_ranges, const uint32_t* gauss_ids, int32_t levels,
+                                         int32_t K, int32_t L, const uint8_t* idx, const float* w,
+                                         const float* codebook, int32_t D, int32_t Q, int32_t n_neg,
+                                         const float* text, float tau, void* workspace, size_t workspace_bytes,
+                                         void* feat, void* rel, lsv2_dtype rel_dtype, float* final_T,
+                                         uint32_t* n_last, int32_t* dev_status, void* stream)
+{
+    if (!cam || cam->width <= 0 || cam->height <= 0 || n < 0 || !proj || !tile_ranges || !gauss_ids || !final_T ||
+        !n_last || !codebook)
+        return LSV2_ERR_INVALID_ARGUMENT;
+    if (!fused_supported(levels, K, L, D, Q, n_neg, cam->tile_w, cam->tile_h)) return LSV2_ERR_UNSUPPORTED;
+    if (n > 0 && (!idx || !w || !proj->xy || !proj->axes || !proj->conic_o || !proj->extent))
+        return LSV2_ERR_INVALID_ARGUMENT;
+    if (!feat && Q == 0) return LSV2_ERR_INVALID_ARGUMENT;
+    if (Q > 0 && (!text || !rel || (rel_dtype != LSV2_F32 && rel_dtype != LSV2_BF16))) return LSV2_ERR_INVALID_ARGUMENT;
+    if ((feat && (reinterpret_cast<uintptr_t>(feat) & 15u)) || (reinterpret_cast<uintptr_t>(codebook) & 15u) ||
+        (text && (reinterpret_cast<uintptr_t>(text) & 15u)))
+        return LSV2_ERR_INVALID_ARGUMENT;
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255u) ||
+        workspace_bytes < fused_workspace_bytes(n, levels, K, D, Q, n_neg))
+        return LSV2_ERR_INVALID_ARGUMENT;
+    const cudaError_t e = launch_fused(*cam, n, *proj, tile_ranges, gauss_ids, idx, w, codebook, D, Q, n_neg, text, tau,
+                                       workspace, feat, rel, rel_dtype == LSV2_BF16, final_T, n_last, dev_status,
+                                       static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? LSV2_OK : LSV2_ERR_CUDA;
+}

@@ -1,11 +1,14 @@
 // query_tc.cu -- relevancy (Sec. 3.2) through the linearity of Eq. 7 on the tensor cores.
 //
-// Per level, Y = W B with B = [S S^T | S t_0 | S t_1 | ...] (64 x N, N = 64 + #texts padded to a
-// multiple of 16) is one (128 x 64)(64 x N) tcgen05 product per 128-pixel tile (BF16 operands,
-// FP32 accumulation in TMEM).  The epilogue thread that owns a pixel (one TMEM lane) forms
-//     |F|^2 = sum_j W_j Y_j (j < 64),   cos_t = Y_{64+t} / (|F| |t|)   (0 when |F| < 1e-12),
-//     rel_q = sigmoid(tau (cos_pos - max_i cos_neg_i)),
-// and writes rel[q][lev][p] (coalesced over the warp's 32 consecutive pixels).  F is never
+// Per level, Y = W B with B = [S S^T | S t ...] (64 x N) is one (128 x 64)(64 x N) tcgen05
+// product per 128-pixel tile (BF16 operands, FP32 accumulation in TMEM).  The text columns are
+// staged text-major: column 64 + t Qp + q holds text t (0 = positive, 1.. = negatives) of query
+// q, Qp = Q rounded up to 8, so a thread reads 8 queries' positives and each negative with one
+// 8-column TMEM load apiece.  The epilogue thread that owns a pixel (one TMEM lane) forms
+//     |F|^2 = sum_j W_j Y_j (j < 64),
+//     rel_q = sigmoid(tau (cos_pos - max_i cos_neg_i)),  cos_t = Y_t / (|F| |t|) (0 if |F| < 1e-12)
+// as sigmoid(tau / |F| (Y_pos / |t_pos| - max_i Y_neg_i / |t_neg_i|)) (|F| > 0 commutes with the
+// max), and writes rel[q][lev][p] (coalesced over the warp's 32 consecutive pixels).  F is never
 // formed.  Persistent CTAs split over levels, B^T swizzled once per CTA.  Each 128-pixel W tile
 // is 32 KB contiguous in HBM: one thread keeps a ring of two cp.async.bulk copies in flight
 // (mbarrier transaction counts), all threads convert the landed tile to the swizzled BF16
@@ -21,11 +24,11 @@ constexpr int kK = 64;
 constexpr int kThreads = 256;
 
 struct QueryTcArgs {
-    int Q, n_neg, ncol, npad;      // ncol = 64 + Q (1 + n_neg); npad = ncol rounded up to 16
+    int Q, n_neg, Qp, npad;        // Qp = Q rounded up to 8; npad = 64 + (1 + n_neg) Qp rounded up to 16
     float tau;
     const float* W;                // per view v: [levels][P_v][64] f32 at W + seg[v].w_off
-    const float* Bt;               // [levels][ncol][64] f32 (rows of B^T)
-    const float* tnorm;            // [Q (1 + n_neg)]
+    const float* Bt;               // [levels][64 + Q (1 + n_neg)][64] f32 (rows of B^T, query-major texts)
+    const float* tnorm;            // [Q (1 + n_neg)] (query-major)
     void* rel;                     // per view v: [Q][levels][P_v] at rel + seg[v].rel_off
     int rel_bf16;
     int levels;
@@ -38,9 +41,13 @@ struct QueryTcArgs {
 constexpr int kStages = 2;                      // W tiles in flight per CTA (bulk copies)
 constexpr int kTileBytes = kM * kK * 4;         // one FP32 W tile: 32 KB, contiguous in HBM
 
-__host__ __device__ constexpr size_t smem_bytes(int npad, int nt)
+__host__ __device__ constexpr int pad8(int q) { return (q + 7) / 8 * 8; }
+__host__ __device__ constexpr int npad_of(int Q, int n_neg) { return (64 + (1 + n_neg) * pad8(Q) + 15) / 16 * 16; }
+
+// ntp = (1 + n_neg) Qp reciprocal text norms, text-major
+__host__ __device__ constexpr size_t smem_bytes(int npad, int ntp)
 {
-    return 1024 + (size_t)kStages * kTileBytes + (size_t)npad * 128 + (size_t)kM * 128 + (size_t)nt * 4 + 128;
+    return 1024 + (size_t)kStages * kTileBytes + (size_t)npad * 128 + (size_t)kM * 128 + (size_t)ntp * 4 + 128;
 }
 
 __host__ __device__ constexpr uint32_t tmem_cols(int npad)
@@ -61,11 +68,6 @@ __device__ __forceinline__ void convert_w(const float* src, int valid_rows, uint
     }
 }
 
-__device__ __forceinline__ float bf16_at(const uint8_t* sA, int row, int k)
-{
-    return __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(sA + tc::sw128(row, k)));
-}
-
 __global__ void __launch_bounds__(kThreads, 2) query_tc_kernel(QueryTcArgs a)
 {
     extern __shared__ uint8_t smem_raw[];
@@ -74,8 +76,9 @@ __global__ void __launch_bounds__(kThreads, 2) query_tc_kernel(QueryTcArgs a)
     uint8_t* sB = smem + (size_t)kStages * kTileBytes;
     uint8_t* sA = sB + (size_t)a.npad * 128;
     float* sTn = reinterpret_cast<float*>(sA + kM * 128);
-    const int nt = a.Q * (1 + a.n_neg);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(sTn) + (((size_t)nt * 4 + 15) & ~size_t(15)));
+    const int per = 1 + a.n_neg;
+    const int ntp = per * a.Qp;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(sTn) + (((size_t)ntp * 4 + 15) & ~size_t(15)));
     uint64_t* full = bar + 1;                 // kStages barriers: W tile landed in the ring
     uint32_t* tslot = reinterpret_cast<uint32_t*>(full + kStages);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -110,14 +113,23 @@ __global__ void __launch_bounds__(kThreads, 2) query_tc_kernel(QueryTcArgs a)
         tc::mbar_init(tc::smem_u32(bar), 1);
         for (int s = 0; s < kStages; ++s) tc::mbar_init(tc::smem_u32(full + s), 1);
     }
-    // B^T rows (N x 64 K-major, swizzled), zero padding rows
-    const float* Bl = a.Bt + (size_t)lev * a.ncol * kK;
+    // B^T rows (N x 64 K-major, swizzled): the 64 rows of S S^T, then the text rows permuted
+    // from query-major (64 + q per + t) to text-major (64 + t Qp + q); zero padding rows
+    const float* Bl = a.Bt + (size_t)lev * (64 + a.Q * per) * kK;
     for (int i = tid; i < a.npad * kK; i += kThreads) {
         const int n = i >> 6, k = i & 63;
-        const float v = n < a.ncol ? Bl[i] : 0.0f;
+        int src = n < 64 ? n : -1;
+        if (n >= 64 && n < 64 + ntp) {
+            const int t = (n - 64) / a.Qp, q = (n - 64) % a.Qp;
+            src = q < a.Q ? 64 + q * per + t : -1;
+        }
+        const float v = src >= 0 ? Bl[(size_t)src * kK + k] : 0.0f;
         *reinterpret_cast<__nv_bfloat16*>(sB + tc::sw128(n, k)) = __float2bfloat16_rn(v);
     }
-    for (int i = tid; i < nt; i += kThreads) sTn[i] = 1.0f / a.tnorm[i];   // reciprocal norms
+    for (int i = tid; i < ntp; i += kThreads) {   // reciprocal norms, text-major
+        const int t = i / a.Qp, q = i % a.Qp;
+        sTn[i] = q < a.Q ? 1.0f / a.tnorm[q * per + t] : 0.0f;
+    }
     tc::fence_proxy_async();
     tc::fence_before();
     __syncthreads();
@@ -128,10 +140,9 @@ __global__ void __launch_bounds__(kThreads, 2) query_tc_kernel(QueryTcArgs a)
     const int q4 = warp & 3, half = warp >> 2;
     const int row = q4 * 32 + lane;
     const uint32_t trow = tmem + ((uint32_t)(q4 * 32) << 16);
-    // queries handled by this warp: half 0 -> [0, Qh), half 1 -> [Qh, Q)
-    const int Qh = (a.Q + 1) / 2;
-    const int qb = half ? Qh : 0, qe = half ? a.Q : Qh;
-    const int per = 1 + a.n_neg;
+    // 8-query chunks handled by this warp: half 0 -> [0, ch), half 1 -> [ch, nch)
+    const int nch = a.Qp / 8, ch = (nch + 1) / 2;
+    const int cb = half ? ch : 0, ce = half ? nch : ch;
     uint32_t phase = 0;
     bool failed = false;
 
@@ -192,38 +203,38 @@ __global__ void __launch_bounds__(kThreads, 2) query_tc_kernel(QueryTcArgs a)
             }
         }
         const float nf = sqrtf(fmaxf(n2, 0.0f));
-        const float inv = nf < 1e-12f ? 0.0f : 1.0f / nf;
-        // text columns of this warp's queries, read in 32-column chunks; (query, text) counters
-        // advance column by column (the columns of a query are consecutive)
-        const int cb = 64 + qb * per, ce = 64 + qe * per;
-        float cpos = 0.0f, best = -INFINITY;
-        int q = qb, t = 0;
-        for (int c0 = cb & ~31; qb < qe && c0 < ce; c0 += 32) {
-            uint32_t r[32];
-            tc::tmem_ld32(trow + (uint32_t)c0, r);
-            tc::tmem_wait_ld();
+        const float kneg = nf < 1e-12f ? 0.0f : -a.tau / nf;   // exp(-tau (cos_p - max cos_n)) = exp(kneg d)
+        for (int c = cb; c < ce; ++c) {
+            const int q0 = c * 8;
+            uint32_t rp[8], rn[8];
+            tc::tmem_ld8(trow + (uint32_t)(64 + q0), rp);
+            float best[8];
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const int c = c0 + j;
-                if (c < cb || c >= ce) continue;
-                const float cv = __uint_as_float(r[j]) * inv * sTn[c - 64];
-                if (t == 0) {
-                    cpos = cv;
-                    best = -INFINITY;
-                } else {
-                    best = fmaxf(best, cv);
-                }
-                if (t == a.n_neg) {
-                    if (p < Pv) {
-                        const float rv = 1.0f / (1.0f + __expf(-a.tau * (cpos - best)));
+            for (int j = 0; j < 8; ++j) best[j] = -INFINITY;
+            for (int t = 1; t < per; ++t) {
+                tc::tmem_ld8(trow + (uint32_t)(64 + t * a.Qp + q0), rn);
+                tc::tmem_wait_ld();
+                const float4 u0 = *reinterpret_cast<const float4*>(sTn + t * a.Qp + q0);
+                const float4 u1 = *reinterpret_cast<const float4*>(sTn + t * a.Qp + q0 + 4);
+                const float tn[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+#pragma unroll
+                for (int j = 0; j < 8; ++j) best[j] = fmaxf(best[j], __uint_as_float(rn[j]) * tn[j]);
+            }
+            tc::tmem_wait_ld();
+            const float4 u0 = *reinterpret_cast<const float4*>(sTn + q0);
+            const float4 u1 = *reinterpret_cast<const float4*>(sTn + q0 + 4);
+            const float tp[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+            if (p < Pv) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int q = q0 + j;
+                    if (q < a.Q) {
+                        const float d = __uint_as_float(rp[j]) * tp[j] - (per > 1 ? best[j] : 0.0f);
+                        const float rv = __fdividef(1.0f, 1.0f + __expf(kneg * d));
                         const size_t o = a.seg[vw].rel_off + ((size_t)q * a.levels + lev) * Pv + p;
                         if (a.rel_bf16) static_cast<__nv_bfloat16*>(a.rel)[o] = __float2bfloat16_rn(rv);
                         else static_cast<float*>(a.rel)[o] = rv;
                     }
-                    t = 0;
-                    ++q;
-                } else {
-                    ++t;
                 }
             }
         }
@@ -246,10 +257,12 @@ __global__ void __launch_bounds__(kThreads, 2) query_tc_kernel(QueryTcArgs a)
 
 }  // namespace
 
-bool query_tc_supported(int nt)
+bool query_tc_supported(int Q, int n_neg)
 {
-    const int npad = ((64 + nt) + 15) / 16 * 16;
-    return 64 + nt <= 512 && smem_bytes(npad, nt) <= 232448 && (512u / tmem_cols(npad) >= 2 || smem_bytes(npad, nt) >= 117760);
+    if (Q < 1 || n_neg < 1) return false;
+    const int npad = npad_of(Q, n_neg), ntp = (1 + n_neg) * pad8(Q);
+    return npad <= 512 && smem_bytes(npad, ntp) <= 232448 &&
+           (512u / tmem_cols(npad) >= 2 || smem_bytes(npad, ntp) >= 117760);
 }
 
 cudaError_t launch_query_tc_views(int levels, int V, const int64_t* P, int Q, int n_neg, float tau, const float* W,
@@ -257,11 +270,12 @@ cudaError_t launch_query_tc_views(int levels, int V, const int64_t* P, int Q, in
                                   int32_t* status, cudaStream_t stream)
 {
     if (V < 1 || V > kMaxQueryViews) return cudaErrorInvalidValue;
-    const int nt = Q * (1 + n_neg), ncol = 64 + nt, npad = (ncol + 15) / 16 * 16;
+    const int npad = npad_of(Q, n_neg), ntp = (1 + n_neg) * pad8(Q);
+    if (npad > 512) return cudaErrorInvalidValue;
     QueryTcArgs a{};
     a.Q = Q;
     a.n_neg = n_neg;
-    a.ncol = ncol;
+    a.Qp = pad8(Q);
     a.npad = npad;
     a.tau = tau;
     a.W = W;
@@ -287,7 +301,7 @@ cudaError_t launch_query_tc_views(int levels, int V, const int64_t* P, int Q, in
     // other's epilogue); the shared-memory request keeps one more CTA from being resident, so
     // tcgen05.alloc never waits on another CTA.
     const int resident = 512u / tmem_cols(npad) >= 2 ? 2 : 1;
-    size_t smem = smem_bytes(npad, nt);
+    size_t smem = smem_bytes(npad, ntp);
     const size_t floor_bytes = 233472 / (size_t)(resident + 1) + 1024;
     if (smem < floor_bytes) smem = floor_bytes;
     if (smem > 232448) return cudaErrorInvalidValue;

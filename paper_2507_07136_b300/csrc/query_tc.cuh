@@ -14,7 +14,8 @@ struct QuerySeg {
     size_t rel_off;     // elements: this view's relevancy block [Q][levels][P_v]
 };
 
-bool query_tc_supported(int nt);
+// Q queries of 1 + n_neg texts each: 64 + (1 + n_neg) * ceil(Q / 8) * 8 <= 512 and shared memory.
+bool query_tc_supported(int Q, int n_neg);
 cudaError_t launch_query_tc_views(int levels, int V, const int64_t* P, int Q, int n_neg, float tau, const float* W,
                                   const float* Bt, const float* tnorm, void* rel, bool rel_bf16, int num_sms,
                                   int32_t* status, cudaStream_t stream);

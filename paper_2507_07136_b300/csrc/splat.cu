@@ -22,6 +22,7 @@
 //    issued before any store.
 #include "device.cuh"
 #include "splat.cuh"
+#include "splat_core.cuh"
 #include "tc.cuh"
 
 namespace lsv2 {
@@ -85,317 +86,6 @@ __global__ void __launch_bounds__(256) pack_records_kernel(PackArgs a)
             }
     }
     reinterpret_cast<float2*>(rec + rec_floats - 4)[0] = reinterpret_cast<const float2*>(a.extent)[o];
-}
-
-// One tile of one view.
-struct TileJob {
-    int width, height, GX, tile;
-    uint32_t beg, end;
-    const uint32_t* gauss_ids;
-    const float* recs;
-    float* coeff;
-    float* final_T;
-    uint32_t* n_last;
-    int32_t* status;
-};
-
-namespace {
-
-constexpr uint64_t kWaitNs = 1000000000ull;   // bound of every wait on a stage barrier (1 s)
-
-// Shared memory of one CTA: accumulators [kWarps][kAccFloats], stage barriers and flags, then
-// kStages stages of [kBatch records][kBatch culling boxes (u, v, ex, ey)].  The barriers are
-// initialised once per CTA; batches are numbered across the CTA's tiles (stage = batch %
-// kStages, phase parity = (batch / kStages) & 1), so a persistent CTA never re-initialises them.
-template <class C>
-struct SplatSmem {
-    float* acc;
-    uint64_t* full;    // a stage's batch has landed (32 producer arrivals + the copies' bytes)
-    uint64_t* empty;   // every consumer warp is done with the stage (kWarps arrivals)
-    int* done_warps;   // consumer warps of the current tile whose pixels have all terminated
-    int* abort;        // a wait of this CTA ran out: every later wait gives up at once
-    uint32_t* issued;  // batches the producer issued for the current tile
-    int* skip;         // a wait ran out somewhere (status word): skip the remaining tiles
-    unsigned char* stages;
-    __device__ explicit SplatSmem(unsigned char* base)
-        : acc(reinterpret_cast<float*>(base)),
-          full(reinterpret_cast<uint64_t*>(base + C::kAccBytes)),
-          empty(reinterpret_cast<uint64_t*>(base + C::kAccBytes) + 8),
-          done_warps(reinterpret_cast<int*>(base + C::kAccBytes + 128)),
-          abort(reinterpret_cast<int*>(base + C::kAccBytes + 132)),
-          issued(reinterpret_cast<uint32_t*>(base + C::kAccBytes + 136)),
-          skip(reinterpret_cast<int*>(base + C::kAccBytes + 140)),
-          stages(base + C::kFixedBytes)
-    {
-    }
-    __device__ const unsigned char* rec(int s) const { return stages + s * C::kStageBytes; }
-    __device__ float4* box(int s) const
-    {
-        return reinterpret_cast<float4*>(stages + s * C::kStageBytes + C::kBatch * C::kRecBytes);
-    }
-    // once per CTA, by one thread, before a __syncthreads
-    __device__ void init() const
-    {
-        for (int s = 0; s < C::kStages; ++s) {
-            tc::mbar_init(tc::smem_u32(full + s), 32);
-            tc::mbar_init(tc::smem_u32(empty + s), C::kWarps);
-        }
-        *done_warps = 0;
-        *abort = 0;
-        *skip = 0;
-    }
-};
-
-constexpr int kWaitDone = 1, kWaitStopped = 0, kWaitTimeout = -1, kWaitAborted = -2;
-
-// Warp-uniform bounded wait for a barrier phase.  `done_warps` (optional) ends the wait early
-// once all_done consumer warps have finished; a wait that runs out raises the CTA's abort flag
-// (and the caller reports LSV2_ERR_TIMEOUT), after which every other wait returns at once.
-__device__ __forceinline__ int warp_wait(uint64_t* bar, uint32_t parity, const volatile int* done_warps,
-                                         int all_done, volatile int* abort)
-{
-    const uint64_t t0 = tc::globaltimer();
-    while (true) {
-        if (__all_sync(0xffffffffu, tc::mbar_try(tc::smem_u32(bar), parity))) return kWaitDone;
-        if (__shfl_sync(0xffffffffu, *abort, 0)) return kWaitAborted;
-        if (done_warps && __shfl_sync(0xffffffffu, *done_warps, 0) >= all_done) return kWaitStopped;
-        if (__any_sync(0xffffffffu, tc::globaltimer() - t0 > kWaitNs)) {
-            *abort = 1;
-            return kWaitTimeout;
-        }
-    }
-}
-
-// Producer warp: the tile's batch b is CTA batch g = bbase + b and goes to stage g % kStages
-// once every consumer warp has released the stage's previous batch; each lane copies one
-// record (bulk async copy, completing on the stage's barrier) and writes its culling box.
-// Before returning it waits until every copy it issued has landed, so no copy is in flight
-// into shared memory that is reused, and publishes the number of batches it issued.
-template <class C>
-__device__ void splat_produce(const TileJob& a, const SplatSmem<C>& sm, int lane, uint32_t bbase)
-{
-    const uint32_t n = a.end - a.beg;
-    const uint32_t nb = (n + C::kBatch - 1) / C::kBatch;
-    const volatile int* done_warps = sm.done_warps;
-    uint32_t issued = 0;
-    for (uint32_t b = 0; b < nb; ++b) {
-        const uint32_t g = bbase + b;
-        const int s = (int)(g % C::kStages);
-        if (g >= (uint32_t)C::kStages) {
-            const int w = warp_wait(sm.empty + s, ((g / C::kStages) - 1u) & 1u, done_warps, C::kWarps, sm.abort);
-            if (w == kWaitTimeout && lane == 0) report(a.status, LSV2_ERR_TIMEOUT);
-            if (w != kWaitDone) break;
-        }
-        if (__shfl_sync(0xffffffffu, *done_warps, 0) >= C::kWarps) break;
-        const uint32_t cnt = min((uint32_t)C::kBatch, n - b * C::kBatch);
-        const uint32_t full = tc::smem_u32(sm.full + s);
-        if (lane == 0) tc::mbar_expect_tx(full, cnt * (uint32_t)C::kRecBytes);
-        __syncwarp();
-        float4 box = make_float4(0.0f, 0.0f, -1.0f, -1.0f);
-        if ((uint32_t)lane < cnt) {
-            const uint32_t id = a.gauss_ids[a.beg + b * C::kBatch + lane];
-            const float* src = a.recs + (size_t)id * C::kRecFloats;
-            tc::bulk_load(tc::smem_u32(sm.rec(s) + lane * C::kRecBytes), src, (uint32_t)C::kRecBytes, full);
-            const float2 xy = __ldg(reinterpret_cast<const float2*>(src));
-            const float2 ex = __ldg(reinterpret_cast<const float2*>(src + C::kRecFloats - 4));
-            box = make_float4(xy.x, xy.y, ex.x, ex.y);
-        }
-        if (lane < C::kBatch) sm.box(s)[lane] = box;
-        tc::mbar_arrive(full);
-        issued = b + 1;
-    }
-    const uint32_t first = issued > (uint32_t)C::kStages ? issued - C::kStages : 0u;
-    for (uint32_t b = first; b < issued; ++b) {
-        const uint32_t g = bbase + b;
-        const int w = warp_wait(sm.full + (int)(g % C::kStages), (g / C::kStages) & 1u, nullptr, 0, sm.abort);
-        if (w == kWaitTimeout && lane == 0) report(a.status, LSV2_ERR_TIMEOUT);
-        if (w != kWaitDone) break;
-    }
-    if (lane == 0) *sm.issued = issued;
-}
-
-// Consumer warp: 32 pixels (one per lane), front to back over the tile's batches.
-template <class C, int LEVELS, int K, int TW, int TH>
-__device__ uint32_t splat_consume(const TileJob& a, const SplatSmem<C>& sm, int warp, int lane, uint32_t bbase)
-{
-    constexpr int kB = C::kBatch;
-    constexpr int kChunk = 4;   // kept records evaluated together
-    float* acc = sm.acc + warp * C::kAccFloats;
-    unsigned char* acc_lane = reinterpret_cast<unsigned char*>(acc + lane);
-    const int GX = a.GX;
-    const int tx = a.tile % GX, ty = a.tile / GX;
-    const int lx = lane % TW, ly = warp * (32 / TW) + lane / TW;
-    const int px = tx * TW + lx, py = ty * TH + ly;
-    const bool inside = px < a.width && py < a.height;
-    // pixel strip covered by this warp
-    constexpr int kRows = 32 / TW;
-    const float wx0 = (float)(tx * TW), wx1 = (float)(tx * TW + TW - 1);
-    const float wy0 = (float)(ty * TH + warp * kRows), wy1 = wy0 + (float)(kRows - 1);
-
-    for (int i = lane * 4; i < C::kAccFloats; i += 128)
-        *reinterpret_cast<float4*>(acc + i) = make_float4(0.f, 0.f, 0.f, 0.f);
-    __syncwarp();
-
-    const uint32_t n = a.end - a.beg;
-    const uint32_t nb = (n + kB - 1) / kB;
-    float T = 1.0f;
-    uint32_t last = 0;
-    bool done = !inside, wdone = false;
-    const float pxf = (float)px, pyf = (float)py;
-    const volatile int* done_warps = sm.done_warps;
-
-    uint32_t consumed = 0;   // batches this warp has released
-    for (uint32_t b = 0; b < nb; ++b) {
-        const uint32_t g = bbase + b;
-        const int s = (int)(g % C::kStages);
-        if (!wdone && __all_sync(0xffffffffu, done)) {
-            wdone = true;
-            if (lane == 0) atomicAdd(sm.done_warps, 1);
-        }
-        if (wdone && __shfl_sync(0xffffffffu, *done_warps, 0) >= C::kWarps) break;
-        // (the producer issues no further batch once every warp is done)
-        const int w = warp_wait(sm.full + s, (g / C::kStages) & 1u, done_warps, C::kWarps, sm.abort);
-        if (w != kWaitDone) {
-            if (w == kWaitTimeout && lane == 0) report(a.status, LSV2_ERR_TIMEOUT);
-            if (!wdone && lane == 0) atomicAdd(sm.done_warps, 1);
-            break;
-        }
-        if (!wdone) {
-            const float4 box = lane < kB ? sm.box(s)[lane] : make_float4(0.0f, 0.0f, -1.0f, -1.0f);
-            const bool keep = box.z >= 0.0f && box.x + box.z >= wx0 && box.x - box.z <= wx1 &&
-                              box.y + box.w >= wy0 && box.y - box.w <= wy1;
-            const unsigned char* recs = sm.rec(s);
-            // kept records in list order, kChunk at a time
-            uint32_t m = __ballot_sync(0xffffffffu, keep);
-            while (m != 0u) {
-                if (__all_sync(0xffffffffu, done)) break;
-                int sl[kChunk];
-#pragma unroll
-                for (int j = 0; j < kChunk; ++j) {
-                    sl[j] = m ? __ffs(m) - 1 : -1;
-                    m &= m - 1u;
-                }
-                // (A) alpha_j and 1 - alpha_j of the chunk's records at this pixel: independent
-                // of one another (instruction-level parallelism across the chunk)
-                float al[kChunk], om[kChunk], p2s[kChunk], os[kChunk];
-                bool high = false;
-#pragma unroll
-                for (int j = 0; j < kChunk; ++j) {
-                    const float* r = reinterpret_cast<const float*>(recs + max(sl[j], 0) * C::kRecBytes);
-                    const float4 g0 = *reinterpret_cast<const float4*>(r);
-                    const float4 ax = *reinterpret_cast<const float4*>(r + 4);
-                    const float4 axl = *reinterpret_cast<const float4*>(r + 8);
-                    const float p2 = eval_power2(g0, ax, axl, pxf, pyf);
-                    float ex2;
-                    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(ex2) : "f"(p2));
-                    const float alpha = fminf(kAlphaMax, axl.w * ex2);
-                    al[j] = (sl[j] >= 0 && p2 <= 0.0f && alpha >= kAlphaMin) ? alpha : 0.0f;
-                    om[j] = 1.0f - al[j];
-                    p2s[j] = p2;
-                    os[j] = axl.w;
-                    high = high || al[j] > 0.5f;
-                }
-                // 1 - alpha without cancellation where some pixel of the warp has alpha > 1/2
-                // (rare: the plain difference is exact to within alpha's own error otherwise)
-                if (__any_sync(0xffffffffu, high)) {
-#pragma unroll
-                    for (int j = 0; j < kChunk; ++j) om[j] = one_minus_alpha(al[j], os[j], p2s[j]);
-                }
-                // (B) front-to-back transmittance (Eq. 3): e_j = alpha_j T_j, the serial part;
-                // al[j] becomes e_j (0 where the pixel skips or has terminated)
-                uint32_t take_bits = 0;
-                int li = -1;
-#pragma unroll
-                for (int j = 0; j < kChunk; ++j) {
-                    const bool act = !done && al[j] > 0.0f;
-                    const float test_T = T * om[j];
-                    const bool stop = act && test_T < kTMin;
-                    const bool take = act && !stop;
-                    done = done || stop;
-                    al[j] = take ? al[j] * T : 0.0f;
-                    T = take ? test_T : T;
-                    take_bits |= take ? (1u << j) : 0u;
-                    li = take ? sl[j] : li;
-                }
-                if (li >= 0) last = b * kB + (uint32_t)li + 1u;
-                // (C) W_col += w e_j for the pairs of every record some pixel of the warp takes
-                const uint32_t used = __reduce_or_sync(0xffffffffu, take_bits);
-#pragma unroll
-                for (int j = 0; j < kChunk; ++j) {
-                    if (used & (1u << j)) {
-                        const float* r = reinterpret_cast<const float*>(recs + sl[j] * C::kRecBytes);
-                        const float* wr = r + 12;
-                        const uint32_t* cw = reinterpret_cast<const uint32_t*>(r + 12 + C::kPairs);
-                        float v[C::kPairs];
-                        float* addr[C::kPairs];
-#pragma unroll
-                        for (int p = 0; p < C::kPairs; ++p) {
-                            addr[p] = reinterpret_cast<float*>(acc_lane + cw[p]);
-                            v[p] = *addr[p];
-                        }
-#pragma unroll
-                        for (int p = 0; p < C::kPairs; ++p) v[p] = fmaf(al[j], wr[p], v[p]);
-#pragma unroll
-                        for (int p = 0; p < C::kPairs; ++p) *addr[p] = v[p];
-                    }
-                }
-            }
-        }
-        __syncwarp();
-        if (lane == 0) tc::mbar_arrive(tc::smem_u32(sm.empty + s));
-        consumed = b + 1;
-    }
-
-    if (inside) {
-        const size_t pix = (size_t)py * a.width + px;
-        a.final_T[pix] = T;
-        a.n_last[pix] = last;
-    }
-    __syncwarp();
-    // write this warp's 32 pixels: per row segment TW pixels x 64 floats (contiguous in HBM)
-    const size_t P = (size_t)a.width * a.height;
-#pragma unroll 1
-    for (int lev = 0; lev < LEVELS; ++lev) {
-        for (int q = lane; q < 32 * 16; q += 32) {
-            const int pl = q >> 4;  // pixel within the warp (row-major over the strip)
-            const int c4 = (q & 15) * 4;
-            const int gx = tx * TW + (pl % TW), gy = ty * TH + warp * kRows + pl / TW;
-            if (gx < a.width && gy < a.height) {
-                const float* col = acc + (lev * 64 + c4) * 33 + pl;
-                float4 val = make_float4(col[0], col[33], col[66], col[99]);
-                __stcs(reinterpret_cast<float4*>(a.coeff + ((size_t)lev * P + (size_t)gy * a.width + gx) * 64 + c4), val);
-            }
-        }
-    }
-    return consumed;
-}
-
-}  // namespace
-
-// One tile by all threads of the CTA: kWarps consumer warps and the producer warp (the last
-// one).  Precondition: the CTA's barriers are initialised, no tile is in progress and every
-// thread is synchronised.  Returns the number of batches the tile used (the caller adds it to
-// bbase).
-template <int LEVELS, int K, int TW, int TH, int BATCH>
-__device__ __forceinline__ uint32_t splat_tile(const TileJob& a, const SplatSmem<SplatCfg<LEVELS, K, TW, TH, BATCH>>& sm,
-                                               uint32_t bbase)
-{
-    using C = SplatCfg<LEVELS, K, TW, TH, BATCH>;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint32_t consumed = 0;
-    if (warp == C::kWarps)
-        splat_produce<C>(a, sm, lane, bbase);
-    else
-        consumed = splat_consume<C, LEVELS, K, TW, TH>(a, sm, warp, lane, bbase);
-    __syncthreads();
-    const uint32_t issued = *sm.issued;
-    if (threadIdx.x == 0) *sm.done_warps = 0;
-    // Warps that stopped early release the stages of the batches they skipped (every one of
-    // them lies within the last kStages batches, whose predecessors all warps released), so
-    // each stage's barriers stay in step for the next tile.
-    if (warp < C::kWarps && lane == 0 && !*reinterpret_cast<volatile int*>(sm.abort))
-        for (uint32_t b = consumed; b < issued; ++b) tc::mbar_arrive(tc::smem_u32(sm.empty + (int)((bbase + b) % C::kStages)));
-    return issued;
 }
 
 template <int LEVELS, int K, int TW, int TH>

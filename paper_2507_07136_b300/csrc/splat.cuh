@@ -38,7 +38,7 @@ struct SplatCfg {
     static constexpr int kBatch = BATCH != 0 ? BATCH : 32;
     static constexpr int kAccBytes = kWarps * kAccFloats * 4;
     static constexpr int kStageBytes = kBatch * (kRecBytes + 16);   // records + culling boxes
-    static constexpr int kFixedBytes = kAccBytes + 256;             // + barriers and flags
+    static constexpr int kFixedBytes = kAccBytes + 512;             // + barriers and flags
     static constexpr int kStagesFit = (232448 - 64 - kFixedBytes) / kStageBytes;
     static constexpr int kStages = kWarps >= 8 ? (kStagesFit < 8 ? kStagesFit : 8) : 4;
     static constexpr int kSmemBytes = kFixedBytes + kStages * kStageBytes;

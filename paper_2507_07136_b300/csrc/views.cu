@@ -118,7 +118,7 @@ extern "C" lsv2_status lsv2_query_views(int32_t V, const lsv2_camera* cams, int6
     if (n > 0 && (!means || !scales || !quats || !opacity || !idx || !w)) return LSV2_ERR_INVALID_ARGUMENT;
     if (!codebook || !text || capacity < 1 || capacity > 0x7FFFFFFFll) return LSV2_ERR_INVALID_ARGUMENT;
     if (L != 64 || !splat_supported(levels, K, L, cams[0].tile_w, cams[0].tile_h) || K != 4 ||
-        !query_tc_supported(Q * (1 + n_neg)) || D % 4 != 0 || D > 12288)
+        !query_tc_supported(Q, n_neg) || D % 4 != 0 || D > 12288)
         return LSV2_ERR_UNSUPPORTED;
     if (rel_dtype != LSV2_F32 && rel_dtype != LSV2_BF16) return LSV2_ERR_INVALID_ARGUMENT;
     const ViewsLayout Lo = views_layout(V, cams, n, levels, K, capacity, Q, n_neg);

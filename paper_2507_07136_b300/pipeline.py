@@ -115,6 +115,23 @@ class Frame:
                             _ptr(self.coeff), _ptr(self.final_T), _ptr(self.n_last), _ptr(self.status),
                             _stream(stream))
 
+    def render_fused(self, feat: torch.Tensor | None, text: torch.Tensor | None = None, rel: torch.Tensor | None = None,
+                     tau: float = 10.0, stream=None):
+        """Splat + decode (BF16 feat [levels, P, D], or None) + relevancy (rel [Q, levels, P]) in one kernel
+        (lsv2_render_fused); W is not written (self.coeff is left untouched)."""
+        s = self.scene
+        Q, n_neg = (0, 1) if text is None else (text.shape[0], text.shape[1] - 1)
+        need = L.lsv2_render_fused_workspace_bytes(s.n, s.levels, s.K, s.D, Q, n_neg)
+        if need == 0:
+            raise L.LSV2Error("lsv2_render_fused_workspace_bytes", 2)
+        if getattr(self, "fused_ws", None) is None or self.fused_ws.numel() < need:
+            self.fused_ws = torch.empty(need, dtype=torch.uint8, device=self.device)
+        rel_dt = L.LSV2_BF16 if (rel is not None and rel.dtype == torch.bfloat16) else L.LSV2_F32
+        L.lsv2_render_fused(self.ccam, s.n, self.proj, _ptr(self.tile_ranges), _ptr(self.gauss_ids), s.levels, s.K,
+                            L_CODEBOOK, _ptr(s.idx), _ptr(s.weights), _ptr(s.codebook), s.D, Q, n_neg, _ptr(text),
+                            float(tau), _ptr(self.fused_ws), need, _ptr(feat), _ptr(rel), rel_dt, _ptr(self.final_T),
+                            _ptr(self.n_last), _ptr(self.status), _stream(stream))
+
     def render(self, stream=None):
         self.project(stream)
         self.bin_sort(stream)

@@ -94,3 +94,15 @@ def test_query_tc_at_scale_sampled():
     ro = O.relevancy(O.decode(bl.out, sc.codebook), text, 10.0)
     ok = bl.margin > KNIFE_EDGE
     assert np.abs(rel[:, :, pix][:, :, ok] - ro[:, :, ok]).max() <= 1e-2
+
+
+@pytest.mark.parametrize("Q,n_neg", [(3, 1), (13, 2), (88, 4)])
+def test_query_tc_ragged_query_counts(Q, n_neg):
+    """Query counts that are not multiples of the 8-query chunk (padding columns), up to the
+    largest count that fits 512 TMEM columns at four negatives."""
+    sc = syn.make_scene(2000, 2, seed=12, mean_kind="uniform", mean_param=1.0, log_scale_mu=-3.2, log_scale_sigma=0.4)
+    cam = syn.orbit_camera(97, 71, 4.0)
+    text = syn.text_queries(syn.SEED + 2 + Q, Q, n_neg)
+    fr, rel = run_query(sc, cam, text)
+    rb = rounded_reference(fr.coeff.cpu().numpy(), sc.codebook, text, 10.0)
+    assert np.abs(rel - rb).max() <= 1e-4
