@@ -27,65 +27,94 @@
 
 namespace lsv2 {
 
+// One thread per (view, Gaussian): the record in registers (fully unrolled over the pairs, so no
+// local memory), written with 16-byte stores.
+template <int LEVELS, int K>
 __global__ void __launch_bounds__(256) pack_records_kernel(PackArgs a)
 {
+    constexpr int P = LEVELS * K;
+    constexpr int kRecFloats = record_bytes(P) / 4;
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // Gaussian
     if (g >= a.n) return;
     const int64_t o = (int64_t)blockIdx.y * a.n + g;                     // projection slot of this view
-    const int P = a.levels * a.K;
-    const int rec_floats = a.rec_bytes / 4;
-    float* rec = a.recs + (size_t)o * rec_floats;
+    float r[kRecFloats];
+#pragma unroll
+    for (int i = 0; i < kRecFloats; ++i) r[i] = 0.0f;
+    const float4 m = reinterpret_cast<const float4*>(a.xy)[o];
+    const float4 ax0 = reinterpret_cast<const float4*>(a.axes)[2 * o];
     const float4 ax1 = reinterpret_cast<const float4*>(a.axes)[2 * o + 1];
-    reinterpret_cast<float4*>(rec)[0] = reinterpret_cast<const float4*>(a.xy)[o];
-    reinterpret_cast<float4*>(rec)[1] = reinterpret_cast<const float4*>(a.axes)[2 * o];
-    reinterpret_cast<float4*>(rec)[2] = make_float4(ax1.x, ax1.y, ax1.z, reinterpret_cast<const float4*>(a.conic_o)[o].w);
-    // gather pairs, merge repeats of a column into the first occurrence
-    float wv[kMaxPairs];
-    int col[kMaxPairs];
-    bool real[kMaxPairs];
-    for (int lev = 0; lev < a.levels; ++lev)
-        for (int k = 0; k < a.K; ++k) {
-            const int p = lev * a.K + k;
-            const size_t src = ((size_t)g * a.levels + lev) * a.K + k;
-            const int ix = a.idx[src];
-            col[p] = lev * 64 + (ix < 64 ? ix : 0);
-            wv[p] = ix < 64 ? a.w[src] : 0.0f;
-            real[p] = ix < 64;
-            if (ix >= 64) report(a.status, LSV2_ERR_INVALID_ARGUMENT);
-            for (int p2 = lev * a.K; p2 < p; ++p2)
-                if (real[p] && real[p2] && col[p2] == col[p]) {
-                    wv[p2] += wv[p];
-                    wv[p] = 0.0f;
-                    real[p] = false;
-                    break;
-                }
-        }
-    // within each level: emptied pairs first (pointing at the level's first real column), real
-    // pairs last, so every level's K slots stay contiguous
-    uint32_t* cb = reinterpret_cast<uint32_t*>(rec + 12 + P);
-    for (int lev = 0; lev < a.levels; ++lev) {
-        const int p0 = lev * a.K;
-        int first_real = -1;
-        for (int p = p0; p < p0 + a.K; ++p)
-            if (real[p]) {
-                first_real = p;
-                break;
-            }
-        int slot = p0;
-        for (int p = p0; p < p0 + a.K; ++p)
-            if (!real[p]) {
-                rec[12 + slot] = 0.0f;
-                cb[slot] = (uint32_t)(first_real >= 0 ? col[first_real] : lev * 64) * 132u;
-                ++slot;
-            }
-        for (int p = p0; p < p0 + a.K; ++p)
-            if (real[p]) {
-                rec[12 + slot] = wv[p];
-                cb[slot] = (uint32_t)col[p] * 132u;
-                ++slot;
-            }
+    const float op = reinterpret_cast<const float4*>(a.conic_o)[o].w;
+    r[0] = m.x, r[1] = m.y, r[2] = m.z, r[3] = m.w;
+    r[4] = ax0.x, r[5] = ax0.y, r[6] = ax0.z, r[7] = ax0.w;
+    r[8] = ax1.x, r[9] = ax1.y, r[10] = ax1.z, r[11] = op;
+    // gather the pairs; merge repeats of a column within a level into the first occurrence
+    float wv[P];
+    int col[P];
+    bool real[P];
+    bool bad = false;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const int lev = p / K;
+        const size_t src = (size_t)g * P + p;
+        const int ix = a.idx[src];
+        bad |= ix >= 64;
+        col[p] = lev * 64 + (ix < 64 ? ix : 0);
+        wv[p] = ix < 64 ? a.w[src] : 0.0f;
+        real[p] = ix < 64;
     }
-    reinterpret_cast<float2*>(rec + rec_floats - 4)[0] = reinterpret_cast<const float2*>(a.extent)[o];
+    if (bad) report(a.status, LSV2_ERR_INVALID_ARGUMENT);
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        bool merged = false;
+#pragma unroll
+        for (int p2 = (p / K) * K; p2 < p; ++p2) {
+            const bool m2 = !merged && real[p] && real[p2] && col[p2] == col[p];
+            wv[p2] = m2 ? wv[p2] + wv[p] : wv[p2];
+            merged |= m2;
+        }
+        wv[p] = merged ? 0.0f : wv[p];
+        real[p] = real[p] && !merged;
+    }
+    // within each level: emptied pairs first (pointing at the level's first real column), real
+    // pairs last, so every level's K slots stay contiguous; slot of each pair, then a gather
+#pragma unroll
+    for (int lev = 0; lev < LEVELS; ++lev) {
+        int first_col = lev * 64, seen = 0, n_empty = 0;
+#pragma unroll
+        for (int k = K - 1; k >= 0; --k)
+            if (real[lev * K + k]) first_col = col[lev * K + k];
+#pragma unroll
+        for (int k = 0; k < K; ++k) n_empty += real[lev * K + k] ? 0 : 1;
+        int slot[K];
+        int e = 0;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const bool rk = real[lev * K + k];
+            slot[k] = rk ? n_empty + seen : e;
+            seen += rk ? 1 : 0;
+            e += rk ? 0 : 1;
+        }
+#pragma unroll
+        for (int s2 = 0; s2 < K; ++s2) {
+            float wsel = 0.0f;
+            uint32_t csel = 0;
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const bool hit = slot[k] == s2;
+                const bool rk = real[lev * K + k];
+                wsel = hit ? (rk ? wv[lev * K + k] : 0.0f) : wsel;
+                csel = hit ? (uint32_t)(rk ? col[lev * K + k] : first_col) * 132u : csel;
+            }
+            r[12 + lev * K + s2] = wsel;
+            r[12 + P + lev * K + s2] = __uint_as_float(csel);
+        }
+    }
+    const float2 ex = reinterpret_cast<const float2*>(a.extent)[o];
+    r[kRecFloats - 4] = ex.x;
+    r[kRecFloats - 3] = ex.y;
+    float4* dst = reinterpret_cast<float4*>(a.recs + (size_t)o * kRecFloats);
+#pragma unroll
+    for (int v = 0; v < kRecFloats / 4; ++v) dst[v] = make_float4(r[4 * v], r[4 * v + 1], r[4 * v + 2], r[4 * v + 3]);
 }
 
 template <int LEVELS, int K, int TW, int TH>
@@ -219,7 +248,14 @@ cudaError_t launch_pack(const PackArgs& a, cudaStream_t stream, int V)
 {
     if (a.n == 0 || V == 0) return cudaSuccess;
     const int threads = 256;
-    pack_records_kernel<<<dim3((unsigned)((a.n + threads - 1) / threads), (unsigned)V), threads, 0, stream>>>(a);
+    const dim3 grid((unsigned)((a.n + threads - 1) / threads), (unsigned)V);
+    if (a.levels == 3 && a.K == 4) pack_records_kernel<3, 4><<<grid, threads, 0, stream>>>(a);
+    else if (a.levels == 2 && a.K == 4) pack_records_kernel<2, 4><<<grid, threads, 0, stream>>>(a);
+    else if (a.levels == 1 && a.K == 2) pack_records_kernel<1, 2><<<grid, threads, 0, stream>>>(a);
+    else if (a.levels == 1 && a.K == 4) pack_records_kernel<1, 4><<<grid, threads, 0, stream>>>(a);
+    else if (a.levels == 1 && a.K == 6) pack_records_kernel<1, 6><<<grid, threads, 0, stream>>>(a);
+    else if (a.levels == 1 && a.K == 8) pack_records_kernel<1, 8><<<grid, threads, 0, stream>>>(a);
+    else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 
