@@ -158,6 +158,52 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- speed ablation
+def ablation_section(dev, reps: int = 10):
+    """The paper's speed ablation on B300 (Table 9 and the K ablation): at 300k Gaussians, three
+    levels, 1440x1080, the splat (record packing + blend) with K = 2, 4, 6, 8 nonzeros per level,
+    and the dense blend over all 64 coefficients per level ("Sparse, not Efficient") at K = 4.
+    Same Gaussians for every K; L2 flushed between repetitions."""
+    import torch
+    import lsv2_synth as syn
+    from paper_2507_07136_b300.pipeline import DeviceScene, Frame
+
+    _, cam, _ = syn.at_scale()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+            flush.fill_(1)
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(reps):
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record()
+            fn()
+            e.record()
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            tot += s.elapsed_time(e)
+        return tot / reps
+
+    out = {"workload": "300k Gaussians, 3 levels, L=64, 1440x1080 (the at-scale frame)", "splat_ms": {}}
+    for K in (2, 4, 6, 8):
+        sc = syn.make_scene(300_000, 3, K=K)
+        fr = Frame(DeviceScene.from_numpy(sc, device=dev), cam, device=dev)
+        fr.render()
+        fr.check()
+        out["splat_ms"][str(K)] = timed(fr.splat)
+        if K == 4:
+            out["dense_ms"] = timed(fr.splat_dense)
+        fr.check()
+        del fr
+        torch.cuda.empty_cache()
+    out["dense_over_sparse"] = out["dense_ms"] / out["splat_ms"]["4"]
+    out["paper_a100_ms"] = {"dense (Sparse, not Efficient)": 5.3, "sparse (Efficient)": 2.0}
+    return out
+
+
 # ----------------------------------------------------------------------------- batched views
 def batched_section(dev, reps: int = 5):
     """500,000 Gaussians, three levels, 16 views (4 each at 1440x1080, 960x720, 640x480, 320x240),
@@ -228,6 +274,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32-path", action="store_true", help="skip the plain FP32 comparison measurement")
     ap.add_argument("--no-batched", action="store_true", help="skip the 16-view x 64-query batched measurement")
+    ap.add_argument("--no-ablation", action="store_true", help="skip the sparse/dense and K speed ablation")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)
@@ -324,6 +371,27 @@ def main():
         fns["decode"] = lambda: frame.decode(F, codebook=cb16)
         fns["query"] = lambda: frame.query(text_d, rel, compute=Lb.LSV2_BF16)
 
+    # ---- splat + decode + query in one kernel (lsv2_render_fused): W never leaves the SM ----
+    fused_ms = None
+    if not args.no_fp32_path:
+        for _ in range(3):
+            frame.render_fused(F, text_d, rel)
+            flush.fill_(1)
+        torch.cuda.synchronize()
+        tot = 0.0
+        n_f = max(3, args.steps // 4)
+        for _ in range(n_f):
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            frame.render_fused(F, text_d, rel)
+            s1.record(stream)
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            tot += s0.elapsed_time(s1)
+        frame.check()
+        fused_ms = tot / n_f
+        frame.splat()   # restore the coefficient map the timed step left
+
     # ---- end to end through the C ABI with host buffers ----
     text_h = torch.as_tensor(text).pin_memory()
     rel_h = torch.empty(rel.shape, dtype=rel.dtype).pin_memory()
@@ -380,6 +448,8 @@ def main():
             "roofline": dict(roofs[dom]),
             "rooflines": roofs,
             "fp32_path": fp32,
+            "fused_splat_decode_query_ms": fused_ms,
+            "split_splat_decode_query_ms": stage_ms["splat"] + stage_ms["decode"] + stage_ms["query"],
             "e2e": {"value": world * 1e3 / e2e_ms, "unit": "frames/s", "h2d_bytes_per_step": text_h.numel() * 4,
                     "d2h_bytes_per_step": rel_h.numel() * 4},
             "gpu_launches": gpu_launches,
@@ -389,6 +459,9 @@ def main():
         del F
         torch.cuda.empty_cache()
         line["batched"] = batched_section(dev)
+    if not args.no_ablation and world == 1:
+        torch.cuda.empty_cache()
+        line["ablation"] = ablation_section(dev)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()

@@ -248,6 +248,24 @@ lsv2_status lsv2_query_views(int32_t V, const lsv2_camera* cams, int64_t n, cons
                              lsv2_dtype rel_dtype, int64_t* dev_num_instances,
                              int32_t* dev_status, void* stream);
 
+/* Workspace for lsv2_splat_coeffs_dense (one dense record per Gaussian). 0 if unsupported. */
+size_t lsv2_splat_dense_workspace_bytes(int64_t n, int32_t levels);
+
+/* The blend of lsv2_splat_coeffs WITHOUT the sparse splatting of Sec. 3.4: every Gaussian
+ * carries its full 64-entry coefficient vector per level (the K pairs scattered, zeros
+ * elsewhere) and every contributing Gaussian updates all 64 coefficients of every level -- the
+ * "Sparse, not Efficient" configuration of the paper's speed ablation (Table 9), kept to measure
+ * what the sparse splatting saves.  Blending zeros does not alter the result (Sec. 3.4), so the
+ * outputs equal lsv2_splat_coeffs' bit for bit.  Arguments as for lsv2_splat_coeffs;
+ * workspace lsv2_splat_dense_workspace_bytes(n, levels).  Supported: levels 1 or 3, L = 64,
+ * 16 x 16 tiles. */
+lsv2_status lsv2_splat_coeffs_dense(const lsv2_camera* cam, int64_t n, const lsv2_proj* proj,
+                                    const uint32_t* tile_ranges, const uint32_t* gauss_ids,
+                                    int32_t levels, int32_t K, int32_t L, const uint8_t* idx,
+                                    const float* w, void* workspace, size_t workspace_bytes,
+                                    float* coeff, float* final_T, uint32_t* n_last,
+                                    int32_t* dev_status, void* stream);
+
 /* Workspace for lsv2_render_fused (per-Gaussian records, the BF16 codebook and query operands).
  * 0 for an unsupported configuration. */
 size_t lsv2_render_fused_workspace_bytes(int64_t n, int32_t levels, int32_t K, int32_t D, int32_t Q,

@@ -46,6 +46,8 @@ _SIGS = {
     "lsv2_bin_sort": ([P, I64, P, P, SZ, P, I64, P, P, P, P], I32),
     "lsv2_splat_workspace_bytes": ([I64, I32, I32], SZ),
     "lsv2_splat_coeffs": ([P, I64, P, P, P, I32, I32, I32, P, P, P, SZ, P, P, P, P, P], I32),
+    "lsv2_splat_dense_workspace_bytes": ([I64, I32], SZ),
+    "lsv2_splat_coeffs_dense": ([P, I64, P, P, P, I32, I32, I32, P, P, P, SZ, P, P, P, P, P], I32),
     "lsv2_splat_coeffs_noalloc": ([P, I64, P, P, P, I32, I32, I32, P, P, P, P, P, P, P], I32),
     "lsv2_decode": ([I32, I64, I32, I32, P, I32, P, I32, P, I32, P, P], I32),
     "lsv2_query_workspace_bytes": ([I32, I32, I32, I32], SZ),
@@ -199,3 +201,13 @@ def lsv2_render_fused(cam, n, proj, tile_ranges, gauss_ids, levels, K, L, idx, w
                       ws_bytes, feat, rel, rel_dtype, final_T, n_last, dev_status, stream):
     call("lsv2_render_fused", C.byref(cam), n, C.byref(proj), tile_ranges, gauss_ids, levels, K, L, idx, w, codebook, D,
          Q, n_neg, text, tau, ws, ws_bytes, feat, rel, rel_dtype, final_T, n_last, dev_status, stream)
+
+
+def lsv2_splat_dense_workspace_bytes(n, levels) -> int:
+    return lib().lsv2_splat_dense_workspace_bytes(n, levels)
+
+
+def lsv2_splat_coeffs_dense(cam, n, proj, tile_ranges, gauss_ids, levels, K, L, idx, w, ws, ws_bytes, coeff, final_T,
+                            n_last, dev_status, stream):
+    call("lsv2_splat_coeffs_dense", C.byref(cam), n, C.byref(proj), tile_ranges, gauss_ids, levels, K, L, idx, w, ws,
+         ws_bytes, coeff, final_T, n_last, dev_status, stream)

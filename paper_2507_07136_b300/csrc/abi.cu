@@ -144,6 +144,34 @@ lsv2_status lsv2_splat_coeffs(const lsv2_camera* cam, int64_t n, const lsv2_proj
     return cuda_status(launch_splat(levels, K, sa, S(stream)));
 }
 
+size_t lsv2_splat_dense_workspace_bytes(int64_t n, int32_t levels)
+{
+    if (n < 0 || (levels != 1 && levels != 3)) return 0;
+    return align256((size_t)n * (size_t)splat_dense_record_bytes(levels));
+}
+
+lsv2_status lsv2_splat_coeffs_dense(const lsv2_camera* cam, int64_t n, const lsv2_proj* proj,
+                                    const uint32_t* tile_ranges, const uint32_t* gauss_ids, int32_t levels, int32_t K,
+                                    int32_t L, const uint8_t* idx, const float* w, void* workspace,
+                                    size_t workspace_bytes, float* coeff, float* final_T, uint32_t* n_last,
+                                    int32_t* dev_status, void* stream)
+{
+    if (!camera_ok(cam) || n < 0 || !proj_ok(proj) || !tile_ranges || !gauss_ids || !coeff || !final_T || !n_last ||
+        K < 1)
+        return LSV2_ERR_INVALID_ARGUMENT;
+    if (n > 0 && (!idx || !w)) return LSV2_ERR_INVALID_ARGUMENT;
+    if (!splat_dense_supported(levels, L, cam->tile_w, cam->tile_h)) return LSV2_ERR_UNSUPPORTED;
+    if (!aligned16(coeff) || !workspace || !aligned16(workspace) ||
+        workspace_bytes < lsv2_splat_dense_workspace_bytes(n, levels))
+        return LSV2_ERR_INVALID_ARGUMENT;
+    PackArgs pa{n, levels, K, splat_dense_record_bytes(levels), proj->xy, proj->axes, proj->conic_o, proj->extent,
+                idx, w, static_cast<float*>(workspace), dev_status};
+    cudaError_t e = launch_pack_dense(pa, S(stream));
+    if (e != cudaSuccess) return LSV2_ERR_CUDA;
+    SplatArgs sa{*cam, tile_ranges, gauss_ids, static_cast<const float*>(workspace), coeff, final_T, n_last, dev_status};
+    return cuda_status(launch_splat_dense(levels, sa, S(stream)));
+}
+
 lsv2_status lsv2_decode(int32_t levels, int64_t P, int32_t L, int32_t D, const void* coeff, lsv2_dtype coeff_dtype,
                         const void* codebook, lsv2_dtype codebook_dtype, void* feat, lsv2_dtype out_dtype,
                         int32_t* dev_status, void* stream)

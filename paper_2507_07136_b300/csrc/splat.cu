@@ -117,10 +117,40 @@ __global__ void __launch_bounds__(256) pack_records_kernel(PackArgs a)
     for (int v = 0; v < kRecFloats / 4; ++v) dst[v] = make_float4(r[4 * v], r[4 * v + 1], r[4 * v + 2], r[4 * v + 3]);
 }
 
-template <int LEVELS, int K, int TW, int TH>
+// Dense records for the comparison blend: the header of the sparse record, then every level's 64
+// coefficients (the K pairs scattered, repeats summed in pair order, zeros elsewhere).
+template <int LEVELS>
+__global__ void __launch_bounds__(256) pack_dense_kernel(PackArgs a)
+{
+    constexpr int kRecFloats = dense_record_bytes(LEVELS) / 4;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= a.n) return;
+    float* rec = a.recs + (size_t)g * kRecFloats;
+    const float4 m = reinterpret_cast<const float4*>(a.xy)[g];
+    const float4 ax0 = reinterpret_cast<const float4*>(a.axes)[2 * g];
+    const float4 ax1 = reinterpret_cast<const float4*>(a.axes)[2 * g + 1];
+    const float op = reinterpret_cast<const float4*>(a.conic_o)[g].w;
+    reinterpret_cast<float4*>(rec)[0] = m;
+    reinterpret_cast<float4*>(rec)[1] = ax0;
+    reinterpret_cast<float4*>(rec)[2] = make_float4(ax1.x, ax1.y, ax1.z, op);
+    for (int i = 12; i < kRecFloats; i += 4) *reinterpret_cast<float4*>(rec + i) = make_float4(0.f, 0.f, 0.f, 0.f);
+    bool bad = false;
+    for (int lev = 0; lev < LEVELS; ++lev)
+        for (int k = 0; k < a.K; ++k) {
+            const size_t src = ((size_t)g * LEVELS + lev) * a.K + k;
+            const int ix = a.idx[src];
+            bad |= ix >= 64;
+            if (ix < 64) rec[12 + lev * 64 + ix] += a.w[src];
+        }
+    if (bad) report(a.status, LSV2_ERR_INVALID_ARGUMENT);
+    const float2 ex = reinterpret_cast<const float2*>(a.extent)[g];
+    reinterpret_cast<float4*>(rec + kRecFloats - 4)[0] = make_float4(ex.x, ex.y, 0.f, 0.f);
+}
+
+template <int LEVELS, int K, int TW, int TH, bool DENSE = false>
 __global__ void __launch_bounds__(TW* TH + 32, 1) splat_kernel(SplatArgs a)
 {
-    using C = SplatCfg<LEVELS, K, TW, TH, 0>;
+    using C = SplatCfg<LEVELS, K, TW, TH, 0, DENSE>;
     extern __shared__ __align__(16) unsigned char smem[];
     const SplatSmem<C> sm(smem);
     if (threadIdx.x == 0) {
@@ -133,7 +163,7 @@ __global__ void __launch_bounds__(TW* TH + 32, 1) splat_kernel(SplatArgs a)
     const int tile = blockIdx.x;
     TileJob j{a.cam.width, a.cam.height, (a.cam.width + TW - 1) / TW, tile, a.tile_ranges[2 * tile],
               a.tile_ranges[2 * tile + 1], a.gauss_ids, a.recs, a.coeff, a.final_T, a.n_last, a.status};
-    (void)splat_tile<LEVELS, K, TW, TH, 0>(j, sm, 0u);
+    (void)splat_tile<LEVELS, K, TW, TH, 0, true, DENSE>(j, sm, 0u);
 }
 
 // Persistent over the (view, tile) work items of several views: each CTA takes the next global
@@ -169,12 +199,12 @@ __global__ void __launch_bounds__(TW* TH + 32, 1) splat_views_kernel(SplatViewsA
 
 namespace {
 
-template <int LEVELS, int K, int TW, int TH>
+template <int LEVELS, int K, int TW, int TH, bool DENSE = false>
 cudaError_t launch_t(const SplatArgs& a, cudaStream_t stream)
 {
-    using C = SplatCfg<LEVELS, K, TW, TH>;
+    using C = SplatCfg<LEVELS, K, TW, TH, 0, DENSE>;
     static_assert(C::kSmemBytes <= 232448, "shared memory budget");
-    auto kern = splat_kernel<LEVELS, K, TW, TH>;
+    auto kern = splat_kernel<LEVELS, K, TW, TH, DENSE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
     if (e != cudaSuccess) return e;
     const int GX = (a.cam.width + TW - 1) / TW, GY = (a.cam.height + TH - 1) / TH;
@@ -237,8 +267,33 @@ bool splat_supported(int levels, int K, int L, int tw, int th)
     const bool tile_ok = (tw == 16 && th == 16) || (tw == 8 && th == 8) || (tw == 32 && th == 8);
     if (!tile_ok) return false;
     if (levels == 1) return K == 2 || K == 4 || K == 6 || K == 8;
-    if (levels == 2 || levels == 3) return K == 4;
+    if (levels == 2) return K == 4;
+    if (levels == 3) return K == 4 || (tw == 16 && th == 16 && (K == 2 || K == 6 || K == 8));
     return false;
+}
+
+bool splat_dense_supported(int levels, int L, int tw, int th)
+{
+    return L == 64 && (levels == 1 || levels == 3) && tw == 16 && th == 16;
+}
+
+int splat_dense_record_bytes(int levels) { return dense_record_bytes(levels); }
+
+cudaError_t launch_pack_dense(const PackArgs& a, cudaStream_t stream)
+{
+    if (a.n == 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((a.n + 255) / 256);
+    if (a.levels == 3) pack_dense_kernel<3><<<blocks, 256, 0, stream>>>(a);
+    else if (a.levels == 1) pack_dense_kernel<1><<<blocks, 256, 0, stream>>>(a);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_splat_dense(int levels, const SplatArgs& a, cudaStream_t stream)
+{
+    if (levels == 3) return launch_t<3, 4, 16, 16, true>(a, stream);
+    if (levels == 1) return launch_t<1, 4, 16, 16, true>(a, stream);
+    return cudaErrorInvalidValue;
 }
 
 int splat_record_bytes(int levels, int K) { return record_bytes(levels * K); }
@@ -250,6 +305,9 @@ cudaError_t launch_pack(const PackArgs& a, cudaStream_t stream, int V)
     const int threads = 256;
     const dim3 grid((unsigned)((a.n + threads - 1) / threads), (unsigned)V);
     if (a.levels == 3 && a.K == 4) pack_records_kernel<3, 4><<<grid, threads, 0, stream>>>(a);
+    else if (a.levels == 3 && a.K == 2) pack_records_kernel<3, 2><<<grid, threads, 0, stream>>>(a);
+    else if (a.levels == 3 && a.K == 6) pack_records_kernel<3, 6><<<grid, threads, 0, stream>>>(a);
+    else if (a.levels == 3 && a.K == 8) pack_records_kernel<3, 8><<<grid, threads, 0, stream>>>(a);
     else if (a.levels == 2 && a.K == 4) pack_records_kernel<2, 4><<<grid, threads, 0, stream>>>(a);
     else if (a.levels == 1 && a.K == 2) pack_records_kernel<1, 2><<<grid, threads, 0, stream>>>(a);
     else if (a.levels == 1 && a.K == 4) pack_records_kernel<1, 4><<<grid, threads, 0, stream>>>(a);
@@ -280,6 +338,11 @@ cudaError_t launch_splat(int levels, int K, const SplatArgs& a, cudaStream_t str
     }
     if (levels == 2 && K == 4) return launch_tile<2, 4>(a, stream);
     if (levels == 3 && K == 4) return launch_tile<3, 4>(a, stream);
+    if (levels == 3 && a.cam.tile_w == 16 && a.cam.tile_h == 16) {   // K sweep at three levels
+        if (K == 2) return launch_t<3, 2, 16, 16>(a, stream);
+        if (K == 6) return launch_t<3, 6, 16, 16>(a, stream);
+        if (K == 8) return launch_t<3, 8, 16, 16>(a, stream);
+    }
     return cudaErrorInvalidValue;
 }
 

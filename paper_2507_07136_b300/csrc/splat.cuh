@@ -21,11 +21,17 @@ constexpr int kMaxPairs = 24;  // levels * K
 // wins.
 __host__ __device__ constexpr int smem_record_bytes(int P) { return ((48 + 8 * P) + 15) / 16 * 16; }
 __host__ __device__ constexpr int record_bytes(int P) { return smem_record_bytes(P) + 16; }
+// Dense record (the non-sparse baseline: every level's 64 coefficients, zeros included):
+//   floats [0, 12) as above, floats [12, 12 + 64 levels) dense coefficients, last 16 bytes extents.
+__host__ __device__ constexpr int dense_record_bytes(int levels) { return ((48 + 256 * levels) + 15) / 16 * 16 + 16; }
 
 // One CTA per tile: kWarps consumer warps (one pixel per lane, 32 pixels per warp) and one
 // producer warp that gathers the tile's records, BATCH at a time, into a ring of kStages
-// shared-memory stages with bulk async copies.  BATCH: 16 or 32 records per stage (0 = 32).
-template <int LEVELS, int K, int TW, int TH, int BATCH = 0>
+// shared-memory stages with bulk async copies.  BATCH: 16 or 32 records per stage (0 = 32, or
+// 16 for dense records).  DENSE: records carry all 64 coefficients of each level and every
+// contributing Gaussian updates all 64 columns of each level (the blend without the sparse
+// splatting, kept for comparison).
+template <int LEVELS, int K, int TW, int TH, int BATCH = 0, bool DENSE = false>
 struct SplatCfg {
     static constexpr int kPixels = TW * TH;
     static constexpr int kWarps = kPixels / 32;      // consumer warps
@@ -33,9 +39,10 @@ struct SplatCfg {
     static constexpr int kPairs = LEVELS * K;        // pairs in a record
     static constexpr int kCols = LEVELS * 64;
     static constexpr int kAccFloats = (kCols * 33 + 3) / 4 * 4;
-    static constexpr int kRecBytes = record_bytes(kPairs);
+    static constexpr bool kDense = DENSE;
+    static constexpr int kRecBytes = DENSE ? dense_record_bytes(LEVELS) : record_bytes(kPairs);
     static constexpr int kRecFloats = kRecBytes / 4;
-    static constexpr int kBatch = BATCH != 0 ? BATCH : 32;
+    static constexpr int kBatch = BATCH != 0 ? BATCH : (DENSE ? 16 : 32);
     static constexpr int kAccBytes = kWarps * kAccFloats * 4;
     static constexpr int kStageBytes = kBatch * (kRecBytes + 16);   // records + culling boxes
     static constexpr int kFixedBytes = kAccBytes + 512;             // + barriers and flags
@@ -95,6 +102,11 @@ struct SplatViewsArgs {
 };
 
 bool splat_supported(int levels, int K, int L, int tw, int th);
+// The dense-coefficient baseline: levels 1 or 3, 16 x 16 tiles.
+bool splat_dense_supported(int levels, int L, int tw, int th);
+int splat_dense_record_bytes(int levels);
+cudaError_t launch_pack_dense(const PackArgs& a, cudaStream_t stream);
+cudaError_t launch_splat_dense(int levels, const SplatArgs& a, cudaStream_t stream);
 // batch: records staged per warp (16 or 32; 0 = default).
 cudaError_t launch_splat_views(int levels, int K, int tw, int th, int batch, const SplatViewsArgs& a, int num_sms,
                                cudaStream_t stream);

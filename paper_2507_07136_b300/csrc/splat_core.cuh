@@ -249,18 +249,31 @@ __device__ uint32_t splat_consume(const TileJob& a, const SplatSmem<C>& sm, int 
                     if (used & (1u << j)) {
                         const float* r = reinterpret_cast<const float*>(recs + sl[j] * C::kRecBytes);
                         const float* wr = r + 12;
-                        const uint32_t* cw = reinterpret_cast<const uint32_t*>(r + 12 + C::kPairs);
-                        float v[C::kPairs];
-                        float* addr[C::kPairs];
+                        if constexpr (C::kDense) {
+                            // every column of every level (zeros included)
+#pragma unroll 4
+                            for (int c4 = 0; c4 < C::kCols; c4 += 4) {
+                                const float4 w4 = *reinterpret_cast<const float4*>(wr + c4);
+                                float* a0 = acc + c4 * 33 + lane;
+                                a0[0] = fmaf(al[j], w4.x, a0[0]);
+                                a0[33] = fmaf(al[j], w4.y, a0[33]);
+                                a0[66] = fmaf(al[j], w4.z, a0[66]);
+                                a0[99] = fmaf(al[j], w4.w, a0[99]);
+                            }
+                        } else {
+                            const uint32_t* cw = reinterpret_cast<const uint32_t*>(r + 12 + C::kPairs);
+                            float v[C::kPairs];
+                            float* addr[C::kPairs];
 #pragma unroll
-                        for (int p = 0; p < C::kPairs; ++p) {
-                            addr[p] = reinterpret_cast<float*>(acc_lane + cw[p]);
-                            v[p] = *addr[p];
+                            for (int p = 0; p < C::kPairs; ++p) {
+                                addr[p] = reinterpret_cast<float*>(acc_lane + cw[p]);
+                                v[p] = *addr[p];
+                            }
+#pragma unroll
+                            for (int p = 0; p < C::kPairs; ++p) v[p] = fmaf(al[j], wr[p], v[p]);
+#pragma unroll
+                            for (int p = 0; p < C::kPairs; ++p) *addr[p] = v[p];
                         }
-#pragma unroll
-                        for (int p = 0; p < C::kPairs; ++p) v[p] = fmaf(al[j], wr[p], v[p]);
-#pragma unroll
-                        for (int p = 0; p < C::kPairs; ++p) *addr[p] = v[p];
                     }
                 }
             }
@@ -299,11 +312,12 @@ __device__ uint32_t splat_consume(const TileJob& a, const SplatSmem<C>& sm, int 
 // one).  Precondition: the CTA's barriers are initialised, no tile is in progress and every
 // thread is synchronised.  Returns the number of batches the tile used (the caller adds it to
 // bbase).
-template <int LEVELS, int K, int TW, int TH, int BATCH, bool kWriteCoeff = true>
-__device__ __forceinline__ uint32_t splat_tile(const TileJob& a, const SplatSmem<SplatCfg<LEVELS, K, TW, TH, BATCH>>& sm,
+template <int LEVELS, int K, int TW, int TH, int BATCH, bool kWriteCoeff = true, bool DENSE = false>
+__device__ __forceinline__ uint32_t splat_tile(const TileJob& a,
+                                               const SplatSmem<SplatCfg<LEVELS, K, TW, TH, BATCH, DENSE>>& sm,
                                                uint32_t bbase)
 {
-    using C = SplatCfg<LEVELS, K, TW, TH, BATCH>;
+    using C = SplatCfg<LEVELS, K, TW, TH, BATCH, DENSE>;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint32_t consumed = 0;
     if (warp == C::kWarps)

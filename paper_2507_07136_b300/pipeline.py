@@ -115,6 +115,20 @@ class Frame:
                             _ptr(self.coeff), _ptr(self.final_T), _ptr(self.n_last), _ptr(self.status),
                             _stream(stream))
 
+    def splat_dense(self, stream=None):
+        """The blend without the sparse splatting (dense 64-entry coefficients per level;
+        lsv2_splat_coeffs_dense): same outputs as splat(), for timing the comparison."""
+        s = self.scene
+        need = L.lsv2_splat_dense_workspace_bytes(s.n, s.levels)
+        if need == 0:
+            raise L.LSV2Error("lsv2_splat_dense_workspace_bytes", 2)
+        if getattr(self, "dense_ws", None) is None or self.dense_ws.numel() < need:
+            self.dense_ws = torch.empty(need, dtype=torch.uint8, device=self.device)
+        L.lsv2_splat_coeffs_dense(self.ccam, s.n, self.proj, _ptr(self.tile_ranges), _ptr(self.gauss_ids), s.levels,
+                                  s.K, L_CODEBOOK, _ptr(s.idx), _ptr(s.weights), _ptr(self.dense_ws), need,
+                                  _ptr(self.coeff), _ptr(self.final_T), _ptr(self.n_last), _ptr(self.status),
+                                  _stream(stream))
+
     def render_fused(self, feat: torch.Tensor | None, text: torch.Tensor | None = None, rel: torch.Tensor | None = None,
                      tau: float = 10.0, stream=None):
         """Splat + decode (BF16 feat [levels, P, D], or None) + relevancy (rel [Q, levels, P]) in one kernel
