@@ -205,17 +205,24 @@ def ablation_section(dev, reps: int = 10):
 
 
 # ----------------------------------------------------------------------------- batched views
-def batched_section(dev, reps: int = 5):
+def batched_section(dev, reps: int = 5, rank: int = 0, world: int = 1):
     """500,000 Gaussians, three levels, 16 views (4 each at 1440x1080, 960x720, 640x480, 320x240),
     64 queries with four negatives each: one CUDA-graph launch of lsv2_query_views (tile shape and
-    staging batch from the autotuner) against 16 sequential single-view pipelines."""
+    staging batch from the autotuner) against sequential single-view pipelines.  With several
+    ranks the views are sharded by pixel count (no collective on the data path) and the batch time
+    is the maximum over ranks."""
     import torch
+    import torch.distributed as dist
     import lsv2_synth as syn
     from paper_2507_07136_b300 import _lib as Lb
     from paper_2507_07136_b300.pipeline import DeviceScene, Frame
+    from paper_2507_07136_b300.shard import rank_views
     from paper_2507_07136_b300.views import ViewsBatch, autotune
 
-    sc, cams, text = syn.batched()
+    sc, all_cams, text = syn.batched()
+    n_views = len(all_cams)
+    mine = rank_views([c.width * c.height for c in all_cams], rank, world)
+    cams = [all_cams[v] for v in mine]
     scene = DeviceScene.from_numpy(sc, device=dev)
     t = torch.as_tensor(text, device=dev)
     tile, batch = autotune(scene, cams, t, reps=3)
@@ -255,7 +262,14 @@ def batched_section(dev, reps: int = 5):
     for f in frames:
         f.check()
     seq_ms = s.elapsed_time(e) / reps
-    nq = len(cams) * text.shape[0]
+    if world > 1:
+        tm = torch.tensor([batched_ms, seq_ms], device=dev)
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        batched_ms, seq_ms = float(tm[0].item()), float(tm[1].item())
+        cnt = torch.tensor([inst, pix, rel_elems], dtype=torch.int64, device=dev)
+        dist.all_reduce(cnt)
+        inst, pix, rel_elems = (int(v) for v in cnt.tolist())
+    nq = n_views * text.shape[0]
     return {"workload": "500k Gaussians, 3 levels, 16 views (4 each 1440x1080, 960x720, 640x480, 320x240), "
                         "64 queries x (1 + 4 negatives)",
             "queries_per_s": nq * 1e3 / batched_ms, "ms_per_batch": batched_ms,
@@ -458,7 +472,7 @@ def main():
     if not args.no_batched:
         del F
         torch.cuda.empty_cache()
-        line["batched"] = batched_section(dev)
+        line["batched"] = batched_section(dev, rank=rank, world=world)
     if not args.no_ablation and world == 1:
         torch.cuda.empty_cache()
         line["ablation"] = ablation_section(dev)
