@@ -21,7 +21,6 @@ namespace {
 
 constexpr int kM = 128;
 constexpr int kK = 64;
-constexpr int kThreads = 256;
 
 struct QueryTcArgs {
     int Q, n_neg, Qp, npad;        // Qp = Q rounded up to 8; npad = 64 + (1 + n_neg) Qp rounded up to 16
@@ -56,11 +55,12 @@ __host__ __device__ constexpr uint32_t tmem_cols(int npad)
 }
 
 // FP32 tile (row-major, 64 floats per row, in the ring) -> BF16 swizzled K-major operand.
+template <int NT>
 __device__ __forceinline__ void convert_w(const float* src, int valid_rows, uint8_t* sA)
 {
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const int c = threadIdx.x + kThreads * j, row = c >> 4, c4 = c & 15;
+    for (int j = 0; j < 2048 / NT; ++j) {
+        const int c = threadIdx.x + NT * j, row = c >> 4, c4 = c & 15;
         const float4 v = row < valid_rows ? *reinterpret_cast<const float4*>(src + row * kK + c4 * 4)
                                           : make_float4(0.f, 0.f, 0.f, 0.f);
         *reinterpret_cast<uint2*>(sA + tc::sw128(row, c4 * 4)) =
@@ -68,8 +68,12 @@ __device__ __forceinline__ void convert_w(const float* src, int valid_rows, uint
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 2) query_tc_kernel(QueryTcArgs a)
+// NT threads: 256 when two CTAs share an SM (TMEM allows), else 512, so that the epilogue of the
+// one resident CTA has 16 warps (four per TMEM lane quarter).
+template <int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) query_tc_kernel(QueryTcArgs a)
 {
+    constexpr int kThreads = NT;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     float* ring = reinterpret_cast<float*>(smem);
@@ -137,12 +141,13 @@ __global__ void __launch_bounds__(kThreads, 2) query_tc_kernel(QueryTcArgs a)
     if (tid == 0)
         for (int64_t i = 0; i < kStages && i < my_tiles; ++i) issue(i);
     const uint32_t tmem = *tslot;
-    const int q4 = warp & 3, half = warp >> 2;
+    const int q4 = warp & 3, part = warp >> 2;   // TMEM lane quarter; share of the query chunks
     const int row = q4 * 32 + lane;
     const uint32_t trow = tmem + ((uint32_t)(q4 * 32) << 16);
-    // 8-query chunks handled by this warp: half 0 -> [0, ch), half 1 -> [ch, nch)
-    const int nch = a.Qp / 8, ch = (nch + 1) / 2;
-    const int cb = half ? ch : 0, ce = half ? nch : ch;
+    // 8-query chunks handled by this warp: contiguous shares of the NT / 128 warps of a quarter
+    constexpr int kParts = NT / 128;
+    const int nch = a.Qp / 8, ch = (nch + kParts - 1) / kParts;
+    const int cb = part * ch < nch ? part * ch : nch, ce = (part + 1) * ch < nch ? (part + 1) * ch : nch;
     uint32_t phase = 0;
     bool failed = false;
 
@@ -158,7 +163,7 @@ __global__ void __launch_bounds__(kThreads, 2) query_tc_kernel(QueryTcArgs a)
             break;
         }
         const int valid = Pv - p0 < kM ? (int)(Pv - p0) : kM;
-        convert_w(ring + (size_t)s * kM * kK, valid, sA);
+        convert_w<NT>(ring + (size_t)s * kM * kK, valid, sA);
         tc::fence_proxy_async();
         tc::fence_before();
         __syncthreads();          // stage s is consumed; sA holds this tile; TMEM drained
@@ -320,12 +325,13 @@ cudaError_t launch_query_tc_views(int levels, int V, const int64_t* P, int Q, in
     const size_t floor_bytes = 233472 / (size_t)(resident + 1) + 1024;
     if (smem < floor_bytes) smem = floor_bytes;
     if (smem > 232448) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(query_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = resident == 2 ? query_tc_kernel<256> : query_tc_kernel<512>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_level = num_sms * resident / levels;
     if (per_level < 1) per_level = 1;
     if (per_level > tiles) per_level = (int)tiles;
-    query_tc_kernel<<<dim3(per_level, levels), kThreads, smem, stream>>>(a);
+    kern<<<dim3(per_level, levels), resident == 2 ? 256 : 512, smem, stream>>>(a);
     return cudaGetLastError();
 }
 
