@@ -70,7 +70,20 @@ __global__ void __launch_bounds__(256) column_kernel(int V, int nblk, ViewsDev v
     const int t = tg - vd.tile_base[v], T = vd.T[v];
     uint32_t* col = hist + vd.hist_base[v] + t;
     uint32_t run = 0;
-    for (int b = 0; b < nblk; ++b) {
+    // 16 block counts are loaded before any is overwritten, so their latencies overlap
+    constexpr int kU = 16;
+    int b = 0;
+    for (; b + kU <= nblk; b += kU) {
+        uint32_t c[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) c[u] = col[(size_t)(b + u) * T];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            col[(size_t)(b + u) * T] = run;
+            run += c[u];
+        }
+    }
+    for (; b < nblk; ++b) {
         const uint32_t c = col[(size_t)b * T];
         col[(size_t)b * T] = run;
         run += c;
