@@ -123,7 +123,8 @@ __global__ void __launch_bounds__(FC::kThreads, 1) fused_kernel(FusedArgs a)
 
     if (!skip) {
         // ---- splat: W stays in the consumer warps' shared-memory columns
-        TileJob j{a.width, a.height, a.GX, tile, a.tile_ranges[2 * tile], a.tile_ranges[2 * tile + 1], a.gauss_ids,
+        TileJob j{a.width, a.height, (tile % a.GX) * kTW, (tile / a.GX) * kTH, a.tile_ranges[2 * tile],
+                  a.tile_ranges[2 * tile + 1], a.gauss_ids,
                   a.recs, nullptr, a.final_T, a.n_last, a.status};
         (void)splat_tile<kLev, kKp, kTW, kTH, 0, false>(j, sm, 0u);
     }

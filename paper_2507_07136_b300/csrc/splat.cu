@@ -147,7 +147,9 @@ __global__ void __launch_bounds__(256) pack_dense_kernel(PackArgs a)
     reinterpret_cast<float4*>(rec + kRecFloats - 4)[0] = make_float4(ex.x, ex.y, 0.f, 0.f);
 }
 
-template <int LEVELS, int K, int TW, int TH, bool DENSE = false>
+// One CTA per TW x TH pixel block; SUB blocks stacked vertically share one bin tile of
+// TW x (TH SUB) pixels (and its list), so a bin tile's halves can run as two CTAs per SM.
+template <int LEVELS, int K, int TW, int TH, bool DENSE = false, int SUB = 1>
 __global__ void __launch_bounds__(TW* TH + 32, 1) splat_kernel(SplatArgs a)
 {
     using C = SplatCfg<LEVELS, K, TW, TH, 0, DENSE>;
@@ -160,8 +162,9 @@ __global__ void __launch_bounds__(TW* TH + 32, 1) splat_kernel(SplatArgs a)
     }
     __syncthreads();
     if (*sm.skip) return;
-    const int tile = blockIdx.x;
-    TileJob j{a.cam.width, a.cam.height, (a.cam.width + TW - 1) / TW, tile, a.tile_ranges[2 * tile],
+    const int tile = blockIdx.x / SUB, sub = blockIdx.x % SUB;
+    const int GX = (a.cam.width + TW - 1) / TW;
+    TileJob j{a.cam.width, a.cam.height, (tile % GX) * TW, (tile / GX) * (TH * SUB) + sub * TH, a.tile_ranges[2 * tile],
               a.tile_ranges[2 * tile + 1], a.gauss_ids, a.recs, a.coeff, a.final_T, a.n_last, a.status};
     (void)splat_tile<LEVELS, K, TW, TH, 0, true, DENSE>(j, sm, 0u);
 }
@@ -190,7 +193,8 @@ __global__ void __launch_bounds__(TW* TH + 32, 1) splat_views_kernel(SplatViewsA
         int v = 0;
         while (v + 1 < a.V && tg >= a.view[v + 1].tile_base) ++v;
         const SplatView& w = a.view[v];
-        TileJob j{w.width, w.height, w.GX, tg - w.tile_base, a.tile_ranges[2 * tg], a.tile_ranges[2 * tg + 1],
+        const int tl = tg - w.tile_base;
+        TileJob j{w.width, w.height, (tl % w.GX) * TW, (tl / w.GX) * TH, a.tile_ranges[2 * tg], a.tile_ranges[2 * tg + 1],
                   a.gauss_ids, a.recs + w.rec_off, a.coeff + w.coeff_off, a.final_T + w.pix_off,
                   a.n_last + w.pix_off, a.status};
         bbase += splat_tile<LEVELS, K, TW, TH, BATCH>(j, sm, bbase);
@@ -199,17 +203,22 @@ __global__ void __launch_bounds__(TW* TH + 32, 1) splat_views_kernel(SplatViewsA
 
 namespace {
 
-template <int LEVELS, int K, int TW, int TH, bool DENSE = false>
+// CTAs per 16 x 16 bin tile in the single-view splat
+constexpr int kSub16 = 2;
+
+// Bin tiles of TW x TH pixels, each run as SUB CTAs of TW x (TH / SUB) pixels.
+template <int LEVELS, int K, int TW, int TH, bool DENSE = false, int SUB = 1>
 cudaError_t launch_t(const SplatArgs& a, cudaStream_t stream)
 {
-    using C = SplatCfg<LEVELS, K, TW, TH, 0, DENSE>;
+    constexpr int kTHc = TH / SUB;
+    using C = SplatCfg<LEVELS, K, TW, kTHc, 0, DENSE>;
     static_assert(C::kSmemBytes <= 232448, "shared memory budget");
-    auto kern = splat_kernel<LEVELS, K, TW, TH, DENSE>;
+    auto kern = splat_kernel<LEVELS, K, TW, kTHc, DENSE, SUB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
     if (e != cudaSuccess) return e;
     const int GX = (a.cam.width + TW - 1) / TW, GY = (a.cam.height + TH - 1) / TH;
     if (GX * GY == 0) return cudaSuccess;
-    kern<<<GX * GY, C::kThreads, C::kSmemBytes, stream>>>(a);
+    kern<<<GX * GY * SUB, C::kThreads, C::kSmemBytes, stream>>>(a);
     return cudaGetLastError();
 }
 
@@ -253,7 +262,7 @@ cudaError_t launch_views_tile(const SplatViewsArgs& a, int tw, int th, int batch
 template <int LEVELS, int K>
 cudaError_t launch_tile(const SplatArgs& a, cudaStream_t stream)
 {
-    if (a.cam.tile_w == 16 && a.cam.tile_h == 16) return launch_t<LEVELS, K, 16, 16>(a, stream);
+    if (a.cam.tile_w == 16 && a.cam.tile_h == 16) return launch_t<LEVELS, K, 16, 16, false, kSub16>(a, stream);
     if (a.cam.tile_w == 8 && a.cam.tile_h == 8) return launch_t<LEVELS, K, 8, 8>(a, stream);
     if (a.cam.tile_w == 32 && a.cam.tile_h == 8) return launch_t<LEVELS, K, 32, 8>(a, stream);
     return cudaErrorInvalidValue;

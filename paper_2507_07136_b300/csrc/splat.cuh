@@ -47,7 +47,9 @@ struct SplatCfg {
     static constexpr int kStageBytes = kBatch * (kRecBytes + 16);   // records + culling boxes
     static constexpr int kFixedBytes = kAccBytes + 512;             // + barriers and flags
     static constexpr int kStagesFit = (232448 - 64 - kFixedBytes) / kStageBytes;
-    static constexpr int kStages = kWarps >= 8 ? (kStagesFit < 8 ? kStagesFit : 8) : 4;
+    // 8 consumer warps: as many stages as fit (one CTA per SM); 4 warps: 2 stages, so two CTAs
+    // share an SM; fewer warps: 4 stages
+    static constexpr int kStages = kWarps >= 8 ? (kStagesFit < 8 ? kStagesFit : 8) : (kWarps >= 4 ? 2 : 4);
     static constexpr int kSmemBytes = kFixedBytes + kStages * kStageBytes;
     static_assert(kPixels % 32 == 0 && 32 % TW == 0, "a warp covers whole rows of a tile");
     static_assert(kPairs <= kMaxPairs, "pairs per record");

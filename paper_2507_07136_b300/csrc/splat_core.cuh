@@ -13,7 +13,7 @@ namespace {
 
 // One tile of one view.
 struct TileJob {
-    int width, height, GX, tile;
+    int width, height, x0, y0;   // image size; first pixel of this CTA's TW x TH block
     uint32_t beg, end;
     const uint32_t* gauss_ids;
     const float* recs;
@@ -146,15 +146,14 @@ __device__ uint32_t splat_consume(const TileJob& a, const SplatSmem<C>& sm, int 
     constexpr int kChunk = 4;   // kept records evaluated together
     float* acc = sm.acc + warp * C::kAccFloats;
     unsigned char* acc_lane = reinterpret_cast<unsigned char*>(acc + lane);
-    const int GX = a.GX;
-    const int tx = a.tile % GX, ty = a.tile / GX;
+
     const int lx = lane % TW, ly = warp * (32 / TW) + lane / TW;
-    const int px = tx * TW + lx, py = ty * TH + ly;
+    const int px = a.x0 + lx, py = a.y0 + ly;
     const bool inside = px < a.width && py < a.height;
     // pixel strip covered by this warp
     constexpr int kRows = 32 / TW;
-    const float wx0 = (float)(tx * TW), wx1 = (float)(tx * TW + TW - 1);
-    const float wy0 = (float)(ty * TH + warp * kRows), wy1 = wy0 + (float)(kRows - 1);
+    const float wx0 = (float)a.x0, wx1 = (float)(a.x0 + TW - 1);
+    const float wy0 = (float)(a.y0 + warp * kRows), wy1 = wy0 + (float)(kRows - 1);
 
     for (int i = lane * 4; i < C::kAccFloats; i += 128)
         *reinterpret_cast<float4*>(acc + i) = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -297,7 +296,7 @@ __device__ uint32_t splat_consume(const TileJob& a, const SplatSmem<C>& sm, int 
         for (int q = lane; q < 32 * 16; q += 32) {
             const int pl = q >> 4;  // pixel within the warp (row-major over the strip)
             const int c4 = (q & 15) * 4;
-            const int gx = tx * TW + (pl % TW), gy = ty * TH + warp * kRows + pl / TW;
+            const int gx = a.x0 + (pl % TW), gy = a.y0 + warp * kRows + pl / TW;
             if (gx < a.width && gy < a.height) {
                 const float* col = acc + (lev * 64 + c4) * 33 + pl;
                 float4 val = make_float4(col[0], col[33], col[66], col[99]);
