@@ -169,9 +169,10 @@ __global__ void __launch_bounds__(TW* TH + 32, 1) splat_kernel(SplatArgs a)
     (void)splat_tile<LEVELS, K, TW, TH, 0, true, DENSE>(j, sm, 0u);
 }
 
-// Persistent over the (view, tile) work items of several views: each CTA takes the next global
-// tile id from an atomic counter (largest views first, as they come first in the numbering).
-template <int LEVELS, int K, int TW, int TH, int BATCH>
+// Persistent over the (view, tile) work items of several views: each CTA takes the next work
+// item from an atomic counter (largest views first, as they come first in the numbering); a
+// TW x (TH SUB) bin tile is SUB items of TW x TH pixels.
+template <int LEVELS, int K, int TW, int TH, int BATCH, int SUB = 1>
 __global__ void __launch_bounds__(TW* TH + 32, 1) splat_views_kernel(SplatViewsArgs a)
 {
     using C = SplatCfg<LEVELS, K, TW, TH, BATCH>;
@@ -186,15 +187,17 @@ __global__ void __launch_bounds__(TW* TH + 32, 1) splat_views_kernel(SplatViewsA
             *sm.skip = *sm.abort || (a.status && *reinterpret_cast<volatile int32_t*>(a.status) == LSV2_ERR_TIMEOUT);
         }
         __syncthreads();
-        const int tg = s_tile;
+        const int item = s_tile;
         const bool stop = *sm.skip;
         __syncthreads();
+        const int tg = item / SUB, sub = item % SUB;
         if (tg >= a.total_tiles || stop) break;
         int v = 0;
         while (v + 1 < a.V && tg >= a.view[v + 1].tile_base) ++v;
         const SplatView& w = a.view[v];
         const int tl = tg - w.tile_base;
-        TileJob j{w.width, w.height, (tl % w.GX) * TW, (tl / w.GX) * TH, a.tile_ranges[2 * tg], a.tile_ranges[2 * tg + 1],
+        TileJob j{w.width, w.height, (tl % w.GX) * TW, (tl / w.GX) * (TH * SUB) + sub * TH, a.tile_ranges[2 * tg],
+                  a.tile_ranges[2 * tg + 1],
                   a.gauss_ids, a.recs + w.rec_off, a.coeff + w.coeff_off, a.final_T + w.pix_off,
                   a.n_last + w.pix_off, a.status};
         bbase += splat_tile<LEVELS, K, TW, TH, BATCH>(j, sm, bbase);
@@ -203,7 +206,7 @@ __global__ void __launch_bounds__(TW* TH + 32, 1) splat_views_kernel(SplatViewsA
 
 namespace {
 
-// CTAs per 16 x 16 bin tile in the single-view splat
+// CTAs per 16 x 16 bin tile (two CTAs of 16 x 8 pixels share an SM)
 constexpr int kSub16 = 2;
 
 // Bin tiles of TW x TH pixels, each run as SUB CTAs of TW x (TH / SUB) pixels.
@@ -222,12 +225,12 @@ cudaError_t launch_t(const SplatArgs& a, cudaStream_t stream)
     return cudaGetLastError();
 }
 
-template <int LEVELS, int K, int TW, int TH, int BATCH>
+template <int LEVELS, int K, int TW, int TH, int BATCH, int SUB = 1>
 cudaError_t launch_views_t(const SplatViewsArgs& a, int num_sms, cudaStream_t stream)
 {
     using C = SplatCfg<LEVELS, K, TW, TH, BATCH>;
     static_assert(C::kSmemBytes <= 232448, "shared memory budget");
-    auto kern = splat_views_kernel<LEVELS, K, TW, TH, BATCH>;
+    auto kern = splat_views_kernel<LEVELS, K, TW, TH, BATCH, SUB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -241,19 +244,22 @@ cudaError_t launch_views_t(const SplatViewsArgs& a, int num_sms, cudaStream_t st
     return cudaGetLastError();
 }
 
-template <int LEVELS, int K, int TW, int TH>
+// TW x TH bin tiles as SUB CTAs of TW x (TH / SUB) pixels
+template <int LEVELS, int K, int TW, int TH, int SUB = 1>
 cudaError_t launch_views_b(const SplatViewsArgs& a, int batch, int num_sms, cudaStream_t stream)
 {
-    using Auto = SplatCfg<LEVELS, K, TW, TH>;
-    if (batch == 16) return launch_views_t<LEVELS, K, TW, TH, 16>(a, num_sms, stream);
-    if (batch == 0 || batch == Auto::kBatch) return launch_views_t<LEVELS, K, TW, TH, Auto::kBatch>(a, num_sms, stream);
+    constexpr int kTHc = TH / SUB;
+    using Auto = SplatCfg<LEVELS, K, TW, kTHc>;
+    if (batch == 16) return launch_views_t<LEVELS, K, TW, kTHc, 16, SUB>(a, num_sms, stream);
+    if (batch == 0 || batch == Auto::kBatch)
+        return launch_views_t<LEVELS, K, TW, kTHc, Auto::kBatch, SUB>(a, num_sms, stream);
     return cudaErrorInvalidValue;
 }
 
 template <int LEVELS, int K>
 cudaError_t launch_views_tile(const SplatViewsArgs& a, int tw, int th, int batch, int num_sms, cudaStream_t stream)
 {
-    if (tw == 16 && th == 16) return launch_views_b<LEVELS, K, 16, 16>(a, batch, num_sms, stream);
+    if (tw == 16 && th == 16) return launch_views_b<LEVELS, K, 16, 16, kSub16>(a, batch, num_sms, stream);
     if (tw == 8 && th == 8) return launch_views_b<LEVELS, K, 8, 8>(a, batch, num_sms, stream);
     if (tw == 32 && th == 8) return launch_views_b<LEVELS, K, 32, 8>(a, batch, num_sms, stream);
     return cudaErrorInvalidValue;
