@@ -42,10 +42,7 @@ POST_THRESHOLD = 0.5
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
 # this workload with the kernels as they are now; an entry is removed when its kernel changes.
 SPLAT_KERNEL = "splat_kernel<3,4,16,8> (two CTAs per 16x16 tile)"
-TRAFFIC = {
-    SPLAT_KERNEL: 47868416 + 1145869312,
-    "decode_tc_kernel": 1194813696 + 4714354176,
-}
+TRAFFIC = {}
 
 
 def peaks():
@@ -324,9 +321,11 @@ def main():
     from paper_2507_07136_b300.pipeline import PostResult
     post_out = PostResult(text.shape[0], levels, cam.height, cam.width, dev)
     stages = ["project", "bin_sort", "splat", "decode", "query", "post"]
-    fns = {"project": frame.project, "bin_sort": frame.bin_sort, "splat": frame.splat,
-           "decode": lambda: frame.decode(F, codebook=cb16),
-           "query": lambda: frame.query(text_d, rel, compute=Lb.LSV2_BF16),
+    # the tensor-core path: the splat writes the coefficient map as BF16 (what the decode and the
+    # relevancy round it to before their products), the decode and the relevancy read it
+    fns = {"project": frame.project, "bin_sort": frame.bin_sort, "splat": frame.splat_bf16,
+           "decode": lambda: frame.decode(F, codebook=cb16, from_bf16=True),
+           "query": lambda: frame.query(text_d, rel, compute=Lb.LSV2_BF16, from_bf16=True),
            "post": lambda: frame.postprocess(rel, k=POST_WINDOW, mode=Lb.LSV2_POST_LERF, threshold=POST_THRESHOLD,
                                              out=post_out)}
     # kernels per stage: project; hist/column/scan/scatter/sort (bin); pack + splat; decode;
@@ -376,6 +375,7 @@ def main():
     if not args.no_fp32_path:
         del F
         F32 = torch.empty((levels, P, D), dtype=torch.float32, device=dev)
+        fns["splat"] = frame.splat
         fns["decode"] = lambda: frame.decode(F32)
         fns["query"] = lambda: frame.query(text_d, rel)
         timed(2)
@@ -383,8 +383,9 @@ def main():
         fp32 = {"ms_per_step": ms32, "fps": 1e3 / ms32, "stages_ms": st32}
         del F32
         F = torch.empty((levels, P, D), dtype=torch.bfloat16, device=dev)
-        fns["decode"] = lambda: frame.decode(F, codebook=cb16)
-        fns["query"] = lambda: frame.query(text_d, rel, compute=Lb.LSV2_BF16)
+        fns["splat"] = frame.splat_bf16
+        fns["decode"] = lambda: frame.decode(F, codebook=cb16, from_bf16=True)
+        fns["query"] = lambda: frame.query(text_d, rel, compute=Lb.LSV2_BF16, from_bf16=True)
 
     # ---- splat + decode + query in one kernel (lsv2_render_fused): W never leaves the SM ----
     fused_ms = None
@@ -432,8 +433,8 @@ def main():
     pk, pk_kind = peaks()
     inst = int(frame.num_instances.item())
     rec_bytes = Lb.lsv2_splat_workspace_bytes(scene.n, levels, scene.K)
-    splat_bytes = levels * P * 64 * 4 + rec_bytes + inst * 4 + P * 8
-    decode_bytes = levels * P * (64 * 4 + D * 2)
+    splat_bytes = levels * P * 64 * 2 + rec_bytes + inst * 4 + P * 8      # BF16 coefficient map
+    decode_bytes = levels * P * (64 * 2 + D * 2)                          # BF16 W in, BF16 F out
     roofs = {
         "splat": {"bound": "hbm", "achieved": splat_bytes / (stage_ms["splat"] * 1e-3) / 1e9, "peak": pk["hbm_gbs"],
                   "unit": "GB/s", "traffic": TRAFFIC.get(SPLAT_KERNEL), "kernel": SPLAT_KERNEL,
@@ -451,8 +452,9 @@ def main():
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic",
             "config": {"workload": "300k Gaussians, 3 levels, K=4, L=64, D=512, 1440x1080, 1 query + 4 negatives",
-                       "path": "FP32 projection and splat; BF16 tensor-core decode to a BF16 feature map and "
-                               "BF16 tensor-core relevancy (FP32 accumulation); post-processing (LERF rule, "
+                       "path": "FP32 projection and splat (coefficient map stored as BF16); BF16 tensor-core decode "
+                               "to a BF16 feature map and BF16 tensor-core relevancy (FP32 accumulation); "
+                               "post-processing (LERF rule, "
                                f"{POST_WINDOW}x{POST_WINDOW} mean filter, level, point, mask at {POST_THRESHOLD})",
                        "parallelism": f"replicas x{world}",
                        "l2": "flushed between steps (256 MiB write, untimed)", "instances": inst},

@@ -150,14 +150,25 @@ size_t lsv2_splat_workspace_bytes(int64_t n, int32_t levels, int32_t K);
  *   coeff float[levels][H*W][L]  output coefficient map W (pixel-major, L contiguous)
  *   final_T float[H*W], n_last uint32[H*W]: transmittance after the last contributor and
  *   the list position (+1, relative to the tile start) of that contributor (0: none).
- * Blending is FP32.  Supported: L = 64; levels 1 with K in {2, 4, 6, 8}, levels 2 or 3
- * with K = 4; tiles 16x16, 8x8, 32x8. */
+ * Blending is FP32.  Supported: L = 64; levels 1 with K in {2, 4, 6, 8}, levels 2 with K = 4,
+ * levels 3 with K = 4 (any tile) or K in {2, 6, 8} (16x16 tiles); tiles 16x16, 8x8, 32x8. */
 lsv2_status lsv2_splat_coeffs(const lsv2_camera* cam, int64_t n, const lsv2_proj* proj,
                               const uint32_t* tile_ranges, const uint32_t* gauss_ids,
                               int32_t levels, int32_t K, int32_t L, const uint8_t* idx,
                               const float* w, void* workspace, size_t workspace_bytes,
                               float* coeff, float* final_T, uint32_t* n_last,
                               int32_t* dev_status, void* stream);
+
+/* lsv2_splat_coeffs with the coefficient map written as BF16 (round to nearest even of the FP32
+ * blend; 16-byte aligned).  The tensor-core decode and relevancy round W to BF16 before their
+ * products, so feeding them this map gives results bit-equal to feeding them the FP32 map, at
+ * half the map's bytes.  Other arguments and outputs as for lsv2_splat_coeffs. */
+lsv2_status lsv2_splat_coeffs_bf16(const lsv2_camera* cam, int64_t n, const lsv2_proj* proj,
+                                   const uint32_t* tile_ranges, const uint32_t* gauss_ids,
+                                   int32_t levels, int32_t K, int32_t L, const uint8_t* idx,
+                                   const float* w, void* workspace, size_t workspace_bytes,
+                                   void* coeff_bf16, float* final_T, uint32_t* n_last,
+                                   int32_t* dev_status, void* stream);
 
 /* Size of the fixed device scratch used by lsv2_splat_coeffs_noalloc (held on every device
  * that loads this library, until the process exits). */
@@ -202,7 +213,7 @@ size_t lsv2_query_workspace_bytes(int32_t levels, int32_t L, int32_t Q, int32_t 
  *   <F, t> = W . u_t,  |F|^2 = W^T G W,  cos_t = <F, t> / (|F| |t|)  (0 when |F| < 1e-12)
  *   rel[q][lev][p] = min_i softmax(tau [cos_pos, cos_neg_i])_0
  *                  = sigmoid(tau (cos_pos - max_i cos_neg_i))
- *   coeff    float[levels][P][L]
+ *   coeff    [levels][P][L], dtype coeff_dtype: F32, or BF16 with compute_dtype BF16
  *   codebook float[levels][L][D]
  *   text     float[Q][1 + n_neg][D]  (positive first)
  *   rel      [Q][levels][P]  dtype rel_dtype (F32 or BF16)

@@ -46,6 +46,7 @@ _SIGS = {
     "lsv2_bin_sort": ([P, I64, P, P, SZ, P, I64, P, P, P, P], I32),
     "lsv2_splat_workspace_bytes": ([I64, I32, I32], SZ),
     "lsv2_splat_coeffs": ([P, I64, P, P, P, I32, I32, I32, P, P, P, SZ, P, P, P, P, P], I32),
+    "lsv2_splat_coeffs_bf16": ([P, I64, P, P, P, I32, I32, I32, P, P, P, SZ, P, P, P, P, P], I32),
     "lsv2_splat_dense_workspace_bytes": ([I64, I32], SZ),
     "lsv2_splat_coeffs_dense": ([P, I64, P, P, P, I32, I32, I32, P, P, P, SZ, P, P, P, P, P], I32),
     "lsv2_splat_coeffs_noalloc": ([P, I64, P, P, P, I32, I32, I32, P, P, P, P, P, P, P], I32),
@@ -211,3 +212,9 @@ def lsv2_splat_coeffs_dense(cam, n, proj, tile_ranges, gauss_ids, levels, K, L, 
                             n_last, dev_status, stream):
     call("lsv2_splat_coeffs_dense", C.byref(cam), n, C.byref(proj), tile_ranges, gauss_ids, levels, K, L, idx, w, ws,
          ws_bytes, coeff, final_T, n_last, dev_status, stream)
+
+
+def lsv2_splat_coeffs_bf16(cam, n, proj, tile_ranges, gauss_ids, levels, K, L, idx, w, ws, ws_bytes, coeff_bf16,
+                           final_T, n_last, dev_status, stream):
+    call("lsv2_splat_coeffs_bf16", C.byref(cam), n, C.byref(proj), tile_ranges, gauss_ids, levels, K, L, idx, w, ws,
+         ws_bytes, coeff_bf16, final_T, n_last, dev_status, stream)

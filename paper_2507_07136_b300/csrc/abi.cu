@@ -144,6 +144,29 @@ lsv2_status lsv2_splat_coeffs(const lsv2_camera* cam, int64_t n, const lsv2_proj
     return cuda_status(launch_splat(levels, K, sa, S(stream)));
 }
 
+lsv2_status lsv2_splat_coeffs_bf16(const lsv2_camera* cam, int64_t n, const lsv2_proj* proj,
+                                   const uint32_t* tile_ranges, const uint32_t* gauss_ids, int32_t levels, int32_t K,
+                                   int32_t L, const uint8_t* idx, const float* w, void* workspace,
+                                   size_t workspace_bytes, void* coeff_bf16, float* final_T, uint32_t* n_last,
+                                   int32_t* dev_status, void* stream)
+{
+    if (!camera_ok(cam) || n < 0 || !proj_ok(proj) || !tile_ranges || !gauss_ids || !coeff_bf16 || !final_T ||
+        !n_last)
+        return LSV2_ERR_INVALID_ARGUMENT;
+    if (n > 0 && (!idx || !w)) return LSV2_ERR_INVALID_ARGUMENT;
+    if (!splat_supported(levels, K, L, cam->tile_w, cam->tile_h)) return LSV2_ERR_UNSUPPORTED;
+    if (!aligned16(coeff_bf16) || !workspace || !aligned16(workspace) ||
+        workspace_bytes < lsv2_splat_workspace_bytes(n, levels, K))
+        return LSV2_ERR_INVALID_ARGUMENT;
+    PackArgs pa{n, levels, K, splat_record_bytes(levels, K), proj->xy, proj->axes, proj->conic_o, proj->extent, idx,
+                w, static_cast<float*>(workspace), dev_status};
+    cudaError_t e = launch_pack(pa, S(stream));
+    if (e != cudaSuccess) return LSV2_ERR_CUDA;
+    SplatArgs sa{*cam, tile_ranges, gauss_ids, static_cast<const float*>(workspace), static_cast<float*>(coeff_bf16),
+                 final_T, n_last, dev_status, 1};
+    return cuda_status(launch_splat(levels, K, sa, S(stream)));
+}
+
 size_t lsv2_splat_dense_workspace_bytes(int64_t n, int32_t levels)
 {
     if (n < 0 || (levels != 1 && levels != 3)) return 0;
@@ -211,8 +234,9 @@ lsv2_status lsv2_query(int32_t levels, int64_t P, int32_t L, int32_t D, const vo
     const int nt = Q * (1 + n_neg);
     if (!workspace || !aligned16(workspace) || workspace_bytes < query_workspace_bytes(levels, nt))
         return LSV2_ERR_INVALID_ARGUMENT;
-    if (!aligned16(coeff) || coeff_dtype != LSV2_F32) return coeff_dtype != LSV2_F32 ? LSV2_ERR_UNSUPPORTED
-                                                                                       : LSV2_ERR_INVALID_ARGUMENT;
+    if (!aligned16(coeff)) return LSV2_ERR_INVALID_ARGUMENT;
+    if (coeff_dtype != LSV2_F32 && !(coeff_dtype == LSV2_BF16 && compute_dtype == LSV2_BF16))
+        return LSV2_ERR_UNSUPPORTED;
     if (rel_dtype != LSV2_F32 && rel_dtype != LSV2_BF16) return LSV2_ERR_INVALID_ARGUMENT;
     cudaError_t e = launch_query_prepare(levels, D, nt, codebook, text, workspace, S(stream));
     if (e != cudaSuccess) return LSV2_ERR_CUDA;
@@ -221,7 +245,7 @@ lsv2_status lsv2_query(int32_t levels, int64_t P, int32_t L, int32_t D, const vo
                                             static_cast<float*>(rel), S(stream)));
     if (compute_dtype == LSV2_BF16) {
         if (!query_tc_supported(Q, n_neg)) return LSV2_ERR_UNSUPPORTED;
-        return cuda_status(launch_query_tc(levels, P, Q, n_neg, tau, static_cast<const float*>(coeff),
+        return cuda_status(launch_query_tc(levels, P, Q, n_neg, tau, coeff, coeff_dtype == LSV2_BF16,
                                            query_ws_bt(workspace), query_ws_tnorm(workspace, levels, nt), rel,
                                            rel_dtype == LSV2_BF16, sm_count(), dev_status, S(stream)));
     }

@@ -25,7 +25,8 @@ constexpr int kK = 64;
 struct QueryTcArgs {
     int Q, n_neg, Qp, npad;        // Qp = Q rounded up to 8; npad = 64 + (1 + n_neg) Qp rounded up to 16
     float tau;
-    const float* W;                // per view v: [levels][P_v][64] f32 at W + seg[v].w_off
+    const void* W;                 // per view v: [levels][P_v][64] at W + seg[v].w_off elements
+    int w_bf16;                    // W in BF16 (else FP32)
     const float* Bt;               // [levels][64 + Q (1 + n_neg)][64] f32 (rows of B^T, query-major texts)
     const float* tnorm;            // [Q (1 + n_neg)] (query-major)
     void* rel;                     // per view v: [Q][levels][P_v] at rel + seg[v].rel_off
@@ -38,7 +39,7 @@ struct QueryTcArgs {
 };
 
 constexpr int kStages = 2;                      // W tiles in flight per CTA (bulk copies)
-constexpr int kTileBytes = kM * kK * 4;         // one FP32 W tile: 32 KB, contiguous in HBM
+constexpr int kTileBytes = kM * kK * 4;         // one W tile (FP32: 32 KB; BF16: 16 KB), contiguous in HBM
 
 __host__ __device__ constexpr int pad8(int q) { return (q + 7) / 8 * 8; }
 __host__ __device__ constexpr int npad_of(int Q, int n_neg) { return (64 + (1 + n_neg) * pad8(Q) + 15) / 16 * 16; }
@@ -52,6 +53,19 @@ __host__ __device__ constexpr size_t smem_bytes(int npad, int ntp)
 __host__ __device__ constexpr uint32_t tmem_cols(int npad)
 {
     return npad <= 32 ? 32u : npad <= 64 ? 64u : npad <= 128 ? 128u : npad <= 256 ? 256u : 512u;
+}
+
+// BF16 tile (row-major, 128 bytes per row, in the ring) -> the swizzled K-major operand.
+template <int NT>
+__device__ __forceinline__ void copy_w_bf16(const uint8_t* src, int valid_rows, uint8_t* sA)
+{
+#pragma unroll
+    for (int j = 0; j < 1024 / NT; ++j) {
+        const int c = threadIdx.x + NT * j, row = c >> 3, kc = c & 7;
+        const uint4 v = row < valid_rows ? *reinterpret_cast<const uint4*>(src + row * 128 + kc * 16)
+                                         : make_uint4(0, 0, 0, 0);
+        *reinterpret_cast<uint4*>(sA + tc::sw128(row, kc * 8)) = v;
+    }
 }
 
 // FP32 tile (row-major, 64 floats per row, in the ring) -> BF16 swizzled K-major operand.
@@ -105,9 +119,10 @@ __global__ void __launch_bounds__(NT, 512 / NT) query_tc_kernel(QueryTcArgs a)
         locate(blockIdx.x + i * gridDim.x, v, p0);
         const int64_t Pv = a.seg[v].P;
         const int64_t rows = Pv - p0 < kM ? Pv - p0 : kM;
-        const uint32_t bytes = (uint32_t)(rows * kK * 4);
+        const int esz = a.w_bf16 ? 2 : 4;
+        const uint32_t bytes = (uint32_t)(rows * kK * esz);
         const int s = (int)(i % kStages);
-        const float* src = a.W + a.seg[v].w_off + ((size_t)lev * Pv + p0) * kK;
+        const uint8_t* src = static_cast<const uint8_t*>(a.W) + (a.seg[v].w_off + ((size_t)lev * Pv + p0) * kK) * esz;
         tc::bulk_load_arm(tc::smem_u32(full + s), bytes);
         tc::bulk_load(tc::smem_u32(ring + (size_t)s * kM * kK), src, bytes, tc::smem_u32(full + s));
     };
@@ -163,7 +178,8 @@ __global__ void __launch_bounds__(NT, 512 / NT) query_tc_kernel(QueryTcArgs a)
             break;
         }
         const int valid = Pv - p0 < kM ? (int)(Pv - p0) : kM;
-        convert_w<NT>(ring + (size_t)s * kM * kK, valid, sA);
+        if (a.w_bf16) copy_w_bf16<NT>(reinterpret_cast<const uint8_t*>(ring + (size_t)s * kM * kK), valid, sA);
+        else convert_w<NT>(ring + (size_t)s * kM * kK, valid, sA);
         tc::fence_proxy_async();
         tc::fence_before();
         __syncthreads();          // stage s is consumed; sA holds this tile; TMEM drained
@@ -285,7 +301,8 @@ bool query_tc_supported(int Q, int n_neg)
            (512u / tmem_cols(npad) >= 2 || smem_bytes(npad, ntp) >= 117760);
 }
 
-cudaError_t launch_query_tc_views(int levels, int V, const int64_t* P, int Q, int n_neg, float tau, const float* W,
+cudaError_t launch_query_tc_views(int levels, int V, const int64_t* P, int Q, int n_neg, float tau, const void* W,
+                                  bool w_bf16,
                                   const float* Bt, const float* tnorm, void* rel, bool rel_bf16, int num_sms,
                                   int32_t* status, cudaStream_t stream)
 {
@@ -299,6 +316,7 @@ cudaError_t launch_query_tc_views(int levels, int V, const int64_t* P, int Q, in
     a.npad = npad;
     a.tau = tau;
     a.W = W;
+    a.w_bf16 = w_bf16 ? 1 : 0;
     a.Bt = Bt;
     a.tnorm = tnorm;
     a.rel = rel;
@@ -335,12 +353,14 @@ cudaError_t launch_query_tc_views(int levels, int V, const int64_t* P, int Q, in
     return cudaGetLastError();
 }
 
-cudaError_t launch_query_tc(int levels, int64_t P, int Q, int n_neg, float tau, const float* W, const float* Bt,
+cudaError_t launch_query_tc(int levels, int64_t P, int Q, int n_neg, float tau, const void* W, bool w_bf16,
+                            const float* Bt,
                             const float* tnorm, void* rel, bool rel_bf16, int num_sms, int32_t* status,
                             cudaStream_t stream)
 {
     if (P == 0) return cudaSuccess;
-    return launch_query_tc_views(levels, 1, &P, Q, n_neg, tau, W, Bt, tnorm, rel, rel_bf16, num_sms, status, stream);
+    return launch_query_tc_views(levels, 1, &P, Q, n_neg, tau, W, w_bf16, Bt, tnorm, rel, rel_bf16, num_sms, status,
+                                 stream);
 }
 
 }  // namespace lsv2

@@ -16,11 +16,12 @@ struct QuerySeg {
 
 // Q queries of 1 + n_neg texts each: 64 + (1 + n_neg) * ceil(Q / 8) * 8 <= 512 and shared memory.
 bool query_tc_supported(int Q, int n_neg);
-cudaError_t launch_query_tc_views(int levels, int V, const int64_t* P, int Q, int n_neg, float tau, const float* W,
-                                  const float* Bt, const float* tnorm, void* rel, bool rel_bf16, int num_sms,
-                                  int32_t* status, cudaStream_t stream);
-cudaError_t launch_query_tc(int levels, int64_t P, int Q, int n_neg, float tau, const float* W, const float* Bt,
-                            const float* tnorm, void* rel, bool rel_bf16, int num_sms, int32_t* status,
-                            cudaStream_t stream);
+// W: [levels][P][64] coefficient maps, BF16 when w_bf16 else FP32 (the views concatenated).
+cudaError_t launch_query_tc_views(int levels, int V, const int64_t* P, int Q, int n_neg, float tau, const void* W,
+                                  bool w_bf16, const float* Bt, const float* tnorm, void* rel, bool rel_bf16,
+                                  int num_sms, int32_t* status, cudaStream_t stream);
+cudaError_t launch_query_tc(int levels, int64_t P, int Q, int n_neg, float tau, const void* W, bool w_bf16,
+                            const float* Bt, const float* tnorm, void* rel, bool rel_bf16, int num_sms,
+                            int32_t* status, cudaStream_t stream);
 
 }  // namespace lsv2

@@ -165,7 +165,8 @@ __global__ void __launch_bounds__(TW* TH + 32, 1) splat_kernel(SplatArgs a)
     const int tile = blockIdx.x / SUB, sub = blockIdx.x % SUB;
     const int GX = (a.cam.width + TW - 1) / TW;
     TileJob j{a.cam.width, a.cam.height, (tile % GX) * TW, (tile / GX) * (TH * SUB) + sub * TH, a.tile_ranges[2 * tile],
-              a.tile_ranges[2 * tile + 1], a.gauss_ids, a.recs, a.coeff, a.final_T, a.n_last, a.status};
+              a.tile_ranges[2 * tile + 1], a.gauss_ids, a.recs, a.coeff, a.final_T, a.n_last, a.status,
+              a.coeff_bf16};
     (void)splat_tile<LEVELS, K, TW, TH, 0, true, DENSE>(j, sm, 0u);
 }
 
@@ -198,8 +199,10 @@ __global__ void __launch_bounds__(TW* TH + 32, 1) splat_views_kernel(SplatViewsA
         const int tl = tg - w.tile_base;
         TileJob j{w.width, w.height, (tl % w.GX) * TW, (tl / w.GX) * (TH * SUB) + sub * TH, a.tile_ranges[2 * tg],
                   a.tile_ranges[2 * tg + 1],
-                  a.gauss_ids, a.recs + w.rec_off, a.coeff + w.coeff_off, a.final_T + w.pix_off,
-                  a.n_last + w.pix_off, a.status};
+                  a.gauss_ids, a.recs + w.rec_off,
+                  a.coeff_bf16 ? reinterpret_cast<float*>(reinterpret_cast<__nv_bfloat16*>(a.coeff) + w.coeff_off)
+                               : a.coeff + w.coeff_off,
+                  a.final_T + w.pix_off, a.n_last + w.pix_off, a.status, a.coeff_bf16};
         bbase += splat_tile<LEVELS, K, TW, TH, BATCH>(j, sm, bbase);
     }
 }

@@ -75,10 +75,11 @@ struct SplatArgs {
     const uint32_t* tile_ranges;
     const uint32_t* gauss_ids;
     const float* recs;
-    float* coeff;
+    float* coeff;                       // [levels][P][64] F32, or BF16 when coeff_bf16
     float* final_T;
     uint32_t* n_last;
     int32_t* status;
+    int coeff_bf16 = 0;                 // write the coefficient map rounded to BF16 (nearest even)
 };
 
 constexpr int kMaxSplatViews = 64;
@@ -86,7 +87,7 @@ constexpr int kMaxSplatViews = 64;
 struct SplatView {
     int width, height, GX, tile_base;   // tile_base: first global tile id of this view
     size_t rec_off;                     // floats: start of this view's records
-    size_t coeff_off;                   // floats: start of this view's coefficient map
+    size_t coeff_off;                   // elements: start of this view's coefficient map
     size_t pix_off;                     // start of this view's final_T / n_last
 };
 
@@ -101,6 +102,7 @@ struct SplatViewsArgs {
     uint32_t* n_last;
     uint32_t* queue;                    // work-queue counter (zeroed by the launcher)
     int32_t* status;
+    int coeff_bf16 = 0;                 // coefficient maps in BF16
 };
 
 bool splat_supported(int levels, int K, int L, int tw, int th);

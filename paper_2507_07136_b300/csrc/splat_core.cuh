@@ -17,10 +17,11 @@ struct TileJob {
     uint32_t beg, end;
     const uint32_t* gauss_ids;
     const float* recs;
-    float* coeff;
+    float* coeff;                // F32 coefficient map, or BF16 when coeff_bf16
     float* final_T;
     uint32_t* n_last;
     int32_t* status;
+    int coeff_bf16 = 0;
 };
 
 constexpr uint64_t kWaitNs = 1000000000ull;   // bound of every wait on a stage barrier (1 s)
@@ -289,8 +290,26 @@ __device__ uint32_t splat_consume(const TileJob& a, const SplatSmem<C>& sm, int 
     }
     __syncwarp();
     if (!kWriteCoeff) return consumed;
-    // write this warp's 32 pixels: per row segment TW pixels x 64 floats (contiguous in HBM)
+    // write this warp's 32 pixels: per row segment TW pixels x 64 coefficients (contiguous in HBM)
     const size_t P = (size_t)a.width * a.height;
+    if (a.coeff_bf16) {
+        __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(a.coeff);
+#pragma unroll 1
+        for (int lev = 0; lev < LEVELS; ++lev) {
+            for (int q = lane; q < 32 * 8; q += 32) {
+                const int pl = q >> 3;  // pixel within the warp (row-major over the strip)
+                const int c8 = (q & 7) * 8;
+                const int gx = a.x0 + (pl % TW), gy = a.y0 + warp * kRows + pl / TW;
+                if (gx < a.width && gy < a.height) {
+                    const float* col = acc + (lev * 64 + c8) * 33 + pl;
+                    const uint4 val = make_uint4(tc::pack_bf16(col[0], col[33]), tc::pack_bf16(col[66], col[99]),
+                                                 tc::pack_bf16(col[132], col[165]), tc::pack_bf16(col[198], col[231]));
+                    __stcs(reinterpret_cast<uint4*>(out + ((size_t)lev * P + (size_t)gy * a.width + gx) * 64 + c8), val);
+                }
+            }
+        }
+        return consumed;
+    }
 #pragma unroll 1
     for (int lev = 0; lev < LEVELS; ++lev) {
         for (int q = lane; q < 32 * 16; q += 32) {

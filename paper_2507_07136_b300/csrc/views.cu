@@ -60,7 +60,7 @@ ViewsLayout views_layout(int V, const lsv2_camera* cams, int64_t n, int levels, 
     L.ids = take((size_t)capacity * 4);
     L.ranges = take((size_t)L.T_total * 8);
     L.recs = take(vn * (size_t)splat_record_bytes(levels, K));
-    L.coeff = take((size_t)levels * (size_t)L.P_total * 64 * 4);
+    L.coeff = take((size_t)levels * (size_t)L.P_total * 64 * 2);   // BF16: the relevancy rounds W to BF16
     L.finalT = take((size_t)L.P_total * 4);
     L.nlast = take((size_t)L.P_total * 4);
     L.query_bytes = query_workspace_bytes(levels, Q * (1 + n_neg));
@@ -188,6 +188,7 @@ extern "C" lsv2_status lsv2_query_views(int32_t V, const lsv2_camera* cams, int6
     sa.n_last = reinterpret_cast<uint32_t*>(ws + Lo.nlast);
     sa.queue = reinterpret_cast<uint32_t*>(ws + Lo.queue);
     sa.status = dev_status;
+    sa.coeff_bf16 = 1;
     e = launch_splat_views(levels, K, cams[0].tile_w, cams[0].tile_h, stage_batch, sa, sm_count(), st);
     if (e == cudaErrorInvalidValue) return LSV2_ERR_UNSUPPORTED;
     if (e != cudaSuccess) return LSV2_ERR_CUDA;
@@ -196,7 +197,7 @@ extern "C" lsv2_status lsv2_query_views(int32_t V, const lsv2_camera* cams, int6
     void* qws = ws + Lo.query;
     e = launch_query_prepare(levels, D, nt, codebook, text, qws, st);
     if (e != cudaSuccess) return LSV2_ERR_CUDA;
-    e = launch_query_tc_views(levels, V, P.data(), Q, n_neg, tau, sa.coeff, query_ws_bt(qws),
+    e = launch_query_tc_views(levels, V, P.data(), Q, n_neg, tau, sa.coeff, true, query_ws_bt(qws),
                               query_ws_tnorm(qws, levels, nt), rel, rel_dtype == LSV2_BF16, sm_count(), dev_status,
                               st);
     return e == cudaSuccess ? LSV2_OK : LSV2_ERR_CUDA;

@@ -146,13 +146,24 @@ class Frame:
                             float(tau), _ptr(self.fused_ws), need, _ptr(feat), _ptr(rel), rel_dt, _ptr(self.final_T),
                             _ptr(self.n_last), _ptr(self.status), _stream(stream))
 
+    def splat_bf16(self, stream=None):
+        """The splat with the coefficient map written as BF16 into self.coeff16 (what the tensor-core
+        decode and relevancy consume)."""
+        s = self.scene
+        if getattr(self, "coeff16", None) is None:
+            self.coeff16 = torch.empty((s.levels, self.P, L_CODEBOOK), dtype=torch.bfloat16, device=self.device)
+        L.lsv2_splat_coeffs_bf16(self.ccam, s.n, self.proj, _ptr(self.tile_ranges), _ptr(self.gauss_ids), s.levels,
+                                 s.K, L_CODEBOOK, _ptr(s.idx), _ptr(s.weights), _ptr(self.splat_ws),
+                                 self.splat_ws_bytes, _ptr(self.coeff16), _ptr(self.final_T), _ptr(self.n_last),
+                                 _ptr(self.status), _stream(stream))
+
     def render(self, stream=None):
         self.project(stream)
         self.bin_sort(stream)
         self.splat(stream)
 
     def decode(self, out: torch.Tensor, codebook: torch.Tensor | None = None, tensor_cores: bool | None = None,
-               stream=None):
+               stream=None, from_bf16: bool = False):
         """F = W S.  FP32 out + FP32 codebook -> CUDA-core FP32 path unless tensor_cores=True;
         any BF16 operand or tensor_cores=True -> tcgen05 path (BF16 operands, FP32 accumulation)."""
         cb = self.scene.codebook if codebook is None else codebook
@@ -160,16 +171,19 @@ class Frame:
         out_dt = L.LSV2_BF16 if out.dtype == torch.bfloat16 else L.LSV2_F32
         if tensor_cores and cb_dt == L.LSV2_F32 and out_dt == L.LSV2_F32:
             raise ValueError("the tensor-core decode needs a BF16 codebook or BF16 output")
-        L.lsv2_decode(self.scene.levels, self.P, L_CODEBOOK, self.scene.D, _ptr(self.coeff), L.LSV2_F32, _ptr(cb),
+        W, w_dt = (self.coeff16, L.LSV2_BF16) if from_bf16 else (self.coeff, L.LSV2_F32)
+        L.lsv2_decode(self.scene.levels, self.P, L_CODEBOOK, self.scene.D, _ptr(W), w_dt, _ptr(cb),
                       cb_dt, _ptr(out), out_dt, _ptr(self.status), _stream(stream))
 
-    def query(self, text: torch.Tensor, out: torch.Tensor, tau: float = 10.0, compute=L.LSV2_F32, stream=None):
+    def query(self, text: torch.Tensor, out: torch.Tensor, tau: float = 10.0, compute=L.LSV2_F32, stream=None,
+              from_bf16: bool = False):
         Q, nt, D = text.shape
         need = L.lsv2_query_workspace_bytes(self.scene.levels, L_CODEBOOK, Q, nt - 1)
         if self.query_ws is None or self.query_ws.numel() < need:
             self.query_ws = torch.empty(need, dtype=torch.uint8, device=self.device)
         out_dt = L.LSV2_BF16 if out.dtype == torch.bfloat16 else L.LSV2_F32
-        L.lsv2_query(self.scene.levels, self.P, L_CODEBOOK, D, _ptr(self.coeff), L.LSV2_F32, _ptr(self.scene.codebook),
+        W, w_dt = (self.coeff16, L.LSV2_BF16) if from_bf16 else (self.coeff, L.LSV2_F32)
+        L.lsv2_query(self.scene.levels, self.P, L_CODEBOOK, D, _ptr(W), w_dt, _ptr(self.scene.codebook),
                      Q, nt - 1, _ptr(text), float(tau), _ptr(self.query_ws), need, _ptr(out), out_dt, compute,
                      _ptr(self.status), _stream(stream))
 
