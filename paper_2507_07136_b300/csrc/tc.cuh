@@ -173,7 +173,34 @@ __device__ __forceinline__ void bulk_store(void* gdst, uint32_t ssrc, uint32_t b
     asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(ssrc), "r"(bytes)
                  : "memory");
 }
+// Tiled TMA load of one box of a 3-D tensor map into shared memory, completing on an mbarrier
+// armed with the box bytes by the issuing thread (bulk_load_arm).  `map` is the generic address
+// of a __grid_constant__ CUtensorMap; x is in elements and must be a multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_3d(uint32_t sdst, const void* map, int x, int y, int z, uint32_t mbar_saddr)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(sdst),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(mbar_saddr)
+        : "memory");
+}
+
+// Tiled TMA store of one box from shared memory into a 3-D tensor map (bulk-group completion);
+// the part of the box outside the tensor is not written.  x as for tma_load_3d, y and z >= 0.
+__device__ __forceinline__ void tma_store_3d(const void* map, int x, int y, int z, uint32_t ssrc)
+{
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(map),
+                 "r"(x), "r"(y), "r"(z), "r"(ssrc)
+                 : "memory");
+}
+
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// Wait until at most N of this thread's most recent bulk groups still read shared memory.
+template <int N>
+__device__ __forceinline__ void bulk_wait_read()
+{
+    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
 __device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 

@@ -61,3 +61,34 @@ def test_f32_query_of_a_bf16_map_is_unsupported():
     with pytest.raises(L.LSV2Error) as e:
         fr.query(text, rel, compute=L.LSV2_F32, from_bf16=True)
     assert e.value.code == 2
+
+
+@pytest.mark.parametrize("D", [128, 256, 384, 512])
+@pytest.mark.parametrize("out_dtype", [torch.bfloat16, torch.float32])
+@pytest.mark.parametrize("size", [(141, 99), (10, 7)])
+def test_decode_from_bf16_map_widths(D, out_dtype, size):
+    """Every supported width and both output types, on a ragged frame (141x99 = 13959 pixels) and on
+    one smaller than a 128-pixel tile: the decode from the BF16 map equals the decode from the FP32
+    map bit for bit, and both are the FP64 product of the BF16-rounded operands within 1e-5 of
+    sum |W||S| (plus the output rounding for BF16 output)."""
+    sc = syn.make_scene(3000, 3, seed=12, mean_kind="uniform", mean_param=1.0, log_scale_mu=-3.2,
+                        log_scale_sigma=0.4, D=D)
+    ds = DeviceScene.from_numpy(sc)
+    fr = Frame(ds, syn.orbit_camera(size[0], size[1], 4.0))
+    fr.render()
+    fr.splat_bf16()
+    cb = ds.codebook.to(torch.bfloat16)
+    Fa = torch.full((ds.levels, fr.P, D), float("nan"), dtype=out_dtype, device="cuda")
+    Fb = torch.full_like(Fa, float("nan"))
+    fr.decode(Fa, codebook=cb)
+    fr.decode(Fb, codebook=cb, from_bf16=True)
+    fr.check()
+    assert torch.equal(Fa.view(torch.int16 if out_dtype == torch.bfloat16 else torch.int32),
+                       Fb.view(torch.int16 if out_dtype == torch.bfloat16 else torch.int32))
+    Wb = fr.coeff16.double().cpu().numpy()
+    Sb = cb.double().cpu().numpy()
+    ref = np.matmul(Wb, Sb)
+    bound = 1e-5 * np.matmul(np.abs(Wb), np.abs(Sb)) + 1e-9
+    if out_dtype == torch.bfloat16:
+        bound = bound + 2.0 ** -8 * np.abs(ref)
+    assert np.all(np.abs(Fb.double().cpu().numpy() - ref) <= bound)
