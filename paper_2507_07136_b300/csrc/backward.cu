@@ -239,7 +239,12 @@ struct BwdCfg {
     static constexpr int kRecFloats = bwd_record_floats(kPairs);
     static constexpr int kSmemRecFloats = kRecFloats - 4;  // staged without the 2D mean
     static constexpr int kSmemBytes = kWarps * (kGFloats + 32 * kSmemRecFloats) * 4;
+    // lane -> pixel as in the forward splat: each warp covers an 8 x 4 block, warps row-major
+    static constexpr int kWarpW = 8, kWarpH = 4, kWarpsX = TW / kWarpW;
+    __host__ __device__ static constexpr int lane_x(int warp, int lane) { return (warp % kWarpsX) * kWarpW + lane % kWarpW; }
+    __host__ __device__ static constexpr int lane_y(int warp, int lane) { return (warp / kWarpsX) * kWarpH + lane / kWarpW; }
     static_assert(kPairs + 6 <= 32, "quantities per Gaussian");
+    static_assert(TW % 8 == 0 && TH % 4 == 0 && (TW * TH) % 32 == 0, "warps cover 8 x 4 blocks of a tile");
 };
 
 template <int LEVELS, int K, int TW, int TH>
@@ -253,20 +258,18 @@ __global__ void __launch_bounds__(TW* TH) splat_backward_kernel(SplatBwdArgs a)
     const int GX = (a.cam.width + TW - 1) / TW;
     const int tile = blockIdx.x;
     const int tx = tile % GX, ty = tile / GX;
-    constexpr int kRows = 32 / TW;
-    const int lx = threadIdx.x % TW, ly = threadIdx.x / TW;
-    const int px = tx * TW + lx, py = ty * TH + ly;
+    const int px = tx * TW + C::lane_x(warp, lane), py = ty * TH + C::lane_y(warp, lane);
     const bool inside = px < a.cam.width && py < a.cam.height;
     const size_t P = (size_t)a.cam.width * a.cam.height;
     const size_t pix = (size_t)py * a.cam.width + px;
-    const float wx0 = (float)(tx * TW), wx1 = (float)(tx * TW + TW - 1);
-    const float wy0 = (float)(ty * TH + warp * kRows), wy1 = wy0 + (float)(kRows - 1);
+    const float wx0 = (float)(tx * TW + C::lane_x(warp, 0)), wx1 = wx0 + (float)(C::kWarpW - 1);
+    const float wy0 = (float)(ty * TH + C::lane_y(warp, 0)), wy1 = wy0 + (float)(C::kWarpH - 1);
 
     // stage dLoss/dW of this warp's pixels as columns gW[col][lane]
     for (int lev = 0; lev < LEVELS; ++lev)
         for (int q = lane; q < 32 * 16; q += 32) {
             const int pl = q >> 4, c4 = (q & 15) * 4;
-            const int gx = tx * TW + (pl % TW), gy = ty * TH + warp * kRows + pl / TW;
+            const int gx = tx * TW + C::lane_x(warp, pl), gy = ty * TH + C::lane_y(warp, pl);
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
             if (gx < a.cam.width && gy < a.cam.height)
                 v = __ldg(reinterpret_cast<const float4*>(a.dcoeff + ((size_t)lev * P + (size_t)gy * a.cam.width + gx) * 64 + c4));

@@ -79,8 +79,8 @@ struct FusedBars {
 __device__ __forceinline__ bool tile_pixel(const FusedArgs& a, int tile, int h, int q, int lane, size_t& pix)
 {
     const int tx = tile % a.GX, ty = tile / a.GX;
-    const int sw = 4 * h + q;   // splat warp: 2 rows of 16 pixels
-    const int px = tx * kTW + (lane % kTW), py = ty * kTH + sw * (32 / kTW) + lane / kTW;
+    const int sw = 4 * h + q;   // splat warp
+    const int px = tx * kTW + FC::lane_x(sw, lane), py = ty * kTH + FC::lane_y(sw, lane);
     pix = (size_t)py * a.width + px;
     return px < a.width && py < a.height;
 }

@@ -51,7 +51,13 @@ struct SplatCfg {
     // share an SM; fewer warps: 4 stages
     static constexpr int kStages = kWarps >= 8 ? (kStagesFit < 8 ? kStagesFit : 8) : (kWarps >= 4 ? 2 : 4);
     static constexpr int kSmemBytes = kFixedBytes + kStages * kStageBytes;
-    static_assert(kPixels % 32 == 0 && 32 % TW == 0, "a warp covers whole rows of a tile");
+    // lane -> pixel: each consumer warp covers an 8 x 4 block of the TW x TH block (warps in
+    // row-major order).  A square-ish block keeps more of a warp's lanes inside the footprints
+    // that pass its culling test than a 16 x 2 or 32 x 1 strip.
+    static constexpr int kWarpW = 8, kWarpH = 4, kWarpsX = TW / kWarpW;
+    __host__ __device__ static constexpr int lane_x(int warp, int lane) { return (warp % kWarpsX) * kWarpW + lane % kWarpW; }
+    __host__ __device__ static constexpr int lane_y(int warp, int lane) { return (warp / kWarpsX) * kWarpH + lane / kWarpW; }
+    static_assert(kPixels % 32 == 0 && TW % 8 == 0 && TH % 4 == 0, "warps cover 8 x 4 blocks of a tile");
     static_assert(kPairs <= kMaxPairs, "pairs per record");
     static_assert(kRecBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
     static_assert(kStages >= 2, "at least two stages");

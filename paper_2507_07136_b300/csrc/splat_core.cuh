@@ -148,13 +148,11 @@ __device__ uint32_t splat_consume(const TileJob& a, const SplatSmem<C>& sm, int 
     float* acc = sm.acc + warp * C::kAccFloats;
     unsigned char* acc_lane = reinterpret_cast<unsigned char*>(acc + lane);
 
-    const int lx = lane % TW, ly = warp * (32 / TW) + lane / TW;
-    const int px = a.x0 + lx, py = a.y0 + ly;
+    const int px = a.x0 + C::lane_x(warp, lane), py = a.y0 + C::lane_y(warp, lane);
     const bool inside = px < a.width && py < a.height;
-    // pixel strip covered by this warp
-    constexpr int kRows = 32 / TW;
-    const float wx0 = (float)a.x0, wx1 = (float)(a.x0 + TW - 1);
-    const float wy0 = (float)(a.y0 + warp * kRows), wy1 = wy0 + (float)(kRows - 1);
+    // pixel block covered by this warp
+    const float wx0 = (float)(a.x0 + C::lane_x(warp, 0)), wx1 = wx0 + (float)(C::kWarpW - 1);
+    const float wy0 = (float)(a.y0 + C::lane_y(warp, 0)), wy1 = wy0 + (float)(C::kWarpH - 1);
 
     for (int i = lane * 4; i < C::kAccFloats; i += 128)
         *reinterpret_cast<float4*>(acc + i) = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -290,16 +288,16 @@ __device__ uint32_t splat_consume(const TileJob& a, const SplatSmem<C>& sm, int 
     }
     __syncwarp();
     if (!kWriteCoeff) return consumed;
-    // write this warp's 32 pixels: per row segment TW pixels x 64 coefficients (contiguous in HBM)
+    // write this warp's 32 pixels (each pixel's 64 coefficients of a level are contiguous in HBM)
     const size_t P = (size_t)a.width * a.height;
     if (a.coeff_bf16) {
         __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(a.coeff);
 #pragma unroll 1
         for (int lev = 0; lev < LEVELS; ++lev) {
             for (int q = lane; q < 32 * 8; q += 32) {
-                const int pl = q >> 3;  // pixel within the warp (row-major over the strip)
+                const int pl = q >> 3;  // pixel within the warp (its lane)
                 const int c8 = (q & 7) * 8;
-                const int gx = a.x0 + (pl % TW), gy = a.y0 + warp * kRows + pl / TW;
+                const int gx = a.x0 + C::lane_x(warp, pl), gy = a.y0 + C::lane_y(warp, pl);
                 if (gx < a.width && gy < a.height) {
                     const float* col = acc + (lev * 64 + c8) * 33 + pl;
                     const uint4 val = make_uint4(tc::pack_bf16(col[0], col[33]), tc::pack_bf16(col[66], col[99]),
@@ -313,9 +311,9 @@ __device__ uint32_t splat_consume(const TileJob& a, const SplatSmem<C>& sm, int 
 #pragma unroll 1
     for (int lev = 0; lev < LEVELS; ++lev) {
         for (int q = lane; q < 32 * 16; q += 32) {
-            const int pl = q >> 4;  // pixel within the warp (row-major over the strip)
+            const int pl = q >> 4;  // pixel within the warp (its lane)
             const int c4 = (q & 15) * 4;
-            const int gx = a.x0 + (pl % TW), gy = a.y0 + warp * kRows + pl / TW;
+            const int gx = a.x0 + C::lane_x(warp, pl), gy = a.y0 + C::lane_y(warp, pl);
             if (gx < a.width && gy < a.height) {
                 const float* col = acc + (lev * 64 + c4) * 33 + pl;
                 float4 val = make_float4(col[0], col[33], col[66], col[99]);
