@@ -277,6 +277,40 @@ def batched_section(dev, reps: int = 5, rank: int = 0, world: int = 1):
 
 
 # ----------------------------------------------------------------------------- GPU arm
+def profile_stage(args, frame, scene, text, dev):
+    """One stage of the at-scale frame, repeated, for a profiler: the device holds the scene, the
+    frame's buffers and the stage's output only (the decode writes one level's 1.59 GB feature
+    map: the same kernel over the level's 1,555,200 pixels, its grid spread over one level)."""
+    import torch
+    from paper_2507_07136_b300 import _lib as Lb
+    from paper_2507_07136_b300.pipeline import _ptr, L_CODEBOOK
+    frame.project()
+    frame.bin_sort()
+    frame.splat_bf16()
+    P, D = frame.P, scene.D
+    if args.profile == "splat":
+        fn = frame.splat_bf16
+    elif args.profile == "decode":
+        F = torch.empty((1, P, D), dtype=torch.bfloat16, device=dev)
+        cb16 = scene.codebook[:1].to(torch.bfloat16).contiguous()
+        stream = torch.cuda.current_stream().cuda_stream
+
+        def fn():
+            Lb.lsv2_decode(1, P, L_CODEBOOK, D, _ptr(frame.coeff16), Lb.LSV2_BF16, _ptr(cb16), Lb.LSV2_BF16, _ptr(F),
+                           Lb.LSV2_BF16, _ptr(frame.status), stream)
+    else:
+        text_d = torch.as_tensor(text, device=dev)
+        rel = torch.empty((text.shape[0], scene.levels, P), dtype=torch.float32, device=dev)
+
+        def fn():
+            frame.query(text_d, rel, compute=Lb.LSV2_BF16, from_bf16=True)
+    for _ in range(args.warmup + args.steps):
+        fn()
+    frame.check()
+    print(json.dumps({"profile": args.profile, "launches": args.warmup + args.steps,
+                      "device_gb": round(torch.cuda.max_memory_allocated(dev) / 1e9, 2)}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -287,6 +321,9 @@ def main():
     ap.add_argument("--no-fp32-path", action="store_true", help="skip the plain FP32 comparison measurement")
     ap.add_argument("--no-batched", action="store_true", help="skip the 16-view x 64-query batched measurement")
     ap.add_argument("--no-ablation", action="store_true", help="skip the sparse/dense and K speed ablation")
+    ap.add_argument("--profile", choices=["splat", "decode", "query"], default=None,
+                    help="for a profiler capture: prepare the at-scale frame, then run only this stage "
+                         "(--warmup + --steps launches) with only the buffers it needs; prints one status line")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)
@@ -311,6 +348,9 @@ def main():
     frame = Frame(scene, cam, device=dev)
     P = cam.num_pixels
     levels, D = scene.levels, scene.D
+    if args.profile:
+        profile_stage(args, frame, scene, text, dev)
+        return
     F = torch.empty((levels, P, D), dtype=torch.bfloat16, device=dev)
     cb16 = scene.codebook.to(torch.bfloat16)
     text_d = torch.as_tensor(text, device=dev)

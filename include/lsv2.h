@@ -218,8 +218,8 @@ size_t lsv2_query_workspace_bytes(int32_t levels, int32_t L, int32_t Q, int32_t 
  *   text     float[Q][1 + n_neg][D]  (positive first)
  *   rel      [Q][levels][P]  dtype rel_dtype (F32 or BF16)
  * compute_dtype F32: FP32 FMA on CUDA cores (rel_dtype F32).  BF16: tcgen05 tensor cores with
- * W and [G | u] rounded to BF16 and FP32 accumulation.  S S^T and S t are formed per call with
- * FP64 accumulation.  L = 64, D % 4 == 0, n_neg >= 1; BF16: 64 + (1 + n_neg) * 8 * ceil(Q / 8)
+ * W and [G | u] rounded to BF16 and FP32 accumulation.  S S^T and S t are formed per call in
+ * twice-FP32 precision (error-free products and sums) and rounded to FP32.  L = 64, D % 4 == 0, n_neg >= 1; BF16: 64 + (1 + n_neg) * 8 * ceil(Q / 8)
  * <= 512 (Q <= 88 at n_neg = 4); F32: Q (1 + n_neg) <= 512.  All arrays 16-byte aligned.
  * A bounded device wait that expires sets LSV2_ERR_TIMEOUT. */
 lsv2_status lsv2_query(int32_t levels, int64_t P, int32_t L, int32_t D, const void* coeff,

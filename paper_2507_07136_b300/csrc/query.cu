@@ -3,7 +3,7 @@
 // The rendered feature is F = W S, so for a text embedding t
 //     <F, t> = W . (S t),     |F|^2 = W^T (S S^T) W,
 // and the relevancy never needs the D-dim feature map.  Per level a small prepare kernel
-// forms, in FP64 accumulation rounded to float, the columns of
+// forms, accumulated in twice-FP32 precision and rounded to float, the columns of
 //     B = [ S S^T | S t_0 | S t_1 | ... ]            (64 x (64 + #texts))
 // and the text norms; the main kernel gives every (pixel, level) one thread that holds W in
 // registers, forms y = W^T B column by column (B^T in shared memory, read as warp-wide
@@ -17,38 +17,62 @@ namespace {
 
 constexpr int kL = 64;
 
-// grid (64 + nt, levels), 64 threads (one per codebook row k): B^T[lev][j][k] = <x_j, S_k> with
-// x_j = S_j (j < 64, Gram rows) or the text vector j - 64; FP64 accumulation, rounded to float.
-// Also the text norms (level 0 only).
-__global__ void __launch_bounds__(64) query_prepare_kernel(int D, int nt, const float* __restrict__ S,
-                                                           const float* __restrict__ text,
-                                                           float* __restrict__ Bt, float* __restrict__ tnorm)
+// Dot2 step (Ogita, Rump and Oishi, "Accurate sum and dot product", 2005): add a * b to the
+// unevaluated sum hi + lo with an error-free product (FMA remainder) and an error-free sum
+// (TwoSum), so that the result is as accurate as one accumulated in twice the precision.
+__device__ __forceinline__ void dot2_step(float a, float b, float& hi, float& lo)
+{
+    const float p = __fmul_rn(a, b);
+    const float pe = __fmaf_rn(a, b, -p);
+    const float s = __fadd_rn(hi, p);
+    const float bp = __fsub_rn(s, hi);
+    const float se = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(se, pe));
+}
+
+// grid (64 + nt, levels), 256 threads: B^T[lev][j][k] = <x_j, S_k> with x_j = S_j (j < 64, Gram
+// rows) or the text vector j - 64.  Thread (k = t % 64, part = t / 64) accumulates the terms
+// d = 4 part + 16 i (+ 0..3) in Dot2 form; the four parts are added in FP64 and rounded to float.
+// Also the text norms (level 0 only), the same way.
+__global__ void __launch_bounds__(256) query_prepare_kernel(int D, int nt, const float* __restrict__ S,
+                                                            const float* __restrict__ text,
+                                                            float* __restrict__ Bt, float* __restrict__ tnorm)
 {
     extern __shared__ float xs[];
-    __shared__ double red[2];
-    const int j = blockIdx.x, lev = blockIdx.y, k = threadIdx.x;
+    __shared__ double part_sum[4][kL];
+    __shared__ double red[8];
+    const int j = blockIdx.x, lev = blockIdx.y, t = threadIdx.x, k = t & 63, part = t >> 6;
     const int ncol = kL + nt;
     const float* Sl = S + (size_t)lev * kL * D;
     const float* x = j < kL ? Sl + (size_t)j * D : text + (size_t)(j - kL) * D;
-    for (int d = k; d < D; d += 64) xs[d] = x[d];
+    for (int d = t; d < D; d += 256) xs[d] = x[d];
     __syncthreads();
     const float* sk = Sl + (size_t)k * D;
-    double acc = 0.0;
-    for (int d = 0; d < D; d += 4) {
+    float hi = 0.0f, lo = 0.0f;
+    for (int d = part * 4; d < D; d += 16) {
         const float4 s4 = __ldg(reinterpret_cast<const float4*>(sk + d));
-        acc = fma((double)xs[d], (double)s4.x, acc);
-        acc = fma((double)xs[d + 1], (double)s4.y, acc);
-        acc = fma((double)xs[d + 2], (double)s4.z, acc);
-        acc = fma((double)xs[d + 3], (double)s4.w, acc);
+        dot2_step(xs[d], s4.x, hi, lo);
+        dot2_step(xs[d + 1], s4.y, hi, lo);
+        dot2_step(xs[d + 2], s4.z, hi, lo);
+        dot2_step(xs[d + 3], s4.w, hi, lo);
     }
-    Bt[((size_t)lev * ncol + j) * kL + k] = (float)acc;
+    part_sum[part][k] = (double)hi + (double)lo;
+    __syncthreads();
+    if (part == 0)
+        Bt[((size_t)lev * ncol + j) * kL + k] = (float)((part_sum[0][k] + part_sum[1][k]) + (part_sum[2][k] + part_sum[3][k]));
     if (lev == 0 && j >= kL) {
-        double q = 0.0;
-        for (int d = k; d < D; d += 64) q = fma((double)xs[d], (double)xs[d], q);
+        float qh = 0.0f, ql = 0.0f;
+        for (int d = t; d < D; d += 256) dot2_step(xs[d], xs[d], qh, ql);
+        double q = (double)qh + (double)ql;
         for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
-        if ((k & 31) == 0) red[k >> 5] = q;
+        if ((t & 31) == 0) red[t >> 5] = q;
         __syncthreads();
-        if (k == 0) tnorm[j - kL] = (float)sqrt(red[0] + red[1]);
+        if (t == 0) {
+            double sum = 0.0;
+            for (int w = 0; w < 8; ++w) sum += red[w];
+            tnorm[j - kL] = (float)sqrt(sum);
+        }
     }
 }
 
@@ -137,7 +161,9 @@ cudaError_t launch_query_prepare(int levels, int D, int nt, const float* S, cons
     float* tnorm = reinterpret_cast<float*>(static_cast<char*>(ws) +
                                             ((size_t)levels * (kL + nt) * kL * 4 + 255) / 256 * 256);
     dim3 grid((unsigned)(kL + nt), (unsigned)levels);
-    query_prepare_kernel<<<grid, 64, (size_t)D * 4, stream>>>(D, nt, S, text, Bt, tnorm);
+    cudaError_t e = cudaFuncSetAttribute(query_prepare_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, D * 4);
+    if (e != cudaSuccess) return e;
+    query_prepare_kernel<<<grid, 256, (size_t)D * 4, stream>>>(D, nt, S, text, Bt, tnorm);
     return cudaGetLastError();
 }
 

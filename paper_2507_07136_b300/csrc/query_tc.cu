@@ -15,6 +15,7 @@
 // operand, one thread issues the MMA.  All waits are bounded.
 #include "query_tc.cuh"
 #include "tc.cuh"
+#include "tmap.cuh"
 
 namespace lsv2 {
 namespace {
@@ -291,6 +292,253 @@ __global__ void __launch_bounds__(NT, 512 / NT) query_tc_kernel(QueryTcArgs a)
             (void)tc::mbar_wait(tc::smem_u32(full + (int)(i % kStages)), (uint32_t)((i / kStages) & 1), 100000000ull);
 }
 
+// ---- Pipelined form for a BF16 coefficient map and N <= 256 columns --------------------------
+// Warp 0 streams W tiles into a ring of shared-memory stages with TMA tensor loads (the map's
+// 128-byte swizzle is the MMA operand layout, so no copy or conversion); warp 1 issues each
+// tile's MMA into one of kNb TMEM accumulators (kNb = 512 / columns, 2 or 4); warps 2..9 form two
+// epilogue warpgroups that take alternate tiles.  The epilogue releases the W stage once it has
+// read its pixel rows (for |F|^2) and the accumulator once its TMEM loads are done, through
+// mbarriers, so tiles overlap: no block-wide barrier per tile.  W is addressed as rows of 64
+// BF16 (row = view offset + level * P_v + pixel); a level's ragged last tile loads rows of the
+// next level (or zeros past the end), whose results are not stored.
+
+constexpr int kPStages = 8;
+constexpr int kPThreads = 320;
+
+__host__ __device__ constexpr size_t pipe_smem_bytes(int npad, int ntp)
+{
+    return 1024 + (size_t)kPStages * kM * 128 + (size_t)npad * 128 + (((size_t)ntp * 4 + 15) & ~size_t(15)) + 256;
+}
+
+// Bounded wait on a barrier phase: false once the CTA's abort flag is up, or after 1 s (which
+// raises the flag).
+__device__ __forceinline__ bool pipe_wait(uint32_t bar, uint32_t parity, volatile int* abort)
+{
+    const uint64_t t0 = tc::globaltimer();
+    while (!tc::mbar_try(bar, parity)) {
+        if (*abort) return false;
+        if (tc::globaltimer() - t0 > 1000000000ull) {
+            *abort = 1;
+            return false;
+        }
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(kPThreads, 1) query_pipe_kernel(const __grid_constant__ CUtensorMap tmW, QueryTcArgs a)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t* ring = smem;                                        // kPStages x (128 x 128 bytes)
+    uint8_t* sB = ring + (size_t)kPStages * kM * 128;
+    float* sTn = reinterpret_cast<float*>(sB + (size_t)a.npad * 128);
+    const int per = 1 + a.n_neg;
+    const int ntp = per * a.Qp;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(sTn) + (((size_t)ntp * 4 + 15) & ~size_t(15)));
+    uint64_t* w_full = bar;                  // [kPStages] W tile landed (transaction bytes)
+    uint64_t* w_empty = bar + kPStages;      // [kPStages] the epilogue has read the tile's rows (4 warps)
+    uint64_t* m_full = bar + 2 * kPStages;   // [4] accumulator b holds its tile (MMA commit)
+    uint64_t* t_empty = m_full + 4;          // [4] accumulator b has been read (4 warps)
+    volatile int* abort = reinterpret_cast<volatile int*>(t_empty + 4);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(t_empty + 5);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int lev = blockIdx.y;
+    const uint32_t bufcols = tmem_cols(a.npad);
+    const int nb = (int)(512u / bufcols) >= 4 ? 4 : 2;
+    const uint32_t ncols_alloc = (uint32_t)nb * bufcols;
+    const int64_t ntiles = a.total_tiles;
+    auto locate = [&](int64_t tile, int& v, int64_t& p0) {
+        v = 0;
+        while (v + 1 < a.nseg && tile >= a.seg[v + 1].tile_base) ++v;
+        p0 = (tile - a.seg[v].tile_base) * kM;
+    };
+    const int64_t my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+
+    if (warp == 0) tc::tmem_alloc(tc::smem_u32(tslot), ncols_alloc);
+    if (tid == 0) {
+        for (int s = 0; s < kPStages; ++s) {
+            tc::mbar_init(tc::smem_u32(w_full + s), 1);
+            tc::mbar_init(tc::smem_u32(w_empty + s), 4);
+        }
+        for (int b = 0; b < 4; ++b) {
+            tc::mbar_init(tc::smem_u32(m_full + b), 1);
+            tc::mbar_init(tc::smem_u32(t_empty + b), 4);
+        }
+        *abort = 0;
+    }
+    // B^T rows as in query_tc_kernel: S S^T, then the text rows text-major, zero padding
+    const float* Bl = a.Bt + (size_t)lev * (64 + a.Q * per) * kK;
+    for (int i = tid; i < a.npad * kK; i += kPThreads) {
+        const int n = i >> 6, k = i & 63;
+        int src = n < 64 ? n : -1;
+        if (n >= 64 && n < 64 + ntp) {
+            const int t = (n - 64) / a.Qp, q = (n - 64) % a.Qp;
+            src = q < a.Q ? 64 + q * per + t : -1;
+        }
+        const float v = src >= 0 ? Bl[(size_t)src * kK + k] : 0.0f;
+        *reinterpret_cast<__nv_bfloat16*>(sB + tc::sw128(n, k)) = __float2bfloat16_rn(v);
+    }
+    for (int i = tid; i < ntp; i += kPThreads) {
+        const int t = i / a.Qp, q = i % a.Qp;
+        sTn[i] = q < a.Q ? 1.0f / a.tnorm[q * per + t] : 0.0f;
+    }
+    tc::fence_proxy_async();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (warp == 0) {
+        // TMA producer
+        if (lane == 0) {
+            int64_t issued = 0;
+            for (int64_t i = 0; i < my_tiles; ++i) {
+                const int s = (int)(i % kPStages);
+                if (i >= kPStages && !pipe_wait(tc::smem_u32(w_empty + s), (uint32_t)((i / kPStages - 1) & 1), abort))
+                    break;
+                int v;
+                int64_t p0;
+                locate(blockIdx.x + i * gridDim.x, v, p0);
+                const int64_t row = (int64_t)(a.seg[v].w_off / kK) + (int64_t)lev * a.seg[v].P + p0;
+                tc::bulk_load_arm(tc::smem_u32(w_full + s), kM * 128);
+                tc::tma_load_3d(tc::smem_u32(ring + (size_t)s * kM * 128), &tmW, 0, (int)row, 0, tc::smem_u32(w_full + s));
+                issued = i + 1;
+            }
+            // no copy may still be landing when the CTA retires
+            for (int64_t i = issued > kPStages ? issued - kPStages : 0; i < issued; ++i)
+                (void)tc::mbar_wait(tc::smem_u32(w_full + (int)(i % kPStages)), (uint32_t)((i / kPStages) & 1), 100000000ull);
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // MMA issuer
+        if (lane == 0) {
+            int64_t done = 0;
+            for (int64_t i = 0; i < my_tiles; ++i) {
+                const int s = (int)(i % kPStages), b = (int)(i % nb);
+                if (!pipe_wait(tc::smem_u32(w_full + s), (uint32_t)((i / kPStages) & 1), abort)) break;
+                if (i >= nb && !pipe_wait(tc::smem_u32(t_empty + b), (uint32_t)((i / nb - 1) & 1), abort)) break;
+                tc::fence_after();
+                const uint32_t a0 = tc::smem_u32(ring + (size_t)s * kM * 128), b0 = tc::smem_u32(sB);
+                const uint32_t idesc = tc::idesc_bf16(kM, a.npad);
+#pragma unroll
+                for (int k = 0; k < kK / 16; ++k)
+                    tc::mma_bf16(tmem + (uint32_t)b * bufcols, tc::desc_sw128(a0 + k * 32), tc::desc_sw128(b0 + k * 32),
+                                 idesc, k > 0 ? 1u : 0u);
+                tc::mma_commit(tc::smem_u32(m_full + b));
+                done = i + 1;
+            }
+            // no MMA may still be writing TMEM when it is freed
+            if (done > 0) {
+                const int64_t i = done - 1;
+                (void)tc::mbar_wait(tc::smem_u32(m_full + (int)(i % nb)), (uint32_t)((i / nb) & 1), 100000000ull);
+            }
+        }
+        __syncwarp();
+    } else {
+        // epilogue: warpgroup g takes local tiles g, g + 2, ...; this warp owns TMEM lane quarter q4
+        const int g = (warp - 2) >> 2, q4 = warp & 3;
+        const int row = q4 * 32 + lane;
+        const int nch = a.Qp / 8;
+        for (int64_t i = g; i < my_tiles; i += 2) {
+            const int s = (int)(i % kPStages), b = (int)(i % nb);
+            if (!__all_sync(0xffffffffu, pipe_wait(tc::smem_u32(m_full + b), (uint32_t)((i / nb) & 1), abort))) break;
+            // (already complete) acquire of the TMA's writes of the W stage read below; the stage
+            // is reloaded only after this warpgroup releases it, so the phase cannot move on
+            if (!__all_sync(0xffffffffu, pipe_wait(tc::smem_u32(w_full + s), (uint32_t)((i / kPStages) & 1), abort)))
+                break;
+            tc::fence_after();
+            int vw;
+            int64_t p0;
+            locate(blockIdx.x + i * gridDim.x, vw, p0);
+            const int64_t Pv = a.seg[vw].P;
+            const uint32_t trow = tmem + (uint32_t)b * bufcols + ((uint32_t)(q4 * 32) << 16);
+            const uint8_t* sA = ring + (size_t)s * kM * 128;
+            // |F|^2 = W . (G W): columns 0..63 of Y, W from the landed (swizzled) BF16 tile
+            float n2 = 0.0f;
+            for (int c = 0; c < 64; c += 32) {
+                uint32_t r[32];
+                tc::tmem_ld32(trow + (uint32_t)c, r);
+                tc::tmem_wait_ld();
+#pragma unroll
+                for (int kc = 0; kc < 4; ++kc) {
+                    const uint4 wq = *reinterpret_cast<const uint4*>(sA + row * 128 + ((((c >> 3) + kc) ^ (row & 7)) << 4));
+                    const uint32_t wv[4] = {wq.x, wq.y, wq.z, wq.w};
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        const __nv_bfloat162 w2 = *reinterpret_cast<const __nv_bfloat162*>(&wv[h]);
+                        n2 = fmaf(__low2float(w2), __uint_as_float(r[kc * 8 + 2 * h]), n2);
+                        n2 = fmaf(__high2float(w2), __uint_as_float(r[kc * 8 + 2 * h + 1]), n2);
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(tc::smem_u32(w_empty + s));
+            const float nf = sqrtf(fmaxf(n2, 0.0f));
+            const float kneg = nf < 1e-12f ? 0.0f : -a.tau / nf;
+            const int64_t p = p0 + row;
+            for (int c = 0; c < nch; ++c) {
+                const int q0 = c * 8;
+                uint32_t rp[8], rn[8];
+                tc::tmem_ld8(trow + (uint32_t)(64 + q0), rp);
+                float best[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) best[j] = -INFINITY;
+                for (int t = 1; t < per; ++t) {
+                    tc::tmem_ld8(trow + (uint32_t)(64 + t * a.Qp + q0), rn);
+                    tc::tmem_wait_ld();
+                    const float4 u0 = *reinterpret_cast<const float4*>(sTn + t * a.Qp + q0);
+                    const float4 u1 = *reinterpret_cast<const float4*>(sTn + t * a.Qp + q0 + 4);
+                    const float tn[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) best[j] = fmaxf(best[j], __uint_as_float(rn[j]) * tn[j]);
+                }
+                tc::tmem_wait_ld();
+                if (c == nch - 1) {
+                    // the last TMEM load of this tile is done: release the accumulator
+                    tc::fence_before();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(tc::smem_u32(t_empty + b));
+                }
+                const float4 u0 = *reinterpret_cast<const float4*>(sTn + q0);
+                const float4 u1 = *reinterpret_cast<const float4*>(sTn + q0 + 4);
+                const float tp[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+                if (p < Pv) {
+                    const size_t stride = (size_t)a.levels * Pv;
+                    const size_t o0 = a.seg[vw].rel_off + (size_t)lev * Pv + p + (size_t)q0 * stride;
+                    const int nq = a.Q - q0 < 8 ? a.Q - q0 : 8;
+                    if (a.rel_bf16) {
+                        __nv_bfloat16* out = static_cast<__nv_bfloat16*>(a.rel) + o0;
+                        const float hk = -0.5f * kneg;
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            if (j >= nq) break;
+                            const float d = __uint_as_float(rp[j]) * tp[j] - (per > 1 ? best[j] : 0.0f);
+                            float th;
+                            asm("tanh.approx.f32 %0, %1;" : "=f"(th) : "f"(hk * d));
+                            out[(size_t)j * stride] = __float2bfloat16_rn(fmaf(0.5f, th, 0.5f));
+                        }
+                    } else {
+                        float* out = static_cast<float*>(a.rel) + o0;
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            if (j >= nq) break;
+                            const float d = __uint_as_float(rp[j]) * tp[j] - (per > 1 ? best[j] : 0.0f);
+                            out[(size_t)j * stride] = __fdividef(1.0f, 1.0f + __expf(kneg * d));
+                        }
+                    }
+                }
+            }
+        }
+    }
+    if (tid == 0 && *abort) report(a.status, LSV2_ERR_TIMEOUT);
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after();
+        tc::tmem_dealloc(tmem, ncols_alloc);
+    }
+}
+
 }  // namespace
 
 bool query_tc_supported(int Q, int n_neg)
@@ -335,6 +583,22 @@ cudaError_t launch_query_tc_views(int levels, int V, const int64_t* P, int Q, in
     a.seg[V] = QuerySeg{0, tiles, w_off, rel_off};
     a.total_tiles = tiles;
     if (tiles == 0) return cudaSuccess;
+    if (w_bf16 && tmem_cols(npad) <= 256) {
+        // pipelined form: W as rows of 64 BF16 over all views and levels
+        CUtensorMap tmW;
+        if (!encode_tmap_3d(&tmW, W, true, (uint64_t)kK, (uint64_t)(w_off / kK), 1u, (uint32_t)kK, (uint32_t)kM, true))
+            return cudaErrorInvalidValue;
+        size_t smem = pipe_smem_bytes(npad, ntp);
+        if (smem < 117760) smem = 117760;   // one CTA per SM: its TMEM allocation never waits
+        if (smem > 232448) return cudaErrorInvalidValue;
+        cudaError_t e = cudaFuncSetAttribute(query_pipe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int per_level = num_sms / levels;
+        if (per_level < 1) per_level = 1;
+        if (per_level > tiles) per_level = (int)tiles;
+        query_pipe_kernel<<<dim3(per_level, levels), kPThreads, smem, stream>>>(tmW, a);
+        return cudaGetLastError();
+    }
     // Two CTAs per SM when their TMEM allocations fit (one CTA's MMA and W conversion overlap the
     // other's epilogue); the shared-memory request keeps one more CTA from being resident, so
     // tcgen05.alloc never waits on another CTA.

@@ -92,3 +92,25 @@ def test_decode_from_bf16_map_widths(D, out_dtype, size):
     if out_dtype == torch.bfloat16:
         bound = bound + 2.0 ** -8 * np.abs(ref)
     assert np.all(np.abs(Fb.double().cpu().numpy() - ref) <= bound)
+
+
+@pytest.mark.parametrize("Q,n_neg", [(1, 1), (1, 4), (5, 4), (8, 1), (9, 4), (17, 3), (32, 4)])
+@pytest.mark.parametrize("out_dtype", [torch.float32, torch.bfloat16])
+@pytest.mark.parametrize("size", [(141, 99), (10, 7)])
+def test_query_from_bf16_map_counts(Q, n_neg, out_dtype, size):
+    """Relevancy from the BF16 map (TMA-fed pipelined kernel, 2 or 4 TMEM accumulators by column
+    count) equals the relevancy from the FP32 map (rounded to BF16 in the kernel) bit for bit:
+    query counts ragged against the 8-query chunks, both output types, a ragged frame and one
+    smaller than a 128-pixel tile (its rows past a level's end belong to the next level)."""
+    sc = syn.make_scene(3000, 3, seed=13, mean_kind="uniform", mean_param=1.0, log_scale_mu=-3.2, log_scale_sigma=0.4)
+    fr = Frame(DeviceScene.from_numpy(sc), syn.orbit_camera(size[0], size[1], 4.0))
+    fr.render()
+    fr.splat_bf16()
+    text = torch.as_tensor(syn.text_queries(syn.SEED + 21, Q, n_neg), device="cuda")
+    ra = torch.full((Q, 3, fr.P), float("nan"), dtype=out_dtype, device="cuda")
+    rb = torch.full_like(ra, float("nan"))
+    fr.query(text, ra, compute=L.LSV2_BF16)
+    fr.query(text, rb, compute=L.LSV2_BF16, from_bf16=True)
+    fr.check()
+    assert not torch.isnan(rb).any()
+    assert torch.equal(ra, rb)
