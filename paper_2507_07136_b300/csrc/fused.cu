@@ -27,6 +27,7 @@
 
 #include "query.cuh"
 #include "splat_core.cuh"
+#include "gram.cuh"
 
 namespace lsv2 {
 namespace {
@@ -310,22 +311,13 @@ __global__ void __launch_bounds__(FC::kThreads, 1) fused_kernel(FusedArgs a)
                     const bool in = tile_pixel(a, tile, h, q4, lane, pix);
                     // |F|^2 = W . (S S^T W): columns 0..63, W from this level's A tile
                     const uint8_t* A = smem + kAOff + (l * 2 + h) * kATile;
-                    float n2 = 0.0f;
-                    for (int c = 0; c < 64; c += 32) {
-                        uint32_t r[32];
-                        tc::tmem_ld32(lrow + 256u + (uint32_t)c, r);
+                    float n2;
+                    {
+                        uint32_t y0[32], y1[32];
+                        tc::tmem_ld32(lrow + 256u, y0);
+                        tc::tmem_ld32(lrow + 256u + 32u, y1);
                         tc::tmem_wait_ld();
-#pragma unroll
-                        for (int kc = 0; kc < 4; ++kc) {
-                            const uint4 wq = *reinterpret_cast<const uint4*>(A + tc::sw128(row, c + 8 * kc));
-                            const uint32_t wv[4] = {wq.x, wq.y, wq.z, wq.w};
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                const __nv_bfloat162 w2 = *reinterpret_cast<const __nv_bfloat162*>(&wv[e]);
-                                n2 = fmaf(__low2float(w2), __uint_as_float(r[kc * 8 + 2 * e]), n2);
-                                n2 = fmaf(__high2float(w2), __uint_as_float(r[kc * 8 + 2 * e + 1]), n2);
-                            }
-                        }
+                        n2 = gram_norm2(A, row, y0, y1);
                     }
                     const float nf = sqrtf(fmaxf(n2, 0.0f));
                     const float kneg = nf < 1e-12f ? 0.0f : -a.tau / nf;

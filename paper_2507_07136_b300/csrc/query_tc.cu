@@ -16,6 +16,7 @@
 #include "query_tc.cuh"
 #include "tc.cuh"
 #include "tmap.cuh"
+#include "gram.cuh"
 
 namespace lsv2 {
 namespace {
@@ -206,23 +207,14 @@ __global__ void __launch_bounds__(NT, 512 / NT) query_tc_kernel(QueryTcArgs a)
         phase ^= 1u;
         tc::fence_after();
         const int64_t p = p0 + row;
-        // |F|^2 = W . (G W): columns 0..63 of Y, W from the staged BF16 tile (16-byte chunks)
-        float n2 = 0.0f;
-        for (int c = 0; c < 64; c += 32) {
-            uint32_t r[32];
-            tc::tmem_ld32(trow + (uint32_t)c, r);
+        // |F|^2 = W . (G W): columns 0..63 of Y, W from the staged BF16 tile
+        float n2;
+        {
+            uint32_t y0[32], y1[32];
+            tc::tmem_ld32(trow, y0);
+            tc::tmem_ld32(trow + 32u, y1);
             tc::tmem_wait_ld();
-#pragma unroll
-            for (int kc = 0; kc < 4; ++kc) {
-                const uint4 wq = *reinterpret_cast<const uint4*>(sA + row * 128 + ((((c >> 3) + kc) ^ (row & 7)) << 4));
-                const uint32_t wv[4] = {wq.x, wq.y, wq.z, wq.w};
-#pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    const __nv_bfloat162 w2 = *reinterpret_cast<const __nv_bfloat162*>(&wv[h]);
-                    n2 = fmaf(__low2float(w2), __uint_as_float(r[kc * 8 + 2 * h]), n2);
-                    n2 = fmaf(__high2float(w2), __uint_as_float(r[kc * 8 + 2 * h + 1]), n2);
-                }
-            }
+            n2 = gram_norm2(sA, row, y0, y1);
         }
         const float nf = sqrtf(fmaxf(n2, 0.0f));
         const float kneg = nf < 1e-12f ? 0.0f : -a.tau / nf;   // exp(-tau (cos_p - max cos_n)) = exp(kneg d)
@@ -295,15 +287,18 @@ __global__ void __launch_bounds__(NT, 512 / NT) query_tc_kernel(QueryTcArgs a)
 // ---- Pipelined form for a BF16 coefficient map and N <= 256 columns --------------------------
 // Warp 0 streams W tiles into a ring of shared-memory stages with TMA tensor loads (the map's
 // 128-byte swizzle is the MMA operand layout, so no copy or conversion); warp 1 issues each
-// tile's MMA into one of kNb TMEM accumulators (kNb = 512 / columns, 2 or 4); warps 2..9 form two
-// epilogue warpgroups that take alternate tiles.  The epilogue releases the W stage once it has
-// read its pixel rows (for |F|^2) and the accumulator once its TMEM loads are done, through
-// mbarriers, so tiles overlap: no block-wide barrier per tile.  W is addressed as rows of 64
+// tile's MMA into one of ng TMEM accumulators; the remaining warps form ng epilogue warpgroups
+// (ng = 3 for accumulators of up to 128 columns, else 2), tile i going to accumulator i % ng and
+// warpgroup i % ng, so each accumulator's phases are consumed in order by one warpgroup.  The
+// epilogue releases the W stage once it has read its pixel rows (for |F|^2) and the accumulator
+// once its TMEM loads are done, through mbarriers, so tiles overlap: no block-wide barrier per
+// tile.  W is addressed as rows of 64
 // BF16 (row = view offset + level * P_v + pixel); a level's ragged last tile loads rows of the
 // next level (or zeros past the end), whose results are not stored.
 
 constexpr int kPStages = 8;
-constexpr int kPThreads = 320;
+// epilogue warpgroups (= TMEM accumulators) for accumulators of `bufcols` columns
+__host__ __device__ constexpr int pipe_groups(uint32_t bufcols) { return bufcols <= 128 ? 3 : 2; }
 
 __host__ __device__ constexpr size_t pipe_smem_bytes(int npad, int ntp)
 {
@@ -325,7 +320,10 @@ __device__ __forceinline__ bool pipe_wait(uint32_t bar, uint32_t parity, volatil
     return true;
 }
 
-__global__ void __launch_bounds__(kPThreads, 1) query_pipe_kernel(const __grid_constant__ CUtensorMap tmW, QueryTcArgs a)
+// NB: epilogue warpgroups = TMEM accumulators (a template parameter, so that the per-tile ring
+// and phase arithmetic divides by constants).
+template <int NB>
+__global__ void __launch_bounds__(64 + 128 * NB, 1) query_pipe_kernel(const __grid_constant__ CUtensorMap tmW, QueryTcArgs a)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -344,15 +342,16 @@ __global__ void __launch_bounds__(kPThreads, 1) query_pipe_kernel(const __grid_c
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int lev = blockIdx.y;
     const uint32_t bufcols = tmem_cols(a.npad);
-    const int nb = (int)(512u / bufcols) >= 4 ? 4 : 2;
-    const uint32_t ncols_alloc = (uint32_t)nb * bufcols;
+    constexpr int nb = NB;
+    const uint32_t ncols_alloc = nb * bufcols <= 256u ? (nb * bufcols <= 128u ? 128u : 256u) : 512u;
     const int64_t ntiles = a.total_tiles;
     auto locate = [&](int64_t tile, int& v, int64_t& p0) {
         v = 0;
         while (v + 1 < a.nseg && tile >= a.seg[v + 1].tile_base) ++v;
         p0 = (tile - a.seg[v].tile_base) * kM;
     };
-    const int64_t my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    // local tile counts fit 32 bits (at most 2^31 / 128 tiles per view and level)
+    const int my_tiles = blockIdx.x < ntiles ? (int)((ntiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
 
     if (warp == 0) tc::tmem_alloc(tc::smem_u32(tslot), ncols_alloc);
     if (tid == 0) {
@@ -368,7 +367,7 @@ __global__ void __launch_bounds__(kPThreads, 1) query_pipe_kernel(const __grid_c
     }
     // B^T rows as in query_tc_kernel: S S^T, then the text rows text-major, zero padding
     const float* Bl = a.Bt + (size_t)lev * (64 + a.Q * per) * kK;
-    for (int i = tid; i < a.npad * kK; i += kPThreads) {
+    for (int i = tid; i < a.npad * kK; i += (int)blockDim.x) {
         const int n = i >> 6, k = i & 63;
         int src = n < 64 ? n : -1;
         if (n >= 64 && n < 64 + ntp) {
@@ -378,7 +377,7 @@ __global__ void __launch_bounds__(kPThreads, 1) query_pipe_kernel(const __grid_c
         const float v = src >= 0 ? Bl[(size_t)src * kK + k] : 0.0f;
         *reinterpret_cast<__nv_bfloat16*>(sB + tc::sw128(n, k)) = __float2bfloat16_rn(v);
     }
-    for (int i = tid; i < ntp; i += kPThreads) {
+    for (int i = tid; i < ntp; i += (int)blockDim.x) {
         const int t = i / a.Qp, q = i % a.Qp;
         sTn[i] = q < a.Q ? 1.0f / a.tnorm[q * per + t] : 0.0f;
     }
@@ -391,30 +390,30 @@ __global__ void __launch_bounds__(kPThreads, 1) query_pipe_kernel(const __grid_c
     if (warp == 0) {
         // TMA producer
         if (lane == 0) {
-            int64_t issued = 0;
-            for (int64_t i = 0; i < my_tiles; ++i) {
-                const int s = (int)(i % kPStages);
+            int issued = 0;
+            for (int i = 0; i < my_tiles; ++i) {
+                const int s = i % kPStages;
                 if (i >= kPStages && !pipe_wait(tc::smem_u32(w_empty + s), (uint32_t)((i / kPStages - 1) & 1), abort))
                     break;
                 int v;
                 int64_t p0;
-                locate(blockIdx.x + i * gridDim.x, v, p0);
+                locate((int64_t)blockIdx.x + (int64_t)i * gridDim.x, v, p0);
                 const int64_t row = (int64_t)(a.seg[v].w_off / kK) + (int64_t)lev * a.seg[v].P + p0;
                 tc::bulk_load_arm(tc::smem_u32(w_full + s), kM * 128);
                 tc::tma_load_3d(tc::smem_u32(ring + (size_t)s * kM * 128), &tmW, 0, (int)row, 0, tc::smem_u32(w_full + s));
                 issued = i + 1;
             }
             // no copy may still be landing when the CTA retires
-            for (int64_t i = issued > kPStages ? issued - kPStages : 0; i < issued; ++i)
-                (void)tc::mbar_wait(tc::smem_u32(w_full + (int)(i % kPStages)), (uint32_t)((i / kPStages) & 1), 100000000ull);
+            for (int i = issued > kPStages ? issued - kPStages : 0; i < issued; ++i)
+                (void)tc::mbar_wait(tc::smem_u32(w_full + i % kPStages), (uint32_t)((i / kPStages) & 1), 100000000ull);
         }
         __syncwarp();
     } else if (warp == 1) {
         // MMA issuer
         if (lane == 0) {
-            int64_t done = 0;
-            for (int64_t i = 0; i < my_tiles; ++i) {
-                const int s = (int)(i % kPStages), b = (int)(i % nb);
+            int done = 0;
+            for (int i = 0; i < my_tiles; ++i) {
+                const int s = i % kPStages, b = i % nb;
                 if (!pipe_wait(tc::smem_u32(w_full + s), (uint32_t)((i / kPStages) & 1), abort)) break;
                 if (i >= nb && !pipe_wait(tc::smem_u32(t_empty + b), (uint32_t)((i / nb - 1) & 1), abort)) break;
                 tc::fence_after();
@@ -429,18 +428,18 @@ __global__ void __launch_bounds__(kPThreads, 1) query_pipe_kernel(const __grid_c
             }
             // no MMA may still be writing TMEM when it is freed
             if (done > 0) {
-                const int64_t i = done - 1;
-                (void)tc::mbar_wait(tc::smem_u32(m_full + (int)(i % nb)), (uint32_t)((i / nb) & 1), 100000000ull);
+                const int i = done - 1;
+                (void)tc::mbar_wait(tc::smem_u32(m_full + i % nb), (uint32_t)((i / nb) & 1), 100000000ull);
             }
         }
         __syncwarp();
     } else {
-        // epilogue: warpgroup g takes local tiles g, g + 2, ...; this warp owns TMEM lane quarter q4
+        // epilogue: warpgroup g takes local tiles g, g + nb, ...; this warp owns TMEM lane quarter q4
         const int g = (warp - 2) >> 2, q4 = warp & 3;
         const int row = q4 * 32 + lane;
         const int nch = a.Qp / 8;
-        for (int64_t i = g; i < my_tiles; i += 2) {
-            const int s = (int)(i % kPStages), b = (int)(i % nb);
+        for (int i = g; i < my_tiles; i += nb) {
+            const int s = i % kPStages, b = i % nb;
             if (!__all_sync(0xffffffffu, pipe_wait(tc::smem_u32(m_full + b), (uint32_t)((i / nb) & 1), abort))) break;
             // (already complete) acquire of the TMA's writes of the W stage read below; the stage
             // is reloaded only after this warpgroup releases it, so the phase cannot move on
@@ -449,27 +448,18 @@ __global__ void __launch_bounds__(kPThreads, 1) query_pipe_kernel(const __grid_c
             tc::fence_after();
             int vw;
             int64_t p0;
-            locate(blockIdx.x + i * gridDim.x, vw, p0);
+            locate((int64_t)blockIdx.x + (int64_t)i * gridDim.x, vw, p0);
             const int64_t Pv = a.seg[vw].P;
             const uint32_t trow = tmem + (uint32_t)b * bufcols + ((uint32_t)(q4 * 32) << 16);
             const uint8_t* sA = ring + (size_t)s * kM * 128;
             // |F|^2 = W . (G W): columns 0..63 of Y, W from the landed (swizzled) BF16 tile
-            float n2 = 0.0f;
-            for (int c = 0; c < 64; c += 32) {
-                uint32_t r[32];
-                tc::tmem_ld32(trow + (uint32_t)c, r);
+            float n2;
+            {
+                uint32_t y0[32], y1[32];
+                tc::tmem_ld32(trow, y0);
+                tc::tmem_ld32(trow + 32u, y1);
                 tc::tmem_wait_ld();
-#pragma unroll
-                for (int kc = 0; kc < 4; ++kc) {
-                    const uint4 wq = *reinterpret_cast<const uint4*>(sA + row * 128 + ((((c >> 3) + kc) ^ (row & 7)) << 4));
-                    const uint32_t wv[4] = {wq.x, wq.y, wq.z, wq.w};
-#pragma unroll
-                    for (int h = 0; h < 4; ++h) {
-                        const __nv_bfloat162 w2 = *reinterpret_cast<const __nv_bfloat162*>(&wv[h]);
-                        n2 = fmaf(__low2float(w2), __uint_as_float(r[kc * 8 + 2 * h]), n2);
-                        n2 = fmaf(__high2float(w2), __uint_as_float(r[kc * 8 + 2 * h + 1]), n2);
-                    }
-                }
+                n2 = gram_norm2(sA, row, y0, y1);
             }
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(tc::smem_u32(w_empty + s));
@@ -591,12 +581,14 @@ cudaError_t launch_query_tc_views(int levels, int V, const int64_t* P, int Q, in
         size_t smem = pipe_smem_bytes(npad, ntp);
         if (smem < 117760) smem = 117760;   // one CTA per SM: its TMEM allocation never waits
         if (smem > 232448) return cudaErrorInvalidValue;
-        cudaError_t e = cudaFuncSetAttribute(query_pipe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const int ng = pipe_groups(tmem_cols(npad));
+        auto kern = ng == 3 ? query_pipe_kernel<3> : query_pipe_kernel<2>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int per_level = num_sms / levels;
         if (per_level < 1) per_level = 1;
         if (per_level > tiles) per_level = (int)tiles;
-        query_pipe_kernel<<<dim3(per_level, levels), kPThreads, smem, stream>>>(tmW, a);
+        kern<<<dim3(per_level, levels), 64 + 128 * ng, smem, stream>>>(tmW, a);
         return cudaGetLastError();
     }
     // Two CTAs per SM when their TMEM allocations fit (one CTA's MMA and W conversion overlap the
