@@ -23,7 +23,7 @@ namespace lsv2 {
 namespace {
 
 constexpr int kMaxWindow = 63;
-constexpr int kTile = 32;          // output tile: kTile x kTile pixels per CTA
+constexpr int kTX = 64, kTY = 32;  // output tile of one box-filter CTA
 constexpr int kPostThreads = 256;
 
 // Per (q, l) map statistics in the workspace.
@@ -65,51 +65,69 @@ struct BoxArgs {
     MapStats* st;
 };
 
-// One kTile x kTile output tile of map blockIdx.z: the input tile with its halo is staged in
-// shared memory, summed along rows (k terms), then along columns (k terms), and divided by the
-// number of in-image pixels of each window.
+// One kTX x kTY output tile of map blockIdx.z.  The input tile with its halo (r = (k - 1) / 2 on
+// each side) is staged in shared memory; the column pass slides a k-row sum down each staged
+// column (k loads to start, then one added and one dropped row per output row), the row pass
+// slides a k-column sum along 8 outputs per thread; each sum is divided by the number of
+// in-image pixels of its window.  (Sliding sums round differently from direct sums by a few
+// ulps of a window sum.)
 __global__ void __launch_bounds__(kPostThreads) box_filter_kernel(BoxArgs a)
 {
     extern __shared__ float sm[];
     const int r = (a.k - 1) / 2;
-    const int E = kTile + 2 * r;                   // staged extent per side
-    float* in = sm;                                // [E][E]
-    float* hs = sm + E * E;                        // [E][kTile] row sums
+    const int EX = kTX + 2 * r, EY = kTY + 2 * r;  // staged extents (EX <= 128)
+    float* in = sm;                                // [EY][EX]
+    float* vs = sm + EX * EY;                      // [kTY][EX] column sums
     const int map = blockIdx.z;
     const size_t P = (size_t)a.H * a.W;
-    const int x0 = blockIdx.x * kTile, y0 = blockIdx.y * kTile;
-    for (int i = threadIdx.x; i < E * E; i += kPostThreads) {
-        const int yy = y0 - r + i / E, xx = x0 - r + i % E;
-        in[i] = (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W) ? load_rel(a.rel, a.bf16, map * P + (size_t)yy * a.W + xx)
-                                                             : 0.0f;
+    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
+    {
+        const int c = threadIdx.x & 127, xx = x0 - r + c;
+        for (int row = threadIdx.x >> 7; row < EY; row += kPostThreads / 128) {
+            const int yy = y0 - r + row;
+            if (c < EX)
+                in[row * EX + c] = (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W)
+                                       ? load_rel(a.rel, a.bf16, map * P + (size_t)yy * a.W + xx)
+                                       : 0.0f;
+        }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < E * kTile; i += kPostThreads) {
-        const int row = i / kTile, c = i % kTile;
-        const float* src = in + row * E + c;
+    for (int c = threadIdx.x; c < EX; c += kPostThreads) {
         float s = 0.0f;
-        for (int d = 0; d < a.k; ++d) s += src[d];
-        hs[i] = s;
+        for (int d = 0; d < a.k; ++d) s += in[d * EX + c];
+        vs[c] = s;
+        for (int ty = 1; ty < kTY; ++ty) {
+            s += in[(ty + a.k - 1) * EX + c] - in[(ty - 1) * EX + c];
+            vs[ty * EX + c] = s;
+        }
     }
     __syncthreads();
     unsigned long long best = 0ull;
     unsigned int lo = 0xFFFFFFFFu;
-    for (int i = threadIdx.x; i < kTile * kTile; i += kPostThreads) {
-        const int ty = i / kTile, tx = i % kTile;
-        const int x = x0 + tx, y = y0 + ty;
-        if (x >= a.W || y >= a.H) continue;
+    {
+        // thread -> (row ty, outputs tx0 .. tx0 + 7); kTY x kTX / 8 = kPostThreads segments
+        const int ty = threadIdx.x >> 3, tx0 = (threadIdx.x & 7) * 8;
+        const int y = y0 + ty;
+        const float* row = vs + ty * EX + tx0;
         float s = 0.0f;
-        for (int d = 0; d < a.k; ++d) s += hs[(ty + d) * kTile + tx];
-        const int cx = min(x + r, a.W - 1) - max(x - r, 0) + 1;
+        for (int d = 0; d < a.k; ++d) s += row[d];
         const int cy = min(y + r, a.H - 1) - max(y - r, 0) + 1;
-        float v = s / (float)(cx * cy);
-        if (a.mode == LSV2_POST_BLENDED) v = 0.5f * (in[(ty + r) * E + tx + r] + v);
-        const size_t pix = (size_t)y * a.W + x;
-        a.smoothed[map * P + pix] = v;
-        const unsigned int kv = orderable(v);
-        const unsigned long long key = ((unsigned long long)kv << 32) | (0xFFFFFFFFull - pix);
-        best = key > best ? key : best;
-        lo = kv < lo ? kv : lo;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (j > 0) s += row[j + a.k - 1] - row[j - 1];
+            const int x = x0 + tx0 + j;
+            if (x < a.W && y < a.H) {
+                const int cx = min(x + r, a.W - 1) - max(x - r, 0) + 1;
+                float v = s / (float)(cx * cy);
+                if (a.mode == LSV2_POST_BLENDED) v = 0.5f * (in[(ty + r) * EX + tx0 + j + r] + v);
+                const size_t pix = (size_t)y * a.W + x;
+                a.smoothed[map * P + pix] = v;
+                const unsigned int kv = orderable(v);
+                const unsigned long long key = ((unsigned long long)kv << 32) | (0xFFFFFFFFull - pix);
+                best = key > best ? key : best;
+                lo = kv < lo ? kv : lo;
+            }
+        }
     }
     // block reduction, then one atomic per block and quantity
     for (int o = 16; o > 0; o >>= 1) {
@@ -245,10 +263,12 @@ extern "C" lsv2_status lsv2_postprocess(int32_t Q, int32_t levels, int32_t H, in
     MapStats* ms = static_cast<MapStats*>(workspace);
     const size_t P = (size_t)H * W;
     post_init_kernel<<<(maps + 255) / 256, 256, 0, st>>>(ms, maps);
-    const int r = (k - 1) / 2, E = kTile + 2 * r;
-    const size_t smem = (size_t)(E * E + E * kTile) * sizeof(float);
+    const int r = (k - 1) / 2, EX = kTX + 2 * r, EY = kTY + 2 * r;
+    const size_t smem = (size_t)(EX * EY + kTY * EX) * sizeof(float);
     BoxArgs ba{H, W, k, mode, rel, rel_dtype == LSV2_BF16, smoothed, ms};
-    box_filter_kernel<<<dim3((W + kTile - 1) / kTile, (H + kTile - 1) / kTile, maps), kPostThreads, smem, st>>>(ba);
+    if (cudaFuncSetAttribute(box_filter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return LSV2_ERR_CUDA;
+    box_filter_kernel<<<dim3((W + kTX - 1) / kTX, (H + kTY - 1) / kTY, maps), kPostThreads, smem, st>>>(ba);
     if (mode == LSV2_POST_BLENDED)
         masked_sum_kernel<<<dim3(grid_cap(P), maps), kPostThreads, 0, st>>>(smoothed, P, threshold, ms);
     select_kernel<<<(Q + 127) / 128, 128, 0, st>>>(Q, levels, W, mode, ms, point, level, score);
