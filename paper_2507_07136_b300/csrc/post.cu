@@ -66,9 +66,9 @@ struct BoxArgs {
 };
 
 // One kTX x kTY output tile of map blockIdx.z.  The input tile with its halo (r = (k - 1) / 2 on
-// each side) is staged in shared memory; the column pass slides a k-row sum down each staged
-// column (k loads to start, then one added and one dropped row per output row), the row pass
-// slides a k-column sum along 8 outputs per thread; each sum is divided by the number of
+// each side) is staged in shared memory; the column pass slides a k-row sum down each half of
+// each staged column (k loads in four partial sums to start, then one added and one dropped row
+// per output row), the row pass slides a k-column sum along 8 outputs per thread; each sum is divided by the number of
 // in-image pixels of its window.  (Sliding sums round differently from direct sums by a few
 // ulps of a window sum.)
 __global__ void __launch_bounds__(kPostThreads) box_filter_kernel(BoxArgs a)
@@ -81,24 +81,53 @@ __global__ void __launch_bounds__(kPostThreads) box_filter_kernel(BoxArgs a)
     const int map = blockIdx.z;
     const size_t P = (size_t)a.H * a.W;
     const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
-    {
-        const int c = threadIdx.x & 127, xx = x0 - r + c;
-        for (int row = threadIdx.x >> 7; row < EY; row += kPostThreads / 128) {
+    const int c = threadIdx.x & 127, xx = x0 - r + c;
+    const bool col_in = c < EX && xx >= 0 && xx < a.W;
+    if (!a.bf16) {
+        // FP32 maps: staged column c = thread % 128, rows thread / 128 + 2 j, every element by an
+        // asynchronous 4-byte copy (all of them in flight at once; zero-filled outside the image)
+        const float* rel = static_cast<const float*>(a.rel) + map * P;
+        for (int row = threadIdx.x >> 7; row < EY; row += 2) {
             const int yy = y0 - r + row;
+            const bool ok = col_in && yy >= 0 && yy < a.H;
+            const float* src = ok ? rel + (size_t)yy * a.W + xx : rel;
             if (c < EX)
-                in[row * EX + c] = (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W)
-                                       ? load_rel(a.rel, a.bf16, map * P + (size_t)yy * a.W + xx)
-                                       : 0.0f;
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(in + row * EX + c)),
+                             "l"(src), "r"(ok ? 4 : 0)
+                             : "memory");
+        }
+        asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+    } else {
+        // BF16 maps: eight loads in flight per thread, converted on the way to shared memory
+        for (int row0 = threadIdx.x >> 7; row0 < EY; row0 += 16) {
+            float v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int row = row0 + 2 * j, yy = y0 - r + row;
+                v[j] = (col_in && row < EY && yy >= 0 && yy < a.H) ? load_rel(a.rel, a.bf16, map * P + (size_t)yy * a.W + xx)
+                                                                  : 0.0f;
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (c < EX && row0 + 2 * j < EY) in[(row0 + 2 * j) * EX + c] = v[j];
         }
     }
     __syncthreads();
-    for (int c = threadIdx.x; c < EX; c += kPostThreads) {
-        float s = 0.0f;
-        for (int d = 0; d < a.k; ++d) s += in[d * EX + c];
-        vs[c] = s;
-        for (int ty = 1; ty < kTY; ++ty) {
-            s += in[(ty + a.k - 1) * EX + c] - in[(ty - 1) * EX + c];
-            vs[ty * EX + c] = s;
+    // column pass: thread -> (column c, output rows h * 16 .. h * 16 + 15)
+    if (threadIdx.x < 2 * EX) {
+        const int h = threadIdx.x < EX ? 0 : 1, c = threadIdx.x - h * EX, t0 = h * (kTY / 2);
+        const float* col = in + t0 * EX + c;
+        float p[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        int d = 0;
+        for (; d + 4 <= a.k; d += 4)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) p[u] += col[(d + u) * EX];
+        for (; d < a.k; ++d) p[0] += col[d * EX];
+        float s = (p[0] + p[1]) + (p[2] + p[3]);
+        vs[t0 * EX + c] = s;
+        for (int ty = 1; ty < kTY / 2; ++ty) {
+            s += col[(ty + a.k - 1) * EX] - col[(ty - 1) * EX];
+            vs[(t0 + ty) * EX + c] = s;
         }
     }
     __syncthreads();
@@ -109,8 +138,13 @@ __global__ void __launch_bounds__(kPostThreads) box_filter_kernel(BoxArgs a)
         const int ty = threadIdx.x >> 3, tx0 = (threadIdx.x & 7) * 8;
         const int y = y0 + ty;
         const float* row = vs + ty * EX + tx0;
-        float s = 0.0f;
-        for (int d = 0; d < a.k; ++d) s += row[d];
+        float p[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        int d = 0;
+        for (; d + 4 <= a.k; d += 4)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) p[u] += row[d + u];
+        for (; d < a.k; ++d) p[0] += row[d];
+        float s = (p[0] + p[1]) + (p[2] + p[3]);
         const int cy = min(y + r, a.H - 1) - max(y - r, 0) + 1;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
