@@ -181,17 +181,84 @@ __device__ void bitonic_smem(unsigned long long* s, int npow2)
     }
 }
 
+// Bitonic sorting network over 32 K keys held by one warp, key i = j * 32 + lane in register j:
+// partners i ^ m with m >= 32 are registers of the same lane, the others are exchanged by
+// shuffles.  Ascending on return.
+template <int K>
+__device__ __forceinline__ void warp_bitonic(unsigned long long (&x)[K], int lane)
+{
+#pragma unroll
+    for (int k = 2; k <= 32 * K; k <<= 1) {
+#pragma unroll
+        for (int m = k >> 1; m > 0; m >>= 1) {
+            if (m >= 32) {
+                const int mj = m >> 5;
+#pragma unroll
+                for (int j = 0; j < K; ++j) {
+                    if ((j & mj) == 0) {
+                        const bool up = ((j * 32) & k) == 0;   // k >= 64 here: the lane bits do not matter
+                        const unsigned long long lo = x[j], hi = x[j | mj];
+                        const bool sw = (lo > hi) == up;
+                        x[j] = sw ? hi : lo;
+                        x[j | mj] = sw ? lo : hi;
+                    }
+                }
+            } else {
+                const bool lower = (lane & m) == 0;        // this lane holds the pair's lower index
+#pragma unroll
+                for (int j = 0; j < K; ++j) {
+                    const bool up = (((j * 32) | lane) & k) == 0;
+                    const unsigned long long o = __shfl_xor_sync(0xffffffffu, x[j], m);
+                    x[j] = (lower == up) ? (o < x[j] ? o : x[j]) : (o > x[j] ? o : x[j]);
+                }
+            }
+        }
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void warp_sort_tile(const unsigned long long* keys, uint32_t* ids, uint32_t b, int n, int lane)
+{
+    unsigned long long x[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) x[j] = j * 32 + lane < n ? keys[b + j * 32 + lane] : ~0ull;
+    warp_bitonic<K>(x, lane);
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+        if (j * 32 + lane < n) ids[b + j * 32 + lane] = (uint32_t)x[j];
+}
+
+// One warp per tile of at most kWarpCap keys (the common case), four tiles per block; the key
+// (depth bits, Gaussian id) is unique, so the sorted order is.
+constexpr int kWarpCap = 512;
+__global__ void __launch_bounds__(128) sort_warp_kernel(int T, const uint32_t* tile_ranges,
+                                                        const unsigned long long* keys, uint32_t* ids)
+{
+    const int tile = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (tile >= T) return;
+    const uint32_t b = tile_ranges[2 * tile], e = tile_ranges[2 * tile + 1];
+    const int n = (int)(e - b);
+    if (n <= 1) {
+        if (n == 1 && lane == 0) ids[b] = (uint32_t)keys[b];
+    } else if (n <= 64) {
+        warp_sort_tile<2>(keys, ids, b, n, lane);
+    } else if (n <= 128) {
+        warp_sort_tile<4>(keys, ids, b, n, lane);
+    } else if (n <= 256) {
+        warp_sort_tile<8>(keys, ids, b, n, lane);
+    } else if (n <= kWarpCap) {
+        warp_sort_tile<16>(keys, ids, b, n, lane);
+    }
+}
+
+// Tiles of kWarpCap < n <= kSmallCap keys: one block, bitonic in shared memory.
 __global__ void __launch_bounds__(256) sort_small_kernel(const uint32_t* tile_ranges,
                                                          const unsigned long long* keys, uint32_t* ids)
 {
     __shared__ unsigned long long s[kSmallCap];
     const uint32_t b = tile_ranges[2 * blockIdx.x], e = tile_ranges[2 * blockIdx.x + 1];
     const int n = (int)(e - b);
-    if (n <= 1) {
-        if (n == 1 && threadIdx.x == 0) ids[b] = (uint32_t)keys[b];
-        return;
-    }
-    if (n > kSmallCap) return;
+    if (n <= kWarpCap || n > kSmallCap) return;
     int np = 2;
     while (np < n) np <<= 1;
     for (int i = threadIdx.x; i < np; i += blockDim.x) s[i] = i < n ? keys[b + i] : ~0ull;
@@ -331,6 +398,7 @@ cudaError_t launch_binsort_views(const BinSortViews& a, cudaStream_t stream)
     column_kernel<<<(Tt + 255) / 256, 256, 0, stream>>>(V, (int)nblk, vd, hist, total, Tt);
     scan_kernel<<<1, 1024, 0, stream>>>(Tt, total, start, a.tile_ranges, a.capacity, a.num_instances, big, a.status);
     scatter_kernel<<<grid, kGB, cnt_smem, stream>>>(a, vd, hist, start, keys);
+    sort_warp_kernel<<<(Tt + 3) / 4, 128, 0, stream>>>((int)Tt, a.tile_ranges, keys, a.gauss_ids);
     sort_small_kernel<<<Tt, 256, 0, stream>>>(a.tile_ranges, keys, a.gauss_ids);
     const int large_smem = kChunk * 8;
     e = cudaFuncSetAttribute(sort_large_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, large_smem);
