@@ -39,10 +39,16 @@ FP32_ALU_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 POST_WINDOW = 29
 POST_THRESHOLD = 0.5
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
-# this workload with the kernels as they are now; an entry is removed when its kernel changes.
 SPLAT_KERNEL = "splat_kernel<3,4,16,8> (two CTAs per 16x16 tile)"
-TRAFFIC = {}
+# DRAM bytes (read + write) per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum) on
+# the same frame via `bench.py --profile STAGE`, with the kernels as they are now (an entry is
+# removed when its kernel changes): the splat and the relevancy as launched here; the decode
+# captured over one level (one third of the launch's pixels and bytes) and scaled by 3.
+TRAFFIC = {
+    SPLAT_KERNEL: 47581952 + 550764544,
+    "decode_tc_kernel": 3 * (199166976 + 1532453376),
+    "query_pipe_kernel<3>": 597312000 + 18906368,
+}
 
 
 def peaks():
@@ -368,9 +374,9 @@ def main():
            "query": lambda: frame.query(text_d, rel, compute=Lb.LSV2_BF16, from_bf16=True),
            "post": lambda: frame.postprocess(rel, k=POST_WINDOW, mode=Lb.LSV2_POST_LERF, threshold=POST_THRESHOLD,
                                              out=post_out)}
-    # kernels per stage: project; hist/column/scan/scatter/sort (bin); pack + splat; decode;
-    # prepare + query; init + box filter + select + mask (post)
-    launches_per_step = {"project": 1, "bin_sort": 5, "splat": 2, "decode": 1, "query": 2, "post": 4}
+    # kernels per stage: project; hist/column/scan/scatter + warp, block and large-tile sorts (bin);
+    # pack + splat; decode; prepare + query; init + box filter + select + mask (post)
+    launches_per_step = {"project": 1, "bin_sort": 7, "splat": 2, "decode": 1, "query": 2, "post": 4}
 
     def step(ev=None):
         for i, s in enumerate(stages):
@@ -475,6 +481,7 @@ def main():
     rec_bytes = Lb.lsv2_splat_workspace_bytes(scene.n, levels, scene.K)
     splat_bytes = levels * P * 64 * 2 + rec_bytes + inst * 4 + P * 8      # BF16 coefficient map
     decode_bytes = levels * P * (64 * 2 + D * 2)                          # BF16 W in, BF16 F out
+    query_bytes = levels * P * 64 * 2 + text.shape[0] * levels * P * 4     # BF16 W in, FP32 relevancy out
     roofs = {
         "splat": {"bound": "hbm", "achieved": splat_bytes / (stage_ms["splat"] * 1e-3) / 1e9, "peak": pk["hbm_gbs"],
                   "unit": "GB/s", "traffic": TRAFFIC.get(SPLAT_KERNEL), "kernel": SPLAT_KERNEL,
@@ -482,6 +489,10 @@ def main():
         "decode": {"bound": "hbm", "achieved": decode_bytes / (stage_ms["decode"] * 1e-3) / 1e9, "peak": pk["hbm_gbs"],
                    "unit": "GB/s", "traffic": TRAFFIC.get("decode_tc_kernel"), "kernel": "decode_tc_kernel",
                    "algorithmic_bytes": decode_bytes, "peak_source": pk_kind},
+        # the stage's time includes the prepare kernel ([S S^T | S t], about 13 us)
+        "query": {"bound": "hbm", "achieved": query_bytes / (stage_ms["query"] * 1e-3) / 1e9, "peak": pk["hbm_gbs"],
+                  "unit": "GB/s", "traffic": TRAFFIC.get("query_pipe_kernel<3>"), "kernel": "query_pipe_kernel<3> + prepare",
+                  "algorithmic_bytes": query_bytes, "peak_source": pk_kind},
     }
     for r in roofs.values():
         r["frac"] = r["achieved"] / r["peak"]
