@@ -284,8 +284,9 @@ size_t lsv2_render_fused_workspace_bytes(int64_t n, int32_t levels, int32_t K, i
 
 /* The splat of lsv2_splat_coeffs (Sec. 3.4, Algorithm 1), the decode of lsv2_decode (Eq. 7,
  * BF16 operands and output, FP32 accumulation) and the relevancy of lsv2_query (Sec. 3.2 through
- * Eq. 7, BF16 compute) in one kernel per tile: the coefficient map W stays in shared memory and
- * tensor memory and is never written to HBM.  F and rel equal what lsv2_splat_coeffs followed by
+ * Eq. 7, BF16 compute) in one kernel, one CTA per 16 x 8 half of each tile and two per SM (one's
+ * decode overlaps the other's splat): the coefficient map W stays in shared memory and tensor
+ * memory and is never written to HBM.  F and rel equal what lsv2_splat_coeffs followed by
  * lsv2_decode (BF16) and lsv2_query (BF16 compute) produce.
  *   cam, n, proj, tile_ranges, gauss_ids, idx, w   as for lsv2_splat_coeffs (tile 16 x 16)
  *   codebook  float[levels][64][D], D a multiple of 128, <= 512
@@ -294,8 +295,9 @@ size_t lsv2_render_fused_workspace_bytes(int64_t n, int32_t levels, int32_t K, i
  *   rel       [Q][levels][P], dtype rel_dtype (F32 or BF16); unused when Q = 0
  *   final_T, n_last   as for lsv2_splat_coeffs
  *   workspace lsv2_render_fused_workspace_bytes(...) bytes, 256-byte aligned
- * Supported: levels = 3, K = 4, L = 64, 64 + (1 + n_neg) * 8 * ceil(Q / 8) <= 256.  At least one of
- * feat and Q > 0.  A bounded device wait that expires sets LSV2_ERR_TIMEOUT. */
+ * Supported: levels = 3, K = 4, L = 64, 64 + (1 + n_neg) * 8 * ceil(Q / 8) <= 128 (Q <= 8 at
+ * n_neg = 4).  At least one of feat and Q > 0.  A bounded device wait that expires sets
+ * LSV2_ERR_TIMEOUT. */
 lsv2_status lsv2_render_fused(const lsv2_camera* cam, int64_t n, const lsv2_proj* proj,
                               const uint32_t* tile_ranges, const uint32_t* gauss_ids, int32_t levels,
                               int32_t K, int32_t L, const uint8_t* idx, const float* w,

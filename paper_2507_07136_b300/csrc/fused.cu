@@ -2,55 +2,59 @@
 // (Eq. 7) and relevancy (Sec. 3.2 through Eq. 7) in one kernel: the coefficient map W never
 // leaves the SM.
 //
-// One CTA per 16x16 tile: 8 consumer warps and one producer warp, as in the plain splat
+// One CTA per 16x8 half of a 16x16 bin tile, two CTAs per SM, so that one CTA's decode (bound by
+// the HBM write stream) overlaps the other's splat (bound by shared memory and latency).  A CTA
+// is 4 consumer warps (8x4 pixels each) and one producer warp, as in the plain splat
 // (splat_core.cuh).  After the splat each consumer warp holds the FP32 coefficients of its 32
-// pixels in shared-memory columns.  Then, per CTA:
+// pixels in shared-memory columns.  Then:
 //  1. Transit: every thread stores its pixel's 3 x 64 coefficients, rounded to BF16, into its
-//     TMEM lane (tcgen05.st; lane = pixel row of a 128-pixel M tile), which frees the
-//     accumulator memory; after a barrier it reads them back (tcgen05.ld) and writes the
-//     128-byte-swizzled K-major A tiles (one per level and 128-pixel half) into that memory.
-//  2. The producer warp streams the codebook S_lev^T in 16 KB chunks (128 rows of the
-//     pre-swizzled BF16 copy) through a 3-slot ring with bulk async copies, and the query
-//     matrices [S S^T | S t ...] (text-major rows, as in query_tc.cu; all three levels at once
-//     when they fit in 32 KB, else one level at a time); its lane 0
-//     issues the tcgen05.mma: per level, Y = W [S S^T | S t] (M = 128, N = npadq) into TMEM
-//     columns [256, 256 + npadq), then F chunks of 128 features (M = 128, N = 128, K = 64) into
-//     two TMEM buffers [0, 128) and [128, 256) that alternate, each committed to an mbarrier.
-//  3. The consumer warps run the epilogues in the same order: relevancy as in query_tc.cu
-//     (|F|^2 = W . (S S^T W), sigmoid of the scaled cosine gap), and F chunks converted to BF16,
-//     staged per warp in shared memory (32 rows x 128 bytes) and written with coalesced
-//     512-byte warp stores (4 pixels' 128-byte segments per store).
+//     TMEM lane (tcgen05.st), which frees the accumulator memory; after a barrier it reads them
+//     back (tcgen05.ld) and writes the 128-byte-swizzled K-major A tile of each level (128 rows =
+//     the block's pixels in row-major order) into that memory.
+//  2. The producer warp streams the codebook S_lev^T in 8 KB chunks of 64 rows (the pre-swizzled
+//     BF16 copy) through a 2-slot ring with bulk async copies, and each level's query matrix
+//     [S S^T | S t ...] (text-major rows, as in query_tc.cu); its lane 0 issues the tcgen05.mma:
+//     per level Y = W [S S^T | S t] (M = 128, N = npadq <= 128) into TMEM columns [128, 256), then
+//     F chunks of 64 features (M = 128, N = 64, K = 64) into two TMEM buffers [0, 64) and
+//     [64, 128) that alternate, each committed to an mbarrier.
+//  3. The consumer warps run the epilogues in the same order (warp q reads TMEM lanes 32q ..,
+//     i.e. image rows 2q and 2q + 1 of the block): relevancy as in query_tc.cu (|F|^2 = W . (S
+//     S^T W), sigmoid of the scaled cosine gap), and F chunks converted to BF16 into two
+//     16-pixel x 128-byte staging boxes per warp, each sent by one TMA tensor store through a
+//     {D, W, H, levels} map (columns past the image edge are clipped by the map).
 // The operands and the MMA sequence (K = 64 in four steps of 16) are those of decode_tc.cu and
 // query_tc.cu, so F and the relevancy equal those kernels' results on the splat's W.  Every wait
 // is time-bounded: on expiry the CTA records LSV2_ERR_TIMEOUT, skips the rest and frees TMEM.
 #include <cuda_bf16.h>
 
+#include <cstring>
+
 #include "query.cuh"
 #include "splat_core.cuh"
 #include "gram.cuh"
+#include "tmap.cuh"
 
 namespace lsv2 {
 namespace {
 
-constexpr int kLev = 3, kKp = 4, kTW = 16, kTH = 16;
-using FC = SplatCfg<kLev, kKp, kTW, kTH, 0>;
-constexpr int kM = 128;
-constexpr int kATile = kM * 128;             // one A tile: 128 rows x 64 BF16
-constexpr int kBChunk = 128 * 128;           // 128 codebook rows x 64 BF16
-constexpr int kBSlots = 3;
-constexpr int kAOff = 0;                           // A [level][half] (6 x 16 KB)
-constexpr int kBOff = kAOff + kLev * 2 * kATile;   // B ring (3 x 16 KB)
-constexpr int kQOff = kBOff + kBSlots * kBChunk;   // query matrices: all levels if they fit, else one
-constexpr int kQBytes = 32768;
-constexpr int kQMaxRows = 256;
-constexpr int kTnOff = kQOff + kQBytes;            // reciprocal text norms (<= 448 floats)
-constexpr int kStageRow = 128 + 16;                // F staging: 128 bytes per pixel row + skew
-constexpr int kStage0Off = kTnOff + 448 * 4;       // staging of the warps with column half 0
-constexpr int kBarOff = FC::kAccBytes + 256;       // fused-phase barriers (after the splat's)
-constexpr int kStage1Off = FC::kFixedBytes;        // column half 1: the splat's record ring
-static_assert(kStage0Off + kM * kStageRow <= FC::kAccBytes, "fused operands fit in the accumulator memory");
-static_assert(kStage1Off + kM * kStageRow <= FC::kSmemBytes, "staging fits in the record ring");
-static_assert(kBarOff + 32 * 8 <= FC::kFixedBytes, "fused barriers fit in the fixed area");
+constexpr int kLev = 3, kKp = 4, kTW = 16, kTH = 16, kHH = 8;   // bin tile 16x16, CTA block 16x8
+using FC = SplatCfg<kLev, kKp, kTW, kHH, 0>;                     // 4 consumer warps + the producer
+constexpr int kM = 128;                                          // pixels of a CTA block = MMA rows
+constexpr int kATile = kM * 128;                                 // one A tile: 128 rows x 64 BF16
+constexpr int kBChunk = 64 * 128;                                // 64 codebook rows x 64 BF16
+constexpr int kBSlots = 2;
+constexpr int kQMaxRows = 128;
+constexpr int kAOff = 0;                                         // A [level] (3 x 16 KB)
+constexpr int kBOff = kAOff + kLev * kATile;                     // B ring (2 x 8 KB)
+constexpr int kQOff = kBOff + kBSlots * kBChunk;                 // one level's query matrix (<= 16 KB)
+constexpr int kTnOff = kQOff + kQMaxRows * 128;                  // reciprocal text norms (<= 128 floats)
+constexpr int kBoxBytes = 16 * 128;                              // F staging box: 16 pixels x 128 bytes
+constexpr int kStgOff = kTnOff + 1024;                           // 4 warps x 2 boxes
+constexpr int kBarOff = FC::kAccBytes + 256;                     // fused-phase barriers (after the splat's)
+constexpr uint32_t kTmemCols = 256;                              // F buffers [0, 128), Y [128, 256)
+static_assert(kStgOff + FC::kWarps * 2 * kBoxBytes <= FC::kAccBytes, "fused operands fit in the accumulator memory");
+static_assert(kStgOff % 1024 == 0 && kQOff % 1024 == 0 && kBOff % 1024 == 0, "swizzled tiles are 1024-byte aligned");
+static_assert(FC::kWarps == 4, "one consumer warp per TMEM lane quarter");
 
 struct FusedArgs {
     int width, height, GX;
@@ -60,8 +64,8 @@ struct FusedArgs {
     float* final_T;
     uint32_t* n_last;
     int D;                       // features (multiple of 128, <= 512)
-    const uint8_t* Bdec;         // [levels][D / 128][128 rows x 128 B] swizzled BF16 S^T
-    void* F;                     // [levels][P][D] BF16, or null
+    const uint8_t* Bdec;         // [levels][D / 64][64 rows x 128 B] swizzled BF16 S^T
+    int do_dec;                  // write F (through the tensor map)
     int Q, n_neg, Qp, npadq;     // Q = 0: no query
     float tau;
     const uint8_t* Bq;           // [levels][npadq rows x 128 B] swizzled BF16 [S S^T | S t] (text-major)
@@ -75,18 +79,9 @@ struct FusedBars {
     uint64_t bfull[kBSlots], bempty[kBSlots], dfull[2], dempty[2], qfull, qempty, qload, qfree;
     uint32_t tslot;
 };
+static_assert(kBarOff + sizeof(FusedBars) <= FC::kFixedBytes, "fused barriers fit in the fixed area");
 
-// (M-half h, lane quarter q, lane) -> pixel of the tile; false outside the image
-__device__ __forceinline__ bool tile_pixel(const FusedArgs& a, int tile, int h, int q, int lane, size_t& pix)
-{
-    const int tx = tile % a.GX, ty = tile / a.GX;
-    const int sw = 4 * h + q;   // splat warp
-    const int px = tx * kTW + FC::lane_x(sw, lane), py = ty * kTH + FC::lane_y(sw, lane);
-    pix = (size_t)py * a.width + px;
-    return px < a.width && py < a.height;
-}
-
-__global__ void __launch_bounds__(FC::kThreads, 1) fused_kernel(FusedArgs a)
+__global__ void __launch_bounds__(FC::kThreads, 2) fused_kernel(const __grid_constant__ CUtensorMap tmF, FusedArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // the swizzled operand tiles need 1024-byte alignment (1 KB of slack is requested)
@@ -94,10 +89,11 @@ __global__ void __launch_bounds__(FC::kThreads, 1) fused_kernel(FusedArgs a)
     const SplatSmem<FC> sm(smem);
     FusedBars* fb = reinterpret_cast<FusedBars*>(smem + kBarOff);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int tile = blockIdx.x;
+    const int tile = blockIdx.x >> 1, sub = blockIdx.x & 1;
+    const int x0 = (tile % a.GX) * kTW, y0 = (tile / a.GX) * kTH + sub * kHH;
     const size_t P = (size_t)a.width * a.height;
-    const bool do_query = a.Q > 0, do_dec = a.F != nullptr;
-    const int nchunk = a.D / 128;
+    const bool do_query = a.Q > 0, do_dec = a.do_dec != 0;
+    const int nfc = a.D / 64;    // F chunks per level
 
     if (tid == 0) {
         sm.init();
@@ -115,7 +111,7 @@ __global__ void __launch_bounds__(FC::kThreads, 1) fused_kernel(FusedArgs a)
         tc::mbar_init(tc::smem_u32(&fb->qload), 1);
         tc::mbar_init(tc::smem_u32(&fb->qfree), 1);
     }
-    if (warp == 0) tc::tmem_alloc(tc::smem_u32(&fb->tslot), 512);
+    if (warp == 0) tc::tmem_alloc(tc::smem_u32(&fb->tslot), kTmemCols);
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
@@ -124,46 +120,44 @@ __global__ void __launch_bounds__(FC::kThreads, 1) fused_kernel(FusedArgs a)
 
     if (!skip) {
         // ---- splat: W stays in the consumer warps' shared-memory columns
-        TileJob j{a.width, a.height, (tile % a.GX) * kTW, (tile / a.GX) * kTH, a.tile_ranges[2 * tile],
-                  a.tile_ranges[2 * tile + 1], a.gauss_ids,
+        TileJob j{a.width, a.height, x0, y0, a.tile_ranges[2 * tile], a.tile_ranges[2 * tile + 1], a.gauss_ids,
                   a.recs, nullptr, a.final_T, a.n_last, a.status};
-        (void)splat_tile<kLev, kKp, kTW, kTH, 0, false>(j, sm, 0u);
+        (void)splat_tile<kLev, kKp, kTW, kHH, 0, false>(j, sm, 0u);
     }
     bool ok = !skip && !*reinterpret_cast<volatile int*>(sm.abort);
-    // ---- transit: coefficients -> BF16 rows in TMEM (lane = pixel row of its 128-pixel half)
+    // ---- transit: coefficients -> BF16 in this thread's TMEM lane, columns [32 l, 32 l + 32)
+    const uint32_t lrow = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
     if (ok && warp < FC::kWarps) {
         const float* acc = sm.acc + warp * FC::kAccFloats;
-        const uint32_t lrow = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
 #pragma unroll 1
         for (int l = 0; l < kLev; ++l) {
             uint32_t r[32];
 #pragma unroll
             for (int i = 0; i < 32; ++i)
                 r[i] = tc::pack_bf16(acc[(l * 64 + 2 * i) * 33 + lane], acc[(l * 64 + 2 * i + 1) * 33 + lane]);
-            tc::tmem_st32(lrow + (uint32_t)(l * 64 + (warp >> 2) * 32), r);
+            tc::tmem_st32(lrow + (uint32_t)(l * 32), r);
         }
         tc::tmem_wait_st();
     }
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    // ---- TMEM -> swizzled A tiles in the freed accumulator memory; the producer starts the
-    //      operand copies into the same memory
+    // ---- TMEM -> swizzled A tiles in the freed accumulator memory, row = the pixel's row-major
+    //      index in the 16x8 block; the producer starts the operand copies into the same memory
     if (ok && warp < FC::kWarps) {
-        const int row = 32 * (warp & 3) + lane, h = warp >> 2;
-        const uint32_t lrow = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+        const int row = FC::lane_y(warp, lane) * kTW + FC::lane_x(warp, lane);
 #pragma unroll 1
         for (int l = 0; l < kLev; ++l) {
             uint32_t r[32];
-            tc::tmem_ld32(lrow + (uint32_t)(l * 64 + h * 32), r);
+            tc::tmem_ld32(lrow + (uint32_t)(l * 32), r);
             tc::tmem_wait_ld();
-            uint8_t* A = smem + kAOff + (l * 2 + h) * kATile;
+            uint8_t* A = smem + kAOff + l * kATile;
 #pragma unroll
             for (int c = 0; c < 8; ++c)
                 *reinterpret_cast<uint4*>(A + tc::sw128(row, 8 * c)) = make_uint4(r[4 * c], r[4 * c + 1], r[4 * c + 2], r[4 * c + 3]);
         }
     }
-    const int nb = do_dec ? kLev * nchunk : 0;   // B chunks per tile
+    const int nb = do_dec ? kLev * nfc : 0;   // B chunks per block
     if (ok && warp == FC::kWarps && lane == 0) {
         for (int g = 0; g < kBSlots && g < nb; ++g) {
             tc::bulk_load_arm(tc::smem_u32(&fb->bfull[g]), kBChunk);
@@ -172,9 +166,8 @@ __global__ void __launch_bounds__(FC::kThreads, 1) fused_kernel(FusedArgs a)
         }
         if (do_query) {
             const uint32_t qb = (uint32_t)a.npadq * 128;
-            const uint32_t first = kLev * qb <= (uint32_t)kQBytes ? kLev * qb : qb;   // all levels if they fit
-            tc::bulk_load_arm(tc::smem_u32(&fb->qload), first);
-            tc::bulk_load(tc::smem_u32(smem + kQOff), a.Bq, first, tc::smem_u32(&fb->qload));
+            tc::bulk_load_arm(tc::smem_u32(&fb->qload), qb);
+            tc::bulk_load(tc::smem_u32(smem + kQOff), a.Bq, qb, tc::smem_u32(&fb->qload));
         }
     }
     if (do_query)
@@ -188,47 +181,34 @@ __global__ void __launch_bounds__(FC::kThreads, 1) fused_kernel(FusedArgs a)
     volatile int* abort_flag = sm.abort;
     if (ok && warp == FC::kWarps) {
         // ---- MMA issue (lane 0) and operand copies, in the epilogue's order
-        const uint32_t idd = tc::idesc_bf16(kM, 128);
-        int g = 0;            // decode MMA groups issued
+        const uint32_t idd = tc::idesc_bf16(kM, 64);
+        int g = 0;            // F MMA groups issued
         int bc = 0;           // B chunks consumed
         int b_loaded = nb < kBSlots ? nb : kBSlots;   // B chunks whose copies were issued
         int q_loaded = do_query ? 1 : 0;              // query-matrix copies issued
-        int last_commit = -1; // 0: qfull of group gq_last; 1: dfull of group g - 1
+        int last_commit = -1;                         // 1: dfull of group g - 1 was committed last
         const uint32_t qb = (uint32_t)a.npadq * 128;
-        const bool q_all = kLev * qb <= (uint32_t)kQBytes;
         for (int l = 0; l < kLev && ok; ++l) {
             if (do_query) {
-                if ((l == 0 || !q_all) &&
-                    warp_wait(&fb->qload, (uint32_t)(l & 1), nullptr, 0, abort_flag) != kWaitDone) {
+                if (warp_wait(&fb->qload, (uint32_t)(l & 1), nullptr, 0, abort_flag) != kWaitDone ||
+                    (l > 0 && warp_wait(&fb->qempty, (uint32_t)((l - 1) & 1), nullptr, 0, abort_flag) != kWaitDone)) {
                     ok = false;
                     break;
                 }
-                for (int h = 0; h < 2; ++h) {
-                    const int gq = 2 * l + h;
-                    if (gq > 0 && warp_wait(&fb->qempty, (uint32_t)((gq - 1) & 1), nullptr, 0, abort_flag) != kWaitDone) {
-                        ok = false;
-                        break;
-                    }
-                    if (lane == 0) {
-                        tc::fence_after();
-                        const uint32_t a0 = tc::smem_u32(smem + kAOff + (l * 2 + h) * kATile);
-                        const uint32_t b0 = tc::smem_u32(smem + kQOff + (q_all ? l * qb : 0u));
-                        for (int n0 = 0; n0 < a.npadq; n0 += 256) {
-                            const int nn = a.npadq - n0 < 256 ? a.npadq - n0 : 256;
+                if (lane == 0) {
+                    tc::fence_after();
+                    const uint32_t a0 = tc::smem_u32(smem + kAOff + l * kATile), b0 = tc::smem_u32(smem + kQOff);
 #pragma unroll
-                            for (int k = 0; k < 4; ++k)
-                                tc::mma_bf16(tmem + 256u + (uint32_t)n0, tc::desc_sw128(a0 + k * 32),
-                                             tc::desc_sw128(b0 + n0 * 128 + k * 32), tc::idesc_bf16(kM, nn), k > 0 ? 1u : 0u);
-                        }
-                        tc::mma_commit(tc::smem_u32(&fb->qfull));
-                        if (h == 1) tc::mma_commit(tc::smem_u32(&fb->qfree));
-                    }
-                    __syncwarp();
-                    last_commit = 0;
+                    for (int k = 0; k < 4; ++k)
+                        tc::mma_bf16(tmem + 128u, tc::desc_sw128(a0 + k * 32), tc::desc_sw128(b0 + k * 32),
+                                     tc::idesc_bf16(kM, a.npadq), k > 0 ? 1u : 0u);
+                    tc::mma_commit(tc::smem_u32(&fb->qfull));
+                    tc::mma_commit(tc::smem_u32(&fb->qfree));
                 }
-                if (!ok) break;
-                if (l + 1 < kLev && !q_all) {
-                    // the next level's query matrix replaces this one once its MMAs have read it
+                __syncwarp();
+                last_commit = 0;
+                if (l + 1 < kLev) {
+                    // the next level's query matrix replaces this one once the MMA has read it
                     if (warp_wait(&fb->qfree, (uint32_t)(l & 1), nullptr, 0, abort_flag) != kWaitDone) { ok = false; break; }
                     if (lane == 0) {
                         tc::bulk_load_arm(tc::smem_u32(&fb->qload), qb);
@@ -238,34 +218,26 @@ __global__ void __launch_bounds__(FC::kThreads, 1) fused_kernel(FusedArgs a)
                 }
             }
             if (!do_dec) continue;
-            for (int c = 0; c < nchunk; ++c, ++bc) {
-                const int s = bc % kBSlots;
-                if (warp_wait(&fb->bfull[s], (uint32_t)((bc / kBSlots) & 1), nullptr, 0, abort_flag) != kWaitDone) {
+            for (int c = 0; c < nfc; ++c, ++bc, ++g) {
+                const int s = bc % kBSlots, buf = g & 1;
+                if (warp_wait(&fb->bfull[s], (uint32_t)((bc / kBSlots) & 1), nullptr, 0, abort_flag) != kWaitDone ||
+                    (g >= 2 && warp_wait(&fb->dempty[buf], (uint32_t)(((g - 2) >> 1) & 1), nullptr, 0, abort_flag) != kWaitDone)) {
                     ok = false;
                     break;
                 }
-                for (int h = 0; h < 2; ++h, ++g) {
-                    const int buf = g & 1;
-                    if (g >= 2 && warp_wait(&fb->dempty[buf], (uint32_t)(((g - 2) >> 1) & 1), nullptr, 0, abort_flag) != kWaitDone) {
-                        ok = false;
-                        break;
-                    }
-                    if (lane == 0) {
-                        tc::fence_after();
-                        const uint32_t a0 = tc::smem_u32(smem + kAOff + (l * 2 + h) * kATile);
-                        const uint32_t b0 = tc::smem_u32(smem + kBOff + s * kBChunk);
+                if (lane == 0) {
+                    tc::fence_after();
+                    const uint32_t a0 = tc::smem_u32(smem + kAOff + l * kATile), b0 = tc::smem_u32(smem + kBOff + s * kBChunk);
 #pragma unroll
-                        for (int k = 0; k < 4; ++k)
-                            tc::mma_bf16(tmem + (uint32_t)(buf * 128), tc::desc_sw128(a0 + k * 32), tc::desc_sw128(b0 + k * 32),
-                                         idd, k > 0 ? 1u : 0u);
-                        tc::mma_commit(tc::smem_u32(&fb->dfull[buf]));
-                        if (h == 1) tc::mma_commit(tc::smem_u32(&fb->bempty[s]));
-                    }
-                    __syncwarp();
-                    last_commit = 1;
+                    for (int k = 0; k < 4; ++k)
+                        tc::mma_bf16(tmem + (uint32_t)(buf * 64), tc::desc_sw128(a0 + k * 32), tc::desc_sw128(b0 + k * 32),
+                                     idd, k > 0 ? 1u : 0u);
+                    tc::mma_commit(tc::smem_u32(&fb->dfull[buf]));
+                    tc::mma_commit(tc::smem_u32(&fb->bempty[s]));
                 }
-                if (!ok) break;
-                // refill this slot with chunk bc + kBSlots once both MMAs have read it
+                __syncwarp();
+                last_commit = 1;
+                // refill this slot with chunk bc + kBSlots once the MMA has read it
                 const int nxt = bc + kBSlots;
                 if (nxt < nb) {
                     if (warp_wait(&fb->bempty[s], (uint32_t)((bc / kBSlots) & 1), nullptr, 0, abort_flag) != kWaitDone) {
@@ -294,115 +266,116 @@ __global__ void __launch_bounds__(FC::kThreads, 1) fused_kernel(FusedArgs a)
                 (void)tc::mbar_wait(tc::smem_u32(&fb->dfull[(g - 1) & 1]), (uint32_t)(((g - 1) >> 1) & 1), 100000000ull);
         }
     } else if (ok && warp < FC::kWarps) {
-        // ---- epilogues
-        const int q4 = warp & 3, wh = warp >> 2;
-        const uint32_t lrow = tmem + ((uint32_t)(32 * q4) << 16);
-        const int row = 32 * q4 + lane;
+        // ---- epilogues: this warp owns MMA rows 32 q4 .. 32 q4 + 31 = image rows 2 q4, 2 q4 + 1
+        const int q4 = warp, row = 32 * q4 + lane;
+        const int gx = x0 + (row & 15), gy = y0 + (row >> 4);
+        const bool in = gx < a.width && gy < a.height;
+        const size_t pix = (size_t)gy * a.width + gx;
         const float* rtn = reinterpret_cast<const float*>(smem + kTnOff);
         const int per = 1 + a.n_neg;
+        uint8_t* box = smem + kStgOff + (size_t)(q4 * 2 + (lane >> 4)) * kBoxBytes;   // this lane's image row
+        const int br = lane & 15;                                                       // its row in the box
         int g = 0;
         for (int l = 0; l < kLev && ok; ++l) {
             if (do_query) {
-                for (int h = 0; h < 2; ++h) {
-                    const int gq = 2 * l + h;
-                    if (warp_wait(&fb->qfull, (uint32_t)(gq & 1), nullptr, 0, abort_flag) != kWaitDone) { ok = false; break; }
-                    tc::fence_after();
-                    size_t pix;
-                    const bool in = tile_pixel(a, tile, h, q4, lane, pix);
-                    // |F|^2 = W . (S S^T W): columns 0..63, W from this level's A tile
-                    const uint8_t* A = smem + kAOff + (l * 2 + h) * kATile;
-                    float n2;
-                    {
-                        uint32_t y0[32], y1[32];
-                        tc::tmem_ld32(lrow + 256u, y0);
-                        tc::tmem_ld32(lrow + 256u + 32u, y1);
+                if (warp_wait(&fb->qfull, (uint32_t)(l & 1), nullptr, 0, abort_flag) != kWaitDone) { ok = false; break; }
+                tc::fence_after();
+                // |F|^2 = W . (S S^T W): columns 0..63 of Y, W from this level's A tile
+                float n2;
+                {
+                    uint32_t ya[32], yb[32];
+                    tc::tmem_ld32(lrow + 128u, ya);
+                    tc::tmem_ld32(lrow + 128u + 32u, yb);
+                    tc::tmem_wait_ld();
+                    n2 = gram_norm2(smem + kAOff + l * kATile, row, ya, yb);
+                }
+                const float nf = sqrtf(fmaxf(n2, 0.0f));
+                const float kneg = nf < 1e-12f ? 0.0f : -a.tau / nf;
+                const int nch = a.Qp / 8;
+                for (int c = 0; c < nch; ++c) {
+                    const int q0 = c * 8;
+                    uint32_t rp[8], rn[8];
+                    tc::tmem_ld8(lrow + 128u + (uint32_t)(64 + q0), rp);
+                    float best[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) best[e] = -INFINITY;
+                    for (int t = 1; t < per; ++t) {
+                        tc::tmem_ld8(lrow + 128u + (uint32_t)(64 + t * a.Qp + q0), rn);
                         tc::tmem_wait_ld();
-                        n2 = gram_norm2(A, row, y0, y1);
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) best[e] = fmaxf(best[e], __uint_as_float(rn[e]) * rtn[t * a.Qp + q0 + e]);
                     }
-                    const float nf = sqrtf(fmaxf(n2, 0.0f));
-                    const float kneg = nf < 1e-12f ? 0.0f : -a.tau / nf;
-                    const int nch = a.Qp / 8, chh = (nch + 1) / 2;
-                    for (int c = wh ? chh : 0; c < (wh ? nch : chh); ++c) {
-                        const int q0 = c * 8;
-                        uint32_t rp[8], rn[8];
-                        tc::tmem_ld8(lrow + 256u + (uint32_t)(64 + q0), rp);
-                        float best[8];
+                    tc::tmem_wait_ld();
+                    if (in) {
 #pragma unroll
-                        for (int e = 0; e < 8; ++e) best[e] = -INFINITY;
-                        for (int t = 1; t < per; ++t) {
-                            tc::tmem_ld8(lrow + 256u + (uint32_t)(64 + t * a.Qp + q0), rn);
-                            tc::tmem_wait_ld();
-#pragma unroll
-                            for (int e = 0; e < 8; ++e) best[e] = fmaxf(best[e], __uint_as_float(rn[e]) * rtn[t * a.Qp + q0 + e]);
-                        }
-                        tc::tmem_wait_ld();
-                        if (in) {
-#pragma unroll
-                            for (int e = 0; e < 8; ++e) {
-                                const int q = q0 + e;
-                                if (q < a.Q) {
-                                    const float d = __uint_as_float(rp[e]) * rtn[q0 + e] - best[e];
-                                    const float rv = __fdividef(1.0f, 1.0f + __expf(kneg * d));
-                                    const size_t o = ((size_t)q * kLev + l) * P + pix;
-                                    if (a.rel_bf16) static_cast<__nv_bfloat16*>(a.rel)[o] = __float2bfloat16_rn(rv);
-                                    else static_cast<float*>(a.rel)[o] = rv;
+                        for (int e = 0; e < 8; ++e) {
+                            const int q = q0 + e;
+                            if (q < a.Q) {
+                                const float d = __uint_as_float(rp[e]) * rtn[q0 + e] - best[e];
+                                const size_t o = ((size_t)q * kLev + l) * P + pix;
+                                if (a.rel_bf16) {
+                                    // as the tensor-core relevancy: sigmoid through the hardware tanh
+                                    float th;
+                                    asm("tanh.approx.f32 %0, %1;" : "=f"(th) : "f"(-0.5f * kneg * d));
+                                    static_cast<__nv_bfloat16*>(a.rel)[o] = __float2bfloat16_rn(fmaf(0.5f, th, 0.5f));
+                                } else {
+                                    static_cast<float*>(a.rel)[o] = __fdividef(1.0f, 1.0f + __expf(kneg * d));
                                 }
                             }
                         }
                     }
-                    tc::fence_before();
-                    __syncwarp();
-                    if (lane == 0) tc::mbar_arrive(tc::smem_u32(&fb->qempty));
                 }
-                if (!ok) break;
+                tc::fence_before();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(tc::smem_u32(&fb->qempty));
             }
             if (!do_dec) continue;
-            for (int c = 0; c < nchunk && ok; ++c) {
-                for (int h = 0; h < 2; ++h, ++g) {
-                    const int buf = g & 1;
-                    if (warp_wait(&fb->dfull[buf], (uint32_t)((g >> 1) & 1), nullptr, 0, abort_flag) != kWaitDone) {
-                        ok = false;
-                        break;
+            for (int c = 0; c < nfc && ok; ++c, ++g) {
+                const int buf = g & 1;
+                if (warp_wait(&fb->dfull[buf], (uint32_t)((g >> 1) & 1), nullptr, 0, abort_flag) != kWaitDone) {
+                    ok = false;
+                    break;
+                }
+                tc::fence_after();
+                uint32_t r[32], r2[32];
+                tc::tmem_ld32(lrow + (uint32_t)(buf * 64), r);
+                tc::tmem_ld32(lrow + (uint32_t)(buf * 64 + 32), r2);
+                tc::tmem_wait_ld();
+                tc::fence_before();
+                __syncwarp();
+                if (lane == 0) {
+                    tc::mbar_arrive(tc::smem_u32(&fb->dempty[buf]));
+                    tc::bulk_wait_read<0>();   // the previous chunk's boxes have been read
+                }
+                __syncwarp();
+                // this lane's 64 features of the chunk -> row br of its image row's box (128-byte
+                // swizzle: 16-byte chunk v at position v ^ (br % 8))
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    *reinterpret_cast<uint4*>(box + br * 128 + ((v ^ (br & 7)) << 4)) =
+                        make_uint4(tc::pack_bf16(__uint_as_float(r[8 * v]), __uint_as_float(r[8 * v + 1])),
+                                   tc::pack_bf16(__uint_as_float(r[8 * v + 2]), __uint_as_float(r[8 * v + 3])),
+                                   tc::pack_bf16(__uint_as_float(r[8 * v + 4]), __uint_as_float(r[8 * v + 5])),
+                                   tc::pack_bf16(__uint_as_float(r[8 * v + 6]), __uint_as_float(r[8 * v + 7])));
+                    *reinterpret_cast<uint4*>(box + br * 128 + (((v + 4) ^ (br & 7)) << 4)) =
+                        make_uint4(tc::pack_bf16(__uint_as_float(r2[8 * v]), __uint_as_float(r2[8 * v + 1])),
+                                   tc::pack_bf16(__uint_as_float(r2[8 * v + 2]), __uint_as_float(r2[8 * v + 3])),
+                                   tc::pack_bf16(__uint_as_float(r2[8 * v + 4]), __uint_as_float(r2[8 * v + 5])),
+                                   tc::pack_bf16(__uint_as_float(r2[8 * v + 6]), __uint_as_float(r2[8 * v + 7])));
+                }
+                tc::fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) {
+                    for (int hh = 0; hh < 2; ++hh) {
+                        const int yy = y0 + 2 * q4 + hh;
+                        if (yy < a.height)
+                            tc::tma_store_4d(&tmF, c * 64, x0, yy, l, tc::smem_u32(smem + kStgOff + (q4 * 2 + hh) * kBoxBytes));
                     }
-                    tc::fence_after();
-                    uint32_t r[32], r2[32];
-                    tc::tmem_ld32(lrow + (uint32_t)(buf * 128 + wh * 64), r);
-                    tc::tmem_ld32(lrow + (uint32_t)(buf * 128 + wh * 64 + 32), r2);
-                    tc::tmem_wait_ld();
-                    tc::fence_before();
-                    __syncwarp();
-                    if (lane == 0) tc::mbar_arrive(tc::smem_u32(&fb->dempty[buf]));
-                    // stage this warp's 32 rows x 128 bytes, then write them with coalesced
-                    // 512-byte warp stores (4 pixel segments of 128 bytes each)
-                    uint8_t* stg = smem + (wh ? kStage1Off : kStage0Off);
-                    uint4* mine = reinterpret_cast<uint4*>(stg + row * kStageRow);
-#pragma unroll
-                    for (int v = 0; v < 4; ++v)
-                        mine[v] = make_uint4(tc::pack_bf16(__uint_as_float(r[8 * v]), __uint_as_float(r[8 * v + 1])),
-                                             tc::pack_bf16(__uint_as_float(r[8 * v + 2]), __uint_as_float(r[8 * v + 3])),
-                                             tc::pack_bf16(__uint_as_float(r[8 * v + 4]), __uint_as_float(r[8 * v + 5])),
-                                             tc::pack_bf16(__uint_as_float(r[8 * v + 6]), __uint_as_float(r[8 * v + 7])));
-#pragma unroll
-                    for (int v = 0; v < 4; ++v)
-                        mine[4 + v] = make_uint4(tc::pack_bf16(__uint_as_float(r2[8 * v]), __uint_as_float(r2[8 * v + 1])),
-                                                 tc::pack_bf16(__uint_as_float(r2[8 * v + 2]), __uint_as_float(r2[8 * v + 3])),
-                                                 tc::pack_bf16(__uint_as_float(r2[8 * v + 4]), __uint_as_float(r2[8 * v + 5])),
-                                                 tc::pack_bf16(__uint_as_float(r2[8 * v + 6]), __uint_as_float(r2[8 * v + 7])));
-                    __syncwarp();
-#pragma unroll
-                    for (int it = 0; it < 8; ++it) {
-                        const int lr = it * 4 + (lane >> 3), ch = lane & 7;   // row within the warp's 32, 16-byte chunk
-                        size_t px2;
-                        if (tile_pixel(a, tile, h, q4, lr, px2)) {
-                            const uint4 v = *reinterpret_cast<const uint4*>(stg + (32 * q4 + lr) * kStageRow + ch * 16);
-                            __stcs(reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(a.F) +
-                                                            ((size_t)l * P + px2) * a.D + c * 128 + wh * 64) + ch, v);
-                        }
-                    }
-                    __syncwarp();
+                    tc::bulk_commit();
                 }
             }
         }
+        if (lane == 0) tc::bulk_wait_all();
         if (!ok && lane == 0) report(a.status, LSV2_ERR_TIMEOUT);
     }
     // every MMA was waited on by an epilogue, or the issuer drained what it started
@@ -410,11 +383,11 @@ __global__ void __launch_bounds__(FC::kThreads, 1) fused_kernel(FusedArgs a)
     __syncthreads();
     if (warp == 0) {
         tc::fence_after();
-        tc::tmem_dealloc(tmem, 512);
+        tc::tmem_dealloc(tmem, kTmemCols);
     }
 }
 
-// Operands of the fused kernel: the codebook S^T of every level as swizzled BF16 chunks of 128
+// Operands of the fused kernel: the codebook S^T of every level as swizzled BF16 chunks of 64
 // rows, and (with queries) the text-major [S S^T | S t] rows and reciprocal text norms.
 __global__ void fused_prep_kernel(int levels, int D, const float* S, int Q, int n_neg, int Qp, int npadq,
                                   const float* Bt, const float* tnorm, uint8_t* Bdec, uint8_t* Bq, float* rtn)
@@ -426,8 +399,8 @@ __global__ void fused_prep_kernel(int levels, int D, const float* S, int Q, int 
         if (i < n_dec) {
             const int n = i >> 6, k = i & 63;      // row n of S^T = column n of S
             const float v = S[((size_t)l * 64 + k) * D + n];
-            uint8_t* chunk = Bdec + ((size_t)l * (D / 128) + n / 128) * kBChunk;
-            *reinterpret_cast<__nv_bfloat16*>(chunk + tc::sw128(n % 128, k)) = __float2bfloat16_rn(v);
+            uint8_t* chunk = Bdec + ((size_t)l * (D / 64) + n / 64) * kBChunk;
+            *reinterpret_cast<__nv_bfloat16*>(chunk + tc::sw128(n % 64, k)) = __float2bfloat16_rn(v);
         } else {
             const int i2 = i - n_dec, n = i2 >> 6, k = i2 & 63;
             int src = n < 64 ? n : -1;
@@ -479,7 +452,7 @@ bool fused_supported(int levels, int K, int L, int D, int Q, int n_neg, int tw, 
 {
     if (levels != kLev || K != kKp || L != 64 || tw != kTW || th != kTH) return false;
     if (D < 128 || D > 512 || D % 128 != 0) return false;
-    if (Q < 0 || (Q > 0 && (n_neg < 1 || npadq_of(Q, n_neg) > kQMaxRows))) return false;
+    if (Q < 0 || (Q > 0 && (n_neg < 1 || npadq_of(Q, n_neg) > kQMaxRows))) return false;   // Q <= 8 at n_neg = 4
     return true;
 }
 
@@ -515,6 +488,15 @@ cudaError_t launch_fused(const lsv2_camera& cam, int64_t n, const lsv2_proj& pro
     if (e != cudaSuccess) return e;
     const int GX = (cam.width + kTW - 1) / kTW, GY = (cam.height + kTH - 1) / kTH;
     if (GX * GY == 0) return cudaSuccess;
+    // F [levels][H][W][D] BF16 in boxes of 64 features x 16 pixels of one image row
+    CUtensorMap tmF;
+    if (F) {
+        if (!encode_tmap_4d(&tmF, F, true, (uint64_t)D, (uint64_t)cam.width, (uint64_t)cam.height, (uint64_t)kLev, 64u,
+                            16u, false))
+            return cudaErrorInvalidValue;
+    } else {
+        std::memset(&tmF, 0, sizeof(tmF));
+    }
     FusedArgs a{};
     a.width = cam.width;
     a.height = cam.height;
@@ -526,7 +508,7 @@ cudaError_t launch_fused(const lsv2_camera& cam, int64_t n, const lsv2_proj& pro
     a.n_last = n_last;
     a.D = D;
     a.Bdec = reinterpret_cast<const uint8_t*>(base + Lo.bdec);
-    a.F = F;
+    a.do_dec = F != nullptr ? 1 : 0;
     a.Q = Q;
     a.n_neg = n_neg;
     a.Qp = Qp;
@@ -538,10 +520,10 @@ cudaError_t launch_fused(const lsv2_camera& cam, int64_t n, const lsv2_proj& pro
     a.rel_bf16 = rel_bf16 ? 1 : 0;
     a.status = status;
     constexpr int kSmem = FC::kSmemBytes + 1024;
-    static_assert(kSmem <= 232448, "shared memory budget");
+    static_assert(2 * (kSmem + 1024) <= 233472, "two CTAs per SM");
     e = cudaFuncSetAttribute(fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
     if (e != cudaSuccess) return e;
-    fused_kernel<<<GX * GY, FC::kThreads, kSmem, stream>>>(a);
+    fused_kernel<<<GX * GY * 2, FC::kThreads, kSmem, stream>>>(tmF, a);
     return cudaGetLastError();
 }
 

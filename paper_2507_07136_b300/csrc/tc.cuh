@@ -194,6 +194,14 @@ __device__ __forceinline__ void tma_store_3d(const void* map, int x, int y, int 
                  : "memory");
 }
 
+// The same for a 4-D tensor map.
+__device__ __forceinline__ void tma_store_4d(const void* map, int x, int y, int z, int w, uint32_t ssrc)
+{
+    asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3, %4}], [%5];" ::"l"(map),
+                 "r"(x), "r"(y), "r"(z), "r"(w), "r"(ssrc)
+                 : "memory");
+}
+
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 // Wait until at most N of this thread's most recent bulk groups still read shared memory.
 template <int N>

@@ -17,4 +17,8 @@ namespace lsv2 {
 bool encode_tmap_3d(CUtensorMap* map, const void* base, bool bf16, uint64_t d0, uint64_t d1, uint64_t d2,
                     uint32_t b0, uint32_t b1, bool promote_l2);
 
+// The same for a 4-D tensor {d0, d1, d2, d3} in boxes of {b0, b1, 1, 1}.
+bool encode_tmap_4d(CUtensorMap* map, const void* base, bool bf16, uint64_t d0, uint64_t d1, uint64_t d2, uint64_t d3,
+                    uint32_t b0, uint32_t b1, bool promote_l2);
+
 }  // namespace lsv2

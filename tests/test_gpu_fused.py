@@ -60,12 +60,31 @@ def test_fused_equals_split_path_bitwise():
     assert torch.equal(ra, rb), "relevancy differs from splat -> query"
 
 
-@pytest.mark.parametrize("Q,n_neg", [(8, 4), (13, 2), (32, 4)])
+@pytest.mark.parametrize("Q,n_neg", [(1, 4), (8, 4), (13, 2), (16, 3)])
 def test_fused_query_counts(Q, n_neg):
     sc, cam = small()
     text = syn.text_queries(syn.SEED + 2 + Q, Q, n_neg)
     _, _, (ra, rb) = split_and_fused(sc, cam, text, decode=False)
     assert torch.equal(ra, rb)
+
+
+def test_fused_bf16_relevancy_equals_split_path():
+    """BF16 relevancy output (sigmoid through the hardware tanh on both paths), ragged frame."""
+    sc, cam = small()
+    text = syn.text_queries(syn.SEED + 7, 3, 4)
+    ds = DeviceScene.from_numpy(sc)
+    a = Frame(ds, cam)
+    a.render()
+    td = torch.as_tensor(text, device="cuda")
+    ra = torch.empty((3, ds.levels, cam.num_pixels), dtype=torch.bfloat16, device="cuda")
+    a.query(td, ra, compute=L.LSV2_BF16)
+    b = Frame(ds, cam, capacity=a.capacity)
+    b.project()
+    b.bin_sort()
+    rb = torch.full_like(ra, float("nan"))
+    b.render_fused(None, td, rb)
+    b.check()
+    assert torch.equal(ra.view(torch.int16), rb.view(torch.int16))
 
 
 def test_fused_decode_only_and_against_oracle():
@@ -93,7 +112,8 @@ def test_fused_rejects_unsupported():
     ds = DeviceScene.from_numpy(sc)
     assert L.lsv2_render_fused_workspace_bytes(ds.n, 3, 4, 500, 1, 4) == 0     # D not a multiple of 128
     assert L.lsv2_render_fused_workspace_bytes(ds.n, 2, 4, 512, 1, 4) == 0     # two levels
-    assert L.lsv2_render_fused_workspace_bytes(ds.n, 3, 4, 512, 64, 4) == 0    # 64 + 5 * 64 > 256
+    assert L.lsv2_render_fused_workspace_bytes(ds.n, 3, 4, 512, 64, 4) == 0    # 64 + 5 * 64 > 128
+    assert L.lsv2_render_fused_workspace_bytes(ds.n, 3, 4, 512, 9, 4) == 0     # 64 + 5 * 16 > 128
     fr = Frame(ds, cam.with_tile(8, 8))
     fr.project()
     fr.bin_sort()
