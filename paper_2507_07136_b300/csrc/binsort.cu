@@ -181,9 +181,9 @@ __device__ void bitonic_smem(unsigned long long* s, int npow2)
     }
 }
 
-// Bitonic sorting network over 32 K keys held by one warp, key i = j * 32 + lane in register j:
-// partners i ^ m with m >= 32 are registers of the same lane, the others are exchanged by
-// shuffles.  Ascending on return.
+// Bitonic sorting network over 32 K keys held by one warp, key i = lane * K + j in register j:
+// partners i ^ m with m < K are registers of the same lane, the others (m >= K) are exchanged
+// with lane ^ (m / K) by shuffles.  Ascending on return.
 template <int K>
 __device__ __forceinline__ void warp_bitonic(unsigned long long (&x)[K], int lane)
 {
@@ -191,24 +191,24 @@ __device__ __forceinline__ void warp_bitonic(unsigned long long (&x)[K], int lan
     for (int k = 2; k <= 32 * K; k <<= 1) {
 #pragma unroll
         for (int m = k >> 1; m > 0; m >>= 1) {
-            if (m >= 32) {
-                const int mj = m >> 5;
+            if (m < K) {
 #pragma unroll
                 for (int j = 0; j < K; ++j) {
-                    if ((j & mj) == 0) {
-                        const bool up = ((j * 32) & k) == 0;   // k >= 64 here: the lane bits do not matter
-                        const unsigned long long lo = x[j], hi = x[j | mj];
+                    if ((j & m) == 0) {
+                        const bool up = (((lane * K) | j) & k) == 0;
+                        const unsigned long long lo = x[j], hi = x[j | m];
                         const bool sw = (lo > hi) == up;
                         x[j] = sw ? hi : lo;
-                        x[j | mj] = sw ? lo : hi;
+                        x[j | m] = sw ? lo : hi;
                     }
                 }
             } else {
-                const bool lower = (lane & m) == 0;        // this lane holds the pair's lower index
+                const int ml = m / K;
+                const bool lower = (lane & ml) == 0;       // this lane holds the pair's lower index
 #pragma unroll
                 for (int j = 0; j < K; ++j) {
-                    const bool up = (((j * 32) | lane) & k) == 0;
-                    const unsigned long long o = __shfl_xor_sync(0xffffffffu, x[j], m);
+                    const bool up = (((lane * K) | j) & k) == 0;
+                    const unsigned long long o = __shfl_xor_sync(0xffffffffu, x[j], ml);
                     x[j] = (lower == up) ? (o < x[j] ? o : x[j]) : (o > x[j] ? o : x[j]);
                 }
             }
@@ -221,11 +221,11 @@ __device__ __forceinline__ void warp_sort_tile(const unsigned long long* keys, u
 {
     unsigned long long x[K];
 #pragma unroll
-    for (int j = 0; j < K; ++j) x[j] = j * 32 + lane < n ? keys[b + j * 32 + lane] : ~0ull;
+    for (int j = 0; j < K; ++j) x[j] = lane * K + j < n ? keys[b + lane * K + j] : ~0ull;
     warp_bitonic<K>(x, lane);
 #pragma unroll
     for (int j = 0; j < K; ++j)
-        if (j * 32 + lane < n) ids[b + j * 32 + lane] = (uint32_t)x[j];
+        if (lane * K + j < n) ids[b + lane * K + j] = (uint32_t)x[j];
 }
 
 // One warp per tile of at most kWarpCap keys (the common case), four tiles per block; the key
