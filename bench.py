@@ -294,7 +294,11 @@ def profile_stage(args, frame, scene, text, dev):
     frame.bin_sort()
     frame.splat_bf16()
     P, D = frame.P, scene.D
-    if args.profile == "splat":
+    if args.profile == "project":
+        fn = frame.project
+    elif args.profile == "bin":
+        fn = frame.bin_sort
+    elif args.profile == "splat":
         fn = frame.splat_bf16
     elif args.profile == "decode":
         F = torch.empty((1, P, D), dtype=torch.bfloat16, device=dev)
@@ -327,7 +331,7 @@ def main():
     ap.add_argument("--no-fp32-path", action="store_true", help="skip the plain FP32 comparison measurement")
     ap.add_argument("--no-batched", action="store_true", help="skip the 16-view x 64-query batched measurement")
     ap.add_argument("--no-ablation", action="store_true", help="skip the sparse/dense and K speed ablation")
-    ap.add_argument("--profile", choices=["splat", "decode", "query"], default=None,
+    ap.add_argument("--profile", choices=["project", "bin", "splat", "decode", "query"], default=None,
                     help="for a profiler capture: prepare the at-scale frame, then run only this stage "
                          "(--warmup + --steps launches) with only the buffers it needs; prints one status line")
     args = ap.parse_args()
