@@ -17,6 +17,8 @@ Each function names the passage of the paper it follows (LangSplatV2, arXiv
   l1_grads      gradient of the L1 feature loss (decode adjoint as matmuls,
                 blend adjoint as the literal derivative, projection Jacobian by
                 complex step)
+  sparsify,     Sec. 3.3 sparse coefficients: softmax over the L-dim parameter, top K
+  sparsify_backward   kept and renormalised by their sum; its gradient (NumPy, FP64)
 """
 from __future__ import annotations
 
@@ -248,6 +250,40 @@ def relevancy(F, text, tau: float = 10.0) -> np.ndarray:
     rel = np.zeros((Q, lev, npix))
     lib().orc_relevancy(lev, npix, D, _p(F), Q, nt - 1, _p(text), float(tau), _p(rel))
     return rel
+
+
+def sparsify(logits, K: int):
+    """Sec. 3.3: the L-dim parameter of a Gaussian (per level) is normalised by a softmax, the K
+    largest values are kept as the nonzeros and renormalised by their sum.  logits f32 [..., L] ->
+    (idx u8 [..., K], w f64 [..., K]).  The kept entries are those with the largest logits (the
+    softmax is monotone; selecting on the FP32 logits keeps the integer decision exact), the lower
+    index first among equal logits, listed in that order (descending value)."""
+    z = np.ascontiguousarray(logits, np.float32)
+    L = z.shape[-1]
+    assert 1 <= K <= L <= 256
+    zr = z.reshape(-1, L)
+    zd = zr.astype(np.float64)
+    p = np.exp(zd - zd.max(axis=1, keepdims=True))
+    p = p / p.sum(axis=1, keepdims=True)                       # softmax over the L entries
+    order = np.argsort(-zr, axis=1, kind="stable")[:, :K]      # top K, lower index first on ties
+    pk = np.take_along_axis(p, order, axis=1)
+    w = pk / pk.sum(axis=1, keepdims=True)                     # renormalised by their sum
+    shape = z.shape[:-1] + (K,)
+    return order.astype(np.uint8).reshape(shape), w.reshape(shape)
+
+
+def sparsify_backward(idx, w, dw, L: int) -> np.ndarray:
+    """Gradient of sparsify's weights with respect to the logits.  The kept weights are
+    p_k / sum_m p_m with p = softmax(z), in which the softmax's denominator cancels: they equal a
+    softmax over the K kept logits.  With the selection fixed (it is piecewise constant), dL/dz
+    is zero for the dropped entries and w_k (dw_k - sum_m w_m dw_m) for kept entry k.
+    idx [..., K], w [..., K], dw [..., K] -> dlogits f64 [..., L]."""
+    w = np.asarray(w, np.float64)
+    dw = np.asarray(dw, np.float64)
+    g = w * (dw - (w * dw).sum(axis=-1, keepdims=True))
+    out = np.zeros(np.shape(idx)[:-1] + (L,))
+    np.put_along_axis(out, np.asarray(idx).astype(np.int64), g, axis=-1)
+    return out
 
 
 def mean_filter(M, k: int) -> np.ndarray:

@@ -518,3 +518,97 @@ def test_postprocess_ties_take_lowest_level_and_first_pixel():
     assert r.level[0] == 0 and tuple(r.point[0]) == (6, 2)
     flat = O.postprocess(np.full((1, 1, H * W), 0.7), H, W, k=1, mode=0, thr=0.5)
     assert flat.mask.sum() == 0 and flat.score[0] == pytest.approx(0.7)
+
+
+# ---- Sec. 3.3 sparse coefficients (softmax, top K, renormalisation) and their gradient ----
+
+def test_sparsify_closed_form():
+    """Logits log(p) for p = (0.05, 0.4, 0.1, 0.3, 0.15): softmax = p; top 2 = entries 1, 3;
+    renormalised 0.4 / 0.7, 0.3 / 0.7.  Top 3 adds entry 4: 0.4 / 0.85, 0.3 / 0.85, 0.15 / 0.85."""
+    p = np.array([0.05, 0.4, 0.1, 0.3, 0.15])
+    z = np.log(p).astype(np.float32)
+    idx, w = O.sparsify(z, 2)
+    assert idx.tolist() == [1, 3]
+    np.testing.assert_allclose(w, [0.4 / 0.7, 0.3 / 0.7], rtol=1e-6)
+    idx, w = O.sparsify(z, 3)
+    assert idx.tolist() == [1, 3, 4]
+    np.testing.assert_allclose(w, np.array([0.4, 0.3, 0.15]) / 0.85, rtol=1e-6)
+
+
+def test_sparsify_all_kept_is_the_softmax():
+    """K = L keeps everything: the weights are scipy's softmax of the logits, in descending order."""
+    from scipy.special import softmax
+    rng = np.random.default_rng(3)
+    z = rng.normal(0, 2, (50, 64)).astype(np.float32)
+    idx, w = O.sparsify(z, 64)
+    ref = softmax(z.astype(np.float64), axis=1)
+    np.testing.assert_allclose(w, np.take_along_axis(ref, idx.astype(np.int64), axis=1), rtol=1e-12)
+    assert np.all(np.diff(w, axis=1) <= 0)
+
+
+def test_sparsify_shift_invariance_and_unit_sum():
+    """Logits on a 1/1024 grid, so that adding 8 is exact in float32 (ties included)."""
+    rng = np.random.default_rng(4)
+    z = (rng.integers(-4096, 4096, (200, 64)) / 1024.0).astype(np.float32)
+    idx, w = O.sparsify(z, 4)
+    np.testing.assert_allclose(w.sum(axis=1), 1.0, rtol=1e-12)
+    idx2, w2 = O.sparsify(z + np.float32(8.0), 4)
+    assert np.array_equal(idx, idx2)
+    np.testing.assert_allclose(w, w2, rtol=1e-12)
+    # the kept logits are the K largest
+    zs = np.sort(z, axis=1)[:, ::-1]
+    np.testing.assert_array_equal(np.take_along_axis(z, idx.astype(np.int64), axis=1), zs[:, :4])
+
+
+def test_sparsify_ties_take_the_lower_index():
+    z = np.array([0.5, 2.0, 2.0, 0.5, 2.0, 1.0], np.float32)
+    idx, w = O.sparsify(z, 2)
+    assert idx.tolist() == [1, 2]
+    np.testing.assert_allclose(w, [0.5, 0.5], rtol=1e-15)
+    idx, _ = O.sparsify(np.zeros(8, np.float32), 3)
+    assert idx.tolist() == [0, 1, 2]
+
+
+def test_sparsify_backward_matches_central_fd():
+    """d(sum_k dw_k w_k)/dz by FP64 central differences (step 1e-6) of the forward, on logits whose
+    top K is separated from the rest by a margin (the selection does not change under the step)."""
+    rng = np.random.default_rng(5)
+    L, K = 16, 4
+    for _ in range(10):
+        z = rng.normal(0, 1, L)
+        z[rng.choice(L, K, replace=False)] += 3.0
+        dw = rng.normal(0, 1, K)
+        idx, w = O.sparsify(z.astype(np.float32), K)
+        g = O.sparsify_backward(idx, w, dw, L)
+
+        def f(zz):
+            zz = zz.astype(np.float64)
+            p = np.exp(zz - zz.max())
+            p /= p.sum()
+            pk = p[idx.astype(np.int64)]
+            return float((dw * pk / pk.sum()).sum())
+
+        zd = z.astype(np.float32).astype(np.float64)
+        fd = np.zeros(L)
+        for j in range(L):
+            e = np.zeros(L)
+            e[j] = 1e-6
+            fd[j] = (f(zd + e) - f(zd - e)) / 2e-6
+        np.testing.assert_allclose(g, fd, atol=1e-8)
+
+
+def test_sparsify_backward_invariants():
+    """Zero outside the kept entries; the gradient sums to zero (the weights sum to one)."""
+    rng = np.random.default_rng(6)
+    z = rng.normal(0, 1, (100, 64)).astype(np.float32)
+    idx, w = O.sparsify(z, 4)
+    dw = rng.normal(0, 1, (100, 4))
+    g = O.sparsify_backward(idx, w, dw, 64)
+    mask = np.zeros((100, 64), bool)
+    np.put_along_axis(mask, idx.astype(np.int64), True, axis=1)
+    assert np.all(g[~mask] == 0)
+    np.testing.assert_allclose(g.sum(axis=1), 0.0, atol=1e-14)
+    # top 1: the weight is 1 and the gradient vanishes
+    idx1, w1 = O.sparsify(z, 1)
+    assert np.all(w1 == 1.0)
+    assert np.all(O.sparsify_backward(idx1, w1, dw[:, :1], 64) == 0)
