@@ -306,6 +306,27 @@ lsv2_status lsv2_render_fused(const lsv2_camera* cam, int64_t n, const lsv2_proj
                               void* feat, void* rel, lsv2_dtype rel_dtype, float* final_T,
                               uint32_t* n_last, int32_t* dev_status, void* stream);
 
+/* Sparse coefficients (Sec. 3.3): each Gaussian's L-dim parameter of a level is normalised by a
+ * softmax, its K largest values are kept as the nonzeros and renormalised by their sum.
+ *   rows     number of rows (Gaussians x levels), row-major [rows][L]
+ *   logits   float[rows][L]
+ *   idx      uint8_t[rows][K] out: the kept entries, those with the K largest logits (the
+ *            softmax is monotone), in descending order of value, the lower index first among
+ *            equal logits (the idx input of lsv2_splat_coeffs)
+ *   w        float[rows][K] out: the renormalised weights (= softmax over the kept logits)
+ * Supported: L in {16, 32, 64, 128, 256}, K in {1, 2, 4, 8}, K <= L.  K = 4 needs w 16-byte and
+ * idx 4-byte aligned.  No workspace. */
+lsv2_status lsv2_sparsify(int64_t rows, int32_t L, int32_t K, const float* logits, uint8_t* idx, float* w,
+                          void* stream);
+
+/* Gradient of lsv2_sparsify's weights with respect to the logits, the selection held fixed (it
+ * is piecewise constant): dlogits[r][c] = 0 for a dropped entry c, and for kept entry k
+ * (c = idx[r][k]) w_k (dw_k - sum_m w_m dw_m).
+ *   idx, w   lsv2_sparsify's outputs;  dw  float[rows][K] (dLoss/dw)
+ *   dlogits  float[rows][L] out (every entry written) */
+lsv2_status lsv2_sparsify_backward(int64_t rows, int32_t L, int32_t K, const uint8_t* idx, const float* w,
+                                   const float* dw, float* dlogits, void* stream);
+
 /* Workspace for lsv2_postprocess: per (query, level) statistics (Q * levels * 32 bytes,
  * rounded up to 256).  0 for invalid sizes. */
 size_t lsv2_postprocess_workspace_bytes(int32_t Q, int32_t levels);

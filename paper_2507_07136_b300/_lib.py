@@ -59,6 +59,8 @@ _SIGS = {
     "lsv2_render_fused_workspace_bytes": ([I64, I32, I32, I32, I32, I32], SZ),
     "lsv2_render_fused": ([P, I64, P, P, P, I32, I32, I32, P, P, P, I32, I32, I32, P, F32, P, SZ, P, P, I32, P, P, P, P],
                           I32),
+    "lsv2_sparsify": ([I64, I32, I32, P, P, P, P], I32),
+    "lsv2_sparsify_backward": ([I64, I32, I32, P, P, P, P, P], I32),
     "lsv2_postprocess_workspace_bytes": ([I32, I32], SZ),
     "lsv2_postprocess": ([I32, I32, I32, I32, P, I32, I32, I32, F32, P, SZ, P, P, P, P, P, P, P], I32),
     "lsv2_l1_decode_backward": ([I32, I64, I32, I32, P, P, P, P, P, P, P], I32),
@@ -182,6 +184,14 @@ def lsv2_splat_backward(cam, n, means, scales, quats, proj, tile_ranges, gauss_i
     call("lsv2_splat_backward", C.byref(cam), n, means, scales, quats, C.byref(proj), tile_ranges, gauss_ids,
          levels, K, L, idx, w, final_T, n_last, dcoeff, ws, ws_bytes, dw, dopacity, dmeans, dscales, dquats,
          dev_status, stream)
+
+
+def lsv2_sparsify(rows, L, K, logits, idx, w, stream):
+    call("lsv2_sparsify", rows, L, K, logits, idx, w, stream)
+
+
+def lsv2_sparsify_backward(rows, L, K, idx, w, dw, dlogits, stream):
+    call("lsv2_sparsify_backward", rows, L, K, idx, w, dw, dlogits, stream)
 
 
 def lsv2_postprocess_workspace_bytes(Q, levels) -> int:

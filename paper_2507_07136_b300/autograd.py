@@ -9,6 +9,10 @@ gradients of the coefficient weights, opacities, means, scales and quaternions.
 
 Inputs are activated values (scales > 0, opacity in (0, 1)); apply exp / sigmoid in torch
 before calling it and autograd chains those derivatives.
+
+``Sparsify.apply`` (or ``sparsify``) turns the per-Gaussian L-dim parameters into the K
+(index, weight) pairs of Sec. 3.3 (softmax, top K, renormalised) through lsv2_sparsify, and its
+backward calls lsv2_sparsify_backward, so logits -> sparsify -> render_l1 trains end to end.
 """
 from __future__ import annotations
 
@@ -61,3 +65,33 @@ def render_l1(means, log_scales, quats, opacity_logits, weights, codebook, idx, 
     """Loss = mean |W S - target| with the activations applied here (exp, sigmoid)."""
     return RenderL1.apply(means, torch.exp(log_scales), quats, torch.sigmoid(opacity_logits), weights, codebook,
                           idx, cam, target, capacity)
+
+
+class Sparsify(torch.autograd.Function):
+    """logits [..., L] -> (weights [..., K] float32, differentiable; idx [..., K] uint8)."""
+
+    @staticmethod
+    def forward(ctx, logits, K):
+        z = logits.detach().contiguous().float()
+        Lz = z.shape[-1]
+        rows = z.numel() // Lz
+        idx = torch.empty(z.shape[:-1] + (K,), dtype=torch.uint8, device=z.device)
+        w = torch.empty(z.shape[:-1] + (K,), dtype=torch.float32, device=z.device)
+        L.lsv2_sparsify(rows, Lz, K, _ptr(z), _ptr(idx), _ptr(w), _stream(None))
+        ctx.save_for_backward(idx, w)
+        ctx.Lz, ctx.K = Lz, K
+        ctx.mark_non_differentiable(idx)
+        return w, idx
+
+    @staticmethod
+    def backward(ctx, gw, gidx):
+        idx, w = ctx.saved_tensors
+        dz = torch.empty(w.shape[:-1] + (ctx.Lz,), dtype=torch.float32, device=w.device)
+        L.lsv2_sparsify_backward(w.numel() // ctx.K, ctx.Lz, ctx.K, _ptr(idx), _ptr(w), _ptr(gw.contiguous().float()),
+                                 _ptr(dz), _stream(None))
+        return dz, None
+
+
+def sparsify(logits, K: int):
+    """Sec. 3.3 sparse coefficients of logits [..., L]: (weights [..., K], idx [..., K] uint8)."""
+    return Sparsify.apply(logits, K)

@@ -1,0 +1,224 @@
+// sparsify.cu -- the sparse coefficients of Sec. 3.3 and their gradient.
+//
+// Every Gaussian carries, per level, an L-dim parameter z: the paper normalises it with a
+// softmax, keeps the K largest values as the nonzeros and renormalises them by their sum.  The
+// kept weights are then a softmax over the K kept logits (the full softmax's denominator cancels),
+// so the forward selects the K largest logits (the softmax is monotone; lower index first among
+// equal logits) and takes the softmax of those, and the gradient is zero for the dropped logits
+// and w_k (dw_k - sum_m w_m dw_m) for kept entry k (the selection is piecewise constant).
+//
+// One row of L logits per thread.  A block stages its rows in shared memory with coalesced
+// asynchronous copies (rows padded by one word: conflict-free per-thread row reads), selects with a descending
+// insertion network in registers, and writes idx (K bytes) and w (K floats) per row; the
+// backward scatters the K gradients into a zeroed staged row and writes the rows out coalesced.
+// Both are HBM-bound: 4 L bytes per row in (forward) or out (backward).
+#include "device.cuh"
+
+namespace lsv2 {
+namespace {
+
+template <int L>
+__host__ __device__ constexpr int rows_per_block() { return L <= 64 ? 128 : 32; }
+
+// row r0 + i of a [rows][L] float array <-> staged row i (stride L + 1).  Loads are asynchronous
+// 4-byte copies, all in flight at once (the padded rows are not 16-byte aligned).
+template <int L, int R>
+__device__ __forceinline__ void stage_in(const float* src, int64_t r0, int nr, float* zs)
+{
+    const float* g = src + r0 * L;
+    for (int i = threadIdx.x; i < nr * L; i += R)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
+                         (uint32_t)__cvta_generic_to_shared(zs + (i / L) * (L + 1) + (i % L))),
+                     "l"(g + i)
+                     : "memory");
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+}
+
+template <int L, int R>
+__device__ __forceinline__ void stage_out(float* dst, int64_t r0, int nr, const float* zs)
+{
+    float* g = dst + r0 * L;
+    for (int i = threadIdx.x; i < nr * L; i += R) g[i] = zs[(i / L) * (L + 1) + (i % L)];
+}
+
+template <int K>
+__device__ __forceinline__ void store_row(uint8_t* idx, float* w, int64_t r, const int (&ix)[K], const float (&wv)[K])
+{
+    if constexpr (K == 4) {
+        reinterpret_cast<uint32_t*>(idx)[r] =
+            (uint32_t)ix[0] | ((uint32_t)ix[1] << 8) | ((uint32_t)ix[2] << 16) | ((uint32_t)ix[3] << 24);
+        reinterpret_cast<float4*>(w)[r] = make_float4(wv[0], wv[1], wv[2], wv[3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            idx[r * K + k] = (uint8_t)ix[k];
+            w[r * K + k] = wv[k];
+        }
+    }
+}
+
+template <int L, int K>
+__global__ void __launch_bounds__(rows_per_block<L>()) sparsify_kernel(int64_t rows, const float* __restrict__ z,
+                                                                       uint8_t* __restrict__ idx, float* __restrict__ w)
+{
+    constexpr int R = rows_per_block<L>();
+    extern __shared__ float zs[];
+    const int64_t r0 = (int64_t)blockIdx.x * R;
+    const int nr = rows - r0 < R ? (int)(rows - r0) : R;
+    stage_in<L, R>(z, r0, nr, zs);
+    __syncthreads();
+    if ((int)threadIdx.x >= nr) return;
+    const float* row = zs + threadIdx.x * (L + 1);
+    // the K largest (value, then lower index) in descending order; slots start empty (index L)
+    float v[K];
+    int ix[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        v[k] = -INFINITY;
+        ix[k] = L;
+    }
+    for (int c = 0; c < L; ++c) {
+        const float x = row[c];
+        bool gt[K];   // (x, c) ranks before slot k: larger value, or equal value in an empty slot
+#pragma unroll
+        for (int k = 0; k < K; ++k) gt[k] = x > v[k] || (x == v[k] && ix[k] == L);
+#pragma unroll
+        for (int k = K - 1; k >= 0; --k) {
+            const bool shift = k > 0 && gt[k - 1];
+            if (shift) {
+                v[k] = v[k - 1];
+                ix[k] = ix[k - 1];
+            } else if (gt[k]) {
+                v[k] = x;
+                ix[k] = c;
+            }
+        }
+    }
+    // softmax over the kept logits (v[0] is the largest)
+    float e[K], s = 0.0f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        e[k] = expf(v[k] - v[0]);
+        s += e[k];
+    }
+    float wv[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) wv[k] = e[k] / s;
+    store_row<K>(idx, w, r0 + threadIdx.x, ix, wv);
+}
+
+template <int L, int K>
+__global__ void __launch_bounds__(rows_per_block<L>()) sparsify_backward_kernel(int64_t rows, const uint8_t* __restrict__ idx,
+                                                                                const float* __restrict__ w,
+                                                                                const float* __restrict__ dw,
+                                                                                float* __restrict__ dz)
+{
+    constexpr int R = rows_per_block<L>();
+    extern __shared__ float zs[];
+    const int64_t r0 = (int64_t)blockIdx.x * R;
+    const int nr = rows - r0 < R ? (int)(rows - r0) : R;
+    for (int i = threadIdx.x; i < R * (L + 1); i += R) zs[i] = 0.0f;
+    __syncthreads();
+    if ((int)threadIdx.x < nr) {
+        const int64_t r = r0 + threadIdx.x;
+        float wv[K], g[K], dot = 0.0f;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            wv[k] = w[r * K + k];
+            g[k] = dw[r * K + k];
+            dot = fmaf(wv[k], g[k], dot);
+        }
+        float* row = zs + threadIdx.x * (L + 1);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int c = idx[r * K + k];
+            if (c < L) row[c] = wv[k] * (g[k] - dot);
+        }
+    }
+    __syncthreads();
+    stage_out<L, R>(dz, r0, nr, zs);
+}
+
+template <int L, int K>
+cudaError_t launch_sparsify_t(int64_t rows, const float* z, uint8_t* idx, float* w, const float* dw, float* dz,
+                              bool backward, cudaStream_t stream)
+{
+    constexpr int R = rows_per_block<L>();
+    const size_t smem = (size_t)R * (L + 1) * sizeof(float);
+    const int64_t blocks = (rows + R - 1) / R;
+    if (blocks == 0) return cudaSuccess;
+    if (backward) {
+        cudaError_t e = cudaFuncSetAttribute(sparsify_backward_kernel<L, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        sparsify_backward_kernel<L, K><<<(unsigned)blocks, R, smem, stream>>>(rows, idx, w, dw, dz);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(sparsify_kernel<L, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        sparsify_kernel<L, K><<<(unsigned)blocks, R, smem, stream>>>(rows, z, idx, w);
+    }
+    return cudaGetLastError();
+}
+
+template <int L>
+cudaError_t launch_sparsify_l(int K, int64_t rows, const float* z, uint8_t* idx, float* w, const float* dw, float* dz,
+                              bool backward, cudaStream_t stream)
+{
+    switch (K) {
+        case 1: return launch_sparsify_t<L, 1>(rows, z, idx, w, dw, dz, backward, stream);
+        case 2: return launch_sparsify_t<L, 2>(rows, z, idx, w, dw, dz, backward, stream);
+        case 4: return launch_sparsify_t<L, 4>(rows, z, idx, w, dw, dz, backward, stream);
+        case 8: return launch_sparsify_t<L, 8>(rows, z, idx, w, dw, dz, backward, stream);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+bool sparsify_supported(int L, int K)
+{
+    const bool l_ok = L == 16 || L == 32 || L == 64 || L == 128 || L == 256;
+    return l_ok && (K == 1 || K == 2 || K == 4 || K == 8) && K <= L;
+}
+
+cudaError_t launch_sparsify(int L, int K, int64_t rows, const float* z, uint8_t* idx, float* w, const float* dw,
+                            float* dz, bool backward, cudaStream_t stream)
+{
+    if (rows > 0 && (!idx || !w || (backward ? (!dw || !dz) : !z))) return cudaErrorInvalidValue;
+    switch (L) {
+        case 16: return launch_sparsify_l<16>(K, rows, z, idx, w, dw, dz, backward, stream);
+        case 32: return launch_sparsify_l<32>(K, rows, z, idx, w, dw, dz, backward, stream);
+        case 64: return launch_sparsify_l<64>(K, rows, z, idx, w, dw, dz, backward, stream);
+        case 128: return launch_sparsify_l<128>(K, rows, z, idx, w, dw, dz, backward, stream);
+        case 256: return launch_sparsify_l<256>(K, rows, z, idx, w, dw, dz, backward, stream);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
+
+}  // namespace
+}  // namespace lsv2
+
+using namespace lsv2;
+
+extern "C" lsv2_status lsv2_sparsify(int64_t rows, int32_t L, int32_t K, const float* logits, uint8_t* idx, float* w,
+                                     void* stream)
+{
+    if (rows < 0 || (rows > 0 && (!logits || !idx || !w))) return LSV2_ERR_INVALID_ARGUMENT;
+    if (!sparsify_supported(L, K)) return LSV2_ERR_UNSUPPORTED;
+    if (!aligned(logits, 4) || !aligned(w, K == 4 ? 16 : 4) || !aligned(idx, K == 4 ? 4 : 1))
+        return LSV2_ERR_INVALID_ARGUMENT;
+    const cudaError_t e = launch_sparsify(L, K, rows, logits, idx, w, nullptr, nullptr, false,
+                                          static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? LSV2_OK : LSV2_ERR_CUDA;
+}
+
+extern "C" lsv2_status lsv2_sparsify_backward(int64_t rows, int32_t L, int32_t K, const uint8_t* idx, const float* w,
+                                              const float* dw, float* dlogits, void* stream)
+{
+    if (rows < 0 || (rows > 0 && (!idx || !w || !dw || !dlogits))) return LSV2_ERR_INVALID_ARGUMENT;
+    if (!sparsify_supported(L, K)) return LSV2_ERR_UNSUPPORTED;
+    if (!aligned(w, 4) || !aligned(dw, 4) || !aligned(dlogits, 4)) return LSV2_ERR_INVALID_ARGUMENT;
+    const cudaError_t e = launch_sparsify(L, K, rows, nullptr, const_cast<uint8_t*>(idx), const_cast<float*>(w), dw,
+                                          dlogits, true, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? LSV2_OK : LSV2_ERR_CUDA;
+}
