@@ -166,8 +166,9 @@ def reference_arm(args):
 def ablation_section(dev, reps: int = 10):
     """The paper's speed ablation on B300 (Table 9 and the K ablation): at 300k Gaussians, three
     levels, 1440x1080, the splat (record packing + blend) with K = 2, 4, 6, 8 nonzeros per level,
-    and the dense blend over all 64 coefficients per level ("Sparse, not Efficient") at K = 4.
-    Same Gaussians for every K; L2 flushed between repetitions."""
+    the dense blend over all 64 coefficients per level ("Sparse, not Efficient") at K = 4, and the
+    splat with codebooks of L = 32, 64, 128 entries at K = 4.  Same Gaussians for every K and L;
+    L2 flushed between repetitions."""
     import torch
     import lsv2_synth as syn
     from paper_2507_07136_b300.pipeline import DeviceScene, Frame
@@ -204,6 +205,17 @@ def ablation_section(dev, reps: int = 10):
         del fr
         torch.cuda.empty_cache()
     out["dense_over_sparse"] = out["dense_ms"] / out["splat_ms"]["4"]
+    # the codebook size at K = 4: the blend's work is the same, the map it writes is L columns wide
+    out["splat_ms_by_L"] = {"64": out["splat_ms"]["4"]}
+    for Lc in (32, 128):
+        sc = syn.make_scene(300_000, 3, L=Lc)
+        fr = Frame(DeviceScene.from_numpy(sc, device=dev), cam, device=dev)
+        fr.render()
+        fr.check()
+        out["splat_ms_by_L"][str(Lc)] = timed(fr.splat)
+        fr.check()
+        del fr
+        torch.cuda.empty_cache()
     out["paper_a100_ms"] = {"dense (Sparse, not Efficient)": 5.3, "sparse (Efficient)": 2.0}
     return out
 

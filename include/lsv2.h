@@ -150,8 +150,9 @@ size_t lsv2_splat_workspace_bytes(int64_t n, int32_t levels, int32_t K);
  *   coeff float[levels][H*W][L]  output coefficient map W (pixel-major, L contiguous)
  *   final_T float[H*W], n_last uint32[H*W]: transmittance after the last contributor and
  *   the list position (+1, relative to the tile start) of that contributor (0: none).
- * Blending is FP32.  Supported: L = 64; levels 1 with K in {2, 4, 6, 8}, levels 2 with K = 4,
- * levels 3 with K = 4 (any tile) or K in {2, 6, 8} (16x16 tiles); tiles 16x16, 8x8, 32x8. */
+ * Blending is FP32.  Supported: L = 64 with levels 1 and K in {2, 4, 6, 8}, levels 2 and K = 4,
+ * levels 3 and K = 4 (any tile) or K in {2, 6, 8} (16x16 tiles); tiles 16x16, 8x8, 32x8.  Also
+ * L in {32, 128} with levels 3, K = 4 and 16x16 tiles (the codebook-size sweep). */
 lsv2_status lsv2_splat_coeffs(const lsv2_camera* cam, int64_t n, const lsv2_proj* proj,
                               const uint32_t* tile_ranges, const uint32_t* gauss_ids,
                               int32_t levels, int32_t K, int32_t L, const uint8_t* idx,

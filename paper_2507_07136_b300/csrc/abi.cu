@@ -138,9 +138,11 @@ lsv2_status lsv2_splat_coeffs(const lsv2_camera* cam, int64_t n, const lsv2_proj
         return LSV2_ERR_INVALID_ARGUMENT;
     PackArgs pa{n, levels, K, splat_record_bytes(levels, K), proj->xy, proj->axes, proj->conic_o, proj->extent, idx,
                 w, static_cast<float*>(workspace), dev_status};
+    pa.L = L;
     cudaError_t e = launch_pack(pa, S(stream));
     if (e != cudaSuccess) return LSV2_ERR_CUDA;
     SplatArgs sa{*cam, tile_ranges, gauss_ids, static_cast<const float*>(workspace), coeff, final_T, n_last, dev_status};
+    sa.L = L;
     return cuda_status(launch_splat(levels, K, sa, S(stream)));
 }
 
@@ -160,10 +162,12 @@ lsv2_status lsv2_splat_coeffs_bf16(const lsv2_camera* cam, int64_t n, const lsv2
         return LSV2_ERR_INVALID_ARGUMENT;
     PackArgs pa{n, levels, K, splat_record_bytes(levels, K), proj->xy, proj->axes, proj->conic_o, proj->extent, idx,
                 w, static_cast<float*>(workspace), dev_status};
+    pa.L = L;
     cudaError_t e = launch_pack(pa, S(stream));
     if (e != cudaSuccess) return LSV2_ERR_CUDA;
     SplatArgs sa{*cam, tile_ranges, gauss_ids, static_cast<const float*>(workspace), static_cast<float*>(coeff_bf16),
                  final_T, n_last, dev_status, 1};
+    sa.L = L;
     return cuda_status(launch_splat(levels, K, sa, S(stream)));
 }
 

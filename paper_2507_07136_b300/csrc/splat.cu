@@ -29,7 +29,7 @@ namespace lsv2 {
 
 // One thread per (view, Gaussian): the record in registers (fully unrolled over the pairs, so no
 // local memory), written with 16-byte stores.
-template <int LEVELS, int K>
+template <int LEVELS, int K, int LW = 64>
 __global__ void __launch_bounds__(256) pack_records_kernel(PackArgs a)
 {
     constexpr int P = LEVELS * K;
@@ -57,10 +57,10 @@ __global__ void __launch_bounds__(256) pack_records_kernel(PackArgs a)
         const int lev = p / K;
         const size_t src = (size_t)g * P + p;
         const int ix = a.idx[src];
-        bad |= ix >= 64;
-        col[p] = lev * 64 + (ix < 64 ? ix : 0);
-        wv[p] = ix < 64 ? a.w[src] : 0.0f;
-        real[p] = ix < 64;
+        bad |= ix >= LW;
+        col[p] = lev * LW + (ix < LW ? ix : 0);
+        wv[p] = ix < LW ? a.w[src] : 0.0f;
+        real[p] = ix < LW;
     }
     if (bad) report(a.status, LSV2_ERR_INVALID_ARGUMENT);
 #pragma unroll
@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(256) pack_records_kernel(PackArgs a)
     // pairs last, so every level's K slots stay contiguous; slot of each pair, then a gather
 #pragma unroll
     for (int lev = 0; lev < LEVELS; ++lev) {
-        int first_col = lev * 64, seen = 0, n_empty = 0;
+        int first_col = lev * LW, seen = 0, n_empty = 0;
 #pragma unroll
         for (int k = K - 1; k >= 0; --k)
             if (real[lev * K + k]) first_col = col[lev * K + k];
@@ -149,10 +149,10 @@ __global__ void __launch_bounds__(256) pack_dense_kernel(PackArgs a)
 
 // One CTA per TW x TH pixel block; SUB blocks stacked vertically share one bin tile of
 // TW x (TH SUB) pixels (and its list), so a bin tile's halves can run as two CTAs per SM.
-template <int LEVELS, int K, int TW, int TH, bool DENSE = false, int SUB = 1>
+template <int LEVELS, int K, int TW, int TH, bool DENSE = false, int SUB = 1, int LW = 64>
 __global__ void __launch_bounds__(TW* TH + 32, 1) splat_kernel(SplatArgs a)
 {
-    using C = SplatCfg<LEVELS, K, TW, TH, 0, DENSE>;
+    using C = SplatCfg<LEVELS, K, TW, TH, 0, DENSE, LW>;
     extern __shared__ __align__(16) unsigned char smem[];
     const SplatSmem<C> sm(smem);
     if (threadIdx.x == 0) {
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(TW* TH + 32, 1) splat_kernel(SplatArgs a)
     TileJob j{a.cam.width, a.cam.height, (tile % GX) * TW, (tile / GX) * (TH * SUB) + sub * TH, a.tile_ranges[2 * tile],
               a.tile_ranges[2 * tile + 1], a.gauss_ids, a.recs, a.coeff, a.final_T, a.n_last, a.status,
               a.coeff_bf16};
-    (void)splat_tile<LEVELS, K, TW, TH, 0, true, DENSE>(j, sm, 0u);
+    (void)splat_tile<LEVELS, K, TW, TH, 0, true, DENSE, LW>(j, sm, 0u);
 }
 
 // Persistent over the (view, tile) work items of several views: each CTA takes the next work
@@ -213,13 +213,13 @@ namespace {
 constexpr int kSub16 = 2;
 
 // Bin tiles of TW x TH pixels, each run as SUB CTAs of TW x (TH / SUB) pixels.
-template <int LEVELS, int K, int TW, int TH, bool DENSE = false, int SUB = 1>
+template <int LEVELS, int K, int TW, int TH, bool DENSE = false, int SUB = 1, int LW = 64>
 cudaError_t launch_t(const SplatArgs& a, cudaStream_t stream)
 {
     constexpr int kTHc = TH / SUB;
-    using C = SplatCfg<LEVELS, K, TW, kTHc, 0, DENSE>;
+    using C = SplatCfg<LEVELS, K, TW, kTHc, 0, DENSE, LW>;
     static_assert(C::kSmemBytes <= 232448, "shared memory budget");
-    auto kern = splat_kernel<LEVELS, K, TW, kTHc, DENSE, SUB>;
+    auto kern = splat_kernel<LEVELS, K, TW, kTHc, DENSE, SUB, LW>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
     if (e != cudaSuccess) return e;
     const int GX = (a.cam.width + TW - 1) / TW, GY = (a.cam.height + TH - 1) / TH;
@@ -281,6 +281,8 @@ cudaError_t launch_tile(const SplatArgs& a, cudaStream_t stream)
 
 bool splat_supported(int levels, int K, int L, int tw, int th)
 {
+    // the L sweep: codebooks of 32 and 128 entries at three levels, K = 4, 16 x 16 tiles
+    if (L == 32 || L == 128) return levels == 3 && K == 4 && tw == 16 && th == 16;
     if (L != 64) return false;
     const bool tile_ok = (tw == 16 && th == 16) || (tw == 8 && th == 8) || (tw == 32 && th == 8);
     if (!tile_ok) return false;
@@ -322,6 +324,12 @@ cudaError_t launch_pack(const PackArgs& a, cudaStream_t stream, int V)
     if (a.n == 0 || V == 0) return cudaSuccess;
     const int threads = 256;
     const dim3 grid((unsigned)((a.n + threads - 1) / threads), (unsigned)V);
+    if (a.L != 64) {   // the L sweep: three levels, K = 4
+        if (a.levels == 3 && a.K == 4 && a.L == 32) pack_records_kernel<3, 4, 32><<<grid, threads, 0, stream>>>(a);
+        else if (a.levels == 3 && a.K == 4 && a.L == 128) pack_records_kernel<3, 4, 128><<<grid, threads, 0, stream>>>(a);
+        else return cudaErrorInvalidValue;
+        return cudaGetLastError();
+    }
     if (a.levels == 3 && a.K == 4) pack_records_kernel<3, 4><<<grid, threads, 0, stream>>>(a);
     else if (a.levels == 3 && a.K == 2) pack_records_kernel<3, 2><<<grid, threads, 0, stream>>>(a);
     else if (a.levels == 3 && a.K == 6) pack_records_kernel<3, 6><<<grid, threads, 0, stream>>>(a);
@@ -355,6 +363,9 @@ cudaError_t launch_splat(int levels, int K, const SplatArgs& a, cudaStream_t str
         }
     }
     if (levels == 2 && K == 4) return launch_tile<2, 4>(a, stream);
+    if (levels == 3 && K == 4 && a.L == 32) return launch_t<3, 4, 16, 16, false, kSub16, 32>(a, stream);
+    if (levels == 3 && K == 4 && a.L == 128) return launch_t<3, 4, 16, 16, false, kSub16, 128>(a, stream);
+    if (a.L != 64) return cudaErrorInvalidValue;
     if (levels == 3 && K == 4) return launch_tile<3, 4>(a, stream);
     if (levels == 3 && a.cam.tile_w == 16 && a.cam.tile_h == 16) {   // K sweep at three levels
         if (K == 2) return launch_t<3, 2, 16, 16>(a, stream);

@@ -31,13 +31,14 @@ __host__ __device__ constexpr int dense_record_bytes(int levels) { return ((48 +
 // 16 for dense records).  DENSE: records carry all 64 coefficients of each level and every
 // contributing Gaussian updates all 64 columns of each level (the blend without the sparse
 // splatting, kept for comparison).
-template <int LEVELS, int K, int TW, int TH, int BATCH = 0, bool DENSE = false>
+template <int LEVELS, int K, int TW, int TH, int BATCH = 0, bool DENSE = false, int LW = 64>
 struct SplatCfg {
     static constexpr int kPixels = TW * TH;
     static constexpr int kWarps = kPixels / 32;      // consumer warps
     static constexpr int kThreads = kPixels + 32;    // + the producer warp
     static constexpr int kPairs = LEVELS * K;        // pairs in a record
-    static constexpr int kCols = LEVELS * 64;
+    static constexpr int kLW = LW;                   // codebook size L: accumulator columns per level
+    static constexpr int kCols = LEVELS * LW;
     static constexpr int kAccFloats = (kCols * 33 + 3) / 4 * 4;
     static constexpr bool kDense = DENSE;
     static constexpr int kRecBytes = DENSE ? dense_record_bytes(LEVELS) : record_bytes(kPairs);
@@ -59,6 +60,8 @@ struct SplatCfg {
     __host__ __device__ static constexpr int lane_y(int warp, int lane) { return (warp / kWarpsX) * kWarpH + lane / kWarpW; }
     static_assert(kPixels % 32 == 0 && TW % 8 == 0 && TH % 4 == 0, "warps cover 8 x 4 blocks of a tile");
     static_assert(kPairs <= kMaxPairs, "pairs per record");
+    static_assert(!DENSE || LW == 64, "dense records carry 64 coefficients per level");
+    static_assert(LW % 8 == 0 && LW <= 256, "codebook size");
     static_assert(kRecBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
     static_assert(kStages >= 2, "at least two stages");
 };
@@ -74,6 +77,7 @@ struct PackArgs {
     const float* w;
     float* recs;
     int32_t* status;
+    int L = 64;                         // codebook size: column of pair (level, index) = level * L + index
 };
 
 struct SplatArgs {
@@ -86,6 +90,7 @@ struct SplatArgs {
     uint32_t* n_last;
     int32_t* status;
     int coeff_bf16 = 0;                 // write the coefficient map rounded to BF16 (nearest even)
+    int L = 64;                         // codebook size (columns per level of the map)
 };
 
 constexpr int kMaxSplatViews = 64;

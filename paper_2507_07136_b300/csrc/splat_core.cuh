@@ -288,36 +288,40 @@ __device__ uint32_t splat_consume(const TileJob& a, const SplatSmem<C>& sm, int 
     }
     __syncwarp();
     if (!kWriteCoeff) return consumed;
-    // write this warp's 32 pixels (each pixel's 64 coefficients of a level are contiguous in HBM)
+    // write this warp's 32 pixels (each pixel's L = C::kLW coefficients of a level are contiguous
+    // in HBM)
+    constexpr int LW = C::kLW;
     const size_t P = (size_t)a.width * a.height;
     if (a.coeff_bf16) {
         __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(a.coeff);
+        constexpr int G8 = LW / 8;   // 8-coefficient groups per pixel
 #pragma unroll 1
         for (int lev = 0; lev < LEVELS; ++lev) {
-            for (int q = lane; q < 32 * 8; q += 32) {
-                const int pl = q >> 3;  // pixel within the warp (its lane)
-                const int c8 = (q & 7) * 8;
+            for (int q = lane; q < 32 * G8; q += 32) {
+                const int pl = q / G8;  // pixel within the warp (its lane)
+                const int c8 = (q % G8) * 8;
                 const int gx = a.x0 + C::lane_x(warp, pl), gy = a.y0 + C::lane_y(warp, pl);
                 if (gx < a.width && gy < a.height) {
-                    const float* col = acc + (lev * 64 + c8) * 33 + pl;
+                    const float* col = acc + (lev * LW + c8) * 33 + pl;
                     const uint4 val = make_uint4(tc::pack_bf16(col[0], col[33]), tc::pack_bf16(col[66], col[99]),
                                                  tc::pack_bf16(col[132], col[165]), tc::pack_bf16(col[198], col[231]));
-                    __stcs(reinterpret_cast<uint4*>(out + ((size_t)lev * P + (size_t)gy * a.width + gx) * 64 + c8), val);
+                    __stcs(reinterpret_cast<uint4*>(out + ((size_t)lev * P + (size_t)gy * a.width + gx) * LW + c8), val);
                 }
             }
         }
         return consumed;
     }
+    constexpr int G4 = LW / 4;       // 4-coefficient groups per pixel
 #pragma unroll 1
     for (int lev = 0; lev < LEVELS; ++lev) {
-        for (int q = lane; q < 32 * 16; q += 32) {
-            const int pl = q >> 4;  // pixel within the warp (its lane)
-            const int c4 = (q & 15) * 4;
+        for (int q = lane; q < 32 * G4; q += 32) {
+            const int pl = q / G4;  // pixel within the warp (its lane)
+            const int c4 = (q % G4) * 4;
             const int gx = a.x0 + C::lane_x(warp, pl), gy = a.y0 + C::lane_y(warp, pl);
             if (gx < a.width && gy < a.height) {
-                const float* col = acc + (lev * 64 + c4) * 33 + pl;
+                const float* col = acc + (lev * LW + c4) * 33 + pl;
                 float4 val = make_float4(col[0], col[33], col[66], col[99]);
-                __stcs(reinterpret_cast<float4*>(a.coeff + ((size_t)lev * P + (size_t)gy * a.width + gx) * 64 + c4), val);
+                __stcs(reinterpret_cast<float4*>(a.coeff + ((size_t)lev * P + (size_t)gy * a.width + gx) * LW + c4), val);
             }
         }
     }
@@ -328,12 +332,12 @@ __device__ uint32_t splat_consume(const TileJob& a, const SplatSmem<C>& sm, int 
 // one).  Precondition: the CTA's barriers are initialised, no tile is in progress and every
 // thread is synchronised.  Returns the number of batches the tile used (the caller adds it to
 // bbase).
-template <int LEVELS, int K, int TW, int TH, int BATCH, bool kWriteCoeff = true, bool DENSE = false>
+template <int LEVELS, int K, int TW, int TH, int BATCH, bool kWriteCoeff = true, bool DENSE = false, int LW = 64>
 __device__ __forceinline__ uint32_t splat_tile(const TileJob& a,
-                                               const SplatSmem<SplatCfg<LEVELS, K, TW, TH, BATCH, DENSE>>& sm,
+                                               const SplatSmem<SplatCfg<LEVELS, K, TW, TH, BATCH, DENSE, LW>>& sm,
                                                uint32_t bbase)
 {
-    using C = SplatCfg<LEVELS, K, TW, TH, BATCH, DENSE>;
+    using C = SplatCfg<LEVELS, K, TW, TH, BATCH, DENSE, LW>;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint32_t consumed = 0;
     if (warp == C::kWarps)

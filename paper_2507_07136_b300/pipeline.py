@@ -47,6 +47,10 @@ class DeviceScene:
         return int(self.idx.shape[2])
 
     @property
+    def L(self) -> int:
+        return int(self.codebook.shape[1])
+
+    @property
     def D(self) -> int:
         return int(self.codebook.shape[2])
 
@@ -92,7 +96,7 @@ class Frame:
         self.bin_ws = torch.empty(self.bin_ws_bytes, dtype=torch.uint8, device=dev)
         self.splat_ws_bytes = L.lsv2_splat_workspace_bytes(n, scene.levels, scene.K)
         self.splat_ws = torch.empty(max(self.splat_ws_bytes, 16), dtype=torch.uint8, device=dev)
-        self.coeff = torch.empty((scene.levels, self.P, L_CODEBOOK), dtype=torch.float32, device=dev)
+        self.coeff = torch.empty((scene.levels, self.P, scene.L), dtype=torch.float32, device=dev)
         self.final_T = torch.empty(self.P, dtype=torch.float32, device=dev)
         self.n_last = torch.empty(self.P, dtype=torch.int32, device=dev)
         self.query_ws = None
@@ -111,7 +115,7 @@ class Frame:
     def splat(self, stream=None):
         s = self.scene
         L.lsv2_splat_coeffs(self.ccam, s.n, self.proj, _ptr(self.tile_ranges), _ptr(self.gauss_ids), s.levels, s.K,
-                            L_CODEBOOK, _ptr(s.idx), _ptr(s.weights), _ptr(self.splat_ws), self.splat_ws_bytes,
+                            s.L, _ptr(s.idx), _ptr(s.weights), _ptr(self.splat_ws), self.splat_ws_bytes,
                             _ptr(self.coeff), _ptr(self.final_T), _ptr(self.n_last), _ptr(self.status),
                             _stream(stream))
 
@@ -125,7 +129,7 @@ class Frame:
         if getattr(self, "dense_ws", None) is None or self.dense_ws.numel() < need:
             self.dense_ws = torch.empty(need, dtype=torch.uint8, device=self.device)
         L.lsv2_splat_coeffs_dense(self.ccam, s.n, self.proj, _ptr(self.tile_ranges), _ptr(self.gauss_ids), s.levels,
-                                  s.K, L_CODEBOOK, _ptr(s.idx), _ptr(s.weights), _ptr(self.dense_ws), need,
+                                  s.K, s.L, _ptr(s.idx), _ptr(s.weights), _ptr(self.dense_ws), need,
                                   _ptr(self.coeff), _ptr(self.final_T), _ptr(self.n_last), _ptr(self.status),
                                   _stream(stream))
 
@@ -142,7 +146,7 @@ class Frame:
             self.fused_ws = torch.empty(need, dtype=torch.uint8, device=self.device)
         rel_dt = L.LSV2_BF16 if (rel is not None and rel.dtype == torch.bfloat16) else L.LSV2_F32
         L.lsv2_render_fused(self.ccam, s.n, self.proj, _ptr(self.tile_ranges), _ptr(self.gauss_ids), s.levels, s.K,
-                            L_CODEBOOK, _ptr(s.idx), _ptr(s.weights), _ptr(s.codebook), s.D, Q, n_neg, _ptr(text),
+                            s.L, _ptr(s.idx), _ptr(s.weights), _ptr(s.codebook), s.D, Q, n_neg, _ptr(text),
                             float(tau), _ptr(self.fused_ws), need, _ptr(feat), _ptr(rel), rel_dt, _ptr(self.final_T),
                             _ptr(self.n_last), _ptr(self.status), _stream(stream))
 
@@ -151,9 +155,9 @@ class Frame:
         decode and relevancy consume)."""
         s = self.scene
         if getattr(self, "coeff16", None) is None:
-            self.coeff16 = torch.empty((s.levels, self.P, L_CODEBOOK), dtype=torch.bfloat16, device=self.device)
+            self.coeff16 = torch.empty((s.levels, self.P, s.L), dtype=torch.bfloat16, device=self.device)
         L.lsv2_splat_coeffs_bf16(self.ccam, s.n, self.proj, _ptr(self.tile_ranges), _ptr(self.gauss_ids), s.levels,
-                                 s.K, L_CODEBOOK, _ptr(s.idx), _ptr(s.weights), _ptr(self.splat_ws),
+                                 s.K, s.L, _ptr(s.idx), _ptr(s.weights), _ptr(self.splat_ws),
                                  self.splat_ws_bytes, _ptr(self.coeff16), _ptr(self.final_T), _ptr(self.n_last),
                                  _ptr(self.status), _stream(stream))
 
@@ -172,18 +176,18 @@ class Frame:
         if tensor_cores and cb_dt == L.LSV2_F32 and out_dt == L.LSV2_F32:
             raise ValueError("the tensor-core decode needs a BF16 codebook or BF16 output")
         W, w_dt = (self.coeff16, L.LSV2_BF16) if from_bf16 else (self.coeff, L.LSV2_F32)
-        L.lsv2_decode(self.scene.levels, self.P, L_CODEBOOK, self.scene.D, _ptr(W), w_dt, _ptr(cb),
+        L.lsv2_decode(self.scene.levels, self.P, self.scene.L, self.scene.D, _ptr(W), w_dt, _ptr(cb),
                       cb_dt, _ptr(out), out_dt, _ptr(self.status), _stream(stream))
 
     def query(self, text: torch.Tensor, out: torch.Tensor, tau: float = 10.0, compute=L.LSV2_F32, stream=None,
               from_bf16: bool = False):
         Q, nt, D = text.shape
-        need = L.lsv2_query_workspace_bytes(self.scene.levels, L_CODEBOOK, Q, nt - 1)
+        need = L.lsv2_query_workspace_bytes(self.scene.levels, self.scene.L, Q, nt - 1)
         if self.query_ws is None or self.query_ws.numel() < need:
             self.query_ws = torch.empty(need, dtype=torch.uint8, device=self.device)
         out_dt = L.LSV2_BF16 if out.dtype == torch.bfloat16 else L.LSV2_F32
         W, w_dt = (self.coeff16, L.LSV2_BF16) if from_bf16 else (self.coeff, L.LSV2_F32)
-        L.lsv2_query(self.scene.levels, self.P, L_CODEBOOK, D, _ptr(W), w_dt, _ptr(self.scene.codebook),
+        L.lsv2_query(self.scene.levels, self.P, self.scene.L, D, _ptr(W), w_dt, _ptr(self.scene.codebook),
                      Q, nt - 1, _ptr(text), float(tau), _ptr(self.query_ws), need, _ptr(out), out_dt, compute,
                      _ptr(self.status), _stream(stream))
 

@@ -71,3 +71,33 @@ def test_dense_unsupported_configurations():
     fr.render()
     with pytest.raises(L.LSV2Error):
         fr.splat_dense()
+
+
+@pytest.mark.parametrize("Lc", [32, 128])
+def test_three_level_codebook_size_sweep_vs_oracle(Lc):
+    """The splat with codebooks of 32 and 128 entries (three levels, K = 4), against the FP64 oracle
+    (coefficient map [levels][P][L]), and the BF16 map equal to the FP32 map rounded."""
+    sc = syn.make_scene(2500, 3, seed=40 + Lc, mean_kind="uniform", mean_param=1.0, log_scale_mu=-3.1,
+                        log_scale_sigma=0.4, L=Lc)
+    cam = syn.orbit_camera(112, 88, 4.0)
+    ref = O.render(sc, cam)
+    _, fr = gpu_frame(sc, cam)
+    assert fr.coeff.shape[2] == Lc
+    px, py = O.all_pixels(cam)
+    check_blend(fr, ref.blend, px, py, cam)
+    fr.splat_bf16()
+    fr.check()
+    assert torch.equal(fr.coeff.to(torch.bfloat16).view(torch.int16), fr.coeff16.view(torch.int16))
+
+
+def test_codebook_size_sweep_at_scale_sampled():
+    """The at-scale frame (300k Gaussians, three levels) with a 128-entry codebook: the map on
+    sampled pixels against the oracle."""
+    sc = syn.make_scene(300_000, 3, L=128)
+    cam = syn.orbit_camera(1440, 1080, 6.0)
+    _, fr = gpu_frame(sc, cam)
+    rng = np.random.default_rng(3)
+    px = rng.integers(0, cam.width, 3000).astype(np.int32)
+    py = rng.integers(0, cam.height, 3000).astype(np.int32)
+    ref = O.render(sc, cam, px=px, py=py)
+    check_blend(fr, ref.blend, px, py, cam)
