@@ -26,6 +26,7 @@ constexpr int kK = 64;
 
 struct QueryTcArgs {
     int Q, n_neg, Qp, npad;        // Qp = Q rounded up to 8; npad = 64 + (1 + n_neg) Qp rounded up to 16
+    int q_off, Q_all;              // this launch's queries are q_off .. q_off + Q - 1 of Q_all
     float tau;
     const void* W;                 // per view v: [levels][P_v][64] at W + seg[v].w_off elements
     int w_bf16;                    // W in BF16 (else FP32)
@@ -366,20 +367,20 @@ __global__ void __launch_bounds__(64 + 128 * NB, 1) query_pipe_kernel(const __gr
         *abort = 0;
     }
     // B^T rows as in query_tc_kernel: S S^T, then the text rows text-major, zero padding
-    const float* Bl = a.Bt + (size_t)lev * (64 + a.Q * per) * kK;
+    const float* Bl = a.Bt + (size_t)lev * (64 + a.Q_all * per) * kK;
     for (int i = tid; i < a.npad * kK; i += (int)blockDim.x) {
         const int n = i >> 6, k = i & 63;
         int src = n < 64 ? n : -1;
         if (n >= 64 && n < 64 + ntp) {
             const int t = (n - 64) / a.Qp, q = (n - 64) % a.Qp;
-            src = q < a.Q ? 64 + q * per + t : -1;
+            src = q < a.Q ? 64 + (a.q_off + q) * per + t : -1;
         }
         const float v = src >= 0 ? Bl[(size_t)src * kK + k] : 0.0f;
         *reinterpret_cast<__nv_bfloat16*>(sB + tc::sw128(n, k)) = __float2bfloat16_rn(v);
     }
     for (int i = tid; i < ntp; i += (int)blockDim.x) {
         const int t = i / a.Qp, q = i % a.Qp;
-        sTn[i] = q < a.Q ? 1.0f / a.tnorm[q * per + t] : 0.0f;
+        sTn[i] = q < a.Q ? 1.0f / a.tnorm[(a.q_off + q) * per + t] : 0.0f;
     }
     tc::fence_proxy_async();
     tc::fence_before();
@@ -494,7 +495,7 @@ __global__ void __launch_bounds__(64 + 128 * NB, 1) query_pipe_kernel(const __gr
                 const float tp[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
                 if (p < Pv) {
                     const size_t stride = (size_t)a.levels * Pv;
-                    const size_t o0 = a.seg[vw].rel_off + (size_t)lev * Pv + p + (size_t)q0 * stride;
+                    const size_t o0 = a.seg[vw].rel_off + (size_t)lev * Pv + p + (size_t)(a.q_off + q0) * stride;
                     const int nq = a.Q - q0 < 8 ? a.Q - q0 : 8;
                     if (a.rel_bf16) {
                         __nv_bfloat16* out = static_cast<__nv_bfloat16*>(a.rel) + o0;
@@ -549,6 +550,8 @@ cudaError_t launch_query_tc_views(int levels, int V, const int64_t* P, int Q, in
     if (npad > 512) return cudaErrorInvalidValue;
     QueryTcArgs a{};
     a.Q = Q;
+    a.q_off = 0;
+    a.Q_all = Q;
     a.n_neg = n_neg;
     a.Qp = pad8(Q);
     a.npad = npad;
@@ -573,23 +576,35 @@ cudaError_t launch_query_tc_views(int levels, int V, const int64_t* P, int Q, in
     a.seg[V] = QuerySeg{0, tiles, w_off, rel_off};
     a.total_tiles = tiles;
     if (tiles == 0) return cudaSuccess;
-    if (w_bf16 && tmem_cols(npad) <= 256) {
-        // pipelined form: W as rows of 64 BF16 over all views and levels
+    // pipelined form (BF16 W): queries in groups whose columns fit a 256-column accumulator
+    int Qg = Q;
+    while (Qg > 8 && tmem_cols(npad_of(Qg, n_neg)) > 256) Qg = (Qg - 1) / 8 * 8;
+    if (w_bf16 && tmem_cols(npad_of(Qg, n_neg)) <= 256) {
+        // W as rows of 64 BF16 over all views and levels
         CUtensorMap tmW;
         if (!encode_tmap_3d(&tmW, W, true, (uint64_t)kK, (uint64_t)(w_off / kK), 1u, (uint32_t)kK, (uint32_t)kM, true))
             return cudaErrorInvalidValue;
-        size_t smem = pipe_smem_bytes(npad, ntp);
-        if (smem < 117760) smem = 117760;   // one CTA per SM: its TMEM allocation never waits
-        if (smem > 232448) return cudaErrorInvalidValue;
-        const int ng = pipe_groups(tmem_cols(npad));
-        auto kern = ng == 3 ? query_pipe_kernel<3> : query_pipe_kernel<2>;
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
         int per_level = num_sms / levels;
         if (per_level < 1) per_level = 1;
         if (per_level > tiles) per_level = (int)tiles;
-        kern<<<dim3(per_level, levels), 64 + 128 * ng, smem, stream>>>(tmW, a);
-        return cudaGetLastError();
+        for (int q0 = 0; q0 < Q; q0 += Qg) {
+            QueryTcArgs g = a;
+            g.q_off = q0;
+            g.Q = Q - q0 < Qg ? Q - q0 : Qg;
+            g.Qp = pad8(g.Q);
+            g.npad = npad_of(g.Q, n_neg);
+            size_t smem = pipe_smem_bytes(g.npad, (1 + n_neg) * g.Qp);
+            if (smem < 117760) smem = 117760;   // one CTA per SM: its TMEM allocation never waits
+            if (smem > 232448) return cudaErrorInvalidValue;
+            const int ng = pipe_groups(tmem_cols(g.npad));
+            auto kern = ng == 3 ? query_pipe_kernel<3> : query_pipe_kernel<2>;
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            kern<<<dim3(per_level, levels), 64 + 128 * ng, smem, stream>>>(tmW, g);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
     }
     // Two CTAs per SM when their TMEM allocations fit (one CTA's MMA and W conversion overlap the
     // other's epilogue); the shared-memory request keeps one more CTA from being resident, so

@@ -94,12 +94,13 @@ def test_decode_from_bf16_map_widths(D, out_dtype, size):
     assert np.all(np.abs(Fb.double().cpu().numpy() - ref) <= bound)
 
 
-@pytest.mark.parametrize("Q,n_neg", [(1, 1), (1, 4), (5, 4), (8, 1), (9, 4), (17, 3), (32, 4)])
+@pytest.mark.parametrize("Q,n_neg", [(1, 1), (1, 4), (5, 4), (8, 1), (9, 4), (17, 3), (32, 4), (40, 4), (64, 4)])
 @pytest.mark.parametrize("out_dtype", [torch.float32, torch.bfloat16])
 @pytest.mark.parametrize("size", [(141, 99), (10, 7)])
 def test_query_from_bf16_map_counts(Q, n_neg, out_dtype, size):
-    """Relevancy from the BF16 map (TMA-fed pipelined kernel, 2 or 4 TMEM accumulators by column
-    count) equals the relevancy from the FP32 map (rounded to BF16 in the kernel) bit for bit:
+    """Relevancy from the BF16 map (TMA-fed pipelined kernel, 3 or 2 TMEM accumulators by column
+    count; 40 and 64 queries run as groups of 32) equals the relevancy from the FP32 map (rounded to
+    BF16 in the kernel) bit for bit:
     query counts ragged against the 8-query chunks, both output types, a ragged frame and one
     smaller than a 128-pixel tile (its rows past a level's end belong to the next level)."""
     sc = syn.make_scene(3000, 3, seed=13, mean_kind="uniform", mean_param=1.0, log_scale_mu=-3.2, log_scale_sigma=0.4)
