@@ -8,10 +8,12 @@
 // and w_k (dw_k - sum_m w_m dw_m) for kept entry k (the selection is piecewise constant).
 //
 // One row of L logits per thread.  A block stages its rows in shared memory with coalesced
-// asynchronous copies (rows padded by one word: conflict-free per-thread row reads), selects with a descending
-// insertion network in registers, and writes idx (K bytes) and w (K floats) per row; the
-// backward scatters the K gradients into a zeroed staged row and writes the rows out coalesced.
-// Both are HBM-bound: 4 L bytes per row in (forward) or out (backward).
+// asynchronous copies (rows padded by one word: conflict-free per-thread row reads).  The forward
+// selects with a sorting network over groups of 8 logits and a bitonic merge into the running K
+// (branch-free; one total order, the larger value and then the lower index, so the selection is
+// unique) and writes idx (K bytes) and w (K floats) per row.  The backward scatters the K
+// gradients into a zeroed staged row and writes the rows out coalesced: it is HBM-bound (4 L
+// bytes per row out); the forward reads as many bytes and is bound by the selection's arithmetic.
 #include "device.cuh"
 
 namespace lsv2 {
@@ -39,6 +41,21 @@ __device__ __forceinline__ void stage_out(float* dst, int64_t r0, int nr, const 
 {
     float* g = dst + r0 * L;
     for (int i = threadIdx.x; i < nr * L; i += R) g[i] = zs[(i / L) * (L + 1) + (i % L)];
+}
+
+// (value a, index ia) ranks before (value b, index ib): the larger value, the lower index on ties
+__device__ __forceinline__ bool ranks_before(float a, int ia, float b, int ib) { return a > b || (a == b && ia < ib); }
+
+// put the pair that ranks first in (a, ia)
+__device__ __forceinline__ void order_pair(float& a, int& ia, float& b, int& ib)
+{
+    const bool sw = ranks_before(b, ib, a, ia);
+    const float tv = sw ? b : a;
+    const int ti = sw ? ib : ia;
+    b = sw ? a : b;
+    ib = sw ? ia : ib;
+    a = tv;
+    ia = ti;
 }
 
 template <int K>
@@ -69,29 +86,43 @@ __global__ void __launch_bounds__(rows_per_block<L>()) sparsify_kernel(int64_t r
     __syncthreads();
     if ((int)threadIdx.x >= nr) return;
     const float* row = zs + threadIdx.x * (L + 1);
-    // the K largest (value, then lower index) in descending order; slots start empty (index L)
+    // the K first entries in the order (larger value, then lower index), branch-free: each group
+    // of 8 logits is sorted by Batcher's 19-comparator network, and its first K are merged into
+    // the running K (the better of v[i] and the group's (K-1-i)th is a bitonic sequence, which
+    // the half-cleaners sort).  One total order throughout, so the selection is unique.
+    constexpr int kNet8[19][2] = {{0, 1}, {2, 3}, {4, 5}, {6, 7}, {0, 2}, {1, 3}, {4, 6}, {5, 7}, {1, 2}, {5, 6},
+                                  {0, 4}, {1, 5}, {2, 6}, {3, 7}, {2, 4}, {3, 5}, {1, 2}, {3, 4}, {5, 6}};
     float v[K];
     int ix[K];
+#pragma unroll 1
+    for (int g = 0; g < L; g += 8) {
+        float gv[8];
+        int gi[8];
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        v[k] = -INFINITY;
-        ix[k] = L;
-    }
-    for (int c = 0; c < L; ++c) {
-        const float x = row[c];
-        bool gt[K];   // (x, c) ranks before slot k: larger value, or equal value in an empty slot
+        for (int j = 0; j < 8; ++j) {
+            gv[j] = row[g + j];
+            gi[j] = g + j;
+        }
 #pragma unroll
-        for (int k = 0; k < K; ++k) gt[k] = x > v[k] || (x == v[k] && ix[k] == L);
+        for (int c = 0; c < 19; ++c) order_pair(gv[kNet8[c][0]], gi[kNet8[c][0]], gv[kNet8[c][1]], gi[kNet8[c][1]]);
+        if (g == 0) {
 #pragma unroll
-        for (int k = K - 1; k >= 0; --k) {
-            const bool shift = k > 0 && gt[k - 1];
-            if (shift) {
-                v[k] = v[k - 1];
-                ix[k] = ix[k - 1];
-            } else if (gt[k]) {
-                v[k] = x;
-                ix[k] = c;
+            for (int k = 0; k < K; ++k) {
+                v[k] = gv[k];
+                ix[k] = gi[k];
             }
+        } else {
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+                const bool take = ranks_before(gv[K - 1 - i], gi[K - 1 - i], v[i], ix[i]);
+                v[i] = take ? gv[K - 1 - i] : v[i];
+                ix[i] = take ? gi[K - 1 - i] : ix[i];
+            }
+#pragma unroll
+            for (int m = K / 2; m > 0; m >>= 1)
+#pragma unroll
+                for (int i = 0; i < K; ++i)
+                    if ((i & m) == 0) order_pair(v[i], ix[i], v[i | m], ix[i | m]);
         }
     }
     // softmax over the kept logits (v[0] is the largest)
