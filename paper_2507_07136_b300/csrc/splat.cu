@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(256) pack_dense_kernel(PackArgs a)
 // One CTA per TW x TH pixel block; SUB blocks stacked vertically share one bin tile of
 // TW x (TH SUB) pixels (and its list), so a bin tile's halves can run as two CTAs per SM.
 template <int LEVELS, int K, int TW, int TH, bool DENSE = false, int SUB = 1, int LW = 64>
-__global__ void __launch_bounds__(TW* TH + 32, 1) splat_kernel(SplatArgs a)
+__global__ void __launch_bounds__(TW* TH + 32, (TW * TH <= 128 && LW <= 64) ? 2 : 1) splat_kernel(SplatArgs a)
 {
     using C = SplatCfg<LEVELS, K, TW, TH, 0, DENSE, LW>;
     extern __shared__ __align__(16) unsigned char smem[];

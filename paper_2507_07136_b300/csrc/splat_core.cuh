@@ -198,8 +198,10 @@ __device__ uint32_t splat_consume(const TileJob& a, const SplatSmem<C>& sm, int 
                     m &= m - 1u;
                 }
                 // (A) alpha_j and 1 - alpha_j of the chunk's records at this pixel: independent
-                // of one another (instruction-level parallelism across the chunk)
+                // of one another (instruction-level parallelism across the chunk); the records'
+                // column offsets are loaded here too, so the accumulation's loads need not wait
                 float al[kChunk], om[kChunk], p2s[kChunk], os[kChunk];
+                uint32_t offs[kChunk][C::kDense ? 1 : C::kPairs];
                 bool high = false;
 #pragma unroll
                 for (int j = 0; j < kChunk; ++j) {
@@ -207,6 +209,22 @@ __device__ uint32_t splat_consume(const TileJob& a, const SplatSmem<C>& sm, int 
                     const float4 g0 = *reinterpret_cast<const float4*>(r);
                     const float4 ax = *reinterpret_cast<const float4*>(r + 4);
                     const float4 axl = *reinterpret_cast<const float4*>(r + 8);
+                    if constexpr (!C::kDense) {
+                        const uint32_t* cw = reinterpret_cast<const uint32_t*>(r + 12 + C::kPairs);
+                        if constexpr (C::kPairs % 4 == 0) {
+#pragma unroll
+                            for (int i = 0; i < C::kPairs / 4; ++i) {
+                                const uint4 v4 = reinterpret_cast<const uint4*>(cw)[i];
+                                offs[j][4 * i] = v4.x;
+                                offs[j][4 * i + 1] = v4.y;
+                                offs[j][4 * i + 2] = v4.z;
+                                offs[j][4 * i + 3] = v4.w;
+                            }
+                        } else {
+#pragma unroll
+                            for (int p = 0; p < C::kPairs; ++p) offs[j][p] = cw[p];
+                        }
+                    }
                     const float p2 = eval_power2(g0, ax, axl, pxf, pyf);
                     float ex2;
                     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(ex2) : "f"(p2));
@@ -259,12 +277,11 @@ __device__ uint32_t splat_consume(const TileJob& a, const SplatSmem<C>& sm, int 
                                 a0[99] = fmaf(al[j], w4.w, a0[99]);
                             }
                         } else {
-                            const uint32_t* cw = reinterpret_cast<const uint32_t*>(r + 12 + C::kPairs);
                             float v[C::kPairs];
                             float* addr[C::kPairs];
 #pragma unroll
                             for (int p = 0; p < C::kPairs; ++p) {
-                                addr[p] = reinterpret_cast<float*>(acc_lane + cw[p]);
+                                addr[p] = reinterpret_cast<float*>(acc_lane + offs[j][p]);
                                 v[p] = *addr[p];
                             }
 #pragma unroll
