@@ -13,8 +13,8 @@
 //     the block's pixels in row-major order) into that memory.
 //  2. The producer warp streams the codebook S_lev^T in 8 KB chunks of 64 rows (the pre-swizzled
 //     BF16 copy) through a 2-slot ring with bulk async copies, and each level's query matrix
-//     [S S^T | S t ...] (text-major rows, as in query_tc.cu); its lane 0 issues the tcgen05.mma:
-//     per level Y = W [S S^T | S t] (M = 128, N = npadq <= 128) into TMEM columns [128, 256), then
+//     [S S^T | S t / |t| ...] (text-major rows, as in query_tc.cu); its lane 0 issues the tcgen05.mma:
+//     per level Y = W [S S^T | S t / |t|] (M = 128, N = npadq <= 128) into TMEM columns [128, 256), then
 //     F chunks of 64 features (M = 128, N = 64, K = 64) into two TMEM buffers [0, 64) and
 //     [64, 128) that alternate, each committed to an mbarrier.
 //  3. The consumer warps run the epilogues in the same order (warp q reads TMEM lanes 32q ..,
@@ -47,9 +47,8 @@ constexpr int kQMaxRows = 128;
 constexpr int kAOff = 0;                                         // A [level] (3 x 16 KB)
 constexpr int kBOff = kAOff + kLev * kATile;                     // B ring (2 x 8 KB)
 constexpr int kQOff = kBOff + kBSlots * kBChunk;                 // one level's query matrix (<= 16 KB)
-constexpr int kTnOff = kQOff + kQMaxRows * 128;                  // reciprocal text norms (<= 128 floats)
 constexpr int kBoxBytes = 16 * 128;                              // F staging box: 16 pixels x 128 bytes
-constexpr int kStgOff = kTnOff + 1024;                           // 4 warps x 2 boxes
+constexpr int kStgOff = kQOff + kQMaxRows * 128;                 // 4 warps x 2 boxes
 constexpr int kBarOff = FC::kAccBytes + 256;                     // fused-phase barriers (after the splat's)
 constexpr uint32_t kTmemCols = 256;                              // F buffers [0, 128), Y [128, 256)
 static_assert(kStgOff + FC::kWarps * 2 * kBoxBytes <= FC::kAccBytes, "fused operands fit in the accumulator memory");
@@ -68,8 +67,7 @@ struct FusedArgs {
     int do_dec;                  // write F (through the tensor map)
     int Q, n_neg, Qp, npadq;     // Q = 0: no query
     float tau;
-    const uint8_t* Bq;           // [levels][npadq rows x 128 B] swizzled BF16 [S S^T | S t] (text-major)
-    const float* rtn;            // [(1 + n_neg) Qp] reciprocal text norms, text-major
+    const uint8_t* Bq;           // [levels][npadq rows x 128 B] swizzled BF16 [S S^T | S t / |t|] (text-major)
     void* rel;                   // [Q][levels][P]
     int rel_bf16;
     int32_t* status;
@@ -170,9 +168,6 @@ __global__ void __launch_bounds__(FC::kThreads, 2) fused_kernel(const __grid_con
             tc::bulk_load(tc::smem_u32(smem + kQOff), a.Bq, qb, tc::smem_u32(&fb->qload));
         }
     }
-    if (do_query)
-        for (int i = tid; i < (1 + a.n_neg) * a.Qp; i += FC::kThreads)
-            reinterpret_cast<float*>(smem + kTnOff)[i] = a.rtn[i];
     tc::fence_proxy_async();
     tc::fence_before();
     __syncthreads();
@@ -271,7 +266,6 @@ __global__ void __launch_bounds__(FC::kThreads, 2) fused_kernel(const __grid_con
         const int gx = x0 + (row & 15), gy = y0 + (row >> 4);
         const bool in = gx < a.width && gy < a.height;
         const size_t pix = (size_t)gy * a.width + gx;
-        const float* rtn = reinterpret_cast<const float*>(smem + kTnOff);
         const int per = 1 + a.n_neg;
         uint8_t* box = smem + kStgOff + (size_t)(q4 * 2 + (lane >> 4)) * kBoxBytes;   // this lane's image row
         const int br = lane & 15;                                                       // its row in the box
@@ -298,12 +292,12 @@ __global__ void __launch_bounds__(FC::kThreads, 2) fused_kernel(const __grid_con
                     tc::tmem_ld8(lrow + 128u + (uint32_t)(64 + q0), rp);
                     float best[8];
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) best[e] = -INFINITY;
+                    for (int e = 0; e < 8; ++e) best[e] = per > 1 ? -INFINITY : 0.0f;
                     for (int t = 1; t < per; ++t) {
                         tc::tmem_ld8(lrow + 128u + (uint32_t)(64 + t * a.Qp + q0), rn);
                         tc::tmem_wait_ld();
 #pragma unroll
-                        for (int e = 0; e < 8; ++e) best[e] = fmaxf(best[e], __uint_as_float(rn[e]) * rtn[t * a.Qp + q0 + e]);
+                        for (int e = 0; e < 8; ++e) best[e] = fmaxf(best[e], __uint_as_float(rn[e]));
                     }
                     tc::tmem_wait_ld();
                     if (in) {
@@ -311,7 +305,7 @@ __global__ void __launch_bounds__(FC::kThreads, 2) fused_kernel(const __grid_con
                         for (int e = 0; e < 8; ++e) {
                             const int q = q0 + e;
                             if (q < a.Q) {
-                                const float d = __uint_as_float(rp[e]) * rtn[q0 + e] - best[e];
+                                const float d = __uint_as_float(rp[e]) - best[e];
                                 const size_t o = ((size_t)q * kLev + l) * P + pix;
                                 if (a.rel_bf16) {
                                     // as the tensor-core relevancy: sigmoid through the hardware tanh
@@ -388,9 +382,9 @@ __global__ void __launch_bounds__(FC::kThreads, 2) fused_kernel(const __grid_con
 }
 
 // Operands of the fused kernel: the codebook S^T of every level as swizzled BF16 chunks of 64
-// rows, and (with queries) the text-major [S S^T | S t] rows and reciprocal text norms.
+// rows, and (with queries) the text-major [S S^T | S t / |t|] rows.
 __global__ void fused_prep_kernel(int levels, int D, const float* S, int Q, int n_neg, int Qp, int npadq,
-                                  const float* Bt, const float* tnorm, uint8_t* Bdec, uint8_t* Bq, float* rtn)
+                                  const float* Bt, const float* tnorm, uint8_t* Bdec, uint8_t* Bq)
 {
     const int l = blockIdx.y;
     const int per = 1 + n_neg;
@@ -404,19 +398,16 @@ __global__ void fused_prep_kernel(int levels, int D, const float* S, int Q, int 
         } else {
             const int i2 = i - n_dec, n = i2 >> 6, k = i2 & 63;
             int src = n < 64 ? n : -1;
+            float scale = 1.0f;   // text rows S t / |t|, as the split relevancy
             if (n >= 64 && n < 64 + per * Qp) {
                 const int t = (n - 64) / Qp, q = (n - 64) % Qp;
                 src = q < Q ? 64 + q * per + t : -1;
+                if (q < Q) scale = 1.0f / tnorm[q * per + t];
             }
-            const float v = src >= 0 ? Bt[((size_t)l * (64 + Q * per) + src) * 64 + k] : 0.0f;
+            const float v = src >= 0 ? Bt[((size_t)l * (64 + Q * per) + src) * 64 + k] * scale : 0.0f;
             *reinterpret_cast<__nv_bfloat16*>(Bq + (size_t)l * npadq * 128 + tc::sw128(n, k)) = __float2bfloat16_rn(v);
         }
     }
-    if (Q > 0 && l == 0 && blockIdx.x == 0)
-        for (int i = threadIdx.x; i < per * Qp; i += blockDim.x) {
-            const int t = i / Qp, q = i % Qp;
-            rtn[i] = q < Q ? 1.0f / tnorm[q * per + t] : 0.0f;
-        }
 }
 
 int pad8(int q) { return (q + 7) / 8 * 8; }
@@ -424,7 +415,7 @@ int npadq_of(int Q, int n_neg) { return Q > 0 ? (64 + (1 + n_neg) * pad8(Q) + 15
 size_t a256(size_t b) { return (b + 255) / 256 * 256; }
 
 struct FusedLayout {
-    size_t recs, bdec, qws, bq, rtn, bytes;
+    size_t recs, bdec, qws, bq, bytes;
 };
 
 FusedLayout fused_layout(int64_t n, int levels, int K, int D, int Q, int n_neg)
@@ -441,7 +432,6 @@ FusedLayout fused_layout(int64_t n, int levels, int K, int D, int Q, int n_neg)
     const int nt = Q * (1 + n_neg);
     L.qws = take(Q > 0 ? query_workspace_bytes(levels, nt) : 0);
     L.bq = take((size_t)levels * npadq_of(Q, n_neg) * 128);
-    L.rtn = take((size_t)(1 + n_neg) * pad8(Q) * 4);
     L.bytes = o;
     return L;
 }
@@ -482,8 +472,7 @@ cudaError_t launch_fused(const lsv2_camera& cam, int64_t n, const lsv2_proj& pro
                                                           Q > 0 ? query_ws_bt(base + Lo.qws) : nullptr,
                                                           Q > 0 ? query_ws_tnorm(base + Lo.qws, kLev, nt) : nullptr,
                                                           reinterpret_cast<uint8_t*>(base + Lo.bdec),
-                                                          reinterpret_cast<uint8_t*>(base + Lo.bq),
-                                                          reinterpret_cast<float*>(base + Lo.rtn));
+                                                          reinterpret_cast<uint8_t*>(base + Lo.bq));
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int GX = (cam.width + kTW - 1) / kTW, GY = (cam.height + kTH - 1) / kTH;
@@ -515,7 +504,6 @@ cudaError_t launch_fused(const lsv2_camera& cam, int64_t n, const lsv2_proj& pro
     a.npadq = npadq;
     a.tau = tau;
     a.Bq = reinterpret_cast<const uint8_t*>(base + Lo.bq);
-    a.rtn = reinterpret_cast<const float*>(base + Lo.rtn);
     a.rel = rel;
     a.rel_bf16 = rel_bf16 ? 1 : 0;
     a.status = status;

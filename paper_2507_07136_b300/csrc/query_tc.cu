@@ -323,6 +323,15 @@ __device__ __forceinline__ bool pipe_wait(uint32_t bar, uint32_t parity, volatil
 
 // NB: epilogue warpgroups = TMEM accumulators (a template parameter, so that the per-tile ring
 // and phase arithmetic divides by constants).
+// BF16 relevancy from hk = tau / (2 |F|) and d = cos_pos - max cos_neg (in units of |F|): the
+// sigmoid through the hardware tanh, 1/2 + tanh(hk d) / 2
+__device__ __forceinline__ __nv_bfloat16 rel_bf16_of(float hk, float d)
+{
+    float th;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(th) : "f"(hk * d));
+    return __float2bfloat16_rn(fmaf(0.5f, th, 0.5f));
+}
+
 template <int NB>
 __global__ void __launch_bounds__(64 + 128 * NB, 1) query_pipe_kernel(const __grid_constant__ CUtensorMap tmW, QueryTcArgs a)
 {
@@ -366,21 +375,20 @@ __global__ void __launch_bounds__(64 + 128 * NB, 1) query_pipe_kernel(const __gr
         }
         *abort = 0;
     }
-    // B^T rows as in query_tc_kernel: S S^T, then the text rows text-major, zero padding
+    // B^T rows: S S^T, then the text rows S t / |t| text-major (the cosine's text norm folded in
+    // before the BF16 rounding, so the products are <F, t> / |t|), zero padding
     const float* Bl = a.Bt + (size_t)lev * (64 + a.Q_all * per) * kK;
     for (int i = tid; i < a.npad * kK; i += (int)blockDim.x) {
         const int n = i >> 6, k = i & 63;
         int src = n < 64 ? n : -1;
+        float scale = 1.0f;
         if (n >= 64 && n < 64 + ntp) {
             const int t = (n - 64) / a.Qp, q = (n - 64) % a.Qp;
             src = q < a.Q ? 64 + (a.q_off + q) * per + t : -1;
+            if (q < a.Q) scale = 1.0f / a.tnorm[(a.q_off + q) * per + t];
         }
-        const float v = src >= 0 ? Bl[(size_t)src * kK + k] : 0.0f;
+        const float v = src >= 0 ? Bl[(size_t)src * kK + k] * scale : 0.0f;
         *reinterpret_cast<__nv_bfloat16*>(sB + tc::sw128(n, k)) = __float2bfloat16_rn(v);
-    }
-    for (int i = tid; i < ntp; i += (int)blockDim.x) {
-        const int t = i / a.Qp, q = i % a.Qp;
-        sTn[i] = q < a.Q ? 1.0f / a.tnorm[(a.q_off + q) * per + t] : 0.0f;
     }
     tc::fence_proxy_async();
     tc::fence_before();
@@ -471,17 +479,15 @@ __global__ void __launch_bounds__(64 + 128 * NB, 1) query_pipe_kernel(const __gr
                 const int q0 = c * 8;
                 uint32_t rp[8], rn[8];
                 tc::tmem_ld8(trow + (uint32_t)(64 + q0), rp);
+                // best[j] = max over the negatives of <F, t_neg> / |t_neg| (0 with none)
                 float best[8];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) best[j] = -INFINITY;
+                for (int j = 0; j < 8; ++j) best[j] = per > 1 ? -INFINITY : 0.0f;
                 for (int t = 1; t < per; ++t) {
                     tc::tmem_ld8(trow + (uint32_t)(64 + t * a.Qp + q0), rn);
                     tc::tmem_wait_ld();
-                    const float4 u0 = *reinterpret_cast<const float4*>(sTn + t * a.Qp + q0);
-                    const float4 u1 = *reinterpret_cast<const float4*>(sTn + t * a.Qp + q0 + 4);
-                    const float tn[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) best[j] = fmaxf(best[j], __uint_as_float(rn[j]) * tn[j]);
+                    for (int j = 0; j < 8; ++j) best[j] = fmaxf(best[j], __uint_as_float(rn[j]));
                 }
                 tc::tmem_wait_ld();
                 if (c == nch - 1) {
@@ -490,31 +496,29 @@ __global__ void __launch_bounds__(64 + 128 * NB, 1) query_pipe_kernel(const __gr
                     __syncwarp();
                     if (lane == 0) tc::mbar_arrive(tc::smem_u32(t_empty + b));
                 }
-                const float4 u0 = *reinterpret_cast<const float4*>(sTn + q0);
-                const float4 u1 = *reinterpret_cast<const float4*>(sTn + q0 + 4);
-                const float tp[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
                 if (p < Pv) {
                     const size_t stride = (size_t)a.levels * Pv;
                     const size_t o0 = a.seg[vw].rel_off + (size_t)lev * Pv + p + (size_t)(a.q_off + q0) * stride;
                     const int nq = a.Q - q0 < 8 ? a.Q - q0 : 8;
+                    float d[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) d[j] = __uint_as_float(rp[j]) - best[j];
                     if (a.rel_bf16) {
                         __nv_bfloat16* out = static_cast<__nv_bfloat16*>(a.rel) + o0;
                         const float hk = -0.5f * kneg;
+                        if (nq == 8) {
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            if (j >= nq) break;
-                            const float d = __uint_as_float(rp[j]) * tp[j] - (per > 1 ? best[j] : 0.0f);
-                            float th;
-                            asm("tanh.approx.f32 %0, %1;" : "=f"(th) : "f"(hk * d));
-                            out[(size_t)j * stride] = __float2bfloat16_rn(fmaf(0.5f, th, 0.5f));
+                            for (int j = 0; j < 8; ++j, out += stride) *out = rel_bf16_of(hk, d[j]);
+                        } else {
+                            for (int j = 0; j < nq; ++j, out += stride) *out = rel_bf16_of(hk, d[j]);
                         }
                     } else {
                         float* out = static_cast<float*>(a.rel) + o0;
+                        if (nq == 8) {
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            if (j >= nq) break;
-                            const float d = __uint_as_float(rp[j]) * tp[j] - (per > 1 ? best[j] : 0.0f);
-                            out[(size_t)j * stride] = __fdividef(1.0f, 1.0f + __expf(kneg * d));
+                            for (int j = 0; j < 8; ++j, out += stride) *out = __fdividef(1.0f, 1.0f + __expf(kneg * d[j]));
+                        } else {
+                            for (int j = 0; j < nq; ++j, out += stride) *out = __fdividef(1.0f, 1.0f + __expf(kneg * d[j]));
                         }
                     }
                 }
