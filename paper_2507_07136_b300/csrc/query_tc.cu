@@ -483,13 +483,25 @@ __global__ void __launch_bounds__(64 + 128 * NB, 1) query_pipe_kernel(const __gr
                 float best[8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) best[j] = per > 1 ? -INFINITY : 0.0f;
-                for (int t = 1; t < per; ++t) {
-                    tc::tmem_ld8(trow + (uint32_t)(64 + t * a.Qp + q0), rn);
+                if (per == 5) {
+                    // four negatives: their loads behind one wait
+                    uint32_t r4[4][8];
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) tc::tmem_ld8(trow + (uint32_t)(64 + (t + 1) * a.Qp + q0), r4[t]);
                     tc::tmem_wait_ld();
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) best[j] = fmaxf(best[j], __uint_as_float(rn[j]));
+                    for (int t = 0; t < 4; ++t)
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) best[j] = fmaxf(best[j], __uint_as_float(r4[t][j]));
+                } else {
+                    for (int t = 1; t < per; ++t) {
+                        tc::tmem_ld8(trow + (uint32_t)(64 + t * a.Qp + q0), rn);
+                        tc::tmem_wait_ld();
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) best[j] = fmaxf(best[j], __uint_as_float(rn[j]));
+                    }
+                    tc::tmem_wait_ld();
                 }
-                tc::tmem_wait_ld();
                 if (c == nch - 1) {
                     // the last TMEM load of this tile is done: release the accumulator
                     tc::fence_before();
