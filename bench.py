@@ -45,9 +45,9 @@ SPLAT_KERNEL = "splat_kernel<3,4,16,8> (two CTAs per 16x16 tile)"
 # removed when its kernel changes): the splat and the relevancy as launched here; the decode
 # captured over one level (one third of the launch's pixels and bytes) and scaled by 3.
 TRAFFIC = {
-    SPLAT_KERNEL: 47581952 + 550764544,
+    SPLAT_KERNEL: 47622912 + 550734592,
     "decode_tc_kernel": 3 * (199166976 + 1532453376),
-    "query_pipe_kernel<3>": 597312000 + 18906368,
+    "query_pipe_kernel<3>": 597294848 + 18970880,
 }
 
 
