@@ -75,14 +75,11 @@ __global__ void __launch_bounds__(256) pack_records_kernel(PackArgs a)
         wv[p] = merged ? 0.0f : wv[p];
         real[p] = real[p] && !merged;
     }
-    // within each level: emptied pairs first (pointing at the level's first real column), real
-    // pairs last, so every level's K slots stay contiguous; slot of each pair, then a gather
+    // within each level: emptied pairs first (pointing at the dummy column), real pairs last;
+    // slot of each pair, then a gather
 #pragma unroll
     for (int lev = 0; lev < LEVELS; ++lev) {
-        int first_col = lev * LW, seen = 0, n_empty = 0;
-#pragma unroll
-        for (int k = K - 1; k >= 0; --k)
-            if (real[lev * K + k]) first_col = col[lev * K + k];
+        int seen = 0, n_empty = 0;
 #pragma unroll
         for (int k = 0; k < K; ++k) n_empty += real[lev * K + k] ? 0 : 1;
         int slot[K];
@@ -103,7 +100,7 @@ __global__ void __launch_bounds__(256) pack_records_kernel(PackArgs a)
                 const bool hit = slot[k] == s2;
                 const bool rk = real[lev * K + k];
                 wsel = hit ? (rk ? wv[lev * K + k] : 0.0f) : wsel;
-                csel = hit ? (uint32_t)(rk ? col[lev * K + k] : first_col) * 132u : csel;
+                csel = hit ? (uint32_t)(rk ? col[lev * K + k] : LEVELS * LW) * 132u : csel;
             }
             r[12 + lev * K + s2] = wsel;
             r[12 + P + lev * K + s2] = __uint_as_float(csel);
@@ -170,6 +167,38 @@ __global__ void __launch_bounds__(TW* TH + 32, (TW * TH <= 128 && LW <= 64) ? 2 
     (void)splat_tile<LEVELS, K, TW, TH, 0, true, DENSE, LW>(j, sm, 0u);
 }
 
+// One CTA per 16 x 16 tile with eight consumer warps, the last four accumulating in TMEM (256
+// columns per CTA, two CTAs per SM: the whole of the SM's TMEM), so an SM runs 16 consumer warps
+// where shared memory alone holds the accumulators of 8.
+constexpr uint32_t kSplatTmemCols = 256;
+
+template <int LEVELS, int K>
+__global__ void __launch_bounds__(16 * 16 + 32, 2) splat_tm_kernel(SplatArgs a)
+{
+    using C = SplatCfg<LEVELS, K, 16, 16, 0, false, 64, 4>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const SplatSmem<C> sm(smem);
+    if (threadIdx.x == 0) {
+        sm.init();
+        *sm.skip = a.status && *reinterpret_cast<volatile int32_t*>(a.status) == LSV2_ERR_TIMEOUT;
+    }
+    __syncthreads();
+    if (*sm.skip) return;
+    const int warp = threadIdx.x >> 5;
+    if (warp == C::kSmemAccWarps) tc::tmem_alloc(tc::smem_u32(sm.tmem_slot), kSplatTmemCols);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const int tile = blockIdx.x;
+    const int GX = (a.cam.width + 15) / 16;
+    TileJob j{a.cam.width, a.cam.height, (tile % GX) * 16, (tile / GX) * 16, a.tile_ranges[2 * tile],
+              a.tile_ranges[2 * tile + 1], a.gauss_ids, a.recs, a.coeff, a.final_T, a.n_last, a.status,
+              a.coeff_bf16};
+    (void)splat_tile_tm<C, LEVELS, K>(j, sm, 0u);
+    // every TMEM access of the tile completed before splat_tile_tm's barrier
+    if (warp == C::kSmemAccWarps) tc::tmem_dealloc(*sm.tmem_slot, kSplatTmemCols);
+}
+
 // Persistent over the (view, tile) work items of several views: each CTA takes the next work
 // item from an atomic counter (largest views first, as they come first in the numbering); a
 // TW x (TH SUB) bin tile is SUB items of TW x TH pixels.
@@ -225,6 +254,21 @@ cudaError_t launch_t(const SplatArgs& a, cudaStream_t stream)
     const int GX = (a.cam.width + TW - 1) / TW, GY = (a.cam.height + TH - 1) / TH;
     if (GX * GY == 0) return cudaSuccess;
     kern<<<GX * GY * SUB, C::kThreads, C::kSmemBytes, stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <int LEVELS, int K>
+cudaError_t launch_tm(const SplatArgs& a, cudaStream_t stream)
+{
+    using C = SplatCfg<LEVELS, K, 16, 16, 0, false, 64, 4>;
+    // exactly two CTAs per SM: their TMEM allocations fill the SM's 512 columns
+    static_assert(2 * (C::kSmemBytes + 1024) <= 233472 && 3 * (C::kSmemBytes + 1024) > 233472, "two CTAs per SM");
+    auto kern = splat_tm_kernel<LEVELS, K>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
+    if (e != cudaSuccess) return e;
+    const int GX = (a.cam.width + 15) / 16, GY = (a.cam.height + 15) / 16;
+    if (GX * GY == 0) return cudaSuccess;
+    kern<<<GX * GY, C::kThreads, C::kSmemBytes, stream>>>(a);
     return cudaGetLastError();
 }
 
@@ -366,7 +410,10 @@ cudaError_t launch_splat(int levels, int K, const SplatArgs& a, cudaStream_t str
     if (levels == 3 && K == 4 && a.L == 32) return launch_t<3, 4, 16, 16, false, kSub16, 32>(a, stream);
     if (levels == 3 && K == 4 && a.L == 128) return launch_t<3, 4, 16, 16, false, kSub16, 128>(a, stream);
     if (a.L != 64) return cudaErrorInvalidValue;
-    if (levels == 3 && K == 4) return launch_tile<3, 4>(a, stream);
+    if (levels == 3 && K == 4) {
+        if (a.cam.tile_w == 16 && a.cam.tile_h == 16) return launch_tm<3, 4>(a, stream);
+        return launch_tile<3, 4>(a, stream);
+    }
     if (levels == 3 && a.cam.tile_w == 16 && a.cam.tile_h == 16) {   // K sweep at three levels
         if (K == 2) return launch_t<3, 2, 16, 16>(a, stream);
         if (K == 6) return launch_t<3, 6, 16, 16>(a, stream);

@@ -13,12 +13,13 @@ constexpr int kMaxPairs = 24;  // levels * K
 //   floats [8, 12)    c_lo, s_lo, kappa, opacity
 //   floats [12, 12+P) weights
 //   words [12+P, 12+2P) byte offset of each pair's accumulator column in the splat's shared
-//                     memory: (lev * 64 + idx) * 33 * 4 (a column spans 33 floats)
+//                     memory: (lev * L + idx) * 33 * 4 (a column spans 33 floats); the
+//                     accumulator column is offset / 132
 //   last 16 bytes     culling half-extents (ex, ey, 0, 0)
-// Repeated indices of one level are merged into one pair; the emptied repeats (weight 0, same
-// column) and any invalid index (weight 0) are placed FIRST, so when a record's pairs are
-// loaded together and then stored in order, the pair carrying the weight is stored last and
-// wins.
+// Repeated indices of one level are merged into one pair; the emptied repeats and any invalid
+// index (weight 0) point at the dummy column levels * L, which is accumulated but never
+// written out.  So no two pairs of a record that carry weight share a column, and a record's
+// pairs can all be loaded before any is stored, whatever order the stores land in.
 __host__ __device__ constexpr int smem_record_bytes(int P) { return ((48 + 8 * P) + 15) / 16 * 16; }
 __host__ __device__ constexpr int record_bytes(int P) { return smem_record_bytes(P) + 16; }
 // Dense record (the non-sparse baseline: every level's 64 coefficients, zeros included):
@@ -31,7 +32,10 @@ __host__ __device__ constexpr int dense_record_bytes(int levels) { return ((48 +
 // 16 for dense records).  DENSE: records carry all 64 coefficients of each level and every
 // contributing Gaussian updates all 64 columns of each level (the blend without the sparse
 // splatting, kept for comparison).
-template <int LEVELS, int K, int TW, int TH, int BATCH = 0, bool DENSE = false, int LW = 64>
+// TM: the last TM consumer warps keep their accumulators in tensor memory (TMEM) instead of
+// shared memory (0 or 4, with 8 consumer warps): shared memory then holds the accumulators of
+// only kWarps - TM warps, so a 16 x 16 tile of 8 consumer warps still fits twice per SM.
+template <int LEVELS, int K, int TW, int TH, int BATCH = 0, bool DENSE = false, int LW = 64, int TM = 0>
 struct SplatCfg {
     static constexpr int kPixels = TW * TH;
     static constexpr int kWarps = kPixels / 32;      // consumer warps
@@ -39,18 +43,21 @@ struct SplatCfg {
     static constexpr int kPairs = LEVELS * K;        // pairs in a record
     static constexpr int kLW = LW;                   // codebook size L: accumulator columns per level
     static constexpr int kCols = LEVELS * LW;
-    static constexpr int kAccFloats = (kCols * 33 + 3) / 4 * 4;
+    static constexpr int kAccFloats = ((kCols + 1) * 33 + 3) / 4 * 4;   // + the dummy column
+    static constexpr int kTmemWarps = TM;
+    static constexpr int kSmemAccWarps = kWarps - TM;
     static constexpr bool kDense = DENSE;
     static constexpr int kRecBytes = DENSE ? dense_record_bytes(LEVELS) : record_bytes(kPairs);
     static constexpr int kRecFloats = kRecBytes / 4;
     static constexpr int kBatch = BATCH != 0 ? BATCH : (DENSE ? 16 : 32);
-    static constexpr int kAccBytes = kWarps * kAccFloats * 4;
+    static constexpr int kAccBytes = kSmemAccWarps * kAccFloats * 4;
     static constexpr int kStageBytes = kBatch * (kRecBytes + 16);   // records + culling boxes
     static constexpr int kFixedBytes = kAccBytes + 512;             // + barriers and flags
     static constexpr int kStagesFit = (232448 - 64 - kFixedBytes) / kStageBytes;
     // 8 consumer warps: as many stages as fit (one CTA per SM); 4 warps: 2 stages, so two CTAs
     // share an SM; fewer warps: 4 stages
-    static constexpr int kStages = kWarps >= 8 ? (kStagesFit < 8 ? kStagesFit : 8) : (kWarps >= 4 ? 2 : 4);
+    static constexpr int kStages =
+        TM > 0 ? 2 : (kWarps >= 8 ? (kStagesFit < 8 ? kStagesFit : 8) : (kWarps >= 4 ? 2 : 4));
     static constexpr int kSmemBytes = kFixedBytes + kStages * kStageBytes;
     // lane -> pixel: each consumer warp covers an 8 x 4 block of the TW x TH block (warps in
     // row-major order).  A square-ish block keeps more of a warp's lanes inside the footprints
@@ -64,6 +71,8 @@ struct SplatCfg {
     static_assert(LW % 8 == 0 && LW <= 256, "codebook size");
     static_assert(kRecBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
     static_assert(kStages >= 2, "at least two stages");
+    static_assert(TM == 0 || (TM == 4 && kWarps == 8 && !DENSE && kCols + 1 <= 256),
+                  "TMEM accumulators: warps 4-7 of 8, one lane quarter each, at most 256 columns");
 };
 
 struct PackArgs {

@@ -39,6 +39,7 @@ struct SplatSmem {
     int* abort;        // a wait of this CTA ran out: every later wait gives up at once
     uint32_t* issued;  // batches the producer issued for the current tile
     int* skip;         // a wait ran out somewhere (status word): skip the remaining tiles
+    uint32_t* tmem_slot;   // TMEM base address of the CTA's allocation (TMEM accumulators)
     unsigned char* stages;
     __device__ explicit SplatSmem(unsigned char* base)
         : acc(reinterpret_cast<float*>(base)),
@@ -48,6 +49,7 @@ struct SplatSmem {
           abort(reinterpret_cast<int*>(base + C::kAccBytes + 132)),
           issued(reinterpret_cast<uint32_t*>(base + C::kAccBytes + 136)),
           skip(reinterpret_cast<int*>(base + C::kAccBytes + 140)),
+          tmem_slot(reinterpret_cast<uint32_t*>(base + C::kAccBytes + 144)),
           stages(base + C::kFixedBytes)
     {
     }
@@ -70,6 +72,15 @@ struct SplatSmem {
 };
 
 constexpr int kWaitDone = 1, kWaitStopped = 0, kWaitTimeout = -1, kWaitAborted = -2;
+
+// A pair's accumulator reference: the record's shared-memory byte offset (col * 132), or with
+// TMEM accumulators the column col = (offset / 4) / 33, as (x * 1986) >> 16, exact for x = 33 col
+// with col < 32768.
+template <bool kTM>
+__device__ __forceinline__ uint32_t acc_ref(uint32_t off)
+{
+    return kTM ? ((off >> 2) * 1986u) >> 16 : off;
+}
 
 // Warp-uniform bounded wait for a barrier phase.  `done_warps` (optional) ends the wait early
 // once all_done consumer warps have finished; a wait that runs out raises the CTA's abort flag
@@ -139,14 +150,18 @@ __device__ void splat_produce(const TileJob& a, const SplatSmem<C>& sm, int lane
 
 // Consumer warp: 32 pixels (one per lane), front to back over the tile's batches.
 // kWriteCoeff: write the warp's coefficients to a.coeff at the end (false: they stay in the
-// warp's shared-memory columns for a fused consumer).
-template <class C, int LEVELS, int K, int TW, int TH, bool kWriteCoeff = true>
+// warp's shared-memory columns for a fused consumer).  kTM: the accumulators are TMEM columns
+// of this warp's lane quarter (lane = pixel, column = accumulator column) instead of
+// shared-memory columns; the arithmetic and its order are the same.
+template <class C, int LEVELS, int K, int TW, int TH, bool kWriteCoeff = true, bool kTM = false>
 __device__ uint32_t splat_consume(const TileJob& a, const SplatSmem<C>& sm, int warp, int lane, uint32_t bbase)
 {
     constexpr int kB = C::kBatch;
     constexpr int kChunk = 4;   // kept records evaluated together
-    float* acc = sm.acc + warp * C::kAccFloats;
+    static_assert(!kTM || (C::kLW == 64 && !C::kDense && C::kPairs == 12 && kWriteCoeff), "TMEM accumulators");
+    float* acc = sm.acc + (kTM ? 0 : warp) * C::kAccFloats;
     unsigned char* acc_lane = reinterpret_cast<unsigned char*>(acc + lane);
+    const uint32_t tbase = kTM ? *sm.tmem_slot + ((uint32_t)(32 * (warp & 3)) << 16) : 0u;
 
     const int px = a.x0 + C::lane_x(warp, lane), py = a.y0 + C::lane_y(warp, lane);
     const bool inside = px < a.width && py < a.height;
@@ -154,8 +169,17 @@ __device__ uint32_t splat_consume(const TileJob& a, const SplatSmem<C>& sm, int 
     const float wx0 = (float)(a.x0 + C::lane_x(warp, 0)), wx1 = wx0 + (float)(C::kWarpW - 1);
     const float wy0 = (float)(a.y0 + C::lane_y(warp, 0)), wy1 = wy0 + (float)(C::kWarpH - 1);
 
-    for (int i = lane * 4; i < C::kAccFloats; i += 128)
-        *reinterpret_cast<float4*>(acc + i) = make_float4(0.f, 0.f, 0.f, 0.f);
+    if constexpr (kTM) {
+        uint32_t zero[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) zero[i] = 0u;
+#pragma unroll
+        for (int c = 0; c < C::kCols + 1; c += 32) tc::tmem_st32(tbase + (uint32_t)c, zero);
+        tc::tmem_wait_st();
+    } else {
+        for (int i = lane * 4; i < C::kAccFloats; i += 128)
+            *reinterpret_cast<float4*>(acc + i) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     __syncwarp();
 
     const uint32_t n = a.end - a.beg;
@@ -215,14 +239,14 @@ __device__ uint32_t splat_consume(const TileJob& a, const SplatSmem<C>& sm, int 
 #pragma unroll
                             for (int i = 0; i < C::kPairs / 4; ++i) {
                                 const uint4 v4 = reinterpret_cast<const uint4*>(cw)[i];
-                                offs[j][4 * i] = v4.x;
-                                offs[j][4 * i + 1] = v4.y;
-                                offs[j][4 * i + 2] = v4.z;
-                                offs[j][4 * i + 3] = v4.w;
+                                offs[j][4 * i] = acc_ref<kTM>(v4.x);
+                                offs[j][4 * i + 1] = acc_ref<kTM>(v4.y);
+                                offs[j][4 * i + 2] = acc_ref<kTM>(v4.z);
+                                offs[j][4 * i + 3] = acc_ref<kTM>(v4.w);
                             }
                         } else {
 #pragma unroll
-                            for (int p = 0; p < C::kPairs; ++p) offs[j][p] = cw[p];
+                            for (int p = 0; p < C::kPairs; ++p) offs[j][p] = acc_ref<kTM>(cw[p]);
                         }
                     }
                     const float p2 = eval_power2(g0, ax, axl, pxf, pyf);
@@ -276,6 +300,18 @@ __device__ uint32_t splat_consume(const TileJob& a, const SplatSmem<C>& sm, int 
                                 a0[66] = fmaf(al[j], w4.z, a0[66]);
                                 a0[99] = fmaf(al[j], w4.w, a0[99]);
                             }
+                        } else if constexpr (kTM) {
+                            // the pairs' columns are distinct (repeats and invalid indices sit
+                            // in the dummy column), so all loads go before the stores; the
+                            // stores land before the next record's loads
+                            uint32_t v[C::kPairs];
+#pragma unroll
+                            for (int p = 0; p < C::kPairs; ++p) tc::tmem_ld1(tbase + offs[j][p], v[p]);
+                            tc::tmem_wait_ld_regs(v);
+#pragma unroll
+                            for (int p = 0; p < C::kPairs; ++p)
+                                tc::tmem_st1(tbase + offs[j][p], __float_as_uint(fmaf(al[j], wr[p], __uint_as_float(v[p]))));
+                            tc::tmem_wait_st();
                         } else {
                             float v[C::kPairs];
                             float* addr[C::kPairs];
@@ -309,6 +345,37 @@ __device__ uint32_t splat_consume(const TileJob& a, const SplatSmem<C>& sm, int 
     // in HBM)
     constexpr int LW = C::kLW;
     const size_t P = (size_t)a.width * a.height;
+    if constexpr (kTM) {
+        // each lane writes its own pixel's row of a level, read from TMEM 32 columns at a time
+#pragma unroll 1
+        for (int lev = 0; lev < LEVELS; ++lev) {
+#pragma unroll 1
+            for (int h = 0; h < 2; ++h) {
+                uint32_t r[32];
+                tc::tmem_ld32(tbase + (uint32_t)(lev * 64 + h * 32), r);
+                tc::tmem_wait_ld_regs(r);
+                if (inside) {
+                    const size_t o = ((size_t)lev * P + (size_t)py * a.width + px) * 64 + h * 32;
+                    if (a.coeff_bf16) {
+                        uint4* out = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.coeff) + o);
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            __stcs(out + i, make_uint4(tc::pack_bf16(__uint_as_float(r[8 * i]), __uint_as_float(r[8 * i + 1])),
+                                                       tc::pack_bf16(__uint_as_float(r[8 * i + 2]), __uint_as_float(r[8 * i + 3])),
+                                                       tc::pack_bf16(__uint_as_float(r[8 * i + 4]), __uint_as_float(r[8 * i + 5])),
+                                                       tc::pack_bf16(__uint_as_float(r[8 * i + 6]), __uint_as_float(r[8 * i + 7]))));
+                    } else {
+                        float4* out = reinterpret_cast<float4*>(a.coeff + o);
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+                            __stcs(out + i, make_float4(__uint_as_float(r[4 * i]), __uint_as_float(r[4 * i + 1]),
+                                                        __uint_as_float(r[4 * i + 2]), __uint_as_float(r[4 * i + 3])));
+                    }
+                }
+            }
+        }
+        return consumed;
+    }
     if (a.coeff_bf16) {
         __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(a.coeff);
         constexpr int G8 = LW / 8;   // 8-coefficient groups per pixel
@@ -367,6 +434,32 @@ __device__ __forceinline__ uint32_t splat_tile(const TileJob& a,
     // Warps that stopped early release the stages of the batches they skipped (every one of
     // them lies within the last kStages batches, whose predecessors all warps released), so
     // each stage's barriers stay in step for the next tile.
+    if (warp < C::kWarps && lane == 0 && !*reinterpret_cast<volatile int*>(sm.abort))
+        for (uint32_t b = consumed; b < issued; ++b) tc::mbar_arrive(tc::smem_u32(sm.empty + (int)((bbase + b) % C::kStages)));
+    return issued;
+}
+
+// One 16 x 16 tile with TMEM accumulators for consumer warps 4-7 (SplatCfg with TM = 4): warps
+// 0-3 (rows 0-7) accumulate in shared memory, warps 4-7 (rows 8-15) in TMEM lane quarters 0-3,
+// warp 8 produces.  Same contract as splat_tile; the CTA's TMEM allocation is in *sm.tmem_slot.
+template <class C, int LEVELS, int K>
+__device__ __forceinline__ uint32_t splat_tile_tm(const TileJob& a, const SplatSmem<C>& sm, uint32_t bbase)
+{
+    static_assert(C::kTmemWarps == 4 && C::kWarps == 8, "warps 4-7 in TMEM");
+    constexpr int TW = 16, TH = 16;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t consumed = 0;
+    if (warp == C::kWarps)
+        splat_produce<C>(a, sm, lane, bbase);
+    else if (warp < C::kSmemAccWarps)
+        consumed = splat_consume<C, LEVELS, K, TW, TH, true, false>(a, sm, warp, lane, bbase);
+    else
+        consumed = splat_consume<C, LEVELS, K, TW, TH, true, true>(a, sm, warp, lane, bbase);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t issued = *sm.issued;
+    if (threadIdx.x == 0) *sm.done_warps = 0;
     if (warp < C::kWarps && lane == 0 && !*reinterpret_cast<volatile int*>(sm.abort))
         for (uint32_t b = consumed; b < issued; ++b) tc::mbar_arrive(tc::smem_u32(sm.empty + (int)((bbase + b) % C::kStages)));
     return issued;
