@@ -236,6 +236,49 @@ __global__ void __launch_bounds__(TW* TH + 32, 1) splat_views_kernel(SplatViewsA
     }
 }
 
+// The multi-view splat over 16 x 16 tiles with TMEM accumulators for consumer warps 4-7 (as
+// splat_tm_kernel), persistent: the CTA allocates its TMEM once and takes tiles from the queue.
+template <int LEVELS, int K, int BATCH>
+__global__ void __launch_bounds__(16 * 16 + 32, 2) splat_views_tm_kernel(SplatViewsArgs a)
+{
+    using C = SplatCfg<LEVELS, K, 16, 16, BATCH, false, 64, 4>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_tile;
+    const SplatSmem<C> sm(smem);
+    const int warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) sm.init();
+    if (warp == C::kSmemAccWarps) tc::tmem_alloc(tc::smem_u32(sm.tmem_slot), kSplatTmemCols);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    uint32_t bbase = 0;
+    while (true) {
+        if (threadIdx.x == 0) {
+            s_tile = (int)atomicAdd(a.queue, 1u);
+            *sm.skip = *sm.abort || (a.status && *reinterpret_cast<volatile int32_t*>(a.status) == LSV2_ERR_TIMEOUT);
+        }
+        __syncthreads();
+        const int tg = s_tile;
+        const bool stop = *sm.skip;
+        __syncthreads();
+        if (tg >= a.total_tiles || stop) break;
+        int v = 0;
+        while (v + 1 < a.V && tg >= a.view[v + 1].tile_base) ++v;
+        const SplatView& w = a.view[v];
+        const int tl = tg - w.tile_base;
+        TileJob j{w.width, w.height, (tl % w.GX) * 16, (tl / w.GX) * 16, a.tile_ranges[2 * tg], a.tile_ranges[2 * tg + 1],
+                  a.gauss_ids, a.recs + w.rec_off,
+                  a.coeff_bf16 ? reinterpret_cast<float*>(reinterpret_cast<__nv_bfloat16*>(a.coeff) + w.coeff_off)
+                               : a.coeff + w.coeff_off,
+                  a.final_T + w.pix_off, a.n_last + w.pix_off, a.status, a.coeff_bf16};
+        bbase += splat_tile_tm<C, LEVELS, K>(j, sm, bbase);
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (warp == C::kSmemAccWarps) tc::tmem_dealloc(*sm.tmem_slot, kSplatTmemCols);
+}
+
 namespace {
 
 // CTAs per 16 x 16 bin tile (two CTAs of 16 x 8 pixels share an SM)
@@ -269,6 +312,21 @@ cudaError_t launch_tm(const SplatArgs& a, cudaStream_t stream)
     const int GX = (a.cam.width + 15) / 16, GY = (a.cam.height + 15) / 16;
     if (GX * GY == 0) return cudaSuccess;
     kern<<<GX * GY, C::kThreads, C::kSmemBytes, stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <int LEVELS, int K, int BATCH>
+cudaError_t launch_views_tm(const SplatViewsArgs& a, int num_sms, cudaStream_t stream)
+{
+    using C = SplatCfg<LEVELS, K, 16, 16, BATCH, false, 64, 4>;
+    static_assert(2 * (C::kSmemBytes + 1024) <= 233472 && 3 * (C::kSmemBytes + 1024) > 233472, "two CTAs per SM");
+    auto kern = splat_views_tm_kernel<LEVELS, K, BATCH>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
+    if (e != cudaSuccess) return e;
+    if (a.total_tiles == 0) return cudaSuccess;
+    e = cudaMemsetAsync(a.queue, 0, sizeof(uint32_t), stream);
+    if (e != cudaSuccess) return e;
+    kern<<<num_sms * 2, C::kThreads, C::kSmemBytes, stream>>>(a);
     return cudaGetLastError();
 }
 
@@ -306,7 +364,14 @@ cudaError_t launch_views_b(const SplatViewsArgs& a, int batch, int num_sms, cuda
 template <int LEVELS, int K>
 cudaError_t launch_views_tile(const SplatViewsArgs& a, int tw, int th, int batch, int num_sms, cudaStream_t stream)
 {
-    if (tw == 16 && th == 16) return launch_views_b<LEVELS, K, 16, 16, kSub16>(a, batch, num_sms, stream);
+    if (tw == 16 && th == 16) {
+        if constexpr (LEVELS == 3 && K == 4) {   // TMEM accumulators for half the consumer warps
+            if (batch == 16) return launch_views_tm<LEVELS, K, 16>(a, num_sms, stream);
+            if (batch == 0 || batch == 32) return launch_views_tm<LEVELS, K, 32>(a, num_sms, stream);
+            return cudaErrorInvalidValue;
+        }
+        return launch_views_b<LEVELS, K, 16, 16, kSub16>(a, batch, num_sms, stream);
+    }
     if (tw == 8 && th == 8) return launch_views_b<LEVELS, K, 8, 8>(a, batch, num_sms, stream);
     if (tw == 32 && th == 8) return launch_views_b<LEVELS, K, 32, 8>(a, batch, num_sms, stream);
     return cudaErrorInvalidValue;
