@@ -172,10 +172,10 @@ __global__ void __launch_bounds__(TW* TH + 32, (TW * TH <= 128 && LW <= 64) ? 2 
 // where shared memory alone holds the accumulators of 8.
 constexpr uint32_t kSplatTmemCols = 256;
 
-template <int LEVELS, int K>
+template <int LEVELS, int K, int BATCH>
 __global__ void __launch_bounds__(16 * 16 + 32, 2) splat_tm_kernel(SplatArgs a)
 {
-    using C = SplatCfg<LEVELS, K, 16, 16, 0, false, 64, 4>;
+    using C = SplatCfg<LEVELS, K, 16, 16, BATCH, false, 64, 4>;
     extern __shared__ __align__(16) unsigned char smem[];
     const SplatSmem<C> sm(smem);
     if (threadIdx.x == 0) {
@@ -303,10 +303,12 @@ cudaError_t launch_t(const SplatArgs& a, cudaStream_t stream)
 template <int LEVELS, int K>
 cudaError_t launch_tm(const SplatArgs& a, cudaStream_t stream)
 {
-    using C = SplatCfg<LEVELS, K, 16, 16, 0, false, 64, 4>;
+    // 32 records per stage, 16 for the larger records of K >= 6 (two stages must fit twice per SM)
+    constexpr int kBatch = record_bytes(LEVELS * K) <= 160 ? 32 : 16;
+    using C = SplatCfg<LEVELS, K, 16, 16, kBatch, false, 64, 4>;
     // exactly two CTAs per SM: their TMEM allocations fill the SM's 512 columns
     static_assert(2 * (C::kSmemBytes + 1024) <= 233472 && 3 * (C::kSmemBytes + 1024) > 233472, "two CTAs per SM");
-    auto kern = splat_tm_kernel<LEVELS, K>;
+    auto kern = splat_tm_kernel<LEVELS, K, kBatch>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
     if (e != cudaSuccess) return e;
     const int GX = (a.cam.width + 15) / 16, GY = (a.cam.height + 15) / 16;
@@ -480,7 +482,10 @@ cudaError_t launch_splat(int levels, int K, const SplatArgs& a, cudaStream_t str
         return launch_tile<3, 4>(a, stream);
     }
     if (levels == 3 && a.cam.tile_w == 16 && a.cam.tile_h == 16) {   // K sweep at three levels
-        if (K == 2) return launch_t<3, 2, 16, 16>(a, stream);
+        // TMEM accumulators pay at K = 2 (as at K = 4); at K = 6 and 8 the 18-24 TMEM loads and
+        // stores per record and the smaller stages make them slower than one CTA of eight
+        // shared-memory warps per tile (1.28 and 1.86 ms against 1.06 and 1.26 ms)
+        if (K == 2) return launch_tm<3, 2>(a, stream);
         if (K == 6) return launch_t<3, 6, 16, 16>(a, stream);
         if (K == 8) return launch_t<3, 8, 16, 16>(a, stream);
     }

@@ -158,7 +158,7 @@ __device__ uint32_t splat_consume(const TileJob& a, const SplatSmem<C>& sm, int 
 {
     constexpr int kB = C::kBatch;
     constexpr int kChunk = 4;   // kept records evaluated together
-    static_assert(!kTM || (C::kLW == 64 && !C::kDense && C::kPairs == 12 && kWriteCoeff), "TMEM accumulators");
+    static_assert(!kTM || (C::kLW == 64 && !C::kDense && C::kPairs % 6 == 0 && kWriteCoeff), "TMEM accumulators");
     float* acc = sm.acc + (kTM ? 0 : warp) * C::kAccFloats;
     unsigned char* acc_lane = reinterpret_cast<unsigned char*>(acc + lane);
     const uint32_t tbase = kTM ? *sm.tmem_slot + ((uint32_t)(32 * (warp & 3)) << 16) : 0u;
@@ -225,7 +225,10 @@ __device__ uint32_t splat_consume(const TileJob& a, const SplatSmem<C>& sm, int 
                 // of one another (instruction-level parallelism across the chunk); the records'
                 // column offsets are loaded here too, so the accumulation's loads need not wait
                 float al[kChunk], om[kChunk], p2s[kChunk], os[kChunk];
-                uint32_t offs[kChunk][C::kDense ? 1 : C::kPairs];
+                // (records of up to 12 pairs: larger ones load their offsets in step C, so the
+                // hoisted copies do not spill)
+                constexpr bool kHoist = !C::kDense && C::kPairs <= 12;
+                uint32_t offs[kChunk][kHoist ? C::kPairs : 1];
                 bool high = false;
 #pragma unroll
                 for (int j = 0; j < kChunk; ++j) {
@@ -233,7 +236,7 @@ __device__ uint32_t splat_consume(const TileJob& a, const SplatSmem<C>& sm, int 
                     const float4 g0 = *reinterpret_cast<const float4*>(r);
                     const float4 ax = *reinterpret_cast<const float4*>(r + 4);
                     const float4 axl = *reinterpret_cast<const float4*>(r + 8);
-                    if constexpr (!C::kDense) {
+                    if constexpr (kHoist) {
                         const uint32_t* cw = reinterpret_cast<const uint32_t*>(r + 12 + C::kPairs);
                         if constexpr (C::kPairs % 4 == 0) {
 #pragma unroll
@@ -301,23 +304,32 @@ __device__ uint32_t splat_consume(const TileJob& a, const SplatSmem<C>& sm, int 
                                 a0[99] = fmaf(al[j], w4.w, a0[99]);
                             }
                         } else if constexpr (kTM) {
+                            const uint32_t* cw = reinterpret_cast<const uint32_t*>(r + 12 + C::kPairs);
+                            auto col = [&](int p) -> uint32_t {
+                                if constexpr (kHoist) return offs[j][p];
+                                else return acc_ref<true>(cw[p]);
+                            };
                             // the pairs' columns are distinct (repeats and invalid indices sit
                             // in the dummy column), so all loads go before the stores; the
                             // stores land before the next record's loads
                             uint32_t v[C::kPairs];
 #pragma unroll
-                            for (int p = 0; p < C::kPairs; ++p) tc::tmem_ld1(tbase + offs[j][p], v[p]);
+                            for (int p = 0; p < C::kPairs; ++p) tc::tmem_ld1(tbase + col(p), v[p]);
                             tc::tmem_wait_ld_regs(v);
 #pragma unroll
                             for (int p = 0; p < C::kPairs; ++p)
-                                tc::tmem_st1(tbase + offs[j][p], __float_as_uint(fmaf(al[j], wr[p], __uint_as_float(v[p]))));
+                                tc::tmem_st1(tbase + col(p), __float_as_uint(fmaf(al[j], wr[p], __uint_as_float(v[p]))));
                             tc::tmem_wait_st();
                         } else {
+                            const uint32_t* cw = reinterpret_cast<const uint32_t*>(r + 12 + C::kPairs);
                             float v[C::kPairs];
                             float* addr[C::kPairs];
 #pragma unroll
                             for (int p = 0; p < C::kPairs; ++p) {
-                                addr[p] = reinterpret_cast<float*>(acc_lane + offs[j][p]);
+                                uint32_t o;
+                                if constexpr (kHoist) o = offs[j][p];
+                                else o = cw[p];
+                                addr[p] = reinterpret_cast<float*>(acc_lane + o);
                                 v[p] = *addr[p];
                             }
 #pragma unroll

@@ -162,18 +162,17 @@ __device__ __forceinline__ void tmem_st1(uint32_t taddr, uint32_t v)
     asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" ::"r"(taddr), "r"(v) : "memory");
 }
 // tcgen05.wait::ld with the loaded registers as operands, so no use of them can be scheduled
-// before the wait.
+// before the wait (6 at a time: the first statement waits, the others only tie registers).
+__device__ __forceinline__ void tmem_wait_ld_tie6(uint32_t& a, uint32_t& b, uint32_t& c, uint32_t& d, uint32_t& e,
+                                                  uint32_t& f)
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(a), "+r"(b), "+r"(c), "+r"(d), "+r"(e), "+r"(f) : : "memory");
+}
 template <int N>
 __device__ __forceinline__ void tmem_wait_ld_regs(uint32_t (&v)[N])
 {
-    static_assert(N == 12 || N == 32, "twelve or 32 registers");
-    if constexpr (N == 12) {
-        asm volatile("tcgen05.wait::ld.sync.aligned;"
-                     : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]),
-                       "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11])
-                     :
-                     : "memory");
-    } else {
+    static_assert(N % 6 == 0 || N == 32, "6, 12, 18, 24 or 32 registers");
+    if constexpr (N == 32) {
         asm volatile("tcgen05.wait::ld.sync.aligned;"
                      : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]),
                        "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]), "+r"(v[14]),
@@ -182,6 +181,9 @@ __device__ __forceinline__ void tmem_wait_ld_regs(uint32_t (&v)[N])
                        "+r"(v[29]), "+r"(v[30]), "+r"(v[31])
                      :
                      : "memory");
+    } else {
+#pragma unroll
+        for (int i = 0; i < N; i += 6) tmem_wait_ld_tie6(v[i], v[i + 1], v[i + 2], v[i + 3], v[i + 4], v[i + 5]);
     }
 }
 
