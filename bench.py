@@ -39,13 +39,13 @@ FP32_ALU_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 POST_WINDOW = 29
 POST_THRESHOLD = 0.5
 
-SPLAT_KERNEL = "splat_kernel<3,4,16,8> (two CTAs per 16x16 tile)"
+SPLAT_KERNEL = "splat_tm_kernel<3,4> (one CTA per 16x16 tile, consumer warps 4-7 accumulate in TMEM)"
 # DRAM bytes (read + write) per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum) on
 # the same frame via `bench.py --profile STAGE`, with the kernels as they are now (an entry is
 # removed when its kernel changes): the splat and the relevancy as launched here; the decode
 # captured over one level (one third of the launch's pixels and bytes) and scaled by 3.
 TRAFFIC = {
-    SPLAT_KERNEL: 47622912 + 550734592,
+    SPLAT_KERNEL: 47201024 + 552040960,
     "decode_tc_kernel": 3 * (199166976 + 1532453376),
     "query_pipe_kernel<3>": 597294848 + 18970880,
 }
