@@ -167,15 +167,15 @@ __global__ void __launch_bounds__(TW* TH + 32, (TW * TH <= 128 && LW <= 64) ? 2 
     (void)splat_tile<LEVELS, K, TW, TH, 0, true, DENSE, LW>(j, sm, 0u);
 }
 
-// One CTA per 16 x 16 tile with eight consumer warps, the last four accumulating in TMEM (256
-// columns per CTA, two CTAs per SM: the whole of the SM's TMEM), so an SM runs 16 consumer warps
-// where shared memory alone holds the accumulators of 8.
-constexpr uint32_t kSplatTmemCols = 256;
-
-template <int LEVELS, int K, int BATCH>
-__global__ void __launch_bounds__(16 * 16 + 32, 2) splat_tm_kernel(SplatArgs a)
+// One CTA per 16 x 16 tile with eight consumer warps, the last four accumulating in TMEM (at
+// L = 64: 256 columns per CTA, two CTAs per SM, the whole of the SM's TMEM), so an SM runs 16
+// consumer warps where shared memory alone holds the accumulators of 8 (at L = 128: one CTA and
+// 512 columns per SM, 8 consumer warps where shared memory alone holds those of 4).
+template <int LEVELS, int K, int BATCH, int LW = 64>
+__global__ void __launch_bounds__(16 * 16 + 32, LW <= 64 ? 2 : 1) splat_tm_kernel(SplatArgs a)
 {
-    using C = SplatCfg<LEVELS, K, 16, 16, BATCH, false, 64, 4>;
+    using C = SplatCfg<LEVELS, K, 16, 16, BATCH, false, LW, 4>;
+    constexpr uint32_t kSplatTmemCols = C::kTmemCols;
     extern __shared__ __align__(16) unsigned char smem[];
     const SplatSmem<C> sm(smem);
     if (threadIdx.x == 0) {
@@ -242,6 +242,7 @@ template <int LEVELS, int K, int BATCH>
 __global__ void __launch_bounds__(16 * 16 + 32, 2) splat_views_tm_kernel(SplatViewsArgs a)
 {
     using C = SplatCfg<LEVELS, K, 16, 16, BATCH, false, 64, 4>;
+    constexpr uint32_t kSplatTmemCols = C::kTmemCols;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_tile;
     const SplatSmem<C> sm(smem);
@@ -300,15 +301,16 @@ cudaError_t launch_t(const SplatArgs& a, cudaStream_t stream)
     return cudaGetLastError();
 }
 
-template <int LEVELS, int K>
+template <int LEVELS, int K, int LW = 64>
 cudaError_t launch_tm(const SplatArgs& a, cudaStream_t stream)
 {
     // 32 records per stage, 16 for the larger records of K >= 6 (two stages must fit twice per SM)
     constexpr int kBatch = record_bytes(LEVELS * K) <= 160 ? 32 : 16;
-    using C = SplatCfg<LEVELS, K, 16, 16, kBatch, false, 64, 4>;
-    // exactly two CTAs per SM: their TMEM allocations fill the SM's 512 columns
-    static_assert(2 * (C::kSmemBytes + 1024) <= 233472 && 3 * (C::kSmemBytes + 1024) > 233472, "two CTAs per SM");
-    auto kern = splat_tm_kernel<LEVELS, K, kBatch>;
+    using C = SplatCfg<LEVELS, K, 16, 16, kBatch, false, LW, 4>;
+    // the CTAs an SM holds (by shared memory) must fit its 512 TMEM columns together
+    constexpr int kPerSm = 233472 / (C::kSmemBytes + 1024);
+    static_assert(kPerSm >= 1 && kPerSm * C::kTmemCols <= 512, "TMEM of the resident CTAs");
+    auto kern = splat_tm_kernel<LEVELS, K, kBatch, LW>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
     if (e != cudaSuccess) return e;
     const int GX = (a.cam.width + 15) / 16, GY = (a.cam.height + 15) / 16;
@@ -475,7 +477,8 @@ cudaError_t launch_splat(int levels, int K, const SplatArgs& a, cudaStream_t str
     }
     if (levels == 2 && K == 4) return launch_tile<2, 4>(a, stream);
     if (levels == 3 && K == 4 && a.L == 32) return launch_t<3, 4, 16, 16, false, kSub16, 32>(a, stream);
-    if (levels == 3 && K == 4 && a.L == 128) return launch_t<3, 4, 16, 16, false, kSub16, 128>(a, stream);
+    if (levels == 3 && K == 4 && a.L == 128 && a.cam.tile_w == 16 && a.cam.tile_h == 16)
+        return launch_tm<3, 4, 128>(a, stream);
     if (a.L != 64) return cudaErrorInvalidValue;
     if (levels == 3 && K == 4) {
         if (a.cam.tile_w == 16 && a.cam.tile_h == 16) return launch_tm<3, 4>(a, stream);

@@ -71,8 +71,11 @@ struct SplatCfg {
     static_assert(LW % 8 == 0 && LW <= 256, "codebook size");
     static_assert(kRecBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
     static_assert(kStages >= 2, "at least two stages");
-    static_assert(TM == 0 || (TM == 4 && kWarps == 8 && !DENSE && kCols + 1 <= 256),
-                  "TMEM accumulators: warps 4-7 of 8, one lane quarter each, at most 256 columns");
+    // TMEM columns a CTA allocates: 256 (two CTAs per SM) when the accumulators and the dummy
+    // column fit, else the SM's 512 (one CTA per SM)
+    static constexpr uint32_t kTmemCols = kCols + 1 <= 256 ? 256u : 512u;
+    static_assert(TM == 0 || (TM == 4 && kWarps == 8 && !DENSE && kCols + 1 <= 512),
+                  "TMEM accumulators: warps 4-7 of 8, one lane quarter each, at most 512 columns");
 };
 
 struct PackArgs {

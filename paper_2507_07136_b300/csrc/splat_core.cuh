@@ -158,7 +158,7 @@ __device__ uint32_t splat_consume(const TileJob& a, const SplatSmem<C>& sm, int 
 {
     constexpr int kB = C::kBatch;
     constexpr int kChunk = 4;   // kept records evaluated together
-    static_assert(!kTM || (C::kLW == 64 && !C::kDense && C::kPairs % 6 == 0 && kWriteCoeff), "TMEM accumulators");
+    static_assert(!kTM || (C::kLW % 32 == 0 && !C::kDense && C::kPairs % 6 == 0 && kWriteCoeff), "TMEM accumulators");
     float* acc = sm.acc + (kTM ? 0 : warp) * C::kAccFloats;
     unsigned char* acc_lane = reinterpret_cast<unsigned char*>(acc + lane);
     const uint32_t tbase = kTM ? *sm.tmem_slot + ((uint32_t)(32 * (warp & 3)) << 16) : 0u;
@@ -362,12 +362,12 @@ __device__ uint32_t splat_consume(const TileJob& a, const SplatSmem<C>& sm, int 
 #pragma unroll 1
         for (int lev = 0; lev < LEVELS; ++lev) {
 #pragma unroll 1
-            for (int h = 0; h < 2; ++h) {
+            for (int h = 0; h < LW / 32; ++h) {
                 uint32_t r[32];
-                tc::tmem_ld32(tbase + (uint32_t)(lev * 64 + h * 32), r);
+                tc::tmem_ld32(tbase + (uint32_t)(lev * LW + h * 32), r);
                 tc::tmem_wait_ld_regs(r);
                 if (inside) {
-                    const size_t o = ((size_t)lev * P + (size_t)py * a.width + px) * 64 + h * 32;
+                    const size_t o = ((size_t)lev * P + (size_t)py * a.width + px) * LW + h * 32;
                     if (a.coeff_bf16) {
                         uint4* out = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.coeff) + o);
 #pragma unroll
