@@ -6,9 +6,11 @@ text query with four negatives.  One step renders one frame through every stage 
 project -> bin_sort -> splat_coeffs -> decode (F materialised in HBM) -> query (relevancy).
 
 Printed as one JSON line.  `value` is frames per second over all ranks, device-timed with CUDA
-events per step (L2 flushed between steps, flush not timed).  `e2e` runs the same steps through
-the C ABI with the per-step inputs (camera, text embeddings) copied from pinned host memory
-and the relevancy maps copied back (on a copy stream, while the next step computes), host-timed.  `roofline` is for the stage that dominates the
+events per step, the step launched as one CUDA graph (L2 flushed between steps, flush not
+timed); `stages_ms` times the same step launched eagerly with events between its stages.  `e2e`
+runs the same steps (as graphs) through the C ABI with the per-step inputs (text embeddings)
+copied from pinned host memory and the relevancy maps copied back (on a copy stream, while the
+next step computes), host-timed.  `roofline` is for the stage that dominates the
 step.  `cpu_baseline` times the FP64 oracle (single thread) on a bounded sample of the frame.
 """
 from __future__ import annotations
@@ -458,8 +460,32 @@ def main():
               for i, s in enumerate(stages)}
         return st, float(np.mean([evs[k][0].elapsed_time(evs[k][len(stages)]) for k in range(n_steps)]))
 
+    def capture(rel_buf):
+        """The whole step as one CUDA graph writing rel_buf (every stage is stream-ordered library
+        calls on preallocated buffers, so it captures as is)."""
+        cur["rel"] = rel_buf
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            step()
+        return g
+
+    def timed_graph(g, n_steps):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_steps)]
+        for k in range(n_steps):
+            evs[k][0].record(stream)
+            g.replay()
+            evs[k][1].record(stream)
+            flush.fill_(1)
+        torch.cuda.synchronize()
+        return float(np.mean([a.elapsed_time(b) for a, b in evs]))
+
     for _ in range(args.warmup):
         step()
+        flush.fill_(1)
+    frame.check()
+    graph = capture(rel)
+    for _ in range(args.warmup):
+        graph.replay()
         flush.fill_(1)
     frame.check()
     if world > 1:
@@ -467,11 +493,14 @@ def main():
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         t_wall = time.perf_counter()
-        stage_ms, step_ms = timed(args.steps)
+        step_ms = timed_graph(graph, args.steps)
         t_wall = time.perf_counter() - t_wall
     if world > 1:
         dist.barrier()
     frame.check()
+    del graph   # it holds pointers to F, which the FP32 comparison below reallocates
+    # the per-stage breakdown: the same step with eager launches and events between the stages
+    stage_ms, eager_ms = timed(max(3, args.steps // 2))
     if world > 1:
         t = torch.tensor([step_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -526,13 +555,14 @@ def main():
     copy_stream = torch.cuda.Stream(device=dev)
     copied = [None, None]
 
+    graphs = [capture(rels[0]), capture(rels[1])]
+
     def e2e_step(i):
         b = i % 2
         if copied[b] is not None:
             stream.wait_event(copied[b])
-        cur["rel"] = rels[b]
         text_d.copy_(text_h, non_blocking=True)
-        step()
+        graphs[b].replay()
         computed = torch.cuda.Event()
         computed.record(stream)
         copy_stream.wait_event(computed)
@@ -588,8 +618,10 @@ def main():
                                "post-processing (LERF rule, "
                                f"{POST_WINDOW}x{POST_WINDOW} mean filter, level, point, mask at {POST_THRESHOLD})",
                        "parallelism": f"replicas x{world}",
-                       "l2": "flushed between steps (256 MiB write, untimed)", "instances": inst},
+                       "l2": "flushed between steps (256 MiB write, untimed)", "instances": inst,
+                       "launch": "each step is one CUDA graph replay (stages_ms: the same step launched eagerly)"},
             "stages_ms": stage_ms,
+            "eager_ms_per_step": eager_ms,
             "splat_decode_fps": 1e3 / (stage_ms["project"] + stage_ms["bin_sort"] + stage_ms["splat"] + stage_ms["decode"]),
             "query_fps": 1e3 / (stage_ms["project"] + stage_ms["bin_sort"] + stage_ms["splat"] + stage_ms["query"]
                                 + stage_ms["post"]),
