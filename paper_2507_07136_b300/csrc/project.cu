@@ -110,7 +110,7 @@ __device__ int32_t degenerate_radius(const lsv2_camera& c, const float m[3], con
     return (int32_t)rf;
 }
 
-__global__ void __launch_bounds__(256) project_kernel(ProjectArgs a)
+__global__ void __launch_bounds__(256, 4) project_kernel(ProjectArgs a)   // 4 blocks per SM: latency-bound
 {
     const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (gi >= a.n) return;
