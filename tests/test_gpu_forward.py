@@ -176,6 +176,59 @@ def test_duplicate_indices_and_stacked_closed_form():
     check_blend(fr, ref.blend, px, py, cam)
 
 
+@pytest.mark.parametrize("opacity", [0.05, 0.9])
+def test_crowded_tiles_three_levels(opacity):
+    """Three levels on 16 x 16 tiles (the kernel whose warps 4-7 accumulate in TMEM): 3,000
+    Gaussians packed into a few tiles, so a tile's list runs to thousands of records (many
+    32-record batches through the 2-stage ring, the barriers' phases wrapping many times).
+    Translucent Gaussians (opacity 0.05) keep every pixel blending to the end of its list;
+    opaque ones (0.9) end most pixels early (warps done before the producer is)."""
+    rng = np.random.default_rng(21)
+    n = 3000
+    means = np.stack([rng.uniform(-0.12, 0.12, n), rng.uniform(-0.12, 0.12, n), rng.uniform(-0.5, 0.5, n)],
+                     1).astype(np.float32)
+    scales = np.exp(rng.normal(-3.4, 0.3, (n, 3))).astype(np.float32)
+    q = rng.normal(size=(n, 4))
+    q = (q / np.linalg.norm(q, axis=1, keepdims=True)).astype(np.float32)
+    idx, w = syn.sparse_coefficients(rng, n, 3, 4, 64)
+    sc = syn.Scene(means, scales, q, np.full(n, opacity, np.float32), idx, w, syn.codebooks(5, 3))
+    cam = syn.orbit_camera(64, 48, 4.0)
+    ref = O.render(sc, cam)
+    ds, fr = gpu_frame(sc, cam)
+    ranges = ref.ranges.reshape(-1, 2)
+    assert int((ranges[:, 1] - ranges[:, 0]).max()) > 1000, "the scene should crowd some tiles"
+    check_projection(fr, ref.proj)
+    check_bins(fr, ref.ids, ref.ranges)
+    px, py = O.all_pixels(cam)
+    check_blend(fr, ref.blend, px, py, cam)
+
+
+def test_repeated_indices_three_levels():
+    """Three levels (TMEM-accumulator kernel): repeated indices in every level are merged into one
+    pair and the emptied repeats accumulate nothing, whichever accumulator store a pixel's warp
+    uses; the stacked closed form (13 contributors, T = 2^-13) holds at every level."""
+    n = 20
+    means = np.stack([np.zeros(n), np.zeros(n), 0.1 * np.arange(n)], 1).astype(np.float32)
+    lev = [np.stack([np.arange(n), np.arange(n), 40 + np.arange(n), 60 + np.arange(n) % 4], 1),
+           np.stack([7 + np.zeros(n, int), 7 + np.zeros(n, int), 7 + np.zeros(n, int), 9 + np.arange(n)], 1),
+           np.stack([63 - np.arange(n), 1 + np.arange(n), 63 - np.arange(n), 1 + np.arange(n)], 1)]
+    idx = np.stack(lev, 1).astype(np.uint8)
+    w = np.tile([0.5, 0.25, 0.125, 0.125], (n, 3, 1)).astype(np.float32)
+    sc = syn.Scene(means, np.full((n, 3), 0.05, np.float32), np.tile([1, 0, 0, 0], (n, 1)).astype(np.float32),
+                   np.full(n, 0.5, np.float32), idx, w, syn.codebooks(1, 3))
+    cam = syn.orbit_camera(33, 33, 4.0)
+    ref = O.render(sc, cam)
+    ds, fr = gpu_frame(sc, cam)
+    p = 16 * 33 + 16
+    assert int(fr.n_last[p].item()) == 13
+    assert float(fr.final_T[p].item()) == 2.0 ** -13
+    # level 1 of the centre pixel: entry 7 carries 0.875 of every contribution
+    total = 1.0 - 2.0 ** -13
+    assert abs(float(fr.coeff[1, p, 7].item()) - 0.875 * total) <= 1e-5 * total
+    px, py = O.all_pixels(cam)
+    check_blend(fr, ref.blend, px, py, cam)
+
+
 def test_empty_and_culled_scenes():
     cam = syn.orbit_camera(64, 48, 4.0)
     # every Gaussian behind the camera or with a zero quaternion
