@@ -222,6 +222,101 @@ def ablation_section(dev, reps: int = 10):
     return out
 
 
+def backward_section(dev, reps: int = 10):
+    """The differentiation workload (100,000 Gaussians, one level, K = 4, 720x540, L1 loss against a
+    seeded N(0, 0.05^2) target of D = 512 features): the forward (project, bin, FP32 splat), the
+    fused decode + L1 + adjoint kernel (lsv2_l1_decode_backward: F recomputed, dLoss/dW and
+    dLoss/dS in one pass, F never stored) and the splat and projection adjoints
+    (lsv2_splat_backward), each CUDA-event timed with L2 flushed and the gradient buffers zeroed
+    before it; `step_ms` is one whole training step (forward, both adjoints, the zeroing)."""
+    import torch
+    import lsv2_synth as syn
+    from paper_2507_07136_b300 import _lib as Lb
+    from paper_2507_07136_b300.pipeline import DeviceScene, Frame, _ptr
+    sc, cam = syn.differentiation()
+    scene = DeviceScene.from_numpy(sc, device=dev)
+    fr = Frame(scene, cam, device=dev)
+    target = torch.as_tensor(syn.l1_target(cam), device=dev).contiguous()
+    P, lev, D, n = fr.P, scene.levels, scene.D, scene.n
+    loss = torch.zeros(1, device=dev)
+    dcoeff = torch.empty_like(fr.coeff)
+    dcb = torch.zeros_like(scene.codebook)
+    grads = [torch.zeros_like(scene.weights), torch.zeros(n, device=dev), torch.zeros_like(scene.means),
+             torch.zeros_like(scene.scales), torch.zeros_like(scene.quats)]
+    ws_bytes = Lb.lsv2_splat_backward_workspace_bytes(n)
+    ws = torch.empty(max(ws_bytes, 16), dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    st = torch.cuda.current_stream().cuda_stream
+
+    def zero_l1():
+        loss.zero_()
+        dcb.zero_()
+
+    def zero_bwd():
+        for t in grads:
+            t.zero_()
+
+    def l1():
+        Lb.lsv2_l1_decode_backward(lev, P, 64, D, _ptr(fr.coeff), _ptr(scene.codebook), _ptr(target), _ptr(loss),
+                                   _ptr(dcoeff), _ptr(dcb), st)
+
+    def bwd():
+        Lb.lsv2_splat_backward(fr.ccam, n, _ptr(scene.means), _ptr(scene.scales), _ptr(scene.quats), fr.proj,
+                               _ptr(fr.tile_ranges), _ptr(fr.gauss_ids), scene.levels, scene.K, 64, _ptr(scene.idx),
+                               _ptr(scene.weights), _ptr(fr.final_T), _ptr(fr.n_last), _ptr(dcoeff), _ptr(ws),
+                               ws_bytes, *[_ptr(t) for t in grads], _ptr(fr.status), st)
+
+    def step():
+        fr.render()
+        zero_l1()
+        l1()
+        zero_bwd()
+        bwd()
+
+    def timed(fn, before=None):
+        for _ in range(3):
+            if before:
+                before()
+            fn()
+        ts = []
+        for _ in range(reps):
+            flush.fill_(1)
+            if before:
+                before()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.mean(ts))
+
+    fwd_ms = timed(fr.render)
+    l1_ms = timed(l1, zero_l1)
+    bwd_ms = timed(bwd, zero_bwd)
+    step_ms = timed(step)
+    fr.check()
+    pk, pk_kind = peaks()
+    # FP32 FMA peak from unit counts: 148 SMs x 128 lanes x 2 flop x the maximum SM clock
+    fp32_tflops = 148 * 128 * 2 * 2.032e9 / 1e12
+    l1_flop = P * lev * 3 * 2 * 64 * D        # F = W S, dW = G_F S^T, dS += W^T G_F per pixel
+    l1_tf = l1_flop / (l1_ms * 1e-3) / 1e12
+    inst = int(fr.num_instances.item())
+    bwd_bytes = P * lev * 64 * 4 + P * 8 + inst * 4 + n * (lev * scene.K * 5 + 44) + n * (lev * scene.K + 11) * 4
+    bwd_gbs = bwd_bytes / (bwd_ms * 1e-3) / 1e9
+    return {"workload": "100,000 Gaussians, 1 level, K = 4, L = 64, D = 512, 720x540, L1 loss against a seeded "
+                        "target; gradients of weights, codebook, opacities, means, scales, quaternions",
+            "forward_ms": fwd_ms, "l1_decode_backward_ms": l1_ms, "splat_backward_ms": bwd_ms, "step_ms": step_ms,
+            "steps_per_s": 1e3 / step_ms, "instances": inst,
+            "l1_decode_backward": {"bound": "alu", "achieved": l1_tf, "peak": fp32_tflops, "unit": "TFLOP/s",
+                                   "frac": l1_tf / fp32_tflops, "algorithmic_flop": l1_flop,
+                                   "peak_source": "FP32 FMA lanes x 2 x maximum SM clock"},
+            "splat_backward": {"bound": "hbm", "achieved": bwd_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                               "frac": bwd_gbs / pk["hbm_gbs"], "algorithmic_bytes": bwd_bytes,
+                               "peak_source": pk_kind,
+                               "note": "bound by its atomics and per-pixel latency, not HBM"}}
+
+
 # ----------------------------------------------------------------------------- batched views
 def sparsify_section(dev, reps: int = 20):
     """Sec. 3.3 sparse coefficients on the at-scale shape (300,000 Gaussians x 3 levels of 64 logits,
@@ -641,6 +736,7 @@ def main():
         line["batched"] = batched_section(dev, rank=rank, world=world)
     if world == 1:
         line["sparsify"] = sparsify_section(dev)
+        line["backward"] = backward_section(dev)
     if not args.no_ablation and world == 1:
         torch.cuda.empty_cache()
         line["ablation"] = ablation_section(dev)

@@ -80,6 +80,19 @@ __global__ void __launch_bounds__(256) l1_decode_backward_kernel(int64_t P, int 
             // F block: thread (ty: 4 pixels, tx: 8 features)
             {
                 const int tx = tid & 15, ty = tid >> 4;
+                // the target block is loaded first, so its HBM latency overlaps the products
+                float4 tgt[4][2];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int px = ty * 4 + i;
+                    if (p0 + px < P) {
+                        const float4* tp = reinterpret_cast<const float4*>(Tl + (p0 + px) * D + c0 + tx * 8);
+                        tgt[i][0] = __ldcs(tp);
+                        tgt[i][1] = __ldcs(tp + 1);
+                    } else {
+                        tgt[i][0] = tgt[i][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                }
                 float f[4][8];
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
@@ -101,8 +114,7 @@ __global__ void __launch_bounds__(256) l1_decode_backward_kernel(int64_t P, int 
                     const int px = ty * 4 + i;
                     float g[8];
                     if (p0 + px < P) {
-                        const float4* tp = reinterpret_cast<const float4*>(Tl + (p0 + px) * D + c0 + tx * 8);
-                        const float4 t0 = __ldcs(tp), t1 = __ldcs(tp + 1);
+                        const float4 t0 = tgt[i][0], t1 = tgt[i][1];
                         const float tv[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
 #pragma unroll
                         for (int j = 0; j < 8; ++j) {
