@@ -26,6 +26,7 @@ namespace {
 // ------------------------------------------------------------------------------------ 1
 constexpr int kBP = 64;    // pixels per tile
 constexpr int kBC = 128;   // feature chunk
+constexpr int kSC = kBC + 4;   // S chunk row stride (floats): rows 16 B aligned, 4 banks apart
 constexpr int kL = 64;
 
 __global__ void __launch_bounds__(256) l1_decode_backward_kernel(int64_t P, int D, float inv_n,
@@ -39,8 +40,8 @@ __global__ void __launch_bounds__(256) l1_decode_backward_kernel(int64_t P, int 
     extern __shared__ __align__(16) float sm[];
     float* dSacc = sm;                          // [64][D]
     float* Wt = dSacc + kL * D;                 // [64 l][kBP + 4]
-    float* Sc = Wt + kL * (kBP + 4);            // [64 l][kBC]
-    float* Gs = Sc + kL * kBC;                  // [kBP][kBC + 4]
+    float* Sc = Wt + kL * (kBP + 4);            // [64 l][kSC]
+    float* Gs = Sc + kL * kSC;                  // [kBP][kBC + 4]
     __shared__ float red[8];
     const int lev = blockIdx.y;
     const int tid = threadIdx.x;
@@ -73,11 +74,12 @@ __global__ void __launch_bounds__(256) l1_decode_backward_kernel(int64_t P, int 
             __syncthreads();
             for (int i = tid; i < kL * kBC / 4; i += 256) {
                 const int l = i >> 5, c4 = (i & 31) * 4;
-                *reinterpret_cast<float4*>(Sc + l * kBC + c4) =
+                *reinterpret_cast<float4*>(Sc + l * kSC + c4) =
                     __ldg(reinterpret_cast<const float4*>(Sl + (size_t)l * D + c0 + c4));
             }
             __syncthreads();
-            // F block: thread (ty: 4 pixels, tx: 8 features)
+            // F block: thread (ty: 4 pixels, tx: features 4 tx .. 4 tx + 3 and 64 + 4 tx .. 64 + 4 tx + 3,
+            // so the 16 threads of a row read 256 contiguous bytes per 16-byte load: no bank conflict)
             {
                 const int tx = tid & 15, ty = tid >> 4;
                 // the target block is loaded first, so its HBM latency overlaps the products
@@ -86,9 +88,9 @@ __global__ void __launch_bounds__(256) l1_decode_backward_kernel(int64_t P, int 
                 for (int i = 0; i < 4; ++i) {
                     const int px = ty * 4 + i;
                     if (p0 + px < P) {
-                        const float4* tp = reinterpret_cast<const float4*>(Tl + (p0 + px) * D + c0 + tx * 8);
-                        tgt[i][0] = __ldcs(tp);
-                        tgt[i][1] = __ldcs(tp + 1);
+                        const float* tp = Tl + (p0 + px) * D + c0 + tx * 4;
+                        tgt[i][0] = __ldcs(reinterpret_cast<const float4*>(tp));
+                        tgt[i][1] = __ldcs(reinterpret_cast<const float4*>(tp + 64));
                     } else {
                         tgt[i][0] = tgt[i][1] = make_float4(0.f, 0.f, 0.f, 0.f);
                     }
@@ -100,8 +102,8 @@ __global__ void __launch_bounds__(256) l1_decode_backward_kernel(int64_t P, int 
                     for (int j = 0; j < 8; ++j) f[i][j] = 0.0f;
                 for (int l = 0; l < kL; ++l) {
                     const float4 a = *reinterpret_cast<const float4*>(Wt + l * (kBP + 4) + ty * 4);
-                    const float4 b0 = *reinterpret_cast<const float4*>(Sc + l * kBC + tx * 8);
-                    const float4 b1 = *reinterpret_cast<const float4*>(Sc + l * kBC + tx * 8 + 4);
+                    const float4 b0 = *reinterpret_cast<const float4*>(Sc + l * kSC + tx * 4);
+                    const float4 b1 = *reinterpret_cast<const float4*>(Sc + l * kSC + 64 + tx * 4);
                     const float av[4] = {a.x, a.y, a.z, a.w};
                     const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
@@ -126,12 +128,13 @@ __global__ void __launch_bounds__(256) l1_decode_backward_kernel(int64_t P, int 
 #pragma unroll
                         for (int j = 0; j < 8; ++j) g[j] = 0.0f;
                     }
-                    *reinterpret_cast<float4*>(Gs + px * (kBC + 4) + tx * 8) = make_float4(g[0], g[1], g[2], g[3]);
-                    *reinterpret_cast<float4*>(Gs + px * (kBC + 4) + tx * 8 + 4) = make_float4(g[4], g[5], g[6], g[7]);
+                    *reinterpret_cast<float4*>(Gs + px * (kBC + 4) + tx * 4) = make_float4(g[0], g[1], g[2], g[3]);
+                    *reinterpret_cast<float4*>(Gs + px * (kBC + 4) + 64 + tx * 4) = make_float4(g[4], g[5], g[6], g[7]);
                 }
             }
             __syncthreads();
-            // dS chunk: dSacc[l][c0 + c] += sum_px Wt[l][px] Gs[px][c]   (thread: 4 l x 8 c)
+            // dS chunk: dSacc[l][c0 + c] += sum_px Wt[l][px] Gs[px][c]   (thread: 4 l x 8 c, the
+            // features interleaved as in the F block)
             {
                 const int tc = tid & 15, tl = tid >> 4;
                 float s[4][8];
@@ -140,8 +143,8 @@ __global__ void __launch_bounds__(256) l1_decode_backward_kernel(int64_t P, int 
 #pragma unroll
                     for (int j = 0; j < 8; ++j) s[i][j] = 0.0f;
                 for (int px = 0; px < kBP; ++px) {
-                    const float4 g0 = *reinterpret_cast<const float4*>(Gs + px * (kBC + 4) + tc * 8);
-                    const float4 g1 = *reinterpret_cast<const float4*>(Gs + px * (kBC + 4) + tc * 8 + 4);
+                    const float4 g0 = *reinterpret_cast<const float4*>(Gs + px * (kBC + 4) + tc * 4);
+                    const float4 g1 = *reinterpret_cast<const float4*>(Gs + px * (kBC + 4) + 64 + tc * 4);
                     const float gv[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
@@ -151,11 +154,18 @@ __global__ void __launch_bounds__(256) l1_decode_backward_kernel(int64_t P, int 
                     }
                 }
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) dSacc[(tl * 4 + i) * D + c0 + tc * 8 + j] += s[i][j];
+                for (int i = 0; i < 4; ++i) {
+                    float4* r0 = reinterpret_cast<float4*>(dSacc + (tl * 4 + i) * D + c0 + tc * 4);
+                    float4* r1 = reinterpret_cast<float4*>(dSacc + (tl * 4 + i) * D + c0 + 64 + tc * 4);
+                    float4 v0 = *r0, v1 = *r1;
+                    v0.x += s[i][0], v0.y += s[i][1], v0.z += s[i][2], v0.w += s[i][3];
+                    v1.x += s[i][4], v1.y += s[i][5], v1.z += s[i][6], v1.w += s[i][7];
+                    *r0 = v0;
+                    *r1 = v1;
+                }
             }
-            // dW: dwacc[px][l] += sum_c Gs[px][c] Sc[l][c]   (thread: 4 px x 4 l)
+            // dW: dwacc[px][l] += sum_c Gs[px][c] Sc[l][c]   (thread: 4 px x the 4 l = tl + 16 j, so
+            // the 16 threads of a row read 16 consecutive S rows, 4 banks apart)
             {
                 const int tl = tid & 15, tp = tid >> 4;
                 for (int c = 0; c < kBC; ++c) {
@@ -163,7 +173,7 @@ __global__ void __launch_bounds__(256) l1_decode_backward_kernel(int64_t P, int 
 #pragma unroll
                     for (int i = 0; i < 4; ++i) gv[i] = Gs[(tp * 4 + i) * (kBC + 4) + c];
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) sv[j] = Sc[(tl * 4 + j) * kBC + c];
+                    for (int j = 0; j < 4; ++j) sv[j] = Sc[(tl + 16 * j) * kSC + c];
 #pragma unroll
                     for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -176,9 +186,10 @@ __global__ void __launch_bounds__(256) l1_decode_backward_kernel(int64_t P, int 
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const int64_t p = p0 + tp * 4 + i;
-                if (p < P)
-                    *reinterpret_cast<float4*>(dWl + p * kL + tl * 4) =
-                        make_float4(dwacc[i][0], dwacc[i][1], dwacc[i][2], dwacc[i][3]);
+                if (p < P) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) dWl[p * kL + tl + 16 * j] = dwacc[i][j];
+                }
             }
         }
     }
@@ -532,7 +543,7 @@ cudaError_t launch_l1_decode_backward(int levels, int64_t P, int D, const float*
                                       cudaStream_t stream)
 {
     if (P == 0) return cudaSuccess;
-    const size_t smem = (size_t)(kL * D + kL * (kBP + 4) + kL * kBC + kBP * (kBC + 4)) * 4;
+    const size_t smem = (size_t)(kL * D + kL * (kBP + 4) + kL * kSC + kBP * (kBC + 4)) * 4;
     cudaError_t e = cudaFuncSetAttribute(l1_decode_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t ntiles = (P + kBP - 1) / kBP;
