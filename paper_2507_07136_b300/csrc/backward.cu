@@ -142,15 +142,23 @@ __global__ void __launch_bounds__(256) l1_decode_backward_kernel(int64_t P, int 
                 for (int i = 0; i < 4; ++i)
 #pragma unroll
                     for (int j = 0; j < 8; ++j) s[i][j] = 0.0f;
-                for (int px = 0; px < kBP; ++px) {
-                    const float4 g0 = *reinterpret_cast<const float4*>(Gs + px * (kBC + 4) + tc * 4);
-                    const float4 g1 = *reinterpret_cast<const float4*>(Gs + px * (kBC + 4) + 64 + tc * 4);
-                    const float gv[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+                // four pixels per step: each W row read with one 16-byte load (pixel order kept)
+                for (int p4 = 0; p4 < kBP; p4 += 4) {
+                    float4 wq[4];
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const float wv = Wt[(tl * 4 + i) * (kBP + 4) + px];
+                    for (int i = 0; i < 4; ++i) wq[i] = *reinterpret_cast<const float4*>(Wt + (tl * 4 + i) * (kBP + 4) + p4);
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) s[i][j] = fmaf(wv, gv[j], s[i][j]);
+                    for (int q = 0; q < 4; ++q) {
+                        const int px = p4 + q;
+                        const float4 g0 = *reinterpret_cast<const float4*>(Gs + px * (kBC + 4) + tc * 4);
+                        const float4 g1 = *reinterpret_cast<const float4*>(Gs + px * (kBC + 4) + 64 + tc * 4);
+                        const float gv[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const float wv = q == 0 ? wq[i].x : q == 1 ? wq[i].y : q == 2 ? wq[i].z : wq[i].w;
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) s[i][j] = fmaf(wv, gv[j], s[i][j]);
+                        }
                     }
                 }
 #pragma unroll
@@ -168,16 +176,22 @@ __global__ void __launch_bounds__(256) l1_decode_backward_kernel(int64_t P, int 
             // the 16 threads of a row read 16 consecutive S rows, 4 banks apart)
             {
                 const int tl = tid & 15, tp = tid >> 4;
-                for (int c = 0; c < kBC; ++c) {
-                    float gv[4], sv[4];
+                // four features per step with 16-byte loads (the products still added in feature order)
+                for (int c = 0; c < kBC; c += 4) {
+                    float4 gv[4], sv[4];
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) gv[i] = Gs[(tp * 4 + i) * (kBC + 4) + c];
+                    for (int i = 0; i < 4; ++i) gv[i] = *reinterpret_cast<const float4*>(Gs + (tp * 4 + i) * (kBC + 4) + c);
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) sv[j] = Sc[(tl + 16 * j) * kSC + c];
+                    for (int j = 0; j < 4; ++j) sv[j] = *reinterpret_cast<const float4*>(Sc + (tl + 16 * j) * kSC + c);
 #pragma unroll
                     for (int i = 0; i < 4; ++i)
 #pragma unroll
-                        for (int j = 0; j < 4; ++j) dwacc[i][j] = fmaf(gv[i], sv[j], dwacc[i][j]);
+                        for (int j = 0; j < 4; ++j) {
+                            dwacc[i][j] = fmaf(gv[i].x, sv[j].x, dwacc[i][j]);
+                            dwacc[i][j] = fmaf(gv[i].y, sv[j].y, dwacc[i][j]);
+                            dwacc[i][j] = fmaf(gv[i].z, sv[j].z, dwacc[i][j]);
+                            dwacc[i][j] = fmaf(gv[i].w, sv[j].w, dwacc[i][j]);
+                        }
                 }
             }
         }
