@@ -485,9 +485,10 @@ def main():
     ap.add_argument("--no-fp32-path", action="store_true", help="skip the plain FP32 comparison measurement")
     ap.add_argument("--no-batched", action="store_true", help="skip the 16-view x 64-query batched measurement")
     ap.add_argument("--no-ablation", action="store_true", help="skip the sparse/dense and K speed ablation")
-    ap.add_argument("--profile", choices=["project", "bin", "splat", "decode", "query"], default=None,
+    ap.add_argument("--profile", choices=["project", "bin", "splat", "decode", "query", "backward"], default=None,
                     help="for a profiler capture: prepare the at-scale frame, then run only this stage "
-                         "(--warmup + --steps launches) with only the buffers it needs; prints one status line")
+                         "(--warmup + --steps launches) with only the buffers it needs; `backward` runs the "
+                         "training-step measurement of the differentiation workload instead; prints one status line")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)
@@ -505,6 +506,11 @@ def main():
         dist.init_process_group("nccl")
     assert args.warmup >= 3, "at least 3 warm-up steps"
     dev = torch.device("cuda", local)
+    if args.profile == "backward":
+        r = backward_section(dev, reps=args.steps)
+        print(json.dumps({"profile": "backward", "l1_decode_backward_ms": r["l1_decode_backward_ms"],
+                          "step_ms": r["step_ms"]}), flush=True)
+        return
 
     from paper_2507_07136_b300 import _lib as Lb
     sc, cam, text = syn.at_scale()
