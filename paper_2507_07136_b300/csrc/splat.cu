@@ -4,22 +4,27 @@
 // e_i = alpha_i prod_{j<i} (1 - alpha_j) of Eq. 7, only the K nonzero coefficients of each
 // level are blended: W_lev[idx_k] += w_k e_i.  Blending stays in FP32.
 //
-// Layout on the SM (one CTA per tile, one thread per pixel, warps independent):
-//  * Every warp owns the FP32 accumulators of its 32 pixels in shared memory as columns:
-//    acc[col][lane] with col = lev * 64 + idx and a stride of 33 floats.  The codebook index
-//    of a Gaussian is the same for every pixel of the tile, so a pair update is one
-//    conflict-free LDS / FFMA / STS on a warp-uniform column.  (Registers cannot be indexed
-//    by a runtime value on this architecture; a jump table would cost a uniform indirect
-//    branch per pair.)
-//  * Gaussians are staged per warp in batches of 32 records (one 16-byte-vector gather per
-//    lane, issued one batch ahead into registers).  Each lane tests its record's alpha >= 1/255 bounding box
-//    against the warp's pixel strip; a ballot keeps only the records that can touch the strip
-//    and the warp walks the set bits in list order ("warp-ballot culling").  Culling skips
-//    only work whose alpha is below 1/255 everywhere on the strip, so it changes no result.
+// Layout on the SM (warps independent within a tile, no block barrier in the blend):
+//  * One producer warp per CTA gathers the tile's records, 32 per batch, with bulk async copies
+//    into a ring of shared-memory stages (full / empty mbarriers, every wait bounded) and writes
+//    a compact culling box per record.
+//  * Each consumer warp covers an 8 x 4 pixel block, one pixel per lane.  Its FP32 accumulators
+//    are columns, col = lev * L + idx: in shared memory (acc[col][lane], a stride of 33 floats)
+//    or, for consumer warps 4-7 of the 16 x 16 CTA of splat_tm_kernel, in the warp's TMEM lane
+//    quarter (lane = pixel, TMEM column = col), so twice as many warps hide the blend's latency.
+//    The codebook index of a Gaussian is the same for every pixel of the tile, so a pair update is
+//    one conflict-free load / FFMA / store on a warp-uniform column.  (Registers cannot be
+//    indexed by a runtime value; a jump table would cost a uniform indirect branch per pair.)
+//  * A warp tests each record's alpha >= 1/255 box against its block; a ballot keeps the records
+//    that can touch it, walked in list order four at a time: alpha of the four in parallel (with
+//    the records' column offsets), the transmittance scan, then the accumulation of the records
+//    some lane takes.  Culling skips only work whose alpha is below 1/255 everywhere on the
+//    block, so it changes no result.
 //  * A pre-pass packs per-Gaussian records (2D mean pair, principal frame of the conic,
-//    opacity, weights, columns).  Repeated indices within one level are merged into one pair
-//    and the emptied repeats are stored first, so the loads of a record's pairs can all be
-//    issued before any store.
+//    opacity, weights, column offsets, culling extents).  Repeated indices within one level are
+//    merged into one pair, and the emptied repeats and invalid indices point at a dummy column,
+//    so a record's pairs carrying weight have distinct columns and all their loads can be issued
+//    before any store.
 #include "device.cuh"
 #include "splat.cuh"
 #include "splat_core.cuh"

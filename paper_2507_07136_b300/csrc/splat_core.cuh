@@ -1,7 +1,7 @@
 // splat_core.cuh -- the sparse-coefficient splat of one tile (Sec. 3.4, Algorithm 1; Eq. 3 and
-// Eq. 7 weights), shared by the plain splat kernels and the fused render kernel.  See splat.cu
-// for the design (producer warp + shared-memory ring of records, consumer warps with
-// accumulator columns in shared memory).
+// Eq. 7 weights), shared by the splat kernels and the fused render kernel.  See splat.cu for the
+// design (producer warp + shared-memory ring of records, consumer warps with accumulator columns
+// in shared memory or TMEM).
 #pragma once
 
 #include "device.cuh"
