@@ -100,6 +100,7 @@ __global__ void __launch_bounds__(256) l1_decode_backward_kernel(int64_t P, int 
                 for (int i = 0; i < 4; ++i)
 #pragma unroll
                     for (int j = 0; j < 8; ++j) f[i][j] = 0.0f;
+#pragma unroll 8
                 for (int l = 0; l < kL; ++l) {
                     const float4 a = *reinterpret_cast<const float4*>(Wt + l * (kBP + 4) + ty * 4);
                     const float4 b0 = *reinterpret_cast<const float4*>(Sc + l * kSC + tx * 4);
@@ -143,6 +144,7 @@ __global__ void __launch_bounds__(256) l1_decode_backward_kernel(int64_t P, int 
 #pragma unroll
                     for (int j = 0; j < 8; ++j) s[i][j] = 0.0f;
                 // four pixels per step: each W row read with one 16-byte load (pixel order kept)
+#pragma unroll 8
                 for (int p4 = 0; p4 < kBP; p4 += 4) {
                     float4 wq[4];
 #pragma unroll
@@ -177,6 +179,7 @@ __global__ void __launch_bounds__(256) l1_decode_backward_kernel(int64_t P, int 
             {
                 const int tl = tid & 15, tp = tid >> 4;
                 // four features per step with 16-byte loads (the products still added in feature order)
+#pragma unroll 8
                 for (int c = 0; c < kBC; c += 4) {
                     float4 gv[4], sv[4];
 #pragma unroll
