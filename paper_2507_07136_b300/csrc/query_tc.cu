@@ -85,6 +85,15 @@ __device__ __forceinline__ void convert_w(const float* src, int valid_rows, uint
     }
 }
 
+// BF16 relevancy from hk = tau / (2 |F|) and d = cos_pos - max cos_neg (in units of |F|): the
+// sigmoid through the hardware tanh, 1/2 + tanh(hk d) / 2
+__device__ __forceinline__ __nv_bfloat16 rel_bf16_of(float hk, float d)
+{
+    float th;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(th) : "f"(hk * d));
+    return __float2bfloat16_rn(fmaf(0.5f, th, 0.5f));
+}
+
 // NT threads: 256 when two CTAs share an SM (TMEM allows), else 512, so that the epilogue of the
 // one resident CTA has 16 warps (four per TMEM lane quarter).
 template <int NT>
@@ -135,22 +144,21 @@ __global__ void __launch_bounds__(NT, 512 / NT) query_tc_kernel(QueryTcArgs a)
         tc::mbar_init(tc::smem_u32(bar), 1);
         for (int s = 0; s < kStages; ++s) tc::mbar_init(tc::smem_u32(full + s), 1);
     }
-    // B^T rows (N x 64 K-major, swizzled): the 64 rows of S S^T, then the text rows permuted
-    // from query-major (64 + q per + t) to text-major (64 + t Qp + q); zero padding rows
+    // B^T rows (N x 64 K-major, swizzled): the 64 rows of S S^T, then the text rows S t / |t|
+    // (the text norm folded in before the BF16 rounding, as in query_pipe_kernel) permuted from
+    // query-major (64 + q per + t) to text-major (64 + t Qp + q); zero padding rows
     const float* Bl = a.Bt + (size_t)lev * (64 + a.Q * per) * kK;
     for (int i = tid; i < a.npad * kK; i += kThreads) {
         const int n = i >> 6, k = i & 63;
         int src = n < 64 ? n : -1;
+        float scale = 1.0f;
         if (n >= 64 && n < 64 + ntp) {
             const int t = (n - 64) / a.Qp, q = (n - 64) % a.Qp;
             src = q < a.Q ? 64 + q * per + t : -1;
+            if (q < a.Q) scale = 1.0f / a.tnorm[q * per + t];
         }
-        const float v = src >= 0 ? Bl[(size_t)src * kK + k] : 0.0f;
+        const float v = src >= 0 ? Bl[(size_t)src * kK + k] * scale : 0.0f;
         *reinterpret_cast<__nv_bfloat16*>(sB + tc::sw128(n, k)) = __float2bfloat16_rn(v);
-    }
-    for (int i = tid; i < ntp; i += kThreads) {   // reciprocal norms, text-major
-        const int t = i / a.Qp, q = i % a.Qp;
-        sTn[i] = q < a.Q ? 1.0f / a.tnorm[q * per + t] : 0.0f;
     }
     tc::fence_proxy_async();
     tc::fence_before();
@@ -223,22 +231,18 @@ __global__ void __launch_bounds__(NT, 512 / NT) query_tc_kernel(QueryTcArgs a)
             const int q0 = c * 8;
             uint32_t rp[8], rn[8];
             tc::tmem_ld8(trow + (uint32_t)(64 + q0), rp);
+            // the products are <F, t> / |t| (B's text rows carry 1/|t|): the same arithmetic as
+            // query_pipe_kernel, so both give the same relevancy from the same W
             float best[8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) best[j] = -INFINITY;
+            for (int j = 0; j < 8; ++j) best[j] = per > 1 ? -INFINITY : 0.0f;
             for (int t = 1; t < per; ++t) {
                 tc::tmem_ld8(trow + (uint32_t)(64 + t * a.Qp + q0), rn);
                 tc::tmem_wait_ld();
-                const float4 u0 = *reinterpret_cast<const float4*>(sTn + t * a.Qp + q0);
-                const float4 u1 = *reinterpret_cast<const float4*>(sTn + t * a.Qp + q0 + 4);
-                const float tn[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
 #pragma unroll
-                for (int j = 0; j < 8; ++j) best[j] = fmaxf(best[j], __uint_as_float(rn[j]) * tn[j]);
+                for (int j = 0; j < 8; ++j) best[j] = fmaxf(best[j], __uint_as_float(rn[j]));
             }
             tc::tmem_wait_ld();
-            const float4 u0 = *reinterpret_cast<const float4*>(sTn + q0);
-            const float4 u1 = *reinterpret_cast<const float4*>(sTn + q0 + 4);
-            const float tp[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
             if (p < Pv) {
                 // rel = sigmoid(-kneg d); the element of query q is o0 + q stride
                 const size_t stride = (size_t)a.levels * Pv;
@@ -252,17 +256,14 @@ __global__ void __launch_bounds__(NT, 512 / NT) query_tc_kernel(QueryTcArgs a)
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
                         if (j >= nq) break;
-                        const float d = __uint_as_float(rp[j]) * tp[j] - (per > 1 ? best[j] : 0.0f);
-                        float th;
-                        asm("tanh.approx.f32 %0, %1;" : "=f"(th) : "f"(hk * d));
-                        out[(size_t)j * stride] = __float2bfloat16_rn(fmaf(0.5f, th, 0.5f));
+                        out[(size_t)j * stride] = rel_bf16_of(hk, __uint_as_float(rp[j]) - best[j]);
                     }
                 } else {
                     float* out = static_cast<float*>(a.rel) + o0;
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
                         if (j >= nq) break;
-                        const float d = __uint_as_float(rp[j]) * tp[j] - (per > 1 ? best[j] : 0.0f);
+                        const float d = __uint_as_float(rp[j]) - best[j];
                         out[(size_t)j * stride] = __fdividef(1.0f, 1.0f + __expf(kneg * d));
                     }
                 }
@@ -323,14 +324,6 @@ __device__ __forceinline__ bool pipe_wait(uint32_t bar, uint32_t parity, volatil
 
 // NB: epilogue warpgroups = TMEM accumulators (a template parameter, so that the per-tile ring
 // and phase arithmetic divides by constants).
-// BF16 relevancy from hk = tau / (2 |F|) and d = cos_pos - max cos_neg (in units of |F|): the
-// sigmoid through the hardware tanh, 1/2 + tanh(hk d) / 2
-__device__ __forceinline__ __nv_bfloat16 rel_bf16_of(float hk, float d)
-{
-    float th;
-    asm("tanh.approx.f32 %0, %1;" : "=f"(th) : "f"(hk * d));
-    return __float2bfloat16_rn(fmaf(0.5f, th, 0.5f));
-}
 
 template <int NB>
 __global__ void __launch_bounds__(64 + 128 * NB, 1) query_pipe_kernel(const __grid_constant__ CUtensorMap tmW, QueryTcArgs a)
