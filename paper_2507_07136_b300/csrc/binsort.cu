@@ -251,22 +251,10 @@ __global__ void __launch_bounds__(128) sort_warp_kernel(int T, const uint32_t* t
     }
 }
 
-// Tiles of kWarpCap < n <= kSmallCap keys: one block, bitonic in shared memory.
-__global__ void __launch_bounds__(256) sort_small_kernel(const uint32_t* tile_ranges,
-                                                         const unsigned long long* keys, uint32_t* ids)
-{
-    __shared__ unsigned long long s[kSmallCap];
-    const uint32_t b = tile_ranges[2 * blockIdx.x], e = tile_ranges[2 * blockIdx.x + 1];
-    const int n = (int)(e - b);
-    if (n <= kWarpCap || n > kSmallCap) return;
-    int np = 2;
-    while (np < n) np <<= 1;
-    for (int i = threadIdx.x; i < np; i += blockDim.x) s[i] = i < n ? keys[b + i] : ~0ull;
-    __syncthreads();
-    bitonic_smem(s, np);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) ids[b + i] = (uint32_t)s[i];
-}
-
+// Tiles of kWarpCap < n <= kSmallCap keys: one block of four warps.  Warp r sorts keys
+// [512 r, 512 r + 512) of the tile in registers (warp_bitonic), the runs go to shared memory, and
+// each key's place in the tile is its index in its run plus the number of smaller keys in each
+// other run (a binary search per run; keys are unique, so the places are).  Two barriers in all.
 __device__ __forceinline__ int lower_rank(const unsigned long long* r, int len, unsigned long long key)
 {
     int lo = 0, hi = len;
@@ -277,6 +265,42 @@ __device__ __forceinline__ int lower_rank(const unsigned long long* r, int len, 
     }
     return lo;
 }
+
+__global__ void __launch_bounds__(128) sort_small_kernel(const uint32_t* tile_ranges,
+                                                         const unsigned long long* keys, uint32_t* ids)
+{
+    __shared__ unsigned long long s[kSmallCap];
+    const uint32_t b = tile_ranges[2 * blockIdx.x], e = tile_ranges[2 * blockIdx.x + 1];
+    const int n = (int)(e - b);
+    if (n <= kWarpCap || n > kSmallCap) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nruns = (n + kWarpCap - 1) / kWarpCap;
+    if (warp < nruns) {
+        unsigned long long x[kWarpCap / 32];
+#pragma unroll
+        for (int j = 0; j < kWarpCap / 32; ++j) {
+            const int i = warp * kWarpCap + lane * (kWarpCap / 32) + j;
+            x[j] = i < n ? keys[b + i] : ~0ull;
+        }
+        warp_bitonic<kWarpCap / 32>(x, lane);
+#pragma unroll
+        for (int j = 0; j < kWarpCap / 32; ++j) s[warp * kWarpCap + lane * (kWarpCap / 32) + j] = x[j];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        // the i-th key in run order (runs hold n keys in all, padding at the end of the last run)
+        const int r = i / kWarpCap, p = i - r * kWarpCap;
+        const unsigned long long k = s[i];
+        int place = p;
+        for (int q = 0; q < nruns; ++q) {
+            if (q == r) continue;
+            const int len = q == nruns - 1 ? n - q * kWarpCap : kWarpCap;
+            place += lower_rank(s + q * kWarpCap, len, k);
+        }
+        ids[b + place] = (uint32_t)k;
+    }
+}
+
 
 // Persistent over the list of large tiles.
 __global__ void __launch_bounds__(1024) sort_large_kernel(const uint32_t* tile_ranges, const uint32_t* big,
@@ -399,7 +423,7 @@ cudaError_t launch_binsort_views(const BinSortViews& a, cudaStream_t stream)
     scan_kernel<<<1, 1024, 0, stream>>>(Tt, total, start, a.tile_ranges, a.capacity, a.num_instances, big, a.status);
     scatter_kernel<<<grid, kGB, cnt_smem, stream>>>(a, vd, hist, start, keys);
     sort_warp_kernel<<<(Tt + 3) / 4, 128, 0, stream>>>((int)Tt, a.tile_ranges, keys, a.gauss_ids);
-    sort_small_kernel<<<Tt, 256, 0, stream>>>(a.tile_ranges, keys, a.gauss_ids);
+    sort_small_kernel<<<Tt, 128, 0, stream>>>(a.tile_ranges, keys, a.gauss_ids);
     const int large_smem = kChunk * 8;
     e = cudaFuncSetAttribute(sort_large_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, large_smem);
     if (e != cudaSuccess) return e;

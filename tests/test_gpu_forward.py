@@ -203,6 +203,28 @@ def test_crowded_tiles_three_levels(opacity):
     check_blend(fr, ref.blend, px, py, cam)
 
 
+def test_medium_tiles_three_levels():
+    """Tiles of 513 to 2,048 instances (sorted by four warps in registers and merged by rank):
+    bins bit-exact and the blend against the oracle."""
+    rng = np.random.default_rng(22)
+    n = 2000
+    means = np.stack([rng.uniform(-0.35, 0.35, n), rng.uniform(-0.35, 0.35, n), rng.uniform(-0.5, 0.5, n)],
+                     1).astype(np.float32)
+    scales = np.exp(rng.normal(-3.4, 0.3, (n, 3))).astype(np.float32)
+    q = rng.normal(size=(n, 4))
+    q = (q / np.linalg.norm(q, axis=1, keepdims=True)).astype(np.float32)
+    idx, w = syn.sparse_coefficients(rng, n, 3, 4, 64)
+    sc = syn.Scene(means, scales, q, np.full(n, 0.5, np.float32), idx, w, syn.codebooks(5, 3))
+    cam = syn.orbit_camera(64, 48, 4.0)
+    ref = O.render(sc, cam)
+    counts = np.diff(ref.ranges.reshape(-1, 2), axis=1)[:, 0]
+    assert int(((counts > 512) & (counts <= 2048)).sum()) >= 2, "the scene should give medium tiles"
+    ds, fr = gpu_frame(sc, cam)
+    check_bins(fr, ref.ids, ref.ranges)
+    px, py = O.all_pixels(cam)
+    check_blend(fr, ref.blend, px, py, cam)
+
+
 def test_repeated_indices_three_levels():
     """Three levels (TMEM-accumulator kernel): repeated indices in every level are merged into one
     pair and the emptied repeats accumulate nothing, whichever accumulator store a pixel's warp
