@@ -161,26 +161,6 @@ __global__ void __launch_bounds__(kGB) scatter_kernel(BinSortViews a, ViewsDev v
         }
 }
 
-__device__ void bitonic_smem(unsigned long long* s, int npow2)
-{
-    for (int k = 2; k <= npow2; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < npow2; i += blockDim.x) {
-                const int ixj = i ^ j;
-                if (ixj > i) {
-                    const unsigned long long x = s[i], y = s[ixj];
-                    const bool up = (i & k) == 0;
-                    if ((x > y) == up) {
-                        s[i] = y;
-                        s[ixj] = x;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    }
-}
-
 // Bitonic sorting network over 32 K keys held by one warp, key i = lane * K + j in register j:
 // partners i ^ m with m < K are registers of the same lane, the others (m >= K) are exchanged
 // with lane ^ (m / K) by shuffles.  Ascending on return.
@@ -315,14 +295,35 @@ __global__ void __launch_bounds__(1024) sort_large_kernel(const uint32_t* tile_r
         const int n = (int)(e - b);
         unsigned long long* src = keys + b;
         unsigned long long* dst = alt + b;
+        // each chunk: runs of kWarpCap keys sorted by warps in registers, then every key placed at
+        // its index in its run plus the count of smaller keys in the chunk's other runs
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
         for (int c0 = 0; c0 < n; c0 += kChunk) {
             const int len = min(kChunk, n - c0);
-            int np = 2;
-            while (np < len) np <<= 1;
-            for (int i = threadIdx.x; i < np; i += blockDim.x) sk[i] = i < len ? src[c0 + i] : ~0ull;
+            const int nruns = (len + kWarpCap - 1) / kWarpCap;
+            if (warp < nruns) {
+                unsigned long long x[kWarpCap / 32];
+#pragma unroll
+                for (int j = 0; j < kWarpCap / 32; ++j) {
+                    const int i = warp * kWarpCap + lane * (kWarpCap / 32) + j;
+                    x[j] = i < len ? src[c0 + i] : ~0ull;
+                }
+                warp_bitonic<kWarpCap / 32>(x, lane);
+#pragma unroll
+                for (int j = 0; j < kWarpCap / 32; ++j) sk[warp * kWarpCap + lane * (kWarpCap / 32) + j] = x[j];
+            }
             __syncthreads();
-            bitonic_smem(sk, np);
-            for (int i = threadIdx.x; i < len; i += blockDim.x) src[c0 + i] = sk[i];
+            for (int i = threadIdx.x; i < len; i += blockDim.x) {
+                const int r = i / kWarpCap, p = i - r * kWarpCap;
+                const unsigned long long k = sk[i];
+                int place = p;
+                for (int q = 0; q < nruns; ++q) {
+                    if (q == r) continue;
+                    const int qlen = q == nruns - 1 ? len - q * kWarpCap : kWarpCap;
+                    place += lower_rank(sk + q * kWarpCap, qlen, k);
+                }
+                src[c0 + place] = k;
+            }
             __syncthreads();
         }
         for (int run = kChunk; run < n; run <<= 1) {
