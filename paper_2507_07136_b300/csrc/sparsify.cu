@@ -7,13 +7,15 @@
 // equal logits) and takes the softmax of those, and the gradient is zero for the dropped logits
 // and w_k (dw_k - sum_m w_m dw_m) for kept entry k (the selection is piecewise constant).
 //
-// One row of L logits per thread.  A block stages its rows in shared memory with coalesced
-// asynchronous copies (rows padded by one word: conflict-free per-thread row reads).  The forward
-// selects with a sorting network over groups of 8 logits and a bitonic merge into the running K
-// (branch-free; one total order, the larger value and then the lower index, so the selection is
-// unique) and writes idx (K bytes) and w (K floats) per row.  The backward scatters the K
-// gradients into a zeroed staged row and writes the rows out coalesced: it is HBM-bound (4 L
-// bytes per row out); the forward reads as many bytes and is bound by the selection's arithmetic.
+// Forward: a row of L logits is split over L / 16 adjacent threads of a warp, each loading its
+// 16 logits straight from global memory (four 16-byte loads; no staging, no block barrier).  A
+// thread sorts its two groups of 8 with Batcher's 19-comparator network and keeps the first K of
+// their union; the row's threads then exchange their K by shuffles (butterfly: both partners end
+// with the same K) until every thread holds the row's K.  One total order throughout (the larger
+// value, then the lower index), so the selection is unique, and every step is branch-free.  The
+// first thread of the row writes idx (K bytes) and w (K floats).  The backward (one row per
+// thread) scatters the K gradients into a zeroed row staged in shared memory (rows padded by one
+// word: conflict-free) and writes the rows out coalesced: it is HBM-bound (4 L bytes per row out).
 #include "device.cuh"
 
 namespace lsv2 {
@@ -22,20 +24,7 @@ namespace {
 template <int L>
 __host__ __device__ constexpr int rows_per_block() { return L <= 64 ? 128 : 32; }
 
-// row r0 + i of a [rows][L] float array <-> staged row i (stride L + 1).  Loads are asynchronous
-// 4-byte copies, all in flight at once (the padded rows are not 16-byte aligned).
-template <int L, int R>
-__device__ __forceinline__ void stage_in(const float* src, int64_t r0, int nr, float* zs)
-{
-    const float* g = src + r0 * L;
-    for (int i = threadIdx.x; i < nr * L; i += R)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
-                         (uint32_t)__cvta_generic_to_shared(zs + (i / L) * (L + 1) + (i % L))),
-                     "l"(g + i)
-                     : "memory");
-    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
-}
-
+// staged row i (stride L + 1) -> row r0 + i of a [rows][L] float array, coalesced
 template <int L, int R>
 __device__ __forceinline__ void stage_out(float* dst, int64_t r0, int nr, const float* zs)
 {
@@ -74,57 +63,95 @@ __device__ __forceinline__ void store_row(uint8_t* idx, float* w, int64_t r, con
     }
 }
 
-template <int L, int K>
-__global__ void __launch_bounds__(rows_per_block<L>()) sparsify_kernel(int64_t rows, const float* __restrict__ z,
-                                                                       uint8_t* __restrict__ idx, float* __restrict__ w)
+// (v, ix) and (u, iu) each hold K entries in rank order; leave the K first of their union in
+// (v, ix), in rank order: the better of v[i] and u[K-1-i] form a bitonic sequence, which the
+// half-cleaners sort.
+template <int K>
+__device__ __forceinline__ void merge_first(float (&v)[K], int (&ix)[K], const float (&u)[K], const int (&iu)[K])
 {
-    constexpr int R = rows_per_block<L>();
-    extern __shared__ float zs[];
-    const int64_t r0 = (int64_t)blockIdx.x * R;
-    const int nr = rows - r0 < R ? (int)(rows - r0) : R;
-    stage_in<L, R>(z, r0, nr, zs);
-    __syncthreads();
-    if ((int)threadIdx.x >= nr) return;
-    const float* row = zs + threadIdx.x * (L + 1);
-    // the K first entries in the order (larger value, then lower index), branch-free: each group
-    // of 8 logits is sorted by Batcher's 19-comparator network, and its first K are merged into
-    // the running K (the better of v[i] and the group's (K-1-i)th is a bitonic sequence, which
-    // the half-cleaners sort).  One total order throughout, so the selection is unique.
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        const bool take = ranks_before(u[K - 1 - i], iu[K - 1 - i], v[i], ix[i]);
+        v[i] = take ? u[K - 1 - i] : v[i];
+        ix[i] = take ? iu[K - 1 - i] : ix[i];
+    }
+#pragma unroll
+    for (int m = K / 2; m > 0; m >>= 1)
+#pragma unroll
+        for (int i = 0; i < K; ++i)
+            if ((i & m) == 0) order_pair(v[i], ix[i], v[i | m], ix[i | m]);
+}
+
+// sort 8 (value, index) pairs into rank order with Batcher's odd-even merge network
+__device__ __forceinline__ void sort8(float (&gv)[8], int (&gi)[8])
+{
     constexpr int kNet8[19][2] = {{0, 1}, {2, 3}, {4, 5}, {6, 7}, {0, 2}, {1, 3}, {4, 6}, {5, 7}, {1, 2}, {5, 6},
                                   {0, 4}, {1, 5}, {2, 6}, {3, 7}, {2, 4}, {3, 5}, {1, 2}, {3, 4}, {5, 6}};
-    float v[K];
-    int ix[K];
-#pragma unroll 1
-    for (int g = 0; g < L; g += 8) {
-        float gv[8];
-        int gi[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            gv[j] = row[g + j];
-            gi[j] = g + j;
+    for (int c = 0; c < 19; ++c) order_pair(gv[kNet8[c][0]], gi[kNet8[c][0]], gv[kNet8[c][1]], gi[kNet8[c][1]]);
+}
+
+constexpr int kFwdThreads = 256;
+constexpr int kPerThread = 16;   // logits per thread: two groups of 8
+
+template <int L, int K>
+__global__ void __launch_bounds__(kFwdThreads) sparsify_kernel(int64_t rows, const float* __restrict__ z,
+                                                               uint8_t* __restrict__ idx, float* __restrict__ w)
+{
+    constexpr int T = L / kPerThread;   // threads per row, adjacent lanes of one warp
+    static_assert(L % kPerThread == 0 && (T & (T - 1)) == 0 && T <= 32 && K <= 8, "row split");
+    const int64_t t = (int64_t)blockIdx.x * kFwdThreads + threadIdx.x;
+    const int64_t r = t / T;
+    const int part = (int)(t % T);
+    // threads past the last row work on the last row (their shuffles keep the warp converged)
+    // and store nothing
+    const float* src = z + (r < rows ? r : rows - 1) * L + part * kPerThread;
+    float x[kPerThread];
+    if ((reinterpret_cast<uintptr_t>(z) & 15) == 0) {
+#pragma unroll
+        for (int j = 0; j < kPerThread / 4; ++j) {
+            const float4 q = __ldcs(reinterpret_cast<const float4*>(src) + j);
+            x[4 * j] = q.x;
+            x[4 * j + 1] = q.y;
+            x[4 * j + 2] = q.z;
+            x[4 * j + 3] = q.w;
         }
+    } else {
 #pragma unroll
-        for (int c = 0; c < 19; ++c) order_pair(gv[kNet8[c][0]], gi[kNet8[c][0]], gv[kNet8[c][1]], gi[kNet8[c][1]]);
-        if (g == 0) {
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                v[k] = gv[k];
-                ix[k] = gi[k];
-            }
-        } else {
-#pragma unroll
-            for (int i = 0; i < K; ++i) {
-                const bool take = ranks_before(gv[K - 1 - i], gi[K - 1 - i], v[i], ix[i]);
-                v[i] = take ? gv[K - 1 - i] : v[i];
-                ix[i] = take ? gi[K - 1 - i] : ix[i];
-            }
-#pragma unroll
-            for (int m = K / 2; m > 0; m >>= 1)
-#pragma unroll
-                for (int i = 0; i < K; ++i)
-                    if ((i & m) == 0) order_pair(v[i], ix[i], v[i | m], ix[i | m]);
-        }
+        for (int j = 0; j < kPerThread; ++j) x[j] = __ldcs(src + j);
     }
+    const int base = part * kPerThread;
+    float gv[8], hv[8];
+    int gi[8], hi[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        gv[j] = x[j];
+        gi[j] = base + j;
+        hv[j] = x[8 + j];
+        hi[j] = base + 8 + j;
+    }
+    sort8(gv, gi);
+    sort8(hv, hi);
+    float v[K], u[K];
+    int ix[K], iu[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        v[k] = gv[k];
+        ix[k] = gi[k];
+        u[k] = hv[k];
+        iu[k] = hi[k];
+    }
+    merge_first<K>(v, ix, u, iu);
+#pragma unroll
+    for (int m = 1; m < T; m <<= 1) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            u[k] = __shfl_xor_sync(0xffffffffu, v[k], m);
+            iu[k] = __shfl_xor_sync(0xffffffffu, ix[k], m);
+        }
+        merge_first<K>(v, ix, u, iu);
+    }
+    if (part != 0 || r >= rows) return;
     // softmax over the kept logits (v[0] is the largest)
     float e[K], s = 0.0f;
 #pragma unroll
@@ -135,7 +162,7 @@ __global__ void __launch_bounds__(rows_per_block<L>()) sparsify_kernel(int64_t r
     float wv[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) wv[k] = e[k] / s;
-    store_row<K>(idx, w, r0 + threadIdx.x, ix, wv);
+    store_row<K>(idx, w, r, ix, wv);
 }
 
 template <int L, int K>
@@ -184,9 +211,8 @@ cudaError_t launch_sparsify_t(int64_t rows, const float* z, uint8_t* idx, float*
         if (e != cudaSuccess) return e;
         sparsify_backward_kernel<L, K><<<(unsigned)blocks, R, smem, stream>>>(rows, idx, w, dw, dz);
     } else {
-        cudaError_t e = cudaFuncSetAttribute(sparsify_kernel<L, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        sparsify_kernel<L, K><<<(unsigned)blocks, R, smem, stream>>>(rows, z, idx, w);
+        const int64_t fwd_blocks = (rows * (L / kPerThread) + kFwdThreads - 1) / kFwdThreads;
+        sparsify_kernel<L, K><<<(unsigned)fwd_blocks, kFwdThreads, 0, stream>>>(rows, z, idx, w);
     }
     return cudaGetLastError();
 }
