@@ -462,6 +462,14 @@ def profile_stage(args, frame, scene, text, dev):
         def fn():
             Lb.lsv2_decode(1, P, L_CODEBOOK, D, _ptr(frame.coeff16), Lb.LSV2_BF16, _ptr(cb16), Lb.LSV2_BF16, _ptr(F),
                            Lb.LSV2_BF16, _ptr(frame.status), stream)
+    elif args.profile == "query32":
+        # the batched path's query group: 32 queries x (1 + 4 negatives), BF16 relevancy out
+        g = torch.Generator(device=dev).manual_seed(11)
+        text_d = torch.randn((32, text.shape[1], D), generator=g, device=dev)
+        rel = torch.empty((32, scene.levels, P), dtype=torch.bfloat16, device=dev)
+
+        def fn():
+            frame.query(text_d, rel, compute=Lb.LSV2_BF16, from_bf16=True)
     else:
         text_d = torch.as_tensor(text, device=dev)
         rel = torch.empty((text.shape[0], scene.levels, P), dtype=torch.float32, device=dev)
@@ -485,7 +493,7 @@ def main():
     ap.add_argument("--no-fp32-path", action="store_true", help="skip the plain FP32 comparison measurement")
     ap.add_argument("--no-batched", action="store_true", help="skip the 16-view x 64-query batched measurement")
     ap.add_argument("--no-ablation", action="store_true", help="skip the sparse/dense and K speed ablation")
-    ap.add_argument("--profile", choices=["project", "bin", "splat", "decode", "query", "backward"], default=None,
+    ap.add_argument("--profile", choices=["project", "bin", "splat", "decode", "query", "query32", "backward"], default=None,
                     help="for a profiler capture: prepare the at-scale frame, then run only this stage "
                          "(--warmup + --steps launches) with only the buffers it needs; `backward` runs the "
                          "training-step measurement of the differentiation workload instead; prints one status line")

@@ -82,6 +82,26 @@ def test_sparsify_at_scale_sampled():
     check_rows(z[pick], K, idx.cpu().numpy()[pick], w.cpu().numpy()[pick], dw[pick], dz[pick])
 
 
+@pytest.mark.parametrize("Lz", [16, 64, 256])
+def test_sparsify_unaligned_logits(Lz):
+    """Logits that start one float into their buffer (4-byte, not 16-byte aligned) take the
+    kernel's scalar loads; a ragged row count leaves a partial warp at the end."""
+    rng = np.random.default_rng(Lz + 3)
+    rows, K = 517, 4
+    z = logits(rng, rows, Lz)
+    buf = torch.empty(rows * Lz + 4, device="cuda")
+    buf[1:1 + rows * Lz] = torch.as_tensor(z.ravel(), device="cuda")
+    zt = buf[1:1 + rows * Lz]
+    assert zt.data_ptr() % 16 != 0
+    idx = torch.full((rows, K), 255, dtype=torch.uint8, device="cuda")
+    w = torch.full((rows, K), float("nan"), device="cuda")
+    L.lsv2_sparsify(rows, Lz, K, _ptr(zt), _ptr(idx), _ptr(w), None)
+    torch.cuda.synchronize()
+    oi, ow = O.sparsify(z, K)
+    assert np.array_equal(idx.cpu().numpy(), oi)
+    np.testing.assert_allclose(w.cpu().numpy(), ow, rtol=1e-6, atol=1e-7)
+
+
 def test_sparsify_edges():
     z = torch.zeros((1, 64), device="cuda")
     idx = torch.empty((1, 4), dtype=torch.uint8, device="cuda")
