@@ -493,7 +493,7 @@ def main():
     ap.add_argument("--no-fp32-path", action="store_true", help="skip the plain FP32 comparison measurement")
     ap.add_argument("--no-batched", action="store_true", help="skip the 16-view x 64-query batched measurement")
     ap.add_argument("--no-ablation", action="store_true", help="skip the sparse/dense and K speed ablation")
-    ap.add_argument("--profile", choices=["project", "bin", "splat", "decode", "query", "query32", "backward"], default=None,
+    ap.add_argument("--profile", choices=["project", "bin", "splat", "decode", "query", "query32", "backward", "sparsify"], default=None,
                     help="for a profiler capture: prepare the at-scale frame, then run only this stage "
                          "(--warmup + --steps launches) with only the buffers it needs; `backward` runs the "
                          "training-step measurement of the differentiation workload instead; prints one status line")
@@ -518,6 +518,11 @@ def main():
         r = backward_section(dev, reps=args.steps)
         print(json.dumps({"profile": "backward", "l1_decode_backward_ms": r["l1_decode_backward_ms"],
                           "step_ms": r["step_ms"]}), flush=True)
+        return
+    if args.profile == "sparsify":
+        r = sparsify_section(dev, reps=args.steps)
+        print(json.dumps({"profile": "sparsify", "forward_ms": r["forward_ms"], "backward_ms": r["backward_ms"],
+                          "device_gb": round(torch.cuda.max_memory_allocated(dev) / 1e9, 2)}), flush=True)
         return
 
     from paper_2507_07136_b300 import _lib as Lb
