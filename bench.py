@@ -62,49 +62,106 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms while the timed region runs."""
+    """SM clock, power and clock-event (throttle) reasons sampled while the timed region runs.
 
+    Polls NVML from a thread every `period_s` (read-only queries, a few microseconds each), so a
+    timed region of a few tens of milliseconds still gets samples; falls back to `nvidia-smi -lms`
+    when NVML is unavailable.  The device is found by its PCI bus id, so the NVML index need not
+    equal the CUDA ordinal."""
+
+    REASONS = [("hw_slowdown", "nvmlClocksEventReasonHwSlowdown"),
+               ("hw_thermal_slowdown", "nvmlClocksEventReasonHwThermalSlowdown"),
+               ("sw_thermal_slowdown", "nvmlClocksEventReasonSwThermalSlowdown"),
+               ("sw_power_cap", "nvmlClocksEventReasonSwPowerCap"),
+               ("hw_power_brake_slowdown", "nvmlClocksEventReasonHwPowerBrakeSlowdown")]
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
-        self.index, self.rows, self.proc = index, [], None
+    def __init__(self, cuda_index: int, period_s: float = 0.005):
+        self.index, self.period = cuda_index, period_s
+        self.rows = []          # (sm_mhz, max_mhz, power_w, set of reason names)
+        self.proc = self.thread = None
+        self.stop = threading.Event()
+        self.source = "none"
+
+    def _nvml_handle(self):
+        import pynvml
+        pynvml.nvmlInit()
+        try:
+            import torch
+            pr = torch.cuda.get_device_properties(self.index)
+            bus = f"{pr.pci_domain_id:08X}:{pr.pci_bus_id:02X}:{pr.pci_device_id:02X}.0"
+            return pynvml, pynvml.nvmlDeviceGetHandleByPciBusId(bus)
+        except Exception:
+            return pynvml, pynvml.nvmlDeviceGetHandleByIndex(self.index)
+
+    def _poll_nvml(self, nv, h):
+        mx = nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM)
+        bits = [(name, getattr(nv, const, 0)) for name, const in self.REASONS]
+        while not self.stop.is_set():
+            try:
+                sm = nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM)
+                pw = nv.nvmlDeviceGetPowerUsage(h) / 1000.0
+                rs = nv.nvmlDeviceGetCurrentClocksEventReasons(h)
+                self.rows.append((float(sm), float(mx), pw, {n for n, b in bits if b and rs & b}))
+            except Exception:
+                pass
+            self.stop.wait(self.period)
+
+    def _read_smi(self):
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.proc.stdout:
+            p = [x.strip() for x in line.split(",")]
+            if len(p) == 7:
+                try:
+                    self.rows.append((float(p[0]), float(p[1]), float(p[2]),
+                                      {names[i] for i in range(4) if p[3 + i].lower() == "active"}))
+                except ValueError:
+                    pass
 
     def __enter__(self):
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
-                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
-            self.t.start()
+            nv, h = self._nvml_handle()
+            self.thread = threading.Thread(target=self._poll_nvml, args=(nv, h), daemon=True)
+            self.source = "nvml"
         except Exception:
-            self.proc = None
+            try:
+                self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                              "--format=csv,noheader,nounits", "-lms", "100"],
+                                             stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                self.thread = threading.Thread(target=self._read_smi, daemon=True)
+                self.source = "nvidia-smi"
+            except Exception:
+                self.thread = None
+        if self.thread:
+            self.thread.start()
+            if self.source == "nvidia-smi":   # wait (bounded) for its first row
+                t0 = time.time()
+                while not self.rows and time.time() - t0 < 5.0:
+                    time.sleep(0.05)
         return self
 
-    def _read(self):
-        for line in self.proc.stdout:
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) == 7:
-                self.rows.append(parts)
-
     def __exit__(self, *a):
+        self.stop.set()
         if self.proc:
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
 
     def summary(self):
         if not self.rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
-        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i].lower() == "active"})
-        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.rows)}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0,
+                    "source": self.source}
+        sm = [r[0] for r in self.rows]
+        reasons = sorted(set().union(*[r[3] for r in self.rows]))
+        return {"sm_mhz": float(np.median(sm)), "sm_min_mhz": float(min(sm)),
+                "sm_max_mhz": max(r[1] for r in self.rows), "power_w_max": max(r[2] for r in self.rows),
+                "reasons": reasons, "samples": len(self.rows), "source": self.source}
 
 
 def dist_env():
@@ -114,20 +171,78 @@ def dist_env():
     return rank, world, local
 
 
+def spawn_ranks(gpus: int, argv) -> int | None:
+    """`--gpus N` outside a launcher: run this script as N ranks of one node under
+    torch.distributed.run (rendezvous on 127.0.0.1, a free port) and return their exit code.
+    Returns None when no launch is needed (N = 1, or already running as a rank)."""
+    if gpus <= 1 or "WORLD_SIZE" in os.environ:
+        return None
+    import socket
+    with socket.socket() as so:
+        so.bind(("127.0.0.1", 0))
+        port = so.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={gpus}",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__)] + list(argv)
+    return subprocess.call(cmd)
+
+
+def max_over_ranks(values, world: int, device=None):
+    """Element-wise maximum of a list of floats over all ranks (one all_reduce(MAX); the identity
+    for one rank).  `device` is where the reduction tensor lives: a CUDA device for NCCL, None
+    (CPU) for gloo."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def host_cpu():
+    """CPU model and logical core count of this host (for the CPU-baseline record)."""
+    model = "unknown"
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"cpu": model, "nproc": os.cpu_count()}
+
+
 # ----------------------------------------------------------------------------- CPU baseline
-def cpu_baseline(max_seconds: float = 20.0):
-    """The FP64 oracle as it stands, single-threaded, on a bounded sample of one frame:
-    projection + binning of all 300k Gaussians, then blend + decode + relevancy of a random
-    pixel sample, scaled to the full 1,555,200-pixel frame."""
+def cpu_tiny_full_frame():
+    """The FP64 oracle on one whole frame of the tiny scene (2,000 Gaussians, 128x96, one level,
+    one query with four negatives): projection, binning, the blend of every pixel, decode and
+    relevancy, timed as it runs (no sampling, no extrapolation)."""
     import lsv2_synth as syn
     from oracle import oracle as O
-    sc, cam, text = syn.at_scale()
+    sc, cam = syn.tiny()
+    text = syn.text_queries(syn.SEED + 2, 1, 4)
+    t0 = time.perf_counter()
+    r = O.render(sc, cam)
+    O.relevancy(O.decode(r.blend.out, sc.codebook), text, 10.0)
+    s = time.perf_counter() - t0
+    return {"frame_s": s, "frames_per_s": 1.0 / s, "workload": "2,000 Gaussians, 1 level, 128x96, 1 query + 4 "
+            "negatives: project, bin, blend of all 12,288 pixels, decode, relevancy (whole frame, timed)"}
+
+
+def cpu_baseline(npix: int = 2000, at_scale=None):
+    """The FP64 oracle as it stands, single-threaded, on a bounded sample of one at-scale frame:
+    projection + binning of all 300k Gaussians, then blend + decode + relevancy of `npix` random
+    pixels.  `value` estimates the oracle's whole-frame rate (the per-pixel time scaled to the
+    1,555,200-pixel frame); `sample_s` is the time this sample took."""
+    import lsv2_synth as syn
+    from oracle import oracle as O
+    sc, cam, text = at_scale if at_scale is not None else syn.at_scale()
     t0 = time.perf_counter()
     pr = O.project(cam, sc.means, sc.scales, sc.quats)
     ids, ranges = O.bin(cam, pr)
     t_geom = time.perf_counter() - t0
     rng = np.random.default_rng(0)
-    npix = 2000
     px = rng.integers(0, cam.width, npix).astype(np.int32)
     py = rng.integers(0, cam.height, npix).astype(np.int32)
     t1 = time.perf_counter()
@@ -137,30 +252,42 @@ def cpu_baseline(max_seconds: float = 20.0):
     t_pix = (time.perf_counter() - t1) / npix
     frame_s = t_geom + t_pix * cam.num_pixels
     return {"value": 1.0 / frame_s, "unit": "frames/s", "cores": 1, "kind": "oracle",
+            "sample_s": t_geom + t_pix * npix, "frame_fraction": (t_geom + t_pix * npix) / frame_s,
             "sample": f"project+bin all 300k Gaussians ({t_geom:.2f} s) + blend/decode/relevancy of {npix} random "
-                      f"pixels ({t_pix * 1e3:.3f} ms/px), scaled to 1,555,200 px; single thread, FP64"}
+                      f"pixels ({t_pix * 1e3:.3f} ms/px), the per-pixel time scaled to 1,555,200 px; single "
+                      f"thread, FP64",
+            "host": host_cpu()}
 
 
 def reference_arm(args):
-    """The oracle as the reference arm: each step is one bounded-sample frame estimate."""
+    """The oracle as the reference arm.  Each step is one bounded sample of the at-scale frame
+    (cpu_baseline); `ms_per_step` is the measured time of a step, `value` the whole-frame rate the
+    samples estimate, `frames_per_step` the fraction of a frame's work one step does."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
+    import lsv2_synth as syn
+    data = syn.at_scale()
     for _ in range(args.warmup):
-        cpu_baseline()
+        cpu_baseline(args.cpu_pixels, data)
     t0 = time.perf_counter()
-    samples = [cpu_baseline() for _ in range(args.steps)]
+    samples = [cpu_baseline(args.cpu_pixels, data) for _ in range(args.steps)]
     elapsed = time.perf_counter() - t0
     v = float(np.mean([c["value"] for c in samples]))
+    ms = elapsed * 1e3 / max(1, args.steps)
     cb = dict(samples[-1])
     cb["value"] = v
-    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "frames/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
+    cb["tiny_full_frame"] = cpu_tiny_full_frame()
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "frames/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "frames_per_step": v * ms / 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "300k Gaussians, 3 levels, K=4, L=64, D=512, 1440x1080, 1 query + 4 negatives"},
             "cpu_baseline": cb,
             "e2e": {"value": v, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-            "note": f"FP64 CPU oracle as the reference arm; {args.steps} sampled frames in {elapsed:.1f} s"}
+            "note": f"FP64 CPU oracle (single thread) as the reference arm on rank 0; each step projects and bins the "
+                    f"whole frame and blends, decodes and queries {args.cpu_pixels} sampled pixels; {args.steps} steps "
+                    f"in {elapsed:.1f} s"}
     print(json.dumps(line), flush=True)
 
 
@@ -421,9 +548,7 @@ def batched_section(dev, reps: int = 5, rank: int = 0, world: int = 1):
         f.check()
     seq_ms = s.elapsed_time(e) / reps
     if world > 1:
-        tm = torch.tensor([batched_ms, seq_ms], device=dev)
-        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-        batched_ms, seq_ms = float(tm[0].item()), float(tm[1].item())
+        batched_ms, seq_ms = max_over_ranks([batched_ms, seq_ms], world, dev)
         cnt = torch.tensor([inst, pix, rel_elems], dtype=torch.int64, device=dev)
         dist.all_reduce(cnt)
         inst, pix, rel_elems = (int(v) for v in cnt.tolist())
@@ -497,7 +622,12 @@ def main():
                     help="for a profiler capture: prepare the at-scale frame, then run only this stage "
                          "(--warmup + --steps launches) with only the buffers it needs; `backward` runs the "
                          "training-step measurement of the differentiation workload instead; prints one status line")
+    ap.add_argument("--cpu-pixels", type=int, default=2000,
+                    help="pixels the FP64 oracle blends, decodes and queries per CPU-baseline sample")
     args = ap.parse_args()
+    rc = spawn_ranks(args.gpus, sys.argv[1:])
+    if rc is not None:
+        sys.exit(rc)
     if args.impl == "reference":
         reference_arm(args)
         return
@@ -618,10 +748,7 @@ def main():
     del graph   # it holds pointers to F, which the FP32 comparison below reallocates
     # the per-stage breakdown: the same step with eager launches and events between the stages
     stage_ms, eager_ms = timed(max(3, args.steps // 2))
-    if world > 1:
-        t = torch.tensor([step_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms = float(t.item())
+    step_ms = max_over_ranks([step_ms], world, dev)[0]
     value = world * 1e3 / step_ms
 
     # ---- the plain FP32 GPU form (CUDA-core decode to an FP32 feature map), for comparison ----
@@ -696,10 +823,7 @@ def main():
         e2e_step(i)
     torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks([e2e_ms], world, dev)[0]
 
     # ---- rooflines (algorithmic bytes per launch / CUDA-event duration) ----
     pk, pk_kind = peaks()
@@ -763,7 +887,8 @@ def main():
         line["ablation"] = ablation_section(dev)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline()
+            line["cpu_baseline"] = cpu_baseline(args.cpu_pixels)
+            line["cpu_baseline"]["tiny_full_frame"] = cpu_tiny_full_frame()
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -185,7 +185,9 @@ lsv2_status lsv2_splat_coeffs_bf16(const lsv2_camera* cam, int64_t n, const lsv2
  *     LSV2_SPLAT_NOALLOC_SCRATCH_BYTES (8 MiB: 52,428 Gaussians at 3 levels, K = 4);
  *     larger calls return LSV2_ERR_CAPACITY and launch nothing.
  *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- *     with that device current; make that first call before any stream capture.
+ *     with that device current; make that first call before any stream capture.  The address
+ *     is kept for the life of the process, so do not call this after cudaDeviceReset on that
+ *     device (the reset reloads the module and the kept address would be stale).
  *   - Nothing in the scratch must start at zero (every record is rewritten before use).
  *   - All calls share the one array: calls that overlap on the GPU (e.g. on two streams)
  *     race on it and must be serialised by the caller.

@@ -15,6 +15,7 @@ Each function names the passage of the paper it follows (LangSplatV2, arXiv
   mean_filter,  appendix "Evaluation Details": average pooling of the relevancy map,
   postprocess   level selection, localisation point, normalise + threshold mask
   l1_grads      gradient of the L1 feature loss (decode adjoint as matmuls,
+                l1_decode_adjoint for a given coefficient map,
                 blend adjoint as the literal derivative, projection Jacobian by
                 complex step)
   sparsify,     Sec. 3.3 sparse coefficients: softmax over the L-dim parameter, top K
@@ -370,15 +371,9 @@ def l1_grads(scene, cam, target, tie_eps: float = 1e-6) -> Grads:
     """
     r = render(scene, cam)
     W = r.blend.out                      # [lev, P, L]
-    S = scene.codebook.astype(np.float64)
-    F = np.einsum("lpj,ljd->lpd", W, S)
-    res = F - target.astype(np.float64)
-    lev, P, D = F.shape
-    denom = float(lev * P * D)
-    GF = np.sign(res) / denom
-    loss = float(np.abs(res).sum() / denom)
-    dW = np.einsum("lpd,ljd->lpj", GF, S)
-    dS = np.einsum("lpj,lpd->ljd", W, GF)
+    adj = l1_decode_adjoint(W, scene.codebook, target, tie_eps)
+    loss, dW, dS = adj.loss, adj.dW, adj.dS
+    lev = W.shape[0]
     n = scene.n
     K = scene.K
     dw = np.zeros((n, lev, K))
@@ -399,7 +394,49 @@ def l1_grads(scene, cam, target, tie_eps: float = 1e-6) -> Grads:
     dparams = np.einsum("nk,nkp->np", up, jac)
     dparams[~vis] = 0.0
     return Grads(loss, dW, dS, dw, dop, dm2, dcn, dparams[:, 0:3], dparams[:, 3:6],
-                 dparams[:, 6:10], np.abs(res) < tie_eps)
+                 dparams[:, 6:10], adj.near_tie)
+
+
+@dataclass
+class DecodeAdjoint:
+    loss: float
+    dW: np.ndarray        # [lev, P, L]
+    dS: np.ndarray        # [lev, L, D]
+    near_tie: np.ndarray  # [lev, P, D] bool: |F - target| < tie_eps (sign decided by rounding)
+    tie_px: np.ndarray    # [lev, P] bool: the pixel holds at least one near-tie
+    dS_tie_slack: np.ndarray   # [lev, L, D]: sum_p |W| [near tie] / (lev P D), what a flipped
+                               # sign can move dS by (a flip changes G by up to 2/(lev P D))
+
+
+def l1_decode_adjoint(W, S, target, tie_eps: float = 1e-6, chunk: int = 65536) -> DecodeAdjoint:
+    """Adjoint of the decode (Eq. 7, F = W S, a matmul) under Loss = mean |F - target| for a
+    given coefficient map W [lev, P, L] and codebook S [lev, L, D]: G_F = sign(F - target) /
+    (lev P D) (sign(0) = 0), dW = G_F S^T, dS = W^T G_F.  FP64 library matmuls, taken over
+    blocks of `chunk` pixels so full-size maps fit in memory (the per-pixel quantities do not
+    depend on the blocking; dS is the sum of the blocks' products)."""
+    W = np.asarray(W, np.float64)
+    S = np.asarray(S, np.float64)
+    lev, P, L = W.shape
+    D = S.shape[2]
+    denom = float(lev * P * D)
+    dW = np.zeros((lev, P, L))
+    dS = np.zeros((lev, L, D))
+    slack = np.zeros((lev, L, D))
+    near = np.zeros((lev, P, D), bool)
+    total = 0.0
+    for l in range(lev):
+        for p0 in range(0, P, chunk):
+            p1 = min(P, p0 + chunk)
+            Wb = W[l, p0:p1]
+            res = Wb @ S[l] - np.asarray(target[l, p0:p1], np.float64)
+            total += float(np.abs(res).sum())
+            G = np.sign(res) / denom
+            dW[l, p0:p1] = G @ S[l].T
+            dS[l] += Wb.T @ G
+            tie = np.abs(res) < tie_eps
+            near[l, p0:p1] = tie
+            slack[l] += np.abs(Wb).T @ tie.astype(np.float64) / denom
+    return DecodeAdjoint(total / denom, dW, dS, near, near.any(-1), slack)
 
 
 def l1_loss_fd_eval(scene_params, cam, ids, ranges, tile_mask, idx, S, target):

@@ -18,6 +18,14 @@ LSV2_BF16 = 1
 LSV2_POST_LERF = 0
 LSV2_POST_BLENDED = 1
 
+LSV2_OK = 0
+LSV2_ERR_INVALID_ARGUMENT = 1
+LSV2_ERR_UNSUPPORTED = 2
+LSV2_ERR_CAPACITY = 3
+LSV2_ERR_CUDA = 4
+LSV2_ERR_TIMEOUT = 5
+LSV2_ERR_NONFINITE = 6
+
 STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported configuration", 3: "instance capacity exceeded",
           4: "CUDA error", 5: "device wait timed out", 6: "non-finite value"}
 
@@ -83,6 +91,11 @@ def lib() -> C.CDLL:
             fn.argtypes = args
             fn.restype = res
     return _lib
+
+
+def lib_path() -> str:
+    """Path of the shared library this binding loads."""
+    return LIB
 
 
 def declared_symbols() -> list[str]:

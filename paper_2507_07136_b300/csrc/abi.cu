@@ -121,7 +121,9 @@ lsv2_status lsv2_bin_sort(const lsv2_camera* cam, int64_t n, const lsv2_proj* pr
 size_t lsv2_splat_workspace_bytes(int64_t n, int32_t levels, int32_t K)
 {
     if (n < 0 || levels < 1 || K < 1 || levels * K > kMaxPairs) return 0;
-    return align256((size_t)n * (size_t)splat_record_bytes(levels, K));
+    const size_t rec = (size_t)splat_record_bytes(levels, K);
+    if ((uint64_t)n > (SIZE_MAX - 255) / rec) return 0;   // the size would not fit in size_t
+    return align256((size_t)n * rec);
 }
 
 lsv2_status lsv2_splat_coeffs(const lsv2_camera* cam, int64_t n, const lsv2_proj* proj, const uint32_t* tile_ranges,

@@ -11,7 +11,9 @@
 //
 // The array's name is only a host-side stand-in in host code, not a device address; the
 // device address is obtained with cudaGetSymbolAddress once per device (on the first call
-// made on that device, with the device current) and passed to the kernels.
+// made on that device, with the device current) and passed to the kernels.  The address is kept
+// for the life of the process: after cudaDeviceReset the module is loaded again and the kept
+// address is stale, so this entry point must not be used on a device after it was reset.
 #include <mutex>
 
 #include "device.cuh"
@@ -61,8 +63,11 @@ extern "C" lsv2_status lsv2_splat_coeffs_noalloc(const lsv2_camera* cam, int64_t
         return LSV2_ERR_INVALID_ARGUMENT;
     if (n > 0 && (!idx || !w)) return LSV2_ERR_INVALID_ARGUMENT;
     if (!splat_supported(levels, K, L, cam->tile_w, cam->tile_h)) return LSV2_ERR_UNSUPPORTED;
+    // more Gaussians than the fixed scratch holds (checked before any size product is formed)
+    if ((uint64_t)n > kScratchBytes / (size_t)splat_record_bytes(levels, K)) return LSV2_ERR_CAPACITY;
     const size_t need = lsv2_splat_workspace_bytes(n, levels, K);
-    if (need > kScratchBytes) return LSV2_ERR_CAPACITY;  // more Gaussians than the fixed scratch holds
+    if (need == 0 && n > 0) return LSV2_ERR_INVALID_ARGUMENT;
+    if (need > kScratchBytes) return LSV2_ERR_CAPACITY;
     void* scratch = nullptr;
     if (scratch_address(&scratch) != cudaSuccess) return LSV2_ERR_CUDA;
     // The scratch needs no clearing: the pack kernel writes the record of every Gaussian

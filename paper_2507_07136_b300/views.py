@@ -9,6 +9,7 @@ a small autotuner.
 """
 from __future__ import annotations
 
+import hashlib
 import json
 import os
 
@@ -106,16 +107,33 @@ class ViewsBatch:
             raise L.LSV2Error("device status", code)
 
 
+_LIB_DIGEST = None
+
+
+def _lib_digest() -> str:
+    """Digest of the loaded library file, so a rebuilt kernel invalidates cached choices."""
+    global _LIB_DIGEST
+    if _LIB_DIGEST is None:
+        h = hashlib.sha1()
+        with open(L.lib_path(), "rb") as f:
+            for block in iter(lambda: f.read(1 << 20), b""):
+                h.update(block)
+        _LIB_DIGEST = h.hexdigest()[:16]
+    return _LIB_DIGEST
+
+
 def _key(scene, cams, Q, n_neg):
     name = torch.cuda.get_device_name()
     res = ",".join(f"{c.width}x{c.height}" for c in cams)
-    return f"{name}|{res}|n={scene.n}|levels={scene.levels}|Q={Q}x{1 + n_neg}"
+    return (f"{name}|lib={_lib_digest()}|{res}|n={scene.n}|levels={scene.levels}|K={scene.K}|"
+            f"Q={Q}x{1 + n_neg}")
 
 
 def autotune(scene: DeviceScene, cams, text: torch.Tensor, reps: int = 5, cache: str | None = CACHE,
              candidates=None, verbose: bool = False):
     """Time every (tile shape, staging batch) candidate on this batch and return the fastest,
-    caching the choice in a JSON file keyed by (GPU, resolutions, N, levels, queries)."""
+    caching the choice in a JSON file keyed by (GPU, library build, resolutions, N, levels, K,
+    queries)."""
     Q, nt = text.shape[0], text.shape[1]
     key = _key(scene, cams, Q, nt - 1)
     table = {}

@@ -53,12 +53,20 @@ def test_noalloc_matches_workspace_splat_twice():
     check_against_workspace_version(sc2, syn.orbit_camera(141, 99, 4.0))
 
 
-def test_noalloc_rejects_more_than_its_scratch():
-    sc, cam = syn.tiny()
-    fr = Frame(DeviceScene.from_numpy(sc), cam)
-    too_many = (8 << 20) // 64 + 1      # more Gaussians than 8 MiB of records can hold
-    code = L.lib().lsv2_splat_coeffs_noalloc(C.byref(fr.ccam), too_many, C.byref(fr.proj), _ptr(fr.tile_ranges),
+def test_noalloc_capacity_boundary():
+    """8 MiB of 160-byte records (3 levels, K = 4): 52,428 Gaussians fit, 52,429 do not.  The
+    accepted call runs on a scene of exactly 52,428 Gaussians and matches the workspace splat;
+    the rejected one returns LSV2_ERR_CAPACITY on the host and launches nothing."""
+    rec = 160
+    limit = (8 << 20) // rec
+    assert limit == 52428
+    assert L.lsv2_splat_workspace_bytes(limit, 3, 4) <= 8 << 20 < L.lsv2_splat_workspace_bytes(limit + 1, 3, 4)
+    sc = syn.make_scene(limit, 3, seed=12, mean_kind="uniform", mean_param=1.0, log_scale_mu=-3.5,
+                        log_scale_sigma=0.4)
+    check_against_workspace_version(sc, syn.orbit_camera(96, 80, 4.0))
+    fr = Frame(DeviceScene.from_numpy(sc), syn.orbit_camera(96, 80, 4.0))
+    code = L.lib().lsv2_splat_coeffs_noalloc(C.byref(fr.ccam), limit + 1, C.byref(fr.proj), _ptr(fr.tile_ranges),
                                              _ptr(fr.gauss_ids), 3, 4, 64, _ptr(fr.scene.idx),
                                              _ptr(fr.scene.weights), _ptr(fr.coeff), _ptr(fr.final_T),
                                              _ptr(fr.n_last), _ptr(fr.status), _stream(None))
-    assert code == 3
+    assert code == L.LSV2_ERR_CAPACITY
