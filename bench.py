@@ -84,6 +84,7 @@ class ClockSampler:
         self.proc = self.thread = None
         self.stop = threading.Event()
         self.source = "none"
+        self.nvml_error = None
 
     def _nvml_handle(self):
         import pynvml
@@ -125,7 +126,8 @@ class ClockSampler:
             nv, h = self._nvml_handle()
             self.thread = threading.Thread(target=self._poll_nvml, args=(nv, h), daemon=True)
             self.source = "nvml"
-        except Exception:
+        except Exception as e:
+            self.nvml_error = f"{type(e).__name__}: {e}"[:200]
             try:
                 self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
                                               "--format=csv,noheader,nounits", "-lms", "100"],
@@ -159,9 +161,12 @@ class ClockSampler:
                     "source": self.source}
         sm = [r[0] for r in self.rows]
         reasons = sorted(set().union(*[r[3] for r in self.rows]))
-        return {"sm_mhz": float(np.median(sm)), "sm_min_mhz": float(min(sm)),
-                "sm_max_mhz": max(r[1] for r in self.rows), "power_w_max": max(r[2] for r in self.rows),
-                "reasons": reasons, "samples": len(self.rows), "source": self.source}
+        out = {"sm_mhz": float(np.median(sm)), "sm_min_mhz": float(min(sm)),
+               "sm_max_mhz": max(r[1] for r in self.rows), "power_w_max": max(r[2] for r in self.rows),
+               "reasons": reasons, "samples": len(self.rows), "source": self.source}
+        if self.nvml_error:
+            out["nvml_error"] = self.nvml_error
+        return out
 
 
 def dist_env():

@@ -32,7 +32,8 @@
  *   - Errors found on the host (null pointers, sizes, unsupported shapes) are returned
  *     immediately and nothing is launched.  Conditions found on the device are written to
  *     `*dev_status` (an int32 in device memory the caller zeroes): the first nonzero
- *     lsv2_status wins; kernels never trap.  LSV2_ERR_CUDA reports a launch error.
+ *     lsv2_status wins; kernels never trap, and every device-side wait is bounded
+ *     (lsv2_set_wait_limit_ns).  LSV2_ERR_CUDA reports a launch error.
  *   - Pixel (i, j) is evaluated at image-plane point (i, j).  Images are row-major.
  *   - Constants of the 3DGS rasteriser the paper builds on: 0.3 px^2 dilation, screen
  *     radius ceil(3 sqrt(lambda_max)), guard band 1.3 tan(fov/2), alpha clamp 0.99,
@@ -110,6 +111,19 @@ typedef struct {
 
 int32_t lsv2_abi_version(void);
 const char* lsv2_status_string(lsv2_status s);
+
+/* Bound of the device-side waits of the pipelined kernels (the splats, the tensor-core decode and
+ * relevancy, the fused render, and the many-view call): a wait on another warp's progress (a
+ * pipeline stage, a tensor-core accumulator) that is still unfinished `ns` nanoseconds after it
+ * began gives up, the kernel records LSV2_ERR_TIMEOUT in *dev_status, lets the copies and MMAs it
+ * issued complete (bounded by 100 ms), frees its tensor memory and returns; later CTAs of the
+ * splat see the status and skip their tiles.  0 gives up at the first unsuccessful check (used by
+ * tests to drive this path).  Default 1,000,000,000 (1 s).  The value is read when a call
+ * launches its kernels (a call captured in a CUDA graph keeps the value of its capture); it is
+ * process-wide, not per device or stream.  The paper has no counterpart: this is the library's
+ * failure detection (a wait never spins without bound, a kernel never traps). */
+void lsv2_set_wait_limit_ns(uint64_t ns);
+uint64_t lsv2_wait_limit_ns(void);
 
 /* Project n Gaussians (Sec. 3.1, Eq. 1-2, EWA splatting).
  * means float[n][3], scales float[n][3] (activated, > 0), quats float[n][4] (w, x, y, z;

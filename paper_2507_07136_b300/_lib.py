@@ -49,6 +49,8 @@ class lsv2_proj(C.Structure):
 _SIGS = {
     "lsv2_abi_version": ([], I32),
     "lsv2_status_string": ([I32], C.c_char_p),
+    "lsv2_set_wait_limit_ns": ([C.c_uint64], None),
+    "lsv2_wait_limit_ns": ([], C.c_uint64),
     "lsv2_project": ([P, I64, P, P, P, P, P, P, P], I32),
     "lsv2_bin_sort_workspace_bytes": ([I64, I64, I32], SZ),
     "lsv2_bin_sort": ([P, I64, P, P, SZ, P, I64, P, P, P, P], I32),
@@ -126,6 +128,14 @@ def camera(cam) -> lsv2_camera:
 # thin wrappers with the ABI's names (pointers as Python ints, streams as cudaStream_t ints)
 def lsv2_abi_version() -> int:
     return lib().lsv2_abi_version()
+
+
+def lsv2_set_wait_limit_ns(ns: int) -> None:
+    lib().lsv2_set_wait_limit_ns(int(ns))
+
+
+def lsv2_wait_limit_ns() -> int:
+    return int(lib().lsv2_wait_limit_ns())
 
 
 def lsv2_project(cam, n, means, scales, quats, opacity, out, dev_status, stream):

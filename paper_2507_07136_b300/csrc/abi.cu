@@ -2,6 +2,7 @@
 // checks, then stream-ordered launches.  No entry point allocates device memory or
 // synchronises the host.
 #include <algorithm>
+#include <atomic>
 
 #include "backward.cuh"
 #include "binsort.cuh"
@@ -55,11 +56,19 @@ int sm_count()
 
 size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
+std::atomic<uint64_t> g_wait_ns{kDefaultWaitNs};
+
 }  // namespace
+
+uint64_t lsv2::wait_limit_ns() { return g_wait_ns.load(std::memory_order_relaxed); }
 
 extern "C" {
 
 int32_t lsv2_abi_version(void) { return LSV2_ABI_VERSION; }
+
+void lsv2_set_wait_limit_ns(uint64_t ns) { g_wait_ns.store(ns, std::memory_order_relaxed); }
+
+uint64_t lsv2_wait_limit_ns(void) { return g_wait_ns.load(std::memory_order_relaxed); }
 
 const char* lsv2_status_string(lsv2_status s)
 {

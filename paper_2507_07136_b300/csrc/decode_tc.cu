@@ -16,8 +16,8 @@
 //    store.  A slot is rewritten once the store issued kSlots boxes earlier has read it, so
 //    the stores of consecutive tiles stream back to back; a tile's last box releases TMEM to
 //    the next tile's MMA through an mbarrier, without a block-wide barrier.
-// Every wait is time-bounded: on expiry the CTA records LSV2_ERR_TIMEOUT, drains its bulk
-// stores, frees TMEM and returns.
+// Every wait is time-bounded: on expiry the CTA records LSV2_ERR_TIMEOUT, lets its W load,
+// MMA and bulk stores in flight complete, frees TMEM and returns.
 #include "decode_tc.cuh"
 #include "tc.cuh"
 #include "tmap.cuh"
@@ -43,6 +43,7 @@ struct DecodeTcArgs {
     int s_bf16;
     int out_bf16;
     int32_t* status;
+    uint64_t wait_ns;     // bound of a wait on another warp's progress
 };
 
 __host__ __device__ constexpr size_t smem_bytes(int D)
@@ -149,15 +150,18 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc::fence_after();
     const uint32_t tmem = *tslot;
     bool failed = false;
+    uint32_t w_loads = 0, commits = 0;   // thread 0: TMA loads of W and MMA commits it issued
     if (tid == 0 && tile < ntiles) {
         if (kWTma) {
             tc::bulk_load_arm(w_bar, kM * 128);
             tc::tma_load_3d(tc::smem_u32(sA), &tmW, 0, (int)(tile * kM), lev, w_bar);
-            failed = !tc::mbar_wait(w_bar, 0);
+            ++w_loads;
+            failed = !tc::mbar_wait(w_bar, 0, a.wait_ns);
         }
         if (!failed) {
             issue_mma(tmem, sA, sB, D);
             tc::mma_commit(mma_bar);
+            ++commits;
         }
     }
     __syncwarp();
@@ -171,7 +175,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t g = 0;                              // boxes this warp has stored
     for (int it = 0; tile < ntiles; tile += gridDim.x, ++it) {
         const int64_t next = tile + gridDim.x;
-        if (!__all_sync(0xffffffffu, tc::mbar_wait(mma_bar, (uint32_t)it & 1u))) {
+        if (!__all_sync(0xffffffffu, tc::mbar_wait(mma_bar, (uint32_t)it & 1u, a.wait_ns))) {
             failed = true;
             break;
         }
@@ -182,6 +186,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (tid == 0) {
                     tc::bulk_load_arm(w_bar, kM * 128);
                     tc::tma_load_3d(tc::smem_u32(sA), &tmW, 0, (int)(next * kM), lev, w_bar);
+                    ++w_loads;
                 }
             } else {
                 fetch_w(a, lev, next * kM, pre);
@@ -239,12 +244,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(free_bar);
         if (tid == 0 && next < ntiles) {
-            bool ok = tc::mbar_wait(free_bar, (uint32_t)it & 1u);
-            if (kWTma && ok) ok = tc::mbar_wait(w_bar, (uint32_t)(it + 1) & 1u);
+            bool ok = tc::mbar_wait(free_bar, (uint32_t)it & 1u, a.wait_ns);
+            if (kWTma && ok) ok = tc::mbar_wait(w_bar, (uint32_t)(it + 1) & 1u, a.wait_ns);
             if (ok) {
                 tc::fence_after();
                 issue_mma(tmem, sA, sB, D);
                 tc::mma_commit(mma_bar);
+                ++commits;
             } else {
                 failed = true;
             }
@@ -252,6 +258,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
     }
     if (failed) report(a.status, LSV2_ERR_TIMEOUT);
+    // Thread 0 drains what it issued before TMEM is freed and the CTA retires: the latest W load
+    // (load k completes phase k of w_bar) and the latest MMA commit (commit k completes phase k of
+    // mma_bar; it covers every earlier MMA).  On the normal path both completed already.
+    if (tid == 0) {
+        if (w_loads > 0) (void)tc::mbar_wait(w_bar, (w_loads - 1) & 1u, kDrainNs);
+        if (commits > 0) (void)tc::mbar_wait(mma_bar, (commits - 1) & 1u, kDrainNs);
+    }
     if (lane == 0) tc::bulk_wait_all();
     tc::fence_before();
     __syncthreads();
@@ -280,7 +293,7 @@ cudaError_t launch_decode_tc(int levels, int64_t P, int D, const void* W, bool w
     } else {
         std::memset(&tmW, 0, sizeof(tmW));
     }
-    DecodeTcArgs a{P, D, W, w_bf16 ? 1 : 0, S, s_bf16 ? 1 : 0, out_bf16 ? 1 : 0, status};
+    DecodeTcArgs a{P, D, W, w_bf16 ? 1 : 0, S, s_bf16 ? 1 : 0, out_bf16 ? 1 : 0, status, wait_limit_ns()};
     const size_t smem = smem_bytes(D);
     auto kernel = w_bf16 ? decode_tc_kernel<true> : decode_tc_kernel<false>;
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

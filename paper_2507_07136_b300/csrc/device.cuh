@@ -22,6 +22,17 @@ constexpr float kTMin = 1e-4f;
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
 
+// Bound of a device-side wait on another warp's progress (a pipeline stage, an accumulator):
+// lsv2_set_wait_limit_ns sets it on the host (default 1 s) and every launch passes the value in
+// its arguments; 0 makes a wait give up at its first unsuccessful check.  A wait that runs out
+// records LSV2_ERR_TIMEOUT.
+uint64_t wait_limit_ns();
+constexpr uint64_t kDefaultWaitNs = 1000000000ull;
+// Bound of the waits with which a CTA that gave up drains its own asynchronous work (bulk and
+// tensor copies it issued, MMAs it committed) before it frees TMEM and retires.  Independent of
+// the limit above: work that was issued completes on its own.
+constexpr uint64_t kDrainNs = 100000000ull;
+
 // First nonzero status wins; never traps.
 __device__ __forceinline__ void report(int32_t* status, int32_t code)
 {

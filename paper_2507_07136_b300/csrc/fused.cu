@@ -24,7 +24,8 @@
 //     {D, W, H, levels} map (columns past the image edge are clipped by the map).
 // The operands and the MMA sequence (K = 64 in four steps of 16) are those of decode_tc.cu and
 // query_tc.cu, so F and the relevancy equal those kernels' results on the splat's W.  Every wait
-// is time-bounded: on expiry the CTA records LSV2_ERR_TIMEOUT, skips the rest and frees TMEM.
+// is time-bounded: on expiry the CTA records LSV2_ERR_TIMEOUT, skips the rest, lets the copies
+// and MMAs it issued complete, and frees TMEM.
 #include <cuda_bf16.h>
 
 #include <cstring>
@@ -71,6 +72,7 @@ struct FusedArgs {
     void* rel;                   // [Q][levels][P]
     int rel_bf16;
     int32_t* status;
+    uint64_t wait_ns;            // bound of a wait on another warp's progress
 };
 
 struct FusedBars {
@@ -120,6 +122,7 @@ __global__ void __launch_bounds__(FC::kThreads, 2) fused_kernel(const __grid_con
         // ---- splat: W stays in the consumer warps' shared-memory columns
         TileJob j{a.width, a.height, x0, y0, a.tile_ranges[2 * tile], a.tile_ranges[2 * tile + 1], a.gauss_ids,
                   a.recs, nullptr, a.final_T, a.n_last, a.status};
+        j.wait_ns = a.wait_ns;
         (void)splat_tile<kLev, kKp, kTW, kHH, 0, false>(j, sm, 0u);
     }
     bool ok = !skip && !*reinterpret_cast<volatile int*>(sm.abort);
@@ -181,12 +184,12 @@ __global__ void __launch_bounds__(FC::kThreads, 2) fused_kernel(const __grid_con
         int bc = 0;           // B chunks consumed
         int b_loaded = nb < kBSlots ? nb : kBSlots;   // B chunks whose copies were issued
         int q_loaded = do_query ? 1 : 0;              // query-matrix copies issued
-        int last_commit = -1;                         // 1: dfull of group g - 1 was committed last
+        uint32_t last_bar = 0, last_par = 0;          // the latest MMA commit (it covers all earlier MMAs)
         const uint32_t qb = (uint32_t)a.npadq * 128;
         for (int l = 0; l < kLev && ok; ++l) {
             if (do_query) {
-                if (warp_wait(&fb->qload, (uint32_t)(l & 1), nullptr, 0, abort_flag) != kWaitDone ||
-                    (l > 0 && warp_wait(&fb->qempty, (uint32_t)((l - 1) & 1), nullptr, 0, abort_flag) != kWaitDone)) {
+                if (warp_wait(&fb->qload, (uint32_t)(l & 1), nullptr, 0, abort_flag, a.wait_ns) != kWaitDone ||
+                    (l > 0 && warp_wait(&fb->qempty, (uint32_t)((l - 1) & 1), nullptr, 0, abort_flag, a.wait_ns) != kWaitDone)) {
                     ok = false;
                     break;
                 }
@@ -201,10 +204,11 @@ __global__ void __launch_bounds__(FC::kThreads, 2) fused_kernel(const __grid_con
                     tc::mma_commit(tc::smem_u32(&fb->qfree));
                 }
                 __syncwarp();
-                last_commit = 0;
+                last_bar = tc::smem_u32(&fb->qfree);   // level l's commit: phase l
+                last_par = (uint32_t)(l & 1);
                 if (l + 1 < kLev) {
                     // the next level's query matrix replaces this one once the MMA has read it
-                    if (warp_wait(&fb->qfree, (uint32_t)(l & 1), nullptr, 0, abort_flag) != kWaitDone) { ok = false; break; }
+                    if (warp_wait(&fb->qfree, (uint32_t)(l & 1), nullptr, 0, abort_flag, a.wait_ns) != kWaitDone) { ok = false; break; }
                     if (lane == 0) {
                         tc::bulk_load_arm(tc::smem_u32(&fb->qload), qb);
                         tc::bulk_load(tc::smem_u32(smem + kQOff), a.Bq + (size_t)(l + 1) * qb, qb, tc::smem_u32(&fb->qload));
@@ -215,8 +219,8 @@ __global__ void __launch_bounds__(FC::kThreads, 2) fused_kernel(const __grid_con
             if (!do_dec) continue;
             for (int c = 0; c < nfc; ++c, ++bc, ++g) {
                 const int s = bc % kBSlots, buf = g & 1;
-                if (warp_wait(&fb->bfull[s], (uint32_t)((bc / kBSlots) & 1), nullptr, 0, abort_flag) != kWaitDone ||
-                    (g >= 2 && warp_wait(&fb->dempty[buf], (uint32_t)(((g - 2) >> 1) & 1), nullptr, 0, abort_flag) != kWaitDone)) {
+                if (warp_wait(&fb->bfull[s], (uint32_t)((bc / kBSlots) & 1), nullptr, 0, abort_flag, a.wait_ns) != kWaitDone ||
+                    (g >= 2 && warp_wait(&fb->dempty[buf], (uint32_t)(((g - 2) >> 1) & 1), nullptr, 0, abort_flag, a.wait_ns) != kWaitDone)) {
                     ok = false;
                     break;
                 }
@@ -231,11 +235,12 @@ __global__ void __launch_bounds__(FC::kThreads, 2) fused_kernel(const __grid_con
                     tc::mma_commit(tc::smem_u32(&fb->bempty[s]));
                 }
                 __syncwarp();
-                last_commit = 1;
+                last_bar = tc::smem_u32(&fb->dfull[buf]);   // group g is buffer buf's commit g / 2
+                last_par = (uint32_t)((g >> 1) & 1);
                 // refill this slot with chunk bc + kBSlots once the MMA has read it
                 const int nxt = bc + kBSlots;
                 if (nxt < nb) {
-                    if (warp_wait(&fb->bempty[s], (uint32_t)((bc / kBSlots) & 1), nullptr, 0, abort_flag) != kWaitDone) {
+                    if (warp_wait(&fb->bempty[s], (uint32_t)((bc / kBSlots) & 1), nullptr, 0, abort_flag, a.wait_ns) != kWaitDone) {
                         ok = false;
                         break;
                     }
@@ -250,16 +255,16 @@ __global__ void __launch_bounds__(FC::kThreads, 2) fused_kernel(const __grid_con
         }
         if (!ok) {
             if (lane == 0) report(a.status, LSV2_ERR_TIMEOUT);
-            // Before the CTA frees TMEM and retires: the copies it issued must have landed and
-            // its last MMAs completed (each wait bounded; the status already records the failure).
             *abort_flag = 1;
-            for (int c = b_loaded > kBSlots ? b_loaded - kBSlots : 0; c < b_loaded; ++c)
-                (void)tc::mbar_wait(tc::smem_u32(&fb->bfull[c % kBSlots]), (uint32_t)((c / kBSlots) & 1), 100000000ull);
-            if (q_loaded > 0)
-                (void)tc::mbar_wait(tc::smem_u32(&fb->qload), (uint32_t)((q_loaded - 1) & 1), 100000000ull);
-            if (last_commit == 1 && g > 0)
-                (void)tc::mbar_wait(tc::smem_u32(&fb->dfull[(g - 1) & 1]), (uint32_t)(((g - 1) >> 1) & 1), 100000000ull);
         }
+        // Before the CTA frees TMEM and retires, the copies this warp issued must have landed and
+        // its last MMA (hence every earlier one) completed: also when its own loop finished,
+        // since an epilogue warp may have given up on an MMA that is still running.  On the
+        // normal path these phases completed already.  Each wait is bounded by kDrainNs.
+        for (int c = b_loaded > kBSlots ? b_loaded - kBSlots : 0; c < b_loaded; ++c)
+            (void)tc::mbar_wait(tc::smem_u32(&fb->bfull[c % kBSlots]), (uint32_t)((c / kBSlots) & 1), kDrainNs);
+        if (q_loaded > 0) (void)tc::mbar_wait(tc::smem_u32(&fb->qload), (uint32_t)((q_loaded - 1) & 1), kDrainNs);
+        if (last_bar) (void)tc::mbar_wait(last_bar, last_par, kDrainNs);
     } else if (ok && warp < FC::kWarps) {
         // ---- epilogues: this warp owns MMA rows 32 q4 .. 32 q4 + 31 = image rows 2 q4, 2 q4 + 1
         const int q4 = warp, row = 32 * q4 + lane;
@@ -272,7 +277,7 @@ __global__ void __launch_bounds__(FC::kThreads, 2) fused_kernel(const __grid_con
         int g = 0;
         for (int l = 0; l < kLev && ok; ++l) {
             if (do_query) {
-                if (warp_wait(&fb->qfull, (uint32_t)(l & 1), nullptr, 0, abort_flag) != kWaitDone) { ok = false; break; }
+                if (warp_wait(&fb->qfull, (uint32_t)(l & 1), nullptr, 0, abort_flag, a.wait_ns) != kWaitDone) { ok = false; break; }
                 tc::fence_after();
                 // |F|^2 = W . (S S^T W): columns 0..63 of Y, W from this level's A tile
                 float n2;
@@ -326,7 +331,7 @@ __global__ void __launch_bounds__(FC::kThreads, 2) fused_kernel(const __grid_con
             if (!do_dec) continue;
             for (int c = 0; c < nfc && ok; ++c, ++g) {
                 const int buf = g & 1;
-                if (warp_wait(&fb->dfull[buf], (uint32_t)((g >> 1) & 1), nullptr, 0, abort_flag) != kWaitDone) {
+                if (warp_wait(&fb->dfull[buf], (uint32_t)((g >> 1) & 1), nullptr, 0, abort_flag, a.wait_ns) != kWaitDone) {
                     ok = false;
                     break;
                 }
@@ -507,6 +512,7 @@ cudaError_t launch_fused(const lsv2_camera& cam, int64_t n, const lsv2_proj& pro
     a.rel = rel;
     a.rel_bf16 = rel_bf16 ? 1 : 0;
     a.status = status;
+    a.wait_ns = wait_limit_ns();
     constexpr int kSmem = FC::kSmemBytes + 1024;
     static_assert(2 * (kSmem + 1024) <= 233472, "two CTAs per SM");
     e = cudaFuncSetAttribute(fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);

@@ -39,6 +39,7 @@ struct QueryTcArgs {
     int64_t total_tiles;           // 128-pixel tiles over all views (per level)
     QuerySeg seg[kMaxQueryViews + 1];
     int32_t* status;
+    uint64_t wait_ns;              // bound of a wait on another warp's progress
 };
 
 constexpr int kStages = 2;                      // W tiles in flight per CTA (bulk copies)
@@ -176,6 +177,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) query_tc_kernel(QueryTcArgs a)
     const int cb = part * ch < nch ? part * ch : nch, ce = (part + 1) * ch < nch ? (part + 1) * ch : nch;
     uint32_t phase = 0;
     bool failed = false;
+    bool mma_pending = false;   // thread 0: an MMA was committed and not yet seen complete
 
     for (int64_t i = 0; i < my_tiles; ++i) {
         int vw;
@@ -183,7 +185,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) query_tc_kernel(QueryTcArgs a)
         locate(blockIdx.x + i * gridDim.x, vw, p0);
         const int64_t Pv = a.seg[vw].P;
         const int s = (int)(i % kStages);
-        const bool landed = tc::mbar_wait(tc::smem_u32(full + s), (uint32_t)((i / kStages) & 1));
+        const bool landed = tc::mbar_wait(tc::smem_u32(full + s), (uint32_t)((i / kStages) & 1), a.wait_ns);
         if (__syncthreads_or(!landed)) {
             failed = true;
             break;
@@ -207,12 +209,14 @@ __global__ void __launch_bounds__(NT, 512 / NT) query_tc_kernel(QueryTcArgs a)
                                  idesc, k > 0 ? 1u : 0u);
             }
             tc::mma_commit(tc::smem_u32(bar));
+            mma_pending = true;
         }
-        const bool ok = tc::mbar_wait(tc::smem_u32(bar), phase);
+        const bool ok = tc::mbar_wait(tc::smem_u32(bar), phase, a.wait_ns);
         if (__syncthreads_or(!ok)) {
             failed = true;
             break;
         }
+        mma_pending = false;
         phase ^= 1u;
         tc::fence_after();
         const int64_t p = p0 + row;
@@ -273,6 +277,8 @@ __global__ void __launch_bounds__(NT, 512 / NT) query_tc_kernel(QueryTcArgs a)
         __syncthreads();   // TMEM and the W tile are free
     }
     if (failed && tid == 0) report(a.status, LSV2_ERR_TIMEOUT);
+    // an MMA whose completion the CTA gave up waiting for must finish before TMEM is freed
+    if (tid == 0 && mma_pending) (void)tc::mbar_wait(tc::smem_u32(bar), phase, kDrainNs);
     tc::fence_before();
     __syncthreads();
     if (warp == 0) {
@@ -283,7 +289,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) query_tc_kernel(QueryTcArgs a)
     // them (bounded) before the CTA retires.
     if (failed && tid == 0)
         for (int64_t i = last_issued; i >= 0 && i > last_issued - kStages; --i)
-            (void)tc::mbar_wait(tc::smem_u32(full + (int)(i % kStages)), (uint32_t)((i / kStages) & 1), 100000000ull);
+            (void)tc::mbar_wait(tc::smem_u32(full + (int)(i % kStages)), (uint32_t)((i / kStages) & 1), kDrainNs);
 }
 
 // ---- Pipelined form for a BF16 coefficient map and N <= 256 columns --------------------------
@@ -307,14 +313,14 @@ __host__ __device__ constexpr size_t pipe_smem_bytes(int npad, int ntp)
     return 1024 + (size_t)kPStages * kM * 128 + (size_t)npad * 128 + (((size_t)ntp * 4 + 15) & ~size_t(15)) + 256;
 }
 
-// Bounded wait on a barrier phase: false once the CTA's abort flag is up, or after 1 s (which
-// raises the flag).
-__device__ __forceinline__ bool pipe_wait(uint32_t bar, uint32_t parity, volatile int* abort)
+// Bounded wait on a barrier phase: false once the CTA's abort flag is up, or when the phase is
+// still incomplete limit_ns after the wait began (which raises the flag; at once for 0).
+__device__ __forceinline__ bool pipe_wait(uint32_t bar, uint32_t parity, volatile int* abort, uint64_t limit_ns)
 {
     const uint64_t t0 = tc::globaltimer();
     while (!tc::mbar_try(bar, parity)) {
         if (*abort) return false;
-        if (tc::globaltimer() - t0 > 1000000000ull) {
+        if (tc::globaltimer() - t0 >= limit_ns) {
             *abort = 1;
             return false;
         }
@@ -395,7 +401,7 @@ __global__ void __launch_bounds__(64 + 128 * NB, 1) query_pipe_kernel(const __gr
             int issued = 0;
             for (int i = 0; i < my_tiles; ++i) {
                 const int s = i % kPStages;
-                if (i >= kPStages && !pipe_wait(tc::smem_u32(w_empty + s), (uint32_t)((i / kPStages - 1) & 1), abort))
+                if (i >= kPStages && !pipe_wait(tc::smem_u32(w_empty + s), (uint32_t)((i / kPStages - 1) & 1), abort, a.wait_ns))
                     break;
                 int v;
                 int64_t p0;
@@ -407,7 +413,7 @@ __global__ void __launch_bounds__(64 + 128 * NB, 1) query_pipe_kernel(const __gr
             }
             // no copy may still be landing when the CTA retires
             for (int i = issued > kPStages ? issued - kPStages : 0; i < issued; ++i)
-                (void)tc::mbar_wait(tc::smem_u32(w_full + i % kPStages), (uint32_t)((i / kPStages) & 1), 100000000ull);
+                (void)tc::mbar_wait(tc::smem_u32(w_full + i % kPStages), (uint32_t)((i / kPStages) & 1), kDrainNs);
         }
         __syncwarp();
     } else if (warp == 1) {
@@ -416,8 +422,8 @@ __global__ void __launch_bounds__(64 + 128 * NB, 1) query_pipe_kernel(const __gr
             int done = 0;
             for (int i = 0; i < my_tiles; ++i) {
                 const int s = i % kPStages, b = i % nb;
-                if (!pipe_wait(tc::smem_u32(w_full + s), (uint32_t)((i / kPStages) & 1), abort)) break;
-                if (i >= nb && !pipe_wait(tc::smem_u32(t_empty + b), (uint32_t)((i / nb - 1) & 1), abort)) break;
+                if (!pipe_wait(tc::smem_u32(w_full + s), (uint32_t)((i / kPStages) & 1), abort, a.wait_ns)) break;
+                if (i >= nb && !pipe_wait(tc::smem_u32(t_empty + b), (uint32_t)((i / nb - 1) & 1), abort, a.wait_ns)) break;
                 tc::fence_after();
                 const uint32_t a0 = tc::smem_u32(ring + (size_t)s * kM * 128), b0 = tc::smem_u32(sB);
                 const uint32_t idesc = tc::idesc_bf16(kM, a.npad);
@@ -431,7 +437,7 @@ __global__ void __launch_bounds__(64 + 128 * NB, 1) query_pipe_kernel(const __gr
             // no MMA may still be writing TMEM when it is freed
             if (done > 0) {
                 const int i = done - 1;
-                (void)tc::mbar_wait(tc::smem_u32(m_full + i % nb), (uint32_t)((i / nb) & 1), 100000000ull);
+                (void)tc::mbar_wait(tc::smem_u32(m_full + i % nb), (uint32_t)((i / nb) & 1), kDrainNs);
             }
         }
         __syncwarp();
@@ -442,10 +448,10 @@ __global__ void __launch_bounds__(64 + 128 * NB, 1) query_pipe_kernel(const __gr
         const int nch = a.Qp / 8;
         for (int i = g; i < my_tiles; i += nb) {
             const int s = i % kPStages, b = i % nb;
-            if (!__all_sync(0xffffffffu, pipe_wait(tc::smem_u32(m_full + b), (uint32_t)((i / nb) & 1), abort))) break;
+            if (!__all_sync(0xffffffffu, pipe_wait(tc::smem_u32(m_full + b), (uint32_t)((i / nb) & 1), abort, a.wait_ns))) break;
             // (already complete) acquire of the TMA's writes of the W stage read below; the stage
             // is reloaded only after this warpgroup releases it, so the phase cannot move on
-            if (!__all_sync(0xffffffffu, pipe_wait(tc::smem_u32(w_full + s), (uint32_t)((i / kPStages) & 1), abort)))
+            if (!__all_sync(0xffffffffu, pipe_wait(tc::smem_u32(w_full + s), (uint32_t)((i / kPStages) & 1), abort, a.wait_ns)))
                 break;
             tc::fence_after();
             int vw;
@@ -574,6 +580,7 @@ cudaError_t launch_query_tc_views(int levels, int V, const int64_t* P, int Q, in
     a.levels = levels;
     a.nseg = V;
     a.status = status;
+    a.wait_ns = wait_limit_ns();
     int64_t tiles = 0;
     size_t w_off = 0, rel_off = 0;
     for (int v = 0; v < V; ++v) {

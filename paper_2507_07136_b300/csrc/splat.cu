@@ -169,6 +169,7 @@ __global__ void __launch_bounds__(TW* TH + 32, (TW * TH <= 128 && LW <= 64) ? 2 
     TileJob j{a.cam.width, a.cam.height, (tile % GX) * TW, (tile / GX) * (TH * SUB) + sub * TH, a.tile_ranges[2 * tile],
               a.tile_ranges[2 * tile + 1], a.gauss_ids, a.recs, a.coeff, a.final_T, a.n_last, a.status,
               a.coeff_bf16};
+    j.wait_ns = a.wait_ns;
     (void)splat_tile<LEVELS, K, TW, TH, 0, true, DENSE, LW>(j, sm, 0u);
 }
 
@@ -199,6 +200,7 @@ __global__ void __launch_bounds__(16 * 16 + 32, LW <= 64 ? 2 : 1) splat_tm_kerne
     TileJob j{a.cam.width, a.cam.height, (tile % GX) * 16, (tile / GX) * 16, a.tile_ranges[2 * tile],
               a.tile_ranges[2 * tile + 1], a.gauss_ids, a.recs, a.coeff, a.final_T, a.n_last, a.status,
               a.coeff_bf16};
+    j.wait_ns = a.wait_ns;
     (void)splat_tile_tm<C, LEVELS, K>(j, sm, 0u);
     // every TMEM access of the tile completed before splat_tile_tm's barrier
     if (warp == C::kSmemAccWarps) tc::tmem_dealloc(*sm.tmem_slot, kSplatTmemCols);
@@ -237,6 +239,7 @@ __global__ void __launch_bounds__(TW* TH + 32, 1) splat_views_kernel(SplatViewsA
                   a.coeff_bf16 ? reinterpret_cast<float*>(reinterpret_cast<__nv_bfloat16*>(a.coeff) + w.coeff_off)
                                : a.coeff + w.coeff_off,
                   a.final_T + w.pix_off, a.n_last + w.pix_off, a.status, a.coeff_bf16};
+        j.wait_ns = a.wait_ns;
         bbase += splat_tile<LEVELS, K, TW, TH, BATCH>(j, sm, bbase);
     }
 }
@@ -277,6 +280,7 @@ __global__ void __launch_bounds__(16 * 16 + 32, 2) splat_views_tm_kernel(SplatVi
                   a.coeff_bf16 ? reinterpret_cast<float*>(reinterpret_cast<__nv_bfloat16*>(a.coeff) + w.coeff_off)
                                : a.coeff + w.coeff_off,
                   a.final_T + w.pix_off, a.n_last + w.pix_off, a.status, a.coeff_bf16};
+        j.wait_ns = a.wait_ns;
         bbase += splat_tile_tm<C, LEVELS, K>(j, sm, bbase);
     }
     tc::fence_before();
@@ -427,8 +431,10 @@ cudaError_t launch_pack_dense(const PackArgs& a, cudaStream_t stream)
     return cudaGetLastError();
 }
 
-cudaError_t launch_splat_dense(int levels, const SplatArgs& a, cudaStream_t stream)
+cudaError_t launch_splat_dense(int levels, const SplatArgs& args, cudaStream_t stream)
 {
+    SplatArgs a = args;
+    a.wait_ns = wait_limit_ns();
     if (levels == 3) return launch_t<3, 4, 16, 16, true>(a, stream);
     if (levels == 1) return launch_t<1, 4, 16, 16, true>(a, stream);
     return cudaErrorInvalidValue;
@@ -461,17 +467,21 @@ cudaError_t launch_pack(const PackArgs& a, cudaStream_t stream, int V)
     return cudaGetLastError();
 }
 
-cudaError_t launch_splat_views(int levels, int K, int tw, int th, int batch, const SplatViewsArgs& a, int num_sms,
+cudaError_t launch_splat_views(int levels, int K, int tw, int th, int batch, const SplatViewsArgs& args, int num_sms,
                                cudaStream_t stream)
 {
+    SplatViewsArgs a = args;
+    a.wait_ns = wait_limit_ns();
     if (levels == 1 && K == 4) return launch_views_tile<1, 4>(a, tw, th, batch, num_sms, stream);
     if (levels == 2 && K == 4) return launch_views_tile<2, 4>(a, tw, th, batch, num_sms, stream);
     if (levels == 3 && K == 4) return launch_views_tile<3, 4>(a, tw, th, batch, num_sms, stream);
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_splat(int levels, int K, const SplatArgs& a, cudaStream_t stream)
+cudaError_t launch_splat(int levels, int K, const SplatArgs& args, cudaStream_t stream)
 {
+    SplatArgs a = args;
+    a.wait_ns = wait_limit_ns();
     if (levels == 1) {
         switch (K) {
             case 2: return launch_tile<1, 2>(a, stream);

@@ -103,6 +103,7 @@ struct SplatArgs {
     int32_t* status;
     int coeff_bf16 = 0;                 // write the coefficient map rounded to BF16 (nearest even)
     int L = 64;                         // codebook size (columns per level of the map)
+    uint64_t wait_ns = kDefaultWaitNs;  // bound of a wait on a stage barrier (set at launch)
 };
 
 constexpr int kMaxSplatViews = 64;
@@ -126,6 +127,7 @@ struct SplatViewsArgs {
     uint32_t* queue;                    // work-queue counter (zeroed by the launcher)
     int32_t* status;
     int coeff_bf16 = 0;                 // coefficient maps in BF16
+    uint64_t wait_ns = kDefaultWaitNs;  // bound of a wait on a stage barrier (set at launch)
 };
 
 bool splat_supported(int levels, int K, int L, int tw, int th);

@@ -22,9 +22,8 @@ struct TileJob {
     uint32_t* n_last;
     int32_t* status;
     int coeff_bf16 = 0;
+    uint64_t wait_ns = kDefaultWaitNs;   // bound of every wait on a stage barrier
 };
-
-constexpr uint64_t kWaitNs = 1000000000ull;   // bound of every wait on a stage barrier (1 s)
 
 // Shared memory of one CTA: accumulators [kWarps][kAccFloats], stage barriers and flags, then
 // kStages stages of [kBatch records][kBatch culling boxes (u, v, ex, ey)].  The barriers are
@@ -83,28 +82,40 @@ __device__ __forceinline__ uint32_t acc_ref(uint32_t off)
 }
 
 // Warp-uniform bounded wait for a barrier phase.  `done_warps` (optional) ends the wait early
-// once all_done consumer warps have finished; a wait that runs out raises the CTA's abort flag
-// (and the caller reports LSV2_ERR_TIMEOUT), after which every other wait returns at once.
+// once all_done consumer warps have finished; a wait that is still unfinished `limit_ns` after
+// it began (at once for 0) raises the CTA's abort flag (and the caller reports
+// LSV2_ERR_TIMEOUT), after which every other wait returns at once.
 __device__ __forceinline__ int warp_wait(uint64_t* bar, uint32_t parity, const volatile int* done_warps,
-                                         int all_done, volatile int* abort)
+                                         int all_done, volatile int* abort, uint64_t limit_ns)
 {
     const uint64_t t0 = tc::globaltimer();
     while (true) {
         if (__all_sync(0xffffffffu, tc::mbar_try(tc::smem_u32(bar), parity))) return kWaitDone;
         if (__shfl_sync(0xffffffffu, *abort, 0)) return kWaitAborted;
         if (done_warps && __shfl_sync(0xffffffffu, *done_warps, 0) >= all_done) return kWaitStopped;
-        if (__any_sync(0xffffffffu, tc::globaltimer() - t0 > kWaitNs)) {
+        if (__any_sync(0xffffffffu, tc::globaltimer() - t0 >= limit_ns)) {
             *abort = 1;
             return kWaitTimeout;
         }
     }
 }
 
+// Warp-uniform wait for a phase that this warp's own copies complete (they always land): used
+// to drain a CTA that is giving up, so it ignores the abort flag; bounded by kDrainNs.
+__device__ __forceinline__ bool warp_drain(uint64_t* bar, uint32_t parity)
+{
+    const uint64_t t0 = tc::globaltimer();
+    while (!__all_sync(0xffffffffu, tc::mbar_try(tc::smem_u32(bar), parity)))
+        if (__any_sync(0xffffffffu, tc::globaltimer() - t0 > kDrainNs)) return false;
+    return true;
+}
+
 // Producer warp: the tile's batch b is CTA batch g = bbase + b and goes to stage g % kStages
 // once every consumer warp has released the stage's previous batch; each lane copies one
 // record (bulk async copy, completing on the stage's barrier) and writes its culling box.
-// Before returning it waits until every copy it issued has landed, so no copy is in flight
-// into shared memory that is reused, and publishes the number of batches it issued.
+// Before returning it waits until every copy it issued has landed (also after a wait of the CTA
+// ran out), so no copy is in flight into shared memory that is reused or released, and
+// publishes the number of batches it issued.
 template <class C>
 __device__ void splat_produce(const TileJob& a, const SplatSmem<C>& sm, int lane, uint32_t bbase)
 {
@@ -116,7 +127,8 @@ __device__ void splat_produce(const TileJob& a, const SplatSmem<C>& sm, int lane
         const uint32_t g = bbase + b;
         const int s = (int)(g % C::kStages);
         if (g >= (uint32_t)C::kStages) {
-            const int w = warp_wait(sm.empty + s, ((g / C::kStages) - 1u) & 1u, done_warps, C::kWarps, sm.abort);
+            const int w =
+                warp_wait(sm.empty + s, ((g / C::kStages) - 1u) & 1u, done_warps, C::kWarps, sm.abort, a.wait_ns);
             if (w == kWaitTimeout && lane == 0) report(a.status, LSV2_ERR_TIMEOUT);
             if (w != kWaitDone) break;
         }
@@ -138,12 +150,14 @@ __device__ void splat_produce(const TileJob& a, const SplatSmem<C>& sm, int lane
         tc::mbar_arrive(full);
         issued = b + 1;
     }
+    // the last kStages batches' copies (each stage's earlier batches completed before its reuse)
     const uint32_t first = issued > (uint32_t)C::kStages ? issued - C::kStages : 0u;
     for (uint32_t b = first; b < issued; ++b) {
         const uint32_t g = bbase + b;
-        const int w = warp_wait(sm.full + (int)(g % C::kStages), (g / C::kStages) & 1u, nullptr, 0, sm.abort);
-        if (w == kWaitTimeout && lane == 0) report(a.status, LSV2_ERR_TIMEOUT);
-        if (w != kWaitDone) break;
+        if (!warp_drain(sm.full + (int)(g % C::kStages), (g / C::kStages) & 1u)) {
+            if (lane == 0) report(a.status, LSV2_ERR_TIMEOUT);
+            *sm.abort = 1;
+        }
     }
     if (lane == 0) *sm.issued = issued;
 }
@@ -200,7 +214,7 @@ __device__ uint32_t splat_consume(const TileJob& a, const SplatSmem<C>& sm, int 
         }
         if (wdone && __shfl_sync(0xffffffffu, *done_warps, 0) >= C::kWarps) break;
         // (the producer issues no further batch once every warp is done)
-        const int w = warp_wait(sm.full + s, (g / C::kStages) & 1u, done_warps, C::kWarps, sm.abort);
+        const int w = warp_wait(sm.full + s, (g / C::kStages) & 1u, done_warps, C::kWarps, sm.abort, a.wait_ns);
         if (w != kWaitDone) {
             if (w == kWaitTimeout && lane == 0) report(a.status, LSV2_ERR_TIMEOUT);
             if (!wdone && lane == 0) atomicAdd(sm.done_warps, 1);

@@ -104,8 +104,9 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t mbar_saddr, uint32_t byt
     asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(mbar_saddr), "r"(bytes) : "memory");
 }
 
-// Wait for the mbarrier phase with the given parity; gives up after `limit_ns` and returns false.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar_saddr, uint32_t parity, uint64_t limit_ns = 1000000000ull)
+// Wait for the mbarrier phase with the given parity; returns false once `limit_ns` have passed
+// without it (0: after the first unsuccessful check).
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar_saddr, uint32_t parity, uint64_t limit_ns)
 {
     const uint64_t t0 = globaltimer();
     while (true) {
@@ -117,7 +118,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar_saddr, uint32_t parity, 
             : "r"(mbar_saddr), "r"(parity)
             : "memory");
         if (done) return true;
-        if (globaltimer() - t0 > limit_ns) return false;
+        if (globaltimer() - t0 >= limit_ns) return false;
     }
 }
 

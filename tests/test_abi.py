@@ -66,3 +66,16 @@ def test_host_validation_rejects_bad_arguments(lib):
     assert lib.lsv2_query(1, 10, 64, 512, 16, 0, 16, 1, 4, 0, 10.0, 16, 1 << 20, 16, 0, 0, 0, 0) == 1
     with pytest.raises(L.LSV2Error):
         L.call("lsv2_decode", 1, 10, 32, 512, 16, 0, 16, 0, 16, 0, 0, 0)
+
+
+def test_wait_limit_setting_round_trips(lib):
+    """The bound of the kernels' device-side waits is a host setting read at launch (no GPU
+    needed to set it); default 1 s."""
+    assert L.lsv2_wait_limit_ns() == 1_000_000_000
+    try:
+        L.lsv2_set_wait_limit_ns(0)
+        assert L.lsv2_wait_limit_ns() == 0
+        L.lsv2_set_wait_limit_ns(123456789)
+        assert L.lsv2_wait_limit_ns() == 123456789
+    finally:
+        L.lsv2_set_wait_limit_ns(1_000_000_000)

@@ -1,0 +1,125 @@
+"""Failure detection on the device: a bounded wait that runs out.
+
+lsv2_set_wait_limit_ns(0) makes every wait of the pipelined kernels on another warp's progress
+give up at its first unsuccessful check, which drives the expiry path on purpose: the kernel
+records LSV2_ERR_TIMEOUT in the status word, lets the copies and MMAs it issued complete, frees
+its tensor memory and returns (no hang, no trap, the context stays usable).  After the default
+limit is restored, the next call on the same buffers gives the correct result.  No wait is left
+waiting on something that never happens: the limit only shortens waits on work that is in
+flight anyway.
+"""
+import numpy as np
+import pytest
+
+import lsv2_synth as syn
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2507_07136_b300 import _lib as L  # noqa: E402
+from paper_2507_07136_b300.pipeline import DeviceScene, Frame  # noqa: E402
+from paper_2507_07136_b300.views import ViewsBatch  # noqa: E402
+
+DEFAULT = 1_000_000_000
+
+
+@pytest.fixture(autouse=True)
+def default_limit_after():
+    L.lsv2_set_wait_limit_ns(DEFAULT)
+    yield
+    L.lsv2_set_wait_limit_ns(DEFAULT)
+
+
+def expire_then_recover(fr, run, outputs):
+    """run() once with the default limit (the reference), once with limit 0 (must report
+    LSV2_ERR_TIMEOUT and return), once more with the default limit on the same buffers (must
+    equal the reference bit for bit)."""
+    fr.status.zero_()
+    run()
+    fr.check()
+    ref = [o.clone() for o in outputs]
+    for o in outputs:
+        o.fill_(-7)
+    L.lsv2_set_wait_limit_ns(0)
+    fr.status.zero_()
+    run()
+    torch.cuda.synchronize()          # the kernels returned
+    assert int(fr.status.item()) == L.LSV2_ERR_TIMEOUT
+    L.lsv2_set_wait_limit_ns(DEFAULT)
+    for o in outputs:
+        o.fill_(-7)
+    fr.status.zero_()
+    run()
+    fr.check()
+    for o, r in zip(outputs, ref):
+        assert torch.equal(o, r)
+
+
+def three_level_frame():
+    sc = syn.make_scene(2000, 3, mean_kind="uniform", mean_param=1.0, log_scale_mu=-3.0, log_scale_sigma=0.3)
+    _, cam = syn.tiny()
+    fr = Frame(DeviceScene.from_numpy(sc), cam)
+    fr.project()
+    fr.bin_sort()
+    fr.check()
+    return fr
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8)])
+def test_splat_wait_expires_and_recovers(tile):
+    sc = syn.make_scene(2000, 3, mean_kind="uniform", mean_param=1.0, log_scale_mu=-3.0, log_scale_sigma=0.3)
+    _, cam = syn.tiny()
+    fr = Frame(DeviceScene.from_numpy(sc), cam.with_tile(*tile))
+    fr.project()
+    fr.bin_sort()
+    fr.check()
+    expire_then_recover(fr, fr.splat, [fr.coeff, fr.final_T, fr.n_last])
+
+
+def test_splat_bf16_wait_expires_and_recovers():
+    fr = three_level_frame()
+    fr.splat_bf16()
+    fr.check()
+    expire_then_recover(fr, fr.splat_bf16, [fr.coeff16, fr.final_T, fr.n_last])
+
+
+def test_fused_render_wait_expires_and_recovers():
+    fr = three_level_frame()
+    text = torch.as_tensor(syn.text_queries(syn.SEED + 2, 1, 4), device="cuda")
+    F = torch.empty((3, fr.P, 512), dtype=torch.bfloat16, device="cuda")
+    rel = torch.empty((1, 3, fr.P), dtype=torch.float32, device="cuda")
+    expire_then_recover(fr, lambda: fr.render_fused(F, text, rel), [F, rel, fr.final_T, fr.n_last])
+
+
+@pytest.mark.parametrize("from_bf16", [True, False])
+def test_decode_tc_wait_expires_and_recovers(from_bf16):
+    """BF16 map: W arrives by TMA tensor loads; FP32 map: through registers."""
+    fr = three_level_frame()
+    fr.splat()
+    fr.splat_bf16()
+    fr.check()
+    cb16 = fr.scene.codebook.to(torch.bfloat16)
+    F = torch.empty((3, fr.P, 512), dtype=torch.bfloat16, device="cuda")
+    expire_then_recover(fr, lambda: fr.decode(F, codebook=cb16, from_bf16=from_bf16), [F])
+
+
+@pytest.mark.parametrize("from_bf16", [True, False])
+def test_query_tc_wait_expires_and_recovers(from_bf16):
+    """BF16 map: the pipelined relevancy kernel; FP32 map: the converting one."""
+    fr = three_level_frame()
+    fr.splat()
+    fr.splat_bf16()
+    fr.check()
+    text = torch.as_tensor(syn.text_queries(syn.SEED + 2, 3, 4), device="cuda")
+    rel = torch.empty((3, 3, fr.P), dtype=torch.bfloat16, device="cuda")
+    expire_then_recover(fr, lambda: fr.query(text, rel, compute=L.LSV2_BF16, from_bf16=from_bf16), [rel])
+
+
+def test_views_wait_expires_and_recovers():
+    sc = syn.make_scene(4000, 3, seed=31, mean_kind="uniform", mean_param=1.0, log_scale_mu=-3.2, log_scale_sigma=0.4)
+    cams = [syn.orbit_camera(w, h, 4.0, azimuth_deg=40.0 * k) for k, (w, h) in enumerate([(160, 120), (97, 131)])]
+    text = torch.as_tensor(syn.text_queries(syn.SEED + 2, 3, 4), device="cuda")
+    ds = DeviceScene.from_numpy(sc)
+    vb = ViewsBatch(ds, cams, 3, 4)
+    expire_then_recover(vb, lambda: vb.run(text), [vb.rel])
+    assert np.isfinite(vb.rel.float().cpu().numpy()).all()
