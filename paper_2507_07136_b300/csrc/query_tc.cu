@@ -314,18 +314,20 @@ __host__ __device__ constexpr size_t pipe_smem_bytes(int npad, int ntp)
 }
 
 // Bounded wait on a barrier phase: false once the CTA's abort flag is up, or when the phase is
-// still incomplete limit_ns after the wait began (which raises the flag; at once for 0).
+// still incomplete limit_ns after the wait began (which raises the flag).  The first check is a
+// non-blocking test, so with limit 0 the wait gives up unless the phase is complete at once.
 __device__ __forceinline__ bool pipe_wait(uint32_t bar, uint32_t parity, volatile int* abort, uint64_t limit_ns)
 {
     const uint64_t t0 = tc::globaltimer();
-    while (!tc::mbar_try(bar, parity)) {
+    if (tc::mbar_test(bar, parity)) return true;
+    while (true) {
         if (*abort) return false;
         if (tc::globaltimer() - t0 >= limit_ns) {
             *abort = 1;
             return false;
         }
+        if (tc::mbar_try(bar, parity)) return true;
     }
-    return true;
 }
 
 // NB: epilogue warpgroups = TMEM accumulators (a template parameter, so that the per-tile ring

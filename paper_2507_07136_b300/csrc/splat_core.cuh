@@ -83,14 +83,17 @@ __device__ __forceinline__ uint32_t acc_ref(uint32_t off)
 
 // Warp-uniform bounded wait for a barrier phase.  `done_warps` (optional) ends the wait early
 // once all_done consumer warps have finished; a wait that is still unfinished `limit_ns` after
-// it began (at once for 0) raises the CTA's abort flag (and the caller reports
-// LSV2_ERR_TIMEOUT), after which every other wait returns at once.
+// it began raises the CTA's abort flag (and the caller reports LSV2_ERR_TIMEOUT), after which
+// every other wait returns at once.  The first check is a non-blocking test (a try_wait may
+// suspend the warp until the phase completes), so with limit 0 the wait gives up unless the
+// phase is complete when it starts.
 __device__ __forceinline__ int warp_wait(uint64_t* bar, uint32_t parity, const volatile int* done_warps,
                                          int all_done, volatile int* abort, uint64_t limit_ns)
 {
     const uint64_t t0 = tc::globaltimer();
-    while (true) {
-        if (__all_sync(0xffffffffu, tc::mbar_try(tc::smem_u32(bar), parity))) return kWaitDone;
+    for (bool first = true;; first = false) {
+        const bool ready = first ? tc::mbar_test(tc::smem_u32(bar), parity) : tc::mbar_try(tc::smem_u32(bar), parity);
+        if (__all_sync(0xffffffffu, ready)) return kWaitDone;
         if (__shfl_sync(0xffffffffu, *abort, 0)) return kWaitAborted;
         if (done_warps && __shfl_sync(0xffffffffu, *done_warps, 0) >= all_done) return kWaitStopped;
         if (__any_sync(0xffffffffu, tc::globaltimer() - t0 >= limit_ns)) {

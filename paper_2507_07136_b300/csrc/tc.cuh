@@ -93,6 +93,20 @@ __device__ __forceinline__ bool mbar_try(uint32_t mbar_saddr, uint32_t parity)
     return done != 0;
 }
 
+// Non-blocking test of the phase with the given parity (acquire semantics): unlike try_wait it
+// never suspends the thread, so it reports the state at the moment of the check.
+__device__ __forceinline__ bool mbar_test(uint32_t mbar_saddr, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar_saddr), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
 // Arrival (release semantics) without and with a transaction-count increase, and a bare
 // transaction-count increase.
 __device__ __forceinline__ void mbar_arrive(uint32_t mbar_saddr)
@@ -105,11 +119,14 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t mbar_saddr, uint32_t byt
 }
 
 // Wait for the mbarrier phase with the given parity; returns false once `limit_ns` have passed
-// without it (0: after the first unsuccessful check).
+// without it.  The first check is a non-blocking test, so with limit 0 the wait gives up unless
+// the phase is complete when it starts.
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar_saddr, uint32_t parity, uint64_t limit_ns)
 {
     const uint64_t t0 = globaltimer();
+    if (mbar_test(mbar_saddr, parity)) return true;
     while (true) {
+        if (globaltimer() - t0 >= limit_ns) return false;
         uint32_t done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -118,7 +135,6 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar_saddr, uint32_t parity, 
             : "r"(mbar_saddr), "r"(parity)
             : "memory");
         if (done) return true;
-        if (globaltimer() - t0 >= limit_ns) return false;
     }
 }
 

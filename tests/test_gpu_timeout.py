@@ -1,7 +1,8 @@
 """Failure detection on the device: a bounded wait that runs out.
 
 lsv2_set_wait_limit_ns(0) makes every wait of the pipelined kernels on another warp's progress
-give up at its first unsuccessful check, which drives the expiry path on purpose: the kernel
+give up unless its phase is complete at the first (non-blocking) check, which drives the expiry
+path on purpose: the kernel
 records LSV2_ERR_TIMEOUT in the status word, lets the copies and MMAs it issued complete, frees
 its tensor memory and returns (no hang, no trap, the context stays usable).  After the default
 limit is restored, the next call on the same buffers gives the correct result.  No wait is left
@@ -55,8 +56,14 @@ def expire_then_recover(fr, run, outputs):
         assert torch.equal(o, r)
 
 
+def dense_scene():
+    """20,000 Gaussians in the tiny scene's volume: hundreds of records per tile, so a splat's
+    producer reaches a stage its consumers still hold (the wait that a limit of 0 makes expire)."""
+    return syn.make_scene(20000, 3, mean_kind="uniform", mean_param=1.0, log_scale_mu=-3.0, log_scale_sigma=0.3)
+
+
 def three_level_frame():
-    sc = syn.make_scene(2000, 3, mean_kind="uniform", mean_param=1.0, log_scale_mu=-3.0, log_scale_sigma=0.3)
+    sc = dense_scene()
     _, cam = syn.tiny()
     fr = Frame(DeviceScene.from_numpy(sc), cam)
     fr.project()
@@ -67,7 +74,7 @@ def three_level_frame():
 
 @pytest.mark.parametrize("tile", [(16, 16), (8, 8)])
 def test_splat_wait_expires_and_recovers(tile):
-    sc = syn.make_scene(2000, 3, mean_kind="uniform", mean_param=1.0, log_scale_mu=-3.0, log_scale_sigma=0.3)
+    sc = dense_scene()
     _, cam = syn.tiny()
     fr = Frame(DeviceScene.from_numpy(sc), cam.with_tile(*tile))
     fr.project()
@@ -116,7 +123,7 @@ def test_query_tc_wait_expires_and_recovers(from_bf16):
 
 
 def test_views_wait_expires_and_recovers():
-    sc = syn.make_scene(4000, 3, seed=31, mean_kind="uniform", mean_param=1.0, log_scale_mu=-3.2, log_scale_sigma=0.4)
+    sc = dense_scene()
     cams = [syn.orbit_camera(w, h, 4.0, azimuth_deg=40.0 * k) for k, (w, h) in enumerate([(160, 120), (97, 131)])]
     text = torch.as_tensor(syn.text_queries(syn.SEED + 2, 3, 4), device="cuda")
     ds = DeviceScene.from_numpy(sc)
