@@ -61,6 +61,60 @@ def peaks():
         return FALLBACK_PEAKS, "fallback"
 
 
+class _CtypesNvml:
+    """The few read-only NVML queries the clock sampler makes, through libnvidia-ml directly (for
+    hosts without the pynvml module).  Names and constants follow NVML's C API."""
+
+    NVML_CLOCK_SM = 1
+    nvmlClocksEventReasonSwPowerCap = 0x4
+    nvmlClocksEventReasonHwSlowdown = 0x8
+    nvmlClocksEventReasonSwThermalSlowdown = 0x20
+    nvmlClocksEventReasonHwThermalSlowdown = 0x40
+    nvmlClocksEventReasonHwPowerBrakeSlowdown = 0x80
+
+    def __init__(self):
+        import ctypes
+        self.C = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+
+    def _ok(self, r):
+        if r != 0:
+            raise RuntimeError(f"NVML error {r}")
+
+    def nvmlInit(self):
+        self._ok(self.lib.nvmlInit_v2())
+
+    def _handle(self, fn, arg):
+        h = self.C.c_void_p()
+        self._ok(fn(arg, self.C.byref(h)))
+        return h
+
+    def nvmlDeviceGetHandleByPciBusId(self, bus):
+        return self._handle(self.lib.nvmlDeviceGetHandleByPciBusId_v2, self.C.c_char_p(bus.encode()))
+
+    def nvmlDeviceGetHandleByIndex(self, i):
+        return self._handle(self.lib.nvmlDeviceGetHandleByIndex_v2, self.C.c_uint(i))
+
+    def _uint(self, fn, h, *args):
+        v = self.C.c_uint()
+        self._ok(fn(h, *args, self.C.byref(v)))
+        return v.value
+
+    def nvmlDeviceGetClockInfo(self, h, which):
+        return self._uint(self.lib.nvmlDeviceGetClockInfo, h, self.C.c_int(which))
+
+    def nvmlDeviceGetMaxClockInfo(self, h, which):
+        return self._uint(self.lib.nvmlDeviceGetMaxClockInfo, h, self.C.c_int(which))
+
+    def nvmlDeviceGetPowerUsage(self, h):
+        return self._uint(self.lib.nvmlDeviceGetPowerUsage, h)
+
+    def nvmlDeviceGetCurrentClocksEventReasons(self, h):
+        v = self.C.c_ulonglong()
+        self._ok(self.lib.nvmlDeviceGetCurrentClocksEventReasons(h, self.C.byref(v)))
+        return v.value
+
+
 class ClockSampler:
     """SM clock, power and clock-event (throttle) reasons sampled while the timed region runs.
 
@@ -87,7 +141,10 @@ class ClockSampler:
         self.nvml_error = None
 
     def _nvml_handle(self):
-        import pynvml
+        try:
+            import pynvml
+        except ImportError:
+            pynvml = _CtypesNvml()
         pynvml.nvmlInit()
         try:
             import torch
@@ -390,7 +447,7 @@ def backward_section(dev, reps: int = 10):
 
     def l1():
         Lb.lsv2_l1_decode_backward(lev, P, 64, D, _ptr(fr.coeff), _ptr(scene.codebook), _ptr(target), _ptr(loss),
-                                   _ptr(dcoeff), _ptr(dcb), st)
+                                   _ptr(dcoeff), _ptr(dcb), _ptr(fr.status), st)
 
     def bwd():
         Lb.lsv2_splat_backward(fr.ccam, n, _ptr(scene.means), _ptr(scene.scales), _ptr(scene.quats), fr.proj,

@@ -50,7 +50,7 @@
 extern "C" {
 #endif
 
-#define LSV2_ABI_VERSION 1
+#define LSV2_ABI_VERSION 2
 
 typedef enum {
     LSV2_OK = 0,
@@ -372,15 +372,25 @@ lsv2_status lsv2_postprocess(int32_t Q, int32_t levels, int32_t H, int32_t W, co
                              int32_t* point, int32_t* level, float* score, uint8_t* mask,
                              int32_t* dev_status, void* stream);
 
-/* Backward of Loss = mean_{lev,p,d} |F - target| with F = W S (decode + L1 adjoint).
+/* Backward of Loss = mean_{lev,p,d} |F - target| with F = W S (Eq. 7's decode; the L1 loss and its
+ * adjoint have no counterpart in the paper, which trains the field without stating a gradient):
+ *   G = sign(F - target) / (levels P D)  (sign(0) = 0),  dLoss/dW = G S^T,  dLoss/dS = W^T G.
+ *   coeff     float[levels][P][L]   W
+ *   codebook  float[levels][L][D]   S
+ *   target    float[levels][P][D]
  *   loss      float (device scalar, accumulated: zero it first)
  *   dcoeff    float[levels][P][L]   dLoss/dW  (overwritten)
  *   dcodebook float[levels][L][D]   dLoss/dS  (accumulated: zero it first)
- * sign(0) = 0.  F is recomputed, not read. */
+ * F is recomputed, not read or stored.  The three products run on the tensor cores with W and S
+ * split into BF16 high and low parts (FP32 accumulation): dW and dS within about 4e-6 of the exact
+ * products relative to sum |G| |S| and sum |W| |G|; every sign is the sign of the exact F - target
+ * (elements whose tensor-core F lies within its error bound of the target are recomputed in FP64).
+ * L = 64, D a multiple of 128 up to 512, P < 2^31 - 256, all arrays 16-byte aligned.  A bounded
+ * device wait that expires sets LSV2_ERR_TIMEOUT in *dev_status (may be NULL). */
 lsv2_status lsv2_l1_decode_backward(int32_t levels, int64_t P, int32_t L, int32_t D,
                                     const float* coeff, const float* codebook,
                                     const float* target, float* loss, float* dcoeff,
-                                    float* dcodebook, void* stream);
+                                    float* dcodebook, int32_t* dev_status, void* stream);
 
 /* Workspace for lsv2_splat_backward: per-Gaussian 2D-mean and conic gradients. */
 size_t lsv2_splat_backward_workspace_bytes(int64_t n);

@@ -73,7 +73,7 @@ _SIGS = {
     "lsv2_sparsify_backward": ([I64, I32, I32, P, P, P, P, P], I32),
     "lsv2_postprocess_workspace_bytes": ([I32, I32], SZ),
     "lsv2_postprocess": ([I32, I32, I32, I32, P, I32, I32, I32, F32, P, SZ, P, P, P, P, P, P, P], I32),
-    "lsv2_l1_decode_backward": ([I32, I64, I32, I32, P, P, P, P, P, P, P], I32),
+    "lsv2_l1_decode_backward": ([I32, I64, I32, I32, P, P, P, P, P, P, P, P], I32),
     "lsv2_splat_backward_workspace_bytes": ([I64], SZ),
     "lsv2_splat_backward": ([P, I64, P, P, P, P, P, P, I32, I32, I32, P, P, P, P, P, P, SZ, P, P, P, P, P, P, P],
                             I32),
@@ -194,8 +194,9 @@ def lsv2_query_views(V, cams, n, means, scales, quats, opacity, levels, K, L, id
          text, tau, capacity, stage_batch, ws, ws_bytes, rel, rel_dtype, dev_num, dev_status, stream)
 
 
-def lsv2_l1_decode_backward(levels, P_, L, D, coeff, codebook, target, loss, dcoeff, dcodebook, stream):
-    call("lsv2_l1_decode_backward", levels, P_, L, D, coeff, codebook, target, loss, dcoeff, dcodebook, stream)
+def lsv2_l1_decode_backward(levels, P_, L, D, coeff, codebook, target, loss, dcoeff, dcodebook, dev_status, stream):
+    call("lsv2_l1_decode_backward", levels, P_, L, D, coeff, codebook, target, loss, dcoeff, dcodebook, dev_status,
+         stream)
 
 
 def lsv2_splat_backward_workspace_bytes(n) -> int:

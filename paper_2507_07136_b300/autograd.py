@@ -35,7 +35,8 @@ class RenderL1(torch.autograd.Function):
         dcoeff = torch.empty_like(frame.coeff)
         dcodebook = torch.zeros_like(scene.codebook)
         L.lsv2_l1_decode_backward(lev, P, 64, D, _ptr(frame.coeff), _ptr(scene.codebook), _ptr(target.contiguous()),
-                                  _ptr(loss), _ptr(dcoeff), _ptr(dcodebook), _stream(None))
+                                  _ptr(loss), _ptr(dcoeff), _ptr(dcodebook), _ptr(frame.status), _stream(None))
+        frame.check()
         ctx.frame, ctx.dcoeff, ctx.dcodebook = frame, dcoeff, dcodebook
         return loss[0]
 

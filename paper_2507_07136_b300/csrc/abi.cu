@@ -269,15 +269,16 @@ lsv2_status lsv2_query(int32_t levels, int64_t P, int32_t L, int32_t D, const vo
 
 lsv2_status lsv2_l1_decode_backward(int32_t levels, int64_t P, int32_t L, int32_t D, const float* coeff,
                                     const float* codebook, const float* target, float* loss, float* dcoeff,
-                                    float* dcodebook, void* stream)
+                                    float* dcodebook, int32_t* dev_status, void* stream)
 {
     if (levels < 1 || P < 0 || !coeff || !codebook || !target || !loss || !dcoeff || !dcodebook)
         return LSV2_ERR_INVALID_ARGUMENT;
     if (L != 64 || D <= 0 || D % 128 != 0 || D > 512) return LSV2_ERR_UNSUPPORTED;
+    if (P > (int64_t)0x7FFFFF00ll) return LSV2_ERR_UNSUPPORTED;
     if (!aligned16(coeff) || !aligned16(codebook) || !aligned16(target) || !aligned16(dcoeff))
         return LSV2_ERR_INVALID_ARGUMENT;
-    return cuda_status(launch_l1_decode_backward(levels, P, D, coeff, codebook, target, loss, dcoeff, dcodebook,
-                                                 sm_count(), S(stream)));
+    return cuda_status(launch_l1_decode_backward_tc(levels, P, D, coeff, codebook, target, loss, dcoeff, dcodebook,
+                                                    sm_count(), dev_status, S(stream)));
 }
 
 size_t lsv2_splat_backward_workspace_bytes(int64_t n)

@@ -33,7 +33,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_version_and_status_strings(lib):
-    assert L.lsv2_abi_version() == 1
+    assert L.lsv2_abi_version() == 2
     assert lib.lsv2_status_string(0) == b"ok"
     assert lib.lsv2_status_string(3) == b"instance capacity exceeded"
 

@@ -77,7 +77,7 @@ def test_l1_decode_backward_matches_oracle():
     dS = torch.zeros_like(ds.codebook)
     tg = torch.as_tensor(target, device="cuda")
     L.lsv2_l1_decode_backward(1, fr.P, 64, 512, _ptr(fr.coeff), _ptr(ds.codebook), _ptr(tg), _ptr(loss), _ptr(dW),
-                              _ptr(dS), _stream(None))
+                              _ptr(dS), _ptr(fr.status), _stream(None))
     fr.check()
     # reference from the GPU's own W (isolates the decode/L1 adjoint)
     Wg = fr.coeff.cpu().numpy().astype(np.float64)
