@@ -10,27 +10,32 @@
 // G (S_hi + S_lo)^T, dS^T uses G^T (W_hi + W_lo), F uses W_hi S_hi + W_hi S_lo + W_lo S_hi.
 //
 // Sign decisions.  The split products leave |F_tc - F| below about 1.2e-5 sum_l |W_l| |S_ld|.
-// Where |F_tc - target| < tau_p = 1.3e-5 (sum_l |W_pl|) max|S|, F is recomputed in FP64 from the
-// FP32 inputs, so every sign is the sign of the exact F - target (up to FP64 rounding); such
-// elements are rare (a few per tile), and the loss takes their FP64 residual too.
+// Where |F_tc - target| < tau_p = 1.3e-5 (sum_l |W_pl|) max|S| (a few elements per tile), the
+// sign is provisional: it goes into G, the element is listed, and at the end of the kernel the
+// residual is evaluated from the FP32 inputs as if in twice FP32 precision (Dot2); where its
+// sign differs, dW and dS get the difference of the two signs' terms.  So every sign is the sign
+// of the exact F - target, and the loss takes the accurate residual of the listed elements.
 //
 // One CTA per SM, persistent over the level's tiles; 224 KB of shared memory:
-//  * S_hi, S_lo resident as blocks of 64 features (64 codebook rows x 128 bytes, 128-byte
-//    swizzle): the MN-major B operand of F (K = codebook row, N = feature) and, the same
-//    bytes, the K-major B operand of dW (N = codebook row, K = feature).
+//  * S resident as blocks of 64 features, each S_hi (64 codebook rows x 128 bytes, 128-byte
+//    swizzle) followed by S_lo: the MN-major B operand of F (K = codebook row, N = feature) and,
+//    the same bytes, the K-major B operand of dW with N = 128 rows (S_hi rows then S_lo rows, so
+//    one MMA forms G S_hi^T and G S_lo^T side by side).
 //  * W_hi, W_lo of the tile (128 pixel rows x 64 BF16): the K-major A operand of F and the
 //    MN-major B operand of dS^T (K = pixel, N = codebook row).
 //  * G of one 128-feature chunk as two 64-feature atoms (128 pixel rows x 128 bytes): the
 //    K-major A operand of dW and the MN-major A operand of dS^T (K = pixel, M = feature).
 //  * the target through a two-stage ring of TMA tensor loads (128 pixels x 32 features FP32,
 //    128-byte swizzle), with L2 prefetches of the boxes eight stages ahead.
-//  * TMEM: the F chunk in columns [0, 128), dW [128, 192), dS^T [256, 256 + D / 2) (one
-//    64-column block per 128 features, lane = feature).
+//  * TMEM: the F chunk in columns [0, 128), dW [128, 256) (G S_hi^T, then G S_lo^T), dS^T
+//    [256, 256 + D / 2) (one 64-column block per 128 features, lane = feature).
 // Warps: 0 TMA producer; 1 MMA issuer (and TMEM owner); 2-9 epilogue (warp w reads TMEM lane
 // quarter w % 4, i.e. 32 pixels; warps 2-5 take features 0-15 and warps 6-9 features 16-31 of
 // each ring stage; all eight load and split the next tile's W).  Per chunk the MMA warp issues F
-// of the chunk, then dW and dS^T of the previous chunk once its G is written, so the next F
-// overlaps the epilogue.  Every wait is bounded (the caller's limit); a CTA that gives up
+// of the chunk, then dS^T and dW of the previous chunk once its G is written, so the next F
+// overlaps the epilogue.  The epilogue keeps a chunk's signs in registers while it drains the
+// ring and writes G once the previous chunk's MMAs have read it, so the target stream does not
+// wait for the tensor cores.  Every wait is bounded (the caller's limit); a CTA that gives up
 // records LSV2_ERR_TIMEOUT, lets its TMA loads and MMAs complete and frees TMEM.
 #include <cuda_bf16.h>
 
@@ -52,16 +57,18 @@ constexpr int kPrefetch = 8;                     // ring stages prefetched into 
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kSBlock = kL * 128;                // 64 codebook rows x 64 features BF16 (8 KB)
+constexpr int kSStride = 2 * kSBlock;            // a feature block: S_hi then S_lo
 constexpr int kMaxD = 512;
-constexpr int kSHi = 0;
-constexpr int kSLo = kSHi + (kMaxD / 64) * kSBlock;
-constexpr int kWHi = kSLo + (kMaxD / 64) * kSBlock;
+constexpr int kS = 0;
+constexpr int kWHi = kS + (kMaxD / 64) * kSStride;
 constexpr int kWLo = kWHi + kM * 128;
 constexpr int kGAtom = kM * 128;                 // 64 features of G (16 KB)
 constexpr int kG = kWLo + kM * 128;
 constexpr int kRing = kG + 2 * kGAtom;
 constexpr int kMisc = kRing + kStages * kStageBytes;
-constexpr int kSmemBytes = 1024 + kMisc + 768;   // alignment slack; barriers and pixel sums
+constexpr int kFixCap = 160;                     // listed near-tie elements per CTA
+constexpr int kWsumOff = 128, kFixOff = kWsumOff + kM * 4;
+constexpr int kSmemBytes = 1024 + kMisc + kFixOff + 8 * kFixCap;   // alignment slack; barriers, sums, list
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kColF = 0, kColDW = 128, kColDS = 256;
 constexpr float kTieRel = 1.3e-5f;
@@ -117,6 +124,17 @@ __device__ __forceinline__ void split4(const float4& v, uint2& hi, uint2& lo)
 
 // BF16 bits of sign(r) (sign(0) = 0)
 __device__ __forceinline__ uint32_t sign_bf16(float r) { return r > 0.0f ? 0x3F80u : (r < 0.0f ? 0xBF80u : 0u); }
+
+// sum_l W_l S_ld - t from the FP32 inputs, accumulated as if in twice FP32 precision (Dot2)
+// and rounded: its sign is the sign of the exact residual unless that is within about 1e-13 of
+// sum_l |W_l| |S_ld|.
+__device__ float exact_residual(const float* w_row, const float* S, int D, int d, float t)
+{
+    float hi = -t, lo = 0.0f;
+#pragma unroll 8
+    for (int l = 0; l < kL; ++l) dot2_step(__ldg(w_row + l), __ldg(S + (size_t)l * D + d), hi, lo);
+    return __fadd_rn(hi, lo);
+}
 
 template <int N>
 __device__ __forceinline__ void tie_regs(uint32_t (&v)[N])
@@ -178,7 +196,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 11);
     volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
     unsigned* smax_bits = reinterpret_cast<unsigned*>(tslot + 2);
-    float* wsum = reinterpret_cast<float*>(smem + kMisc + 128);   // [kM] sum_l |W| of the tile's pixels
+    unsigned* fix_count = reinterpret_cast<unsigned*>(tslot + 3);
+    float* wsum = reinterpret_cast<float*>(smem + kMisc + kWsumOff);        // [kM] sum_l |W| of the tile's pixels
+    uint64_t* fix = reinterpret_cast<uint64_t*>(smem + kMisc + kFixOff);   // [kFixCap] listed near ties
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int lev = blockIdx.y;
     const int D = a.D, nc = D / kDC;
@@ -204,9 +224,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc::mbar_init(tc::smem_u32(dw_full), 1);
         *abort = 0;
         *smax_bits = 0u;
+        *fix_count = 0u;
     }
     __syncthreads();
-    // S of the level -> S_hi, S_lo: element (l, d) in block d / 64 at byte sw128(l, d % 64); and max |S|
+    // S of the level -> S_hi, S_lo: element (l, d) of feature block d / 64 at byte sw128(l, d % 64)
+    // of its S_hi (S_lo 8 KB further); and max |S|
     float smax_local = 0.0f;
     const int d4n = D / 4;
     for (int i = tid; i < kL * d4n; i += kThreads) {
@@ -214,9 +236,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         const float4 v = __ldg(reinterpret_cast<const float4*>(Sl + (size_t)l * D + d));
         uint2 hi, lo;
         split4(v, hi, lo);
-        const uint32_t off = (uint32_t)(d >> 6) * kSBlock + tc::sw128(l, d & 63);
-        *reinterpret_cast<uint2*>(smem + kSHi + off) = hi;
-        *reinterpret_cast<uint2*>(smem + kSLo + off) = lo;
+        const uint32_t off = (uint32_t)(d >> 6) * kSStride + tc::sw128(l, d & 63);
+        *reinterpret_cast<uint2*>(smem + kS + off) = hi;
+        *reinterpret_cast<uint2*>(smem + kS + kSBlock + off) = lo;
         smax_local = fmaxf(smax_local, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
     }
     for (int o = 16; o > 0; o >>= 1) smax_local = fmaxf(smax_local, __shfl_xor_sync(0xffffffffu, smax_local, o));
@@ -268,30 +290,21 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ---- MMA issuer
         if (lane == 0 && my_tiles > 0) {
             const uint32_t idF = tc::idesc_bf16_major(kM, kDC, false, true);
-            const uint32_t idW = tc::idesc_bf16_major(kM, kL, false, false);
+            const uint32_t idW = tc::idesc_bf16_major(kM, 2 * kL, false, false);
             const uint32_t idS = tc::idesc_bf16_major(kM, kL, true, true);
             const uint32_t sb = tc::smem_u32(smem);
-            const uint32_t sHi = sb + kSHi, sLo = sb + kSLo, wHi = sb + kWHi, wLo = sb + kWLo, gB = sb + kG;
+            const uint32_t sHi = sb + kS, sLo = sb + kS + kSBlock, wHi = sb + kWHi, wLo = sb + kWLo, gB = sb + kG;
             uint32_t last_bar = 0, last_par = 0;   // the latest commit (it covers every earlier MMA)
             auto commit = [&](uint64_t* b, uint32_t par) {
                 tc::mma_commit(tc::smem_u32(b));
                 last_bar = tc::smem_u32(b);
                 last_par = par;
             };
-            // dW and dS^T of chunk cc (global chunk g) of local tile i, once its G is written
-            auto grads = [&](int g, int cc, int i) -> bool {
+            // dS^T and dW of chunk cc (global chunk g) of local tile i, once its G is written; at the
+            // tile's last chunk W is released (w_free) as soon as dS^T, its last reader, is issued
+            auto grads = [&](int g, int cc, int i, bool last) -> bool {
                 if (!bw_wait(tc::smem_u32(g_full), (uint32_t)(g & 1), abort, a.wait_ns)) return false;
                 tc::fence_after();
-                for (int t = 0; t < 2; ++t) {
-                    const uint32_t sB = t ? sLo : sHi;
-#pragma unroll
-                    for (int j = 0; j < kDC / 16; ++j) {
-                        const int d0 = cc * kDC + 16 * j;
-                        tc::mma_bf16(tmem + kColDW, tc::desc_sw128(gB + (uint32_t)(j >> 2) * kGAtom + (uint32_t)(j & 3) * 32),
-                                     tc::desc_sw128(sB + (uint32_t)(d0 >> 6) * kSBlock + (uint32_t)(j & 3) * 32), idW,
-                                     (cc > 0 || t > 0 || j > 0) ? 1u : 0u);
-                    }
-                }
                 for (int t = 0; t < 2; ++t) {
                     const uint32_t wB = t ? wLo : wHi;
 #pragma unroll
@@ -300,7 +313,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                                      tc::desc_sw128_mn(wB + (uint32_t)j * 2048, kGAtom), idS,
                                      (i > 0 || t > 0 || j > 0) ? 1u : 0u);
                 }
+                if (last) commit(w_free, (uint32_t)(i & 1));
+                // dW += G [S_hi | S_lo]^T: N = 128 rows, the feature block's S_hi rows then its S_lo rows
+#pragma unroll
+                for (int j = 0; j < kDC / 16; ++j) {
+                    const int d0 = cc * kDC + 16 * j;
+                    tc::mma_bf16(tmem + kColDW, tc::desc_sw128(gB + (uint32_t)(j >> 2) * kGAtom + (uint32_t)(j & 3) * 32),
+                                 tc::desc_sw128(sHi + (uint32_t)(d0 >> 6) * kSStride + (uint32_t)(j & 3) * 32), idW,
+                                 (cc > 0 || j > 0) ? 1u : 0u);
+                }
                 commit(g_free, (uint32_t)(g & 1));
+                if (last) commit(dw_full, (uint32_t)(i & 1));
                 return true;
             };
             bool ok = true;
@@ -321,22 +344,20 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                         for (int k = 0; k < kL / 16; ++k)
                             tc::mma_bf16(tmem + kColF, tc::desc_sw128(aB + (uint32_t)k * 32),
-                                         tc::desc_sw128_mn(bB + (uint32_t)(2 * c) * kSBlock + (uint32_t)k * 2048, kSBlock),
+                                         tc::desc_sw128_mn(bB + (uint32_t)(2 * c) * kSStride + (uint32_t)k * 2048, kSStride),
                                          idF, (t > 0 || k > 0) ? 1u : 0u);
                     }
                     commit(f_full, (uint32_t)(gc & 1));
-                    if (c > 0 && !grads(gc - 1, c - 1, i)) {
+                    if (c > 0 && !grads(gc - 1, c - 1, i, false)) {
                         ok = false;
                         break;
                     }
                 }
                 if (!ok) break;
-                if (!grads(gc - 1, nc - 1, i)) {
+                if (!grads(gc - 1, nc - 1, i, true)) {
                     ok = false;
                     break;
                 }
-                commit(dw_full, (uint32_t)(i & 1));
-                commit(w_free, (uint32_t)(i & 1));
             }
             if (!ok) report(a.status, LSV2_ERR_TIMEOUT);
             if (last_bar) (void)tc::mbar_wait(last_bar, last_par, kDrainNs);
@@ -382,11 +403,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tc::fence_before();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(tc::smem_u32(f_free));
-                if (gc > 0 && !bw_wait_warp(tc::smem_u32(g_free), (uint32_t)((gc - 1) & 1), abort, a.wait_ns)) {
-                    ok = false;
-                    break;
-                }
                 float lsum = 0.0f;
+                uint32_t gb[kStagesPerChunk][8];   // the chunk's signs (BF16 pairs) until G is free
                 uint64_t ties = 0;
 #pragma unroll
                 for (int s = 0; s < kStagesPerChunk; ++s, ++k) {
@@ -405,39 +423,49 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     __syncwarp();
                     if (lane == 0) tc::mbar_arrive(tc::smem_u32(ring_empty + slot));
-                    uint32_t gb[8];
 #pragma unroll
                     for (int j = 0; j < 16; j += 2) {
                         const float r0 = __uint_as_float(f[s][j]) - t[j], r1 = __uint_as_float(f[s][j + 1]) - t[j + 1];
-                        const bool n0 = fabsf(r0) < tau, n1 = fabsf(r1) < tau;   // near ties: settled below
+                        const bool n0 = fabsf(r0) < tau, n1 = fabsf(r1) < tau;   // near ties: settled later
                         lsum += (n0 ? 0.0f : fabsf(r0)) + (n1 ? 0.0f : fabsf(r1));
                         ties |= (uint64_t)n0 << (16 * s + j);
                         ties |= (uint64_t)n1 << (16 * s + j + 1);
-                        gb[j / 2] = sign_bf16(r0) | (sign_bf16(r1) << 16);
+                        gb[s][j / 2] = sign_bf16(r0) | (sign_bf16(r1) << 16);
                     }
-                    // G, row `row`, features fo .. fo + 15 of the chunk (atom fo / 64)
-                    const int fo = kSD * s + 16 * h;
-                    uint8_t* gA = smem + kG + (fo >> 6) * kGAtom;
-                    *reinterpret_cast<uint4*>(gA + tc::sw128(row, fo & 63)) = make_uint4(gb[0], gb[1], gb[2], gb[3]);
-                    *reinterpret_cast<uint4*>(gA + tc::sw128(row, (fo & 63) + 8)) = make_uint4(gb[4], gb[5], gb[6], gb[7]);
                 }
                 if (!ok) break;
-                // near ties: the sign of the exact residual, from F recomputed in FP64 (rare)
+                // G of this chunk once the previous chunk's MMAs have read the buffer: row `row`,
+                // features fo .. fo + 15 of the chunk (atom fo / 64) per ring stage
+                if (gc > 0 && !bw_wait_warp(tc::smem_u32(g_free), (uint32_t)((gc - 1) & 1), abort, a.wait_ns)) {
+                    ok = false;
+                    break;
+                }
+#pragma unroll
+                for (int s = 0; s < kStagesPerChunk; ++s) {
+                    const int fo = kSD * s + 16 * h;
+                    uint8_t* gA = smem + kG + (fo >> 6) * kGAtom;
+                    *reinterpret_cast<uint4*>(gA + tc::sw128(row, fo & 63)) = make_uint4(gb[s][0], gb[s][1], gb[s][2], gb[s][3]);
+                    *reinterpret_cast<uint4*>(gA + tc::sw128(row, (fo & 63) + 8)) =
+                        make_uint4(gb[s][4], gb[s][5], gb[s][6], gb[s][7]);
+                }
+                // near ties: listed with their provisional sign for the pass at the end; if the list is
+                // full, settled here from the accurate residual (then G takes its sign)
                 if (__any_sync(0xffffffffu, ties != 0) && valid) {
                     while (ties) {
                         const int b = __ffsll((long long)ties) - 1;
                         ties &= ties - 1;
                         const int fo = kSD * (b >> 4) + 16 * h + (b & 15);   // feature within the chunk
                         const int d = c * kDC + fo;
-                        const float tv = __ldg(a.target + ((size_t)lev * P + p) * D + d);
-                        double acc = 0.0;
-#pragma unroll 8
-                        for (int l = 0; l < kL; ++l)
-                            acc = fma((double)__ldg(Wl + p * kL + l), (double)__ldg(Sl + (size_t)l * D + d), acc);
-                        const double r = acc - (double)tv;
-                        lacc += fabs(r);
-                        *reinterpret_cast<uint16_t*>(smem + kG + (fo >> 6) * kGAtom + tc::sw128(row, fo & 63)) =
-                            (uint16_t)(r > 0.0 ? 0x3F80u : (r < 0.0 ? 0xBF80u : 0u));
+                        uint16_t* gp = reinterpret_cast<uint16_t*>(smem + kG + (fo >> 6) * kGAtom + tc::sw128(row, fo & 63));
+                        const unsigned slot = atomicAdd(fix_count, 1u);
+                        if (slot < (unsigned)kFixCap) {
+                            const uint64_t sg = *gp == 0x3F80u ? 1u : (*gp == 0xBF80u ? 2u : 0u);
+                            fix[slot] = (uint64_t)(uint32_t)p | ((uint64_t)d << 32) | (sg << 48);
+                        } else {
+                            const float r = exact_residual(Wl + p * kL, Sl, D, d, __ldg(a.target + ((size_t)lev * P + p) * D + d));
+                            lacc += (double)fabsf(r);
+                            *gp = (uint16_t)sign_bf16(r);
+                        }
                     }
                 }
                 tc::fence_proxy_async();
@@ -460,16 +488,41 @@ __global__ void __launch_bounds__(kThreads, 1)
                 break;
             }
             tc::fence_after();
-            uint32_t dw[32];
-            tc::tmem_ld32(tq + kColDW + (uint32_t)(32 * h), dw);
-            tc::tmem_wait_ld_regs(dw);
+            uint32_t dwh[32], dwl[32];   // G S_hi^T and G S_lo^T, codebook rows 32 h .. 32 h + 31
+            tc::tmem_ld32(tq + kColDW + (uint32_t)(32 * h), dwh);
+            tc::tmem_ld32(tq + kColDW + (uint32_t)(kL + 32 * h), dwl);
+            tc::tmem_wait_ld_regs(dwh);
+            tc::tmem_wait_ld_regs(dwl);
             tc::fence_before();
             if (valid) {
                 float4* out = reinterpret_cast<float4*>(a.dW + ((size_t)lev * P + p) * kL + 32 * h);
+                auto v4 = [&](int j) { return (__uint_as_float(dwh[j]) + __uint_as_float(dwl[j])) * a.inv_n; };
 #pragma unroll
-                for (int v = 0; v < 8; ++v)
-                    out[v] = make_float4(__uint_as_float(dw[4 * v]) * a.inv_n, __uint_as_float(dw[4 * v + 1]) * a.inv_n,
-                                         __uint_as_float(dw[4 * v + 2]) * a.inv_n, __uint_as_float(dw[4 * v + 3]) * a.inv_n);
+                for (int v = 0; v < 8; ++v) out[v] = make_float4(v4(4 * v), v4(4 * v + 1), v4(4 * v + 2), v4(4 * v + 3));
+            }
+        }
+        // the listed near ties, after every epilogue warp has stored its dW rows (named barrier of
+        // the 8 epilogue warps): the accurate residual's sign; where it differs from the
+        // provisional one, dW and dS get (sign - provisional) / n times S and W
+        asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory");
+        const unsigned nfix = min(*reinterpret_cast<volatile unsigned*>(fix_count), (unsigned)kFixCap);
+        if (ok && !*abort) {
+            for (unsigned fi = (unsigned)et; fi < nfix; fi += 32u * kEpiWarps) {
+                const uint64_t ent = fix[fi];
+                const int64_t pp = (int64_t)(uint32_t)ent;
+                const int d = (int)((ent >> 32) & 0xFFFFu);
+                const int sg = (int)(ent >> 48);
+                const float* wrow = Wl + pp * kL;
+                const float r = exact_residual(wrow, Sl, D, d, __ldg(a.target + ((size_t)lev * P + pp) * D + d));
+                lacc += (double)fabsf(r);
+                const int ge = r > 0.0f ? 1 : (r < 0.0f ? -1 : 0), gp = sg == 1 ? 1 : (sg == 2 ? -1 : 0);
+                if (ge != gp) {
+                    const float delta = (float)(ge - gp) * a.inv_n;
+                    for (int l = 0; l < kL; ++l) {
+                        atomicAdd(a.dW + ((size_t)lev * P + pp) * kL + l, delta * __ldg(Sl + (size_t)l * D + d));
+                        atomicAdd(a.dS + ((size_t)lev * kL + l) * D + d, delta * __ldg(wrow + l));
+                    }
+                }
             }
         }
         if (ok && my_tiles > 0) {

@@ -33,6 +33,20 @@ constexpr uint64_t kDefaultWaitNs = 1000000000ull;
 // the limit above: work that was issued completes on its own.
 constexpr uint64_t kDrainNs = 100000000ull;
 
+// Dot2 step (Ogita, Rump and Oishi, "Accurate sum and dot product", 2005): add a * b to the
+// unevaluated sum hi + lo with an error-free product (FMA remainder) and an error-free sum
+// (TwoSum), so that the result is as accurate as one accumulated in twice the precision.
+__device__ __forceinline__ void dot2_step(float a, float b, float& hi, float& lo)
+{
+    const float p = __fmul_rn(a, b);
+    const float pe = __fmaf_rn(a, b, -p);
+    const float s = __fadd_rn(hi, p);
+    const float bp = __fsub_rn(s, hi);
+    const float se = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(se, pe));
+}
+
 // First nonzero status wins; never traps.
 __device__ __forceinline__ void report(int32_t* status, int32_t code)
 {

@@ -17,20 +17,6 @@ namespace {
 
 constexpr int kL = 64;
 
-// Dot2 step (Ogita, Rump and Oishi, "Accurate sum and dot product", 2005): add a * b to the
-// unevaluated sum hi + lo with an error-free product (FMA remainder) and an error-free sum
-// (TwoSum), so that the result is as accurate as one accumulated in twice the precision.
-__device__ __forceinline__ void dot2_step(float a, float b, float& hi, float& lo)
-{
-    const float p = __fmul_rn(a, b);
-    const float pe = __fmaf_rn(a, b, -p);
-    const float s = __fadd_rn(hi, p);
-    const float bp = __fsub_rn(s, hi);
-    const float se = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(p, bp));
-    hi = s;
-    lo = __fadd_rn(lo, __fadd_rn(se, pe));
-}
-
 // grid (64 + nt, levels), 256 threads: B^T[lev][j][k] = <x_j, S_k> with x_j = S_j (j < 64, Gram
 // rows) or the text vector j - 64.  Thread (k = t % 64, part = t / 64) accumulates the terms
 // d = 4 part + 16 i (+ 0..3) in Dot2 form; the four parts are added in FP64 and rounded to float.
