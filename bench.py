@@ -708,8 +708,9 @@ def main():
     dev = torch.device("cuda", local)
     if args.profile == "backward":
         r = backward_section(dev, reps=args.steps)
-        print(json.dumps({"profile": "backward", "l1_decode_backward_ms": r["l1_decode_backward_ms"],
-                          "step_ms": r["step_ms"]}), flush=True)
+        print(json.dumps({"profile": "backward", "forward_ms": r["forward_ms"],
+                          "l1_decode_backward_ms": r["l1_decode_backward_ms"],
+                          "splat_backward_ms": r["splat_backward_ms"], "step_ms": r["step_ms"]}), flush=True)
         return
     if args.profile == "sparsify":
         r = sparsify_section(dev, reps=args.steps)

@@ -3,16 +3,14 @@
 // The paper trains the coefficient field (Sec. 3.3, Sec. 4.1) but gives no gradient; this
 // is the adjoint of the forward path implemented here.
 //
-// 1. l1_decode_backward: Loss = mean |F - target|, F = W S (Eq. 7).  G = sign(F - target)/N,
-//    dW = G S^T, dS = W^T G.  Persistent CTAs walk 64-pixel tiles; F is recomputed per
-//    128-feature chunk (never stored), dW accumulates in registers across chunks, and each
-//    CTA keeps its dS partial in shared memory and adds it to HBM once at the end.
+// 1. The decode adjoint (Loss = mean |F - target|, F = W S, Eq. 7) is in backward_tc.cu.
 // 2. splat_backward: per pixel, back to front from its last contributor.  The transmittance
 //    is recomputed from final_T as T_i = T_{i+1} / (1 - alpha_i).  Because each Gaussian has
 //    only K nonzeros per level, the running sum of later contributions is one scalar:
 //        g_i = sum_pairs dW[col] w,   dalpha_i = T_i (g_i - B),   B <- alpha_i g_i + (1 - alpha_i) B.
-//    Per-Gaussian sums over the 32 pixels of a warp use a butterfly reduce-scatter (31
-//    shuffles for up to 32 quantities), then one atomic per quantity.
+//    Per-Gaussian sums over the 32 pixels of a warp use a butterfly reduce-scatter (16 shuffles
+//    for up to 16 quantities, 31 for up to 32), then one atomic per quantity.  The list entries
+//    and records of the next batch are loaded while the current batch is evaluated.
 // 3. project_backward: one thread per Gaussian, chain rule from (u, v, conic) to (mean,
 //    scale, quaternion) through Sigma' = N N^T + 0.3 I, N = J W R diag(s).
 #include "device.cuh"
@@ -23,215 +21,18 @@
 namespace lsv2 {
 namespace {
 
-// ------------------------------------------------------------------------------------ 1
-constexpr int kBP = 64;    // pixels per tile
-constexpr int kBC = 128;   // feature chunk
-constexpr int kSC = kBC + 4;   // S chunk row stride (floats): rows 16 B aligned, 4 banks apart
-constexpr int kL = 64;
-
-__global__ void __launch_bounds__(256) l1_decode_backward_kernel(int64_t P, int D, float inv_n,
-                                                                 const float* __restrict__ W,
-                                                                 const float* __restrict__ S,
-                                                                 const float* __restrict__ target,
-                                                                 float* __restrict__ loss,
-                                                                 float* __restrict__ dW,
-                                                                 float* __restrict__ dS)
-{
-    extern __shared__ __align__(16) float sm[];
-    float* dSacc = sm;                          // [64][D]
-    float* Wt = dSacc + kL * D;                 // [64 l][kBP + 4]
-    float* Sc = Wt + kL * (kBP + 4);            // [64 l][kSC]
-    float* Gs = Sc + kL * kSC;                  // [kBP][kBC + 4]
-    __shared__ float red[8];
-    const int lev = blockIdx.y;
-    const int tid = threadIdx.x;
-    const float* Wl = W + (size_t)lev * P * kL;
-    const float* Sl = S + (size_t)lev * kL * D;
-    const float* Tl = target + (size_t)lev * P * D;
-    float* dWl = dW + (size_t)lev * P * kL;
-    for (int i = tid; i < kL * D; i += 256) dSacc[i] = 0.0f;
-    float lsum = 0.0f;
-    const int64_t ntiles = (P + kBP - 1) / kBP;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int64_t p0 = tile * kBP;
-        __syncthreads();
-        // W tile, transposed: Wt[l][px]
-        for (int i = tid; i < kBP * kL / 4; i += 256) {
-            const int px = i >> 4, c4 = (i & 15) * 4;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (p0 + px < P) v = __ldg(reinterpret_cast<const float4*>(Wl + (p0 + px) * kL + c4));
-            Wt[(c4 + 0) * (kBP + 4) + px] = v.x;
-            Wt[(c4 + 1) * (kBP + 4) + px] = v.y;
-            Wt[(c4 + 2) * (kBP + 4) + px] = v.z;
-            Wt[(c4 + 3) * (kBP + 4) + px] = v.w;
-        }
-        float dwacc[4][4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) dwacc[i][j] = 0.0f;
-        for (int c0 = 0; c0 < D; c0 += kBC) {
-            __syncthreads();
-            for (int i = tid; i < kL * kBC / 4; i += 256) {
-                const int l = i >> 5, c4 = (i & 31) * 4;
-                *reinterpret_cast<float4*>(Sc + l * kSC + c4) =
-                    __ldg(reinterpret_cast<const float4*>(Sl + (size_t)l * D + c0 + c4));
-            }
-            __syncthreads();
-            // F block: thread (ty: 4 pixels, tx: features 4 tx .. 4 tx + 3 and 64 + 4 tx .. 64 + 4 tx + 3,
-            // so the 16 threads of a row read 256 contiguous bytes per 16-byte load: no bank conflict)
-            {
-                const int tx = tid & 15, ty = tid >> 4;
-                // the target block is loaded first, so its HBM latency overlaps the products
-                float4 tgt[4][2];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int px = ty * 4 + i;
-                    if (p0 + px < P) {
-                        const float* tp = Tl + (p0 + px) * D + c0 + tx * 4;
-                        tgt[i][0] = __ldcs(reinterpret_cast<const float4*>(tp));
-                        tgt[i][1] = __ldcs(reinterpret_cast<const float4*>(tp + 64));
-                    } else {
-                        tgt[i][0] = tgt[i][1] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    }
-                }
-                float f[4][8];
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) f[i][j] = 0.0f;
-#pragma unroll 8
-                for (int l = 0; l < kL; ++l) {
-                    const float4 a = *reinterpret_cast<const float4*>(Wt + l * (kBP + 4) + ty * 4);
-                    const float4 b0 = *reinterpret_cast<const float4*>(Sc + l * kSC + tx * 4);
-                    const float4 b1 = *reinterpret_cast<const float4*>(Sc + l * kSC + 64 + tx * 4);
-                    const float av[4] = {a.x, a.y, a.z, a.w};
-                    const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-                    for (int i = 0; i < 4; ++i)
-#pragma unroll
-                        for (int j = 0; j < 8; ++j) f[i][j] = fmaf(av[i], bv[j], f[i][j]);
-                }
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int px = ty * 4 + i;
-                    float g[8];
-                    if (p0 + px < P) {
-                        const float4 t0 = tgt[i][0], t1 = tgt[i][1];
-                        const float tv[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
-#pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            const float r = f[i][j] - tv[j];
-                            lsum += fabsf(r);
-                            g[j] = r > 0.0f ? inv_n : (r < 0.0f ? -inv_n : 0.0f);
-                        }
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < 8; ++j) g[j] = 0.0f;
-                    }
-                    *reinterpret_cast<float4*>(Gs + px * (kBC + 4) + tx * 4) = make_float4(g[0], g[1], g[2], g[3]);
-                    *reinterpret_cast<float4*>(Gs + px * (kBC + 4) + 64 + tx * 4) = make_float4(g[4], g[5], g[6], g[7]);
-                }
-            }
-            __syncthreads();
-            // dS chunk: dSacc[l][c0 + c] += sum_px Wt[l][px] Gs[px][c]   (thread: 4 l x 8 c, the
-            // features interleaved as in the F block)
-            {
-                const int tc = tid & 15, tl = tid >> 4;
-                float s[4][8];
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) s[i][j] = 0.0f;
-                // four pixels per step: each W row read with one 16-byte load (pixel order kept)
-#pragma unroll 8
-                for (int p4 = 0; p4 < kBP; p4 += 4) {
-                    float4 wq[4];
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) wq[i] = *reinterpret_cast<const float4*>(Wt + (tl * 4 + i) * (kBP + 4) + p4);
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int px = p4 + q;
-                        const float4 g0 = *reinterpret_cast<const float4*>(Gs + px * (kBC + 4) + tc * 4);
-                        const float4 g1 = *reinterpret_cast<const float4*>(Gs + px * (kBC + 4) + 64 + tc * 4);
-                        const float gv[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            const float wv = q == 0 ? wq[i].x : q == 1 ? wq[i].y : q == 2 ? wq[i].z : wq[i].w;
-#pragma unroll
-                            for (int j = 0; j < 8; ++j) s[i][j] = fmaf(wv, gv[j], s[i][j]);
-                        }
-                    }
-                }
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    float4* r0 = reinterpret_cast<float4*>(dSacc + (tl * 4 + i) * D + c0 + tc * 4);
-                    float4* r1 = reinterpret_cast<float4*>(dSacc + (tl * 4 + i) * D + c0 + 64 + tc * 4);
-                    float4 v0 = *r0, v1 = *r1;
-                    v0.x += s[i][0], v0.y += s[i][1], v0.z += s[i][2], v0.w += s[i][3];
-                    v1.x += s[i][4], v1.y += s[i][5], v1.z += s[i][6], v1.w += s[i][7];
-                    *r0 = v0;
-                    *r1 = v1;
-                }
-            }
-            // dW: dwacc[px][l] += sum_c Gs[px][c] Sc[l][c]   (thread: 4 px x the 4 l = tl + 16 j, so
-            // the 16 threads of a row read 16 consecutive S rows, 4 banks apart)
-            {
-                const int tl = tid & 15, tp = tid >> 4;
-                // four features per step with 16-byte loads (the products still added in feature order)
-#pragma unroll 8
-                for (int c = 0; c < kBC; c += 4) {
-                    float4 gv[4], sv[4];
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) gv[i] = *reinterpret_cast<const float4*>(Gs + (tp * 4 + i) * (kBC + 4) + c);
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) sv[j] = *reinterpret_cast<const float4*>(Sc + (tl + 16 * j) * kSC + c);
-#pragma unroll
-                    for (int i = 0; i < 4; ++i)
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            dwacc[i][j] = fmaf(gv[i].x, sv[j].x, dwacc[i][j]);
-                            dwacc[i][j] = fmaf(gv[i].y, sv[j].y, dwacc[i][j]);
-                            dwacc[i][j] = fmaf(gv[i].z, sv[j].z, dwacc[i][j]);
-                            dwacc[i][j] = fmaf(gv[i].w, sv[j].w, dwacc[i][j]);
-                        }
-                }
-            }
-        }
-        {
-            const int tl = tid & 15, tp = tid >> 4;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int64_t p = p0 + tp * 4 + i;
-                if (p < P) {
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) dWl[p * kL + tl + 16 * j] = dwacc[i][j];
-                }
-            }
-        }
-    }
-    __syncthreads();
-    float* dSl = dS + (size_t)lev * kL * D;
-    for (int i = tid; i < kL * D; i += 256) atomicAdd(dSl + i, dSacc[i]);
-    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
-    if ((tid & 31) == 0) red[tid >> 5] = lsum;
-    __syncthreads();
-    if (tid == 0) {
-        float t = 0.0f;
-        for (int i = 0; i < 8; ++i) t += red[i];
-        atomicAdd(loss, t * inv_n);
-    }
-}
-
 // ------------------------------------------------------------------------------------ 2
 // Backward splat record (global, per Gaussian): g0 = (u_hi, v_hi, u_lo, v_lo), the principal
 // frame and opacity exactly as in the forward record (so alpha is recomputed bit for bit), the
-// conic (a, b, c, 0) for the gradient formulas, then P weights and P column bytes (no merging).
+// conic (a, b, c) and the culling half-width ex.x, then P weights and P column bytes (no merging),
+// and the culling half-height ex.y in the record's last float.
 __host__ __device__ constexpr int bwd_record_floats(int P) { return (64 + 5 * P + 15) / 16 * 4; }
+// floats in use before the last one: header 16, P weights, P column bytes
+__host__ __device__ constexpr bool bwd_record_last_free(int P) { return 16 + P + (P + 3) / 4 < bwd_record_floats(P); }
 
 __global__ void __launch_bounds__(256) pack_bwd_kernel(int64_t n, int levels, int K, const float* xy,
-                                                       const float* axes, const float* conic_o, const uint8_t* idx,
-                                                       const float* w, float* recs)
+                                                       const float* axes, const float* conic_o, const float* extent,
+                                                       const uint8_t* idx, const float* w, float* recs)
 {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n) return;
@@ -242,7 +43,9 @@ __global__ void __launch_bounds__(256) pack_bwd_kernel(int64_t n, int levels, in
     reinterpret_cast<float4*>(rec)[0] = reinterpret_cast<const float4*>(xy)[g];
     reinterpret_cast<float4*>(rec)[1] = reinterpret_cast<const float4*>(axes)[2 * g];
     reinterpret_cast<float4*>(rec)[2] = make_float4(ax1.x, ax1.y, ax1.z, cn.w);
-    reinterpret_cast<float4*>(rec)[3] = make_float4(cn.x, cn.y, cn.z, 0.0f);
+    const float2 ex = reinterpret_cast<const float2*>(extent)[g];
+    reinterpret_cast<float4*>(rec)[3] = make_float4(cn.x, cn.y, cn.z, ex.x);
+    rec[bwd_record_floats(P) - 1] = ex.y;
     uint8_t* cb = reinterpret_cast<uint8_t*>(rec + 16 + P);
     for (int p = 0; p < P; ++p) {
         const int lev = p / K;
@@ -252,6 +55,23 @@ __global__ void __launch_bounds__(256) pack_bwd_kernel(int64_t n, int levels, in
         rec[16 + p] = ok ? w[src] : 0.0f;
         cb[p] = (uint8_t)(lev * 64 + (ok ? ix : 0));
     }
+}
+
+// lane L ends with the warp-wide sum of v[L >> 1] (lanes 2 q and 2 q + 1 hold the sum of v[q]):
+// four halving butterfly levels on lane bits 4..1 (8 + 4 + 2 + 1 shuffles), then one full step
+__device__ __forceinline__ float reduce_scatter16(float (&v)[16], int lane)
+{
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) {
+        const bool upper = (lane & (o << 1)) != 0;
+#pragma unroll
+        for (int i = 0; i < o; ++i) {
+            const float send = upper ? v[i] : v[i + o];
+            const float keep = upper ? v[i + o] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o << 1);
+        }
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
 // lane L ends with the warp-wide sum of v[L]
@@ -284,6 +104,9 @@ struct BwdCfg {
     __host__ __device__ static constexpr int lane_x(int warp, int lane) { return (warp % kWarpsX) * kWarpW + lane % kWarpW; }
     __host__ __device__ static constexpr int lane_y(int warp, int lane) { return (warp / kWarpsX) * kWarpH + lane / kWarpW; }
     static_assert(kPairs + 6 <= 32, "quantities per Gaussian");
+    static constexpr int kQ = kPairs + 6;              // gradient quantities per Gaussian and pixel
+    static constexpr int kV = kQ <= 16 ? 16 : 32;      // reduce-scatter width
+    static_assert(bwd_record_last_free(kPairs), "the record's last float holds the culling half-height");
     static_assert(TW % 8 == 0 && TH % 4 == 0 && (TW * TH) % 32 == 0, "warps cover 8 x 4 blocks of a tile");
 };
 
@@ -329,26 +152,47 @@ __global__ void __launch_bounds__(TW* TH) splat_backward_kernel(SplatBwdArgs a)
     for (int o = 16; o > 0; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
     const float pxf = (float)px, pyf = (float)py;
 
-    for (int top = (int)wmax; top > 0; top -= 32) {
-        const int lo = max(0, top - 32);
-        // stage positions [lo, top) of the tile list, lane i <-> position lo + i; the 2D mean
-        // and the Gaussian id stay in the staging lane's registers
-        bool keep = false;
-        const int pos = lo + lane;
-        uint32_t my_g = 0u;
-        float4 my_xy = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (pos < top) {
-            my_g = a.gauss_ids[beg + pos];
-            my_xy = __ldg(reinterpret_cast<const float4*>(a.xy) + my_g);
-            const float2 ex = __ldg(reinterpret_cast<const float2*>(a.extent) + my_g);
-            keep = ex.x >= 0.0f && my_xy.x + ex.x >= wx0 && my_xy.x - ex.x <= wx1 && my_xy.y + ex.y >= wy0 &&
-                   my_xy.y - ex.y <= wy1;
-            if (keep) {
-                const float4* src = reinterpret_cast<const float4*>(a.recs + (size_t)my_g * C::kRecFloats) + 1;
-                float4* dst = reinterpret_cast<float4*>(stage + lane * C::kSmemRecFloats);
+    // The list back to front in batches of 32 positions [top - 32, top): lane i <-> position
+    // top - 32 + i (negative positions are empty).  Each lane's record (2D mean, culling extent
+    // and the rest) is loaded one batch ahead and its list entry two batches ahead, so the loads
+    // are in flight while the current batch is evaluated; kept records are staged in shared
+    // memory, the 2D mean and the id stay in the staging lane's registers.
+    constexpr int kR = C::kRecFloats / 4;
+    constexpr uint32_t kNone = 0xFFFFFFFFu;
+    // (every load is inside its condition: no address outside the list or the records is formed)
+    auto load_id = [&](int t) -> uint32_t {
+        const int pos = t - 32 + lane;
+        uint32_t id = kNone;
+        if (t > 0 && pos >= 0) id = __ldg(a.gauss_ids + beg + pos);
+        return id;
+    };
+    auto load_rec = [&](uint32_t id, float4 (&r)[kR]) {
+        if (id != kNone) {
+            const float4* src = reinterpret_cast<const float4*>(a.recs + (size_t)id * C::kRecFloats);
 #pragma unroll
-                for (int v = 0; v < C::kSmemRecFloats / 4; ++v) dst[v] = __ldg(src + v);
-            }
+            for (int v = 0; v < kR; ++v) r[v] = __ldg(src + v);
+        } else {
+#pragma unroll
+            for (int v = 0; v < kR; ++v) r[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    };
+    int top = (int)wmax;
+    uint32_t my_g = load_id(top), id_nxt = load_id(top - 32);
+    float4 rc[kR];
+    load_rec(my_g, rc);
+    for (; top > 0; top -= 32) {
+        float4 rn[kR];
+        load_rec(id_nxt, rn);
+        const uint32_t id_nn = load_id(top - 64);
+        const int lo = top - 32;
+        const float4 my_xy = rc[0];
+        const float exx = rc[3].w, exy = rc[kR - 1].w;
+        const bool keep = my_g != kNone && exx >= 0.0f && my_xy.x + exx >= wx0 && my_xy.x - exx <= wx1 &&
+                          my_xy.y + exy >= wy0 && my_xy.y - exy <= wy1;
+        if (keep) {
+            float4* dst = reinterpret_cast<float4*>(stage + lane * C::kSmemRecFloats);
+#pragma unroll
+            for (int v = 1; v < kR; ++v) dst[v - 1] = rc[v];
         }
         uint32_t mask = __ballot_sync(0xffffffffu, keep);
         __syncwarp();
@@ -370,9 +214,9 @@ __global__ void __launch_bounds__(TW* TH) splat_backward_kernel(SplatBwdArgs a)
             const float dx = __fadd_rn(__fsub_rn(g0.x, pxf), g0.z);
             const float dy = __fadd_rn(__fsub_rn(g0.y, pyf), g0.w);
             const float p2 = eval_power2(g0, ax, axl, pxf, pyf);
-            float vals[32];
+            float vals[C::kV];
 #pragma unroll
-            for (int k = 0; k < 32; ++k) vals[k] = 0.0f;
+            for (int k = 0; k < C::kV; ++k) vals[k] = 0.0f;
             bool contrib = false;
             if (lo + i < (int)my_last && p2 <= 0.0f) {
                 float ex2;
@@ -407,17 +251,28 @@ __global__ void __launch_bounds__(TW* TH) splat_backward_kernel(SplatBwdArgs a)
                 }
             }
             if (__any_sync(0xffffffffu, contrib)) {
-                const float tot = reduce_scatter32(vals, lane);
-                if (lane < C::kPairs) {
-                    atomicAdd(a.dw + (size_t)g * C::kPairs + lane, tot);
-                } else if (lane < C::kPairs + 5) {
-                    atomicAdd(a.grad2d + (size_t)g * 8 + (lane - C::kPairs), tot);
-                } else if (lane == C::kPairs + 5) {
+                float tot;
+                int q = lane;   // the quantity this lane adds
+                if constexpr (C::kV == 16) {
+                    tot = reduce_scatter16(vals, lane);
+                    q = (lane & 1) ? C::kQ : lane >> 1;   // one lane of each pair adds
+                } else {
+                    tot = reduce_scatter32(vals, lane);
+                }
+                if (q < C::kPairs) {
+                    atomicAdd(a.dw + (size_t)g * C::kPairs + q, tot);
+                } else if (q < C::kPairs + 5) {
+                    atomicAdd(a.grad2d + (size_t)g * 8 + (q - C::kPairs), tot);
+                } else if (q == C::kPairs + 5) {
                     atomicAdd(a.dopacity + g, tot);
                 }
             }
         }
         __syncwarp();
+#pragma unroll
+        for (int v = 0; v < kR; ++v) rc[v] = rn[v];
+        my_g = id_nxt;
+        id_nxt = id_nn;
     }
 }
 
@@ -555,21 +410,6 @@ size_t splat_backward_workspace_bytes(int64_t n, int levels, int K)
     return g2 + recs;
 }
 
-cudaError_t launch_l1_decode_backward(int levels, int64_t P, int D, const float* W, const float* S,
-                                      const float* target, float* loss, float* dW, float* dS, int num_sms,
-                                      cudaStream_t stream)
-{
-    if (P == 0) return cudaSuccess;
-    const size_t smem = (size_t)(kL * D + kL * (kBP + 4) + kL * kSC + kBP * (kBC + 4)) * 4;
-    cudaError_t e = cudaFuncSetAttribute(l1_decode_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    const int64_t ntiles = (P + kBP - 1) / kBP;
-    const int ctas = (int)std::min<int64_t>(ntiles, (int64_t)num_sms);
-    const float inv_n = (float)(1.0 / ((double)levels * (double)P * (double)D));
-    l1_decode_backward_kernel<<<dim3(ctas, levels), 256, smem, stream>>>(P, D, inv_n, W, S, target, loss, dW, dS);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_splat_backward(int levels, int K, const SplatBwdArgs& args, const ProjBwdArgs& pargs,
                                   const uint8_t* idx, const float* w, cudaStream_t stream)
 {
@@ -581,7 +421,7 @@ cudaError_t launch_splat_backward(int levels, int K, const SplatBwdArgs& args, c
     if (e != cudaSuccess) return e;
     if (pargs.n > 0)
         pack_bwd_kernel<<<(unsigned)((pargs.n + 255) / 256), 256, 0, stream>>>(pargs.n, levels, K, a.xy, a.axes,
-                                                                              a.conic_o, idx, w, a.recs);
+                                                                              a.conic_o, a.extent, idx, w, a.recs);
     if (levels == 1 && K == 4) e = launch_bwd_tile<1, 4>(a, stream);
     else if (levels == 1 && K == 2) e = launch_bwd_tile<1, 2>(a, stream);
     else if (levels == 1 && K == 8) e = launch_bwd_tile<1, 8>(a, stream);

@@ -38,10 +38,8 @@ struct ProjBwdArgs {
 
 size_t splat_backward_workspace_bytes(int64_t n, int levels, int K);
 bool splat_backward_supported(int levels, int K);
-cudaError_t launch_l1_decode_backward(int levels, int64_t P, int D, const float* W, const float* S,
-                                      const float* target, float* loss, float* dW, float* dS, int num_sms,
-                                      cudaStream_t stream);
-// The same adjoint on the tensor cores (backward_tc.cu): D a multiple of 128, at most 512.
+// The decode adjoint of the L1 loss on the tensor cores (backward_tc.cu): D a multiple of 128, at
+// most 512.
 bool l1_decode_backward_tc_supported(int D);
 cudaError_t launch_l1_decode_backward_tc(int levels, int64_t P, int D, const float* W, const float* S,
                                          const float* target, float* loss, float* dW, float* dS, int num_sms,
