@@ -8,9 +8,11 @@
 //    is recomputed from final_T as T_i = T_{i+1} / (1 - alpha_i).  Because each Gaussian has
 //    only K nonzeros per level, the running sum of later contributions is one scalar:
 //        g_i = sum_pairs dW[col] w,   dalpha_i = T_i (g_i - B),   B <- alpha_i g_i + (1 - alpha_i) B.
-//    Per-Gaussian sums over the 32 pixels of a warp use a butterfly reduce-scatter (16 shuffles
-//    for up to 16 quantities, 31 for up to 32), then one atomic per quantity.  The list entries
-//    and records of the next batch are loaded while the current batch is evaluated.
+//    Gaussians are taken two at a time where their quantities fit 32 lanes (independent
+//    evaluations; the transmittance and running sum pass from one to the next); the per-Gaussian
+//    sums over the 32 pixels of a warp use one butterfly reduce-scatter (31 shuffles for up to 32
+//    quantities), then one atomic per quantity.  The list entries and records of the next batch
+//    are loaded while the current batch is evaluated.
 // 3. project_backward: one thread per Gaussian, chain rule from (u, v, conic) to (mean,
 //    scale, quaternion) through Sigma' = N N^T + 0.3 I, N = J W R diag(s).
 #include "device.cuh"
@@ -57,23 +59,6 @@ __global__ void __launch_bounds__(256) pack_bwd_kernel(int64_t n, int levels, in
     }
 }
 
-// lane L ends with the warp-wide sum of v[L >> 1] (lanes 2 q and 2 q + 1 hold the sum of v[q]):
-// four halving butterfly levels on lane bits 4..1 (8 + 4 + 2 + 1 shuffles), then one full step
-__device__ __forceinline__ float reduce_scatter16(float (&v)[16], int lane)
-{
-#pragma unroll
-    for (int o = 8; o > 0; o >>= 1) {
-        const bool upper = (lane & (o << 1)) != 0;
-#pragma unroll
-        for (int i = 0; i < o; ++i) {
-            const float send = upper ? v[i] : v[i + o];
-            const float keep = upper ? v[i + o] : v[i];
-            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o << 1);
-        }
-    }
-    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
-}
-
 // lane L ends with the warp-wide sum of v[L]
 __device__ __forceinline__ float reduce_scatter32(float (&v)[32], int lane)
 {
@@ -105,7 +90,7 @@ struct BwdCfg {
     __host__ __device__ static constexpr int lane_y(int warp, int lane) { return (warp / kWarpsX) * kWarpH + lane / kWarpW; }
     static_assert(kPairs + 6 <= 32, "quantities per Gaussian");
     static constexpr int kQ = kPairs + 6;              // gradient quantities per Gaussian and pixel
-    static constexpr int kV = kQ <= 16 ? 16 : 32;      // reduce-scatter width
+    static constexpr int kPer = 2 * kQ <= 32 ? 2 : 1;  // Gaussians evaluated per step (one reduce-scatter)
     static_assert(bwd_record_last_free(kPairs), "the record's last float holds the culling half-height");
     static_assert(TW % 8 == 0 && TH % 4 == 0 && (TW * TH) % 32 == 0, "warps cover 8 x 4 blocks of a tile");
 };
@@ -196,75 +181,95 @@ __global__ void __launch_bounds__(TW* TH) splat_backward_kernel(SplatBwdArgs a)
         }
         uint32_t mask = __ballot_sync(0xffffffffu, keep);
         __syncwarp();
+        // kPer Gaussians per step (two when 2 kQ <= 32), back to front: the first is the one further
+        // back in the list.  Their evaluations are independent; the transmittance and the running
+        // sum pass from one to the next; one reduce-scatter of all their quantities serves both.
+        constexpr int kPer = C::kPer;
         while (mask) {
-            const int i = 31 - __clz(mask);
-            mask &= ~(1u << i);
-            const uint32_t g = __shfl_sync(0xffffffffu, my_g, i);
-            float4 g0;
-            g0.x = __shfl_sync(0xffffffffu, my_xy.x, i);
-            g0.y = __shfl_sync(0xffffffffu, my_xy.y, i);
-            g0.z = __shfl_sync(0xffffffffu, my_xy.z, i);
-            g0.w = __shfl_sync(0xffffffffu, my_xy.w, i);
-            const float* r = stage + i * C::kSmemRecFloats;
-            const float4 ax = *reinterpret_cast<const float4*>(r);
-            const float4 axl = *reinterpret_cast<const float4*>(r + 4);
-            const float4 g2 = *reinterpret_cast<const float4*>(r + 8);
-            const float* wr = r + 12;
-            const uint8_t* cr = reinterpret_cast<const uint8_t*>(r + 12 + C::kPairs);
-            const float dx = __fadd_rn(__fsub_rn(g0.x, pxf), g0.z);
-            const float dy = __fadd_rn(__fsub_rn(g0.y, pyf), g0.w);
-            const float p2 = eval_power2(g0, ax, axl, pxf, pyf);
-            float vals[C::kV];
+            int idx[kPer];
 #pragma unroll
-            for (int k = 0; k < C::kV; ++k) vals[k] = 0.0f;
+            for (int u = 0; u < kPer; ++u) {
+                idx[u] = mask ? 31 - __clz(mask) : -1;   // (warp-uniform)
+                if (mask) mask &= ~(1u << idx[u]);
+            }
+            uint32_t gid[kPer];
+            float p2[kPer], dx[kPer], dy[kPer];
+            float4 axl[kPer], g2[kPer];
+            const float* rr[kPer];
+#pragma unroll
+            for (int u = 0; u < kPer; ++u) {
+                const int i = idx[u] < 0 ? idx[0] : idx[u];   // an absent second Gaussian re-reads the first (unused)
+                gid[u] = __shfl_sync(0xffffffffu, my_g, i);
+                float4 g0;
+                g0.x = __shfl_sync(0xffffffffu, my_xy.x, i);
+                g0.y = __shfl_sync(0xffffffffu, my_xy.y, i);
+                g0.z = __shfl_sync(0xffffffffu, my_xy.z, i);
+                g0.w = __shfl_sync(0xffffffffu, my_xy.w, i);
+                rr[u] = stage + i * C::kSmemRecFloats;
+                const float4 ax = *reinterpret_cast<const float4*>(rr[u]);
+                axl[u] = *reinterpret_cast<const float4*>(rr[u] + 4);
+                g2[u] = *reinterpret_cast<const float4*>(rr[u] + 8);
+                dx[u] = __fadd_rn(__fsub_rn(g0.x, pxf), g0.z);
+                dy[u] = __fadd_rn(__fsub_rn(g0.y, pyf), g0.w);
+                p2[u] = eval_power2(g0, ax, axl[u], pxf, pyf);
+            }
+            float vals[32];
+#pragma unroll
+            for (int k = 0; k < 32; ++k) vals[k] = 0.0f;
             bool contrib = false;
-            if (lo + i < (int)my_last && p2 <= 0.0f) {
-                float ex2;
-                asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(ex2) : "f"(p2));
-                const float raw = axl.w * ex2;
-                const float alpha = fminf(kAlphaMax, raw);
-                if (alpha >= kAlphaMin) {
-                    contrib = true;
-                    const float oma = one_minus_alpha(alpha, axl.w, p2);
-                    const float Ti = T / oma;
-                    const float e = alpha * Ti;
-                    float gsum = 0.0f;
 #pragma unroll
-                    for (int p = 0; p < C::kPairs; ++p) {
-                        const float gw = gW[(int)cr[p] * 33 + lane];
-                        vals[p] = gw * e;
-                        gsum = fmaf(gw, wr[p], gsum);
-                    }
-                    const float dalpha = Ti * (gsum - Bsum);
-                    Bsum = fmaf(alpha, gsum, oma * Bsum);
-                    T = Ti;
-                    if (!(raw > kAlphaMax)) {
-                        const float dpow = dalpha * alpha;
-                        const float ca = g2.x, cb = g2.y, cc = g2.z;
-                        vals[C::kPairs + 0] = dpow * -(ca * dx + cb * dy);        // d/du
-                        vals[C::kPairs + 1] = dpow * -(cb * dx + cc * dy);        // d/dv
-                        vals[C::kPairs + 2] = dpow * (-0.5f * dx * dx);           // d/da
-                        vals[C::kPairs + 3] = dpow * (-dx * dy);                  // d/db
-                        vals[C::kPairs + 4] = dpow * (-0.5f * dy * dy);           // d/dc
-                        vals[C::kPairs + 5] = dalpha * ex2;                       // d/dopacity
+            for (int u = 0; u < kPer; ++u) {
+                if (idx[u] >= 0 && lo + idx[u] < (int)my_last && p2[u] <= 0.0f) {
+                    float ex2;
+                    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(ex2) : "f"(p2[u]));
+                    const float raw = axl[u].w * ex2;
+                    const float alpha = fminf(kAlphaMax, raw);
+                    if (alpha >= kAlphaMin) {
+                        contrib = true;
+                        float oma = 1.0f - alpha;   // exact to within alpha's own error up to alpha = 1/2
+                        if (alpha > 0.5f) oma = one_minus_alpha(alpha, axl[u].w, p2[u]);
+                        const float Ti = __fdividef(T, oma);   // within 2 ulp: far below the gradients' error bound
+                        const float e = alpha * Ti;
+                        const float* wr = rr[u] + 12;
+                        const uint8_t* cr = reinterpret_cast<const uint8_t*>(rr[u] + 12 + C::kPairs);
+                        float gsum = 0.0f;
+#pragma unroll
+                        for (int p = 0; p < C::kPairs; ++p) {
+                            const float gw = gW[(int)cr[p] * 33 + lane];
+                            vals[u * C::kQ + p] = gw * e;
+                            gsum = fmaf(gw, wr[p], gsum);
+                        }
+                        const float dalpha = Ti * (gsum - Bsum);
+                        Bsum = fmaf(alpha, gsum, oma * Bsum);
+                        T = Ti;
+                        if (!(raw > kAlphaMax)) {
+                            const float dpow = dalpha * alpha;
+                            const float ca = g2[u].x, cb = g2[u].y, cc = g2[u].z, x = dx[u], y = dy[u];
+                            float* v = vals + u * C::kQ + C::kPairs;
+                            v[0] = dpow * -(ca * x + cb * y);   // d/du
+                            v[1] = dpow * -(cb * x + cc * y);   // d/dv
+                            v[2] = dpow * (-0.5f * x * x);      // d/da
+                            v[3] = dpow * (-x * y);             // d/db
+                            v[4] = dpow * (-0.5f * y * y);      // d/dc
+                            v[5] = dalpha * ex2;                // d/dopacity
+                        }
                     }
                 }
             }
             if (__any_sync(0xffffffffu, contrib)) {
-                float tot;
-                int q = lane;   // the quantity this lane adds
-                if constexpr (C::kV == 16) {
-                    tot = reduce_scatter16(vals, lane);
-                    q = (lane & 1) ? C::kQ : lane >> 1;   // one lane of each pair adds
-                } else {
-                    tot = reduce_scatter32(vals, lane);
-                }
-                if (q < C::kPairs) {
-                    atomicAdd(a.dw + (size_t)g * C::kPairs + q, tot);
-                } else if (q < C::kPairs + 5) {
-                    atomicAdd(a.grad2d + (size_t)g * 8 + (q - C::kPairs), tot);
-                } else if (q == C::kPairs + 5) {
-                    atomicAdd(a.dopacity + g, tot);
+                // lane L holds quantity L % kQ of Gaussian L / kQ of the step
+                const float tot = reduce_scatter32(vals, lane);
+                const int u = lane / C::kQ, q = lane - u * C::kQ;
+                const bool here = u < kPer && (u == 0 || idx[kPer - 1] >= 0);
+                const uint32_t g = u == 0 ? gid[0] : gid[kPer - 1];
+                if (here) {
+                    if (q < C::kPairs) {
+                        atomicAdd(a.dw + (size_t)g * C::kPairs + q, tot);
+                    } else if (q < C::kPairs + 5) {
+                        atomicAdd(a.grad2d + (size_t)g * 8 + (q - C::kPairs), tot);
+                    } else {
+                        atomicAdd(a.dopacity + g, tot);
+                    }
                 }
             }
         }
