@@ -353,6 +353,133 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- measured unit rates
+def unit_rates(dev, target_ms: float = 20.0):
+    """Throughput of the units the splat's blend uses, measured on this device with the library's
+    rate probes (lsv2_rate_probe): FP32 FMA (per second; one FP32 pipe operation each), ex2 on the
+    MUFU unit, and 4-byte shared-memory accesses (a load + store stream without bank conflicts).
+    Each probe fills every SM (4 CTAs of 512 threads per SM) and is timed with CUDA events."""
+    import torch
+    from paper_2507_07136_b300 import _lib as Lb
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks = 4 * sms
+    sink = torch.zeros(blocks, device=dev)
+    st = torch.cuda.current_stream().cuda_stream
+    out = {}
+    for kind, name in ((0, "fp32_fma_per_s"), (1, "ex2_per_s"), (2, "smem_access_per_s")):
+        iters = 1000
+        for _ in range(8):   # grow the launch until it takes about target_ms
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            Lb.call("lsv2_rate_probe", kind, iters, blocks, sink.data_ptr(), st)
+            b.record()
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            if ms >= target_ms:
+                break
+            iters = int(iters * max(2.0, target_ms / max(ms, 1e-3)))
+        out[name] = Lb.lib().lsv2_rate_probe_ops(kind, iters, blocks) / (ms * 1e-3)
+    out["probe"] = f"{blocks} CTAs x 512 threads, 8 independent chains per thread, about {target_ms:.0f} ms per probe"
+    return out
+
+
+def splat_work(sc, cam, npix: int = 20000, seed: int = 0):
+    """The blend's algorithmic work on this frame (Algorithm 1, counted by the FP64 oracle on `npix`
+    random pixels and scaled to the frame): list entries evaluated (up to and including the one
+    that stops a pixel's walk) and contributions (entries that add their K pairs per level)."""
+    from oracle import oracle as O
+    pr = O.project(cam, sc.means, sc.scales, sc.quats)
+    ids, ranges = O.bin(cam, pr)
+    rng = np.random.default_rng(seed)
+    px = rng.integers(0, cam.width, npix).astype(np.int32)
+    py = rng.integers(0, cam.height, npix).astype(np.int32)
+    bl = O.blend(cam, pr, sc.opacity, ids, ranges, idx=sc.idx, w=sc.weights, px=px, py=py)
+    P = cam.num_pixels
+    return {"evaluations": float(bl.n_eval.mean()) * P, "contributions": float(bl.n_contrib.mean()) * P,
+            "sample_pixels": npix}
+
+
+def splat_alu_roofline(work, levels: int, K: int, splat_ms: float, rates):
+    """The splat against the units its arithmetic needs, per frame: per evaluation 13 FP32
+    operations (offset, quadratic form, scale, clamp, compare) and one ex2; per contribution
+    4 + levels K FP32 operations (1 - alpha, T update, compare, alpha T, the levels K weighted adds)
+    and 2 levels K accumulator accesses (a read and a write per pair, counted as shared-memory
+    accesses whatever memory holds the accumulator).  The fraction of each unit's measured rate
+    the splat stage reaches; the largest names the bound."""
+    t = splat_ms * 1e-3
+    E, C = work["evaluations"], work["contributions"]
+    fp32 = E * 13 + C * (4 + levels * K)
+    need = {"fp32": (fp32, rates["fp32_fma_per_s"]), "ex2": (E, rates["ex2_per_s"]),
+            "shared_memory": (C * 2 * levels * K, rates["smem_access_per_s"])}
+    fr = {k: (n / t) / peak for k, (n, peak) in need.items()}
+    bound = max(fr, key=fr.get)
+    return {"bound": bound, "frac": fr[bound], "fracs": fr,
+            "ops_per_frame": {k: n for k, (n, _) in need.items()},
+            "achieved_per_s": {k: n / t for k, (n, _) in need.items()},
+            "peak_per_s": {k: p for k, (_, p) in need.items()}, "peak_source": "measured (lsv2_rate_probe)",
+            "work": work}
+
+
+def precision_report(dev, chunk: int = 131072):
+    """The precision workload (the tiny scene rendered at 1440x1080, one level): the BF16 path
+    (coefficient map stored as BF16, tensor-core decode to BF16 F, tensor-core relevancy with one
+    query and four negatives) against the FP64 oracle over every pixel: max and mean absolute error
+    of the coefficient map W, the feature map F and the relevancy map; pixels whose blend decisions
+    sit within 1e-4 relative of a threshold (knife edges, decided by rounding) counted and also
+    left out in a second set of figures."""
+    import torch
+    import lsv2_synth as syn
+    from oracle import oracle as O
+    from paper_2507_07136_b300 import _lib as Lb
+    from paper_2507_07136_b300.pipeline import DeviceScene, Frame
+    sc, cam = syn.precision()
+    text = syn.text_queries(syn.SEED + 2, 1, 4)
+    fr = Frame(DeviceScene.from_numpy(sc, device=dev), cam, device=dev)
+    fr.project()
+    fr.bin_sort()
+    fr.splat_bf16()
+    F = torch.empty((1, fr.P, sc.D), dtype=torch.bfloat16, device=dev)
+    fr.decode(F, codebook=fr.scene.codebook.to(torch.bfloat16), from_bf16=True)
+    rel = torch.empty((1, 1, fr.P), dtype=torch.float32, device=dev)
+    fr.query(torch.as_tensor(text, device=dev), rel, compute=Lb.LSV2_BF16, from_bf16=True)
+    fr.check()
+    r = O.render(sc, cam)
+    Wo = r.blend.out[0]
+    ok = r.blend.margin > 1e-4
+    S = sc.codebook[0].astype(np.float64)
+    stats = {k: {"max": 0.0, "sum": 0.0, "max_ok": 0.0, "sum_ok": 0.0, "n": 0, "n_ok": 0} for k in ("W", "F", "rel")}
+
+    def acc(name, err, okm):
+        d = stats[name]
+        d["max"] = max(d["max"], float(err.max()))
+        d["sum"] += float(err.sum())
+        d["n"] += err.size
+        e2 = err[okm]
+        if e2.size:
+            d["max_ok"] = max(d["max_ok"], float(e2.max()))
+            d["sum_ok"] += float(e2.sum())
+            d["n_ok"] += e2.size
+
+    for p0 in range(0, fr.P, chunk):
+        p1 = min(fr.P, p0 + chunk)
+        okc = ok[p0:p1]
+        Wg = fr.coeff16[0, p0:p1].float().cpu().numpy().astype(np.float64)
+        acc("W", np.abs(Wg - Wo[p0:p1]), np.repeat(okc[:, None], Wg.shape[1], 1))
+        Fo = Wo[p0:p1] @ S
+        Fg = F[0, p0:p1].float().cpu().numpy().astype(np.float64)
+        acc("F", np.abs(Fg - Fo), np.repeat(okc[:, None], Fg.shape[1], 1))
+        ro = O.relevancy(Fo[None], text, 10.0)[0, 0]
+        acc("rel", np.abs(rel[0, 0, p0:p1].cpu().numpy().astype(np.float64) - ro), okc)
+    out = {"workload": "2,000 Gaussians, 1 level, K=4, L=64, D=512, 1440x1080 (the tiny scene at full size), "
+                       "1 query + 4 negatives, tau = 10",
+           "path": "FP32 blend stored as BF16; BF16 tensor-core decode (BF16 F) and relevancy (FP32 accumulation)",
+           "knife_edge_pixels": int((~ok).sum()), "pixels": int(fr.P)}
+    for k, d in stats.items():
+        out[k] = {"max_abs": d["max"], "mean_abs": d["sum"] / max(1, d["n"]),
+                  "max_abs_excl_knife_edge": d["max_ok"], "mean_abs_excl_knife_edge": d["sum_ok"] / max(1, d["n_ok"])}
+    return out
+
+
 # ----------------------------------------------------------------------------- speed ablation
 def ablation_section(dev, reps: int = 10):
     """The paper's speed ablation on B300 (Table 9 and the K ablation): at 300k Gaussians, three
@@ -609,8 +736,39 @@ def batched_section(dev, reps: int = 5, rank: int = 0, world: int = 1):
     for f in frames:
         f.check()
     seq_ms = s.elapsed_time(e) / reps
+    del frames, rels
+    torch.cuda.empty_cache()
+    # the relevancy part alone at the batch's size: one lsv2_query (BF16) over a coefficient map of
+    # all views' pixels and the batch's 64 queries (the same kernels and query groups the batched
+    # call runs over its per-view maps)
+    Q = text.shape[0]
+    W16 = (torch.rand((scene.levels, pix, 64), device=dev) * 0.05).to(torch.bfloat16)
+    rel16 = torch.empty((Q, scene.levels, pix), dtype=torch.bfloat16, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    qws_bytes = Lb.lsv2_query_workspace_bytes(scene.levels, 64, Q, text.shape[1] - 1)
+    qws = torch.empty(qws_bytes, dtype=torch.uint8, device=dev)
+    st = torch.cuda.current_stream().cuda_stream
+
+    def rel_call():
+        Lb.lsv2_query(scene.levels, pix, 64, scene.D, W16.data_ptr(), Lb.LSV2_BF16, scene.codebook.data_ptr(), Q,
+                      text.shape[1] - 1, t.data_ptr(), 10.0, qws.data_ptr(), qws_bytes, rel16.data_ptr(), Lb.LSV2_BF16,
+                      Lb.LSV2_BF16, status.data_ptr(), st)
+    rel_call()
+    torch.cuda.synchronize()
+    s.record()
+    for _ in range(reps):
+        rel_call()
+    e.record()
+    torch.cuda.synchronize()
+    rel_ms = s.elapsed_time(e) / reps
+    assert int(status.item()) == 0
+    del W16, rel16, qws
+    torch.cuda.empty_cache()
+    pk, pk_kind = peaks()
+    rel_flop = 2.0 * pix * scene.levels * 64 * (64 + (text.shape[1]) * Q)
+    rel_bytes = scene.levels * pix * 64 * 2 + Q * scene.levels * pix * 2
     if world > 1:
-        batched_ms, seq_ms = max_over_ranks([batched_ms, seq_ms], world, dev)
+        batched_ms, seq_ms, rel_ms = max_over_ranks([batched_ms, seq_ms, rel_ms], world, dev)
         cnt = torch.tensor([inst, pix, rel_elems], dtype=torch.int64, device=dev)
         dist.all_reduce(cnt)
         inst, pix, rel_elems = (int(v) for v in cnt.tolist())
@@ -620,7 +778,17 @@ def batched_section(dev, reps: int = 5, rank: int = 0, world: int = 1):
             "queries_per_s": nq * 1e3 / batched_ms, "ms_per_batch": batched_ms,
             "sequential_ms": seq_ms, "sequential_queries_per_s": nq * 1e3 / seq_ms,
             "speedup_vs_sequential": seq_ms / batched_ms, "tile": list(tile), "stage_batch": batch,
-            "pixels": pix, "instances": inst, "relevancy_values": rel_elems, "launch": "one CUDA graph"}
+            "pixels": pix, "instances": inst, "relevancy_values": rel_elems, "launch": "one CUDA graph",
+            "relevancy_ms": rel_ms, "relevancy_share": rel_ms / batched_ms,
+            "relevancy_roofline": {
+                "tensor": {"achieved": rel_flop / (rel_ms * 1e-3) / 1e12, "peak": pk["bf16_tflops_sustained"],
+                           "unit": "TFLOP/s", "frac": rel_flop / (rel_ms * 1e-3) / 1e12 / pk["bf16_tflops_sustained"],
+                           "algorithmic_flop": rel_flop, "peak_source": pk_kind + " (sustained BF16)"},
+                "hbm": {"achieved": rel_bytes / (rel_ms * 1e-3) / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                        "frac": rel_bytes / (rel_ms * 1e-3) / 1e9 / pk["hbm_gbs"], "algorithmic_bytes": rel_bytes,
+                        "peak_source": pk_kind},
+                "note": "relevancy of all views' pixels for the 64 queries (2 P levels 64 (64 + 5 Q) flop with "
+                        "[S S^T] counted once; BF16 W read + BF16 relevancy write), one lsv2_query call timed alone"}}
 
 
 # ----------------------------------------------------------------------------- GPU arm
@@ -684,6 +852,8 @@ def main():
                     help="for a profiler capture: prepare the at-scale frame, then run only this stage "
                          "(--warmup + --steps launches) with only the buffers it needs; `backward` runs the "
                          "training-step measurement of the differentiation workload instead; prints one status line")
+    ap.add_argument("--precision", action="store_true",
+                    help="print the precision workload's max/mean errors against the FP64 oracle (about a minute of CPU)")
     ap.add_argument("--cpu-pixels", type=int, default=2000,
                     help="pixels the FP64 oracle blends, decodes and queries per CPU-baseline sample")
     args = ap.parse_args()
@@ -711,6 +881,9 @@ def main():
         print(json.dumps({"profile": "backward", "forward_ms": r["forward_ms"],
                           "l1_decode_backward_ms": r["l1_decode_backward_ms"],
                           "splat_backward_ms": r["splat_backward_ms"], "step_ms": r["step_ms"]}), flush=True)
+        return
+    if args.precision:
+        print(json.dumps({"precision": precision_report(dev)}), flush=True)
         return
     if args.profile == "sparsify":
         r = sparsify_section(dev, reps=args.steps)
@@ -907,8 +1080,12 @@ def main():
                   "unit": "GB/s", "traffic": TRAFFIC.get("query_pipe_kernel<3>"), "kernel": "query_pipe_kernel<3> + prepare",
                   "algorithmic_bytes": query_bytes, "peak_source": pk_kind},
     }
-    for r in roofs.values():
+    for k, r in roofs.items():
         r["frac"] = r["achieved"] / r["peak"]
+    # the splat against the units its blend needs (FP32 pipe, MUFU ex2, accumulator accesses)
+    rates = unit_rates(dev)
+    roofs["splat_units"] = splat_alu_roofline(splat_work(sc, cam), levels, scene.K, stage_ms["splat"], rates)
+    roofs["splat_units"]["kernel"] = SPLAT_KERNEL + " + record packing"
     dom = max(["splat", "decode"], key=lambda k: stage_ms[k])
     gpu_launches = sum(launches_per_step.values()) * args.steps
 
@@ -930,6 +1107,7 @@ def main():
                                 + stage_ms["post"]),
             "roofline": dict(roofs[dom]),
             "rooflines": roofs,
+            "unit_rates": rates,
             "fp32_path": fp32,
             "fused_splat_decode_query_ms": fused_ms,
             "split_splat_decode_query_ms": stage_ms["splat"] + stage_ms["decode"] + stage_ms["query"],

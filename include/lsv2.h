@@ -410,6 +410,17 @@ lsv2_status lsv2_splat_backward(const lsv2_camera* cam, int64_t n, const float* 
                                 float* dw, float* dopacity, float* dmeans, float* dscales,
                                 float* dquats, int32_t* dev_status, void* stream);
 
+/* Rate probes of the units that bind the splat's blend, for roofline denominators measured on the
+ * device at hand (no counterpart in the paper).  lsv2_rate_probe launches `blocks` CTAs of 512
+ * threads, each running `iters` steps of eight independent chains of one operation:
+ *   kind 0  FP32 FMA         kind 1  ex2 (the MUFU unit)
+ *   kind 2  4-byte shared-memory load + store of a thread's own words (conflict-free)
+ * lsv2_rate_probe_ops gives the operations one such launch performs (FMAs, ex2, or shared-memory
+ * accesses); the caller times the launch on `stream` and divides.  sink: float[blocks] on the
+ * device (written only to keep the work live).  Asynchronous like every other call. */
+double lsv2_rate_probe_ops(int32_t kind, int64_t iters, int32_t blocks);
+lsv2_status lsv2_rate_probe(int32_t kind, int64_t iters, int32_t blocks, float* sink, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

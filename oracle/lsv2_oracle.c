@@ -443,6 +443,8 @@ int64_t orc_bin(const orc_camera* c, int64_t n, const uint8_t* flags, const int3
  *    out[lev][p][ch] (ch < L for modes 0/1, < D for mode 2).
  *    margin[p] = smallest relative distance of a decision quantity (alpha vs 1/255,
  *    test_T vs 1e-4) from its threshold; tiny margins mark knife-edge pixels.
+ *    n_eval[p] (optional) = list entries examined, up to and including the one that stops
+ *    the walk (the count of evaluations Algorithm 1 makes at this pixel).
  * ==================================================================================== */
 
 void orc_blend(const orc_camera* c, int64_t npix, const int32_t* px, const int32_t* py,
@@ -450,7 +452,8 @@ void orc_blend(const orc_camera* c, int64_t npix, const int32_t* px, const int32
                const uint32_t* gauss_ids, const uint32_t* tile_ranges,
                int32_t mode, int32_t levels, int32_t K, int32_t C,
                const uint8_t* idx, const float* w, const double* dense,
-               double* out, double* final_T, int32_t* n_last, int32_t* n_contrib, double* margin)
+               double* out, double* final_T, int32_t* n_last, int32_t* n_contrib, double* margin,
+               int32_t* n_eval)
 {
     int32_t GX = grid_x(c);
     for (int64_t p = 0; p < npix; ++p) {
@@ -460,9 +463,10 @@ void orc_blend(const orc_camera* c, int64_t npix, const int32_t* px, const int32
         int32_t tile = (y / c->tile_h) * GX + (x / c->tile_w);
         uint32_t beg = tile_ranges[2 * tile], end = tile_ranges[2 * tile + 1];
         double T = 1.0, mg = INFINITY;
-        int32_t last = 0, cnt = 0;
+        int32_t last = 0, cnt = 0, ev = 0;
         for (uint32_t j = beg; j < end; ++j) {
             uint32_t g = gauss_ids[j];
+            ++ev;
             double dx = mean2d[2 * g] - (double)x, dy = mean2d[2 * g + 1] - (double)y;
             double a = conic[3 * g], b = conic[3 * g + 1], cc = conic[3 * g + 2];
             double power = -0.5 * (a * dx * dx + cc * dy * dy) - b * dx * dy;
@@ -496,6 +500,7 @@ void orc_blend(const orc_camera* c, int64_t npix, const int32_t* px, const int32
         n_last[p] = last;
         if (n_contrib) n_contrib[p] = cnt;
         if (margin) margin[p] = mg;
+        if (n_eval) n_eval[p] = ev;
     }
 }
 

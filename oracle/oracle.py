@@ -70,7 +70,7 @@ def lib():
         _lib.orc_bin.argtypes = [P, I64, P, P, P, P, P]
         _lib.orc_bin.restype = I64
         _lib.orc_blend.argtypes = [P, I64, P, P, P, P, P, P, P, I32, I32, I32, I32, P, P, P, P, P,
-                                   P, P, P]
+                                   P, P, P, P]
         _lib.orc_decode.argtypes = [I32, I64, I32, I32, P, P, P]
         _lib.orc_relevancy.argtypes = [I32, I64, I32, P, I32, I32, P, D, P]
         _lib.orc_blend_backward.argtypes = [P, I64, P, P, P, P, P, I32, I32, I32, P, P, P, P, P, P,
@@ -181,6 +181,7 @@ class Blend:
     n_last: np.ndarray     # i32 [npix] list position + 1 of the last contributor
     n_contrib: np.ndarray  # i32 [npix]
     margin: np.ndarray     # f64 [npix]
+    n_eval: np.ndarray = None   # i32 [npix] list entries examined (up to and including the stop)
 
 
 def all_pixels(cam):
@@ -218,7 +219,7 @@ def blend(cam, proj: Projection, opacity, ids, ranges, idx=None, w=None, dense=N
         dense_p = _p(dense)
     out = np.zeros((levels, npix, C_out))
     res = Blend(out, np.zeros(npix), np.zeros(npix, np.int32), np.zeros(npix, np.int32),
-                np.zeros(npix))
+                np.zeros(npix), np.zeros(npix, np.int32))
     ids = np.ascontiguousarray(ids, np.uint32)
     if ids.size == 0:
         ids = np.zeros(1, np.uint32)
@@ -226,7 +227,8 @@ def blend(cam, proj: Projection, opacity, ids, ranges, idx=None, w=None, dense=N
     c = cam_struct(cam)
     lib().orc_blend(C.byref(c), npix, _p(px), _p(py), _p(proj.mean2d), _p(proj.conic), _p(opacity),
                     _p(ids), _p(ranges), mode, levels, K, C_out, _p(idx), _p(w), dense_p,
-                    _p(out), _p(res.final_T), _p(res.n_last), _p(res.n_contrib), _p(res.margin))
+                    _p(out), _p(res.final_T), _p(res.n_last), _p(res.n_contrib), _p(res.margin),
+                    _p(res.n_eval))
     return res
 
 

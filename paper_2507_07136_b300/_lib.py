@@ -50,6 +50,8 @@ _SIGS = {
     "lsv2_abi_version": ([], I32),
     "lsv2_status_string": ([I32], C.c_char_p),
     "lsv2_set_wait_limit_ns": ([C.c_uint64], None),
+    "lsv2_rate_probe_ops": ([I32, I64, I32], C.c_double),
+    "lsv2_rate_probe": ([I32, I64, I32, P, P], I32),
     "lsv2_wait_limit_ns": ([], C.c_uint64),
     "lsv2_project": ([P, I64, P, P, P, P, P, P, P], I32),
     "lsv2_bin_sort_workspace_bytes": ([I64, I64, I32], SZ),
