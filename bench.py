@@ -47,9 +47,9 @@ SPLAT_KERNEL = "splat_tm_kernel<3,4> (one CTA per 16x16 tile, consumer warps 4-7
 # removed when its kernel changes): the splat and the relevancy as launched here; the decode
 # captured over one level (one third of the launch's pixels and bytes) and scaled by 3.
 TRAFFIC = {
-    SPLAT_KERNEL: 47201024 + 552040960,
-    "decode_tc_kernel": 3 * (199166976 + 1532453376),
-    "query_pipe_kernel<3>": 597294848 + 18970880,
+    SPLAT_KERNEL: 47180288 + 551101696,
+    "decode_tc_kernel": 3 * (199180032 + 1531681536),
+    "query_pipe_kernel<3>": 597294592 + 18291456,
 }
 
 
