@@ -14,7 +14,12 @@ pairs per Gaussian and semantic level over an L=64 codebook of D=512-d unit
 features (Sec. 3.3, Eq. 5; Sec. 4.1 sets L=64, K=4, three levels), and unit
 512-d text embeddings for the relevancy query (Sec. 3.2).
 
-Seeds: 20250707 scene, +1 codebook, +2 text, +3 L1 target, +4 batched scene, +5 relevancy maps.
+The decoder-based comparison path (LangSplat*, Sec. 3.1) needs per-Gaussian latent features
+(d = 3 per level, Eq. 4) and the weights of a decoder MLP; the trained ones are not available,
+so both are drawn at random with the right shapes (``latent_features``, ``decoder_mlp``).
+
+Seeds: 20250707 scene, +1 codebook, +2 text, +3 L1 target, +4 batched scene, +5 relevancy maps,
++6 latent features, +7 decoder weights.
 """
 from __future__ import annotations
 
@@ -27,6 +32,10 @@ SEED = 20250707
 L_CODEBOOK = 64
 K_PAIRS = 4
 D_FEAT = 512
+LATENT_D = 3
+# decoder widths, latent in -> CLIP feature out: the paper fixes only the ends (3 and 512); the
+# hidden widths are a widening stack of the kind a scene autoencoder's decoder uses
+DECODER_WIDTHS = (LATENT_D, 16, 32, 64, 128, 256, 256, D_FEAT)
 
 
 def _rng(seed: int) -> np.random.Generator:
@@ -257,3 +266,38 @@ def relevancy_maps(seed: int, Q: int, levels: int, H: int, W: int, blobs: int = 
                 m += h * np.exp(-((x - cx) ** 2 + (y - cy) ** 2) / (2 * s * s))
             out[q, l] = (m / (1.0 + m)).reshape(-1)
     return out
+
+
+def latent_features(n: int, levels: int, d: int = LATENT_D, seed: int = SEED + 6) -> np.ndarray:
+    """Per-Gaussian latent features f_i of the decoder-based path (Eq. 4): f32 [n, levels, d],
+    N(0, 1) entries (an autoencoder's latent codes, of unit scale)."""
+    return _rng(seed).standard_normal((n, levels, d)).astype(np.float32)
+
+
+def bf16_representable(x: np.ndarray) -> np.ndarray:
+    """float32 values rounded (to nearest, ties to even) onto the BF16 grid: weights stored in
+    BF16, held as float32 so every consumer reads the same numbers."""
+    b = np.ascontiguousarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32)
+
+
+def decoder_mlp(widths=DECODER_WIDTHS, seed: int = SEED + 7):
+    """Random weights of the decoder MLP: a list of (W [w_in, w_out], b [w_out]) float32 pairs.
+    W ~ N(0, 2 / w_in) before a ReLU and N(0, 1 / w_in) for the last layer (so activations keep
+    their scale through the stack), stored on the BF16 grid; b ~ N(0, 0.05^2) in float32."""
+    rng = _rng(seed)
+    layers = []
+    for l in range(len(widths) - 1):
+        gain = 1.0 if l == len(widths) - 2 else 2.0
+        W = rng.normal(0.0, math.sqrt(gain / widths[l]), (widths[l], widths[l + 1]))
+        b = rng.normal(0.0, 0.05, widths[l + 1])
+        layers.append((bf16_representable(W.astype(np.float32)), b.astype(np.float32)))
+    return layers
+
+
+def latent_at_scale():
+    """The at-scale frame's Gaussians (300,000, three levels, 1440x1080) carrying latent features
+    instead of sparse coefficients, and the decoder's weights."""
+    sc, cam, text = at_scale()
+    return sc, cam, latent_features(sc.n, sc.levels), decoder_mlp()

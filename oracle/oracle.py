@@ -20,6 +20,8 @@ Each function names the passage of the paper it follows (LangSplatV2, arXiv
                 complex step)
   sparsify,     Sec. 3.3 sparse coefficients: softmax over the L-dim parameter, top K
   sparsify_backward   kept and renormalised by their sum; its gradient (NumPy, FP64)
+  mlp_decode    Sec. 3.1: the decoder g_d of the decoder-based path (LangSplat*) applied to a
+                rendered latent feature (Eq. 4 is ``blend`` mode 2 with d-dim features)
 """
 from __future__ import annotations
 
@@ -461,3 +463,19 @@ def l1_loss_fd_eval(scene_params, cam, ids, ranges, tile_mask, idx, S, target):
                                   _p(np.ascontiguousarray(idx, np.uint8)), _p(w), _p(_f32(S)),
                                   _p(_f32(target)), _p(per_pixel), C.byref(sig))
     return per_pixel, sig.value
+
+
+# --------------------------------------------------------------------------------------
+# The decoder-based comparison path (LangSplat*).
+
+def mlp_decode(x, layers) -> np.ndarray:
+    """Sec. 3.1: the decoder g_d maps a rendered latent feature (Eq. 4) back to the D-dim CLIP space.
+    g_d is an MLP: every layer but the last is affine then ReLU, the last is affine.  FP64 NumPy,
+    one layer at a time.  x [rows, d_in]; layers: list of (W [w_in, w_out], b [w_out]).
+    -> [rows, w_out of the last layer]."""
+    h = np.asarray(x, np.float64)
+    for i, (W, b) in enumerate(layers):
+        h = h @ np.asarray(W, np.float64) + np.asarray(b, np.float64)
+        if i < len(layers) - 1:
+            h = np.maximum(h, 0.0)
+    return h

@@ -612,3 +612,61 @@ def test_sparsify_backward_invariants():
     idx1, w1 = O.sparsify(z, 1)
     assert np.all(w1 == 1.0)
     assert np.all(O.sparsify_backward(idx1, w1, dw[:, :1], 64) == 0)
+
+
+# ----------------------------------------------------------------------------- decoder-based path
+
+def test_mlp_decode_worked_example():
+    """A two-layer g_d evaluated by hand.  x = (1, -2): the hidden pre-activation is
+    x W1 + b1 = (1 + 2 + 0.5, -2 + 0, 2 + 0 - 3) = (3.5, -2, -1), ReLU keeps (3.5, 0, 0), and the
+    output is 3.5 * 2 - 1 = 6.  x = (-1, 0): pre-activation (-0.5, 0, -5), all cut by the ReLU, so
+    the output is the last bias, -1 (negative: no ReLU after the last layer)."""
+    W1 = np.array([[1.0, 0.0, 2.0], [-1.0, 1.0, 0.0]])
+    b1 = np.array([0.5, 0.0, -3.0])
+    W2 = np.array([[2.0], [5.0], [7.0]])
+    b2 = np.array([-1.0])
+    y = O.mlp_decode(np.array([[1.0, -2.0], [-1.0, 0.0]]), [(W1, b1), (W2, b2)])
+    assert y.shape == (2, 1)
+    assert y[0, 0] == 6.0 and y[1, 0] == -1.0
+
+
+def test_mlp_decode_relu_identity_and_homogeneity():
+    """With zero biases a ReLU network is positively homogeneous, f(c x) = c f(x) for c > 0, and
+    for one hidden layer relu(a) - relu(-a) = a gives f(x) - f(-x) = x W1 W2 (a missing ReLU would
+    give twice that; a ReLU after the last layer would make every output nonnegative)."""
+    rng = np.random.default_rng(11)
+    W1, W2 = rng.standard_normal((3, 16)), rng.standard_normal((16, 5))
+    z1, z2 = np.zeros(16), np.zeros(5)
+    x = rng.standard_normal((50, 3))
+    f = O.mlp_decode(x, [(W1, z1), (W2, z2)])
+    fm = O.mlp_decode(-x, [(W1, z1), (W2, z2)])
+    np.testing.assert_allclose(f - fm, x @ W1 @ W2, rtol=0, atol=1e-12)
+    assert (f < 0).any()
+    layers = [(l[0], np.zeros_like(l[1])) for l in syn.decoder_mlp()]
+    np.testing.assert_allclose(O.mlp_decode(2.5 * x, layers), 2.5 * O.mlp_decode(x, layers), rtol=1e-12, atol=1e-12)
+
+
+def test_mlp_decode_identity_layers():
+    """Identity weights and zero biases: the hidden ReLUs clamp negatives to zero and the last
+    layer passes its input through, so g_d(x) = relu(x); a bias shifts the output by exactly b."""
+    x = np.array([[1.5, -2.0, 0.25], [-0.5, 3.0, -1.0]])
+    eye, z = np.eye(3), np.zeros(3)
+    np.testing.assert_array_equal(O.mlp_decode(x, [(eye, z), (eye, z), (eye, z)]), np.maximum(x, 0.0))
+    b = np.array([0.5, -1.0, 2.0])
+    np.testing.assert_array_equal(O.mlp_decode(x, [(eye, z), (eye, b)]), np.maximum(x, 0.0) + b)
+
+
+def test_latent_render_as_pairs():
+    """Eq. 4 with a d = 3 latent per Gaussian (blend mode 2) equals the sparse blend of the pairs
+    (index k, weight f_k) for k < 3 plus (3, 0) over an 8-column map: channels 0..2 carry the
+    latent render, channels 3..7 stay exactly zero."""
+    sc, cam = syn.tiny()
+    r = O.render(sc, cam)
+    lat = syn.latent_features(sc.n, 1)
+    direct = O.blend(cam, r.proj, sc.opacity, r.ids, r.ranges, dense=lat.astype(np.float64), mode=2)
+    idx = np.broadcast_to(np.arange(4, dtype=np.uint8), (sc.n, 1, 4)).copy()
+    w = np.concatenate([lat, np.zeros((sc.n, 1, 1), np.float32)], axis=2)
+    pairs = O.blend(cam, r.proj, sc.opacity, r.ids, r.ranges, idx=idx, w=w, C_out=8)
+    np.testing.assert_allclose(pairs.out[:, :, :3], direct.out, rtol=0, atol=1e-14)
+    assert np.all(pairs.out[:, :, 3:] == 0.0)
+    assert np.abs(direct.out).max() > 0.1
