@@ -633,6 +633,87 @@ def backward_section(dev, reps: int = 10):
                                "note": "bound by its atomics and per-pixel latency, not HBM"}}
 
 
+def decoder_path_section(dev, v2_render_decode_ms: float | None = None, reps: int = 10):
+    """Table 1's contrast on B300: the decoder-based path (LangSplat*: a d = 3 latent per level
+    rendered by Eq. 4, then the MLP decoder g_d to 512-d features for every pixel and level) against
+    LangSplatV2's render + linear decode (Eq. 7), both at the at-scale frame (300,000 Gaussians,
+    three levels, 1440x1080).  The latent render is the library's splat at L = 8; the decoder is
+    lsv2_mlp_decode (cuBLASLt BF16 GEMMs with fused bias/ReLU, 4.67 M rows of the widths
+    8-16-32-64-128-256-256-512), timed as one CUDA graph per row-block size (the decoder launches
+    eight kernels per row block).  L2 flushed between repetitions."""
+    import torch
+    import lsv2_synth as syn
+    from paper_2507_07136_b300.decoder_path import Decoder, DecoderFrame
+    from paper_2507_07136_b300.pipeline import DeviceScene
+
+    sc, cam, lat, layers = syn.latent_at_scale()
+    ds = DeviceScene.from_numpy(sc, device=dev)
+    dec = Decoder(layers, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    F = torch.empty((sc.levels, cam.num_pixels, dec.out_width), dtype=torch.bfloat16, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+            flush.fill_(1)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.mean(ts))
+
+    def graph_of(fn):
+        fn()                       # the first call of each shape plans its GEMMs on the host
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            fn()
+        return g
+
+    decode_ms, fr = {}, None
+    for block_rows in (16384, 65536, 262144):
+        fr = DecoderFrame(ds, torch.as_tensor(lat), dec, cam, block_rows=block_rows, device=dev)
+        fr.render()
+        fr.check()
+        g = graph_of(lambda: fr.decode(F))
+        decode_ms[str(block_rows)] = timed(g.replay)
+        fr.check()
+        del g
+    best = min(decode_ms, key=decode_ms.get)
+    render = {"project": timed(fr.project), "bin_sort": timed(fr.bin_sort), "latent_splat": timed(fr.splat)}
+    fr.check()
+    render_ms = sum(render.values())
+    rows = sc.levels * cam.num_pixels
+    flop = rows * dec.flops_per_row()
+    pk, pk_kind = peaks()
+    tf = flop / (decode_ms[best] * 1e-3) / 1e12
+    byts = rows * (8 * 4 + dec.out_width * 2)    # the F32 latent map in, the BF16 features out
+    out = {"workload": "300k Gaussians, 3 levels, 1440x1080; latent d = 3 per level (padded to 8 channels), "
+                       "decoder 8-16-32-64-128-256-256-512 (ReLU), BF16 out",
+           "render_ms": render, "decode_ms_by_block_rows": decode_ms, "block_rows": int(best),
+           "render_decode_ms": render_ms + decode_ms[best],
+           "render_decode_fps": 1e3 / (render_ms + decode_ms[best]),
+           "decode": {"bound": "tensor", "achieved": tf, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
+                      "frac": tf / pk["bf16_tflops"], "algorithmic_flop": flop, "algorithmic_bytes": byts,
+                      "hbm_floor_ms": byts / pk["hbm_gbs"] / 1e6, "peak_source": pk_kind + " (burst)",
+                      "kernel": "cuBLASLt BF16 GEMMs (library) + to_bf16_kernel"},
+           "paper_a100_ms": {"LangSplat* rendering": 2.0, "LangSplat* decoding": 83.1,
+                             "LangSplatV2 rendering": 2.0, "LangSplatV2 decoding": 0.1}}
+    if v2_render_decode_ms is not None:
+        out["langsplatv2_render_decode_ms"] = v2_render_decode_ms
+        out["decoder_over_v2"] = out["render_decode_ms"] / v2_render_decode_ms
+    del fr, F
+    torch.cuda.empty_cache()
+    return out
+
+
 # ----------------------------------------------------------------------------- batched views
 def sparsify_section(dev, reps: int = 20):
     """Sec. 3.3 sparse coefficients on the at-scale shape (300,000 Gaussians x 3 levels of 64 logits,
@@ -848,10 +929,13 @@ def main():
     ap.add_argument("--no-fp32-path", action="store_true", help="skip the plain FP32 comparison measurement")
     ap.add_argument("--no-batched", action="store_true", help="skip the 16-view x 64-query batched measurement")
     ap.add_argument("--no-ablation", action="store_true", help="skip the sparse/dense and K speed ablation")
-    ap.add_argument("--profile", choices=["project", "bin", "splat", "decode", "query", "query32", "backward", "sparsify"], default=None,
+    ap.add_argument("--no-decoder-path", action="store_true",
+                    help="skip the decoder-based (LangSplat*) comparison measurement")
+    ap.add_argument("--profile", choices=["project", "bin", "splat", "decode", "query", "query32", "backward", "sparsify", "decoder"], default=None,
                     help="for a profiler capture: prepare the at-scale frame, then run only this stage "
                          "(--warmup + --steps launches) with only the buffers it needs; `backward` runs the "
-                         "training-step measurement of the differentiation workload instead; prints one status line")
+                         "training-step measurement of the differentiation workload instead, `decoder` the decoder-based "
+                         "comparison path (--steps repetitions); prints one status line")
     ap.add_argument("--precision", action="store_true",
                     help="print the precision workload's max/mean errors against the FP64 oracle (about a minute of CPU)")
     ap.add_argument("--cpu-pixels", type=int, default=2000,
@@ -884,6 +968,10 @@ def main():
         return
     if args.precision:
         print(json.dumps({"precision": precision_report(dev)}), flush=True)
+        return
+    if args.profile == "decoder":
+        r = decoder_path_section(dev, reps=args.steps)
+        print(json.dumps({"profile": "decoder", **r}), flush=True)
         return
     if args.profile == "sparsify":
         r = sparsify_section(dev, reps=args.steps)
@@ -1126,6 +1214,10 @@ def main():
     if not args.no_ablation and world == 1:
         torch.cuda.empty_cache()
         line["ablation"] = ablation_section(dev)
+    if not args.no_decoder_path and world == 1:
+        torch.cuda.empty_cache()
+        v2 = stage_ms["project"] + stage_ms["bin_sort"] + stage_ms["splat"] + stage_ms["decode"]
+        line["decoder_path"] = decoder_path_section(dev, v2)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.cpu_pixels)

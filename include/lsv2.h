@@ -19,6 +19,8 @@
  *   lsv2_render_fused  splat + decode + query of one frame in one kernel (W stays on chip)
  *   lsv2_postprocess   mean filter, level selection, localisation point and segmentation mask
  *                      of relevancy maps (appendix "Evaluation Details")
+ *   lsv2_mlp_decode    the MLP decoder of the decoder-based comparison path (LangSplat*,
+ *                      Sec. 3.1, Table 1), which Eq. 7 replaces
  *   lsv2_splat_backward, lsv2_l1_decode_backward
  *                      gradients of an L1 feature loss (no counterpart in the paper, which
  *                      trains the field but does not describe its gradient)
@@ -166,7 +168,9 @@ size_t lsv2_splat_workspace_bytes(int64_t n, int32_t levels, int32_t K);
  *   the list position (+1, relative to the tile start) of that contributor (0: none).
  * Blending is FP32.  Supported: L = 64 with levels 1 and K in {2, 4, 6, 8}, levels 2 and K = 4,
  * levels 3 and K = 4 (any tile) or K in {2, 6, 8} (16x16 tiles); tiles 16x16, 8x8, 32x8.  Also
- * L in {32, 128} with levels 3, K = 4 and 16x16 tiles (the codebook-size sweep). */
+ * L in {32, 128} with levels 3, K = 4 and 16x16 tiles (the codebook-size sweep), and L = 8 with
+ * levels 3, K = 4 and 16x16 tiles: a dense low-dimensional feature splat (the latent of the
+ * decoder-based comparison path, lsv2_mlp_decode) as pairs with indices 0..3. */
 lsv2_status lsv2_splat_coeffs(const lsv2_camera* cam, int64_t n, const lsv2_proj* proj,
                               const uint32_t* tile_ranges, const uint32_t* gauss_ids,
                               int32_t levels, int32_t K, int32_t L, const uint8_t* idx,
@@ -409,6 +413,35 @@ lsv2_status lsv2_splat_backward(const lsv2_camera* cam, int64_t n, const float* 
                                 const float* dcoeff, void* workspace, size_t workspace_bytes,
                                 float* dw, float* dopacity, float* dmeans, float* dscales,
                                 float* dquats, int32_t* dev_status, void* stream);
+
+/* Workspace for lsv2_mlp_decode (0 for invalid arguments): two activation buffers of one row
+ * block at the widest hidden layer, a BF16 copy of an F32 input block, and 32 MiB for the
+ * library GEMM's own scratch. */
+size_t lsv2_mlp_decode_workspace_bytes(int64_t rows, int32_t n_layers, const int32_t* widths,
+                                       int32_t x_dtype, int64_t block_rows);
+
+/* The decoder of the decoder-based comparison path (LangSplat*, Sec. 3.1: the latent feature
+ * rendered by Eq. 4 is decoded to the D-dim CLIP space by the MLP g_d; Table 1 times it as the
+ * dominant stage).  Not part of LangSplatV2's own path, which replaces g_d by Eq. 7.
+ * For every row r:  h_0 = x[r];  h_{l+1} = relu(h_l W_l + b_l)  (l < n_layers - 1);
+ *                   y[r] = h_{n_layers-1} W_{n_layers-1} + b_{n_layers-1}.
+ *   widths   int32[n_layers + 1], HOST memory: w_0 (input) .. w_n (output); each a multiple of
+ *            8 in [8, 4096] (pad a narrower input with zero columns and zero weight rows)
+ *   x        [rows][w_0]  dtype x_dtype (F32: rounded to BF16 per block first; or BF16)
+ *   weights  bf16, the W_l one after another, each row-major [w_l][w_{l+1}]
+ *   biases   float, the b_l one after another, each [w_{l+1}]
+ *   y        bf16 [rows][w_n]
+ * Each layer is a library GEMM (cuBLASLt) with BF16 operands, FP32 accumulation and a fused
+ * bias (+ ReLU) epilogue; intermediate activations are rounded to BF16.  Rows go in blocks of
+ * block_rows (a multiple of 128; 0 = 65,536) so a block's activations stay in L2 between
+ * layers.  All pointers 16-byte aligned.  Returns LSV2_ERR_UNSUPPORTED for a width outside the
+ * rule, LSV2_ERR_CUDA if a GEMM cannot be planned or launched.  Allocates nothing; capturable in
+ * a CUDA graph after one uncaptured call of the same shapes (the first call of a shape asks
+ * the library's heuristic for its algorithm on the host). */
+lsv2_status lsv2_mlp_decode(int64_t rows, int32_t n_layers, const int32_t* widths, const void* x,
+                            int32_t x_dtype, const void* weights, const float* biases, void* y,
+                            int64_t block_rows, void* workspace, size_t workspace_bytes,
+                            void* stream);
 
 /* Rate probes of the units that bind the splat's blend, for roofline denominators measured on the
  * device at hand (no counterpart in the paper).  lsv2_rate_probe launches `blocks` CTAs of 512

@@ -77,6 +77,8 @@ _SIGS = {
     "lsv2_postprocess": ([I32, I32, I32, I32, P, I32, I32, I32, F32, P, SZ, P, P, P, P, P, P, P], I32),
     "lsv2_l1_decode_backward": ([I32, I64, I32, I32, P, P, P, P, P, P, P, P], I32),
     "lsv2_splat_backward_workspace_bytes": ([I64], SZ),
+    "lsv2_mlp_decode_workspace_bytes": ([I64, I32, P, I32, I64], SZ),
+    "lsv2_mlp_decode": ([I64, I32, P, P, I32, P, P, P, I64, P, SZ, P], I32),
     "lsv2_splat_backward": ([P, I64, P, P, P, P, P, P, I32, I32, I32, P, P, P, P, P, P, SZ, P, P, P, P, P, P, P],
                             I32),
 }
@@ -254,3 +256,12 @@ def lsv2_splat_coeffs_bf16(cam, n, proj, tile_ranges, gauss_ids, levels, K, L, i
                            final_T, n_last, dev_status, stream):
     call("lsv2_splat_coeffs_bf16", C.byref(cam), n, C.byref(proj), tile_ranges, gauss_ids, levels, K, L, idx, w, ws,
          ws_bytes, coeff_bf16, final_T, n_last, dev_status, stream)
+
+
+def lsv2_mlp_decode_workspace_bytes(rows, n_layers, widths, x_dtype, block_rows=0) -> int:
+    """widths: host int32 array (ctypes array or anything accepted as a pointer)."""
+    return lib().lsv2_mlp_decode_workspace_bytes(rows, n_layers, widths, x_dtype, block_rows)
+
+
+def lsv2_mlp_decode(rows, n_layers, widths, x, x_dtype, weights, biases, y, block_rows, ws, ws_bytes, stream):
+    call("lsv2_mlp_decode", rows, n_layers, widths, x, x_dtype, weights, biases, y, block_rows, ws, ws_bytes, stream)

@@ -1,7 +1,8 @@
 """Build the sm_103a CUDA library ``_build/liblsv2.so`` in-tree with nvcc.
 
 Each ``csrc/*.cu`` is compiled to an object (in parallel), then linked into one shared
-library with the CUDA runtime linked statically.  ``build()`` only recompiles sources that
+library with the CUDA runtime linked statically and cuBLASLt (the decoder-based comparison
+path's MLP layers) dynamically.  ``build()`` only recompiles sources that
 are newer than their object.  Run ``python -m paper_2507_07136_b300.build`` to build.
 """
 from __future__ import annotations
@@ -50,7 +51,7 @@ def build(verbose: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=min(8, max(1, len(jobs)))) as ex:
         list(ex.map(run, jobs))
     if jobs or _needs(LIB, objs):
-        run([NVCC, *ARCH, "-shared", "-o", LIB, *objs])
+        run([NVCC, *ARCH, "-shared", "-o", LIB, *objs, "-lcublasLt"])
     return LIB
 
 

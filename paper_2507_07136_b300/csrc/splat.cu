@@ -403,8 +403,9 @@ cudaError_t launch_tile(const SplatArgs& a, cudaStream_t stream)
 
 bool splat_supported(int levels, int K, int L, int tw, int th)
 {
-    // the L sweep: codebooks of 32 and 128 entries at three levels, K = 4, 16 x 16 tiles
-    if (L == 32 || L == 128) return levels == 3 && K == 4 && tw == 16 && th == 16;
+    // the L sweep: codebooks of 32 and 128 entries at three levels, K = 4, 16 x 16 tiles; and an
+    // 8-column map at three levels (the low-dimensional latent of the decoder-based comparison path)
+    if (L == 8 || L == 32 || L == 128) return levels == 3 && K == 4 && tw == 16 && th == 16;
     if (L != 64) return false;
     const bool tile_ok = (tw == 16 && th == 16) || (tw == 8 && th == 8) || (tw == 32 && th == 8);
     if (!tile_ok) return false;
@@ -449,7 +450,8 @@ cudaError_t launch_pack(const PackArgs& a, cudaStream_t stream, int V)
     const int threads = 256;
     const dim3 grid((unsigned)((a.n + threads - 1) / threads), (unsigned)V);
     if (a.L != 64) {   // the L sweep: three levels, K = 4
-        if (a.levels == 3 && a.K == 4 && a.L == 32) pack_records_kernel<3, 4, 32><<<grid, threads, 0, stream>>>(a);
+        if (a.levels == 3 && a.K == 4 && a.L == 8) pack_records_kernel<3, 4, 8><<<grid, threads, 0, stream>>>(a);
+        else if (a.levels == 3 && a.K == 4 && a.L == 32) pack_records_kernel<3, 4, 32><<<grid, threads, 0, stream>>>(a);
         else if (a.levels == 3 && a.K == 4 && a.L == 128) pack_records_kernel<3, 4, 128><<<grid, threads, 0, stream>>>(a);
         else return cudaErrorInvalidValue;
         return cudaGetLastError();
@@ -491,6 +493,7 @@ cudaError_t launch_splat(int levels, int K, const SplatArgs& args, cudaStream_t 
         }
     }
     if (levels == 2 && K == 4) return launch_tile<2, 4>(a, stream);
+    if (levels == 3 && K == 4 && a.L == 8) return launch_t<3, 4, 16, 16, false, kSub16, 8>(a, stream);
     if (levels == 3 && K == 4 && a.L == 32) return launch_t<3, 4, 16, 16, false, kSub16, 32>(a, stream);
     if (levels == 3 && K == 4 && a.L == 128 && a.cam.tile_w == 16 && a.cam.tile_h == 16)
         return launch_tm<3, 4, 128>(a, stream);

@@ -79,3 +79,27 @@ def test_wait_limit_setting_round_trips(lib):
         assert L.lsv2_wait_limit_ns() == 123456789
     finally:
         L.lsv2_set_wait_limit_ns(1_000_000_000)
+
+
+def test_mlp_decode_host_checks(lib):
+    """Workspace sizing and the host-side rejections of lsv2_mlp_decode (all before any CUDA call)."""
+    w = (C.c_int32 * 8)(8, 16, 32, 64, 128, 256, 256, 512)
+    lt = 32 << 20
+    # two activation buffers of a 65,536-row block at width 256, plus the BF16 copy of an F32 input
+    assert L.lsv2_mlp_decode_workspace_bytes(1 << 22, 7, w, 0, 0) == 2 * 65536 * 256 * 2 + 65536 * 8 * 2 + lt
+    assert L.lsv2_mlp_decode_workspace_bytes(1 << 22, 7, w, 1, 0) == 2 * 65536 * 256 * 2 + lt
+    assert L.lsv2_mlp_decode_workspace_bytes(1000, 7, w, 1, 0) == 2 * 512000 + lt
+    assert L.lsv2_mlp_decode_workspace_bytes(1 << 22, 7, w, 1, 1024) == 2 * 1024 * 256 * 2 + lt
+    assert L.lsv2_mlp_decode_workspace_bytes(-1, 7, w, 0, 0) == 0
+    assert L.lsv2_mlp_decode_workspace_bytes(10, 0, w, 0, 0) == 0
+    assert L.lsv2_mlp_decode_workspace_bytes(10, 7, w, 2, 0) == 0
+    big = 1 << 30
+    ok = [10, 7, w, 256, 0, 256, 256, 256, 0, 256, big, 0]
+    assert lib.lsv2_mlp_decode(0, 7, w, 256, 0, 256, 256, 256, 0, 256, big, 0) == 0   # no rows: nothing to do
+    for i, bad in [(3, 0), (3, 260), (4, 5), (8, 100), (8, -128), (10, 1000)]:
+        args = list(ok)
+        args[i] = bad
+        assert lib.lsv2_mlp_decode(*args) == 1, (i, bad)
+    for widths in [(8, 12, 512), (4, 16, 512), (8, 16, 8192)]:
+        wb = (C.c_int32 * 3)(*widths)
+        assert lib.lsv2_mlp_decode(10, 2, wb, 256, 0, 256, 256, 256, 0, 256, big, 0) == 2, widths
