@@ -678,7 +678,7 @@ def decoder_path_section(dev, v2_render_decode_ms: float | None = None, reps: in
         return g
 
     decode_ms, fr = {}, None
-    for block_rows in (16384, 65536, 262144):
+    for block_rows in (65536, 262144, 1048576):
         fr = DecoderFrame(ds, torch.as_tensor(lat), dec, cam, block_rows=block_rows, device=dev)
         fr.render()
         fr.check()

@@ -429,17 +429,17 @@ size_t lsv2_mlp_decode_workspace_bytes(int64_t rows, int32_t n_layers, const int
  *            8 in [8, 4096] (pad a narrower input with zero columns and zero weight rows)
  *   x        [rows][w_0]  dtype x_dtype (F32: rounded to BF16 per block first; or BF16)
  *   weights  bf16, the W_l one after another, each row-major [w_l][w_{l+1}]
- *   biases   float, the b_l one after another, each [w_{l+1}]
+ *   biases   bf16, the b_l one after another, each [w_{l+1}]
  *   y        bf16 [rows][w_n]
  * Each layer is a library GEMM (cuBLASLt) with BF16 operands, FP32 accumulation and a fused
  * bias (+ ReLU) epilogue; intermediate activations are rounded to BF16.  Rows go in blocks of
- * block_rows (a multiple of 128; 0 = 65,536) so a block's activations stay in L2 between
- * layers.  All pointers 16-byte aligned.  Returns LSV2_ERR_UNSUPPORTED for a width outside the
- * rule, LSV2_ERR_CUDA if a GEMM cannot be planned or launched.  Allocates nothing; capturable in
+ * block_rows (a multiple of 128; 0 = 262,144), which bounds the intermediate buffers.  All
+ * pointers 16-byte aligned.  Returns LSV2_ERR_UNSUPPORTED for a width outside the rule,
+ * LSV2_ERR_CUDA if a GEMM cannot be planned or launched.  Allocates nothing; capturable in
  * a CUDA graph after one uncaptured call of the same shapes (the first call of a shape asks
  * the library's heuristic for its algorithm on the host). */
 lsv2_status lsv2_mlp_decode(int64_t rows, int32_t n_layers, const int32_t* widths, const void* x,
-                            int32_t x_dtype, const void* weights, const float* biases, void* y,
+                            int32_t x_dtype, const void* weights, const void* biases, void* y,
                             int64_t block_rows, void* workspace, size_t workspace_bytes,
                             void* stream);
 

@@ -285,14 +285,14 @@ def bf16_representable(x: np.ndarray) -> np.ndarray:
 def decoder_mlp(widths=DECODER_WIDTHS, seed: int = SEED + 7):
     """Random weights of the decoder MLP: a list of (W [w_in, w_out], b [w_out]) float32 pairs.
     W ~ N(0, 2 / w_in) before a ReLU and N(0, 1 / w_in) for the last layer (so activations keep
-    their scale through the stack), stored on the BF16 grid; b ~ N(0, 0.05^2) in float32."""
+    their scale through the stack), and b ~ N(0, 0.05^2), both stored on the BF16 grid."""
     rng = _rng(seed)
     layers = []
     for l in range(len(widths) - 1):
         gain = 1.0 if l == len(widths) - 2 else 2.0
         W = rng.normal(0.0, math.sqrt(gain / widths[l]), (widths[l], widths[l + 1]))
         b = rng.normal(0.0, 0.05, widths[l + 1])
-        layers.append((bf16_representable(W.astype(np.float32)), b.astype(np.float32)))
+        layers.append((bf16_representable(W.astype(np.float32)), bf16_representable(b.astype(np.float32))))
     return layers
 
 

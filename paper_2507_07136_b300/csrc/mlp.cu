@@ -3,11 +3,12 @@
 // CLIP space, the stage the paper measures as LangSplat*'s bottleneck.  Each layer is a plain
 // GEMM with a bias (+ ReLU) epilogue,
 //     H_{l+1} = act(H_l W_l + b_l),   H_l rows x w_l,  W_l w_l x w_{l+1},  act = ReLU except after the last,
-// with BF16 operands and activations and FP32 accumulation, run by cuBLASLt (a library GEMM:
-// nothing about these layers is specific to the method).  Rows are processed in blocks so the
-// two intermediate activation buffers stay small enough to live in L2 between layers; the
-// buffers, the BF16 copy of an FP32 input block and cuBLASLt's own workspace all live in the
-// caller's workspace, so a call allocates nothing and can be captured in a CUDA graph.
+// with BF16 operands, biases and activations and FP32 accumulation, run by cuBLASLt (a library GEMM:
+// nothing about these layers is specific to the method).  Rows are processed in blocks that bound
+// the two intermediate activation buffers (smaller blocks keep them in L2 but make the GEMMs too
+// small to fill the GPU: measured, 2^18 rows beats 2^14 and 2^16); the buffers, the BF16 copy of
+// an FP32 input block and cuBLASLt's own workspace all live in the caller's workspace, so a call
+// allocates nothing and can be captured in a CUDA graph.
 #include <cublasLt.h>
 #include <cuda_bf16.h>
 
@@ -20,7 +21,7 @@
 namespace lsv2 {
 namespace {
 
-constexpr int64_t kDefaultBlockRows = 1 << 16;
+constexpr int64_t kDefaultBlockRows = 1 << 18;
 constexpr size_t kLtWorkspace = 32u << 20;   // cuBLASLt's workspace (inside the caller's)
 constexpr int kMaxLayers = 16;
 
@@ -81,18 +82,17 @@ struct LayerDesc {
 #define LT_OK(x) ((x) == CUBLAS_STATUS_SUCCESS)
 
 // Y (row-major rows x n) = act(X (rows x k) W (k x n, row-major) + b).  In cuBLASLt's column-major
-// terms: Y^T (n x rows, ld n) = W^T (n x k, ld n) X^T (k x rows, ld k), bias along the n rows.
-bool describe(LayerDesc& d, int64_t rows, int k, int n, const float* b, bool relu)
+// terms: Y^T (n x rows, ld n) = W^T (n x k, ld n) X^T (k x rows, ld k), bias along the n rows.  The
+// bias has the output's type (BF16): the library takes no FP32 bias with a BF16 output.
+bool describe(LayerDesc& d, int64_t rows, int k, int n, const void* b, bool relu)
 {
     const cublasOperation_t tn = CUBLAS_OP_N;
     const cublasLtEpilogue_t epi = relu ? CUBLASLT_EPILOGUE_RELU_BIAS : CUBLASLT_EPILOGUE_BIAS;
-    const cudaDataType_t bias_t = CUDA_R_32F;
     return LT_OK(cublasLtMatmulDescCreate(&d.op, CUBLAS_COMPUTE_32F, CUDA_R_32F)) &&
            LT_OK(cublasLtMatmulDescSetAttribute(d.op, CUBLASLT_MATMUL_DESC_TRANSA, &tn, sizeof(tn))) &&
            LT_OK(cublasLtMatmulDescSetAttribute(d.op, CUBLASLT_MATMUL_DESC_TRANSB, &tn, sizeof(tn))) &&
            LT_OK(cublasLtMatmulDescSetAttribute(d.op, CUBLASLT_MATMUL_DESC_EPILOGUE, &epi, sizeof(epi))) &&
            LT_OK(cublasLtMatmulDescSetAttribute(d.op, CUBLASLT_MATMUL_DESC_BIAS_POINTER, &b, sizeof(b))) &&
-           LT_OK(cublasLtMatmulDescSetAttribute(d.op, CUBLASLT_MATMUL_DESC_BIAS_DATA_TYPE, &bias_t, sizeof(bias_t))) &&
            LT_OK(cublasLtMatrixLayoutCreate(&d.la, CUDA_R_16BF, (uint64_t)n, (uint64_t)k, (int64_t)n)) &&
            LT_OK(cublasLtMatrixLayoutCreate(&d.lb, CUDA_R_16BF, (uint64_t)k, (uint64_t)rows, (int64_t)k)) &&
            LT_OK(cublasLtMatrixLayoutCreate(&d.ly, CUDA_R_16BF, (uint64_t)n, (uint64_t)rows, (int64_t)n));
@@ -125,7 +125,7 @@ bool plan(cublasLtHandle_t h, const LayerDesc& d, int64_t rows, int k, int n, bo
     return true;
 }
 
-bool layer(cublasLtHandle_t h, int64_t rows, int k, int n, const void* X, const void* W, const float* b, void* Y,
+bool layer(cublasLtHandle_t h, int64_t rows, int k, int n, const void* X, const void* W, const void* b, void* Y,
            bool relu, void* lt_ws, cudaStream_t stream)
 {
     LayerDesc d;
@@ -161,7 +161,7 @@ extern "C" size_t lsv2_mlp_decode_workspace_bytes(int64_t rows, int32_t n_layers
 }
 
 extern "C" lsv2_status lsv2_mlp_decode(int64_t rows, int32_t n_layers, const int32_t* widths, const void* x,
-                                       int32_t x_dtype, const void* weights, const float* biases, void* y,
+                                       int32_t x_dtype, const void* weights, const void* biases, void* y,
                                        int64_t block_rows, void* workspace, size_t workspace_bytes, void* stream)
 {
     if (rows < 0 || n_layers < 1 || n_layers > kMaxLayers || !widths || !x || !weights || !biases || !y ||
@@ -206,7 +206,8 @@ extern "C" lsv2_status lsv2_mlp_decode(int64_t rows, int32_t n_layers, const int
             const bool last = l == n_layers - 1;
             void* out = last ? static_cast<void*>(static_cast<__nv_bfloat16*>(y) + (size_t)r0 * n) : buf[l & 1];
             const void* W = static_cast<const __nv_bfloat16*>(weights) + woff;
-            if (!layer(h, nr, k, n, in, W, biases + boff, out, !last, lt_ws, s)) return LSV2_ERR_CUDA;
+            const void* b = static_cast<const __nv_bfloat16*>(biases) + boff;
+            if (!layer(h, nr, k, n, in, W, b, out, !last, lt_ws, s)) return LSV2_ERR_CUDA;
             woff += (size_t)k * n;
             boff += (size_t)n;
             in = out;

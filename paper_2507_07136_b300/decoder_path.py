@@ -43,7 +43,7 @@ def latent_pairs(latent: torch.Tensor) -> tuple[torch.Tensor, torch.Tensor]:
 
 class Decoder:
     """The MLP's weights packed for lsv2_mlp_decode: BF16 weight matrices one after another
-    (row-major [w_in][w_out]), FP32 biases, the widths in host memory.  The first layer's input
+    (row-major [w_in][w_out]), BF16 biases, the widths in host memory.  The first layer's input
     is padded to LATENT_CHANNELS with zero weight rows."""
 
     def __init__(self, layers, device="cuda"):
@@ -62,7 +62,7 @@ class Decoder:
         self.widths = (C.c_int32 * len(widths))(*widths)
         self.out_width = widths[-1]
         self.weights = torch.cat(mats).to(device=device, dtype=torch.bfloat16).contiguous()
-        self.biases = torch.cat(biases).to(device=device).contiguous()
+        self.biases = torch.cat(biases).to(device=device, dtype=torch.bfloat16).contiguous()
 
     def flops_per_row(self) -> int:
         w = list(self.widths)
