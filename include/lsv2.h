@@ -227,7 +227,9 @@ lsv2_status lsv2_decode(int32_t levels, int64_t P, int32_t L, int32_t D, const v
                         lsv2_dtype coeff_dtype, const void* codebook, lsv2_dtype codebook_dtype,
                         void* feat, lsv2_dtype out_dtype, int32_t* dev_status, void* stream);
 
-/* Workspace for lsv2_query: per level the Gram matrix S S^T and the projected texts S t. */
+/* Workspace for lsv2_query.  After a call it holds, from its start, float B^T[levels][64 + Q (1 +
+ * n_neg)][64]: per level 64 rows of G = S S^T (compute F32) or of C^T (compute BF16: G = C C^T, C
+ * lower triangular), then the rows S t of the texts in query-major order; then the text norms. */
 size_t lsv2_query_workspace_bytes(int32_t levels, int32_t L, int32_t Q, int32_t n_neg);
 
 /* Relevancy (Sec. 3.2) through the linearity of Eq. 7: with u_t = S t and G = S S^T,
@@ -239,15 +241,35 @@ size_t lsv2_query_workspace_bytes(int32_t levels, int32_t L, int32_t Q, int32_t 
  *   text     float[Q][1 + n_neg][D]  (positive first)
  *   rel      [Q][levels][P]  dtype rel_dtype (F32 or BF16)
  * compute_dtype F32: FP32 FMA on CUDA cores (rel_dtype F32).  BF16: tcgen05 tensor cores with
- * W and [G | u] rounded to BF16 and FP32 accumulation.  S S^T and S t are formed per call in
- * twice-FP32 precision (error-free products and sums) and rounded to FP32.  L = 64, D % 4 == 0, n_neg >= 1; BF16: 64 + (1 + n_neg) * 8 * ceil(Q / 8)
- * <= 512 (Q <= 88 at n_neg = 4); F32: Q (1 + n_neg) <= 512.  All arrays 16-byte aligned.
+ * W and [C | u] rounded to BF16 and FP32 accumulation, |F|^2 = |W C|^2 where G = C C^T (Cholesky in
+ * FP32; a pivot below 1e-5 of its diagonal entry, a codebook row within about 3e-3 of its length
+ * of the span of the rows before it, gives a zero column).  S S^T and S t are formed per call in
+ * twice-FP32 precision (error-free products and sums) and rounded to FP32.  L = 64, D % 4 == 0,
+ * n_neg >= 1; BF16: 64 + (1 + n_neg) * 8 * ceil(Q / 8) <= 512 (Q <= 88 at n_neg = 4);
+ * F32: Q (1 + n_neg) <= 512.  All arrays 16-byte aligned.
  * A bounded device wait that expires sets LSV2_ERR_TIMEOUT. */
 lsv2_status lsv2_query(int32_t levels, int64_t P, int32_t L, int32_t D, const void* coeff,
                        lsv2_dtype coeff_dtype, const float* codebook, int32_t Q, int32_t n_neg,
                        const float* text, float tau, void* workspace, size_t workspace_bytes,
                        void* rel, lsv2_dtype rel_dtype, lsv2_dtype compute_dtype,
                        int32_t* dev_status, void* stream);
+
+/* The two halves of lsv2_query, for callers that prepare the query operands ahead of the map
+ * (e.g. on a second stream while the frame renders): lsv2_query_prepare forms, in the workspace,
+ * B^T and the text norms from the codebook and the texts (and, for compute_dtype BF16, the factor
+ * C of S S^T); lsv2_query_prepared then computes the relevancy of a coefficient map from that
+ * workspace.  lsv2_query_prepare + lsv2_query_prepared on one stream is lsv2_query, bit for bit.
+ * The workspace must stay untouched in between, and the prepared call must use the same levels,
+ * Q, n_neg and compute_dtype.  Arguments as for lsv2_query. */
+lsv2_status lsv2_query_prepare(int32_t levels, int32_t L, int32_t D, const float* codebook,
+                               int32_t Q, int32_t n_neg, const float* text,
+                               lsv2_dtype compute_dtype, void* workspace, size_t workspace_bytes,
+                               void* stream);
+lsv2_status lsv2_query_prepared(int32_t levels, int64_t P, int32_t L, const void* coeff,
+                                lsv2_dtype coeff_dtype, int32_t Q, int32_t n_neg, float tau,
+                                const void* workspace, size_t workspace_bytes, void* rel,
+                                lsv2_dtype rel_dtype, lsv2_dtype compute_dtype,
+                                int32_t* dev_status, void* stream);
 
 /* Workspace for lsv2_query_views (projections, lists, records and coefficient maps of all
  * views, the query matrices and a work-queue counter). */
@@ -433,7 +455,7 @@ size_t lsv2_mlp_decode_workspace_bytes(int64_t rows, int32_t n_layers, const int
  *   y        bf16 [rows][w_n]
  * Each layer is a library GEMM (cuBLASLt) with BF16 operands, FP32 accumulation and a fused
  * bias (+ ReLU) epilogue; intermediate activations are rounded to BF16.  Rows go in blocks of
- * block_rows (a multiple of 128; 0 = 262,144), which bounds the intermediate buffers.  All
+ * block_rows (a multiple of 128; 0 = 1,048,576), which bounds the intermediate buffers.  All
  * pointers 16-byte aligned.  Returns LSV2_ERR_UNSUPPORTED for a width outside the rule,
  * LSV2_ERR_CUDA if a GEMM cannot be planned or launched.  Allocates nothing; capturable in
  * a CUDA graph after one uncaptured call of the same shapes (the first call of a shape asks

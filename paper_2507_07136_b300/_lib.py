@@ -65,6 +65,8 @@ _SIGS = {
     "lsv2_decode": ([I32, I64, I32, I32, P, I32, P, I32, P, I32, P, P], I32),
     "lsv2_query_workspace_bytes": ([I32, I32, I32, I32], SZ),
     "lsv2_query": ([I32, I64, I32, I32, P, I32, P, I32, I32, P, F32, P, SZ, P, I32, I32, P, P], I32),
+    "lsv2_query_prepare": ([I32, I32, I32, P, I32, I32, P, I32, P, SZ, P], I32),
+    "lsv2_query_prepared": ([I32, I64, I32, P, I32, I32, I32, F32, P, SZ, P, I32, I32, P, P], I32),
     "lsv2_query_views_workspace_bytes": ([I32, P, I64, I32, I32, I64, I32, I32], SZ),
     "lsv2_query_views": ([I32, P, I64, P, P, P, P, I32, I32, I32, P, P, P, I32, I32, I32, P, F32, I64, I32, P, SZ, P,
                           I32, P, P, P], I32),
@@ -178,6 +180,16 @@ def lsv2_query(levels, P_, L, D, coeff, coeff_dtype, codebook, Q, n_neg, text, t
                compute_dtype, dev_status, stream):
     call("lsv2_query", levels, P_, L, D, coeff, coeff_dtype, codebook, Q, n_neg, text, tau, ws, ws_bytes, rel,
          rel_dtype, compute_dtype, dev_status, stream)
+
+
+def lsv2_query_prepare(levels, L, D, codebook, Q, n_neg, text, compute_dtype, ws, ws_bytes, stream):
+    call("lsv2_query_prepare", levels, L, D, codebook, Q, n_neg, text, compute_dtype, ws, ws_bytes, stream)
+
+
+def lsv2_query_prepared(levels, P_, L, coeff, coeff_dtype, Q, n_neg, tau, ws, ws_bytes, rel, rel_dtype, compute_dtype,
+                        dev_status, stream):
+    call("lsv2_query_prepared", levels, P_, L, coeff, coeff_dtype, Q, n_neg, tau, ws, ws_bytes, rel, rel_dtype,
+         compute_dtype, dev_status, stream)
 
 
 def cameras(cams) -> C.Array:

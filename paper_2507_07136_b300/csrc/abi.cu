@@ -237,11 +237,56 @@ size_t lsv2_query_workspace_bytes(int32_t levels, int32_t L, int32_t Q, int32_t 
     return query_workspace_bytes(levels, Q * (1 + n_neg));
 }
 
+lsv2_status lsv2_query_prepare(int32_t levels, int32_t L, int32_t D, const float* codebook, int32_t Q, int32_t n_neg,
+                               const float* text, lsv2_dtype compute_dtype, void* workspace, size_t workspace_bytes,
+                               void* stream)
+{
+    if (levels < 1 || !codebook || !text || Q < 1 || n_neg < 1 || D <= 0) return LSV2_ERR_INVALID_ARGUMENT;
+    if (L != 64 || Q * (1 + n_neg) > 512 || D % 4 != 0 || D > 12288) return LSV2_ERR_UNSUPPORTED;
+    if (!aligned16(codebook) || !aligned16(text)) return LSV2_ERR_INVALID_ARGUMENT;
+    const int nt = Q * (1 + n_neg);
+    if (!workspace || !aligned16(workspace) || workspace_bytes < query_workspace_bytes(levels, nt))
+        return LSV2_ERR_INVALID_ARGUMENT;
+    if (compute_dtype != LSV2_F32 && compute_dtype != LSV2_BF16) return LSV2_ERR_INVALID_ARGUMENT;
+    if (compute_dtype == LSV2_BF16 && !query_tc_supported(Q, n_neg)) return LSV2_ERR_UNSUPPORTED;
+    cudaError_t e = launch_query_prepare(levels, D, nt, codebook, text, workspace, S(stream));
+    if (e != cudaSuccess) return LSV2_ERR_CUDA;
+    if (compute_dtype == LSV2_BF16) e = launch_query_factor(levels, nt, workspace, S(stream));
+    return cuda_status(e);
+}
+
+lsv2_status lsv2_query_prepared(int32_t levels, int64_t P, int32_t L, const void* coeff, lsv2_dtype coeff_dtype,
+                                int32_t Q, int32_t n_neg, float tau, const void* workspace, size_t workspace_bytes,
+                                void* rel, lsv2_dtype rel_dtype, lsv2_dtype compute_dtype, int32_t* dev_status,
+                                void* stream)
+{
+    if (levels < 1 || P < 0 || !coeff || !rel || Q < 1 || n_neg < 1) return LSV2_ERR_INVALID_ARGUMENT;
+    if (L != 64 || Q * (1 + n_neg) > 512) return LSV2_ERR_UNSUPPORTED;
+    const int nt = Q * (1 + n_neg);
+    if (!workspace || !aligned16(workspace) || workspace_bytes < query_workspace_bytes(levels, nt))
+        return LSV2_ERR_INVALID_ARGUMENT;
+    if (!aligned16(coeff)) return LSV2_ERR_INVALID_ARGUMENT;
+    if (coeff_dtype != LSV2_F32 && !(coeff_dtype == LSV2_BF16 && compute_dtype == LSV2_BF16))
+        return LSV2_ERR_UNSUPPORTED;
+    if (rel_dtype != LSV2_F32 && rel_dtype != LSV2_BF16) return LSV2_ERR_INVALID_ARGUMENT;
+    if (compute_dtype == LSV2_F32 && rel_dtype == LSV2_F32)
+        return cuda_status(launch_query_f32(levels, P, Q, n_neg, tau, static_cast<const float*>(coeff), workspace,
+                                            static_cast<float*>(rel), S(stream)));
+    if (compute_dtype == LSV2_BF16) {
+        if (!query_tc_supported(Q, n_neg)) return LSV2_ERR_UNSUPPORTED;
+        return cuda_status(launch_query_tc(levels, P, Q, n_neg, tau, coeff, coeff_dtype == LSV2_BF16,
+                                           query_ws_bt(workspace), query_ws_tnorm(workspace, levels, nt), rel,
+                                           rel_dtype == LSV2_BF16, sm_count(), dev_status, S(stream)));
+    }
+    return LSV2_ERR_UNSUPPORTED;
+}
+
 lsv2_status lsv2_query(int32_t levels, int64_t P, int32_t L, int32_t D, const void* coeff, lsv2_dtype coeff_dtype,
                        const float* codebook, int32_t Q, int32_t n_neg, const float* text, float tau, void* workspace,
                        size_t workspace_bytes, void* rel, lsv2_dtype rel_dtype, lsv2_dtype compute_dtype,
                        int32_t* dev_status, void* stream)
 {
+    // every host check of both halves before anything is launched
     if (levels < 1 || P < 0 || !coeff || !codebook || !text || !rel || Q < 1 || n_neg < 1 || D <= 0)
         return LSV2_ERR_INVALID_ARGUMENT;
     if (L != 64 || Q * (1 + n_neg) > 512 || D % 4 != 0 || D > 12288) return LSV2_ERR_UNSUPPORTED;
@@ -253,18 +298,14 @@ lsv2_status lsv2_query(int32_t levels, int64_t P, int32_t L, int32_t D, const vo
     if (coeff_dtype != LSV2_F32 && !(coeff_dtype == LSV2_BF16 && compute_dtype == LSV2_BF16))
         return LSV2_ERR_UNSUPPORTED;
     if (rel_dtype != LSV2_F32 && rel_dtype != LSV2_BF16) return LSV2_ERR_INVALID_ARGUMENT;
-    cudaError_t e = launch_query_prepare(levels, D, nt, codebook, text, workspace, S(stream));
-    if (e != cudaSuccess) return LSV2_ERR_CUDA;
-    if (compute_dtype == LSV2_F32 && rel_dtype == LSV2_F32)
-        return cuda_status(launch_query_f32(levels, P, Q, n_neg, tau, static_cast<const float*>(coeff), workspace,
-                                            static_cast<float*>(rel), S(stream)));
-    if (compute_dtype == LSV2_BF16) {
-        if (!query_tc_supported(Q, n_neg)) return LSV2_ERR_UNSUPPORTED;
-        return cuda_status(launch_query_tc(levels, P, Q, n_neg, tau, coeff, coeff_dtype == LSV2_BF16,
-                                           query_ws_bt(workspace), query_ws_tnorm(workspace, levels, nt), rel,
-                                           rel_dtype == LSV2_BF16, sm_count(), dev_status, S(stream)));
-    }
-    return LSV2_ERR_UNSUPPORTED;
+    if (compute_dtype != LSV2_F32 && compute_dtype != LSV2_BF16) return LSV2_ERR_UNSUPPORTED;
+    if (compute_dtype == LSV2_F32 && rel_dtype != LSV2_F32) return LSV2_ERR_UNSUPPORTED;
+    if (compute_dtype == LSV2_BF16 && !query_tc_supported(Q, n_neg)) return LSV2_ERR_UNSUPPORTED;
+    const lsv2_status st = lsv2_query_prepare(levels, L, D, codebook, Q, n_neg, text, compute_dtype, workspace,
+                                              workspace_bytes, stream);
+    if (st != LSV2_OK) return st;
+    return lsv2_query_prepared(levels, P, L, coeff, coeff_dtype, Q, n_neg, tau, workspace, workspace_bytes, rel,
+                               rel_dtype, compute_dtype, dev_status, stream);
 }
 
 lsv2_status lsv2_l1_decode_backward(int32_t levels, int64_t P, int32_t L, int32_t D, const float* coeff,

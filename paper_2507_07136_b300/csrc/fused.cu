@@ -13,13 +13,14 @@
 //     the block's pixels in row-major order) into that memory.
 //  2. The producer warp streams the codebook S_lev^T in 8 KB chunks of 64 rows (the pre-swizzled
 //     BF16 copy) through a 2-slot ring with bulk async copies, and each level's query matrix
-//     [S S^T | S t / |t| ...] (text-major rows, as in query_tc.cu); its lane 0 issues the tcgen05.mma:
-//     per level Y = W [S S^T | S t / |t|] (M = 128, N = npadq <= 128) into TMEM columns [128, 256), then
+//     [C | S t / |t| ...] (S S^T = C C^T; text-major rows, as in query_tc.cu); its lane 0 issues the
+//     tcgen05.mma: per level Y = W [C | S t / |t|] (M = 128, N = npadq <= 128) into TMEM columns
+//     [128, 256), then
 //     F chunks of 64 features (M = 128, N = 64, K = 64) into two TMEM buffers [0, 64) and
 //     [64, 128) that alternate, each committed to an mbarrier.
 //  3. The consumer warps run the epilogues in the same order (warp q reads TMEM lanes 32q ..,
-//     i.e. image rows 2q and 2q + 1 of the block): relevancy as in query_tc.cu (|F|^2 = W . (S
-//     S^T W), sigmoid of the scaled cosine gap), and F chunks converted to BF16 into two
+//     i.e. image rows 2q and 2q + 1 of the block): relevancy as in query_tc.cu (|F|^2 = |W C|^2,
+//     sigmoid of the scaled cosine gap), and F chunks converted to BF16 into two
 //     16-pixel x 128-byte staging boxes per warp, each sent by one TMA tensor store through a
 //     {D, W, H, levels} map (columns past the image edge are clipped by the map).
 // The operands and the MMA sequence (K = 64 in four steps of 16) are those of decode_tc.cu and
@@ -68,7 +69,7 @@ struct FusedArgs {
     int do_dec;                  // write F (through the tensor map)
     int Q, n_neg, Qp, npadq;     // Q = 0: no query
     float tau;
-    const uint8_t* Bq;           // [levels][npadq rows x 128 B] swizzled BF16 [S S^T | S t / |t|] (text-major)
+    const uint8_t* Bq;           // [levels][npadq rows x 128 B] swizzled BF16 [C | S t / |t|] (text-major)
     void* rel;                   // [Q][levels][P]
     int rel_bf16;
     int32_t* status;
@@ -279,14 +280,14 @@ __global__ void __launch_bounds__(FC::kThreads, 2) fused_kernel(const __grid_con
             if (do_query) {
                 if (warp_wait(&fb->qfull, (uint32_t)(l & 1), nullptr, 0, abort_flag, a.wait_ns) != kWaitDone) { ok = false; break; }
                 tc::fence_after();
-                // |F|^2 = W . (S S^T W): columns 0..63 of Y, W from this level's A tile
+                // |F|^2 = |W C|^2 (S S^T = C C^T): columns 0..63 of Y
                 float n2;
                 {
                     uint32_t ya[32], yb[32];
                     tc::tmem_ld32(lrow + 128u, ya);
                     tc::tmem_ld32(lrow + 128u + 32u, yb);
                     tc::tmem_wait_ld();
-                    n2 = gram_norm2(smem + kAOff + l * kATile, row, ya, yb);
+                    n2 = chol_norm2(ya, yb);
                 }
                 const float nf = sqrtf(fmaxf(n2, 0.0f));
                 const float kneg = nf < 1e-12f ? 0.0f : -a.tau / nf;
@@ -387,7 +388,7 @@ __global__ void __launch_bounds__(FC::kThreads, 2) fused_kernel(const __grid_con
 }
 
 // Operands of the fused kernel: the codebook S^T of every level as swizzled BF16 chunks of 64
-// rows, and (with queries) the text-major [S S^T | S t / |t|] rows.
+// rows, and (with queries) the text-major [C | S t / |t|] rows (S S^T = C C^T).
 __global__ void fused_prep_kernel(int levels, int D, const float* S, int Q, int n_neg, int Qp, int npadq,
                                   const float* Bt, const float* tnorm, uint8_t* Bdec, uint8_t* Bq)
 {
@@ -470,6 +471,8 @@ cudaError_t launch_fused(const lsv2_camera& cam, int64_t n, const lsv2_proj& pro
     const int nt = Q * (1 + n_neg);
     if (Q > 0) {
         e = launch_query_prepare(kLev, D, nt, codebook, text, base + Lo.qws, stream);
+        if (e != cudaSuccess) return e;
+        e = launch_query_factor(kLev, nt, base + Lo.qws, stream);
         if (e != cudaSuccess) return e;
     }
     const int Qp = pad8(Q), npadq = npadq_of(Q, n_neg);

@@ -5,7 +5,8 @@
 // and the relevancy never needs the D-dim feature map.  Per level a small prepare kernel
 // forms, accumulated in twice-FP32 precision and rounded to float, the columns of
 //     B = [ S S^T | S t_0 | S t_1 | ... ]            (64 x (64 + #texts))
-// and the text norms; the main kernel gives every (pixel, level) one thread that holds W in
+// and the text norms (for the tensor-core relevancy, query_factor_kernel then replaces the Gram
+// rows by the rows of C^T, S S^T = C C^T); the FP32 kernel gives every (pixel, level) one thread that holds W in
 // registers, forms y = W^T B column by column (B^T in shared memory, read as warp-wide
 // broadcasts), |F|^2 = sum_j W_j y_j, and writes
 //     rel = min_i softmax(tau [cos_pos, cos_neg_i])_0 = sigmoid(tau (cos_pos - max_i cos_neg_i)).
@@ -59,6 +60,100 @@ __global__ void __launch_bounds__(256) query_prepare_kernel(int D, int nt, const
             for (int w = 0; w < 8; ++w) sum += red[w];
             tnorm[j - kL] = (float)sqrt(sum);
         }
+    }
+}
+
+// S S^T = C C^T with C lower triangular (Cholesky in FP32), one CTA of 256 threads per level.  In
+// place: the 64 Gram rows of B^T (row j = G[j][0..63]) become the rows of C^T (row j holds C[k][j]
+// at k, zero for k < j), the first 64 columns of B for the tensor-core relevancy, which then forms
+// |F|^2 = W^T G W as |W C|^2, a sum of squares of its MMA's output.  Only the backward error
+// matters for that quadratic form, and FP32 Cholesky's is far below the BF16 rounding of the
+// operands.  A pivot at or below kPivotFloor times its diagonal entry of G (codebook row j within
+// about 3e-3 of its length of the span of the rows before it, as for a repeated or zero row) gives
+// a zero column; the factor then reproduces G to within about 3e-3 of sqrt(G_ii G_jj).
+// Blocked by 8 columns, right-looking, in shared memory: per block one thread factors the 8 x 8
+// diagonal block in registers, one thread per row below solves that row's 8 entries (forward
+// substitution), and all threads subtract the block's outer products from the trailing lower
+// triangle: three barriers per block, 24 in all.
+constexpr float kPivotFloor = 1e-5f;
+constexpr int kFb = 8;   // factor block
+
+__global__ void __launch_bounds__(256) query_factor_kernel(int ncol, float* __restrict__ Bt)
+{
+    __shared__ float A[kL][kL + 1];   // lower triangle: G, updated in place into C
+    __shared__ float gd[kL];          // diagonal of G (for the pivot floor)
+    __shared__ float rinv[kL];        // 1 / C[j][j] (0 for a dropped pivot)
+    const int t = threadIdx.x;
+    float* G = Bt + (size_t)blockIdx.x * ncol * kL;
+    for (int e = t; e < kL * kL; e += 256) A[e >> 6][e & 63] = G[e];
+    __syncthreads();
+    if (t < kL) gd[t] = A[t][t];
+    __syncthreads();
+#pragma unroll 1
+    for (int j0 = 0; j0 < kL; j0 += kFb) {
+        if (t == 0) {
+            float a[kFb][kFb];
+#pragma unroll
+            for (int r = 0; r < kFb; ++r)
+#pragma unroll
+                for (int c = 0; c <= r; ++c) a[r][c] = A[j0 + r][j0 + c];
+#pragma unroll
+            for (int c = 0; c < kFb; ++c) {
+                float s = a[c][c];
+#pragma unroll
+                for (int k = 0; k < c; ++k) s = fmaf(-a[c][k], a[c][k], s);
+                // the pivot and its reciprocal from one reciprocal square root (a few ulp: C
+                // feeds BF16 operands)
+                const float ri = s > kPivotFloor * gd[j0 + c] ? rsqrtf(s) : 0.0f;
+                const float d = s * ri;
+                a[c][c] = d;
+                rinv[j0 + c] = ri;
+#pragma unroll
+                for (int r = c + 1; r < kFb; ++r) {
+                    float v = a[r][c];
+#pragma unroll
+                    for (int k = 0; k < c; ++k) v = fmaf(-a[r][k], a[c][k], v);
+                    a[r][c] = v * ri;
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < kFb; ++r)
+#pragma unroll
+                for (int c = 0; c <= r; ++c) A[j0 + r][j0 + c] = a[r][c];
+        }
+        __syncthreads();
+        // rows below the block: x L_bb^T = A[i][j0 .. j0 + 7]
+        const int i = j0 + kFb + t;
+        if (i < kL) {
+            float x[kFb];
+#pragma unroll
+            for (int c = 0; c < kFb; ++c) {
+                float v = A[i][j0 + c];
+#pragma unroll
+                for (int k = 0; k < c; ++k) v = fmaf(-x[k], A[j0 + c][j0 + k], v);
+                x[c] = v * rinv[j0 + c];
+            }
+#pragma unroll
+            for (int c = 0; c < kFb; ++c) A[i][j0 + c] = x[c];
+        }
+        __syncthreads();
+        // trailing lower triangle: A[r][c] -= sum_k C[r][j0 + k] C[c][j0 + k], j0 + 8 <= c <= r
+        const int m = kL - j0 - kFb;
+        for (int e = t; e < m * m; e += 256) {
+            const int r = j0 + kFb + e / m, c = j0 + kFb + e % m;
+            if (c <= r) {
+                float v = A[r][c];
+#pragma unroll
+                for (int k = 0; k < kFb; ++k) v = fmaf(-A[r][j0 + k], A[c][j0 + k], v);
+                A[r][c] = v;
+            }
+        }
+        __syncthreads();
+    }
+    // every read of G is done: overwrite its rows with those of C^T (C's upper triangle is zero)
+    for (int e = t; e < kL * kL; e += 256) {
+        const int j = e >> 6, k = e & 63;
+        G[e] = k >= j ? A[k][j] : 0.0f;
     }
 }
 
@@ -150,6 +245,12 @@ cudaError_t launch_query_prepare(int levels, int D, int nt, const float* S, cons
     cudaError_t e = cudaFuncSetAttribute(query_prepare_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, D * 4);
     if (e != cudaSuccess) return e;
     query_prepare_kernel<<<grid, 256, (size_t)D * 4, stream>>>(D, nt, S, text, Bt, tnorm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_query_factor(int levels, int nt, void* ws, cudaStream_t stream)
+{
+    query_factor_kernel<<<levels, 256, 0, stream>>>(kL + nt, static_cast<float*>(ws));
     return cudaGetLastError();
 }
 

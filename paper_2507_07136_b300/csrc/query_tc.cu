@@ -1,11 +1,12 @@
 // query_tc.cu -- relevancy (Sec. 3.2) through the linearity of Eq. 7 on the tensor cores.
 //
-// Per level, Y = W B with B = [S S^T | S t ...] (64 x N) is one (128 x 64)(64 x N) tcgen05
-// product per 128-pixel tile (BF16 operands, FP32 accumulation in TMEM).  The text columns are
-// staged text-major: column 64 + t Qp + q holds text t (0 = positive, 1.. = negatives) of query
-// q, Qp = Q rounded up to 8, so a thread reads 8 queries' positives and each negative with one
-// 8-column TMEM load apiece.  The epilogue thread that owns a pixel (one TMEM lane) forms
-//     |F|^2 = sum_j W_j Y_j (j < 64),
+// Per level, Y = W B with B = [C | S t ...] (64 x N), S S^T = C C^T (C lower triangular, factored
+// once per call), is one (128 x 64)(64 x N) tcgen05 product per 128-pixel tile (BF16 operands, FP32
+// accumulation in TMEM).  The text columns are staged text-major: column 64 + t Qp + q holds text
+// t (0 = positive, 1.. = negatives) of query q, Qp = Q rounded up to 8, so a thread reads 8
+// queries' positives and each negative with one 8-column TMEM load apiece.  The epilogue thread
+// that owns a pixel (one TMEM lane) forms
+//     |F|^2 = W^T C C^T W = sum_j Y_j^2 (j < 64),
 //     rel_q = sigmoid(tau (cos_pos - max_i cos_neg_i)),  cos_t = Y_t / (|F| |t|) (0 if |F| < 1e-12)
 // as sigmoid(tau / |F| (Y_pos / |t_pos| - max_i Y_neg_i / |t_neg_i|)) (|F| > 0 commutes with the
 // max), and writes rel[q][lev][p] (coalesced over the warp's 32 consecutive pixels).  F is never
@@ -145,7 +146,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) query_tc_kernel(QueryTcArgs a)
         tc::mbar_init(tc::smem_u32(bar), 1);
         for (int s = 0; s < kStages; ++s) tc::mbar_init(tc::smem_u32(full + s), 1);
     }
-    // B^T rows (N x 64 K-major, swizzled): the 64 rows of S S^T, then the text rows S t / |t|
+    // B^T rows (N x 64 K-major, swizzled): the 64 rows of C^T (S S^T = C C^T), then the text rows S t / |t|
     // (the text norm folded in before the BF16 rounding, as in query_pipe_kernel) permuted from
     // query-major (64 + q per + t) to text-major (64 + t Qp + q); zero padding rows
     const float* Bl = a.Bt + (size_t)lev * (64 + a.Q * per) * kK;
@@ -220,14 +221,14 @@ __global__ void __launch_bounds__(NT, 512 / NT) query_tc_kernel(QueryTcArgs a)
         phase ^= 1u;
         tc::fence_after();
         const int64_t p = p0 + row;
-        // |F|^2 = W . (G W): columns 0..63 of Y, W from the staged BF16 tile
+        // |F|^2 = |W C|^2: columns 0..63 of Y
         float n2;
         {
             uint32_t y0[32], y1[32];
             tc::tmem_ld32(trow, y0);
             tc::tmem_ld32(trow + 32u, y1);
             tc::tmem_wait_ld();
-            n2 = gram_norm2(sA, row, y0, y1);
+            n2 = chol_norm2(y0, y1);
         }
         const float nf = sqrtf(fmaxf(n2, 0.0f));
         const float kneg = nf < 1e-12f ? 0.0f : -a.tau / nf;   // exp(-tau (cos_p - max cos_n)) = exp(kneg d)
@@ -308,9 +309,16 @@ constexpr int kPStages = 8;
 // epilogue warpgroups (= TMEM accumulators) for accumulators of `bufcols` columns
 __host__ __device__ constexpr int pipe_groups(uint32_t bufcols) { return bufcols <= 128 ? 3 : 2; }
 
+// per accumulator two warpgroups (splitting |F|^2 and the query chunks) when there are at least
+// two 8-query chunks and two accumulators, else one
+__host__ __device__ constexpr int pipe_split(int ng, int nch) { return ng == 2 && nch >= 2 ? 2 : 1; }
+
 __host__ __device__ constexpr size_t pipe_smem_bytes(int npad, int ntp)
 {
-    return 1024 + (size_t)kPStages * kM * 128 + (size_t)npad * 128 + (((size_t)ntp * 4 + 15) & ~size_t(15)) + 256;
+    // + the split epilogue's exchange: |F|^2 halves [accumulator][parity][half][row] and go-on
+    // flags [accumulator][parity][warp]
+    return 1024 + (size_t)kPStages * kM * 128 + (size_t)npad * 128 + (((size_t)ntp * 4 + 15) & ~size_t(15)) + 256 +
+           2 * 2 * 2 * kM * 4 + 2 * 2 * 8 * 4;
 }
 
 // Bounded wait on a barrier phase: false once the CTA's abort flag is up, or when the phase is
@@ -330,11 +338,19 @@ __device__ __forceinline__ bool pipe_wait(uint32_t bar, uint32_t parity, volatil
     }
 }
 
-// NB: epilogue warpgroups = TMEM accumulators (a template parameter, so that the per-tile ring
-// and phase arithmetic divides by constants).
+// Named barrier of the 256 threads of one accumulator's two epilogue warpgroups.
+__device__ __forceinline__ void pair_sync(int id) { asm volatile("bar.sync %0, 256;" ::"r"(id) : "memory"); }
 
-template <int NB>
-__global__ void __launch_bounds__(64 + 128 * NB, 1) query_pipe_kernel(const __grid_constant__ CUtensorMap tmW, QueryTcArgs a)
+// NB: TMEM accumulators; WPA: epilogue warpgroups per accumulator (template parameters, so that
+// the per-tile ring and phase arithmetic divides by constants).  With WPA = 2 the two warpgroups
+// of an accumulator each sum the squares of 32 of its 64 factor columns, exchange the halves
+// through shared memory (a named barrier per tile) and take alternate 8-query chunks.  Both take
+// the same decision to go on or stop at every tile (from the flags both published before the
+// barrier), so neither can be left waiting at the barrier.
+
+template <int NB, int WPA>
+__global__ void __launch_bounds__(64 + 128 * NB * WPA, 1)
+    query_pipe_kernel(const __grid_constant__ CUtensorMap tmW, QueryTcArgs a)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -345,11 +361,13 @@ __global__ void __launch_bounds__(64 + 128 * NB, 1) query_pipe_kernel(const __gr
     const int ntp = per * a.Qp;
     uint64_t* bar = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(sTn) + (((size_t)ntp * 4 + 15) & ~size_t(15)));
     uint64_t* w_full = bar;                  // [kPStages] W tile landed (transaction bytes)
-    uint64_t* w_empty = bar + kPStages;      // [kPStages] the epilogue has read the tile's rows (4 warps)
+    uint64_t* w_empty = bar + kPStages;      // [kPStages] the MMA that read the tile has completed
     uint64_t* m_full = bar + 2 * kPStages;   // [4] accumulator b holds its tile (MMA commit)
-    uint64_t* t_empty = m_full + 4;          // [4] accumulator b has been read (4 warps)
+    uint64_t* t_empty = m_full + 4;          // [4] accumulator b has been read (4 WPA warps)
     volatile int* abort = reinterpret_cast<volatile int*>(t_empty + 4);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(t_empty + 5);
+    float* xpart = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(bar) + 256);   // [2][2][2][kM]
+    volatile int* xok = reinterpret_cast<volatile int*>(xpart + 2 * 2 * 2 * kM);      // [2][2][8]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int lev = blockIdx.y;
     const uint32_t bufcols = tmem_cols(a.npad);
@@ -368,16 +386,16 @@ __global__ void __launch_bounds__(64 + 128 * NB, 1) query_pipe_kernel(const __gr
     if (tid == 0) {
         for (int s = 0; s < kPStages; ++s) {
             tc::mbar_init(tc::smem_u32(w_full + s), 1);
-            tc::mbar_init(tc::smem_u32(w_empty + s), 4);
+            tc::mbar_init(tc::smem_u32(w_empty + s), 1);
         }
         for (int b = 0; b < 4; ++b) {
             tc::mbar_init(tc::smem_u32(m_full + b), 1);
-            tc::mbar_init(tc::smem_u32(t_empty + b), 4);
+            tc::mbar_init(tc::smem_u32(t_empty + b), 4 * WPA);
         }
         *abort = 0;
     }
-    // B^T rows: S S^T, then the text rows S t / |t| text-major (the cosine's text norm folded in
-    // before the BF16 rounding, so the products are <F, t> / |t|), zero padding
+    // B^T rows: C^T (S S^T = C C^T), then the text rows S t / |t| text-major (the cosine's text
+    // norm folded in before the BF16 rounding, so the products are <F, t> / |t|), zero padding
     const float* Bl = a.Bt + (size_t)lev * (64 + a.Q_all * per) * kK;
     for (int i = tid; i < a.npad * kK; i += (int)blockDim.x) {
         const int n = i >> 6, k = i & 63;
@@ -419,7 +437,8 @@ __global__ void __launch_bounds__(64 + 128 * NB, 1) query_pipe_kernel(const __gr
         }
         __syncwarp();
     } else if (warp == 1) {
-        // MMA issuer
+        // MMA issuer: the W stage is released by the MMA's own completion (the epilogue does not
+        // read W), the accumulator by its epilogue warps
         if (lane == 0) {
             int done = 0;
             for (int i = 0; i < my_tiles; ++i) {
@@ -434,6 +453,7 @@ __global__ void __launch_bounds__(64 + 128 * NB, 1) query_pipe_kernel(const __gr
                     tc::mma_bf16(tmem + (uint32_t)b * bufcols, tc::desc_sw128(a0 + k * 32), tc::desc_sw128(b0 + k * 32),
                                  idesc, k > 0 ? 1u : 0u);
                 tc::mma_commit(tc::smem_u32(m_full + b));
+                tc::mma_commit(tc::smem_u32(w_empty + s));
                 done = i + 1;
             }
             // no MMA may still be writing TMEM when it is freed
@@ -444,39 +464,62 @@ __global__ void __launch_bounds__(64 + 128 * NB, 1) query_pipe_kernel(const __gr
         }
         __syncwarp();
     } else {
-        // epilogue: warpgroup g takes local tiles g, g + nb, ...; this warp owns TMEM lane quarter q4
-        const int g = (warp - 2) >> 2, q4 = warp & 3;
+        // epilogue: accumulator g's warpgroups (member m) take local tiles g, g + nb, ...; this
+        // warp owns TMEM lane quarter q4
+        const int e = warp - 2;
+        const int g = e / (4 * WPA), m = (e >> 2) % WPA, q4 = warp & 3;
         const int row = q4 * 32 + lane;
         const int nch = a.Qp / 8;
         for (int i = g; i < my_tiles; i += nb) {
-            const int s = i % kPStages, b = i % nb;
-            if (!__all_sync(0xffffffffu, pipe_wait(tc::smem_u32(m_full + b), (uint32_t)((i / nb) & 1), abort, a.wait_ns))) break;
-            // (already complete) acquire of the TMA's writes of the W stage read below; the stage
-            // is reloaded only after this warpgroup releases it, so the phase cannot move on
-            if (!__all_sync(0xffffffffu, pipe_wait(tc::smem_u32(w_full + s), (uint32_t)((i / kPStages) & 1), abort, a.wait_ns)))
-                break;
-            tc::fence_after();
-            int vw;
-            int64_t p0;
-            locate((int64_t)blockIdx.x + (int64_t)i * gridDim.x, vw, p0);
-            const int64_t Pv = a.seg[vw].P;
+            const int b = i % nb;
             const uint32_t trow = tmem + (uint32_t)b * bufcols + ((uint32_t)(q4 * 32) << 16);
-            const uint8_t* sA = ring + (size_t)s * kM * 128;
-            // |F|^2 = W . (G W): columns 0..63 of Y, W from the landed (swizzled) BF16 tile
+            const bool ok = __all_sync(0xffffffffu, pipe_wait(tc::smem_u32(m_full + b), (uint32_t)((i / nb) & 1), abort, a.wait_ns));
             float n2;
-            {
+            if constexpr (WPA == 1) {
+                if (!ok) break;
+                tc::fence_after();
                 uint32_t y0[32], y1[32];
                 tc::tmem_ld32(trow, y0);
                 tc::tmem_ld32(trow + 32u, y1);
                 tc::tmem_wait_ld();
-                n2 = gram_norm2(sA, row, y0, y1);
+                n2 = chol_norm2(y0, y1);
+            } else {
+                // each member sums the squares of its 32 factor columns; the halves meet in shared memory
+                const int par = (i / nb) & 1;
+                float h = 0.0f;
+                if (ok) {
+                    tc::fence_after();
+                    uint32_t y[32];
+                    tc::tmem_ld32(trow + (uint32_t)(32 * m), y);
+                    tc::tmem_wait_ld();
+                    h = sumsq32(y);
+                }
+                float* xp = xpart + ((size_t)(g * 2 + par) * 2) * kM;
+                volatile int* xf = xok + (g * 2 + par) * 8;
+                xp[m * kM + row] = h;
+                if (lane == 0) xf[m * 4 + q4] = ok ? 1 : 0;
+                pair_sync(1 + g);
+                bool go = true;
+#pragma unroll
+                for (int w = 0; w < 8; ++w) go = go && xf[w] != 0;
+                if (!go) break;
+                n2 = xp[row] + xp[kM + row];
             }
-            __syncwarp();
-            if (lane == 0) tc::mbar_arrive(tc::smem_u32(w_empty + s));
             const float nf = sqrtf(fmaxf(n2, 0.0f));
             const float kneg = nf < 1e-12f ? 0.0f : -a.tau / nf;
+            int vw;
+            int64_t p0;
+            locate((int64_t)blockIdx.x + (int64_t)i * gridDim.x, vw, p0);
+            const int64_t Pv = a.seg[vw].P;
             const int64_t p = p0 + row;
-            for (int c = 0; c < nch; ++c) {
+            // this member's chunks m, m + WPA, ...; the accumulator is released after its last TMEM load
+            const int c_last = m + ((nch - 1 - m) / WPA) * WPA;   // (WPA = 2 only with nch >= 2)
+            if (m >= nch) {   // no chunk for this member: its last TMEM load was the norm's
+                tc::fence_before();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(tc::smem_u32(t_empty + b));
+            }
+            for (int c = m; c < nch; c += WPA) {
                 const int q0 = c * 8;
                 uint32_t rp[8], rn[8];
                 tc::tmem_ld8(trow + (uint32_t)(64 + q0), rp);
@@ -503,8 +546,8 @@ __global__ void __launch_bounds__(64 + 128 * NB, 1) query_pipe_kernel(const __gr
                     }
                     tc::tmem_wait_ld();
                 }
-                if (c == nch - 1) {
-                    // the last TMEM load of this tile is done: release the accumulator
+                if (c == c_last) {
+                    // this warp's last TMEM load of the tile is done: release the accumulator
                     tc::fence_before();
                     __syncwarp();
                     if (lane == 0) tc::mbar_arrive(tc::smem_u32(t_empty + b));
@@ -614,11 +657,11 @@ cudaError_t launch_query_tc_views(int levels, int V, const int64_t* P, int Q, in
             size_t smem = pipe_smem_bytes(g.npad, (1 + n_neg) * g.Qp);
             if (smem < 117760) smem = 117760;   // one CTA per SM: its TMEM allocation never waits
             if (smem > 232448) return cudaErrorInvalidValue;
-            const int ng = pipe_groups(tmem_cols(g.npad));
-            auto kern = ng == 3 ? query_pipe_kernel<3> : query_pipe_kernel<2>;
+            const int ng = pipe_groups(tmem_cols(g.npad)), split = pipe_split(ng, g.Qp / 8);
+            auto kern = ng == 3 ? query_pipe_kernel<3, 1> : split == 2 ? query_pipe_kernel<2, 2> : query_pipe_kernel<2, 1>;
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
-            kern<<<dim3(per_level, levels), 64 + 128 * ng, smem, stream>>>(tmW, g);
+            kern<<<dim3(per_level, levels), 64 + 128 * ng * split, smem, stream>>>(tmW, g);
             e = cudaGetLastError();
             if (e != cudaSuccess) return e;
         }

@@ -4,7 +4,7 @@
 // be captured once in a CUDA graph and replayed:
 //   project (grid.y = view) -> bin/sort over the concatenated tiles of all views -> pack records
 //   (grid.y = view) -> persistent splat over (view, tile) work items from an atomic queue ->
-//   B = [S S^T | S t] per level -> tensor-core relevancy over all views' pixels.
+//   B = [C | S t] per level (S S^T = C C^T) -> tensor-core relevancy over all views' pixels.
 #include <vector>
 
 #include "binsort.cuh"
@@ -196,6 +196,8 @@ extern "C" lsv2_status lsv2_query_views(int32_t V, const lsv2_camera* cams, int6
     const int nt = Q * (1 + n_neg);
     void* qws = ws + Lo.query;
     e = launch_query_prepare(levels, D, nt, codebook, text, qws, st);
+    if (e != cudaSuccess) return LSV2_ERR_CUDA;
+    e = launch_query_factor(levels, nt, qws, st);
     if (e != cudaSuccess) return LSV2_ERR_CUDA;
     e = launch_query_tc_views(levels, V, P.data(), Q, n_neg, tau, sa.coeff, true, query_ws_bt(qws),
                               query_ws_tnorm(qws, levels, nt), rel, rel_dtype == LSV2_BF16, sm_count(), dev_status,

@@ -179,17 +179,37 @@ class Frame:
         L.lsv2_decode(self.scene.levels, self.P, self.scene.L, self.scene.D, _ptr(W), w_dt, _ptr(cb),
                       cb_dt, _ptr(out), out_dt, _ptr(self.status), _stream(stream))
 
-    def query(self, text: torch.Tensor, out: torch.Tensor, tau: float = 10.0, compute=L.LSV2_F32, stream=None,
-              from_bf16: bool = False):
-        Q, nt, D = text.shape
-        need = L.lsv2_query_workspace_bytes(self.scene.levels, self.scene.L, Q, nt - 1)
+    def _query_ws(self, Q: int, n_neg: int) -> int:
+        need = L.lsv2_query_workspace_bytes(self.scene.levels, self.scene.L, Q, n_neg)
         if self.query_ws is None or self.query_ws.numel() < need:
             self.query_ws = torch.empty(need, dtype=torch.uint8, device=self.device)
+        return need
+
+    def query(self, text: torch.Tensor, out: torch.Tensor, tau: float = 10.0, compute=L.LSV2_F32, stream=None,
+              from_bf16: bool = False, prepared: bool = False):
+        """Relevancy maps out [Q, levels, P] of the texts [Q, 1 + n_neg, D] (lsv2_query); with
+        prepared=True the query operands come from an earlier query_prepare of the same texts and
+        compute dtype (lsv2_query_prepared)."""
+        Q, nt, D = text.shape
+        need = self._query_ws(Q, nt - 1)
         out_dt = L.LSV2_BF16 if out.dtype == torch.bfloat16 else L.LSV2_F32
         W, w_dt = (self.coeff16, L.LSV2_BF16) if from_bf16 else (self.coeff, L.LSV2_F32)
+        if prepared:
+            L.lsv2_query_prepared(self.scene.levels, self.P, self.scene.L, _ptr(W), w_dt, Q, nt - 1, float(tau),
+                                  _ptr(self.query_ws), need, _ptr(out), out_dt, compute, _ptr(self.status),
+                                  _stream(stream))
+            return
         L.lsv2_query(self.scene.levels, self.P, self.scene.L, D, _ptr(W), w_dt, _ptr(self.scene.codebook),
                      Q, nt - 1, _ptr(text), float(tau), _ptr(self.query_ws), need, _ptr(out), out_dt, compute,
                      _ptr(self.status), _stream(stream))
+
+    def query_prepare(self, text: torch.Tensor, compute=L.LSV2_F32, stream=None):
+        """The query operands of the texts (lsv2_query_prepare), for a later query(prepared=True); it
+        reads only the codebook and the texts, so it can run on another stream beside the render."""
+        Q, nt, D = text.shape
+        need = self._query_ws(Q, nt - 1)
+        L.lsv2_query_prepare(self.scene.levels, self.scene.L, D, _ptr(self.scene.codebook), Q, nt - 1, _ptr(text),
+                             compute, _ptr(self.query_ws), need, _stream(stream))
 
     def postprocess(self, rel: torch.Tensor, k: int = 29, mode: int = L.LSV2_POST_LERF, threshold: float = 0.5,
                     out: "PostResult | None" = None, with_mask: bool = True, stream=None) -> "PostResult":

@@ -85,8 +85,8 @@ def test_mlp_decode_host_checks(lib):
     """Workspace sizing and the host-side rejections of lsv2_mlp_decode (all before any CUDA call)."""
     w = (C.c_int32 * 8)(8, 16, 32, 64, 128, 256, 256, 512)
     lt = 32 << 20
-    # two activation buffers of a 262,144-row block at width 256, plus the BF16 copy of an F32 input
-    blk = 1 << 18
+    # two activation buffers of a 1,048,576-row block at width 256, plus the BF16 copy of an F32 input
+    blk = 1 << 20
     assert L.lsv2_mlp_decode_workspace_bytes(1 << 22, 7, w, 0, 0) == 2 * blk * 256 * 2 + blk * 8 * 2 + lt
     assert L.lsv2_mlp_decode_workspace_bytes(1 << 22, 7, w, 1, 0) == 2 * blk * 256 * 2 + lt
     assert L.lsv2_mlp_decode_workspace_bytes(1000, 7, w, 1, 0) == 2 * 512000 + lt

@@ -114,15 +114,18 @@ def test_decode_tc_wait_expires_and_recovers(from_bf16):
     expire_then_recover(fr, lambda: fr.decode(F, codebook=cb16, from_bf16=from_bf16), [F])
 
 
+@pytest.mark.parametrize("Q", [3, 16])
 @pytest.mark.parametrize("from_bf16", [True, False])
-def test_query_tc_wait_expires_and_recovers(from_bf16):
-    """BF16 map: the pipelined relevancy kernel; FP32 map: the converting one."""
+def test_query_tc_wait_expires_and_recovers(from_bf16, Q):
+    """BF16 map: the pipelined relevancy kernel (3 queries: three accumulators, one epilogue
+    warpgroup each; 16 queries: two accumulators, two warpgroups each meeting at a named barrier
+    per tile); FP32 map: the converting one."""
     fr = three_level_frame()
     fr.splat()
     fr.splat_bf16()
     fr.check()
-    text = torch.as_tensor(syn.text_queries(syn.SEED + 2, 3, 4), device="cuda")
-    rel = torch.empty((3, 3, fr.P), dtype=torch.bfloat16, device="cuda")
+    text = torch.as_tensor(syn.text_queries(syn.SEED + 2, Q, 4), device="cuda")
+    rel = torch.empty((Q, 3, fr.P), dtype=torch.bfloat16, device="cuda")
     expire_then_recover(fr, lambda: fr.query(text, rel, compute=L.LSV2_BF16, from_bf16=from_bf16), [rel])
 
 
