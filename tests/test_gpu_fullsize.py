@@ -1,5 +1,9 @@
 """Parity at the sizes the benchmark runs, where the persistent kernels loop.
 
+* The whole at-scale frame (300,000 Gaussians, three levels, 1440x1080): all 1,555,200 pixels'
+  coefficient maps, final transmittances and last contributors against the oracle's FP64 blend,
+  the pixels split over a pool of host processes.
+
 * lsv2_l1_decode_backward on the differentiation workload (100,000 Gaussians, one level,
   720x540, D = 512): 388,800 pixels, so every persistent CTA walks many pixel tiles and adds
   its codebook-gradient partial once at the end.  Loss, dLoss/dW on sampled pixels and the
@@ -9,12 +13,16 @@
   sequential single-view pipelines, and within the BF16 relevancy bound (1e-2) of the oracle on
   sampled pixels.
 """
+import multiprocessing as mp
+import os
+
 import numpy as np
 import pytest
 
 import lsv2_synth as syn
 from oracle import oracle as O
 
+import oracle_workers
 from gpu_helpers import KNIFE_EDGE
 
 torch = pytest.importorskip("torch")
@@ -23,6 +31,35 @@ pytestmark = pytest.mark.gpu
 from paper_2507_07136_b300 import _lib as L  # noqa: E402
 from paper_2507_07136_b300.pipeline import DeviceScene, Frame, _ptr, _stream  # noqa: E402
 from paper_2507_07136_b300.views import ViewsBatch  # noqa: E402
+
+
+def test_at_scale_whole_frame_coefficient_map():
+    sc, cam, _ = syn.at_scale()
+    pr = O.project(cam, sc.means, sc.scales, sc.quats)
+    ids, ranges = O.bin(cam, pr)
+    fr = Frame(DeviceScene.from_numpy(sc), cam)
+    fr.render()
+    fr.check()
+    W = fr.coeff.cpu().numpy()
+    T = fr.final_T.cpu().numpy()
+    nl = fr.n_last.cpu().numpy()
+    px, py = O.all_pixels(cam)
+    workers = max(1, min(16, os.cpu_count() or 1))
+    chunks = np.array_split(np.arange(cam.num_pixels), workers * 8)
+    tasks = [(px[c], py[c], np.ascontiguousarray(W[:, c]), T[c], nl[c]) for c in chunks]
+    with mp.get_context("spawn").Pool(workers, initializer=oracle_workers.init_blend,
+                                      initargs=(cam, pr, sc.opacity, ids, ranges, sc.idx, sc.weights,
+                                                KNIFE_EDGE)) as pool:
+        res = pool.map(oracle_workers.blend_check, tasks)
+    assert sum(r["pixels"] for r in res) == cam.num_pixels
+    checked = sum(r["checked"] for r in res)
+    assert checked > 0.99 * cam.num_pixels
+    assert sum(r["contributions"] for r in res) > 10 * cam.num_pixels
+    assert max(r["w_worst"] for r in res) <= 1.0, f"W: worst x{max(r['w_worst'] for r in res):.2f} of bound"
+    assert max(r["t_worst"] for r in res) <= 1.0
+    assert sum(r["n_last_mismatch"] for r in res) == 0
+    # knife-edge pixels: one decision may flip, which moves W by at most one contribution
+    assert max(r["knife_err"] for r in res) < 0.05
 
 
 def test_l1_decode_backward_full_size():
