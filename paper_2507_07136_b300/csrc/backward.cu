@@ -90,7 +90,8 @@ struct BwdCfg {
     __host__ __device__ static constexpr int lane_y(int warp, int lane) { return (warp / kWarpsX) * kWarpH + lane / kWarpW; }
     static_assert(kPairs + 6 <= 32, "quantities per Gaussian");
     static constexpr int kQ = kPairs + 6;              // gradient quantities per Gaussian and pixel
-    static constexpr int kPer = 2 * kQ <= 32 ? 2 : 1;  // Gaussians evaluated per step (one reduce-scatter)
+    // Gaussians evaluated per step: as many as their quantities fit the 32 lanes of one reduce-scatter
+    static constexpr int kPer = 32 / kQ > 4 ? 4 : 32 / kQ;
     static_assert(bwd_record_last_free(kPairs), "the record's last float holds the culling half-height");
     static_assert(TW % 8 == 0 && TH % 4 == 0 && (TW * TH) % 32 == 0, "warps cover 8 x 4 blocks of a tile");
 };
@@ -181,7 +182,7 @@ __global__ void __launch_bounds__(TW* TH) splat_backward_kernel(SplatBwdArgs a)
         }
         uint32_t mask = __ballot_sync(0xffffffffu, keep);
         __syncwarp();
-        // kPer Gaussians per step (two when 2 kQ <= 32), back to front: the first is the one further
+        // kPer Gaussians per step (as many as kPer kQ <= 32 allows), back to front: the first is the one further
         // back in the list.  Their evaluations are independent; the transmittance and the running
         // sum pass from one to the next; one reduce-scatter of all their quantities serves both.
         constexpr int kPer = C::kPer;
@@ -260,8 +261,14 @@ __global__ void __launch_bounds__(TW* TH) splat_backward_kernel(SplatBwdArgs a)
                 // lane L holds quantity L % kQ of Gaussian L / kQ of the step
                 const float tot = reduce_scatter32(vals, lane);
                 const int u = lane / C::kQ, q = lane - u * C::kQ;
-                const bool here = u < kPer && (u == 0 || idx[kPer - 1] >= 0);
-                const uint32_t g = u == 0 ? gid[0] : gid[kPer - 1];
+                bool here = false;
+                uint32_t g = 0;
+#pragma unroll
+                for (int v = 0; v < kPer; ++v)
+                    if (u == v) {
+                        here = idx[v] >= 0;
+                        g = gid[v];
+                    }
                 if (here) {
                     if (q < C::kPairs) {
                         atomicAdd(a.dw + (size_t)g * C::kPairs + q, tot);
