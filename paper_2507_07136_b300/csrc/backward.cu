@@ -17,6 +17,7 @@
 //    scale, quaternion) through Sigma' = N N^T + 0.3 I, N = J W R diag(s).
 #include "device.cuh"
 #include "backward.cuh"
+#include "tc.cuh"
 
 #include <algorithm>
 
@@ -75,6 +76,15 @@ __device__ __forceinline__ float reduce_scatter32(float (&v)[32], int lane)
     return v[0];
 }
 
+// 16-byte asynchronous copy global -> shared (cp.async, L2 only), its group commit and wait
+__device__ __forceinline__ void cp_async16(float* sdst, const float* gsrc)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(sdst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 template <int LEVELS, int K, int TW, int TH>
 struct BwdCfg {
     static constexpr int kWarps = TW * TH / 32;
@@ -96,14 +106,23 @@ struct BwdCfg {
     static_assert(TW % 8 == 0 && TH % 4 == 0 && (TW * TH) % 32 == 0, "warps cover 8 x 4 blocks of a tile");
 };
 
-template <int LEVELS, int K, int TW, int TH>
-__global__ void __launch_bounds__(TW* TH) splat_backward_kernel(SplatBwdArgs a)
+// TM: dLoss/dW of each warp's 32 pixels in tensor memory instead of shared memory (one level, 16 x 16
+// tiles: 8 warps, two per TMEM lane quarter, 64 columns each, 128 per CTA): shared memory then holds
+// only the staged records, and three CTAs (24 warps) share an SM where shared memory held two.
+template <int LEVELS, int K, int TW, int TH, bool TM = false>
+__global__ void __launch_bounds__(TW* TH, TM ? 3 : 1) splat_backward_kernel(SplatBwdArgs a)
 {
     using C = BwdCfg<LEVELS, K, TW, TH>;
+    static_assert(!TM || (LEVELS == 1 && TW == 16 && TH == 16), "TMEM dLoss/dW: one level, 16 x 16 tiles");
+    constexpr uint32_t kTmCols = 128;
     extern __shared__ __align__(16) float smem[];
+    __shared__ uint32_t tslot;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float* gW = smem + warp * C::kGFloats;
-    float* stage = smem + C::kWarps * C::kGFloats + warp * 32 * C::kSmemRecFloats;
+    float* gW = TM ? nullptr : smem + warp * C::kGFloats;
+    float* stage = TM ? nullptr : smem + C::kWarps * C::kGFloats + warp * 32 * C::kSmemRecFloats;
+    // TM: each lane's record of the current and the next batch, [2][32 lanes][record], filled by
+    // asynchronous copies (no record buffers in registers)
+    float* rbuf = TM ? smem + warp * 2 * 32 * C::kRecFloats : nullptr;
     const int GX = (a.cam.width + TW - 1) / TW;
     const int tile = blockIdx.x;
     const int tx = tile % GX, ty = tile / GX;
@@ -114,8 +133,32 @@ __global__ void __launch_bounds__(TW* TH) splat_backward_kernel(SplatBwdArgs a)
     const float wx0 = (float)(tx * TW + C::lane_x(warp, 0)), wx1 = wx0 + (float)(C::kWarpW - 1);
     const float wy0 = (float)(ty * TH + C::lane_y(warp, 0)), wy1 = wy0 + (float)(C::kWarpH - 1);
 
+    uint32_t tcol = 0;   // TM: this warp's 64 columns in its lane quarter
+    if constexpr (TM) {
+        if (warp == 0) tc::tmem_alloc(tc::smem_u32(&tslot), kTmCols);
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+        tcol = tslot + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(64 * (warp >> 2));
+        // each lane's pixel row of dLoss/dW (64 floats) into its TMEM lane
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            uint32_t v[32];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (inside) x = __ldg(reinterpret_cast<const float4*>(a.dcoeff + pix * 64 + 32 * h) + i);
+                v[4 * i] = __float_as_uint(x.x);
+                v[4 * i + 1] = __float_as_uint(x.y);
+                v[4 * i + 2] = __float_as_uint(x.z);
+                v[4 * i + 3] = __float_as_uint(x.w);
+            }
+            tc::tmem_st32(tcol + 32u * h, v);
+        }
+        tc::tmem_wait_st();
+    }
     // stage dLoss/dW of this warp's pixels as columns gW[col][lane]
-    for (int lev = 0; lev < LEVELS; ++lev)
+    for (int lev = 0; lev < (TM ? 0 : LEVELS); ++lev)
         for (int q = lane; q < 32 * 16; q += 32) {
             const int pl = q >> 4, c4 = (q & 15) * 4;
             const int gx = tx * TW + C::lane_x(warp, pl), gy = ty * TH + C::lane_y(warp, pl);
@@ -162,20 +205,38 @@ __global__ void __launch_bounds__(TW* TH) splat_backward_kernel(SplatBwdArgs a)
             for (int v = 0; v < kR; ++v) r[v] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
     };
+    auto fetch = [&](uint32_t id, int slot) {   // TM: this lane's record into rbuf[slot] (one copy group)
+        if (id != kNone) {
+            const float* src = a.recs + (size_t)id * C::kRecFloats;
+            float* dst = rbuf + (slot * 32 + lane) * C::kRecFloats;
+#pragma unroll
+            for (int v = 0; v < kR; ++v) cp_async16(dst + 4 * v, src + 4 * v);
+        }
+        cp_async_commit();
+    };
     int top = (int)wmax;
     uint32_t my_g = load_id(top), id_nxt = load_id(top - 32);
-    float4 rc[kR];
-    load_rec(my_g, rc);
+    float4 rc[TM ? 1 : kR];
+    if constexpr (TM) fetch(my_g, 0);
+    else load_rec(my_g, rc);
+    int slot = 0;
     for (; top > 0; top -= 32) {
-        float4 rn[kR];
-        load_rec(id_nxt, rn);
+        float4 rn[TM ? 1 : kR];
+        if constexpr (TM) {
+            fetch(id_nxt, slot ^ 1);
+            cp_async_wait<1>();   // this lane's copies of the current batch have landed
+            __syncwarp();         // ... and every lane's, for the reads of other lanes' records below
+        } else {
+            load_rec(id_nxt, rn);
+        }
         const uint32_t id_nn = load_id(top - 64);
         const int lo = top - 32;
-        const float4 my_xy = rc[0];
-        const float exx = rc[3].w, exy = rc[kR - 1].w;
+        const float* myrec = TM ? rbuf + (slot * 32 + lane) * C::kRecFloats : nullptr;
+        const float4 my_xy = TM ? *reinterpret_cast<const float4*>(myrec) : rc[0];
+        const float exx = TM ? myrec[15] : rc[3].w, exy = TM ? myrec[C::kRecFloats - 1] : rc[kR - 1].w;
         const bool keep = my_g != kNone && exx >= 0.0f && my_xy.x + exx >= wx0 && my_xy.x - exx <= wx1 &&
                           my_xy.y + exy >= wy0 && my_xy.y - exy <= wy1;
-        if (keep) {
+        if (!TM && keep) {
             float4* dst = reinterpret_cast<float4*>(stage + lane * C::kSmemRecFloats);
 #pragma unroll
             for (int v = 1; v < kR; ++v) dst[v - 1] = rc[v];
@@ -202,17 +263,35 @@ __global__ void __launch_bounds__(TW* TH) splat_backward_kernel(SplatBwdArgs a)
                 const int i = idx[u] < 0 ? idx[0] : idx[u];   // an absent second Gaussian re-reads the first (unused)
                 gid[u] = __shfl_sync(0xffffffffu, my_g, i);
                 float4 g0;
-                g0.x = __shfl_sync(0xffffffffu, my_xy.x, i);
-                g0.y = __shfl_sync(0xffffffffu, my_xy.y, i);
-                g0.z = __shfl_sync(0xffffffffu, my_xy.z, i);
-                g0.w = __shfl_sync(0xffffffffu, my_xy.w, i);
-                rr[u] = stage + i * C::kSmemRecFloats;
+                if constexpr (TM) {
+                    const float* ri = rbuf + (slot * 32 + i) * C::kRecFloats;
+                    g0 = *reinterpret_cast<const float4*>(ri);
+                    rr[u] = ri + 4;
+                } else {
+                    g0.x = __shfl_sync(0xffffffffu, my_xy.x, i);
+                    g0.y = __shfl_sync(0xffffffffu, my_xy.y, i);
+                    g0.z = __shfl_sync(0xffffffffu, my_xy.z, i);
+                    g0.w = __shfl_sync(0xffffffffu, my_xy.w, i);
+                    rr[u] = stage + i * C::kSmemRecFloats;
+                }
                 const float4 ax = *reinterpret_cast<const float4*>(rr[u]);
                 axl[u] = *reinterpret_cast<const float4*>(rr[u] + 4);
                 g2[u] = *reinterpret_cast<const float4*>(rr[u] + 8);
                 dx[u] = __fadd_rn(__fsub_rn(g0.x, pxf), g0.z);
                 dy[u] = __fadd_rn(__fsub_rn(g0.y, pyf), g0.w);
                 p2[u] = eval_power2(g0, ax, axl[u], pxf, pyf);
+            }
+            // TM: the dLoss/dW columns of every pair of the step's Gaussians (warp-uniform columns,
+            // loaded by all lanes together before the per-lane conditions)
+            uint32_t gwt[TM ? kPer : 1][TM ? C::kPairs : 1];
+            if constexpr (TM) {
+#pragma unroll
+                for (int u = 0; u < kPer; ++u) {
+                    const uint8_t* cr = reinterpret_cast<const uint8_t*>(rr[u] + 12 + C::kPairs);
+#pragma unroll
+                    for (int p = 0; p < C::kPairs; ++p) tc::tmem_ld1(tcol + (uint32_t)cr[p], gwt[u][p]);
+                }
+                tc::tmem_wait_ld();
             }
             float vals[32];
 #pragma unroll
@@ -236,7 +315,9 @@ __global__ void __launch_bounds__(TW* TH) splat_backward_kernel(SplatBwdArgs a)
                         float gsum = 0.0f;
 #pragma unroll
                         for (int p = 0; p < C::kPairs; ++p) {
-                            const float gw = gW[(int)cr[p] * 33 + lane];
+                            float gw;
+                            if constexpr (TM) gw = __uint_as_float(gwt[u][p]);
+                            else gw = gW[(int)cr[p] * 33 + lane];
                             vals[u * C::kQ + p] = gw * e;
                             gsum = fmaf(gw, wr[p], gsum);
                         }
@@ -281,31 +362,53 @@ __global__ void __launch_bounds__(TW* TH) splat_backward_kernel(SplatBwdArgs a)
             }
         }
         __syncwarp();
+        if constexpr (TM) {
+            slot ^= 1;
+        } else {
 #pragma unroll
-        for (int v = 0; v < kR; ++v) rc[v] = rn[v];
+            for (int v = 0; v < kR; ++v) rc[v] = rn[v];
+        }
         my_g = id_nxt;
         id_nxt = id_nn;
     }
+    if constexpr (TM) {
+        cp_async_wait<0>();   // no copy may still be landing when the CTA retires
+        // every warp's TMEM loads completed at their waits
+        tc::fence_before();
+        __syncthreads();
+        if (warp == 0) {
+            tc::fence_after();
+            tc::tmem_dealloc(tslot, kTmCols);
+        }
+    }
 }
 
-template <int LEVELS, int K, int TW, int TH>
+template <int LEVELS, int K, int TW, int TH, bool TM = false>
 cudaError_t launch_bwd_t(const SplatBwdArgs& a, cudaStream_t stream)
 {
     using C = BwdCfg<LEVELS, K, TW, TH>;
     static_assert(C::kSmemBytes <= 232448, "shared memory budget");
-    auto kern = splat_backward_kernel<LEVELS, K, TW, TH>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
+    // TM: the double-buffered records only, padded so that at most four CTAs (4 x 128 TMEM columns)
+    // share an SM and a CTA's TMEM allocation never waits
+    constexpr int kRecBytes = C::kWarps * 2 * 32 * C::kRecFloats * 4;
+    constexpr int kSmem = TM ? (kRecBytes > 49152 ? kRecBytes : 49152) : C::kSmemBytes;
+    static_assert(!TM || 5 * (kSmem + 1024 + 16) > 233472, "at most four CTAs per SM");
+    auto kern = splat_backward_kernel<LEVELS, K, TW, TH, TM>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
     if (e != cudaSuccess) return e;
     const int GX = (a.cam.width + TW - 1) / TW, GY = (a.cam.height + TH - 1) / TH;
     if (GX * GY == 0) return cudaSuccess;
-    kern<<<GX * GY, TW * TH, C::kSmemBytes, stream>>>(a);
+    kern<<<GX * GY, TW * TH, kSmem, stream>>>(a);
     return cudaGetLastError();
 }
 
 template <int LEVELS, int K>
 cudaError_t launch_bwd_tile(const SplatBwdArgs& a, cudaStream_t stream)
 {
-    if (a.cam.tile_w == 16 && a.cam.tile_h == 16) return launch_bwd_t<LEVELS, K, 16, 16>(a, stream);
+    if (a.cam.tile_w == 16 && a.cam.tile_h == 16) {
+        if constexpr (LEVELS == 1) return launch_bwd_t<LEVELS, K, 16, 16, true>(a, stream);
+        return launch_bwd_t<LEVELS, K, 16, 16>(a, stream);
+    }
     if (a.cam.tile_w == 8 && a.cam.tile_h == 8) return launch_bwd_t<LEVELS, K, 8, 8>(a, stream);
     if (a.cam.tile_w == 32 && a.cam.tile_h == 8) return launch_bwd_t<LEVELS, K, 32, 8>(a, stream);
     return cudaErrorInvalidValue;
