@@ -358,6 +358,7 @@ lsv2_status lsv2_splat_backward(const lsv2_camera* cam, int64_t n, const float* 
     a.workspace = workspace;
     a.dw = dw;
     a.dopacity = dopacity;
+    a.num_sms = sm_count();
     ProjBwdArgs pa{*cam, n, means, scales, quats, proj->flags, nullptr, dmeans, dscales, dquats};
     return cuda_status(launch_splat_backward(levels, K, a, pa, idx, w, S(stream)));
 }

@@ -106,25 +106,16 @@ struct BwdCfg {
     static_assert(TW % 8 == 0 && TH % 4 == 0 && (TW * TH) % 32 == 0, "warps cover 8 x 4 blocks of a tile");
 };
 
-// TM: dLoss/dW of each warp's 32 pixels in tensor memory instead of shared memory (one level, 16 x 16
-// tiles: 8 warps, two per TMEM lane quarter, 64 columns each, 128 per CTA): shared memory then holds
-// only the staged records, and three CTAs (24 warps) share an SM where shared memory held two.
-template <int LEVELS, int K, int TW, int TH, bool TM = false>
-__global__ void __launch_bounds__(TW* TH, TM ? 3 : 1) splat_backward_kernel(SplatBwdArgs a)
+// The adjoint of one warp's 8 x 4 pixel block `warp` of bin tile `tile`: its pixels' dLoss/dW
+// staged as columns gW[col][lane] in shared memory, or (TM) in this warp's 64 TMEM columns at tcol;
+// then the tile's list back to front.  stage: 32 staged records (without TM); rbuf: TM's
+// double-buffered records.
+template <int LEVELS, int K, int TW, int TH, bool TM>
+__device__ __forceinline__ void bwd_warp_block(const SplatBwdArgs& a, int tile, int warp, int lane, float* gW,
+                                               uint32_t tcol, float* stage, float* rbuf)
 {
     using C = BwdCfg<LEVELS, K, TW, TH>;
-    static_assert(!TM || (LEVELS == 1 && TW == 16 && TH == 16), "TMEM dLoss/dW: one level, 16 x 16 tiles");
-    constexpr uint32_t kTmCols = 128;
-    extern __shared__ __align__(16) float smem[];
-    __shared__ uint32_t tslot;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float* gW = TM ? nullptr : smem + warp * C::kGFloats;
-    float* stage = TM ? nullptr : smem + C::kWarps * C::kGFloats + warp * 32 * C::kSmemRecFloats;
-    // TM: each lane's record of the current and the next batch, [2][32 lanes][record], filled by
-    // asynchronous copies (no record buffers in registers)
-    float* rbuf = TM ? smem + warp * 2 * 32 * C::kRecFloats : nullptr;
     const int GX = (a.cam.width + TW - 1) / TW;
-    const int tile = blockIdx.x;
     const int tx = tile % GX, ty = tile / GX;
     const int px = tx * TW + C::lane_x(warp, lane), py = ty * TH + C::lane_y(warp, lane);
     const bool inside = px < a.cam.width && py < a.cam.height;
@@ -133,14 +124,9 @@ __global__ void __launch_bounds__(TW* TH, TM ? 3 : 1) splat_backward_kernel(Spla
     const float wx0 = (float)(tx * TW + C::lane_x(warp, 0)), wx1 = wx0 + (float)(C::kWarpW - 1);
     const float wy0 = (float)(ty * TH + C::lane_y(warp, 0)), wy1 = wy0 + (float)(C::kWarpH - 1);
 
-    uint32_t tcol = 0;   // TM: this warp's 64 columns in its lane quarter
     if constexpr (TM) {
-        if (warp == 0) tc::tmem_alloc(tc::smem_u32(&tslot), kTmCols);
-        tc::fence_before();
-        __syncthreads();
-        tc::fence_after();
-        tcol = tslot + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(64 * (warp >> 2));
-        // each lane's pixel row of dLoss/dW (64 floats) into its TMEM lane
+        // each lane's pixel row of dLoss/dW (64 floats) into its TMEM lane (the previous block's
+        // TMEM loads completed at their waits)
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             uint32_t v[32];
@@ -372,33 +358,92 @@ __global__ void __launch_bounds__(TW* TH, TM ? 3 : 1) splat_backward_kernel(Spla
         id_nxt = id_nn;
     }
     if constexpr (TM) {
-        cp_async_wait<0>();   // no copy may still be landing when the CTA retires
-        // every warp's TMEM loads completed at their waits
-        tc::fence_before();
-        __syncthreads();
-        if (warp == 0) {
-            tc::fence_after();
-            tc::tmem_dealloc(tslot, kTmCols);
-        }
+        cp_async_wait<0>();   // the last prefetch has landed before rbuf is reused
+        __syncwarp();
     }
 }
 
-template <int LEVELS, int K, int TW, int TH, bool TM = false>
+template <int LEVELS, int K, int TW, int TH>
+__global__ void __launch_bounds__(TW* TH) splat_backward_kernel(SplatBwdArgs a)
+{
+    using C = BwdCfg<LEVELS, K, TW, TH>;
+    extern __shared__ __align__(16) float smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    bwd_warp_block<LEVELS, K, TW, TH, false>(a, blockIdx.x, warp, lane, smem + warp * C::kGFloats, 0u,
+                                             smem + C::kWarps * C::kGFloats + warp * 32 * C::kSmemRecFloats, nullptr);
+}
+
+// One level, 16 x 16 tiles: dLoss/dW of each warp's 32 pixels in tensor memory (8 warps, two per TMEM
+// lane quarter, 64 columns each, 128 per CTA) and each lane's records double-buffered in shared
+// memory by asynchronous copies, so three CTAs (24 warps) share an SM (registers), where the
+// shared-memory columns allowed two.  Persistent: every warp takes (tile, 8 x 4 block) work items
+// from a queue on its own, so a warp that finishes early starts the next block instead of waiting
+// for the slowest warp of its tile.
+template <int K>
+__global__ void __launch_bounds__(256, 3) splat_backward_tm_kernel(SplatBwdArgs a, uint32_t items)
+{
+    using C = BwdCfg<1, K, 16, 16>;
+    constexpr uint32_t kTmCols = 128;
+    extern __shared__ __align__(16) float smem[];
+    __shared__ uint32_t tslot;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 0) tc::tmem_alloc(tc::smem_u32(&tslot), kTmCols);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tcol = tslot + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(64 * (warp >> 2));
+    float* rbuf = smem + warp * 2 * 32 * C::kRecFloats;
+    while (true) {
+        uint32_t item = 0;
+        if (lane == 0) item = atomicAdd(a.queue, 1u);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= items) break;
+        bwd_warp_block<1, K, 16, 16, true>(a, (int)(item / C::kWarps), (int)(item % C::kWarps), lane, nullptr, tcol,
+                                           nullptr, rbuf);
+    }
+    // every warp's TMEM loads completed at their waits
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after();
+        tc::tmem_dealloc(tslot, kTmCols);
+    }
+}
+
+template <int LEVELS, int K, int TW, int TH>
 cudaError_t launch_bwd_t(const SplatBwdArgs& a, cudaStream_t stream)
 {
     using C = BwdCfg<LEVELS, K, TW, TH>;
     static_assert(C::kSmemBytes <= 232448, "shared memory budget");
-    // TM: the double-buffered records only, padded so that at most four CTAs (4 x 128 TMEM columns)
-    // share an SM and a CTA's TMEM allocation never waits
-    constexpr int kRecBytes = C::kWarps * 2 * 32 * C::kRecFloats * 4;
-    constexpr int kSmem = TM ? (kRecBytes > 49152 ? kRecBytes : 49152) : C::kSmemBytes;
-    static_assert(!TM || 5 * (kSmem + 1024 + 16) > 233472, "at most four CTAs per SM");
-    auto kern = splat_backward_kernel<LEVELS, K, TW, TH, TM>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    auto kern = splat_backward_kernel<LEVELS, K, TW, TH>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
     if (e != cudaSuccess) return e;
     const int GX = (a.cam.width + TW - 1) / TW, GY = (a.cam.height + TH - 1) / TH;
     if (GX * GY == 0) return cudaSuccess;
-    kern<<<GX * GY, TW * TH, kSmem, stream>>>(a);
+    kern<<<GX * GY, TW * TH, C::kSmemBytes, stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <int K>
+cudaError_t launch_bwd_tm(const SplatBwdArgs& a, cudaStream_t stream)
+{
+    using C = BwdCfg<1, K, 16, 16>;
+    // the double-buffered records, padded so that at most four CTAs (4 x 128 TMEM columns) could
+    // share an SM: a CTA's TMEM allocation never waits
+    constexpr int kRecBytes = C::kWarps * 2 * 32 * C::kRecFloats * 4;
+    constexpr int kSmem = kRecBytes > 49152 ? kRecBytes : 49152;
+    static_assert(5 * (kSmem + 1024 + 16) > 233472, "at most four CTAs per SM");
+    auto kern = splat_backward_tm_kernel<K>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    if (e != cudaSuccess) return e;
+    const int GX = (a.cam.width + 15) / 16, GY = (a.cam.height + 15) / 16;
+    const uint32_t items = (uint32_t)(GX * GY) * C::kWarps;
+    if (items == 0) return cudaSuccess;
+    e = cudaMemsetAsync(a.queue, 0, sizeof(uint32_t), stream);
+    if (e != cudaSuccess) return e;
+    int grid = 3 * (a.num_sms > 0 ? a.num_sms : 1);
+    if ((uint32_t)grid * C::kWarps > items) grid = (int)((items + C::kWarps - 1) / C::kWarps);
+    kern<<<grid, 256, kSmem, stream>>>(a, items);
     return cudaGetLastError();
 }
 
@@ -406,7 +451,7 @@ template <int LEVELS, int K>
 cudaError_t launch_bwd_tile(const SplatBwdArgs& a, cudaStream_t stream)
 {
     if (a.cam.tile_w == 16 && a.cam.tile_h == 16) {
-        if constexpr (LEVELS == 1) return launch_bwd_t<LEVELS, K, 16, 16, true>(a, stream);
+        if constexpr (LEVELS == 1) return launch_bwd_tm<K>(a, stream);
         return launch_bwd_t<LEVELS, K, 16, 16>(a, stream);
     }
     if (a.cam.tile_w == 8 && a.cam.tile_h == 8) return launch_bwd_t<LEVELS, K, 8, 8>(a, stream);
@@ -522,7 +567,7 @@ size_t splat_backward_workspace_bytes(int64_t n, int levels, int K)
 {
     const size_t g2 = ((size_t)n * 8 * 4 + 255) / 256 * 256;
     const size_t recs = ((size_t)n * bwd_record_floats(levels * K) * 4 + 255) / 256 * 256;
-    return g2 + recs;
+    return g2 + recs + 256;   // + the work queue of the persistent kernel
 }
 
 cudaError_t launch_splat_backward(int levels, int K, const SplatBwdArgs& args, const ProjBwdArgs& pargs,
@@ -532,6 +577,8 @@ cudaError_t launch_splat_backward(int levels, int K, const SplatBwdArgs& args, c
     const size_t g2 = ((size_t)pargs.n * 8 * 4 + 255) / 256 * 256;
     a.grad2d = static_cast<float*>(a.workspace);
     a.recs = reinterpret_cast<float*>(static_cast<char*>(a.workspace) + g2);
+    a.queue = reinterpret_cast<uint32_t*>(static_cast<char*>(a.workspace) + g2 +
+                                          ((size_t)pargs.n * bwd_record_floats(levels * K) * 4 + 255) / 256 * 256);
     cudaError_t e = cudaMemsetAsync(a.grad2d, 0, (size_t)pargs.n * 8 * 4, stream);
     if (e != cudaSuccess) return e;
     if (pargs.n > 0)

@@ -19,8 +19,10 @@ struct SplatBwdArgs {
     void* workspace;
     float* recs;      // set by the launcher (inside workspace)
     float* grad2d;    // set by the launcher (inside workspace): [n][8] du dv da db dc
+    uint32_t* queue;  // set by the launcher (inside workspace): work items taken (persistent kernel)
     float* dw;
     float* dopacity;
+    int num_sms;      // SMs of the device (grid of the persistent kernel)
 };
 
 struct ProjBwdArgs {
