@@ -170,6 +170,47 @@ def test_autograd_activations_chain():
     assert cb.grad is not None and float(cb.grad.abs().sum()) > 0
 
 
+def oracle_blend_adjoint(sc, cam, dW):
+    """The oracle's blend adjoint for a given dLoss/dW, chained through the projection Jacobian:
+    (dw, dopacity, dmeans, dscales, dquats)."""
+    import ctypes as C
+    r = O.render(sc, cam)
+    n, lev, K = sc.n, sc.levels, sc.K
+    dw = np.zeros((n, lev, K))
+    dop = np.zeros(n)
+    dm2 = np.zeros((n, 2))
+    dcn = np.zeros((n, 3))
+    c = O.cam_struct(cam)
+    op32, ids32, rng32 = O._f32(sc.opacity), np.ascontiguousarray(r.ids, np.uint32), np.ascontiguousarray(r.ranges)
+    if ids32.size == 0:
+        ids32 = np.zeros(1, np.uint32)
+    idx8, w32, G64 = np.ascontiguousarray(sc.idx), O._f32(sc.weights), np.ascontiguousarray(dW, np.float64)
+    O.lib().orc_blend_backward(C.byref(c), n, O._p(r.proj.mean2d), O._p(r.proj.conic), O._p(op32), O._p(ids32),
+                               O._p(rng32), lev, K, 64, O._p(idx8), O._p(w32), O._p(G64), O._p(dw), O._p(dop),
+                               O._p(dm2), O._p(dcn))
+    jac = O.project_jacobian(cam, sc.means, sc.scales, sc.quats)
+    dp = np.einsum("nk,nkp->np", np.concatenate([dm2, dcn], 1), jac)
+    dp[~r.proj.visible] = 0
+    return dw, dop, dp[:, :3], dp[:, 3:6], dp[:, 6:]
+
+
+@pytest.mark.parametrize("levels,K,tile", [(1, 2, 16), (1, 8, 16), (1, 4, 8), (3, 4, 16), (2, 4, 16)])
+def test_splat_adjoint_configurations(levels, K, tile):
+    """Every (levels, K) the adjoint supports, on both of its kernels: at one level with 16 x 16
+    tiles the persistent one with dLoss/dW in tensor memory (K = 2: four Gaussians per
+    reduce-scatter, K = 8: two), otherwise one CTA per tile with shared-memory columns."""
+    sc = syn.make_scene(3000, levels, seed=31 + K, mean_kind="uniform", mean_param=1.0, log_scale_mu=-3.2,
+                        log_scale_sigma=0.4, K=K)
+    cam = syn.orbit_camera(150, 110, 4.0, tile=(tile, tile))
+    rng = np.random.default_rng(14)
+    dW = (rng.standard_normal((levels, cam.num_pixels, 64)) * 1e-3).astype(np.float32)
+    out = gpu_splat_backward(sc, cam, dW)
+    ref = oracle_blend_adjoint(sc, cam, dW)
+    for k, r in zip(("dw", "dop", "dm", "ds", "dq"), ref):
+        assert np.abs(r).max() > 0, k
+        close_groupwise(out[k], r, what=k)
+
+
 def test_backward_full_scale_splat_adjoint():
     """100,000 Gaussians at 720x540: feed the same dLoss/dW to the GPU splat backward and the
     oracle's blend adjoint; per-Gaussian gradients must agree."""
