@@ -104,3 +104,21 @@ def test_mlp_decode_host_checks(lib):
     for widths in [(8, 12, 512), (4, 16, 512), (8, 16, 8192)]:
         wb = (C.c_int32 * 3)(*widths)
         assert lib.lsv2_mlp_decode(10, 2, wb, 256, 0, 256, 256, 256, 0, 256, big, 0) == 2, widths
+
+
+def test_query_prepare_host_checks(lib):
+    """lsv2_query_prepare / lsv2_query_prepared reject bad arguments on the host, before any launch."""
+    big = 1 << 24
+    # prepare: null codebook or text, unsupported L, a BF16 query count beyond 512 columns,
+    # unknown compute dtype, workspace too small
+    assert lib.lsv2_query_prepare(3, 64, 512, 0, 1, 4, 256, 1, 256, big, 0) == 1
+    assert lib.lsv2_query_prepare(3, 64, 512, 256, 1, 4, 0, 1, 256, big, 0) == 1
+    assert lib.lsv2_query_prepare(3, 32, 512, 256, 1, 4, 256, 1, 256, big, 0) == 2
+    assert lib.lsv2_query_prepare(3, 64, 512, 256, 96, 4, 256, 1, 256, big, 0) == 2
+    assert lib.lsv2_query_prepare(3, 64, 512, 256, 1, 4, 256, 7, 256, big, 0) == 1
+    assert lib.lsv2_query_prepare(3, 64, 512, 256, 1, 4, 256, 1, 256, 16, 0) == 1
+    # prepared: null map or output, unsupported map dtype with FP32 compute, small workspace
+    assert lib.lsv2_query_prepared(3, 100, 64, 0, 0, 1, 4, 10.0, 256, big, 256, 0, 1, 0, 0) == 1
+    assert lib.lsv2_query_prepared(3, 100, 64, 256, 0, 1, 4, 10.0, 256, big, 0, 0, 1, 0, 0) == 1
+    assert lib.lsv2_query_prepared(3, 100, 64, 256, 1, 1, 4, 10.0, 256, big, 256, 0, 0, 0, 0) == 2
+    assert lib.lsv2_query_prepared(3, 100, 64, 256, 0, 1, 4, 10.0, 256, 16, 256, 0, 1, 0, 0) == 1
