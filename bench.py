@@ -640,14 +640,16 @@ def backward_section(dev, reps: int = 10):
                                "note": "bound by its atomics and per-pixel latency, not HBM"}}
 
 
-def decoder_path_section(dev, v2_render_decode_ms: float | None = None, reps: int = 10):
+def decoder_path_section(dev, v2_render_decode_ms: float | None = None, reps: int = 10,
+                         block_sizes=(1048576, 4194304, -1)):
     """Table 1's contrast on B300: the decoder-based path (LangSplat*: a d = 3 latent per level
     rendered by Eq. 4, then the MLP decoder g_d to 512-d features for every pixel and level) against
     LangSplatV2's render + linear decode (Eq. 7), both at the at-scale frame (300,000 Gaussians,
     three levels, 1440x1080).  The latent render is the library's splat at L = 8; the decoder is
-    lsv2_mlp_decode (cuBLASLt BF16 GEMMs with fused bias/ReLU, 4.67 M rows of the widths
-    8-16-32-64-128-256-256-512), timed as one CUDA graph per row-block size (the decoder launches
-    eight kernels per row block).  L2 flushed between repetitions."""
+    lsv2_mlp_decode over 4.67 M rows of the widths 8-16-32-64-128-256-256-512: one cuBLASLt GEMM per
+    layer over row blocks of the given size, and block_rows -1 (LSV2_MLP_FUSED) the fused
+    tensor-core kernel (one persistent launch, activations on chip).  Each timed as one CUDA graph;
+    L2 flushed between repetitions; the line reports the fastest."""
     import torch
     import lsv2_synth as syn
     from paper_2507_07136_b300.decoder_path import Decoder, DecoderFrame
@@ -677,7 +679,7 @@ def decoder_path_section(dev, v2_render_decode_ms: float | None = None, reps: in
         return float(np.mean(ts))
 
     def graph_of(fn):
-        fn()                       # the first call of each shape plans its GEMMs on the host
+        fn()                       # the first call of each shape plans the library's GEMMs on the host
         torch.cuda.synchronize()
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):
@@ -685,7 +687,7 @@ def decoder_path_section(dev, v2_render_decode_ms: float | None = None, reps: in
         return g
 
     decode_ms, fr = {}, None
-    for block_rows in (262144, 1048576, 4194304):
+    for block_rows in block_sizes:
         fr = DecoderFrame(ds, torch.as_tensor(lat), dec, cam, block_rows=block_rows, device=dev)
         fr.render()
         fr.check()
@@ -702,23 +704,67 @@ def decoder_path_section(dev, v2_render_decode_ms: float | None = None, reps: in
     pk, pk_kind = peaks()
     tf = flop / (decode_ms[best] * 1e-3) / 1e12
     byts = rows * (8 * 4 + dec.out_width * 2)    # the F32 latent map in, the BF16 features out
+    kernel = ("mlp_fused_kernel (tcgen05, persistent, activations in shared memory) + mlp_pack_kernel"
+              if best == "-1" else "cuBLASLt BF16 GEMMs (library) + to_bf16_kernel")
     out = {"workload": "300k Gaussians, 3 levels, 1440x1080; latent d = 3 per level (padded to 8 channels), "
                        "decoder 8-16-32-64-128-256-256-512 (ReLU), BF16 out",
-           "render_ms": render, "decode_ms_by_block_rows": decode_ms, "block_rows": int(best),
+           "render_ms": render, "decode_ms_by_block_rows": decode_ms,
+           "block_rows_note": "-1 = the fused tensor-core kernel; > 0 = library GEMMs over row blocks of that size",
+           "block_rows": int(best),
            "render_decode_ms": render_ms + decode_ms[best],
            "render_decode_fps": 1e3 / (render_ms + decode_ms[best]),
            "decode": {"bound": "tensor", "achieved": tf, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
                       "frac": tf / pk["bf16_tflops"], "algorithmic_flop": flop, "algorithmic_bytes": byts,
                       "hbm_floor_ms": byts / pk["hbm_gbs"] / 1e6, "peak_source": pk_kind + " (burst)",
-                      "kernel": "cuBLASLt BF16 GEMMs (library) + to_bf16_kernel"},
+                      "kernel": kernel},
            "paper_a100_ms": {"LangSplat* rendering": 2.0, "LangSplat* decoding": 83.1,
                              "LangSplatV2 rendering": 2.0, "LangSplatV2 decoding": 0.1}}
+    if "-1" in decode_ms and len(decode_ms) > 1:
+        lib_best = min((v for k, v in decode_ms.items() if k != "-1"))
+        out["fused_kernel"] = {"ms": decode_ms["-1"], "library_ms": lib_best,
+                               "tflops": flop / (decode_ms["-1"] * 1e-3) / 1e12,
+                               "frac": flop / (decode_ms["-1"] * 1e-3) / 1e12 / pk["bf16_tflops"],
+                               "workspace_bytes": dec.workspace_bytes(rows, 0, -1),
+                               "library_workspace_bytes": dec.workspace_bytes(rows, 0, int(min(
+                                   (k for k in decode_ms if k != "-1"), key=decode_ms.get)))}
     if v2_render_decode_ms is not None:
         out["langsplatv2_render_decode_ms"] = v2_render_decode_ms
         out["decoder_over_v2"] = out["render_decode_ms"] / v2_render_decode_ms
     del fr, F
     torch.cuda.empty_cache()
     return out
+
+
+def mlp_profile(dev, steps: int, warmup: int, rows: int = 1 << 20):
+    """The decoder MLP alone (the workload's widths 8-16-32-64-128-256-256-512) on `rows` synthetic
+    latent rows (standard normal in the 3 latent channels): the fused kernel (block_rows -1,
+    LSV2_MLP_FUSED), eager launches timed with CUDA events.  A small case for a capture of the fused
+    kernel (1 GB of output)."""
+    import torch
+    import lsv2_synth as syn
+    from paper_2507_07136_b300.decoder_path import LATENT_CHANNELS, Decoder
+    dec = Decoder(syn.decoder_mlp(), device=dev)
+    gen = torch.Generator(device=dev).manual_seed(7)
+    x = torch.zeros((rows, LATENT_CHANNELS), device=dev)
+    x[:, :3] = torch.randn((rows, 3), generator=gen, device=dev)
+    y = torch.empty((rows, dec.out_width), dtype=torch.bfloat16, device=dev)
+    ws = torch.empty(dec.workspace_bytes(rows, 0, -1), dtype=torch.uint8, device=dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+    ts = []
+    for i in range(warmup + steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        dec(x, y, ws, -1, None, st)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if i >= warmup:
+            ts.append(a.elapsed_time(b))
+    if int(st.item()) != 0:
+        raise RuntimeError(f"device status {int(st.item())}")
+    ms = float(np.mean(ts))
+    return {"rows": rows, "ms": ms, "tflops": rows * dec.flops_per_row() / (ms * 1e-3) / 1e12,
+            "device_gb": round(torch.cuda.max_memory_allocated(dev) / 1e9, 2)}
 
 
 # ----------------------------------------------------------------------------- batched views
@@ -939,7 +985,7 @@ def main():
     ap.add_argument("--no-ablation", action="store_true", help="skip the sparse/dense and K speed ablation")
     ap.add_argument("--no-decoder-path", action="store_true",
                     help="skip the decoder-based (LangSplat*) comparison measurement")
-    ap.add_argument("--profile", choices=["project", "bin", "splat", "decode", "query", "query32", "backward", "sparsify", "decoder",
+    ap.add_argument("--profile", choices=["project", "bin", "splat", "decode", "query", "query32", "backward", "sparsify", "decoder", "mlp",
                              "batched"], default=None,
                     help="for a profiler capture: prepare the at-scale frame, then run only this stage "
                          "(--warmup + --steps launches) with only the buffers it needs; `backward` runs the "
@@ -982,6 +1028,9 @@ def main():
     if args.profile == "decoder":
         r = decoder_path_section(dev, reps=args.steps)
         print(json.dumps({"profile": "decoder", **r}), flush=True)
+        return
+    if args.profile == "mlp":
+        print(json.dumps({"profile": "mlp", **mlp_profile(dev, args.steps, args.warmup)}), flush=True)
         return
     if args.profile == "batched":
         from paper_2507_07136_b300.views import ViewsBatch

@@ -436,9 +436,13 @@ lsv2_status lsv2_splat_backward(const lsv2_camera* cam, int64_t n, const float* 
                                 float* dw, float* dopacity, float* dmeans, float* dscales,
                                 float* dquats, int32_t* dev_status, void* stream);
 
-/* Workspace for lsv2_mlp_decode (0 for invalid arguments): two activation buffers of one row
- * block at the widest hidden layer, a BF16 copy of an F32 input block, and 32 MiB for the
- * library GEMM's own scratch. */
+/* block_rows value of lsv2_mlp_decode that selects the fused tensor-core kernel. */
+#define LSV2_MLP_FUSED (-1)
+
+/* Workspace for lsv2_mlp_decode (0 for invalid arguments, or for LSV2_MLP_FUSED with widths the
+ * fused kernel does not take).  block_rows >= 0: two activation buffers of one row block at the
+ * widest hidden layer, a BF16 copy of an F32 input block, and 32 MiB for the library GEMM's own
+ * scratch.  LSV2_MLP_FUSED: the packed weights only (under 2 MiB for any row count). */
 size_t lsv2_mlp_decode_workspace_bytes(int64_t rows, int32_t n_layers, const int32_t* widths,
                                        int32_t x_dtype, int64_t block_rows);
 
@@ -449,21 +453,32 @@ size_t lsv2_mlp_decode_workspace_bytes(int64_t rows, int32_t n_layers, const int
  *                   y[r] = h_{n_layers-1} W_{n_layers-1} + b_{n_layers-1}.
  *   widths   int32[n_layers + 1], HOST memory: w_0 (input) .. w_n (output); each a multiple of
  *            8 in [8, 4096] (pad a narrower input with zero columns and zero weight rows)
- *   x        [rows][w_0]  dtype x_dtype (F32: rounded to BF16 per block first; or BF16)
+ *   x        [rows][w_0]  dtype x_dtype (F32, rounded to BF16 as it is read; or BF16)
  *   weights  bf16, the W_l one after another, each row-major [w_l][w_{l+1}]
  *   biases   bf16, the b_l one after another, each [w_{l+1}]
  *   y        bf16 [rows][w_n]
- * Each layer is a library GEMM (cuBLASLt) with BF16 operands, FP32 accumulation and a fused
- * bias (+ ReLU) epilogue; intermediate activations are rounded to BF16.  Rows go in blocks of
- * block_rows (a multiple of 128; 0 = 1,048,576), which bounds the intermediate buffers.  All
- * pointers 16-byte aligned.  Returns LSV2_ERR_UNSUPPORTED for a width outside the rule,
- * LSV2_ERR_CUDA if a GEMM cannot be planned or launched.  Allocates nothing; capturable in
- * a CUDA graph after one uncaptured call of the same shapes (the first call of a shape asks
- * the library's heuristic for its algorithm on the host). */
+ * BF16 operands, FP32 accumulation, bias (+ ReLU) applied to the FP32 sum, every layer's output
+ * rounded to BF16.  Two implementations, chosen by block_rows:
+ *   >= 0             each layer a library GEMM (cuBLASLt) with a fused bias (+ ReLU) epilogue,
+ *                    rows in blocks of block_rows (a multiple of 128; 0 = 1,048,576), which bounds
+ *                    the intermediate activation buffers.  The faster of the two on B300 at the
+ *                    workload's widths (it streams every activation through HBM, but at full
+ *                    bandwidth).
+ *   LSV2_MLP_FUSED   one persistent tcgen05 kernel, the hidden activations kept on chip, the
+ *                    weights repacked into the workspace on every call; for w_0 <= 32, hidden
+ *                    widths that are multiples of 16 up to 256 and an output width that is a
+ *                    multiple of 16 (at most 16 products of <= 256 outputs, at most 4,800 biases),
+ *                    else LSV2_ERR_UNSUPPORTED.  A workspace under 2 MiB instead of about 1 GiB.
+ * All pointers 16-byte aligned.  Returns LSV2_ERR_UNSUPPORTED for a width outside the rule,
+ * LSV2_ERR_CUDA if a launch fails or a GEMM cannot be planned.  A device wait of the fused
+ * kernel that runs out (lsv2_set_wait_limit_ns) records LSV2_ERR_TIMEOUT in *dev_status (may
+ * be NULL; the library path does not use it).  Allocates nothing; capturable in a CUDA graph
+ * (the library path after one uncaptured call of the same shapes: its first call of a shape
+ * asks the library's heuristic for an algorithm on the host). */
 lsv2_status lsv2_mlp_decode(int64_t rows, int32_t n_layers, const int32_t* widths, const void* x,
                             int32_t x_dtype, const void* weights, const void* biases, void* y,
                             int64_t block_rows, void* workspace, size_t workspace_bytes,
-                            void* stream);
+                            int32_t* dev_status, void* stream);
 
 /* Rate probes of the units that bind the splat's blend, for roofline denominators measured on the
  * device at hand (no counterpart in the paper).  lsv2_rate_probe launches `blocks` CTAs of 512

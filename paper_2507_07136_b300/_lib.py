@@ -15,6 +15,7 @@ I32, I64, F32, SZ = C.c_int32, C.c_int64, C.c_float, C.c_size_t
 
 LSV2_F32 = 0
 LSV2_BF16 = 1
+LSV2_MLP_FUSED = -1   # block_rows of lsv2_mlp_decode selecting the fused tensor-core kernel
 LSV2_POST_LERF = 0
 LSV2_POST_BLENDED = 1
 
@@ -80,7 +81,7 @@ _SIGS = {
     "lsv2_l1_decode_backward": ([I32, I64, I32, I32, P, P, P, P, P, P, P, P], I32),
     "lsv2_splat_backward_workspace_bytes": ([I64], SZ),
     "lsv2_mlp_decode_workspace_bytes": ([I64, I32, P, I32, I64], SZ),
-    "lsv2_mlp_decode": ([I64, I32, P, P, I32, P, P, P, I64, P, SZ, P], I32),
+    "lsv2_mlp_decode": ([I64, I32, P, P, I32, P, P, P, I64, P, SZ, P, P], I32),
     "lsv2_splat_backward": ([P, I64, P, P, P, P, P, P, I32, I32, I32, P, P, P, P, P, P, SZ, P, P, P, P, P, P, P],
                             I32),
 }
@@ -275,5 +276,7 @@ def lsv2_mlp_decode_workspace_bytes(rows, n_layers, widths, x_dtype, block_rows=
     return lib().lsv2_mlp_decode_workspace_bytes(rows, n_layers, widths, x_dtype, block_rows)
 
 
-def lsv2_mlp_decode(rows, n_layers, widths, x, x_dtype, weights, biases, y, block_rows, ws, ws_bytes, stream):
-    call("lsv2_mlp_decode", rows, n_layers, widths, x, x_dtype, weights, biases, y, block_rows, ws, ws_bytes, stream)
+def lsv2_mlp_decode(rows, n_layers, widths, x, x_dtype, weights, biases, y, block_rows, ws, ws_bytes, dev_status,
+                    stream):
+    call("lsv2_mlp_decode", rows, n_layers, widths, x, x_dtype, weights, biases, y, block_rows, ws, ws_bytes,
+         dev_status, stream)

@@ -3,13 +3,14 @@
 // CLIP space, the stage the paper measures as LangSplat*'s bottleneck.  Each layer is a plain
 // GEMM with a bias (+ ReLU) epilogue,
 //     H_{l+1} = act(H_l W_l + b_l),   H_l rows x w_l,  W_l w_l x w_{l+1},  act = ReLU except after the last,
-// with BF16 operands, biases and activations and FP32 accumulation, run by cuBLASLt (a library GEMM:
-// nothing about these layers is specific to the method).  Rows are processed in blocks that bound
-// the two intermediate activation buffers (smaller blocks keep them in L2 but make the GEMMs too
-// small to fill the GPU: measured at 4.67 M rows, 2^20 rows per block 3.33 ms, 2^18 3.64, 2^16
-// 4.86); the buffers, the BF16 copy of
-// an FP32 input block and cuBLASLt's own workspace all live in the caller's workspace, so a call
-// allocates nothing and can be captured in a CUDA graph.
+// with BF16 operands, biases and activations and FP32 accumulation, run by cuBLASLt (a library
+// GEMM: nothing about these layers is specific to the method), or on request (block_rows ==
+// LSV2_MLP_FUSED) by the fused tensor-core kernel of mlp_fused.cu.  The library path processes
+// rows in blocks that bound the two intermediate activation buffers (smaller blocks keep them in
+// L2 but make the GEMMs too small to fill the GPU: measured at 4.67 M rows, 2^20 rows per block
+// 3.33 ms, 2^18 3.64, 2^16 4.86); the buffers, the BF16 copy of an FP32 input block and
+// cuBLASLt's own workspace all live in the caller's workspace, so a call allocates nothing and
+// can be captured in a CUDA graph.
 #include <cublasLt.h>
 #include <cuda_bf16.h>
 
@@ -18,6 +19,7 @@
 #include <tuple>
 
 #include "device.cuh"
+#include "mlp_fused.cuh"
 
 namespace lsv2 {
 namespace {
@@ -147,6 +149,9 @@ __global__ void to_bf16_kernel(const float4* __restrict__ x, uint2* __restrict__
     }
 }
 
+// block_rows == LSV2_MLP_FUSED asks for the fused tensor-core kernel.
+bool fused_requested(int64_t block_rows) { return block_rows == LSV2_MLP_FUSED; }
+
 }  // namespace
 }  // namespace lsv2
 
@@ -155,18 +160,25 @@ using namespace lsv2;
 extern "C" size_t lsv2_mlp_decode_workspace_bytes(int64_t rows, int32_t n_layers, const int32_t* widths,
                                                   int32_t x_dtype, int64_t block_rows)
 {
-    if (rows < 0 || n_layers < 1 || n_layers > kMaxLayers || !widths || block_rows < 0) return 0;
+    if (rows < 0 || n_layers < 1 || n_layers > kMaxLayers || !widths || (block_rows < 0 && !fused_requested(block_rows)))
+        return 0;
     if (x_dtype != LSV2_F32 && x_dtype != LSV2_BF16) return 0;
+    if (fused_requested(block_rows)) {
+        MlpPlan plan;
+        size_t image = 0;
+        return mlp_fused_plan(n_layers, widths, &plan, &image) ? a256(image) : 0;
+    }
     const Sizes z = sizes(rows, n_layers, widths, block_rows, x_dtype == LSV2_F32);
     return 2 * z.act + z.xin + kLtWorkspace;
 }
 
 extern "C" lsv2_status lsv2_mlp_decode(int64_t rows, int32_t n_layers, const int32_t* widths, const void* x,
                                        int32_t x_dtype, const void* weights, const void* biases, void* y,
-                                       int64_t block_rows, void* workspace, size_t workspace_bytes, void* stream)
+                                       int64_t block_rows, void* workspace, size_t workspace_bytes,
+                                       int32_t* dev_status, void* stream)
 {
     if (rows < 0 || n_layers < 1 || n_layers > kMaxLayers || !widths || !x || !weights || !biases || !y ||
-        !workspace || block_rows < 0 || block_rows % 128 != 0)
+        !workspace || (block_rows < 0 && !fused_requested(block_rows)) || (block_rows > 0 && block_rows % 128 != 0))
         return LSV2_ERR_INVALID_ARGUMENT;
     if (x_dtype != LSV2_F32 && x_dtype != LSV2_BF16) return LSV2_ERR_INVALID_ARGUMENT;
     for (int l = 0; l <= n_layers; ++l)
@@ -175,6 +187,17 @@ extern "C" lsv2_status lsv2_mlp_decode(int64_t rows, int32_t n_layers, const int
          reinterpret_cast<uintptr_t>(biases) | reinterpret_cast<uintptr_t>(workspace)) & 15u)
         return LSV2_ERR_INVALID_ARGUMENT;
     const bool x_f32 = x_dtype == LSV2_F32;
+    if (fused_requested(block_rows)) {
+        MlpPlan plan;
+        size_t image = 0;
+        if (!mlp_fused_plan(n_layers, widths, &plan, &image)) return LSV2_ERR_UNSUPPORTED;
+        if (workspace_bytes < a256(image)) return LSV2_ERR_INVALID_ARGUMENT;
+        if (rows == 0) return LSV2_OK;
+        return launch_mlp_fused(plan, rows, x, x_f32, weights, biases, y, workspace, dev_status,
+                                static_cast<cudaStream_t>(stream)) == cudaSuccess
+                   ? LSV2_OK
+                   : LSV2_ERR_CUDA;
+    }
     if (workspace_bytes < lsv2_mlp_decode_workspace_bytes(rows, n_layers, widths, x_dtype, block_rows))
         return LSV2_ERR_INVALID_ARGUMENT;
     if (rows == 0) return LSV2_OK;

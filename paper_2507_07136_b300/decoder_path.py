@@ -10,7 +10,9 @@ the linear decode of Eq. 7.  Here:
   so the splat accumulates exactly sum_i f_i alpha_i T_i into channels 0..2 and channels 3..7
   stay zero;
 * the decode is ``lsv2_mlp_decode`` over all levels' pixels as rows, the latent's 3 channels
-  padded to 8 (zero columns in x, zero rows in the first weight matrix).
+  padded to 8 (zero columns in x, zero rows in the first weight matrix): by default one library
+  GEMM per layer over row blocks, or, with ``block_rows=L.LSV2_MLP_FUSED``, the fused tensor-core
+  kernel (every layer on tcgen05, the hidden activations kept on chip, a workspace of < 2 MB).
 
 PyTorch holds the buffers; every step runs in the CUDA library.
 """
@@ -71,12 +73,16 @@ class Decoder:
     def workspace_bytes(self, rows: int, x_dtype: int = L.LSV2_F32, block_rows: int = 0) -> int:
         return L.lsv2_mlp_decode_workspace_bytes(rows, self.n_layers, self.widths, x_dtype, block_rows)
 
-    def __call__(self, x: torch.Tensor, y: torch.Tensor, ws: torch.Tensor, block_rows: int = 0, stream=None):
-        """y [rows, out] (BF16) = g_d(x [rows, LATENT_CHANNELS] (F32 or BF16))."""
+    def __call__(self, x: torch.Tensor, y: torch.Tensor, ws: torch.Tensor, block_rows: int = 0, stream=None,
+                 status: torch.Tensor | None = None):
+        """y [rows, out] (BF16) = g_d(x [rows, LATENT_CHANNELS] (F32 or BF16)).  block_rows >= 0: library
+        GEMMs over blocks of that many rows (0: 2^20); L.LSV2_MLP_FUSED: the fused tensor-core
+        kernel.  status: an int32 device word that records a device-side timeout (optional)."""
         rows = x.numel() // LATENT_CHANNELS
         x_dt = L.LSV2_BF16 if x.dtype == torch.bfloat16 else L.LSV2_F32
         L.lsv2_mlp_decode(rows, self.n_layers, self.widths, _ptr(x), x_dt, _ptr(self.weights), _ptr(self.biases),
-                          _ptr(y), block_rows, _ptr(ws), ws.numel(), _stream(stream))
+                          _ptr(y), block_rows, _ptr(ws), ws.numel(), _ptr(status),
+                          _stream(stream))
 
 
 class DecoderFrame:
@@ -114,7 +120,7 @@ class DecoderFrame:
 
     def decode(self, out: torch.Tensor, stream=None):
         """out bf16 [levels, P, D] = g_d(latent map)."""
-        self.decoder(self.frame.coeff, out, self.ws, self.block_rows, stream)
+        self.decoder(self.frame.coeff, out, self.ws, self.block_rows, stream, self.frame.status)
 
     def check(self):
         self.frame.check()

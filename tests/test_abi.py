@@ -82,28 +82,46 @@ def test_wait_limit_setting_round_trips(lib):
 
 
 def test_mlp_decode_host_checks(lib):
-    """Workspace sizing and the host-side rejections of lsv2_mlp_decode (all before any CUDA call)."""
+    """Workspace sizing, the choice between the fused kernel and the library GEMMs, and the host-side
+    rejections of lsv2_mlp_decode (all before any CUDA call)."""
     w = (C.c_int32 * 8)(8, 16, 32, 64, 128, 256, 256, 512)
     lt = 32 << 20
-    # two activation buffers of a 1,048,576-row block at width 256, plus the BF16 copy of an F32 input
+    # LSV2_MLP_FUSED: only the packed weights, per part its ceil(K / 64) chunks of N x 128 bytes
+    # (the last layer in two parts of 256), for any row count
+    fused = L.LSV2_MLP_FUSED
+    image = (16 + 32 + 64 + 128) * 128 + 2 * 256 * 128 + 3 * 4 * 256 * 128
+    for rows in (1, 1000, 1 << 22):
+        for dt in (0, 1):
+            assert L.lsv2_mlp_decode_workspace_bytes(rows, 7, w, dt, fused) == image
+    # widths the fused kernel does not take: a hidden width not a multiple of 16, one above 256,
+    # an output not a multiple of 16, an input above 32
+    for ws in [(8, 24, 512), (8, 272, 512), (8, 64, 520), (40, 64, 512)]:
+        wb = (C.c_int32 * 3)(*ws)
+        assert L.lsv2_mlp_decode_workspace_bytes(10, 2, wb, 1, fused) == 0, ws
+        assert lib.lsv2_mlp_decode(10, 2, wb, 256, 1, 256, 256, 256, fused, 256, 1 << 30, 0, 0) == 2, ws
+    # block_rows >= 0: two activation buffers of a block at width 256, plus the BF16 copy of an F32 input
     blk = 1 << 20
-    assert L.lsv2_mlp_decode_workspace_bytes(1 << 22, 7, w, 0, 0) == 2 * blk * 256 * 2 + blk * 8 * 2 + lt
-    assert L.lsv2_mlp_decode_workspace_bytes(1 << 22, 7, w, 1, 0) == 2 * blk * 256 * 2 + lt
+    for b in (0, blk):
+        assert L.lsv2_mlp_decode_workspace_bytes(1 << 22, 7, w, 0, b) == 2 * blk * 256 * 2 + blk * 8 * 2 + lt
+        assert L.lsv2_mlp_decode_workspace_bytes(1 << 22, 7, w, 1, b) == 2 * blk * 256 * 2 + lt
     assert L.lsv2_mlp_decode_workspace_bytes(1000, 7, w, 1, 0) == 2 * 512000 + lt
     assert L.lsv2_mlp_decode_workspace_bytes(1 << 22, 7, w, 1, 1024) == 2 * 1024 * 256 * 2 + lt
+    assert L.lsv2_mlp_decode_workspace_bytes(1 << 22, 7, w, 1, -2) == 0
     assert L.lsv2_mlp_decode_workspace_bytes(-1, 7, w, 0, 0) == 0
     assert L.lsv2_mlp_decode_workspace_bytes(10, 0, w, 0, 0) == 0
     assert L.lsv2_mlp_decode_workspace_bytes(10, 7, w, 2, 0) == 0
     big = 1 << 30
-    ok = [10, 7, w, 256, 0, 256, 256, 256, 0, 256, big, 0]
-    assert lib.lsv2_mlp_decode(0, 7, w, 256, 0, 256, 256, 256, 0, 256, big, 0) == 0   # no rows: nothing to do
-    for i, bad in [(3, 0), (3, 260), (4, 5), (8, 100), (8, -128), (10, 1000)]:
+    ok = [10, 7, w, 256, 0, 256, 256, 256, 0, 256, big, 0, 0]
+    assert lib.lsv2_mlp_decode(0, 7, w, 256, 0, 256, 256, 256, 0, 256, big, 0, 0) == 0   # no rows: nothing to do
+    assert lib.lsv2_mlp_decode(0, 7, w, 256, 0, 256, 256, 256, fused, 256, image, 0, 0) == 0
+    assert lib.lsv2_mlp_decode(10, 7, w, 256, 0, 256, 256, 256, fused, 256, image - 1, 0, 0) == 1
+    for i, bad in [(3, 0), (3, 260), (4, 5), (8, 100), (8, -128), (8, -2), (10, 1000)]:
         args = list(ok)
         args[i] = bad
         assert lib.lsv2_mlp_decode(*args) == 1, (i, bad)
     for widths in [(8, 12, 512), (4, 16, 512), (8, 16, 8192)]:
         wb = (C.c_int32 * 3)(*widths)
-        assert lib.lsv2_mlp_decode(10, 2, wb, 256, 0, 256, 256, 256, 0, 256, big, 0) == 2, widths
+        assert lib.lsv2_mlp_decode(10, 2, wb, 256, 0, 256, 256, 256, 0, 256, big, 0, 0) == 2, widths
 
 
 def test_query_prepare_host_checks(lib):

@@ -5,8 +5,13 @@
   scales with the sum of magnitudes, not with the possibly cancelled result); channels 3..7 zero.
 * lsv2_mlp_decode on integer-valued inputs, weights and biases whose every intermediate is an
   integer below 256 (exact in BF16, exact in FP32 accumulation): equal to the oracle bit for bit,
-  over several row blocks and a ragged tail -- a check of the layouts, bias, ReLU placement and
-  blocking with no rounding in the way.
+  over several row blocks and a ragged tail, on both implementations -- a check of the layouts,
+  bias, ReLU placement and blocking with no rounding in the way.
+* The fused tensor-core kernel (LSV2_MLP_FUSED) on integer-valued MLPs of other shapes, each equal
+  to the oracle bit for bit: widths of 16 mod 32 (the epilogue's last piece is 16 columns), a
+  last layer cut into parts of 256 and 144 outputs, a single layer, an input of 24 columns, and the
+  workload's seven layers over enough rows that every CTA of the persistent grid runs several
+  tile pairs (with a ragged tail and the BF16 input).
 * lsv2_mlp_decode with the random decoder of the workload: within the BF16 bound of the FP64
   oracle.  The GPU rounds the input and each of the seven layer outputs to BF16 (relative 2^-9
   each); eight such roundings add in quadrature to about sqrt(8) 2^-9 = 0.55% of a row's norm.
@@ -82,7 +87,7 @@ def integer_decoder(widths, fan_in, rng):
     return layers
 
 
-@pytest.mark.parametrize("block_rows", [0, 1024])
+@pytest.mark.parametrize("block_rows", [0, 1024, L.LSV2_MLP_FUSED])
 def test_mlp_exact_on_integers(block_rows):
     rng = np.random.default_rng(21)
     widths = (LATENT_CHANNELS, 64, 128, 512)
@@ -106,6 +111,69 @@ def test_mlp_exact_on_integers(block_rows):
     assert torch.equal(y16, y)
 
 
+def pack_layers(layers):
+    W = torch.cat([torch.as_tensor(np.asarray(w, np.float32)).reshape(-1) for w, _ in layers])
+    b = torch.cat([torch.as_tensor(np.asarray(bb, np.float32)).reshape(-1) for _, bb in layers])
+    return W.to("cuda", torch.bfloat16).contiguous(), b.to("cuda", torch.bfloat16).contiguous()
+
+
+def run_mlp(layers, x, block_rows=0, x_dtype=torch.float32):
+    """lsv2_mlp_decode through the C ABI on host arrays; returns the output as float64 and the status."""
+    widths = [x.shape[1]] + [int(w.shape[1]) for w, _ in layers]
+    wc = (C.c_int32 * len(widths))(*widths)
+    W, b = pack_layers(layers)
+    rows = x.shape[0]
+    xd = torch.as_tensor(x, device="cuda").to(x_dtype).contiguous()
+    dt = L.LSV2_BF16 if x_dtype == torch.bfloat16 else L.LSV2_F32
+    y = torch.full((rows, widths[-1]), float("nan"), dtype=torch.bfloat16, device="cuda")
+    ws = torch.empty(max(L.lsv2_mlp_decode_workspace_bytes(rows, len(layers), wc, dt, block_rows), 16),
+                     dtype=torch.uint8, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    L.lsv2_mlp_decode(rows, len(layers), wc, xd.data_ptr(), dt, W.data_ptr(), b.data_ptr(), y.data_ptr(),
+                      block_rows, ws.data_ptr(), ws.numel(), st.data_ptr(), 0)
+    torch.cuda.synchronize()
+    return y.float().cpu().numpy().astype(np.float64), int(st.item())
+
+
+@pytest.mark.parametrize("widths,fan_in,x_max,rows", [
+    ((8, 48, 80, 400), 4, 2, 3 * 1024 + 77),         # widths of 16 mod 32; last layer 256 + 144
+    ((8, 64), 4, 2, 1000),                           # one layer: input straight to output
+    ((24, 256, 256, 512), 2, 2, 2 * 1024 + 5),       # input of 24 columns, zero-padded to 32
+    ((8, 16, 32, 64, 128, 256, 256, 512), 2, 1, 148 * 128 * 5 + 77),   # several tile pairs per CTA
+])
+def test_mlp_fused_exact_on_integers(widths, fan_in, x_max, rows):
+    rng = np.random.default_rng(24)
+    layers = integer_decoder(widths, fan_in, rng)
+    x = rng.integers(-x_max, x_max + 1, (rows, widths[0])).astype(np.float32)
+    ref = O.mlp_decode(x, layers)
+    assert np.abs(ref).max() <= 256 and np.all(ref == np.round(ref))
+    got, st = run_mlp(layers, x, block_rows=L.LSV2_MLP_FUSED)
+    assert st == 0
+    np.testing.assert_array_equal(got, ref)
+    got16, st = run_mlp(layers, x, block_rows=L.LSV2_MLP_FUSED, x_dtype=torch.bfloat16)
+    assert st == 0
+    np.testing.assert_array_equal(got16, ref)
+
+
+def test_mlp_fused_and_library_agree_on_the_workload_decoder():
+    """The fused kernel and the library GEMMs round the same FP32 sums to BF16 after every layer and
+    differ only in summation order: both within the BF16 bound of the FP64 oracle, and of each other."""
+    rng = np.random.default_rng(25)
+    layers = syn.decoder_mlp()
+    rows = 4096 + 33
+    x = np.zeros((rows, LATENT_CHANNELS), np.float32)
+    x[:, :3] = rng.standard_normal((rows, 3))
+    W0 = np.concatenate([layers[0][0], np.zeros((LATENT_CHANNELS - 3, layers[0][0].shape[1]), np.float32)])
+    padded = [(W0, layers[0][1])] + list(layers[1:])
+    fused, st = run_mlp(padded, x, block_rows=L.LSV2_MLP_FUSED)
+    assert st == 0
+    lib_, _ = run_mlp(padded, x, block_rows=1024)
+    ref = O.mlp_decode(x[:, :3], layers)
+    assert_decoder_close(fused, ref, "fused")
+    assert_decoder_close(lib_, ref, "library")
+    assert_decoder_close(fused, lib_, "fused vs library")
+
+
 def test_mlp_random_decoder_against_oracle():
     rng = np.random.default_rng(22)
     layers = syn.decoder_mlp()
@@ -115,7 +183,7 @@ def test_mlp_random_decoder_against_oracle():
     ref = O.mlp_decode(x[:, :3], layers)
     dec = Decoder(layers)
     y = torch.empty((rows, 512), dtype=torch.bfloat16, device="cuda")
-    for block_rows in (0, 1024):
+    for block_rows in (0, 1024, L.LSV2_MLP_FUSED):
         ws = torch.empty(dec.workspace_bytes(rows, L.LSV2_F32, block_rows), dtype=torch.uint8, device="cuda")
         y.fill_(float("nan"))
         dec(torch.as_tensor(x, device="cuda"), y, ws, block_rows)
@@ -129,16 +197,16 @@ def test_mlp_empty_and_rejected_calls():
     x = torch.zeros((1, LATENT_CHANNELS), device="cuda")
     y = torch.zeros((1, 512), dtype=torch.bfloat16, device="cuda")
     L.lsv2_mlp_decode(0, dec.n_layers, dec.widths, x.data_ptr(), L.LSV2_F32, dec.weights.data_ptr(),
-                      dec.biases.data_ptr(), y.data_ptr(), 0, ws.data_ptr(), ws.numel(), 0)
+                      dec.biases.data_ptr(), y.data_ptr(), 0, ws.data_ptr(), ws.numel(), 0, 0)
     assert float(y.float().abs().sum()) == 0.0
     with pytest.raises(L.LSV2Error) as e:   # a workspace one byte short
         L.lsv2_mlp_decode(1, dec.n_layers, dec.widths, x.data_ptr(), L.LSV2_F32, dec.weights.data_ptr(),
-                          dec.biases.data_ptr(), y.data_ptr(), 0, ws.data_ptr(), dec.workspace_bytes(1) - 1, 0)
+                          dec.biases.data_ptr(), y.data_ptr(), 0, ws.data_ptr(), dec.workspace_bytes(1) - 1, 0, 0)
     assert e.value.code == L.LSV2_ERR_INVALID_ARGUMENT
     bad = (C.c_int32 * 3)(8, 12, 512)       # a width that is not a multiple of 8
     with pytest.raises(L.LSV2Error) as e:
         L.lsv2_mlp_decode(1, 2, bad, x.data_ptr(), L.LSV2_F32, dec.weights.data_ptr(), dec.biases.data_ptr(),
-                          y.data_ptr(), 0, ws.data_ptr(), ws.numel(), 0)
+                          y.data_ptr(), 0, ws.data_ptr(), ws.numel(), 0, 0)
     assert e.value.code == L.LSV2_ERR_UNSUPPORTED
 
 

@@ -156,3 +156,26 @@ def test_l1_decode_backward_wait_expires_and_recovers():
                                   _ptr(dW), _ptr(dS), _ptr(fr.status), _stream(None))
 
     expire_then_recover(fr, run, [loss, dW, dS], inexact=(0, 2))
+
+
+def test_mlp_fused_wait_expires_and_recovers():
+    """The fused tensor-core MLP decoder (weight ring, MMA warp, two slots of epilogue warps)."""
+    from paper_2507_07136_b300.decoder_path import LATENT_CHANNELS, Decoder
+
+    dec = Decoder(syn.decoder_mlp())
+    rows = 148 * 128 * 2 + 77
+    rng = np.random.default_rng(26)
+    x = torch.zeros((rows, LATENT_CHANNELS), device="cuda")
+    x[:, :3] = torch.as_tensor(rng.standard_normal((rows, 3)), dtype=torch.float32, device="cuda")
+    y = torch.empty((rows, dec.out_width), dtype=torch.bfloat16, device="cuda")
+    ws = torch.empty(dec.workspace_bytes(rows, L.LSV2_F32, L.LSV2_MLP_FUSED), dtype=torch.uint8, device="cuda")
+
+    class Holder:
+        status = torch.zeros(1, dtype=torch.int32, device="cuda")
+
+        def check(self):
+            torch.cuda.synchronize()
+            assert int(self.status.item()) == 0
+
+    h = Holder()
+    expire_then_recover(h, lambda: dec(x, y, ws, L.LSV2_MLP_FUSED, None, h.status), [y])
