@@ -155,6 +155,21 @@ def test_mlp_fused_exact_on_integers(widths, fan_in, x_max, rows):
     np.testing.assert_array_equal(got16, ref)
 
 
+@pytest.mark.parametrize("rows", [1, 127, 128, 129, 148 * 128, 148 * 128 + 1])
+def test_mlp_fused_row_counts(rows):
+    """Tile and grid boundaries of the persistent kernel: a single row (grid of one CTA, one
+    ragged tile), one row short of / exactly / one past a 128-row tile, exactly one tile per SM,
+    and one tile past that (the first CTA takes a second tile)."""
+    rng = np.random.default_rng(27)
+    widths = (8, 16, 32, 64, 128, 256, 256, 512)
+    layers = integer_decoder(widths, 2, rng)
+    x = rng.integers(-1, 2, (rows, 8)).astype(np.float32)
+    ref = O.mlp_decode(x, layers)
+    got, st = run_mlp(layers, x, block_rows=L.LSV2_MLP_FUSED)
+    assert st == 0
+    np.testing.assert_array_equal(got, ref)
+
+
 def test_mlp_fused_and_library_agree_on_the_workload_decoder():
     """The fused kernel and the library GEMMs round the same FP32 sums to BF16 after every layer and
     differ only in summation order: both within the BF16 bound of the FP64 oracle, and of each other."""
