@@ -74,20 +74,6 @@ struct MlpArgs {
     uint64_t wait_ns;
 };
 
-// try_wait with a suspend-time hint: the thread sleeps until the phase completes or about
-// hint_ns pass, instead of spinning (the waiting warps leave the issue slots to the working ones).
-__device__ __forceinline__ bool mbar_sleep(uint32_t bar, uint32_t parity, uint32_t hint_ns)
-{
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(bar), "r"(parity), "r"(hint_ns)
-        : "memory");
-    return done != 0;
-}
-
 // Bounded wait of one thread: false once another thread gave up (abort flag) or after limit_ns
 // (then it raises the flag).  The first check is a non-blocking test.
 __device__ __forceinline__ bool mw(uint32_t bar, uint32_t parity, volatile int* abort, uint64_t limit_ns)
@@ -100,7 +86,7 @@ __device__ __forceinline__ bool mw(uint32_t bar, uint32_t parity, volatile int* 
             *abort = 1;
             return false;
         }
-        if (mbar_sleep(bar, parity, 20000u)) return true;
+        if (tc::mbar_sleep(bar, parity, 20000u)) return true;
     }
 }
 

@@ -113,6 +113,20 @@ __device__ __forceinline__ bool mbar_try(uint32_t mbar_saddr, uint32_t parity)
     return done != 0;
 }
 
+// try_wait with a suspend-time hint: a thread whose phase is incomplete sleeps until it completes
+// or about hint_ns pass, instead of spinning (waiting warps leave the issue slots to working ones).
+__device__ __forceinline__ bool mbar_sleep(uint32_t mbar_saddr, uint32_t parity, uint32_t hint_ns)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar_saddr), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return done != 0;
+}
+
 // Non-blocking test of the phase with the given parity (acquire semantics): unlike try_wait it
 // never suspends the thread, so it reports the state at the moment of the check.
 __device__ __forceinline__ bool mbar_test(uint32_t mbar_saddr, uint32_t parity)
