@@ -16,7 +16,8 @@
   oracle.  The GPU rounds the input and each of the seven layer outputs to BF16 (relative 2^-9
   each); eight such roundings add in quadrature to about sqrt(8) 2^-9 = 0.55% of a row's norm.
   Bound: 3% normwise per row and 0.1 x the row's RMS per element.
-* The whole path at 300,000 Gaussians, 1440x1080, three levels on sampled pixels.
+* The whole path at 300,000 Gaussians, 1440x1080, three levels on sampled pixels, with the library
+  decoder and with the fused one (4.67 M rows: about 246 tiles per persistent CTA).
 """
 import ctypes as C
 
@@ -254,3 +255,13 @@ def test_decoder_path_at_scale_sampled():
     got_F = F[:, flat].float().cpu().numpy().reshape(-1, 512)
     ref_F = O.mlp_decode(ref.out[:, ok].reshape(-1, 3), layers)
     assert_decoder_close(got_F, ref_F, "decoded features")
+    # the fused tensor-core decoder over the same 4.67 M rows (about 246 tiles per persistent CTA,
+    # output offsets past 2^31 elements): the same sampled rows within the same bars
+    fr_fused = DecoderFrame(ds, torch.as_tensor(lat), dec, cam, block_rows=L.LSV2_MLP_FUSED)
+    fr_fused.frame.coeff.copy_(fr.frame.coeff)
+    F2 = torch.full_like(F, float("nan"))
+    fr_fused.decode(F2)
+    fr_fused.check()
+    got_F2 = F2[:, flat].float().cpu().numpy().reshape(-1, 512)
+    assert_decoder_close(got_F2, ref_F, "decoded features (fused kernel)")
+    assert not torch.isnan(F2[:, -1]).any()   # the last row of every level was written
