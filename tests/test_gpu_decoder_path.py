@@ -11,7 +11,7 @@
   to the oracle bit for bit: widths of 16 mod 32 (the epilogue's last piece is 16 columns), a
   last layer cut into parts of 256 and 144 outputs, a single layer, an input of 24 columns, and the
   workload's seven layers over enough rows that every CTA of the persistent grid runs several
-  tile pairs (with a ragged tail and the BF16 input).
+  tiles (with a ragged tail and the BF16 input).
 * lsv2_mlp_decode with the random decoder of the workload: within the BF16 bound of the FP64
   oracle.  The GPU rounds the input and each of the seven layer outputs to BF16 (relative 2^-9
   each); eight such roundings add in quadrature to about sqrt(8) 2^-9 = 0.55% of a row's norm.
@@ -140,7 +140,7 @@ def run_mlp(layers, x, block_rows=0, x_dtype=torch.float32):
     ((8, 48, 80, 400), 4, 2, 3 * 1024 + 77),         # widths of 16 mod 32; last layer 256 + 144
     ((8, 64), 4, 2, 1000),                           # one layer: input straight to output
     ((24, 256, 256, 512), 2, 2, 2 * 1024 + 5),       # input of 24 columns, zero-padded to 32
-    ((8, 16, 32, 64, 128, 256, 256, 512), 2, 1, 148 * 128 * 5 + 77),   # several tile pairs per CTA
+    ((8, 16, 32, 64, 128, 256, 256, 512), 2, 1, 148 * 128 * 5 + 77),   # several tiles per CTA
 ])
 def test_mlp_fused_exact_on_integers(widths, fan_in, x_max, rows):
     rng = np.random.default_rng(24)
