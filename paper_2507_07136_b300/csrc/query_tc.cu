@@ -299,9 +299,9 @@ __global__ void __launch_bounds__(NT, 512 / NT) query_tc_kernel(QueryTcArgs a)
 // tile's MMA into one of ng TMEM accumulators; the remaining warps form ng epilogue warpgroups
 // (ng = 3 for accumulators of up to 128 columns, else 2), tile i going to accumulator i % ng and
 // warpgroup i % ng, so each accumulator's phases are consumed in order by one warpgroup.  The
-// epilogue releases the W stage once it has read its pixel rows (for |F|^2) and the accumulator
-// once its TMEM loads are done, through mbarriers, so tiles overlap: no block-wide barrier per
-// tile.  W is addressed as rows of 64
+// W stage is released by the completion of the MMA that read it (tcgen05.commit), the accumulator
+// by its epilogue once the TMEM loads are done, through mbarriers, so tiles overlap: no
+// block-wide barrier per tile.  W is addressed as rows of 64
 // BF16 (row = view offset + level * P_v + pixel); a level's ragged last tile loads rows of the
 // next level (or zeros past the end), whose results are not stored.
 
@@ -309,16 +309,13 @@ constexpr int kPStages = 8;
 // epilogue warpgroups (= TMEM accumulators) for accumulators of `bufcols` columns
 __host__ __device__ constexpr int pipe_groups(uint32_t bufcols) { return bufcols <= 128 ? 3 : 2; }
 
-// per accumulator two warpgroups (splitting |F|^2 and the query chunks) when there are at least
-// two 8-query chunks and two accumulators, else one
+// per accumulator two warpgroups (splitting the query chunks) when there are at least two 8-query
+// chunks and two accumulators, else one
 __host__ __device__ constexpr int pipe_split(int ng, int nch) { return ng == 2 && nch >= 2 ? 2 : 1; }
 
 __host__ __device__ constexpr size_t pipe_smem_bytes(int npad, int ntp)
 {
-    // + the split epilogue's exchange: |F|^2 halves [accumulator][parity][half][row] and go-on
-    // flags [accumulator][parity][warp]
-    return 1024 + (size_t)kPStages * kM * 128 + (size_t)npad * 128 + (((size_t)ntp * 4 + 15) & ~size_t(15)) + 256 +
-           2 * 2 * 2 * kM * 4 + 2 * 2 * 8 * 4;
+    return 1024 + (size_t)kPStages * kM * 128 + (size_t)npad * 128 + (((size_t)ntp * 4 + 15) & ~size_t(15)) + 256;
 }
 
 // Bounded wait on a barrier phase: false once the CTA's abort flag is up, or when the phase is
@@ -338,15 +335,12 @@ __device__ __forceinline__ bool pipe_wait(uint32_t bar, uint32_t parity, volatil
     }
 }
 
-// Named barrier of the 256 threads of one accumulator's two epilogue warpgroups.
-__device__ __forceinline__ void pair_sync(int id) { asm volatile("bar.sync %0, 256;" ::"r"(id) : "memory"); }
-
 // NB: TMEM accumulators; WPA: epilogue warpgroups per accumulator (template parameters, so that
-// the per-tile ring and phase arithmetic divides by constants).  With WPA = 2 the two warpgroups
-// of an accumulator each sum the squares of 32 of its 64 factor columns, exchange the halves
-// through shared memory (a named barrier per tile) and take alternate 8-query chunks.  Both take
-// the same decision to go on or stop at every tile (from the flags both published before the
-// barrier), so neither can be left waiting at the barrier.
+// the per-tile ring and phase arithmetic divides by constants).  With WPA = 2 both warpgroups of
+// an accumulator form |F|^2 from all 64 factor columns themselves (the same two 32-term sums in the
+// same order, so the same value) and take alternate 8-query chunks: no exchange between them and
+// no barrier per tile (sharing the halves through shared memory behind a named barrier measured
+// 0.251 against 0.212 ms at 32 queries).
 
 template <int NB, int WPA>
 __global__ void __launch_bounds__(64 + 128 * NB * WPA, 1)
@@ -366,8 +360,6 @@ __global__ void __launch_bounds__(64 + 128 * NB * WPA, 1)
     uint64_t* t_empty = m_full + 4;          // [4] accumulator b has been read (4 WPA warps)
     volatile int* abort = reinterpret_cast<volatile int*>(t_empty + 4);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(t_empty + 5);
-    float* xpart = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(bar) + 256);   // [2][2][2][kM]
-    volatile int* xok = reinterpret_cast<volatile int*>(xpart + 2 * 2 * 2 * kM);      // [2][2][8]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int lev = blockIdx.y;
     const uint32_t bufcols = tmem_cols(a.npad);
@@ -474,36 +466,15 @@ __global__ void __launch_bounds__(64 + 128 * NB * WPA, 1)
             const int b = i % nb;
             const uint32_t trow = tmem + (uint32_t)b * bufcols + ((uint32_t)(q4 * 32) << 16);
             const bool ok = __all_sync(0xffffffffu, pipe_wait(tc::smem_u32(m_full + b), (uint32_t)((i / nb) & 1), abort, a.wait_ns));
+            if (!ok) break;
+            tc::fence_after();
             float n2;
-            if constexpr (WPA == 1) {
-                if (!ok) break;
-                tc::fence_after();
+            {
                 uint32_t y0[32], y1[32];
                 tc::tmem_ld32(trow, y0);
                 tc::tmem_ld32(trow + 32u, y1);
                 tc::tmem_wait_ld();
                 n2 = chol_norm2(y0, y1);
-            } else {
-                // each member sums the squares of its 32 factor columns; the halves meet in shared memory
-                const int par = (i / nb) & 1;
-                float h = 0.0f;
-                if (ok) {
-                    tc::fence_after();
-                    uint32_t y[32];
-                    tc::tmem_ld32(trow + (uint32_t)(32 * m), y);
-                    tc::tmem_wait_ld();
-                    h = sumsq32(y);
-                }
-                float* xp = xpart + ((size_t)(g * 2 + par) * 2) * kM;
-                volatile int* xf = xok + (g * 2 + par) * 8;
-                xp[m * kM + row] = h;
-                if (lane == 0) xf[m * 4 + q4] = ok ? 1 : 0;
-                pair_sync(1 + g);
-                bool go = true;
-#pragma unroll
-                for (int w = 0; w < 8; ++w) go = go && xf[w] != 0;
-                if (!go) break;
-                n2 = xp[row] + xp[kM + row];
             }
             const float nf = sqrtf(fmaxf(n2, 0.0f));
             const float kneg = nf < 1e-12f ? 0.0f : -a.tau / nf;
