@@ -34,8 +34,14 @@ def default_limit_after():
 def expire_then_recover(fr, run, outputs, inexact=()):
     """run() once with the default limit (the reference), once with limit 0 (must report
     LSV2_ERR_TIMEOUT and return), once more with the default limit on the same buffers (must
-    equal the reference bit for bit; the outputs listed in `inexact`, sums of atomic additions in
-    no fixed order, to 1e-6 relative)."""
+    equal the reference bit for bit, except the outputs listed in `inexact`).
+
+    Those are sums of FP32 atomic additions in no fixed order (the decode adjoint's loss: one per
+    epilogue warp, eight per persistent CTA, one CTA per SM): each addition rounds to within 2^-24
+    of its running sum, so two orders of n partial sums differ by at most n 2^-24 sum|partial|.  For a sum of positive partials (a loss) that is n 2^-24 of the value;
+    where partials of either sign cancel, the bound is taken as 1e-4 of the largest entry, 30x the
+    largest difference seen between runs and far below what a lost or stale partial would leave
+    (about 1/n of the magnitude)."""
     fr.status.zero_()
     run()
     fr.check()
@@ -55,7 +61,11 @@ def expire_then_recover(fr, run, outputs, inexact=()):
     fr.check()
     for n, (o, r) in enumerate(zip(outputs, ref)):
         if n in inexact:
-            assert torch.allclose(o, r, rtol=1e-6, atol=1e-12)
+            if bool((r >= 0).all()):
+                n = 8 * torch.cuda.get_device_properties(0).multi_processor_count
+                assert torch.allclose(o, r, rtol=n * 2.0 ** -24, atol=0.0)
+            else:
+                assert float((o - r).abs().max()) <= 1e-4 * float(r.abs().max())
         else:
             assert torch.equal(o, r)
 
